@@ -1,0 +1,209 @@
+/* dppt.h -- C ABI of the GB300 (sm_103a) differentiable polarized path tracer.
+ *
+ * The library computes, on one GPU, the polarized Monte Carlo image I(pi) of a
+ * scene and the vector-Jacobian product dg/dpi = (dI/dpi)^T dg/dI needed to
+ * minimise g(I(pi)) by gradient descent (problem statement, Sec. 3.1, Eq. 1).
+ * Light transport is the rendering equation (Eq. 2) with radiance replaced by
+ * Stokes vectors and BSDF values by 4x4 Mueller matrices (Sec. 3.3).  The
+ * gradient is computed with path replay and cached suffix replay (Sec. 4.3,
+ * Fig. 2): no Mueller matrix is ever inverted.
+ *
+ * Conventions for every call:
+ *   - pointers named in dppt_scene_desc are HOST memory, read during the call
+ *     and copied; everything else (params, grads, images) is DEVICE memory on
+ *     the context's device, owned by the caller.
+ *   - rendering calls are asynchronous on the given cudaStream_t (NULL = the
+ *     legacy default stream); their status reports argument validation and
+ *     launch errors only.  Device-side failures (a bounded wait that gave up,
+ *     a corrupted BVH stack) set a status word read by dppt_sync_status().
+ *   - no call throws; each returns a dppt_status and, on failure, leaves a
+ *     message for dppt_last_error().
+ *   - a context may grow its device workspace on a call that needs more than
+ *     before; calls made after one warm-up call with the same job shapes
+ *     allocate nothing and may be captured in a CUDA graph.
+ *   - images are float32 [angle][height][width][channel=3][stokes=4], angle
+ *     count 1 when the job has no camera filter; pixel (0,0) is the top-left.
+ */
+#ifndef DPPT_H
+#define DPPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int dppt_status;
+enum {
+    DPPT_OK = 0,
+    DPPT_ERR_INVALID_ARG = -1,
+    DPPT_ERR_OUT_OF_MEMORY = -2,
+    DPPT_ERR_CUDA = -3,
+    DPPT_ERR_TIMEOUT = -4,
+    DPPT_ERR_UNSUPPORTED = -5,
+    DPPT_ERR_DEVICE = -6
+};
+
+/* Optical elements (Sec. 3.3 and the case analysis of Sec. 4.1): ideal
+ * depolarizer, Fresnel dielectric, conductor (complex index) and dielectric
+ * GGX pBRDFs, thin linear-polarizer and retarder sheets; EMITTER marks the
+ * black triangles of a quad light. */
+enum {
+    DPPT_MAT_DIFFUSE = 0,
+    DPPT_MAT_SMOOTH_DIELECTRIC = 1,
+    DPPT_MAT_CONDUCTOR_GGX = 2,
+    DPPT_MAT_PLASTIC_GGX = 3,
+    DPPT_MAT_POLARIZER_SHEET = 4,
+    DPPT_MAT_RETARDER_SHEET = 5,
+    DPPT_MAT_EMITTER = 6
+};
+
+/* Camera filter stack applied in the sensor frame: none, a linear polarizer
+ * P(theta), or a quarter-wave plate Q(pi/2, 0) followed by P(theta). */
+enum { DPPT_FILTER_NONE = 0, DPPT_FILTER_POLARIZER = 1, DPPT_FILTER_QWP_POLARIZER = 2 };
+
+/* Kernel schedule chosen by the autotuner (or set by the caller). */
+enum { DPPT_SCHED_GRID = 0, DPPT_SCHED_PERSISTENT = 1 };
+
+typedef struct dppt_ctx dppt_ctx;
+typedef struct dppt_scene dppt_scene;
+
+typedef struct {
+    int32_t type;          /* DPPT_MAT_* */
+    int32_t albedo_tex;    /* 3-channel texture index (tint / diffuse albedo), -1 = white */
+    int32_t rough_tex;     /* 1-channel GGX roughness texture (alpha), required for GGX types */
+    int32_t ior_index;     /* index into params.ior (dielectrics), -1 otherwise */
+    int32_t sheet_index;   /* index into params.sheet (sheet axis angle), -1 otherwise */
+    float eta_re, eta_im;  /* conductor complex index of refraction (constant) */
+    float t1[3], t2[3];    /* sheet axis basis: axis = cos(a) t1 + sin(a) t2 */
+    float retard;          /* retarder sheet retardance (radians) */
+    float emission;        /* constant unpolarized emission of the surface (both sides) */
+} dppt_material;
+
+typedef struct {
+    int64_t num_vertices;
+    const float* vertices;          /* [V][3] */
+    const float* uvs;               /* [V][2] or NULL */
+    int64_t num_triangles;
+    const int32_t* triangles;       /* [F][3], normal = (v1-v0) x (v2-v0) */
+    const int32_t* tri_material;    /* [F] */
+    const int32_t* tri_light;       /* [F] quad-light index or -1 */
+    int64_t num_spheres;
+    const float* spheres;           /* [S][4] centre, radius */
+    const int32_t* sphere_material; /* [S] */
+    int32_t num_materials;
+    const dppt_material* materials;
+    int32_t num_lights;
+    const float* lights;            /* [L][9] parallelogram o, e1, e2; emits toward e1 x e2 */
+    int32_t num_textures;
+    const int64_t* textures;        /* [T][4] float offset into params.tex, width, height, channels */
+    int64_t tex_size;               /* floats in params.tex */
+    int32_t num_cameras;
+    const float* cameras;           /* [C][10] origin, target, up, vertical fov in degrees */
+    int32_t num_ior;                /* length of params.ior */
+    int32_t num_sheets;             /* length of params.sheet */
+    float ray_eps;                  /* spawn offset along the geometric normal (scene units) */
+} dppt_scene_desc;
+
+/* One render job: a camera view rendered at width x height with spp paths per
+ * pixel and at most max_depth surface vertices per path, seen through the
+ * camera filter at num_angles polarizer angles params.theta[theta_offset + a].
+ * Path p = pixel * spp + sample draws its randoms from Philox4x64-10 with key
+ * (seed ^ pass * 0x9E3779B97F4A7C15, stream) and counter (p, vertex, 0, 0);
+ * the replay regenerates exactly the same stream (Sec. 3.2, phase 3).  Use a
+ * different pass (or seed) for the decorrelated adjoint paths (phase 2). */
+typedef struct {
+    int32_t camera, width, height, spp, max_depth;
+    int32_t filter, num_angles, theta_offset;
+    uint64_t seed, stream;
+    int32_t pass;
+    int32_t reserved;
+    int64_t out_offset;     /* float offset of this job's block in the image buffers */
+    uint32_t* path_sig;     /* optional device output, one signature per path (debug), or NULL */
+} dppt_job;
+
+/* Differentiable parameters pi (device, float32): texture texels, indices of
+ * refraction, quad-light Stokes radiance [L][3][4] in the emitter frame, sheet
+ * axis angles, camera-filter angles. */
+typedef struct {
+    const float* tex;
+    const float* ior;
+    const float* le;
+    const float* sheet;
+    const float* theta;
+} dppt_params;
+
+/* Gradient accumulators (device, float32, same shapes as dppt_params); the
+ * adjoint ADDS into them.  Any pointer may be NULL to skip that group. */
+typedef struct {
+    float* tex;
+    float* ior;
+    float* le;
+    float* sheet;
+    float* theta;
+} dppt_grads;
+
+typedef struct {
+    int32_t schedule;       /* DPPT_SCHED_* */
+    int32_t block_size;     /* threads per block: 64, 128, 256 or 512 */
+    int32_t blocks_per_sm;  /* persistent schedule: resident blocks per SM (0 = occupancy maximum) */
+    int32_t reserved;
+} dppt_launch;
+
+/* Create a context on CUDA device `device` (made current for the call). */
+dppt_status dppt_create(dppt_ctx** out, int device);
+void dppt_destroy(dppt_ctx* ctx);
+/* Message of the last failed call on this context; owned by the context. */
+const char* dppt_last_error(const dppt_ctx* ctx);
+/* Library version string, static storage. */
+const char* dppt_version(void);
+
+/* Validate the scene, build its BVH (binned SAH) on the host and copy
+ * geometry, materials, lights and cameras to the device.  The scene is owned
+ * by the library until dppt_scene_destroy.  Errors: INVALID_ARG for bad
+ * counts, indices or degenerate lights; OUT_OF_MEMORY; CUDA. */
+dppt_status dppt_scene_upload(dppt_ctx* ctx, const dppt_scene_desc* desc, dppt_scene** out);
+void dppt_scene_destroy(dppt_scene* scene);
+/* info[0] = BVH nodes, [1] = triangles, [2] = spheres, [3] = device bytes, [4] = BVH depth */
+dppt_status dppt_scene_info(const dppt_scene* scene, int64_t info[5]);
+
+/* Phase 1 of PRB (Sec. 3.2): the primal image.  For each job, writes its
+ * [num_angles][H][W][3][4] block of `image` (device, caller-owned) at
+ * job.out_offset; the whole block is overwritten.  All jobs of the call run
+ * in one launch (persistent or grid schedule). */
+dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* jobs, int32_t njobs,
+                               const dppt_params* params, float* image, void* stream);
+
+/* Phases 2+3 of PRB with cached suffix replay (Sec. 4.3, Fig. 2): for every
+ * path of every job, a decorrelated primal pass stores the per-vertex
+ * emission E_i and transport factor W_i in thread-local arrays, a backward
+ * fold turns them into suffixes L[i] = E_i + W_i L[i+1], and the replay
+ * regenerates the same path, differentiates the local vertex only and
+ * multiplies by the cached L[i+1].  d_image holds dg/dI in the image layout;
+ * gradients are ADDED into `grads`. */
+dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* jobs, int32_t njobs,
+                                const dppt_params* params, const float* d_image, const dppt_grads* grads,
+                                void* stream);
+
+/* Device workspace (bytes) the jobs need beyond the caller's buffers. */
+dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int32_t njobs, size_t* bytes);
+
+/* Schedule for subsequent launches (the autotuner's choice). */
+dppt_status dppt_set_launch(dppt_ctx* ctx, const dppt_launch* launch);
+dppt_status dppt_get_launch(const dppt_ctx* ctx, dppt_launch* launch);
+
+/* Per-thread local cache bytes and registers of the adjoint kernel used for
+ * max_depth, and the resident threads per SM for the current launch shape:
+ * out[0] = local bytes/thread, out[1] = registers/thread, out[2] = threads/SM,
+ * out[3] = SMs. */
+dppt_status dppt_adjoint_footprint(const dppt_ctx* ctx, int32_t max_depth, int64_t out[4]);
+
+/* Synchronise `stream` and return (then clear) the device status word:
+ * DPPT_OK, DPPT_ERR_DEVICE (a traversal stack overflow) or DPPT_ERR_TIMEOUT. */
+dppt_status dppt_sync_status(dppt_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPPT_H */

@@ -1,0 +1,261 @@
+"""Python binding of the C ABI: contexts, scenes, render_primal / render_adjoint and
+the torch.autograd.Function that puts render_adjoint behind backward().
+
+PyTorch only provides device memory and streams here; every step of the path
+runs in the CUDA library.  Names follow the paper: the primal image I(pi), its
+adjoint dg/dI and the parameter gradient dg/dpi (Sec. 3.1, Eq. 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from .scenegen import FILTER_NONE
+
+
+def _check(ctx_handle, status: int, what: str):
+    if status != L.DPPT_OK:
+        msg = L.load().dppt_last_error(ctx_handle)
+        raise L.DpptError(f"{what} failed ({L.STATUS_NAMES.get(status, status)}): "
+                          f"{msg.decode() if msg else ''}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return ctypes.c_void_p(t.data_ptr()) if t.numel() > 0 else None
+    return t
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A dppt context on one CUDA device (owns its workspace and status word)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = L.load()
+        self.device = device
+        h = ctypes.c_void_p()
+        st = self.lib.dppt_create(ctypes.byref(h), device)
+        if st != L.DPPT_OK:
+            raise L.DpptError(f"dppt_create failed ({L.STATUS_NAMES.get(st, st)})")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dppt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_launch(self, schedule: int, block_size: int, blocks_per_sm: int = 0):
+        l = L.Launch(schedule, block_size, blocks_per_sm, 0)
+        _check(self.h, self.lib.dppt_set_launch(self.h, ctypes.byref(l)), "dppt_set_launch")
+
+    def get_launch(self) -> tuple[int, int, int]:
+        l = L.Launch()
+        _check(self.h, self.lib.dppt_get_launch(self.h, ctypes.byref(l)), "dppt_get_launch")
+        return l.schedule, l.block_size, l.blocks_per_sm
+
+    def adjoint_footprint(self, max_depth: int) -> dict:
+        out = (ctypes.c_int64 * 4)()
+        _check(self.h, self.lib.dppt_adjoint_footprint(self.h, max_depth, out), "dppt_adjoint_footprint")
+        return {"local_bytes_per_thread": out[0], "registers": out[1], "threads_per_sm": out[2], "sms": out[3]}
+
+    def sync_status(self, stream=None):
+        _check(self.h, self.lib.dppt_sync_status(self.h, _stream_ptr(stream)), "dppt_sync_status")
+
+
+class GpuScene:
+    """A scene uploaded to the device (BVH built by the library at upload)."""
+
+    def __init__(self, ctx: Context, scene):
+        self.ctx = ctx
+        self.scene = scene
+        keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(a, dt)
+            keep.append(a)
+            return a
+
+        verts = arr(scene.verts, np.float32)
+        uvs = arr(scene.uvs, np.float32)
+        tris = arr(scene.tris, np.int32)
+        tmat = arr(scene.tri_mat, np.int32)
+        tlight = arr(scene.tri_light, np.int32)
+        sph = arr(scene.spheres, np.float32)
+        smat = arr(scene.sph_mat, np.int32)
+        mats = (L.Material * len(scene.materials))()
+        for i, m in enumerate(scene.materials):
+            mats[i] = L.Material(m.type, m.albedo_tex, m.rough_tex, m.ior_index, m.sheet_index, m.eta_re, m.eta_im,
+                                 (ctypes.c_float * 3)(*m.t1), (ctypes.c_float * 3)(*m.t2), m.retard, m.emission)
+        lights = arr(scene.lights, np.float32)
+        texd = arr(scene.tex_desc, np.int64)
+        cams = arr(scene.cameras, np.float32)
+        p = scene.params()
+        P = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a.size else None
+        d = L.SceneDesc(len(verts), P(verts), P(uvs), len(tris), P(tris), P(tmat), P(tlight),
+                        len(sph), P(sph), P(smat), len(scene.materials), ctypes.cast(mats, ctypes.c_void_p),
+                        len(lights), P(lights), len(texd), P(texd), int(p["tex"].size),
+                        len(cams), P(cams), len(scene.ior), len(scene.sheet), float(scene.ray_eps()))
+        h = ctypes.c_void_p()
+        _check(ctx.h, ctx.lib.dppt_scene_upload(ctx.h, ctypes.byref(d), ctypes.byref(h)), "dppt_scene_upload")
+        self.h = h
+        del keep
+
+    def info(self) -> dict:
+        out = (ctypes.c_int64 * 5)()
+        _check(self.ctx.h, self.ctx.lib.dppt_scene_info(self.h, out), "dppt_scene_info")
+        return {"bvh_nodes": out[0], "triangles": out[1], "spheres": out[2], "device_bytes": out[3], "bvh_depth": out[4]}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.dppt_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class JobBatch:
+    """Jobs packed for the C ABI, with image offsets and the filter-angle vector."""
+    jobs: list
+    c_jobs: object
+    offsets: list
+    image_floats: int
+    theta: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return len(self.jobs)
+
+
+def pack_jobs(jobs, path_sig: torch.Tensor | None = None) -> JobBatch:
+    """Lay the jobs' images out back to back and collect their filter angles."""
+    arr = (L.Job * len(jobs))()
+    off, toff, offsets, thetas = 0, 0, [], []
+    sig_off = 0
+    for i, j in enumerate(jobs):
+        nang = j.num_angles
+        arr[i] = L.Job(j.camera, j.width, j.height, j.spp, j.max_depth, j.filter,
+                       nang if j.filter != FILTER_NONE else 1, toff if j.filter != FILTER_NONE else 0,
+                       j.seed, j.stream, j.pass_id, 0, off, None)
+        if path_sig is not None:
+            arr[i].path_sig = path_sig.data_ptr() + 4 * sig_off
+            sig_off += j.num_paths
+        offsets.append(off)
+        off += nang * j.width * j.height * 12
+        if j.filter != FILTER_NONE:
+            thetas += list(j.thetas)
+            toff += nang
+    return JobBatch(list(jobs), arr, offsets, off, np.array(thetas if thetas else [0.0], np.float64))
+
+
+def device_params(scene, batch: JobBatch | None = None, params: dict | None = None, device="cuda") -> dict:
+    """Float32 device copies of the differentiable parameters {tex, ior, le, sheet, theta}."""
+    p = dict(scene.params() if params is None else params)
+    out = {k: torch.as_tensor(np.asarray(p[k], np.float64).ravel(), dtype=torch.float32, device=device)
+           for k in ("tex", "ior", "le", "sheet")}
+    th = p.get("theta", batch.theta if batch is not None else np.zeros(1))
+    out["theta"] = torch.as_tensor(np.asarray(th, np.float64).ravel(), dtype=torch.float32, device=device)
+    return out
+
+
+def _c_params(p: dict) -> L.Params:
+    return L.Params(_ptr(p["tex"]), _ptr(p["ior"]), _ptr(p["le"]), _ptr(p["sheet"]), _ptr(p["theta"]))
+
+
+def render_primal(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict, image: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """Phase 1: the primal Stokes images of all jobs, in one launch."""
+    if image is None:
+        image = torch.empty(batch.image_floats, dtype=torch.float32, device=params["tex"].device)
+    cp = _c_params(params)
+    _check(ctx.h, ctx.lib.dppt_render_primal(ctx.h, gs.h, batch.c_jobs, batch.n, ctypes.byref(cp), _ptr(image),
+                                             _stream_ptr(stream)), "dppt_render_primal")
+    return image
+
+
+def zero_grads(params: dict) -> dict:
+    return {k: torch.zeros_like(v) for k, v in params.items()}
+
+
+def render_adjoint(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict, d_image: torch.Tensor,
+                   grads: dict | None = None, stream=None) -> dict:
+    """Phases 2+3 (cached suffix replay): ADDS dg/dpi into `grads` and returns it."""
+    if grads is None:
+        grads = zero_grads(params)
+    cp = _c_params(params)
+    cg = L.Grads(_ptr(grads.get("tex")), _ptr(grads.get("ior")), _ptr(grads.get("le")), _ptr(grads.get("sheet")),
+                 _ptr(grads.get("theta")))
+    _check(ctx.h, ctx.lib.dppt_render_adjoint(ctx.h, gs.h, batch.c_jobs, batch.n, ctypes.byref(cp), _ptr(d_image),
+                                              ctypes.byref(cg), _stream_ptr(stream)), "dppt_render_adjoint")
+    return grads
+
+
+def image_views(batch: JobBatch, image: torch.Tensor) -> list:
+    """Per-job views [angles][H][W][3][4] of a packed image buffer."""
+    out = []
+    for j, off in zip(batch.jobs, batch.offsets):
+        n = j.num_angles * j.width * j.height * 12
+        out.append(image[off:off + n].view(j.num_angles, j.height, j.width, 3, 4))
+    return out
+
+
+class PolarizedRender(torch.autograd.Function):
+    """I = render(pi) with dI^T-vector products from render_adjoint (cached suffix replay).
+
+    forward(ctx_obj, gscene, batch, adjoint_batch, tex, ior, le, sheet, theta) -> packed image.
+    The adjoint uses `adjoint_batch` (same jobs with a different pass id: decorrelated
+    paths, PRB phase 2) so that the gradient estimate is independent of the image."""
+
+    @staticmethod
+    def forward(fctx, dctx, gs, batch, adj_batch, tex, ior, le, sheet, theta):
+        params = {"tex": tex.detach(), "ior": ior.detach(), "le": le.detach(), "sheet": sheet.detach(),
+                  "theta": theta.detach()}
+        image = render_primal(dctx, gs, batch, params)
+        fctx.dctx, fctx.gs, fctx.adj_batch = dctx, gs, adj_batch
+        fctx.save_for_backward(tex, ior, le, sheet, theta)
+        return image
+
+    @staticmethod
+    def backward(fctx, d_image):
+        tex, ior, le, sheet, theta = fctx.saved_tensors
+        params = {"tex": tex.detach(), "ior": ior.detach(), "le": le.detach(), "sheet": sheet.detach(),
+                  "theta": theta.detach()}
+        grads = render_adjoint(fctx.dctx, fctx.gs, fctx.adj_batch, params, d_image.contiguous())
+        return (None, None, None, None, grads["tex"], grads["ior"], grads["le"], grads["sheet"], grads["theta"])
+
+
+def adjoint_jobs(jobs, pass_id: int = 1):
+    """Copies of the jobs with another pass id (decorrelated paths for the adjoint)."""
+    import copy
+    out = []
+    for j in jobs:
+        k = copy.copy(j)
+        k.pass_id = pass_id
+        out.append(k)
+    return out
+
+
+def radians(deg) -> float:
+    return math.radians(deg)

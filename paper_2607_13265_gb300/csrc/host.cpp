@@ -1,0 +1,705 @@
+// Host side of the C ABI: validation, binned-SAH BVH construction, scene
+// upload, workspace management and kernel launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+using namespace dppt;
+
+struct dppt_ctx {
+    int device = 0;
+    int sm_count = 1;
+    std::string err;
+    void* ws = nullptr;
+    size_t ws_size = 0;
+    unsigned* d_status = nullptr;
+    unsigned long long* d_counter = nullptr;
+    dppt_launch launch{DPPT_SCHED_GRID, 128, 0, 0};
+};
+
+struct dppt_scene {
+    dppt_ctx* ctx = nullptr;
+    DScene d{};
+    std::vector<void*> allocs;
+    int64_t bytes = 0;
+    int64_t num_nodes = 0;
+    int bvh_depth = 0;
+    int num_cameras = 0;
+    int num_textures = 0;
+    int64_t tex_size = 0;
+};
+
+namespace {
+
+const char* kVersion = "dppt 0.1 (sm_103a)";
+
+dppt_status fail(dppt_ctx* ctx, dppt_status code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+dppt_status cuda_fail(dppt_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? DPPT_ERR_OUT_OF_MEMORY : DPPT_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ BVH (binned SAH)
+struct Box {
+    float lo[3] = {INFINITY, INFINITY, INFINITY};
+    float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    void grow(const Box& b) {
+        for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], b.lo[k]); hi[k] = std::max(hi[k], b.hi[k]); }
+    }
+    void grow(const float* p) {
+        for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], p[k]); hi[k] = std::max(hi[k], p[k]); }
+    }
+    float area() const {
+        float d[3];
+        for (int k = 0; k < 3; ++k) d[k] = std::max(0.0f, hi[k] - lo[k]);
+        return 2.0f * (d[0] * d[1] + d[1] * d[2] + d[2] * d[0]);
+    }
+};
+
+struct Builder {
+    const std::vector<Box>& boxes;
+    const std::vector<float>& cen;   // [F][3]
+    std::vector<int>& order;
+    std::vector<float4> nodes;
+    float pad;
+    int max_depth = 0;
+    static constexpr int kBins = 16;
+    static constexpr int kMaxLeaf = 8;
+
+    Builder(const std::vector<Box>& b, const std::vector<float>& c, std::vector<int>& o, float p)
+        : boxes(b), cen(c), order(o), pad(p) {}
+
+    Box range_box(int b, int e) const {
+        Box r;
+        for (int i = b; i < e; ++i) r.grow(boxes[order[i]]);
+        return r;
+    }
+    static int leaf_ref(int first, int count) { return ~(first | (count << 25)); }
+
+    int alloc_node() {
+        int id = (int)(nodes.size() / 4);
+        nodes.resize(nodes.size() + 4);
+        return id;
+    }
+    void set_node(int id, const Box& l, int lref, const Box& r, int rref) {
+        auto P = [&](float v, bool low) { return low ? v - pad : v + pad; };
+        nodes[4 * id + 0] = make_float4(P(l.lo[0], true), P(l.hi[0], false), P(l.lo[1], true), P(l.hi[1], false));
+        nodes[4 * id + 1] = make_float4(P(r.lo[0], true), P(r.hi[0], false), P(r.lo[1], true), P(r.hi[1], false));
+        nodes[4 * id + 2] = make_float4(P(l.lo[2], true), P(l.hi[2], false), P(r.lo[2], true), P(r.hi[2], false));
+        float4 n3;
+        std::memcpy(&n3.x, &lref, 4);
+        std::memcpy(&n3.y, &rref, 4);
+        n3.z = 0.0f; n3.w = 0.0f;
+        nodes[4 * id + 3] = n3;
+    }
+
+    // choose a split of [b, e); returns the split position or -1 for a leaf
+    int split(int b, int e, const Box& nb) {
+        int n = e - b;
+        Box cb;
+        for (int i = b; i < e; ++i) cb.grow(&cen[3 * order[i]]);
+        int axis = 0;
+        for (int k = 1; k < 3; ++k) if (cb.hi[k] - cb.lo[k] > cb.hi[axis] - cb.lo[axis]) axis = k;
+        float ext = cb.hi[axis] - cb.lo[axis];
+        if (!(ext > 0.0f)) {
+            if (n <= kMaxLeaf) return -1;
+            return b + n / 2;   // coincident centroids: split by count
+        }
+        float best_cost = INFINITY;
+        int best_axis = -1, best_bin = -1;
+        for (int ax = 0; ax < 3; ++ax) {
+            float lo = cb.lo[ax], w = cb.hi[ax] - cb.lo[ax];
+            if (!(w > 0.0f)) continue;
+            Box bb[kBins];
+            int cnt[kBins] = {0};
+            for (int i = b; i < e; ++i) {
+                int t = order[i];
+                int k = std::min(kBins - 1, (int)((cen[3 * t + ax] - lo) / w * kBins));
+                cnt[k]++;
+                bb[k].grow(boxes[t]);
+            }
+            float ra[kBins];
+            int rn[kBins];
+            Box acc;
+            int an = 0;
+            for (int k = kBins - 1; k > 0; --k) { acc.grow(bb[k]); an += cnt[k]; ra[k] = acc.area(); rn[k] = an; }
+            acc = Box();
+            an = 0;
+            for (int k = 0; k < kBins - 1; ++k) {
+                acc.grow(bb[k]); an += cnt[k];
+                if (an == 0 || rn[k + 1] == 0) continue;
+                float cost = acc.area() * an + ra[k + 1] * rn[k + 1];
+                if (cost < best_cost) { best_cost = cost; best_axis = ax; best_bin = k; }
+            }
+        }
+        float leaf_cost = nb.area() * n;
+        if (best_axis < 0 || (best_cost * 1.0f + nb.area() * 1.0f >= leaf_cost && n <= kMaxLeaf)) {
+            if (n <= kMaxLeaf) return -1;
+            if (best_axis < 0) return b + n / 2;
+        }
+        float lo = cb.lo[best_axis], w = cb.hi[best_axis] - cb.lo[best_axis];
+        auto mid = std::partition(order.begin() + b, order.begin() + e, [&](int t) {
+            int k = std::min(kBins - 1, (int)((cen[3 * t + best_axis] - lo) / w * kBins));
+            return k <= best_bin;
+        });
+        int m = (int)(mid - order.begin());
+        if (m == b || m == e) return b + n / 2;
+        return m;
+    }
+
+    // builds the subtree over [b, e) and returns its reference and box
+    int build(int b, int e, Box& out_box, int depth) {
+        max_depth = std::max(max_depth, depth);
+        Box nb = range_box(b, e);
+        out_box = nb;
+        int n = e - b;
+        int m = n <= 2 ? -1 : split(b, e, nb);
+        if (n <= 2 && n <= kMaxLeaf) m = -1;
+        if (m < 0) {
+            if (n > kMaxLeaf) m = b + n / 2;
+            else return leaf_ref(b, n);
+        }
+        int id = alloc_node();
+        Box lb, rb;
+        int l = build(b, m, lb, depth + 1);
+        int r = build(m, e, rb, depth + 1);
+        set_node(id, lb, l, rb, r);
+        return id;
+    }
+};
+
+template <class T>
+bool upload(dppt_scene* s, const T* host, size_t count, const T** dst, cudaError_t& err) {
+    *dst = nullptr;
+    if (count == 0) return true;
+    void* p = nullptr;
+    err = cudaMalloc(&p, count * sizeof(T));
+    if (err != cudaSuccess) return false;
+    s->allocs.push_back(p);
+    s->bytes += (int64_t)(count * sizeof(T));
+    err = cudaMemcpy(p, host, count * sizeof(T), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return false;
+    *dst = static_cast<const T*>(p);
+    return true;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int red_mode(int spp) {
+    if (is_pow2(spp) && spp <= 32) return 0;
+    if (is_pow2(spp)) return 1;
+    return 2;
+}
+
+struct JobPlan {
+    int64_t npix;
+    int nang;
+    bool filtered;
+    size_t ws_a = 0, ws_b = 0;   // workspace offsets (bytes) of raw/dS and S_adj
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+dppt_status check_jobs(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
+                       const dppt_params* p, bool adjoint, std::vector<JobPlan>& plan, size_t& ws_bytes) {
+    if (njobs < 0 || (njobs > 0 && !jobs)) return fail(ctx, DPPT_ERR_INVALID_ARG, "jobs: null or negative count");
+    if (!p) return fail(ctx, DPPT_ERR_INVALID_ARG, "params is null");
+    if (s->tex_size > 0 && !p->tex) return fail(ctx, DPPT_ERR_INVALID_ARG, "params.tex is null");
+    if (s->d.num_ior > 0 && !p->ior) return fail(ctx, DPPT_ERR_INVALID_ARG, "params.ior is null");
+    if (s->d.num_lights > 0 && !p->le) return fail(ctx, DPPT_ERR_INVALID_ARG, "params.le is null");
+    if (s->d.num_sheets > 0 && !p->sheet) return fail(ctx, DPPT_ERR_INVALID_ARG, "params.sheet is null");
+    plan.assign(njobs, JobPlan{});
+    ws_bytes = 0;
+    for (int i = 0; i < njobs; ++i) {
+        const dppt_job& j = jobs[i];
+        char buf[160];
+        auto bad = [&](const char* what) {
+            std::snprintf(buf, sizeof buf, "job %d: %s", i, what);
+            return fail(ctx, DPPT_ERR_INVALID_ARG, buf);
+        };
+        if (j.camera < 0 || j.camera >= s->num_cameras) return bad("camera index out of range");
+        if (j.width < 1 || j.height < 1 || (int64_t)j.width * j.height > (1LL << 31) - 1) return bad("bad image size");
+        if (j.spp < 1 || j.spp > (1 << 20)) return bad("spp out of range [1, 2^20]");
+        if (j.max_depth < 1 || j.max_depth > 64) return bad("max_depth out of range [1, 64]");
+        if (j.filter < DPPT_FILTER_NONE || j.filter > DPPT_FILTER_QWP_POLARIZER) return bad("unknown filter");
+        if (j.out_offset < 0) return bad("negative out_offset");
+        if ((j.out_offset & 3) != 0) return bad("out_offset must be a multiple of 4 floats");
+        int64_t npaths = (int64_t)j.width * j.height * j.spp;
+        if (npaths > (1LL << 40)) return bad("too many paths");
+        JobPlan& q = plan[i];
+        q.npix = (int64_t)j.width * j.height;
+        q.filtered = j.filter != DPPT_FILTER_NONE;
+        q.nang = q.filtered ? j.num_angles : 1;
+        if (q.filtered) {
+            if (j.num_angles < 1 || j.num_angles > 512) return bad("num_angles out of range [1, 512]");
+            if (j.theta_offset < 0) return bad("negative theta_offset");
+            if (!p->theta) return bad("filtered job needs params.theta");
+            q.ws_a = ws_bytes;
+            ws_bytes = align256(ws_bytes + (size_t)q.npix * 12 * sizeof(float));
+            if (adjoint) {
+                q.ws_b = ws_bytes;
+                ws_bytes = align256(ws_bytes + (size_t)q.npix * 12 * sizeof(float));
+            }
+        }
+    }
+    return DPPT_OK;
+}
+
+dppt_status ensure_ws(dppt_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->ws_size) return DPPT_OK;
+    if (ctx->ws) { cudaFree(ctx->ws); ctx->ws = nullptr; ctx->ws_size = 0; }
+    cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+    if (e != cudaSuccess) { ctx->ws = nullptr; return cuda_fail(ctx, e, "workspace allocation"); }
+    ctx->ws_size = bytes;
+    return DPPT_OK;
+}
+
+LaunchCfg launch_cfg(const dppt_ctx* ctx, int which, int max_depth) {
+    LaunchCfg L;
+    L.schedule = ctx->launch.schedule;
+    L.block = ctx->launch.block_size;
+    int occ = occupancy_blocks(which, max_depth, L.block);
+    if (occ < 1) occ = 1;
+    int bps = ctx->launch.blocks_per_sm > 0 ? std::min(ctx->launch.blocks_per_sm, occ) : occ;
+    L.grid = ctx->sm_count * bps;
+    return L;
+}
+
+DParams dparams(const dppt_params* p) { return DParams{p->tex, p->ior, p->le, p->sheet, p->theta}; }
+
+}  // namespace
+
+extern "C" {
+
+const char* dppt_version(void) { return kVersion; }
+
+dppt_status dppt_create(dppt_ctx** out, int device) {
+    if (!out) return DPPT_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return DPPT_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return DPPT_ERR_CUDA;
+    dppt_ctx* c = new dppt_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&c->d_counter, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return DPPT_ERR_OUT_OF_MEMORY;
+    }
+    cudaMemset(c->d_status, 0, sizeof(unsigned));
+    cudaMemset(c->d_counter, 0, sizeof(unsigned long long));
+    *out = c;
+    return DPPT_OK;
+}
+
+void dppt_destroy(dppt_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(ctx->ws);
+    cudaFree(ctx->d_status);
+    cudaFree(ctx->d_counter);
+    delete ctx;
+}
+
+const char* dppt_last_error(const dppt_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+dppt_status dppt_scene_upload(dppt_ctx* ctx, const dppt_scene_desc* d, dppt_scene** out) {
+    if (!ctx || !d || !out) return fail(ctx, DPPT_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    const int64_t V = d->num_vertices, F = d->num_triangles, Sn = d->num_spheres;
+    if (V < 0 || F < 0 || Sn < 0 || d->num_materials < 1 || d->num_lights < 0 || d->num_textures < 0 ||
+        d->num_cameras < 1 || d->num_ior < 0 || d->num_sheets < 0 || d->tex_size < 0)
+        return fail(ctx, DPPT_ERR_INVALID_ARG, "negative count, or no material / camera");
+    if (F >= (1LL << 25)) return fail(ctx, DPPT_ERR_INVALID_ARG, "more than 2^25 triangles");
+    if ((F > 0 && (!d->vertices || !d->triangles || !d->tri_material || !d->tri_light)) ||
+        (Sn > 0 && (!d->spheres || !d->sphere_material)) || !d->materials || !d->cameras ||
+        (d->num_lights > 0 && !d->lights) || (d->num_textures > 0 && !d->textures))
+        return fail(ctx, DPPT_ERR_INVALID_ARG, "null array for a non-zero count");
+    if (!(d->ray_eps > 0.0f) || !std::isfinite(d->ray_eps)) return fail(ctx, DPPT_ERR_INVALID_ARG, "ray_eps must be > 0");
+    const int M = d->num_materials, L = d->num_lights, T = d->num_textures;
+    for (int64_t i = 0; i < 3 * F; ++i)
+        if (d->triangles[i] < 0 || d->triangles[i] >= V) return fail(ctx, DPPT_ERR_INVALID_ARG, "triangle vertex index out of range");
+    for (int64_t i = 0; i < 3 * V; ++i)
+        if (!std::isfinite(d->vertices[i])) return fail(ctx, DPPT_ERR_INVALID_ARG, "non-finite vertex");
+    for (int64_t i = 0; i < F; ++i) {
+        if (d->tri_material[i] < 0 || d->tri_material[i] >= M) return fail(ctx, DPPT_ERR_INVALID_ARG, "triangle material out of range");
+        if (d->tri_light[i] < -1 || d->tri_light[i] >= L) return fail(ctx, DPPT_ERR_INVALID_ARG, "triangle light out of range");
+    }
+    for (int64_t i = 0; i < Sn; ++i) {
+        if (d->sphere_material[i] < 0 || d->sphere_material[i] >= M) return fail(ctx, DPPT_ERR_INVALID_ARG, "sphere material out of range");
+        if (!(d->spheres[4 * i + 3] > 0.0f)) return fail(ctx, DPPT_ERR_INVALID_ARG, "sphere radius must be > 0");
+    }
+    std::vector<DTex> tex(T);
+    for (int t = 0; t < T; ++t) {
+        const int64_t* q = d->textures + 4 * t;
+        if (q[0] < 0 || q[1] < 1 || q[2] < 1 || q[3] < 1 || q[3] > 4 || q[0] + q[1] * q[2] * q[3] > d->tex_size)
+            return fail(ctx, DPPT_ERR_INVALID_ARG, "texture descriptor out of range");
+        tex[t].off = q[0]; tex[t].w = (int)q[1]; tex[t].h = (int)q[2]; tex[t].ch = (int)q[3];
+        tex[t].pad = 1;   // gradients accumulated for every texture
+    }
+    std::vector<DMat> mats(M);
+    for (int i = 0; i < M; ++i) {
+        const dppt_material& m = d->materials[i];
+        DMat& o = mats[i];
+        o.type = m.type; o.albedo_tex = m.albedo_tex; o.rough_tex = m.rough_tex; o.ior_index = m.ior_index;
+        o.sheet_index = m.sheet_index; o.eta_re = m.eta_re; o.eta_im = m.eta_im;
+        for (int k = 0; k < 3; ++k) { o.t1[k] = m.t1[k]; o.t2[k] = m.t2[k]; }
+        o.retard = m.retard; o.emission = m.emission;
+        if (m.type < DPPT_MAT_DIFFUSE || m.type > DPPT_MAT_EMITTER) return fail(ctx, DPPT_ERR_INVALID_ARG, "unknown material type");
+        if (m.albedo_tex < -1 || m.albedo_tex >= T) return fail(ctx, DPPT_ERR_INVALID_ARG, "albedo texture out of range");
+        bool ggx = m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX;
+        if (ggx && (m.rough_tex < 0 || m.rough_tex >= T)) return fail(ctx, DPPT_ERR_INVALID_ARG, "GGX material needs a roughness texture");
+        bool diel = m.type == DPPT_MAT_SMOOTH_DIELECTRIC || m.type == DPPT_MAT_PLASTIC_GGX;
+        if (diel && (m.ior_index < 0 || m.ior_index >= d->num_ior)) return fail(ctx, DPPT_ERR_INVALID_ARG, "ior_index out of range");
+        bool sheet = m.type == DPPT_MAT_POLARIZER_SHEET || m.type == DPPT_MAT_RETARDER_SHEET;
+        if (sheet && (m.sheet_index < 0 || m.sheet_index >= d->num_sheets)) return fail(ctx, DPPT_ERR_INVALID_ARG, "sheet_index out of range");
+        if (!(m.emission >= 0.0f)) return fail(ctx, DPPT_ERR_INVALID_ARG, "negative emission");
+    }
+    std::vector<DLight> lights(L);
+    for (int l = 0; l < L; ++l) {
+        const float* q = d->lights + 9 * l;
+        double e1[3] = {q[3], q[4], q[5]}, e2[3] = {q[6], q[7], q[8]};
+        double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double a = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        if (!(a > 0.0)) return fail(ctx, DPPT_ERR_INVALID_ARG, "degenerate quad light");
+        for (int k = 0; k < 3; ++k) {
+            lights[l].o[k] = q[k]; lights[l].e1[k] = q[3 + k]; lights[l].e2[k] = q[6 + k];
+            lights[l].n[k] = (float)(c[k] / a);
+        }
+        lights[l].area = (float)a;
+    }
+    std::vector<DCam> cams(d->num_cameras);
+    for (int i = 0; i < d->num_cameras; ++i) {
+        const float* q = d->cameras + 10 * i;
+        double o[3] = {q[0], q[1], q[2]}, f[3] = {q[3] - q[0], q[4] - q[1], q[5] - q[2]}, up[3] = {q[6], q[7], q[8]};
+        double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        if (!(fl > 0.0) || !(q[9] > 0.0f && q[9] < 180.0f)) return fail(ctx, DPPT_ERR_INVALID_ARG, "bad camera");
+        for (double& x : f) x /= fl;
+        double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+        double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        if (!(rl > 0.0)) return fail(ctx, DPPT_ERR_INVALID_ARG, "camera up parallel to view direction");
+        for (double& x : r) x /= rl;
+        double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+        for (int k = 0; k < 3; ++k) {
+            cams[i].org[k] = (float)o[k]; cams[i].fwd[k] = (float)f[k]; cams[i].right[k] = (float)r[k]; cams[i].up[k] = (float)u[k];
+        }
+        cams[i].tanh = (float)std::tan(0.5 * q[9] * M_PI / 180.0);
+    }
+
+    // ---- BVH over triangles
+    std::vector<Box> boxes(F);
+    std::vector<float> cen(3 * F);
+    std::vector<int> order(F);
+    float maxabs = 1.0f;
+    for (int64_t i = 0; i < F; ++i) {
+        Box b;
+        for (int k = 0; k < 3; ++k) b.grow(d->vertices + 3 * d->triangles[3 * i + k]);
+        boxes[i] = b;
+        for (int k = 0; k < 3; ++k) {
+            cen[3 * i + k] = 0.5f * (b.lo[k] + b.hi[k]);
+            maxabs = std::max(maxabs, std::max(std::fabs(b.lo[k]), std::fabs(b.hi[k])));
+        }
+        order[i] = (int)i;
+    }
+    Builder B(boxes, cen, order, maxabs * 1e-6f);
+    int depth = 0;
+    if (F > 0) {
+        Box rb;
+        int root_pos = B.alloc_node();   // node 0 is always an inner node
+        int ref = B.build(0, (int)F, rb, 1);
+        if (ref >= 0) {
+            // the tree's root becomes node 0 (its children keep their indices)
+            for (int k = 0; k < 4; ++k) B.nodes[4 * root_pos + k] = B.nodes[4 * ref + k];
+        } else {
+            // a single leaf: node 0 holds it next to an empty leaf
+            B.set_node(root_pos, rb, ref, rb, ~0);
+        }
+        depth = B.max_depth + 1;
+        if (depth >= kBvhStack) return fail(ctx, DPPT_ERR_UNSUPPORTED, "BVH deeper than the traversal stack");
+    }
+    std::vector<float4> tris(3 * F);
+    std::vector<float> tri_uv(6 * F, 0.0f);
+    for (int64_t s = 0; s < F; ++s) {
+        int t = order[s];
+        const float* v0 = d->vertices + 3 * d->triangles[3 * t];
+        const float* v1 = d->vertices + 3 * d->triangles[3 * t + 1];
+        const float* v2 = d->vertices + 3 * d->triangles[3 * t + 2];
+        float idf;
+        std::memcpy(&idf, &t, 4);
+        tris[3 * s + 0] = make_float4(v0[0], v0[1], v0[2], idf);
+        tris[3 * s + 1] = make_float4((float)((double)v1[0] - v0[0]), (float)((double)v1[1] - v0[1]), (float)((double)v1[2] - v0[2]), 0.0f);
+        tris[3 * s + 2] = make_float4((float)((double)v2[0] - v0[0]), (float)((double)v2[1] - v0[1]), (float)((double)v2[2] - v0[2]), 0.0f);
+    }
+    if (d->uvs)
+        for (int64_t t = 0; t < F; ++t)
+            for (int k = 0; k < 3; ++k) {
+                tri_uv[6 * t + 2 * k] = d->uvs[2 * d->triangles[3 * t + k]];
+                tri_uv[6 * t + 2 * k + 1] = d->uvs[2 * d->triangles[3 * t + k] + 1];
+            }
+
+    dppt_scene* s = new dppt_scene();
+    s->ctx = ctx;
+    cudaError_t e = cudaSuccess;
+    DScene& D = s->d;
+    bool ok = upload(s, B.nodes.data(), B.nodes.size(), &D.nodes, e) &&
+              upload(s, tris.data(), tris.size(), &D.tris, e) &&
+              upload(s, d->tri_material, (size_t)F, &D.tri_mat, e) &&
+              upload(s, d->tri_light, (size_t)F, &D.tri_light, e) &&
+              upload(s, tri_uv.data(), tri_uv.size(), &D.tri_uv, e) &&
+              upload(s, reinterpret_cast<const float4*>(d->spheres), (size_t)Sn, &D.spheres, e) &&
+              upload(s, d->sphere_material, (size_t)Sn, &D.sph_mat, e) &&
+              upload(s, mats.data(), mats.size(), &D.mats, e) &&
+              upload(s, lights.data(), lights.size(), &D.lights, e) &&
+              upload(s, tex.data(), tex.size(), &D.tex, e) &&
+              upload(s, cams.data(), cams.size(), &D.cams, e);
+    if (!ok) {
+        dppt_scene_destroy(s);
+        return cuda_fail(ctx, e, "scene upload");
+    }
+    D.num_tris = (int)F;
+    D.num_nodes = (int)(B.nodes.size() / 4);
+    D.num_spheres = (int)Sn;
+    D.num_lights = L;
+    D.eps = d->ray_eps;
+    D.num_ior = d->num_ior;
+    D.num_sheets = d->num_sheets;
+    s->num_nodes = D.num_nodes;
+    s->bvh_depth = depth;
+    s->num_cameras = d->num_cameras;
+    s->num_textures = T;
+    s->tex_size = d->tex_size;
+    *out = s;
+    return DPPT_OK;
+}
+
+void dppt_scene_destroy(dppt_scene* s) {
+    if (!s) return;
+    if (s->ctx) cudaSetDevice(s->ctx->device);
+    for (void* p : s->allocs) cudaFree(p);
+    delete s;
+}
+
+dppt_status dppt_scene_info(const dppt_scene* s, int64_t info[5]) {
+    if (!s || !info) return DPPT_ERR_INVALID_ARG;
+    info[0] = s->num_nodes; info[1] = s->d.num_tris; info[2] = s->d.num_spheres; info[3] = s->bytes; info[4] = s->bvh_depth;
+    return DPPT_OK;
+}
+
+static void build_tables(const dppt_job* jobs, int njobs, const std::vector<JobPlan>& plan, int block,
+                         std::vector<int>& first, std::vector<JobTable>& tables) {
+    first.clear();
+    tables.clear();
+    for (int b = 0; b < njobs; b += kMaxJobsPerLaunch) {
+        JobTable T;
+        std::memset(&T, 0, sizeof T);
+        T.njobs = std::min(kMaxJobsPerLaunch, njobs - b);
+        long long chunks = 0;
+        for (int k = 0; k < T.njobs; ++k) {
+            const dppt_job& j = jobs[b + k];
+            DJob& J = T.job[k];
+            J.cam = j.camera; J.W = j.width; J.H = j.height; J.spp = j.spp; J.depth = j.max_depth;
+            J.red_mode = red_mode(j.spp);
+            J.k0 = j.seed ^ ((unsigned long long)(uint32_t)j.pass * 0x9E3779B97F4A7C15ULL);
+            J.k1 = j.stream;
+            J.npaths = (long long)plan[b + k].npix * j.spp;
+            J.chunk_begin = chunks;
+            J.sig = j.path_sig;
+            chunks += (J.npaths + block - 1) / block;
+        }
+        T.total_chunks = chunks;
+        first.push_back(b);
+        tables.push_back(T);
+    }
+}
+
+dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
+                               const dppt_params* params, float* image, void* stream) {
+    if (!ctx || !s) return fail(ctx, DPPT_ERR_INVALID_ARG, "null context or scene");
+    if (!image && njobs > 0) return fail(ctx, DPPT_ERR_INVALID_ARG, "image is null");
+    cudaSetDevice(ctx->device);
+    std::vector<JobPlan> plan;
+    size_t ws = 0;
+    dppt_status st = check_jobs(ctx, s, jobs, njobs, params, false, plan, ws);
+    if (st != DPPT_OK) return st;
+    if ((st = ensure_ws(ctx, ws)) != DPPT_OK) return st;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    const int block = ctx->launch.block_size;
+    std::vector<int> first;
+    std::vector<JobTable> tables;
+    build_tables(jobs, njobs, plan, block, first, tables);
+    DParams P = dparams(params);
+    for (size_t g = 0; g < tables.size(); ++g) {
+        JobTable& T = tables[g];
+        for (int k = 0; k < T.njobs; ++k) {
+            const int i = first[g] + k;
+            DJob& J = T.job[k];
+            J.raw = plan[i].filtered ? reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_a)
+                                     : image + jobs[i].out_offset;
+            J.dS = nullptr;
+            if (J.red_mode != 0) {
+                cudaError_t e = cudaMemsetAsync(J.raw, 0, (size_t)plan[i].npix * 12 * sizeof(float), cs);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+            }
+        }
+        LaunchCfg L = launch_cfg(ctx, 0, 0);
+        {
+            cudaFuncAttributes a;
+            if (primal_attributes(&a) == cudaSuccess && L.block > a.maxThreadsPerBlock)
+                return fail(ctx, DPPT_ERR_INVALID_ARG, "block_size exceeds the primal kernel's limit of " +
+                                                       std::to_string(a.maxThreadsPerBlock) + " threads");
+        }
+        if (L.schedule == DPPT_SCHED_PERSISTENT) {
+            cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), cs);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+        }
+        cudaError_t e = launch_primal(s->d, P, T, L, reinterpret_cast<unsigned*>(ctx->d_counter), ctx->d_status, cs);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "primal launch");
+    }
+    for (int i = 0; i < njobs; ++i) {
+        if (!plan[i].filtered) continue;
+        const float* raw = reinterpret_cast<const float*>(static_cast<char*>(ctx->ws) + plan[i].ws_a);
+        cudaError_t e = launch_apply_filter(raw, image + jobs[i].out_offset, (int)plan[i].npix, jobs[i].filter,
+                                            params->theta + jobs[i].theta_offset, plan[i].nang, cs);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "filter launch");
+    }
+    return DPPT_OK;
+}
+
+dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
+                                const dppt_params* params, const float* d_image, const dppt_grads* grads,
+                                void* stream) {
+    if (!ctx || !s) return fail(ctx, DPPT_ERR_INVALID_ARG, "null context or scene");
+    if (!grads) return fail(ctx, DPPT_ERR_INVALID_ARG, "grads is null");
+    if (!d_image && njobs > 0) return fail(ctx, DPPT_ERR_INVALID_ARG, "d_image is null");
+    cudaSetDevice(ctx->device);
+    std::vector<JobPlan> plan;
+    size_t ws = 0;
+    dppt_status st = check_jobs(ctx, s, jobs, njobs, params, true, plan, ws);
+    if (st != DPPT_OK) return st;
+    if ((st = ensure_ws(ctx, ws)) != DPPT_OK) return st;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    const int block = ctx->launch.block_size;
+    std::vector<int> first;
+    std::vector<JobTable> tables;
+    build_tables(jobs, njobs, plan, block, first, tables);
+    DParams P = dparams(params);
+    DGrads G{grads->tex, grads->ior, grads->le, grads->sheet};
+    for (size_t g = 0; g < tables.size(); ++g) {
+        JobTable& T = tables[g];
+        int maxd = 1;
+        for (int k = 0; k < T.njobs; ++k) {
+            const int i = first[g] + k;
+            DJob& J = T.job[k];
+            maxd = std::max(maxd, jobs[i].max_depth);
+            if (plan[i].filtered) {
+                float* dS = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_a);
+                float* Sa = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_b);
+                cudaError_t e = launch_filter_adjoint_input(d_image + jobs[i].out_offset, dS, (int)plan[i].npix,
+                                                            jobs[i].filter, params->theta + jobs[i].theta_offset,
+                                                            plan[i].nang, cs);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "filter adjoint launch");
+                J.dS = dS;
+                J.raw = grads->theta ? Sa : nullptr;
+                if (J.raw && J.red_mode != 0) {
+                    e = cudaMemsetAsync(J.raw, 0, (size_t)plan[i].npix * 12 * sizeof(float), cs);
+                    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+                }
+            } else {
+                J.dS = d_image + jobs[i].out_offset;
+                J.raw = nullptr;
+            }
+        }
+        LaunchCfg L = launch_cfg(ctx, 1, maxd);
+        {
+            cudaFuncAttributes a;
+            if (adjoint_attributes(maxd, &a) == cudaSuccess && L.block > a.maxThreadsPerBlock)
+                return fail(ctx, DPPT_ERR_INVALID_ARG, "block_size exceeds the adjoint kernel's limit of " +
+                                                       std::to_string(a.maxThreadsPerBlock) + " threads");
+        }
+        if (L.schedule == DPPT_SCHED_PERSISTENT) {
+            cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), cs);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+        }
+        cudaError_t e = launch_adjoint(s->d, P, G, T, L, maxd, reinterpret_cast<unsigned*>(ctx->d_counter),
+                                       ctx->d_status, cs);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
+    }
+    if (grads->theta) {
+        for (int i = 0; i < njobs; ++i) {
+            if (!plan[i].filtered) continue;
+            const float* Sa = reinterpret_cast<const float*>(static_cast<char*>(ctx->ws) + plan[i].ws_b);
+            cudaError_t e = launch_theta_grad(d_image + jobs[i].out_offset, Sa, (int)plan[i].npix, jobs[i].filter,
+                                              params->theta + jobs[i].theta_offset, plan[i].nang,
+                                              grads->theta + jobs[i].theta_offset, cs);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "theta-gradient launch");
+        }
+    }
+    return DPPT_OK;
+}
+
+dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int32_t njobs, size_t* bytes) {
+    if (!ctx || !bytes || njobs < 0 || (njobs > 0 && !jobs)) return DPPT_ERR_INVALID_ARG;
+    size_t b = 0;
+    for (int i = 0; i < njobs; ++i)
+        if (jobs[i].filter != DPPT_FILTER_NONE)
+            b = align256(b + 2 * (size_t)jobs[i].width * jobs[i].height * 12 * sizeof(float));
+    *bytes = b;
+    return DPPT_OK;
+}
+
+dppt_status dppt_set_launch(dppt_ctx* ctx, const dppt_launch* l) {
+    if (!ctx || !l) return DPPT_ERR_INVALID_ARG;
+    if (l->schedule != DPPT_SCHED_GRID && l->schedule != DPPT_SCHED_PERSISTENT)
+        return fail(ctx, DPPT_ERR_INVALID_ARG, "unknown schedule");
+    if (l->block_size != 64 && l->block_size != 128 && l->block_size != 256 && l->block_size != 512)
+        return fail(ctx, DPPT_ERR_INVALID_ARG, "block_size must be 64, 128, 256 or 512");
+    if (l->blocks_per_sm < 0) return fail(ctx, DPPT_ERR_INVALID_ARG, "negative blocks_per_sm");
+    ctx->launch = *l;
+    return DPPT_OK;
+}
+
+dppt_status dppt_get_launch(const dppt_ctx* ctx, dppt_launch* l) {
+    if (!ctx || !l) return DPPT_ERR_INVALID_ARG;
+    *l = ctx->launch;
+    return DPPT_OK;
+}
+
+dppt_status dppt_adjoint_footprint(const dppt_ctx* ctx, int32_t max_depth, int64_t out[4]) {
+    if (!ctx || !out || max_depth < 1 || max_depth > 64) return DPPT_ERR_INVALID_ARG;
+    cudaFuncAttributes a;
+    if (adjoint_attributes(max_depth, &a) != cudaSuccess) return DPPT_ERR_CUDA;
+    out[0] = (int64_t)a.localSizeBytes;
+    out[1] = a.numRegs;
+    out[2] = (int64_t)occupancy_blocks(1, max_depth, ctx->launch.block_size) * ctx->launch.block_size;
+    out[3] = ctx->sm_count;
+    return DPPT_OK;
+}
+
+dppt_status dppt_sync_status(dppt_ctx* ctx, void* stream) {
+    if (!ctx) return DPPT_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    unsigned v = 0;
+    e = cudaMemcpy(&v, ctx->d_status, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
+    cudaMemset(ctx->d_status, 0, sizeof(unsigned));
+    if (v == 0) return DPPT_OK;
+    return fail(ctx, DPPT_ERR_DEVICE, "device status word set: BVH traversal stack overflow");
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// Structures shared by the host side of the library and its kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dppt.h"
+
+namespace dppt {
+
+constexpr int kMaxJobsPerLaunch = 64;
+constexpr int kBvhStack = 64;
+
+struct DMat {
+    int type, albedo_tex, rough_tex, ior_index, sheet_index;
+    float eta_re, eta_im, t1[3], t2[3], retard, emission;
+};
+struct DLight { float o[3], e1[3], e2[3], n[3], area; };
+struct DTex { long long off; int w, h, ch, pad; };
+struct DCam { float org[3], fwd[3], right[3], up[3], tanh; };
+
+// BVH: two-wide nodes holding the boxes of both children (4 x float4 = 64 B):
+//   n0 = (lx0, lx1, ly0, ly1), n1 = (rx0, rx1, ry0, ry1), n2 = (lz0, lz1, rz0, rz1),
+//   n3 = (left ref, right ref, -, -) as ints.  A ref >= 0 is an inner node; a
+//   ref < 0 is a leaf ~(first | count << 25) over the BVH-ordered triangles.
+// Triangles (3 x float4 = 48 B, BVH order): (v0, original id), (e1, 0), (e2, 0).
+struct DScene {
+    const float4* nodes;
+    const float4* tris;
+    int num_tris;
+    int num_nodes;
+    const int* tri_mat;     // original triangle order
+    const int* tri_light;
+    const float* tri_uv;    // [F][6]
+    const float4* spheres;
+    const int* sph_mat;
+    int num_spheres;
+    int num_lights;
+    const DMat* mats;
+    const DLight* lights;
+    const DTex* tex;
+    const DCam* cams;
+    float eps;
+    int num_ior, num_sheets, pad;
+};
+
+struct DParams {
+    const float* tex;
+    const float* ior;
+    const float* le;
+    const float* sheet;
+    const float* theta;
+};
+struct DGrads {
+    float* tex;
+    float* ior;
+    float* le;
+    float* sheet;
+};
+
+// reduction of a pixel's spp paths: 0 = within a warp segment, plain store
+// (spp a power of two <= 32); 1 = full warps then one atomic per warp (spp a
+// power-of-two multiple of 32); 2 = one atomic per path (any other spp)
+struct DJob {
+    int cam, W, H, spp, depth, red_mode;
+    unsigned long long k0, k1;
+    long long npaths;
+    long long chunk_begin;
+    float* raw;            // primal: mean raw Stokes per pixel [H*W][12]; adjoint: S_adj or null
+    const float* dS;       // adjoint: per-pixel adjoint of the raw image [H*W][12]
+    unsigned* sig;         // optional per-path signature
+};
+struct JobTable {
+    DJob job[kMaxJobsPerLaunch];
+    int njobs;
+    int pad;
+    long long total_chunks;
+};
+
+struct LaunchCfg {
+    int schedule, block, grid;
+};
+
+// kernel entry points (kernels.cu)
+cudaError_t launch_primal(const DScene& S, const DParams& P, const JobTable& T, const LaunchCfg& L,
+                          unsigned* counter, unsigned* status, cudaStream_t st);
+cudaError_t launch_adjoint(const DScene& S, const DParams& P, const DGrads& G, const JobTable& T,
+                           const LaunchCfg& L, int max_depth, unsigned* counter, unsigned* status,
+                           cudaStream_t st);
+// camera-filter folds: image[a][pix] = C(theta_a) raw[pix]; dS[pix] = sum_a C_a^T dI_a[pix];
+// dtheta_a += sum_pix dI_a[pix]^T dC_a/dtheta S_adj[pix]
+cudaError_t launch_apply_filter(const float* raw, float* image, int npix, int filter, const float* theta,
+                                int nang, cudaStream_t st);
+cudaError_t launch_filter_adjoint_input(const float* dimage, float* dS, int npix, int filter,
+                                        const float* theta, int nang, cudaStream_t st);
+cudaError_t launch_theta_grad(const float* dimage, const float* S_adj, int npix, int filter, const float* theta,
+                              int nang, float* dtheta, cudaStream_t st);
+int adjoint_depth_bucket(int max_depth);
+cudaError_t adjoint_attributes(int max_depth, cudaFuncAttributes* attr);
+cudaError_t primal_attributes(cudaFuncAttributes* attr);
+int occupancy_blocks(int which, int max_depth, int block);   // which: 0 primal, 1 adjoint
+
+}  // namespace dppt

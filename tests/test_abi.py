@@ -1,0 +1,69 @@
+"""CPU checks of the boundary: the C-ABI library builds, loads and exports every
+symbol include/dppt.h declares; the ctypes structures match the header's layout.
+No compute call is made (there may be no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "dppt.h")).read()
+    return sorted(set(re.findall(r"\b(dppt_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2607_13265_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2607_13265_gb300 import _lib
+    declared = _declared_symbols()
+    assert len(declared) >= 10
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) == set(_lib.SIGNATURES), "binding and header disagree"
+
+
+def test_version_string(lib):
+    assert lib.dppt_version().decode().startswith("dppt")
+
+
+def test_struct_layouts_match_header():
+    """Sizes of the ctypes mirrors equal the C structs (checked with a tiny C program)."""
+    from paper_2607_13265_gb300 import _lib
+    import subprocess
+    import tempfile
+    src = r'''
+#include <stdio.h>
+#include "dppt.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(dppt_material), sizeof(dppt_scene_desc), sizeof(dppt_job),
+         sizeof(dppt_params), sizeof(dppt_grads), sizeof(dppt_launch));
+  return 0;
+}'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "l.c")
+        exe = os.path.join(d, "l")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        sizes = [int(x) for x in subprocess.check_output([exe]).split()]
+    mine = [ctypes.sizeof(t) for t in (_lib.Material, _lib.SceneDesc, _lib.Job, _lib.Params, _lib.Grads, _lib.Launch)]
+    assert sizes == mine
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2607_13265_gb300 import _lib
+    saved = _lib._lib
+    _lib._lib = None
+    try:
+        with pytest.raises(_lib.DpptError):
+            _lib.load(str(tmp_path / "missing.so"))
+    finally:
+        _lib._lib = saved
