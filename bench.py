@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the polarized path tracer (primal + cached-suffix-replay adjoint).
+
+One step = one inverse-rendering gradient evaluation of the 50k-triangle displaced
+icosphere workload (256x256, 64 spp, depth 8, rough conductor + rough dielectric
+pBRDFs, 128^2x3 albedo and 128^2 roughness maps): render_primal (PRB phase 1), the L2
+loss adjoint dI = 2 (I - T) / N, render_adjoint (phases 2+3) into both maps.
+Metric: primal + adjoint paths per second (each step traces 2 x 4,194,304 paths).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+N > 1 runs under torchrun: every rank renders its own independent view stream (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "primal+adjoint paths/sec and gradient MB vs plain launch at 1e-3 grad rel-err"
+UNIT = "paths/s"
+WORKLOAD = "icosphere50k_256x256_64spp_depth8"
+
+# Algorithmic FP32 work per unit (flops), counted from the operations the method
+# performs: a BVH node visit tests two child boxes (12 FMA = 24 flops), a ray/triangle
+# test ~30 flops, a ray/sphere test ~20; per surface vertex the primal shading
+# (rotations 12, Fresnel 60, GGX D*G 40, sampling 40, next-event estimation 150,
+# Mueller fold 96) = 398 flops, the adjoint per vertex = 398 (cache pass) + 40 (replay
+# sampling) + 96 (a^T W) + 524 (dual-number derivatives, ~2x the 262-flop evaluation).
+F_NODE, F_TRI, F_SPH = 24, 30, 20
+F_VERTEX_PRIMAL = 398
+F_VERTEX_ADJOINT = 398 + 40 + 96 + 524
+
+# DRAM traffic per launch of the adjoint kernel from one ncu capture (bytes), or None
+# when the kernel has changed since the counters were taken.
+ADJOINT_DRAM_BYTES_PER_LAUNCH = None
+
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["_source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "_source": "fallback"}
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+_W = {}
+
+
+def _oracle_init(workload_kw):
+    import oracle
+    from paper_2607_13265_gb300 import scenegen as sg
+    oracle.build()
+    scene, job = sg.icosphere_scene(**workload_kw)
+    _W["o"] = oracle.OracleScene(scene)
+    _W["scene"], _W["job"] = scene, job
+
+
+def _oracle_task(pixels):
+    import copy
+    import numpy as np
+    o, scene, job = _W["o"], _W["scene"], _W["job"]
+    pix = np.asarray(pixels, np.int64)
+    P = scene.params()
+    t0 = time.perf_counter()
+    img = o.render(job, P, pixels=pix)
+    aj = copy.copy(job)
+    aj.pass_id = 1
+    o.gradient(aj, P, np.ones_like(img), pixels=pix, mode="replay")
+    return time.perf_counter() - t0, 2 * len(pix) * job.spp
+
+
+def oracle_sample(num_pixels: int, procs: int, workload_kw: dict, pool=None):
+    """The FP64 oracle (primal + cached-replay adjoint) on an evenly strided pixel
+    sample of the workload, one task per 64 pixels over `procs` worker processes."""
+    import numpy as np
+    npix = 256 * 256
+    pix = np.linspace(0, npix - 1, num_pixels).astype(np.int64)
+    chunks = [pix[i:i + 64].tolist() for i in range(0, len(pix), 64)]
+    own = pool is None
+    if own:
+        pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_init, initargs=(workload_kw,))
+        pool.map(_oracle_task, [chunks[0][:1]] * procs)   # warm every worker
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_task, chunks)
+    wall = time.perf_counter() - t0
+    if own:
+        pool.close()
+        pool.join()
+    paths = sum(r[1] for r in res)
+    return {"value": paths / wall, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{num_pixels} evenly strided pixels x 64 spp of the {WORKLOAD} workload "
+                      f"({paths} primal+adjoint paths, FP64, {wall:.2f} s wall on {procs} processes)",
+            "wall_s": wall, "paths": paths}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- native leg
+def run_native(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    rank, world, local = _env_rank()
+    pool = None
+    cpu_procs = os.cpu_count() or 1
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle's worker processes are spawned before the first CUDA call
+        pool = mp.get_context("spawn").Pool(cpu_procs, initializer=_oracle_init, initargs=({},))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2607_13265_gb300 import api, build, scenegen as sg
+    build.build()
+    dev = torch.device("cuda", local)
+    kw = {}
+    if args.width:
+        kw["width"] = args.width
+    if args.spp:
+        kw["spp"] = args.spp
+    scene, job = sg.icosphere_scene(**kw)
+    job.stream = rank                      # every rank traces its own independent paths
+    target_scene, tjob = sg.icosphere_scene(**kw)
+    tp = target_scene.params()
+    rng = np.random.default_rng(100)
+    off, w, h, ch = target_scene.tex_desc[0]
+    tp["tex"][off:off + w * h * ch] = rng.uniform(0.2, 0.9, w * h * ch)
+    off, w, h, ch = target_scene.tex_desc[1]
+    tp["tex"][off:off + w * h * ch] = rng.uniform(0.05, 0.5, w * h * ch)
+
+    dctx = api.Context(local)
+    gs = api.GpuScene(dctx, scene)
+    if args.schedule is not None:
+        dctx.set_launch(args.schedule, args.block, 0)
+    batch = api.pack_jobs([job])
+    adj = api.pack_jobs(api.adjoint_jobs([job]))
+    P = api.device_params(scene, batch)
+    tjob.seed = 12345
+    target = api.render_primal(dctx, gs, api.pack_jobs([tjob]), api.device_params(scene, batch, tp)).clone()
+    N = float(target.numel())
+    grads = api.zero_grads(P)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        img = api.render_primal(dctx, gs, batch, P, stream=stream)
+        dI = (img - target).mul_(2.0 / N)
+        api.render_adjoint(dctx, gs, adj, P, dI, grads, stream=stream)
+        return img
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dctx.sync_status()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(K):
+            flush.zero_()                               # L2 flush between timed steps (outside the events)
+            e0, e1, e2, e3 = ev[k]
+            e0.record(stream)
+            img = api.render_primal(dctx, gs, batch, P, stream=stream)
+            e1.record(stream)
+            dI = (img - target).mul_(2.0 / N)
+            e2.record(stream)
+            api.render_adjoint(dctx, gs, adj, P, dI, grads, stream=stream)
+            e3.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    dctx.sync_status()
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    prim_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    adj_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    paths_per_step = 2 * job.num_paths
+    value = paths_per_step * world * K / (total_ms / 1000.0)
+
+    # ---- end to end through the public autograd API with host buffers
+    e2e = None
+    if rank == 0 or world > 1:
+        host_tex = torch.from_numpy(np.asarray(scene.params()["tex"], np.float32)).pin_memory()
+        host_grad = torch.empty_like(host_tex).pin_memory()
+        host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+        tex_d = P["tex"].clone().requires_grad_(True)
+        others = {k: P[k].clone().requires_grad_(True) for k in ("ior", "le", "sheet", "theta")}
+
+        def e2e_step():
+            tex_d.data.copy_(host_tex, non_blocking=True)
+            tex_d.grad = None
+            img = api.PolarizedRender.apply(dctx, gs, batch, adj, tex_d, others["ior"], others["le"],
+                                            others["sheet"], others["theta"])
+            loss = ((img - target) ** 2).mean()
+            loss.backward()
+            host_grad.copy_(tex_d.grad, non_blocking=True)
+            host_loss.copy_(loss.detach().view(1), non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for _ in range(K):
+            flush.zero_()
+            a.record(stream)
+            e2e_step()
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+        e2e = {"value": paths_per_step * K / (ms / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": int(host_tex.numel() * 4),
+               "d2h_bytes_per_step": int(host_grad.numel() * 4 + 4),
+               "api": "PolarizedRender.apply + loss.backward()"}
+
+    # ---- roofline of the dominant kernel (the adjoint megakernel)
+    work = api.count_work(dctx, gs, adj, P)
+    trav = F_NODE * (work["nodes"] + work["shadow_nodes"]) + F_TRI * work["tri_tests"] + F_SPH * work["sph_tests"]
+    flops_adj = 2 * trav + F_VERTEX_ADJOINT * work["vertices"]
+    pw = api.count_work(dctx, gs, batch, P)
+    flops_prim = F_NODE * (pw["nodes"] + pw["shadow_nodes"]) + F_TRI * pw["tri_tests"] + \
+        F_SPH * pw["sph_tests"] + F_VERTEX_PRIMAL * pw["vertices"]
+    adj_avg = sum(adj_ms) / K
+    prim_avg = sum(prim_ms) / K
+    props = torch.cuda.get_device_properties(dev)
+    peaks = load_peaks()
+    clocks = clk.summary()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at max clock
+    fp32_peak_loaded = props.multi_processor_count * 128 * 2 * (clocks["sm_mhz"] or sm_max) * 1e6 / 1e12
+    achieved = flops_adj / (adj_avg / 1000.0) / 1e12
+    fp = dctx.adjoint_footprint(job.max_depth)
+    cache_bytes = fp["local_bytes_per_thread"] * fp["threads_per_sm"] * fp["sms"]
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded procedural scene, textures and target)",
+        "config": {"workload": WORKLOAD if not kw else f"{WORKLOAD} reduced {kw}", "triangles": int(scene.num_triangles), "width": job.width,
+                   "height": job.height, "spp": job.spp, "max_depth": job.max_depth,
+                   "paths_per_step": paths_per_step, "grads": "albedo 128x128x3 + roughness 128x128",
+                   "l2": "flushed between timed steps (512 MiB write)",
+                   "schedule": dctx.get_launch(), "parallelism": f"replicas{world}"},
+        "kernels_ms": {"primal": prim_avg, "adjoint": adj_avg},
+        "roofline": {"bound": "alu", "kernel": "k_adjoint", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "frac_at_loaded_clock": achieved / fp32_peak_loaded,
+                     "traffic": ADJOINT_DRAM_BYTES_PER_LAUNCH,
+                     "flops_per_launch": flops_adj, "work_units": work,
+                     "peak_note": f"FP32 pipe: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
+                                  f"({peaks['_source']} max clock)",
+                     "primal": {"achieved": flops_prim / (prim_avg / 1000.0) / 1e12, "flops_per_launch": flops_prim}},
+        "memory": {"prb_cache_bytes_per_thread": fp["local_bytes_per_thread"],
+                   "prb_cache_bytes_resident": cache_bytes, "adjoint_registers": fp["registers"],
+                   "threads_per_sm": fp["threads_per_sm"]},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": 2 * K,
+    }
+    if pool is not None:
+        result["cpu_baseline"] = oracle_sample(args.cpu_pixels, cpu_procs, {}, pool)
+        pool.close()
+        pool.join()
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference leg (the oracle)
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    procs = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_init, initargs=({},))
+    pool.map(_oracle_task, [[0]] * procs)
+    for _ in range(args.warmup):
+        oracle_sample(args.ref_pixels, procs, {}, pool)
+    vals, walls, paths = [], 0.0, 0
+    for _ in range(args.steps):
+        r = oracle_sample(args.ref_pixels, procs, {}, pool)
+        walls += r["wall_s"]
+        paths += r["paths"]
+    pool.close()
+    pool.join()
+    value = paths / walls
+    sample = (f"{args.ref_pixels} evenly strided pixels x 64 spp of the {WORKLOAD} workload per step "
+              f"(FP64 oracle: primal + cached-replay adjoint)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * walls / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded procedural scene)", "config": {"workload": WORKLOAD, "parallelism": f"cpu{procs}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--schedule", type=int, default=None, help="0 grid, 1 persistent (default: library default)")
+    ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--cpu-pixels", type=int, default=4096)
+    ap.add_argument("--ref-pixels", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--width", type=int, default=None, help="smaller image (profiling captures only)")
+    ap.add_argument("--spp", type=int, default=None, help="fewer samples per pixel (profiling captures only)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -63,8 +63,11 @@ enum {
  * P(theta), or a quarter-wave plate Q(pi/2, 0) followed by P(theta). */
 enum { DPPT_FILTER_NONE = 0, DPPT_FILTER_POLARIZER = 1, DPPT_FILTER_QWP_POLARIZER = 2 };
 
-/* Kernel schedule chosen by the autotuner (or set by the caller). */
-enum { DPPT_SCHED_GRID = 0, DPPT_SCHED_PERSISTENT = 1 };
+/* Kernel schedule chosen by the autotuner (or set by the caller): the
+ * megakernel with one block per chunk of paths, the megakernel as a
+ * persistent kernel pulling chunks from an atomic counter, or the wavefront
+ * schedule (stage kernels over compacted lists of live paths). */
+enum { DPPT_SCHED_GRID = 0, DPPT_SCHED_PERSISTENT = 1, DPPT_SCHED_WAVEFRONT = 2 };
 
 typedef struct dppt_ctx dppt_ctx;
 typedef struct dppt_scene dppt_scene;
@@ -144,11 +147,15 @@ typedef struct {
     float* theta;
 } dppt_grads;
 
+/* Launch shape of the primal and of the adjoint (each picked by the autotuner,
+ * or set by the caller). */
 typedef struct {
-    int32_t schedule;       /* DPPT_SCHED_* */
-    int32_t block_size;     /* threads per block: 64, 128, 256 or 512 */
-    int32_t blocks_per_sm;  /* persistent schedule: resident blocks per SM (0 = occupancy maximum) */
-    int32_t reserved;
+    int32_t schedule;           /* DPPT_SCHED_* for render_primal */
+    int32_t block_size;         /* threads per block: 64, 128, 256 (512 for the wavefront stages) */
+    int32_t blocks_per_sm;      /* persistent schedule: resident blocks per SM (0 = occupancy maximum) */
+    int32_t adj_schedule;       /* the same three for render_adjoint */
+    int32_t adj_block_size;
+    int32_t adj_blocks_per_sm;
 } dppt_launch;
 
 /* Create a context on CUDA device `device` (made current for the call). */
@@ -193,11 +200,32 @@ dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int3
 dppt_status dppt_set_launch(dppt_ctx* ctx, const dppt_launch* launch);
 dppt_status dppt_get_launch(const dppt_ctx* ctx, dppt_launch* launch);
 
+/* Autotuner: times render_primal and render_adjoint of the given jobs for
+ * every schedule (grid, persistent, wavefront) and block size (64, 128, 256)
+ * with CUDA events on `stream` (one warm-up call and `reps` timed calls per
+ * candidate), keeps the fastest shape for each of the two calls in the
+ * context and returns it in *best.  times_ms (nullable) receives the
+ * measured mean milliseconds [9 candidates][2: primal, adjoint] in the order
+ * schedule-major, block-minor.  Allocates its scratch image, adjoint input and
+ * gradient buffers on the device and frees them before returning; gradients
+ * produced while tuning are discarded.  Synchronous. */
+dppt_status dppt_autotune(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* jobs, int32_t njobs,
+                          const dppt_params* params, int32_t reps, dppt_launch* best, float* times_ms);
+
 /* Per-thread local cache bytes and registers of the adjoint kernel used for
  * max_depth, and the resident threads per SM for the current launch shape:
  * out[0] = local bytes/thread, out[1] = registers/thread, out[2] = threads/SM,
  * out[3] = SMs. */
 dppt_status dppt_adjoint_footprint(const dppt_ctx* ctx, int32_t max_depth, int64_t out[4]);
+
+/* Work units of the jobs' paths, counted by an instrumented (untimed) instance
+ * of the primal megakernel on the same BVH: out[0..7] = paths, surface
+ * vertices, closest-hit rays, shadow rays, BVH nodes visited by closest-hit
+ * rays, BVH nodes visited by shadow rays, ray/triangle tests, ray/sphere
+ * tests.  Synchronous; writes no image.  Used for the roofline's algorithmic
+ * work per launch. */
+dppt_status dppt_count_work(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* jobs, int32_t njobs,
+                            const dppt_params* params, uint64_t out[8]);
 
 /* Synchronise `stream` and return (then clear) the device status word:
  * DPPT_OK, DPPT_ERR_DEVICE (a traversal stack overflow) or DPPT_ERR_TIMEOUT. */

@@ -52,7 +52,8 @@ class Grads(ctypes.Structure):
 
 
 class Launch(ctypes.Structure):
-    _fields_ = [("schedule", c_i32), ("block_size", c_i32), ("blocks_per_sm", c_i32), ("reserved", c_i32)]
+    _fields_ = [("schedule", c_i32), ("block_size", c_i32), ("blocks_per_sm", c_i32),
+                ("adj_schedule", c_i32), ("adj_block_size", c_i32), ("adj_blocks_per_sm", c_i32)]
 
 
 # every symbol include/dppt.h declares, with (restype, argtypes)
@@ -71,6 +72,10 @@ SIGNATURES = {
     "dppt_set_launch": (c_i32, [c_vp, ctypes.POINTER(Launch)]),
     "dppt_get_launch": (c_i32, [c_vp, ctypes.POINTER(Launch)]),
     "dppt_adjoint_footprint": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_i64)]),
+    "dppt_count_work": (c_i32, [c_vp, c_vp, ctypes.POINTER(Job), c_i32, ctypes.POINTER(Params),
+                                ctypes.POINTER(ctypes.c_uint64)]),
+    "dppt_autotune": (c_i32, [c_vp, c_vp, ctypes.POINTER(Job), c_i32, ctypes.POINTER(Params), c_i32,
+                              ctypes.POINTER(Launch), ctypes.POINTER(ctypes.c_float)]),
     "dppt_sync_status": (c_i32, [c_vp, c_vp]),
 }
 

@@ -62,14 +62,20 @@ class Context:
         except Exception:
             pass
 
-    def set_launch(self, schedule: int, block_size: int, blocks_per_sm: int = 0):
-        l = L.Launch(schedule, block_size, blocks_per_sm, 0)
+    def set_launch(self, schedule: int, block_size: int, blocks_per_sm: int = 0, adj_schedule: int | None = None,
+                   adj_block_size: int | None = None, adj_blocks_per_sm: int | None = None):
+        """Launch shape of render_primal (and of render_adjoint; same as the primal unless given)."""
+        l = L.Launch(schedule, block_size, blocks_per_sm,
+                     schedule if adj_schedule is None else adj_schedule,
+                     block_size if adj_block_size is None else adj_block_size,
+                     blocks_per_sm if adj_blocks_per_sm is None else adj_blocks_per_sm)
         _check(self.h, self.lib.dppt_set_launch(self.h, ctypes.byref(l)), "dppt_set_launch")
 
-    def get_launch(self) -> tuple[int, int, int]:
+    def get_launch(self) -> tuple:
+        """(schedule, block, blocks_per_sm, adj_schedule, adj_block, adj_blocks_per_sm)"""
         l = L.Launch()
         _check(self.h, self.lib.dppt_get_launch(self.h, ctypes.byref(l)), "dppt_get_launch")
-        return l.schedule, l.block_size, l.blocks_per_sm
+        return (l.schedule, l.block_size, l.blocks_per_sm, l.adj_schedule, l.adj_block_size, l.adj_blocks_per_sm)
 
     def adjoint_footprint(self, max_depth: int) -> dict:
         out = (ctypes.c_int64 * 4)()
@@ -193,6 +199,37 @@ def render_primal(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict, ima
     _check(ctx.h, ctx.lib.dppt_render_primal(ctx.h, gs.h, batch.c_jobs, batch.n, ctypes.byref(cp), _ptr(image),
                                              _stream_ptr(stream)), "dppt_render_primal")
     return image
+
+
+WORK_KEYS = ("paths", "vertices", "rays", "shadow_rays", "nodes", "shadow_nodes", "tri_tests", "sph_tests")
+
+
+def count_work(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict) -> dict:
+    """Work units of the jobs' paths (instrumented primal on the same BVH; untimed)."""
+    out = (ctypes.c_uint64 * 8)()
+    cp = _c_params(params)
+    _check(ctx.h, ctx.lib.dppt_count_work(ctx.h, gs.h, batch.c_jobs, batch.n, ctypes.byref(cp), out),
+           "dppt_count_work")
+    return dict(zip(WORK_KEYS, [int(x) for x in out]))
+
+
+SCHEDULE_NAMES = {0: "grid", 1: "persistent", 2: "wavefront"}
+
+
+def autotune(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict, reps: int = 2) -> dict:
+    """Run the library's autotuner on these jobs; the context keeps the fastest shapes."""
+    best = L.Launch()
+    times = (ctypes.c_float * 18)()
+    cp = _c_params(params)
+    _check(ctx.h, ctx.lib.dppt_autotune(ctx.h, gs.h, batch.c_jobs, batch.n, ctypes.byref(cp), reps,
+                                        ctypes.byref(best), times), "dppt_autotune")
+    table = {}
+    for si in range(3):
+        for bi, b in enumerate((64, 128, 256)):
+            k = 3 * si + bi
+            table[f"{SCHEDULE_NAMES[si]}/{b}"] = {"primal_ms": times[2 * k], "adjoint_ms": times[2 * k + 1]}
+    return {"primal": (SCHEDULE_NAMES[best.schedule], best.block_size),
+            "adjoint": (SCHEDULE_NAMES[best.adj_schedule], best.adj_block_size), "times_ms": table}
 
 
 def zero_grads(params: dict) -> dict:

@@ -13,8 +13,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdppt.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "host.cpp"]
-HEADERS = ["device_math.cuh", "internal.h"]
+SOURCES = ["trace_d4.cu", "trace_d8.cu", "trace_d16.cu", "trace_d32.cu", "trace_d64.cu", "wavefront.cu", "folds.cu", "host.cpp"]
+HEADERS = ["device_math.cuh", "internal.h", "trace.cuh"]
 
 
 def _nvcc() -> str:
@@ -22,6 +22,12 @@ def _nvcc() -> str:
         if c and (os.path.isabs(c) and os.path.exists(c) or not os.path.isabs(c)):
             return c
     return "nvcc"
+
+
+def extra_flags() -> list[str]:
+    """Optional -D overrides of the register budgets, e.g. DPPT_NVCC_DEFS="DPPT_MIN_BLOCKS_ADJOINT=2"."""
+    defs = os.environ.get("DPPT_NVCC_DEFS", "").split()
+    return [f"-D{d}" for d in defs]
 
 
 def _stale(target: str, deps: list[str]) -> bool:
@@ -43,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
             cmd = [nvcc, "-std=c++17", *ARCH, "-O3", "-lineinfo", "-Xcompiler", "-fPIC",
-                   "-I", INCLUDE, "-I", CSRC, "-c", s, "-o", o]
+                   "-I", INCLUDE, "-I", CSRC, *extra_flags(), "-c", s, "-o", o]
             if src.endswith(".cu"):
                 cmd += ["-Xptxas", "-v"] if verbose else []
             jobs.append(cmd)

@@ -1,0 +1,155 @@
+// Camera-filter folds for batches of polarizer angles: the filter does not
+// change the paths, so the raw sensor-frame image is rendered once and each
+// angle's image, the adjoint input and the angle gradients are per-pixel maps.
+#include "device_math.cuh"
+#include "internal.h"
+
+namespace dppt {
+
+// ================================================================== camera-filter folds
+// C(theta) for the filter stacks, in the sensor frame (c = cos 2theta, s = sin 2theta):
+// polarizer  1/2 [[1,c,s,0],[c,c^2,cs,0],[s,cs,s^2,0],[0,0,0,0]];
+// quarter-wave plate (fast axis x) then polarizer: columns (0,1,3) as above with the
+// s-column moved to the circular slot.
+__device__ __forceinline__ void filter_matrix(int filter, float theta, float C[16], float dC[16]) {
+    float s, c;
+    sincosf(2.0f * theta, &s, &c);
+    float P[16] = {0.5f, 0.5f * c, 0.5f * s, 0.0f,
+                   0.5f * c, 0.5f * c * c, 0.5f * c * s, 0.0f,
+                   0.5f * s, 0.5f * c * s, 0.5f * s * s, 0.0f,
+                   0.0f, 0.0f, 0.0f, 0.0f};
+    // d/dtheta with dc = -2s, ds = 2c
+    float dP[16] = {0.0f, -s, c, 0.0f,
+                    -s, -2.0f * c * s, c * c - s * s, 0.0f,
+                    c, c * c - s * s, 2.0f * s * c, 0.0f,
+                    0.0f, 0.0f, 0.0f, 0.0f};
+    for (int r = 0; r < 4; ++r) {
+        if (filter == DPPT_FILTER_POLARIZER) {
+            for (int k = 0; k < 4; ++k) { C[4 * r + k] = P[4 * r + k]; dC[4 * r + k] = dP[4 * r + k]; }
+        } else {  // P . Q(pi/2, 0): column 2 <- -column 3 (= 0), column 3 <- column 2
+            C[4 * r + 0] = P[4 * r + 0]; C[4 * r + 1] = P[4 * r + 1]; C[4 * r + 2] = -P[4 * r + 3]; C[4 * r + 3] = P[4 * r + 2];
+            dC[4 * r + 0] = dP[4 * r + 0]; dC[4 * r + 1] = dP[4 * r + 1]; dC[4 * r + 2] = -dP[4 * r + 3]; dC[4 * r + 3] = dP[4 * r + 2];
+        }
+    }
+}
+
+__global__ void k_apply_filter(const float* __restrict__ raw, float* __restrict__ image, int npix, int filter,
+                               const float* __restrict__ theta, int nang) {
+    extern __shared__ float sC[];
+    for (int a = threadIdx.x; a < nang; a += blockDim.x) {
+        float C[16], dC[16];
+        filter_matrix(filter, __ldg(theta + a), C, dC);
+        for (int k = 0; k < 16; ++k) sC[16 * a + k] = C[k];
+    }
+    __syncthreads();
+    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix; pix += (long long)gridDim.x * blockDim.x) {
+        float r[12];
+        const float4* rp = reinterpret_cast<const float4*>(raw + pix * 12);
+        for (int q = 0; q < 3; ++q) { float4 t = __ldg(rp + q); r[4 * q] = t.x; r[4 * q + 1] = t.y; r[4 * q + 2] = t.z; r[4 * q + 3] = t.w; }
+        for (int a = 0; a < nang; ++a) {
+            const float* C = sC + 16 * a;
+            float4* op = reinterpret_cast<float4*>(image + ((long long)a * npix + pix) * 12);
+            for (int c = 0; c < 3; ++c) {
+                const float* v = r + 4 * c;
+                float o[4];
+                for (int i = 0; i < 4; ++i) o[i] = C[4 * i] * v[0] + C[4 * i + 1] * v[1] + C[4 * i + 2] * v[2] + C[4 * i + 3] * v[3];
+                op[c] = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        }
+    }
+}
+
+__global__ void k_filter_adjoint_input(const float* __restrict__ dimage, float* __restrict__ dS, int npix, int filter,
+                                       const float* __restrict__ theta, int nang) {
+    extern __shared__ float sC[];
+    for (int a = threadIdx.x; a < nang; a += blockDim.x) {
+        float C[16], dC[16];
+        filter_matrix(filter, __ldg(theta + a), C, dC);
+        for (int k = 0; k < 16; ++k) sC[16 * a + k] = C[k];
+    }
+    __syncthreads();
+    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix; pix += (long long)gridDim.x * blockDim.x) {
+        float acc[12];
+        for (int k = 0; k < 12; ++k) acc[k] = 0.0f;
+        for (int a = 0; a < nang; ++a) {
+            const float* C = sC + 16 * a;
+            const float4* dp = reinterpret_cast<const float4*>(dimage + ((long long)a * npix + pix) * 12);
+            for (int c = 0; c < 3; ++c) {
+                float4 t = __ldg(dp + c);
+                float g[4] = {t.x, t.y, t.z, t.w};
+                for (int j = 0; j < 4; ++j)
+                    acc[4 * c + j] += C[j] * g[0] + C[4 + j] * g[1] + C[8 + j] * g[2] + C[12 + j] * g[3];
+            }
+        }
+        float4* o = reinterpret_cast<float4*>(dS + pix * 12);
+        for (int q = 0; q < 3; ++q) o[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    }
+}
+
+__global__ void k_theta_grad(const float* __restrict__ dimage, const float* __restrict__ S_adj, int npix, int filter,
+                             const float* __restrict__ theta, int nang, float* __restrict__ dtheta) {
+    extern __shared__ float sm[];
+    float* sdC = sm;               // [nang][16]
+    float* sacc = sm + 16 * nang;  // [nang]
+    for (int a = threadIdx.x; a < nang; a += blockDim.x) {
+        float C[16], dC[16];
+        filter_matrix(filter, __ldg(theta + a), C, dC);
+        for (int k = 0; k < 16; ++k) sdC[16 * a + k] = dC[k];
+        sacc[a] = 0.0f;
+    }
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long rounds = (npix + stride - 1) / stride;
+    for (long long it = 0; it < rounds; ++it) {
+        long long pix = first + it * stride;
+        bool act = pix < npix;
+        float s[12];
+        for (int k = 0; k < 12; ++k) s[k] = 0.0f;
+        if (act) {
+            const float4* sp = reinterpret_cast<const float4*>(S_adj + pix * 12);
+            for (int q = 0; q < 3; ++q) { float4 t = __ldg(sp + q); s[4 * q] = t.x; s[4 * q + 1] = t.y; s[4 * q + 2] = t.z; s[4 * q + 3] = t.w; }
+        }
+        for (int a = 0; a < nang; ++a) {
+            float v = 0.0f;
+            if (act) {
+                const float* dC = sdC + 16 * a;
+                const float4* dp = reinterpret_cast<const float4*>(dimage + ((long long)a * npix + pix) * 12);
+                for (int c = 0; c < 3; ++c) {
+                    float4 t = __ldg(dp + c);
+                    float g[4] = {t.x, t.y, t.z, t.w};
+                    for (int i = 0; i < 4; ++i)
+                        v += g[i] * (dC[4 * i] * s[4 * c] + dC[4 * i + 1] * s[4 * c + 1] + dC[4 * i + 2] * s[4 * c + 2] + dC[4 * i + 3] * s[4 * c + 3]);
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(sacc + a, v);
+        }
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < nang; a += blockDim.x)
+        if (sacc[a] != 0.0f) atomicAdd(dtheta + a, sacc[a]);
+}
+
+
+static int fold_grid(int npix, int block) {
+    long long g = ((long long)npix + block - 1) / block;
+    return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
+}
+cudaError_t launch_apply_filter(const float* raw, float* image, int npix, int filter, const float* theta,
+                                int nang, cudaStream_t st) {
+    k_apply_filter<<<fold_grid(npix, 256), 256, sizeof(float) * 16 * nang, st>>>(raw, image, npix, filter, theta, nang);
+    return cudaGetLastError();
+}
+cudaError_t launch_filter_adjoint_input(const float* dimage, float* dS, int npix, int filter,
+                                        const float* theta, int nang, cudaStream_t st) {
+    k_filter_adjoint_input<<<fold_grid(npix, 256), 256, sizeof(float) * 16 * nang, st>>>(dimage, dS, npix, filter, theta, nang);
+    return cudaGetLastError();
+}
+cudaError_t launch_theta_grad(const float* dimage, const float* S_adj, int npix, int filter, const float* theta,
+                              int nang, float* dtheta, cudaStream_t st) {
+    k_theta_grad<<<fold_grid(npix, 256), 256, sizeof(float) * 17 * nang, st>>>(dimage, S_adj, npix, filter, theta, nang, dtheta);
+    return cudaGetLastError();
+}
+
+}  // namespace dppt

@@ -21,7 +21,7 @@ struct dppt_ctx {
     size_t ws_size = 0;
     unsigned* d_status = nullptr;
     unsigned long long* d_counter = nullptr;
-    dppt_launch launch{DPPT_SCHED_GRID, 128, 0, 0};
+    dppt_launch launch{DPPT_SCHED_GRID, 128, 0, DPPT_SCHED_GRID, 128, 0};
 };
 
 struct dppt_scene {
@@ -201,6 +201,45 @@ int red_mode(int spp) {
     return 2;
 }
 
+int depth_bucket(int max_depth) {
+    for (int b : {4, 8, 16, 32, 64})
+        if (max_depth <= b) return b;
+    return -1;
+}
+
+cudaError_t launch_trace(int bucket, int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T,
+                         const LaunchCfg& L, unsigned long long* counter, unsigned* status, unsigned long long* work,
+                         cudaStream_t st) {
+    switch (bucket) {
+        case 4: return launch_trace_4(mode, S, P, G, T, L, counter, status, work, st);
+        case 8: return launch_trace_8(mode, S, P, G, T, L, counter, status, work, st);
+        case 16: return launch_trace_16(mode, S, P, G, T, L, counter, status, work, st);
+        case 32: return launch_trace_32(mode, S, P, G, T, L, counter, status, work, st);
+        case 64: return launch_trace_64(mode, S, P, G, T, L, counter, status, work, st);
+    }
+    return cudaErrorInvalidValue;
+}
+cudaError_t trace_attributes(int bucket, int mode, cudaFuncAttributes* a) {
+    switch (bucket) {
+        case 4: return trace_attributes_4(mode, a);
+        case 8: return trace_attributes_8(mode, a);
+        case 16: return trace_attributes_16(mode, a);
+        case 32: return trace_attributes_32(mode, a);
+        case 64: return trace_attributes_64(mode, a);
+    }
+    return cudaErrorInvalidValue;
+}
+int trace_occupancy(int bucket, int mode, int block, size_t smem) {
+    switch (bucket) {
+        case 4: return trace_occupancy_4(mode, block, smem);
+        case 8: return trace_occupancy_8(mode, block, smem);
+        case 16: return trace_occupancy_16(mode, block, smem);
+        case 32: return trace_occupancy_32(mode, block, smem);
+        case 64: return trace_occupancy_64(mode, block, smem);
+    }
+    return 0;
+}
+
 struct JobPlan {
     int64_t npix;
     int nang;
@@ -264,15 +303,33 @@ dppt_status ensure_ws(dppt_ctx* ctx, size_t bytes) {
     return DPPT_OK;
 }
 
-LaunchCfg launch_cfg(const dppt_ctx* ctx, int which, int max_depth) {
+struct Shape { int schedule, block, bps; };
+Shape shape_of(const dppt_ctx* ctx, int mode) {
+    const dppt_launch& l = ctx->launch;
+    return mode == 1 ? Shape{l.adj_schedule, l.adj_block_size, l.adj_blocks_per_sm}
+                     : Shape{l.schedule, l.block_size, l.blocks_per_sm};
+}
+
+LaunchCfg launch_cfg(const dppt_ctx* ctx, int bucket, int mode, size_t smem) {
+    const Shape sh = shape_of(ctx, mode);
     LaunchCfg L;
-    L.schedule = ctx->launch.schedule;
-    L.block = ctx->launch.block_size;
-    int occ = occupancy_blocks(which, max_depth, L.block);
+    L.schedule = sh.schedule;
+    L.block = sh.block;
+    int occ = trace_occupancy(bucket, mode, L.block, smem);
     if (occ < 1) occ = 1;
-    int bps = ctx->launch.blocks_per_sm > 0 ? std::min(ctx->launch.blocks_per_sm, occ) : occ;
+    int bps = sh.bps > 0 ? std::min(sh.bps, occ) : occ;
     L.grid = ctx->sm_count * bps;
     return L;
+}
+
+dppt_status check_block(dppt_ctx* ctx, int bucket, int mode, int block) {
+    cudaFuncAttributes a;
+    cudaError_t e = trace_attributes(bucket, mode, &a);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel attributes");
+    if (block > a.maxThreadsPerBlock)
+        return fail(ctx, DPPT_ERR_INVALID_ARG, "block_size exceeds the kernel's limit of " +
+                                                   std::to_string(a.maxThreadsPerBlock) + " threads");
+    return DPPT_OK;
 }
 
 DParams dparams(const dppt_params* p) { return DParams{p->tex, p->ior, p->le, p->sheet, p->theta}; }
@@ -500,14 +557,16 @@ dppt_status dppt_scene_info(const dppt_scene* s, int64_t info[5]) {
 }
 
 static void build_tables(const dppt_job* jobs, int njobs, const std::vector<JobPlan>& plan, int block,
-                         std::vector<int>& first, std::vector<JobTable>& tables) {
+                         std::vector<int>& first, std::vector<JobTable>& tables, std::vector<int>& maxd) {
     first.clear();
     tables.clear();
+    maxd.clear();
     for (int b = 0; b < njobs; b += kMaxJobsPerLaunch) {
         JobTable T;
         std::memset(&T, 0, sizeof T);
         T.njobs = std::min(kMaxJobsPerLaunch, njobs - b);
         long long chunks = 0;
+        int md = 1;
         for (int k = 0; k < T.njobs; ++k) {
             const dppt_job& j = jobs[b + k];
             DJob& J = T.job[k];
@@ -519,11 +578,35 @@ static void build_tables(const dppt_job* jobs, int njobs, const std::vector<JobP
             J.chunk_begin = chunks;
             J.sig = j.path_sig;
             chunks += (J.npaths + block - 1) / block;
+            md = std::max(md, j.max_depth);
         }
         T.total_chunks = chunks;
         first.push_back(b);
         tables.push_back(T);
+        maxd.push_back(md);
     }
+}
+
+constexpr long long kWaveCap = 1LL << 21;   // paths per wave of the wavefront schedule
+
+static long long wave_paths(const dppt_job* jobs, int njobs) {
+    long long q = 0;
+    for (int i = 0; i < njobs; ++i) {
+        long long n = (long long)jobs[i].width * jobs[i].height * jobs[i].spp;
+        long long cap = std::max<long long>(jobs[i].spp, (kWaveCap / jobs[i].spp) * jobs[i].spp);
+        q = std::max(q, std::min(n, cap));
+    }
+    return q;
+}
+
+static int max_depth_of(const dppt_job* jobs, int njobs) {
+    int d = 1;
+    for (int i = 0; i < njobs; ++i) d = std::max(d, jobs[i].max_depth);
+    return d;
+}
+
+static size_t scalar_smem(const dppt_scene* s) {
+    return sizeof(float) * (size_t)(s->d.num_ior + s->d.num_sheets + 12 * s->d.num_lights);
 }
 
 dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
@@ -535,13 +618,19 @@ dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_jo
     size_t ws = 0;
     dppt_status st = check_jobs(ctx, s, jobs, njobs, params, false, plan, ws);
     if (st != DPPT_OK) return st;
+    const Shape shape = shape_of(ctx, 0);
+    const bool wave = shape.schedule == DPPT_SCHED_WAVEFRONT;
+    const long long Q = wave ? wave_paths(jobs, njobs) : 0;
+    const int cap = max_depth_of(jobs, njobs);
+    const size_t ws_jobs = ws;
+    if (wave) ws = ws_jobs + wavefront_bytes(Q, cap);
     if ((st = ensure_ws(ctx, ws)) != DPPT_OK) return st;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    const int block = ctx->launch.block_size;
-    std::vector<int> first;
+    std::vector<int> first, maxd;
     std::vector<JobTable> tables;
-    build_tables(jobs, njobs, plan, block, first, tables);
+    build_tables(jobs, njobs, plan, shape.block, first, tables, maxd);
     DParams P = dparams(params);
+    DGrads G{nullptr, nullptr, nullptr, nullptr};
     for (size_t g = 0; g < tables.size(); ++g) {
         JobTable& T = tables[g];
         for (int k = 0; k < T.njobs; ++k) {
@@ -550,23 +639,27 @@ dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_jo
             J.raw = plan[i].filtered ? reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_a)
                                      : image + jobs[i].out_offset;
             J.dS = nullptr;
-            if (J.red_mode != 0) {
+            if (J.red_mode != 0 && !wave) {
                 cudaError_t e = cudaMemsetAsync(J.raw, 0, (size_t)plan[i].npix * 12 * sizeof(float), cs);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
             }
         }
-        LaunchCfg L = launch_cfg(ctx, 0, 0);
-        {
-            cudaFuncAttributes a;
-            if (primal_attributes(&a) == cudaSuccess && L.block > a.maxThreadsPerBlock)
-                return fail(ctx, DPPT_ERR_INVALID_ARG, "block_size exceeds the primal kernel's limit of " +
-                                                       std::to_string(a.maxThreadsPerBlock) + " threads");
+        if (wave) {
+            for (int k = 0; k < T.njobs; ++k) {
+                cudaError_t e = run_wavefront(0, s->d, P, G, T, k, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
+                                              shape.block, ctx->d_status, cs);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront primal");
+            }
+            continue;
         }
+        const int bucket = depth_bucket(maxd[g]);
+        if ((st = check_block(ctx, bucket, 0, shape.block)) != DPPT_OK) return st;
+        LaunchCfg L = launch_cfg(ctx, bucket, 0, 0);
         if (L.schedule == DPPT_SCHED_PERSISTENT) {
             cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), cs);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
         }
-        cudaError_t e = launch_primal(s->d, P, T, L, reinterpret_cast<unsigned*>(ctx->d_counter), ctx->d_status, cs);
+        cudaError_t e = launch_trace(bucket, 0, s->d, P, G, T, L, ctx->d_counter, ctx->d_status, nullptr, cs);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "primal launch");
     }
     for (int i = 0; i < njobs; ++i) {
@@ -590,21 +683,24 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
     size_t ws = 0;
     dppt_status st = check_jobs(ctx, s, jobs, njobs, params, true, plan, ws);
     if (st != DPPT_OK) return st;
+    const Shape shape = shape_of(ctx, 1);
+    const bool wave = shape.schedule == DPPT_SCHED_WAVEFRONT;
+    const long long Q = wave ? wave_paths(jobs, njobs) : 0;
+    const int cap = max_depth_of(jobs, njobs);
+    const size_t ws_jobs = ws;
+    if (wave) ws = ws_jobs + wavefront_bytes(Q, cap);
     if ((st = ensure_ws(ctx, ws)) != DPPT_OK) return st;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    const int block = ctx->launch.block_size;
-    std::vector<int> first;
+    std::vector<int> first, maxd;
     std::vector<JobTable> tables;
-    build_tables(jobs, njobs, plan, block, first, tables);
+    build_tables(jobs, njobs, plan, shape.block, first, tables, maxd);
     DParams P = dparams(params);
     DGrads G{grads->tex, grads->ior, grads->le, grads->sheet};
     for (size_t g = 0; g < tables.size(); ++g) {
         JobTable& T = tables[g];
-        int maxd = 1;
         for (int k = 0; k < T.njobs; ++k) {
             const int i = first[g] + k;
             DJob& J = T.job[k];
-            maxd = std::max(maxd, jobs[i].max_depth);
             if (plan[i].filtered) {
                 float* dS = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_a);
                 float* Sa = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_b);
@@ -614,7 +710,7 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "filter adjoint launch");
                 J.dS = dS;
                 J.raw = grads->theta ? Sa : nullptr;
-                if (J.raw && J.red_mode != 0) {
+                if (J.raw && J.red_mode != 0 && !wave) {
                     e = cudaMemsetAsync(J.raw, 0, (size_t)plan[i].npix * 12 * sizeof(float), cs);
                     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
                 }
@@ -623,19 +719,22 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
                 J.raw = nullptr;
             }
         }
-        LaunchCfg L = launch_cfg(ctx, 1, maxd);
-        {
-            cudaFuncAttributes a;
-            if (adjoint_attributes(maxd, &a) == cudaSuccess && L.block > a.maxThreadsPerBlock)
-                return fail(ctx, DPPT_ERR_INVALID_ARG, "block_size exceeds the adjoint kernel's limit of " +
-                                                       std::to_string(a.maxThreadsPerBlock) + " threads");
+        if (wave) {
+            for (int k = 0; k < T.njobs; ++k) {
+                cudaError_t e = run_wavefront(1, s->d, P, G, T, k, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
+                                              shape.block, ctx->d_status, cs);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront adjoint");
+            }
+            continue;
         }
+        const int bucket = depth_bucket(maxd[g]);
+        if ((st = check_block(ctx, bucket, 1, shape.block)) != DPPT_OK) return st;
+        LaunchCfg L = launch_cfg(ctx, bucket, 1, scalar_smem(s));
         if (L.schedule == DPPT_SCHED_PERSISTENT) {
             cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), cs);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
         }
-        cudaError_t e = launch_adjoint(s->d, P, G, T, L, maxd, reinterpret_cast<unsigned*>(ctx->d_counter),
-                                       ctx->d_status, cs);
+        cudaError_t e = launch_trace(bucket, 1, s->d, P, G, T, L, ctx->d_counter, ctx->d_status, nullptr, cs);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
     }
     if (grads->theta) {
@@ -651,6 +750,39 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
     return DPPT_OK;
 }
 
+dppt_status dppt_count_work(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
+                            const dppt_params* params, uint64_t out[8]) {
+    if (!ctx || !s || !out) return fail(ctx, DPPT_ERR_INVALID_ARG, "null argument");
+    cudaSetDevice(ctx->device);
+    std::vector<JobPlan> plan;
+    size_t ws = 0;
+    dppt_status st = check_jobs(ctx, s, jobs, njobs, params, false, plan, ws);
+    if (st != DPPT_OK) return st;
+    unsigned long long* d_work = nullptr;
+    cudaError_t e = cudaMalloc(&d_work, 8 * sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "work counters");
+    cudaMemset(d_work, 0, 8 * sizeof(unsigned long long));
+    std::vector<int> first, maxd;
+    std::vector<JobTable> tables;
+    build_tables(jobs, njobs, plan, 128, first, tables, maxd);
+    DParams P = dparams(params);
+    DGrads G{nullptr, nullptr, nullptr, nullptr};
+    LaunchCfg L{DPPT_SCHED_GRID, 128, 0};
+    for (size_t g = 0; g < tables.size(); ++g) {
+        JobTable& T = tables[g];
+        for (int k = 0; k < T.njobs; ++k) { T.job[k].raw = nullptr; T.job[k].sig = nullptr; T.job[k].dS = nullptr; }
+        e = launch_trace(depth_bucket(maxd[g]), 2, s->d, P, G, T, L, nullptr, ctx->d_status, d_work, 0);
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    unsigned long long h[8] = {0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, d_work, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(d_work);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "work count");
+    for (int k = 0; k < 8; ++k) out[k] = h[k];
+    return DPPT_OK;
+}
+
 dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int32_t njobs, size_t* bytes) {
     if (!ctx || !bytes || njobs < 0 || (njobs > 0 && !jobs)) return DPPT_ERR_INVALID_ARG;
     size_t b = 0;
@@ -663,11 +795,12 @@ dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int3
 
 dppt_status dppt_set_launch(dppt_ctx* ctx, const dppt_launch* l) {
     if (!ctx || !l) return DPPT_ERR_INVALID_ARG;
-    if (l->schedule != DPPT_SCHED_GRID && l->schedule != DPPT_SCHED_PERSISTENT)
-        return fail(ctx, DPPT_ERR_INVALID_ARG, "unknown schedule");
-    if (l->block_size != 64 && l->block_size != 128 && l->block_size != 256 && l->block_size != 512)
+    auto sched_ok = [](int s) { return s == DPPT_SCHED_GRID || s == DPPT_SCHED_PERSISTENT || s == DPPT_SCHED_WAVEFRONT; };
+    auto block_ok = [](int b) { return b == 64 || b == 128 || b == 256 || b == 512; };
+    if (!sched_ok(l->schedule) || !sched_ok(l->adj_schedule)) return fail(ctx, DPPT_ERR_INVALID_ARG, "unknown schedule");
+    if (!block_ok(l->block_size) || !block_ok(l->adj_block_size))
         return fail(ctx, DPPT_ERR_INVALID_ARG, "block_size must be 64, 128, 256 or 512");
-    if (l->blocks_per_sm < 0) return fail(ctx, DPPT_ERR_INVALID_ARG, "negative blocks_per_sm");
+    if (l->blocks_per_sm < 0 || l->adj_blocks_per_sm < 0) return fail(ctx, DPPT_ERR_INVALID_ARG, "negative blocks_per_sm");
     ctx->launch = *l;
     return DPPT_OK;
 }
@@ -680,13 +813,81 @@ dppt_status dppt_get_launch(const dppt_ctx* ctx, dppt_launch* l) {
 
 dppt_status dppt_adjoint_footprint(const dppt_ctx* ctx, int32_t max_depth, int64_t out[4]) {
     if (!ctx || !out || max_depth < 1 || max_depth > 64) return DPPT_ERR_INVALID_ARG;
+    const int bucket = depth_bucket(max_depth);
     cudaFuncAttributes a;
-    if (adjoint_attributes(max_depth, &a) != cudaSuccess) return DPPT_ERR_CUDA;
+    if (trace_attributes(bucket, 1, &a) != cudaSuccess) return DPPT_ERR_CUDA;
     out[0] = (int64_t)a.localSizeBytes;
     out[1] = a.numRegs;
-    out[2] = (int64_t)occupancy_blocks(1, max_depth, ctx->launch.block_size) * ctx->launch.block_size;
+    out[2] = (int64_t)trace_occupancy(bucket, 1, ctx->launch.adj_block_size, 1024) * ctx->launch.adj_block_size;
     out[3] = ctx->sm_count;
     return DPPT_OK;
+}
+
+dppt_status dppt_autotune(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
+                          const dppt_params* params, int32_t reps, dppt_launch* best, float* times_ms) {
+    if (!ctx || !s || !best || njobs < 1 || !jobs || reps < 1) return fail(ctx, DPPT_ERR_INVALID_ARG, "bad autotune arguments");
+    cudaSetDevice(ctx->device);
+    int64_t img = 0, nth = 1;
+    for (int i = 0; i < njobs; ++i) {
+        int64_t nang = jobs[i].filter != DPPT_FILTER_NONE ? jobs[i].num_angles : 1;
+        img = std::max(img, jobs[i].out_offset + nang * jobs[i].width * jobs[i].height * 12);
+        if (jobs[i].filter != DPPT_FILTER_NONE) nth = std::max<int64_t>(nth, jobs[i].theta_offset + nang);
+    }
+    float *image = nullptr, *dimage = nullptr, *g = nullptr;
+    const int64_t ng = s->tex_size + s->d.num_ior + 12 * s->d.num_lights + s->d.num_sheets + nth;
+    cudaError_t e = cudaMalloc(&image, sizeof(float) * img);
+    if (e == cudaSuccess) e = cudaMalloc(&dimage, sizeof(float) * img);
+    if (e == cudaSuccess) e = cudaMalloc(&g, sizeof(float) * std::max<int64_t>(ng, 1));
+    cudaStream_t st = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        cudaFree(image); cudaFree(dimage); cudaFree(g);
+        return cuda_fail(ctx, e, "autotune allocation");
+    }
+    cudaMemset(image, 0, sizeof(float) * img);
+    dppt_grads G{g, g + s->tex_size, g + s->tex_size + s->d.num_ior,
+                 g + s->tex_size + s->d.num_ior + 12 * s->d.num_lights,
+                 g + s->tex_size + s->d.num_ior + 12 * s->d.num_lights + s->d.num_sheets};
+    const dppt_launch saved = ctx->launch;
+    const int scheds[3] = {DPPT_SCHED_GRID, DPPT_SCHED_PERSISTENT, DPPT_SCHED_WAVEFRONT};
+    const int blocks[3] = {64, 128, 256};
+    float best_t[2] = {INFINITY, INFINITY};
+    dppt_launch pick = saved;
+    dppt_status result = DPPT_OK;
+    for (int si = 0; si < 3 && result == DPPT_OK; ++si)
+        for (int bi = 0; bi < 3 && result == DPPT_OK; ++bi) {
+            ctx->launch = dppt_launch{scheds[si], blocks[bi], 0, scheds[si], blocks[bi], 0};
+            float t[2] = {INFINITY, INFINITY};
+            for (int mode = 0; mode < 2; ++mode) {
+                auto call = [&]() {
+                    return mode == 0 ? dppt_render_primal(ctx, s, jobs, njobs, params, image, st)
+                                     : dppt_render_adjoint(ctx, s, jobs, njobs, params, dimage, &G, st);
+                };
+                if (call() != DPPT_OK) continue;   // shape not launchable for this kernel
+                cudaEventRecord(a, st);
+                bool ok = true;
+                for (int r = 0; r < reps && ok; ++r) ok = call() == DPPT_OK;
+                cudaEventRecord(b, st);
+                if (cudaEventSynchronize(b) != cudaSuccess) { result = cuda_fail(ctx, cudaGetLastError(), "autotune"); break; }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, a, b);
+                if (ok) t[mode] = ms / reps;
+                if (mode == 0) cudaMemcpyAsync(dimage, image, sizeof(float) * img, cudaMemcpyDeviceToDevice, st);
+            }
+            if (times_ms) { times_ms[2 * (3 * si + bi)] = t[0]; times_ms[2 * (3 * si + bi) + 1] = t[1]; }
+            if (t[0] < best_t[0]) { best_t[0] = t[0]; pick.schedule = scheds[si]; pick.block_size = blocks[bi]; pick.blocks_per_sm = 0; }
+            if (t[1] < best_t[1]) { best_t[1] = t[1]; pick.adj_schedule = scheds[si]; pick.adj_block_size = blocks[bi]; pick.adj_blocks_per_sm = 0; }
+        }
+    cudaStreamSynchronize(st);
+    cudaEventDestroy(a); cudaEventDestroy(b); cudaStreamDestroy(st);
+    cudaFree(image); cudaFree(dimage); cudaFree(g);
+    ctx->launch = result == DPPT_OK ? pick : saved;
+    *best = ctx->launch;
+    if (result == DPPT_OK) ctx->err.clear();
+    return result;
 }
 
 dppt_status dppt_sync_status(dppt_ctx* ctx, void* stream) {

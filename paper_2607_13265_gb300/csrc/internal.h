@@ -57,15 +57,16 @@ struct DGrads {
     float* sheet;
 };
 
-// reduction of a pixel's spp paths: 0 = within a warp segment, plain store
-// (spp a power of two <= 32); 1 = full warps then one atomic per warp (spp a
-// power-of-two multiple of 32); 2 = one atomic per path (any other spp)
+// One render job as the kernels see it.  A launch numbers the blocks' chunks
+// of paths consecutively over its jobs (chunk_begin); a chunk never straddles
+// two jobs.  red_mode selects how a pixel's paths are summed (see pixel_reduce).
 struct DJob {
     int cam, W, H, spp, depth, red_mode;
     unsigned long long k0, k1;
     long long npaths;
     long long chunk_begin;
-    float* raw;            // primal: mean raw Stokes per pixel [H*W][12]; adjoint: S_adj or null
+    float* raw;            // mean raw sensor-frame Stokes per pixel [H*W][12] (primal: image or
+                           // workspace; adjoint: S_adj for the filter-angle gradients, or null)
     const float* dS;       // adjoint: per-pixel adjoint of the raw image [H*W][12]
     unsigned* sig;         // optional per-path signature
 };
@@ -80,12 +81,27 @@ struct LaunchCfg {
     int schedule, block, grid;
 };
 
-// kernel entry points (kernels.cu)
-cudaError_t launch_primal(const DScene& S, const DParams& P, const JobTable& T, const LaunchCfg& L,
-                          unsigned* counter, unsigned* status, cudaStream_t st);
-cudaError_t launch_adjoint(const DScene& S, const DParams& P, const DGrads& G, const JobTable& T,
-                           const LaunchCfg& L, int max_depth, unsigned* counter, unsigned* status,
-                           cudaStream_t st);
+// megakernel entry points, one set per cache-depth bucket (trace_d<B>.cu);
+// mode 0 primal, 1 adjoint, 2 instrumented primal (work counts, no image)
+#define DPPT_DECLARE_BUCKET(B)                                                                                   \
+    cudaError_t launch_trace_##B(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T, \
+                                 const LaunchCfg& L, unsigned long long* counter, unsigned* status,             \
+                                 unsigned long long* work, cudaStream_t st);                                    \
+    cudaError_t trace_attributes_##B(int mode, cudaFuncAttributes* a);                                         \
+    int trace_occupancy_##B(int mode, int block, size_t smem);
+DPPT_DECLARE_BUCKET(4)
+DPPT_DECLARE_BUCKET(8)
+DPPT_DECLARE_BUCKET(16)
+DPPT_DECLARE_BUCKET(32)
+DPPT_DECLARE_BUCKET(64)
+#undef DPPT_DECLARE_BUCKET
+
+// wavefront schedule (wavefront.cu): workspace bytes for waves of Q paths with
+// a cache of `cap` vertices, and the run of one job of a table
+size_t wavefront_bytes(long long Q, int cap);
+cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T, int job,
+                          void* ws, long long Q, int cap, int block, unsigned* status, cudaStream_t st);
+
 // camera-filter folds: image[a][pix] = C(theta_a) raw[pix]; dS[pix] = sum_a C_a^T dI_a[pix];
 // dtheta_a += sum_pix dI_a[pix]^T dC_a/dtheta S_adj[pix]
 cudaError_t launch_apply_filter(const float* raw, float* image, int npix, int filter, const float* theta,
@@ -94,9 +110,4 @@ cudaError_t launch_filter_adjoint_input(const float* dimage, float* dS, int npix
                                         const float* theta, int nang, cudaStream_t st);
 cudaError_t launch_theta_grad(const float* dimage, const float* S_adj, int npix, int filter, const float* theta,
                               int nang, float* dtheta, cudaStream_t st);
-int adjoint_depth_bucket(int max_depth);
-cudaError_t adjoint_attributes(int max_depth, cudaFuncAttributes* attr);
-cudaError_t primal_attributes(cudaFuncAttributes* attr);
-int occupancy_blocks(int which, int max_depth, int block);   // which: 0 primal, 1 adjoint
-
 }  // namespace dppt

@@ -1,0 +1,1054 @@
+// Device code of the polarized path tracer (sm_103a), included by one
+// translation unit per cache-depth bucket.
+//
+// k_trace<MAXD, MODE> is the path-tracing megakernel: one thread per path,
+// blocks take chunks of consecutive paths (one chunk per block in the grid
+// schedule, chunks pulled from an atomic counter in the persistent schedule),
+// and the spp paths of a pixel are summed with warp shuffles.
+//  * MODE 0 (primal, phase 1 of path replay backpropagation, Sec. 3.2): each
+//    path caches its per-vertex emission E_i and compact transport factor W_i
+//    in thread-local arrays and folds them backward into L[1]; the lane sums
+//    the sensor-frame Stokes vectors of its pixel.
+//  * MODE 1 (adjoint, phases 2+3 with cached suffix replay, Sec. 4.3, Fig. 2):
+//    the same cache pass and backward fold L[i] = E_i + W_i L[i+1] (stored over
+//    E_i), then the replay regenerates the same path -- same Philox counters
+//    and the same machine code, because both passes run through the single
+//    call site of walk_step -- and accumulates a^T dE_i + a^T dW_i L[i+1] with
+//    dual numbers before a <- a^T W_i.  No Mueller matrix is inverted.
+#include <cfloat>
+
+#include "device_math.cuh"
+#include "internal.h"
+
+// resident 256-thread blocks per SM the register allocation must allow
+// (2 -> at most 128 registers per thread, 1 -> at most 255)
+#ifndef DPPT_MIN_BLOCKS_PRIMAL
+#define DPPT_MIN_BLOCKS_PRIMAL 2
+#endif
+#ifndef DPPT_MIN_BLOCKS_ADJOINT
+#define DPPT_MIN_BLOCKS_ADJOINT 1
+#endif
+
+namespace dppt {
+
+enum : unsigned { kStatusStackOverflow = 1u };
+
+// ================================================================== traversal
+struct HitRec { float t; int prim, slot; float b1, b2; };
+
+// work units of one path, gathered only by the instrumented primal instance
+struct WorkCount {
+    unsigned vertices, rays, shadow_rays, nodes, shadow_nodes, tri_tests, sph_tests;
+};
+
+__device__ __forceinline__ void child_slabs(float4 n0, float4 n1, float4 n2, f3 inv, f3 oi, float tmax,
+                                            float& tl, float& tr, bool& hl, bool& hr) {
+    float lx0 = fmaf(n0.x, inv.x, -oi.x), lx1 = fmaf(n0.y, inv.x, -oi.x);
+    float ly0 = fmaf(n0.z, inv.y, -oi.y), ly1 = fmaf(n0.w, inv.y, -oi.y);
+    float lz0 = fmaf(n2.x, inv.z, -oi.z), lz1 = fmaf(n2.y, inv.z, -oi.z);
+    float rx0 = fmaf(n1.x, inv.x, -oi.x), rx1 = fmaf(n1.y, inv.x, -oi.x);
+    float ry0 = fmaf(n1.z, inv.y, -oi.y), ry1 = fmaf(n1.w, inv.y, -oi.y);
+    float rz0 = fmaf(n2.z, inv.z, -oi.z), rz1 = fmaf(n2.w, inv.z, -oi.z);
+    float ln = fmaxf(fmaxf(fminf(lx0, lx1), fminf(ly0, ly1)), fmaxf(fminf(lz0, lz1), 0.0f));
+    float lf = fminf(fminf(fmaxf(lx0, lx1), fmaxf(ly0, ly1)), fminf(fmaxf(lz0, lz1), tmax));
+    float rn = fmaxf(fmaxf(fminf(rx0, rx1), fminf(ry0, ry1)), fmaxf(fminf(rz0, rz1), 0.0f));
+    float rf = fminf(fminf(fmaxf(rx0, rx1), fmaxf(ry0, ry1)), fminf(fmaxf(rz0, rz1), tmax));
+    hl = ln <= lf; hr = rn <= rf; tl = ln; tr = rn;
+}
+
+// Moller-Trumbore with precomputed edges; returns t or -1
+__device__ __forceinline__ float tri_test(const float4* tris, int i, f3 o, f3 d, float& b1, float& b2) {
+    float4 a = __ldg(tris + 3 * i), e1v = __ldg(tris + 3 * i + 1), e2v = __ldg(tris + 3 * i + 2);
+    f3 v0 = {a.x, a.y, a.z}, e1 = {e1v.x, e1v.y, e1v.z}, e2 = {e2v.x, e2v.y, e2v.z};
+    f3 pv = cross(d, e2);
+    float det = dot(e1, pv);
+    if (det == 0.0f) return -1.0f;
+    float inv = 1.0f / det;
+    f3 tv = o - v0;
+    float u = dot(tv, pv) * inv;
+    if (u < 0.0f || u > 1.0f) return -1.0f;
+    f3 qv = cross(tv, e1);
+    float w = dot(d, qv) * inv;
+    if (w < 0.0f || u + w > 1.0f) return -1.0f;
+    b1 = u; b2 = w;
+    return dot(e2, qv) * inv;
+}
+
+__device__ __forceinline__ float sphere_test(float4 s, f3 o, f3 d, float tmax) {
+    f3 l = o - f3{s.x, s.y, s.z};
+    float beta = dot(l, d);
+    f3 f = l - d * beta;
+    float disc = s.w * s.w - dot(f, f);
+    if (disc < 0.0f) return -1.0f;
+    float gam = dot(l, l) - s.w * s.w;
+    float h = -beta - copysignf(sqrtf(disc), beta);
+    if (h == 0.0f) return -1.0f;
+    float ta = gam / h, tb = h;
+    float t0 = fminf(ta, tb), t1 = fmaxf(ta, tb);
+    if (t0 > 0.0f && t0 < tmax) return t0;
+    if (t1 > 0.0f && t1 < tmax) return t1;
+    return -1.0f;
+}
+
+__device__ __forceinline__ f3 safe_inv(f3 d) { return {1.0f / d.x, 1.0f / d.y, 1.0f / d.z}; }
+
+// closest hit; ties in t go to the lower primitive id (triangles before spheres)
+template <bool COUNT>
+__device__ bool trace_closest(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* status, WorkCount* wc) {
+    if (COUNT) { wc->rays++; wc->sph_tests += S.num_spheres; }
+    h.t = FLT_MAX; h.prim = -1; h.slot = -1; h.b1 = h.b2 = 0.0f;
+    if (S.num_tris > 0) {
+        f3 inv = safe_inv(d);
+        f3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
+        int stack[kBvhStack];
+        int sp = 0, ref = 0;
+        for (;;) {
+            if (ref >= 0) {
+                const float4* nd = S.nodes + 4 * ref;
+                float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+                float tl, tr; bool hl, hr;
+                if (COUNT) wc->nodes++;
+                child_slabs(n0, n1, n2, inv, oi, h.t, tl, tr, hl, hr);
+                int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+                if (hl && hr) {
+                    int nr = cl, fr = cr;
+                    if (tr < tl) { nr = cr; fr = cl; }
+                    if (sp >= kBvhStack) { atomicOr(status, kStatusStackOverflow); break; }
+                    stack[sp++] = fr;
+                    ref = nr;
+                } else if (hl) ref = cl;
+                else if (hr) ref = cr;
+                else { if (sp == 0) break; ref = stack[--sp]; }
+            } else {
+                unsigned v = ~(unsigned)ref;
+                int first = (int)(v & 0x1FFFFFFu), cnt = (int)(v >> 25);
+                if (COUNT) wc->tri_tests += cnt;
+                for (int i = first; i < first + cnt; ++i) {
+                    float b1, b2;
+                    float t = tri_test(S.tris, i, o, d, b1, b2);
+                    if (t > 0.0f && t <= h.t) {
+                        int id = __float_as_int(__ldg(&S.tris[3 * i].w));
+                        if (t < h.t || id < h.prim) { h.t = t; h.prim = id; h.slot = i; h.b1 = b1; h.b2 = b2; }
+                    }
+                }
+                if (sp == 0) break;
+                ref = stack[--sp];
+            }
+        }
+    }
+    for (int k = 0; k < S.num_spheres; ++k) {
+        float t = sphere_test(__ldg(S.spheres + k), o, d, FLT_MAX);
+        int id = S.num_tris + k;
+        if (t > 0.0f && (t < h.t || (t == h.t && id < h.prim))) { h.t = t; h.prim = id; }
+    }
+    return h.prim >= 0;
+}
+
+template <bool COUNT>
+__device__ bool trace_any(const DScene& S, f3 o, f3 d, float tmax, unsigned* status, WorkCount* wc) {
+    if (COUNT) { wc->shadow_rays++; wc->sph_tests += S.num_spheres; }
+    if (S.num_tris > 0) {
+        f3 inv = safe_inv(d);
+        f3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
+        int stack[kBvhStack];
+        int sp = 0, ref = 0;
+        for (;;) {
+            if (ref >= 0) {
+                const float4* nd = S.nodes + 4 * ref;
+                float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+                float tl, tr; bool hl, hr;
+                if (COUNT) wc->shadow_nodes++;
+                child_slabs(n0, n1, n2, inv, oi, tmax, tl, tr, hl, hr);
+                int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+                if (hl && hr) {
+                    if (sp >= kBvhStack) { atomicOr(status, kStatusStackOverflow); return false; }
+                    stack[sp++] = cr;
+                    ref = cl;
+                } else if (hl) ref = cl;
+                else if (hr) ref = cr;
+                else { if (sp == 0) break; ref = stack[--sp]; }
+            } else {
+                unsigned v = ~(unsigned)ref;
+                int first = (int)(v & 0x1FFFFFFu), cnt = (int)(v >> 25);
+                if (COUNT) wc->tri_tests += cnt;
+                for (int i = first; i < first + cnt; ++i) {
+                    float b1, b2;
+                    float t = tri_test(S.tris, i, o, d, b1, b2);
+                    if (t > 0.0f && t < tmax) return true;
+                }
+                if (sp == 0) break;
+                ref = stack[--sp];
+            }
+        }
+    }
+    for (int k = 0; k < S.num_spheres; ++k) {
+        float t = sphere_test(__ldg(S.spheres + k), o, d, tmax);
+        if (t > 0.0f && t < tmax) return true;
+    }
+    return false;
+}
+
+// ================================================================== textures
+struct Taps { long long idx[4]; float w[4]; };
+__device__ __forceinline__ int wrapi(int a, int n) { int m = a % n; return m < 0 ? m + n : m; }
+__device__ __forceinline__ Taps tex_taps(const DTex& t, float u, float v) {
+    float x = u * (float)t.w - 0.5f, y = v * (float)t.h - 0.5f;
+    float fx0 = floorf(x), fy0 = floorf(y);
+    float fx = x - fx0, fy = y - fy0;
+    int x0 = (int)fx0, y0 = (int)fy0;
+    int xa = wrapi(x0, t.w), xb = wrapi(x0 + 1, t.w), ya = wrapi(y0, t.h), yb = wrapi(y0 + 1, t.h);
+    Taps tp;
+    tp.idx[0] = t.off + ((long long)ya * t.w + xa) * t.ch; tp.w[0] = (1.0f - fx) * (1.0f - fy);
+    tp.idx[1] = t.off + ((long long)ya * t.w + xb) * t.ch; tp.w[1] = fx * (1.0f - fy);
+    tp.idx[2] = t.off + ((long long)yb * t.w + xa) * t.ch; tp.w[2] = (1.0f - fx) * fy;
+    tp.idx[3] = t.off + ((long long)yb * t.w + xb) * t.ch; tp.w[3] = fx * fy;
+    return tp;
+}
+__device__ __forceinline__ float tex_value(const float* data, const Taps& tp, int c) {
+    return __ldg(data + tp.idx[0] + c) * tp.w[0] + __ldg(data + tp.idx[1] + c) * tp.w[1] +
+           __ldg(data + tp.idx[2] + c) * tp.w[2] + __ldg(data + tp.idx[3] + c) * tp.w[3];
+}
+__device__ __forceinline__ float tex_lookup(const DScene& S, const float* data, int tex, int c, float u, float v) {
+    DTex t = S.tex[tex];
+    Taps tp = tex_taps(t, u, v);
+    return tex_value(data, tp, min(c, t.ch - 1));
+}
+
+// ================================================================== vertex context
+// One vertex of a sampled path.  Sampling uses the (detached) parameter values;
+// the Mueller values are evaluated from this record (float or dual numbers).
+struct VCtx {
+    f3 x, ng, n, wo, wl, wi;
+    float tu, tv, w_emit, nee_w, pdf, p_event;
+    int prim, mat, light, nee_light, event;
+    bool emit, nee, scatter, outside;
+};
+
+__device__ __forceinline__ float ggx_pdf(float alpha, f3 n, f3 wo, f3 wi) {
+    f3 h = normalize(wo + wi);
+    float ch = dot(h, n), oh = dot(wo, h);
+    if (ch <= 0.0f || oh <= 0.0f) return 0.0f;
+    return ggx_D<float>(ch, alpha) * ch / (4.0f * oh);
+}
+__device__ __forceinline__ float mean_albedo(const DScene& S, const DParams& P, const DMat& m, float u, float v) {
+    if (m.albedo_tex < 0) return 1.0f;
+    DTex t = S.tex[m.albedo_tex];
+    Taps tp = tex_taps(t, u, v);
+    float a = 0.0f;
+    for (int c = 0; c < 3; ++c) a += tex_value(P.tex, tp, min(c, t.ch - 1));
+    return a / 3.0f;
+}
+__device__ __forceinline__ float plastic_pspec(const DScene& S, const DParams& P, const DMat& m, const VCtx& vc) {
+    float eta = __ldg(P.ior + m.ior_index);
+    float fs = fresnel_unpolarized(dot(vc.wo, vc.n), 1.0f, eta);
+    float fd = mean_albedo(S, P, m, vc.tu, vc.tv);
+    float tot = fs + fd;
+    return tot > 0.0f ? fs / tot : 0.5f;
+}
+__device__ __forceinline__ float bsdf_pdf(const DScene& S, const DParams& P, const DMat& m, const VCtx& vc, f3 wi) {
+    float ci = dot(wi, vc.n);
+    if (ci <= 0.0f) return 0.0f;
+    if (m.type == DPPT_MAT_DIFFUSE) return ci * kInvPi;
+    float al = tex_lookup(S, P.tex, m.rough_tex, 0, vc.tu, vc.tv);
+    if (m.type == DPPT_MAT_CONDUCTOR_GGX) return ggx_pdf(al, vc.n, vc.wo, wi);
+    if (m.type == DPPT_MAT_PLASTIC_GGX) {
+        float ps = plastic_pspec(S, P, m, vc);
+        return ps * ggx_pdf(al, vc.n, vc.wo, wi) + (1.0f - ps) * ci * kInvPi;
+    }
+    return 0.0f;
+}
+
+__device__ __forceinline__ unsigned fnv(unsigned h, unsigned x) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { h ^= (x >> (8 * k)) & 0xffu; h *= 16777619u; }
+    return h;
+}
+
+__device__ __forceinline__ DLight load_light(const DScene& S, int l) { return S.lights[l]; }
+
+// ================================================================== compact Mueller operators
+// W = R(ro) . M . R(ri) per channel with M = [[A+D,B,0,0],[B,A,0,0],[0,0,C,S],[0,0,-S,C]]:
+// every operator of the scene (depolarizer, Fresnel R/T, pBRDF lobes, polarizer,
+// retarder) has this form in its own s/p or axis frame.
+template <class T> struct Compact {
+    Rot<T> ri, ro;
+    T A[3], B[3], C[3], S[3], D[3];
+};
+template <class T> __device__ __forceinline__ void compact_zero(Compact<T>& W) {
+    W.ri = {T(1.0f), T(0.0f)}; W.ro = {T(1.0f), T(0.0f)};
+    for (int c = 0; c < 3; ++c) W.A[c] = W.B[c] = W.C[c] = W.S[c] = W.D[c] = T(0.0f);
+}
+// y = W_c x  (column)
+template <class T, class V> __device__ __forceinline__ void compact_apply(const Compact<T>& W, int c, const V x[4], V y[4]) {
+    V v[4] = {x[0], x[1], x[2], x[3]};
+    rot_apply(W.ri, v);
+    y[0] = (W.A[c] + W.D[c]) * v[0] + W.B[c] * v[1];
+    y[1] = W.B[c] * v[0] + W.A[c] * v[1];
+    y[2] = W.C[c] * v[2] + W.S[c] * v[3];
+    y[3] = W.C[c] * v[3] - W.S[c] * v[2];
+    rot_apply(W.ro, y);
+}
+// a^T <- a^T W_c  (row)
+template <class V> __device__ __forceinline__ void compact_row(const Compact<float>& W, int c, V a[4]) {
+    V u[4] = {a[0], a[1], a[2], a[3]};
+    rot_apply_row(W.ro, u);
+    a[0] = u[0] * (W.A[c] + W.D[c]) + u[1] * W.B[c];
+    a[1] = u[0] * W.B[c] + u[1] * W.A[c];
+    a[2] = u[2] * W.C[c] - u[3] * W.S[c];
+    a[3] = u[2] * W.S[c] + u[3] * W.C[c];
+    rot_apply_row(W.ri, a);
+}
+__device__ __forceinline__ Compact<float> compact_value(const Compact<D3>& W) {
+    Compact<float> r;
+    r.ri = {W.ri.c.v, W.ri.s.v}; r.ro = {W.ro.c.v, W.ro.s.v};
+    for (int c = 0; c < 3; ++c) { r.A[c] = W.A[c].v; r.B[c] = W.B[c].v; r.C[c] = W.C[c].v; r.S[c] = W.S[c].v; r.D[c] = W.D[c].v; }
+    return r;
+}
+
+template <class T> __device__ __forceinline__ T seeded(float v, int slot) {
+    return T(v);
+}
+template <> __device__ __forceinline__ D3 seeded<D3>(float v, int slot) {
+    return D3(v, slot == 0 ? 1.0f : 0.0f, slot == 1 ? 1.0f : 0.0f, slot == 2 ? 1.0f : 0.0f);
+}
+
+// s axis of a reflection/refraction: normal to the plane of (a, b), or any
+// axis normal to a when the plane degenerates
+__device__ __forceinline__ f3 s_axis(f3 a, f3 b) {
+    f3 sx = cross(a, b);
+    float sl = len(sx);
+    return sl > 1e-12f ? sx * (1.0f / sl) : onb_t1(a);
+}
+
+// pBRDF value f(wo, wi) without the cosine, as a compact operator.
+template <class T>
+__device__ void bsdf_compact(const DScene& S, const DParams& P, const DMat& m, const VCtx& vc, f3 wi, Compact<T>& f) {
+    compact_zero(f);
+    float ci = dot(wi, vc.n), co = dot(vc.wo, vc.n);
+    if (ci <= 0.0f || co <= 0.0f) return;
+    T alb[3];
+    if (m.albedo_tex >= 0) {
+        DTex t = S.tex[m.albedo_tex];
+        Taps tp = tex_taps(t, vc.tu, vc.tv);
+        for (int c = 0; c < 3; ++c) alb[c] = seeded<T>(tex_value(P.tex, tp, min(c, t.ch - 1)), 2);
+    } else {
+        for (int c = 0; c < 3; ++c) alb[c] = T(1.0f);
+    }
+    if (m.type == DPPT_MAT_DIFFUSE) {
+        for (int c = 0; c < 3; ++c) f.D[c] = alb[c] * kInvPi;
+        return;
+    }
+    f3 h = normalize(vc.wo + wi);
+    float ch = dot(h, vc.n), oh = dot(vc.wo, h), ih = dot(wi, h);
+    T al = seeded<T>(tex_lookup(S, P.tex, m.rough_tex, 0, vc.tu, vc.tv), 0);
+    T k = ggx_D<T>(ch, al) * ggx_G1<T>(co, oh, al) * ggx_G1<T>(ci, ih, al) / (4.0f * co * ci);
+    ABCS<T> F;
+    if (m.type == DPPT_MAT_CONDUCTOR_GGX) {
+        ABCS<float> Ff = fresnel_reflect<float>(ih, 1.0f, Cx<float>{m.eta_re, m.eta_im});
+        F = {T(Ff.A), T(Ff.B), T(Ff.C), T(Ff.S)};
+    } else {
+        F = fresnel_reflect_real<T>(ih, T(1.0f), seeded<T>(__ldg(P.ior + m.ior_index), 1));
+    }
+    f3 sax = s_axis(vc.wo, h);
+    Rot<float> ri = rot_between(-wi, onb_t1(-wi), sax);
+    Rot<float> ro = rot_between(vc.wo, sax, onb_t1(vc.wo));
+    f.ri = {T(ri.c), T(ri.s)}; f.ro = {T(ro.c), T(ro.s)};
+    for (int c = 0; c < 3; ++c) {
+        T kc = m.type == DPPT_MAT_CONDUCTOR_GGX ? k * alb[c] : k;
+        f.A[c] = F.A * kc; f.B[c] = F.B * kc; f.C[c] = F.C * kc; f.S[c] = F.S * kc;
+        if (m.type == DPPT_MAT_PLASTIC_GGX) f.D[c] = alb[c] * kInvPi;
+    }
+}
+
+template <class T> __device__ __forceinline__ void compact_scale(Compact<T>& W, float s) {
+    for (int c = 0; c < 3; ++c) { W.A[c] = W.A[c] * s; W.B[c] = W.B[c] * s; W.C[c] = W.C[c] * s; W.S[c] = W.S[c] * s; W.D[c] = W.D[c] * s; }
+}
+
+// Emitted Stokes of light l arriving along propagation p, rotated from the
+// emitter frame (x = e1 projected) into the canonical frame of p.
+__device__ __forceinline__ Rot<float> emitter_rot(const DLight& L, f3 p) {
+    f3 e1 = ld3(L.e1);
+    f3 xe = e1 - p * dot(e1, p);
+    return rot_between(p, xe, onb_t1(p));
+}
+
+// E_v (per channel, float) and W_v (compact, T) for one vertex.
+template <class T>
+__device__ void eval_vertex(const DScene& S, const DParams& P, const VCtx& vc, float E[3][4], Compact<T>& W,
+                            Compact<T>* fnee) {
+    const DMat m = S.mats[vc.mat];
+    for (int c = 0; c < 3; ++c) E[c][0] = E[c][1] = E[c][2] = E[c][3] = 0.0f;
+    if (vc.emit) {
+        DLight L = load_light(S, vc.light);
+        Rot<float> R = emitter_rot(L, vc.wo);
+        for (int c = 0; c < 3; ++c) {
+            const float* le = P.le + 12 * vc.light + 4 * c;
+            float v[4] = {__ldg(le), __ldg(le + 1), __ldg(le + 2), __ldg(le + 3)};
+            rot_apply(R, v);
+            for (int k = 0; k < 4; ++k) E[c][k] = v[k] * vc.w_emit;
+        }
+    }
+    if (m.emission > 0.0f)
+        for (int c = 0; c < 3; ++c) E[c][0] += m.emission;
+    if (vc.nee) {
+        DLight L = load_light(S, vc.nee_light);
+        Rot<float> R = emitter_rot(L, -vc.wl);
+        Compact<T> f;
+        bsdf_compact<T>(S, P, m, vc, vc.wl, f);
+        Compact<float> fv;
+        if constexpr (sizeof(T) == sizeof(float)) fv = *reinterpret_cast<Compact<float>*>(&f);
+        else fv = compact_value(*reinterpret_cast<Compact<D3>*>(&f));
+        for (int c = 0; c < 3; ++c) {
+            const float* le = P.le + 12 * vc.nee_light + 4 * c;
+            float v[4] = {__ldg(le), __ldg(le + 1), __ldg(le + 2), __ldg(le + 3)};
+            rot_apply(R, v);
+            float y[4];
+            compact_apply(fv, c, v, y);
+            for (int k = 0; k < 4; ++k) E[c][k] += y[k] * vc.nee_w;
+        }
+        if (fnee) *fnee = f;
+    }
+    compact_zero(W);
+    if (!vc.scatter) return;
+    f3 wi = vc.wi;
+    if (m.type == DPPT_MAT_DIFFUSE || m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX) {
+        bsdf_compact<T>(S, P, m, vc, wi, W);
+        compact_scale(W, dot(wi, vc.n) / vc.pdf);
+    } else if (m.type == DPPT_MAT_SMOOTH_DIELECTRIC) {
+        T eta = seeded<T>(__ldg(P.ior + m.ior_index), 1);
+        T eo = vc.outside ? T(1.0f) : eta, et = vc.outside ? eta : T(1.0f);
+        float c = dot(vc.wo, vc.n);
+        f3 sax = s_axis(vc.wo, vc.n);
+        Rot<float> ri = rot_between(-wi, onb_t1(-wi), sax);
+        Rot<float> ro = rot_between(vc.wo, sax, onb_t1(vc.wo));
+        ABCS<T> F;
+        T sc;
+        if (vc.event == 1) {
+            F = fresnel_reflect_real<T>(c, eo, et);
+            sc = T(1.0f / vc.p_event);
+        } else {
+            float ci = fabsf(dot(wi, vc.n));
+            F = fresnel_transmit<T>(ci, et, eo);
+            T q = eo / et;
+            sc = q * q * (1.0f / vc.p_event);
+        }
+        W.ri = {T(ri.c), T(ri.s)}; W.ro = {T(ro.c), T(ro.s)};
+        for (int cc = 0; cc < 3; ++cc) { W.A[cc] = F.A * sc; W.B[cc] = F.B * sc; W.C[cc] = F.C * sc; W.S[cc] = F.S * sc; }
+    } else if (m.type == DPPT_MAT_POLARIZER_SHEET || m.type == DPPT_MAT_RETARDER_SHEET) {
+        f3 p = vc.wo;
+        T th = seeded<T>(__ldg(P.sheet + m.sheet_index), 0);
+        T ct = tcos(th), st = tsin(th);
+        T t[3] = {ct * m.t1[0] + st * m.t2[0], ct * m.t1[1] + st * m.t2[1], ct * m.t1[2] + st * m.t2[2]};
+        T tp = t[0] * p.x + t[1] * p.y + t[2] * p.z;
+        T xf[3] = {t[0] - tp * p.x, t[1] - tp * p.y, t[2] - tp * p.z};
+        W.ri = rot_to_param<T>(p, onb_t1(p), xf);
+        W.ro = rot_from_param<T>(p, xf, onb_t1(p));
+        float A, B, C, Sv;
+        if (m.type == DPPT_MAT_POLARIZER_SHEET) { A = 0.5f; B = 0.5f; C = 0.0f; Sv = 0.0f; }
+        else { A = 1.0f; B = 0.0f; sincosf(m.retard, &Sv, &C); }
+        for (int cc = 0; cc < 3; ++cc) { W.A[cc] = T(A); W.B[cc] = T(B); W.C[cc] = T(C); W.S[cc] = T(Sv); }
+    }
+}
+
+// ================================================================== path walk
+__device__ __forceinline__ f3 camera_dir(const DCam& c, int W, int H, int px, int py, float ju, float jv) {
+    float aspect = (float)W / (float)H;
+    float sx = (2.0f * ((float)px + ju) / (float)W - 1.0f) * c.tanh * aspect;
+    float sy = (1.0f - 2.0f * ((float)py + jv) / (float)H) * c.tanh;
+    return normalize(ld3(c.fwd) + ld3(c.right) * sx + ld3(c.up) * sy);
+}
+// rotation from the frame of light arriving at the camera along -d1 into the
+// sensor frame (x = camera right projected normal to the ray)
+__device__ __forceinline__ Rot<float> camera_rot(const DCam& c, f3 d1) {
+    f3 p = -d1;
+    f3 xr = ld3(c.right);
+    f3 xs = xr - p * dot(xr, p);
+    return rot_between(p, onb_t1(p), xs);
+}
+
+// State of the path a lane is tracing (sampling uses the detached parameters).
+struct Walk {
+    f3 o, d, xprev, d1;
+    float prev_pdf;
+    unsigned sig;
+    int v, nv;
+    bool prev_delta;
+};
+
+__device__ __forceinline__ void walk_begin(const DScene& S, const DJob& J, unsigned long long pid, long long pix,
+                                           Walk& w) {
+    const DCam& cam = S.cams[J.cam];
+    U8 u0 = draw8(J.k0, J.k1, pid, 0u);
+    w.d = camera_dir(cam, J.W, J.H, (int)(pix % J.W), (int)(pix / J.W), u0.u[0], u0.u[1]);
+    w.d1 = w.d;
+    w.o = ld3(cam.org);
+    w.xprev = w.o;
+    w.prev_delta = true;
+    w.prev_pdf = 0.0f;
+    w.sig = 2166136261u;
+    w.v = 1;
+    w.nv = 0;
+}
+
+// A vertex is produced in three steps so that the wavefront schedule can run
+// them as separate kernels: walk_shade (given the closest hit: surface data,
+// emission MIS weight, light sample and BSDF sample), the shadow ray of the
+// light sample, and walk_finish (next-event weight, signature, per-vertex
+// action, next ray).  walk_step chains them for the megakernel.
+struct NeePending {
+    f3 o2, dir, wl;
+    float tmax, dist2, cl, cx;
+    int l;
+    int state;   // 2: no light sample at this vertex, 0: sample facing away, 1: shadow ray pending
+};
+struct Shade {
+    f3 wi;
+    float pdf;
+    unsigned ev;
+    bool ok, terminal, delta;
+};
+
+__device__ __forceinline__ void walk_shade(const DScene& S, const DParams& P, const DJob& J, unsigned long long pid,
+                                           const Walk& w, const HitRec& h, VCtx& vc, NeePending& ne, Shade& sh) {
+    const int nL = S.num_lights;
+    vc.prim = h.prim;
+    vc.x = w.o + w.d * h.t;
+    vc.wo = -w.d;
+    vc.emit = vc.nee = vc.scatter = false;
+    vc.event = 0; vc.w_emit = 0.0f; vc.nee_w = 0.0f; vc.pdf = 1.0f; vc.p_event = 1.0f;
+    vc.outside = true; vc.nee_light = -1; vc.wl = f3{0.f, 0.f, 0.f}; vc.wi = vc.wl;
+    if (h.prim < S.num_tris) {
+        int f = h.prim;
+        float4 e1v = __ldg(S.tris + 3 * h.slot + 1), e2v = __ldg(S.tris + 3 * h.slot + 2);
+        vc.ng = normalize(cross(f3{e1v.x, e1v.y, e1v.z}, f3{e2v.x, e2v.y, e2v.z}));
+        vc.mat = __ldg(S.tri_mat + f);
+        vc.light = __ldg(S.tri_light + f);
+        const float* uv = S.tri_uv + 6 * (long long)f;
+        float w0 = 1.0f - h.b1 - h.b2;
+        vc.tu = w0 * __ldg(uv) + h.b1 * __ldg(uv + 2) + h.b2 * __ldg(uv + 4);
+        vc.tv = w0 * __ldg(uv + 1) + h.b1 * __ldg(uv + 3) + h.b2 * __ldg(uv + 5);
+    } else {
+        int k = h.prim - S.num_tris;
+        float4 sp = __ldg(S.spheres + k);
+        vc.ng = (vc.x - f3{sp.x, sp.y, sp.z}) * (1.0f / sp.w);
+        vc.mat = __ldg(S.sph_mat + k);
+        vc.tu = atan2f(vc.ng.z, vc.ng.x) * (0.5f * kInvPi) + 0.5f;
+        vc.tv = acosf(fmaxf(-1.0f, fminf(1.0f, vc.ng.y))) * kInvPi;
+        vc.light = -1;
+    }
+    vc.n = dot(vc.ng, vc.wo) >= 0.0f ? vc.ng : -vc.ng;
+    const DMat m = S.mats[vc.mat];
+    if (vc.light >= 0) {
+        DLight L = load_light(S, vc.light);
+        float cl = dot(ld3(L.n), vc.wo);
+        if (cl > 0.0f) {
+            vc.emit = true;
+            if (w.prev_delta) vc.w_emit = 1.0f;
+            else {
+                f3 dx = vc.x - w.xprev;
+                float pl = dot(dx, dx) / (cl * L.area * (float)nL);
+                vc.w_emit = w.prev_pdf * w.prev_pdf / (w.prev_pdf * w.prev_pdf + pl * pl);
+            }
+        }
+    }
+    sh.ev = 0u;
+    sh.ok = false;
+    sh.pdf = 1.0f;
+    sh.wi = f3{0.f, 0.f, 0.f};
+    ne.state = 2;
+    sh.terminal = m.type == DPPT_MAT_EMITTER || w.v == J.depth;
+    sh.delta = m.type == DPPT_MAT_SMOOTH_DIELECTRIC || m.type == DPPT_MAT_POLARIZER_SHEET ||
+               m.type == DPPT_MAT_RETARDER_SHEET;
+    if (sh.terminal) return;
+    U8 U = draw8(J.k0, J.k1, pid, (unsigned)w.v);
+    if (!sh.delta && nL > 0) {
+        int l = min((int)(U.u[4] * (float)nL), nL - 1);
+        DLight L = load_light(S, l);
+        f3 y = ld3(L.o) + ld3(L.e1) * U.u[5] + ld3(L.e2) * U.u[6];
+        f3 dv = y - vc.x;
+        float dist2 = dot(dv, dv), dist = sqrtf(dist2);
+        f3 wl = dv * (1.0f / dist);
+        float cl = -dot(ld3(L.n), wl), cx = dot(vc.n, wl);
+        ne.state = 0;
+        if (cl > 0.0f && cx > 0.0f) {
+            f3 o2 = vc.x + vc.n * S.eps;
+            f3 dd = y - o2;
+            float dl = len(dd);
+            ne.o2 = o2;
+            ne.dir = dd * (1.0f / dl);
+            ne.tmax = dl * (1.0f - 1e-4f);
+            ne.wl = wl;
+            ne.dist2 = dist2;
+            ne.cl = cl;
+            ne.cx = cx;
+            ne.l = l;
+            ne.state = 1;
+        }
+    }
+    bool ok = true;
+    f3 wi = {0.f, 0.f, 0.f};
+    if (m.type == DPPT_MAT_DIFFUSE || m.type == DPPT_MAT_PLASTIC_GGX || m.type == DPPT_MAT_CONDUCTOR_GGX) {
+        bool spec = m.type == DPPT_MAT_CONDUCTOR_GGX;
+        if (m.type == DPPT_MAT_PLASTIC_GGX) { spec = U.u[0] < plastic_pspec(S, P, m, vc); sh.ev = spec ? 1u : 2u; }
+        f3 t1 = onb_t1(vc.n), t2 = onb_t2(vc.n);
+        if (!spec) {
+            float r = sqrtf(U.u[1]), sph, cph;
+            sincosf(2.0f * kPi * U.u[2], &sph, &cph);
+            wi = t1 * (r * cph) + t2 * (r * sph) + vc.n * sqrtf(fmaxf(0.0f, 1.0f - U.u[1]));
+        } else {
+            float al = tex_lookup(S, P.tex, m.rough_tex, 0, vc.tu, vc.tv);
+            float tan2 = al * al * U.u[1] / (1.0f - U.u[1]);
+            float ch = 1.0f / sqrtf(1.0f + tan2);
+            float shv = sqrtf(fmaxf(0.0f, 1.0f - ch * ch));
+            float sph, cph;
+            sincosf(2.0f * kPi * U.u[2], &sph, &cph);
+            f3 hv = t1 * (shv * cph) + t2 * (shv * sph) + vc.n * ch;
+            float oh = dot(vc.wo, hv);
+            if (oh <= 0.0f) ok = false;
+            else wi = hv * (2.0f * oh) - vc.wo;
+        }
+        if (ok && dot(wi, vc.n) <= 0.0f) ok = false;
+        if (ok) { sh.pdf = bsdf_pdf(S, P, m, vc, wi); if (!(sh.pdf > 0.0f)) ok = false; }
+    } else if (m.type == DPPT_MAT_SMOOTH_DIELECTRIC) {
+        float eta = __ldg(P.ior + m.ior_index);
+        float co = dot(vc.wo, vc.ng);
+        vc.outside = co > 0.0f;
+        float eo = vc.outside ? 1.0f : eta, et = vc.outside ? eta : 1.0f;
+        float c = fabsf(co);
+        float F = fresnel_unpolarized(c, eo, et);
+        float r = eo / et, s2 = r * r * (1.0f - c * c);
+        if (s2 >= 1.0f) F = 1.0f;
+        if (U.u[0] < F) {
+            sh.ev = 1u; vc.p_event = F;
+            wi = vc.n * (2.0f * c) - vc.wo;
+        } else {
+            sh.ev = 2u; vc.p_event = 1.0f - F;
+            float ct = sqrtf(1.0f - s2);
+            wi = vc.n * (r * c - ct) - vc.wo * r;
+        }
+        sh.pdf = 1.0f;
+    } else {
+        wi = -vc.wo;
+        sh.pdf = 1.0f;
+    }
+    sh.ok = ok;
+    sh.wi = wi;
+}
+
+// Completes the vertex once the visibility of its light sample is known;
+// returns true when the path continues.
+template <class Vis>
+__device__ __forceinline__ bool walk_finish(const DScene& S, const DParams& P, Walk& w, VCtx& vc,
+                                            const NeePending& ne, bool visible, const Shade& sh, Vis& vis) {
+    unsigned neeflag = 2u;
+    if (!sh.terminal) {
+        vc.event = (int)sh.ev;
+        vc.pdf = sh.pdf;
+        if (ne.state != 2) {
+            neeflag = 0u;
+            if (ne.state == 1 && visible) {
+                const DMat m = S.mats[vc.mat];
+                DLight L = load_light(S, ne.l);
+                float pl = ne.dist2 / (ne.cl * L.area * (float)S.num_lights);
+                float pb = bsdf_pdf(S, P, m, vc, ne.wl);
+                float wm = pl * pl / (pl * pl + pb * pb);
+                vc.nee = true; vc.nee_light = ne.l; vc.wl = ne.wl;
+                vc.nee_w = ne.cx / pl * wm;
+                neeflag = 1u;
+            }
+        }
+    }
+    w.sig = fnv(fnv(fnv(w.sig, (unsigned)vc.prim), sh.ev), neeflag);
+    vc.scatter = !sh.terminal && sh.ok;
+    vc.wi = sh.wi;
+    ++w.nv;
+    vis(vc);
+    if (!vc.scatter) return false;
+    float side = dot(sh.wi, vc.ng) >= 0.0f ? 1.0f : -1.0f;
+    w.xprev = vc.x;
+    w.o = vc.x + vc.ng * (side * S.eps);
+    w.d = sh.wi;
+    w.prev_delta = sh.delta;
+    w.prev_pdf = sh.pdf;
+    ++w.v;
+    return true;
+}
+
+// Traces vertex w.v of the path and calls vis(vc) for it.  Returns true when
+// the path continues with vertex w.v + 1.
+template <class Vis, bool COUNT>
+__device__ __forceinline__ bool walk_step(const DScene& S, const DParams& P, const DJob& J, unsigned long long pid,
+                                          Walk& w, Vis& vis, unsigned* status, WorkCount* wc) {
+    HitRec h;
+    if (!trace_closest<COUNT>(S, w.o, w.d, h, status, wc)) return false;
+    if (COUNT) wc->vertices++;
+    VCtx vc;
+    NeePending ne;
+    Shade sh;
+    walk_shade(S, P, J, pid, w, h, vc, ne, sh);
+    bool visible = false;
+    if (ne.state == 1) visible = !trace_any<COUNT>(S, ne.o2, ne.dir, ne.tmax, status, wc);
+    return walk_finish(S, P, w, vc, ne, visible, sh, vis);
+}
+
+// Warp-aggregated scatter-add: lanes adding to the same element combine their
+// values first, then one lane issues the atomic.
+__device__ __forceinline__ void atomic_add_agg(float* base, long long idx, float val) {
+    const unsigned mask = __activemask();
+    const unsigned peers = __match_any_sync(mask, (unsigned long long)idx);
+    const int lane = threadIdx.x & 31;
+    float sum;
+    if (peers == 0xffffffffu) {
+        sum = val;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    } else {
+        sum = 0.0f;
+        for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, val, __ffs(m) - 1);
+    }
+    if (lane == __ffs(peers) - 1 && sum != 0.0f) atomicAdd(base + idx, sum);
+}
+
+// ================================================================== per-vertex actions
+// Where a path's cached E_v / compact W_v live: thread-local arrays (megakernel)
+// or global memory laid out [vertex][component][path] (wavefront).
+template <int MAXD>
+struct LocalCache {
+    float (*cE)[12];
+    float (*cW)[19];
+    static constexpr int cap = MAXD;
+    __device__ __forceinline__ float& e(int v, int k) const { return cE[v][k]; }
+    __device__ __forceinline__ float& w(int v, int k) const { return cW[v][k]; }
+};
+struct GlobalCache {
+    float* base;
+    long long Q, q;
+    int cap;
+    __device__ __forceinline__ float& e(int v, int k) const { return base[((long long)v * 31 + k) * Q + q]; }
+    __device__ __forceinline__ float& w(int v, int k) const { return base[((long long)v * 31 + 12 + k) * Q + q]; }
+};
+
+// Pass 0 caches E_v (overwritten later by the suffix L[v]) and the compact W_v;
+// pass 1 (adjoint only) replays the vertex with dual numbers.
+template <class Cache>
+struct PathVis {
+    const DScene* S;
+    const DParams* P;
+    const DGrads* G;
+    float* sgrad;       // shared scalar-gradient accumulators [ior | sheet | le]
+    Cache C;
+    float a[3][4];      // adjoint row a^T = dI^T C R_cam W_1 ... W_{v-1}
+    int n, i, phase;
+
+    __device__ __forceinline__ void operator()(const VCtx& vc) {
+        if (phase == 0) {
+            if (n >= C.cap) return;
+            float E[3][4];
+            Compact<float> W;
+            eval_vertex<float>(*S, *P, vc, E, W, nullptr);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) C.e(n, 4 * c + k) = E[c][k];
+            C.w(n, 0) = W.ri.c; C.w(n, 1) = W.ri.s; C.w(n, 2) = W.ro.c; C.w(n, 3) = W.ro.s;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                C.w(n, 4 + c) = W.A[c]; C.w(n, 7 + c) = W.B[c]; C.w(n, 10 + c) = W.C[c];
+                C.w(n, 13 + c) = W.S[c]; C.w(n, 16 + c) = W.D[c];
+            }
+            ++n;
+            return;
+        }
+        if (i >= n) return;
+        replay_vertex(vc);
+        ++i;
+    }
+
+    // backward fold of the cached vertices into suffixes; returns L[1] in L0
+    __device__ __forceinline__ void fold(float L0[12]) {
+        float L[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) L[k] = 0.0f;
+        for (int v = n - 1; v >= 0; --v) {
+            Compact<float> W;
+            W.ri = {C.w(v, 0), C.w(v, 1)}; W.ro = {C.w(v, 2), C.w(v, 3)};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                W.A[c] = C.w(v, 4 + c); W.B[c] = C.w(v, 7 + c); W.C[c] = C.w(v, 10 + c);
+                W.S[c] = C.w(v, 13 + c); W.D[c] = C.w(v, 16 + c);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float y[4];
+                compact_apply(W, c, &L[4 * c], y);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) L[4 * c + k] = C.e(v, 4 * c + k) + y[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 12; ++k) C.e(v, k) = L[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) L0[k] = L[k];
+    }
+
+    __device__ void replay_vertex(const VCtx& vc) {
+        const DMat m = S->mats[vc.mat];
+        float E[3][4];
+        Compact<D3> W, f;
+        eval_vertex<D3>(*S, *P, vc, E, W, &f);
+        float Ln[3][4];
+        if (i + 1 < n) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) Ln[k >> 2][k & 3] = C.e(i + 1, k);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) Ln[k >> 2][k & 3] = 0.0f;
+        }
+        // local vector-Jacobian products: J_c = a_c^T (E_c + W_c L_c) with dual numbers
+        float g_slot0 = 0.0f, g_eta = 0.0f, g_alb[3];
+        Compact<float> fv;
+        if (vc.nee) fv = compact_value(f);
+        Rot<float> Rle = {1.0f, 0.0f};
+        if (vc.nee) Rle = emitter_rot(load_light(*S, vc.nee_light), -vc.wl);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            D3 x[4] = {D3(Ln[c][0]), D3(Ln[c][1]), D3(Ln[c][2]), D3(Ln[c][3])};
+            D3 y[4];
+            compact_apply(W, c, x, y);
+            D3 J = y[0] * a[c][0] + y[1] * a[c][1] + y[2] * a[c][2] + y[3] * a[c][3];
+            if (vc.nee) {
+                const float* le = P->le + 12 * vc.nee_light + 4 * c;
+                float lv[4] = {__ldg(le), __ldg(le + 1), __ldg(le + 2), __ldg(le + 3)};
+                rot_apply(Rle, lv);
+                D3 xe[4] = {D3(lv[0] * vc.nee_w), D3(lv[1] * vc.nee_w), D3(lv[2] * vc.nee_w), D3(lv[3] * vc.nee_w)};
+                D3 ye[4];
+                compact_apply(f, c, xe, ye);
+                J = J + ye[0] * a[c][0] + ye[1] * a[c][1] + ye[2] * a[c][2] + ye[3] * a[c][3];
+            }
+            g_slot0 += J.d0;
+            g_eta += J.d1;
+            g_alb[c] = J.d2;
+        }
+        // emitter Stokes gradients (linear): w R^T a for a hit, nee_w R^T f^T a for NEE
+        if (vc.emit || vc.nee) {
+            const int base = S->num_ior + S->num_sheets;
+            Rot<float> Re = {1.0f, 0.0f};
+            if (vc.emit) Re = emitter_rot(load_light(*S, vc.light), vc.wo);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (vc.emit) {
+                    float g[4] = {a[c][0], a[c][1], a[c][2], a[c][3]};
+                    rot_apply_row(Re, g);
+                    for (int k = 0; k < 4; ++k)
+                        if (g[k] != 0.0f) atomicAdd(sgrad + base + 12 * vc.light + 4 * c + k, g[k] * vc.w_emit);
+                }
+                if (vc.nee) {
+                    float g[4] = {a[c][0], a[c][1], a[c][2], a[c][3]};
+                    compact_row(fv, c, g);
+                    rot_apply_row(Rle, g);
+                    for (int k = 0; k < 4; ++k)
+                        if (g[k] != 0.0f) atomicAdd(sgrad + base + 12 * vc.nee_light + 4 * c + k, g[k] * vc.nee_w);
+                }
+            }
+        }
+        // parameter scatter
+        if (m.type == DPPT_MAT_SMOOTH_DIELECTRIC || m.type == DPPT_MAT_PLASTIC_GGX) {
+            if (g_eta != 0.0f) atomicAdd(sgrad + m.ior_index, g_eta);
+        }
+        if (m.type == DPPT_MAT_POLARIZER_SHEET || m.type == DPPT_MAT_RETARDER_SHEET) {
+            if (g_slot0 != 0.0f) atomicAdd(sgrad + S->num_ior + m.sheet_index, g_slot0);
+        }
+        if (G->tex) {
+            if ((m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.rough_tex].pad) {
+                Taps tp = tex_taps(S->tex[m.rough_tex], vc.tu, vc.tv);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) atomic_add_agg(G->tex, tp.idx[k], g_slot0 * tp.w[k]);
+            }
+            if (m.albedo_tex >= 0 && (m.type == DPPT_MAT_DIFFUSE || m.type == DPPT_MAT_CONDUCTOR_GGX ||
+                                      m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.albedo_tex].pad) {
+                DTex t = S->tex[m.albedo_tex];
+                Taps tp = tex_taps(t, vc.tu, vc.tv);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) atomic_add_agg(G->tex, tp.idx[k] + min(c, t.ch - 1), g_alb[c] * tp.w[k]);
+            }
+        }
+        // advance the adjoint row through the value of W_i
+        Compact<float> Wv = compact_value(W);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) compact_row(Wv, c, a[c]);
+    }
+};
+
+__device__ __forceinline__ int find_job(const JobTable& T, long long chunk) {
+    int j = 0;
+    while (j + 1 < T.njobs && T.job[j + 1].chunk_begin <= chunk) ++j;
+    return j;
+}
+
+// Adds one path's raw Stokes (already divided by spp) to its pixel.  Called by
+// all 32 lanes of the warp (inactive lanes pass zeros); the job is uniform
+// across the block.  red_mode 0: spp a power of two <= 32, a segment of lanes
+// holds whole pixels -> shuffle sum and one plain store; 1: spp a power-of-two
+// multiple of 32 -> warp sum and one atomic per warp; 2: one atomic per path.
+__device__ __forceinline__ void pixel_reduce(const DJob& J, float* dst, long long p, bool active, float v[12]) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    if (J.red_mode == 0) {
+        for (int off = 1; off < J.spp; off <<= 1)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) v[k] += __shfl_xor_sync(FULL, v[k], off);
+        if (active && (lane % J.spp) == 0) {
+            float4* o = reinterpret_cast<float4*>(dst + (p / J.spp) * 12);
+            o[0] = make_float4(v[0], v[1], v[2], v[3]);
+            o[1] = make_float4(v[4], v[5], v[6], v[7]);
+            o[2] = make_float4(v[8], v[9], v[10], v[11]);
+        }
+    } else if (J.red_mode == 1) {
+        for (int off = 1; off < 32; off <<= 1)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) v[k] += __shfl_xor_sync(FULL, v[k], off);
+        if (active && lane == 0)
+            for (int k = 0; k < 12; ++k) atomicAdd(dst + (p / J.spp) * 12 + k, v[k]);
+    } else if (active) {
+        for (int k = 0; k < 12; ++k) atomicAdd(dst + (p / J.spp) * 12 + k, v[k]);
+    }
+}
+
+// ================================================================== megakernel
+template <int MAXD, int MODE, bool COUNT>
+__global__ void __launch_bounds__(256, MODE == 1 ? DPPT_MIN_BLOCKS_ADJOINT : DPPT_MIN_BLOCKS_PRIMAL)
+k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__ JobTable T,
+        unsigned long long* counter, unsigned* status, int persistent, unsigned long long* work) {
+    extern __shared__ float sgrad[];
+    __shared__ long long s_chunk;
+    const int nscal = MODE == 1 ? S.num_ior + S.num_sheets + 12 * S.num_lights : 0;
+    for (int k = threadIdx.x; k < nscal; k += blockDim.x) sgrad[k] = 0.0f;
+    float cE[MAXD][12];
+    float cW[MAXD][19];
+    WorkCount wc = {0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    unsigned long long paths_done = 0;
+    long long chunk = blockIdx.x;
+    for (;;) {
+        if (persistent) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(counter, 1ULL);
+            __syncthreads();
+            chunk = s_chunk;
+        }
+        if (chunk >= T.total_chunks) break;
+        const DJob& J = T.job[find_job(T, chunk)];
+        const long long p = (chunk - J.chunk_begin) * blockDim.x + threadIdx.x;
+        const bool active = p < J.npaths;
+        float raw[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) raw[k] = 0.0f;
+        if (active) {
+            const long long pix = p / J.spp;
+            PathVis<LocalCache<MAXD>> vis;
+            vis.S = &S; vis.P = &P; vis.G = &G; vis.sgrad = sgrad;
+            vis.C.cE = cE; vis.C.cW = cW;
+            vis.n = 0; vis.i = 0;
+            Walk w;
+            const int passes = MODE == 1 ? 2 : 1;
+            // pass 0 caches E_i and W_i; pass 1 replays the same path through the same call site
+#pragma unroll 1
+            for (int phase = 0; phase < passes; ++phase) {
+                vis.phase = phase;
+                walk_begin(S, J, (unsigned long long)p, pix, w);
+                while (walk_step<PathVis<LocalCache<MAXD>>, COUNT>(S, P, J, (unsigned long long)p, w, vis, status, &wc)) {
+                }
+                if (phase == 0) {
+                    float L0[12];
+                    vis.fold(L0);
+                    Rot<float> Rc = camera_rot(S.cams[J.cam], w.d1);
+                    const float inv = 1.0f / (float)J.spp;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        float v[4] = {L0[4 * c], L0[4 * c + 1], L0[4 * c + 2], L0[4 * c + 3]};
+                        rot_apply(Rc, v);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) raw[4 * c + k] = v[k] * inv;
+                    }
+                    if (MODE == 1) {
+                        if (vis.n == 0) break;
+                        const float* ds = J.dS + pix * 12;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            float av[4] = {__ldg(ds + 4 * c) * inv, __ldg(ds + 4 * c + 1) * inv,
+                                           __ldg(ds + 4 * c + 2) * inv, __ldg(ds + 4 * c + 3) * inv};
+                            rot_apply_row(Rc, av);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) vis.a[c][k] = av[k];
+                        }
+                    }
+                }
+            }
+            if (J.sig) J.sig[p] = fnv(w.sig, (unsigned)w.nv);
+            ++paths_done;
+        }
+        if (J.raw) {
+            __syncwarp();
+            pixel_reduce(J, J.raw, p, active, raw);
+        }
+        if (!persistent) break;
+    }
+    if (COUNT) {
+        atomicAdd(work + 0, paths_done);
+        atomicAdd(work + 1, (unsigned long long)wc.vertices);
+        atomicAdd(work + 2, (unsigned long long)wc.rays);
+        atomicAdd(work + 3, (unsigned long long)wc.shadow_rays);
+        atomicAdd(work + 4, (unsigned long long)wc.nodes);
+        atomicAdd(work + 5, (unsigned long long)wc.shadow_nodes);
+        atomicAdd(work + 6, (unsigned long long)wc.tri_tests);
+        atomicAdd(work + 7, (unsigned long long)wc.sph_tests);
+    }
+    if (MODE == 1) {
+        __syncthreads();
+        float* gdst[3] = {G.ior, G.sheet, G.le};
+        const int nI = S.num_ior, nS = S.num_sheets;
+        for (int k = threadIdx.x; k < nscal; k += blockDim.x) {
+            float v = sgrad[k];
+            if (v == 0.0f) continue;
+            float* base;
+            int off;
+            if (k < nI) { base = gdst[0]; off = k; }
+            else if (k < nI + nS) { base = gdst[1]; off = k - nI; }
+            else { base = gdst[2]; off = k - nI - nS; }
+            if (base) atomicAdd(base + off, v);
+        }
+    }
+}
+
+// one translation unit per cache depth instantiates its kernels and launchers
+#define DPPT_TRACE_BUCKET(B)                                                                                        \
+    cudaError_t launch_trace_##B(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T,  \
+                                 const LaunchCfg& L, unsigned long long* counter, unsigned* status,              \
+                                 unsigned long long* work, cudaStream_t st) {                                    \
+        const int pers = L.schedule == DPPT_SCHED_PERSISTENT;                                                    \
+        long long g = pers ? L.grid : T.total_chunks;                                                            \
+        if (g <= 0) return cudaSuccess;                                                                          \
+        if (g > 0x7fffffffLL) g = 0x7fffffffLL;                                                                  \
+        if (mode == 0)                                                                                           \
+            k_trace<B, 0, false><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, nullptr);         \
+        else if (mode == 1) {                                                                                    \
+            size_t sm = sizeof(float) * (size_t)(S.num_ior + S.num_sheets + 12 * S.num_lights);                 \
+            k_trace<B, 1, false><<<(int)g, L.block, sm, st>>>(S, P, G, T, counter, status, pers, nullptr);        \
+        } else                                                                                                   \
+            k_trace<B, 0, true><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, work);             \
+        return cudaGetLastError();                                                                               \
+    }                                                                                                            \
+    cudaError_t trace_attributes_##B(int mode, cudaFuncAttributes* a) {                                         \
+        return cudaFuncGetAttributes(a, mode == 0 ? reinterpret_cast<const void*>(&k_trace<B, 0, false>)          \
+                                                  : reinterpret_cast<const void*>(&k_trace<B, 1, false>));        \
+    }                                                                                                            \
+    int trace_occupancy_##B(int mode, int block, size_t smem) {                                                  \
+        int nb = 0;                                                                                              \
+        const void* f = mode == 0 ? reinterpret_cast<const void*>(&k_trace<B, 0, false>)                          \
+                                  : reinterpret_cast<const void*>(&k_trace<B, 1, false>);                        \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, smem) != cudaSuccess) return 0;          \
+        return nb;                                                                                               \
+    }
+
+}  // namespace dppt

@@ -1,0 +1,6 @@
+// Kernels of the depth-32 cache bucket (paths of at most 32 vertices).
+#include "trace.cuh"
+
+namespace dppt {
+DPPT_TRACE_BUCKET(32)
+}  // namespace dppt

@@ -1,0 +1,6 @@
+// Kernels of the depth-4 cache bucket (paths of at most 4 vertices).
+#include "trace.cuh"
+
+namespace dppt {
+DPPT_TRACE_BUCKET(4)
+}  // namespace dppt

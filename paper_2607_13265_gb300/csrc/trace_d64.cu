@@ -1,0 +1,6 @@
+// Kernels of the depth-64 cache bucket (paths of at most 64 vertices).
+#include "trace.cuh"
+
+namespace dppt {
+DPPT_TRACE_BUCKET(64)
+}  // namespace dppt

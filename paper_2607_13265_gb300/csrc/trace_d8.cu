@@ -1,0 +1,6 @@
+// Kernels of the depth-8 cache bucket (paths of at most 8 vertices).
+#include "trace.cuh"
+
+namespace dppt {
+DPPT_TRACE_BUCKET(8)
+}  // namespace dppt

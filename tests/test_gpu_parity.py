@@ -40,8 +40,20 @@ def small_scenes():
 SCENES = small_scenes()
 
 
+SCHEDULES = {"grid": (0, 128), "persistent": (1, 256), "wavefront": (2, 128)}
+
+
+@pytest.fixture(params=list(SCHEDULES))
+def sched(request, env):
+    _, dctx, _ = env
+    prev = dctx.get_launch()
+    dctx.set_launch(*SCHEDULES[request.param], 0)
+    yield request.param
+    dctx.set_launch(*prev)
+
+
 @pytest.mark.parametrize("name", list(SCENES))
-def test_primal_matches_oracle(env, name):
+def test_primal_matches_oracle(env, sched, name):
     api, dctx, O = env
     scene, job = SCENES[name]
     gs = api.GpuScene(dctx, scene)
@@ -59,7 +71,7 @@ def test_primal_matches_oracle(env, name):
 
 
 @pytest.mark.parametrize("name", list(SCENES))
-def test_adjoint_matches_oracle(env, name):
+def test_adjoint_matches_oracle(env, sched, name):
     import torch
     api, dctx, O = env
     scene, job = SCENES[name]
@@ -169,8 +181,8 @@ def test_batched_angles_equal_separate_jobs(env):
     assert np.linalg.norm(tex_b - tex_s) <= 1e-4 * np.linalg.norm(tex_s)
 
 
-@pytest.mark.parametrize("sched,block", [(0, 64), (0, 256), (1, 128), (1, 256)])
-def test_schedules_agree(env, sched, block):
+@pytest.mark.parametrize("schedule,block", [(0, 64), (0, 256), (1, 128), (1, 256), (2, 64), (2, 256)])
+def test_schedules_agree(env, schedule, block):
     api, dctx, _ = env
     scene, job = SCENES["mixed"]
     gs = api.GpuScene(dctx, scene)
@@ -178,15 +190,18 @@ def test_schedules_agree(env, sched, block):
     try:
         dctx.set_launch(0, 128, 0)
         (ref,), _, _ = gpu_image(api, dctx, gs, [job])
-        dctx.set_launch(sched, block, 0)
+        dctx.set_launch(schedule, block, 0)
         (got,), _, _ = gpu_image(api, dctx, gs, [job])
     finally:
         dctx.set_launch(*prev)
-    assert np.array_equal(ref, got)
+    if schedule == 2:   # another schedule of the same arithmetic: equal up to summation order
+        assert np.allclose(ref, got, rtol=1e-5, atol=1e-6 * np.abs(ref).max())
+    else:            # same kernel, deterministic per-pixel sums: bitwise equal
+        assert np.array_equal(ref, got)
 
 
 @pytest.mark.parametrize("w,h,spp", [(37, 23, 3), (19, 5, 64), (1, 1, 1), (7, 9, 33)])
-def test_ragged_sizes(env, oracle_mod, w, h, spp):
+def test_ragged_sizes(env, sched, oracle_mod, w, h, spp):
     api, dctx, O = env
     scene, job = sg.mixed_scene(width=8, spp=1, depth=5)
     job.width, job.height, job.spp = w, h, spp
