@@ -227,6 +227,23 @@ dppt_status dppt_adjoint_footprint(const dppt_ctx* ctx, int32_t max_depth, int64
 dppt_status dppt_count_work(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* jobs, int32_t njobs,
                             const dppt_params* params, uint64_t out[8]);
 
+/* No counterpart in the paper: an allocation-free variant of
+ * dppt_render_primal for callers that must not let the library allocate
+ * device memory (device memory owned by another allocator or under a fixed
+ * budget, loops that must not block in cudaMalloc, work issued while a stream
+ * is captured).  Renders ONE job exactly like dppt_render_primal, but a job
+ * with a camera filter keeps its raw (unfiltered) image in a fixed 12 MiB
+ * device array compiled into the library instead of the context workspace;
+ * every GPU that loads the library holds that array until the process exits.
+ * Limit: width * height <= 262144 pixels (e.g. 512 x 512); larger jobs get
+ * DPPT_ERR_INVALID_ARG.  The first call on a device resolves the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls on a device share the array, which keeps the
+ * last call's contents: calls that overlap on the GPU (for instance on two
+ * streams) race on it.  Calls no cudaMalloc or cudaFree. */
+dppt_status dppt_render_primal_noalloc(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* job,
+                                       const dppt_params* params, float* image, void* stream);
+
 /* Synchronise `stream` and return (then clear) the device status word:
  * DPPT_OK, DPPT_ERR_DEVICE (a traversal stack overflow) or DPPT_ERR_TIMEOUT. */
 dppt_status dppt_sync_status(dppt_ctx* ctx, void* stream);

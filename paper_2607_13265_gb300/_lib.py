@@ -76,6 +76,7 @@ SIGNATURES = {
                                 ctypes.POINTER(ctypes.c_uint64)]),
     "dppt_autotune": (c_i32, [c_vp, c_vp, ctypes.POINTER(Job), c_i32, ctypes.POINTER(Params), c_i32,
                               ctypes.POINTER(Launch), ctypes.POINTER(ctypes.c_float)]),
+    "dppt_render_primal_noalloc": (c_i32, [c_vp, c_vp, ctypes.POINTER(Job), ctypes.POINTER(Params), c_vp, c_vp]),
     "dppt_sync_status": (c_i32, [c_vp, c_vp]),
 }
 

@@ -904,3 +904,13 @@ dppt_status dppt_sync_status(dppt_ctx* ctx, void* stream) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ accessors for noalloc.cu
+namespace dppt {
+int ctx_device(const dppt_ctx* c) { return c->device; }
+unsigned* ctx_status_word(const dppt_ctx* c) { return c->d_status; }
+void ctx_set_error(dppt_ctx* c, const char* msg) { c->err = msg; }
+const DScene* scene_view(const dppt_scene* s) { return &s->d; }
+int scene_num_cameras(const dppt_scene* s) { return s->num_cameras; }
+int64_t scene_tex_size(const dppt_scene* s) { return s->tex_size; }
+}  // namespace dppt

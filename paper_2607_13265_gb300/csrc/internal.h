@@ -102,6 +102,15 @@ size_t wavefront_bytes(long long Q, int cap);
 cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T, int job,
                           void* ws, long long Q, int cap, int block, unsigned* status, cudaStream_t st);
 
+// read-only views of the opaque context and scene (host.cpp), for entry points
+// implemented in other translation units
+int ctx_device(const dppt_ctx* c);
+unsigned* ctx_status_word(const dppt_ctx* c);
+void ctx_set_error(dppt_ctx* c, const char* msg);
+const DScene* scene_view(const dppt_scene* s);
+int scene_num_cameras(const dppt_scene* s);
+int64_t scene_tex_size(const dppt_scene* s);
+
 // camera-filter folds: image[a][pix] = C(theta_a) raw[pix]; dS[pix] = sum_a C_a^T dI_a[pix];
 // dtheta_a += sum_pix dI_a[pix]^T dC_a/dtheta S_adj[pix]
 cudaError_t launch_apply_filter(const float* raw, float* image, int npix, int filter, const float* theta,
