@@ -33,17 +33,35 @@ WORKLOAD = "icosphere50k_256x256_64spp_depth8"
 
 # Algorithmic FP32 work per unit (flops), counted from the operations the method
 # performs: a BVH node visit tests two child boxes (12 FMA = 24 flops), a ray/triangle
-# test ~30 flops, a ray/sphere test ~20; per surface vertex the primal shading
-# (rotations 12, Fresnel 60, GGX D*G 40, sampling 40, next-event estimation 150,
-# Mueller fold 96) = 398 flops, the adjoint per vertex = 398 (cache pass) + 40 (replay
-# sampling) + 96 (a^T W) + 524 (dual-number derivatives, ~2x the 262-flop evaluation).
+# test ~30 flops, a ray/sphere test ~20.  Per surface vertex and pass: sampling and the
+# light-sample setup 60 (shade stage); the Mueller evaluation and cache store 358
+# (rotations 12, Fresnel 60, GGX D*G 40, next-event estimation 150, fold 96); the
+# replay 620 (dual-number derivatives of the 262-flop evaluation, ~2x = 524, and the
+# adjoint row update a^T W = 96).  The megakernels do the same work in one kernel.
 F_NODE, F_TRI, F_SPH = 24, 30, 20
-F_VERTEX_PRIMAL = 398
-F_VERTEX_ADJOINT = 398 + 40 + 96 + 524
+F_SHADE, F_CACHE, F_REPLAY = 60, 358, 620
+F_VERTEX_PRIMAL = F_SHADE + F_CACHE
+F_VERTEX_ADJOINT = 2 * F_SHADE + F_CACHE + F_REPLAY
 
-# DRAM traffic per launch of the adjoint kernel from one ncu capture (bytes), or None
+# DRAM traffic per launch of the dominant kernel from one ncu capture (bytes), or None
 # when the kernel has changed since the counters were taken.
-ADJOINT_DRAM_BYTES_PER_LAUNCH = None
+DOMINANT_DRAM_BYTES_PER_LAUNCH = None
+
+
+def stage_flops(w: dict, passes: int) -> dict:
+    """Algorithmic flops of each stage for one launch of the work counted in `w`."""
+    closest = F_NODE * w["nodes"] + F_TRI * w["tri_tests"] + F_SPH * w["sph_tests"]
+    shadow = F_NODE * w["shadow_nodes"] + F_TRI * w["shadow_tri_tests"] + F_SPH * w["shadow_sph_tests"]
+    V = w["vertices"]
+    out = {"wf_extend": passes * closest, "wf_shadow": passes * shadow, "wf_shade": passes * V * F_SHADE,
+           "wf_cache": V * F_CACHE}
+    if passes == 2:
+        out["wf_replay"] = V * F_REPLAY
+        out["adjoint"] = 2 * (closest + shadow) + V * F_VERTEX_ADJOINT
+    else:
+        out["primal"] = closest + shadow + V * F_VERTEX_PRIMAL
+    return out
+
 
 L2_FLUSH_BYTES = 512 << 20
 
@@ -193,11 +211,17 @@ def run_native(args):
 
     dctx = api.Context(local)
     gs = api.GpuScene(dctx, scene)
-    if args.schedule is not None:
-        dctx.set_launch(args.schedule, args.block, 0)
     batch = api.pack_jobs([job])
     adj = api.pack_jobs(api.adjoint_jobs([job]))
     P = api.device_params(scene, batch)
+    tuning = None
+    if args.schedule is not None:
+        adj_s = args.schedule if args.adj_schedule is None else args.adj_schedule
+        adj_b = args.block if args.adj_block is None else args.adj_block
+        dctx.set_launch(args.schedule, args.block, 0, adj_s, adj_b, 0)
+    else:
+        # the library's autotuner picks schedule and block size for each call (untimed)
+        tuning = api.autotune(dctx, gs, adj, P, reps=2)
     tjob.seed = 12345
     target = api.render_primal(dctx, gs, api.pack_jobs([tjob]), api.device_params(scene, batch, tp)).clone()
     N = float(target.numel())
@@ -221,6 +245,7 @@ def run_native(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    dctx.stage_stats(timing=True, reset=True)      # per-stage CUDA events on the launching stream
     with ClockSampler(local) as clk:
         for k in range(K):
             flush.zero_()                               # L2 flush between timed steps (outside the events)
@@ -235,6 +260,7 @@ def run_native(args):
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    stages = dctx.stage_stats(timing=False, reset=True)
     dctx.sync_status()
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     prim_ms = [e[0].elapsed_time(e[1]) for e in ev]
@@ -283,13 +309,19 @@ def run_native(args):
                "d2h_bytes_per_step": int(host_grad.numel() * 4 + 4),
                "api": "PolarizedRender.apply + loss.backward()"}
 
-    # ---- roofline of the dominant kernel (the adjoint megakernel)
+    # ---- roofline of the dominant kernel (largest share of the timed region's GPU time)
     work = api.count_work(dctx, gs, adj, P)
-    trav = F_NODE * (work["nodes"] + work["shadow_nodes"]) + F_TRI * work["tri_tests"] + F_SPH * work["sph_tests"]
-    flops_adj = 2 * trav + F_VERTEX_ADJOINT * work["vertices"]
     pw = api.count_work(dctx, gs, batch, P)
-    flops_prim = F_NODE * (pw["nodes"] + pw["shadow_nodes"]) + F_TRI * pw["tri_tests"] + \
-        F_SPH * pw["sph_tests"] + F_VERTEX_PRIMAL * pw["vertices"]
+    lc = dctx.get_launch()
+    flops = {}
+    for name, v in stage_flops(work, 2).items():
+        flops[name] = flops.get(name, 0) + v * K
+    for name, v in stage_flops(pw, 1).items():
+        if name == "primal" or lc[0] == 2:
+            flops[name] = flops.get(name, 0) + v * K
+    timed = {k: v for k, v in stages.items() if v[0] > 0}
+    dom = max(timed, key=lambda k: timed[k][1])
+    dom_launches, dom_ms = timed[dom]
     adj_avg = sum(adj_ms) / K
     prim_avg = sum(prim_ms) / K
     props = torch.cuda.get_device_properties(dev)
@@ -298,9 +330,12 @@ def run_native(args):
     sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at max clock
     fp32_peak_loaded = props.multi_processor_count * 128 * 2 * (clocks["sm_mhz"] or sm_max) * 1e6 / 1e12
-    achieved = flops_adj / (adj_avg / 1000.0) / 1e12
+    achieved = flops.get(dom, 0) / (dom_ms / 1000.0) / 1e12 if dom_ms > 0 else 0.0
     fp = dctx.adjoint_footprint(job.max_depth)
     cache_bytes = fp["local_bytes_per_thread"] * fp["threads_per_sm"] * fp["sms"]
+    stage_report = {k: {"launches": n, "ms_per_step": ms / K,
+                        "tflops": (flops[k] / (ms / 1000.0) / 1e12) if k in flops and ms > 0 else None}
+                    for k, (n, ms) in timed.items()}
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -310,22 +345,29 @@ def run_native(args):
                    "height": job.height, "spp": job.spp, "max_depth": job.max_depth,
                    "paths_per_step": paths_per_step, "grads": "albedo 128x128x3 + roughness 128x128",
                    "l2": "flushed between timed steps (512 MiB write)",
-                   "schedule": dctx.get_launch(), "parallelism": f"replicas{world}"},
-        "kernels_ms": {"primal": prim_avg, "adjoint": adj_avg},
-        "roofline": {"bound": "alu", "kernel": "k_adjoint", "achieved": achieved, "peak": fp32_peak,
+                   "schedule": {"primal": [api.SCHEDULE_NAMES[lc[0]], lc[1]], "adjoint": [api.SCHEDULE_NAMES[lc[3]], lc[4]],
+                                "chosen_by": "autotuner" if tuning else "command line"},
+                   "parallelism": f"replicas{world}"},
+        "calls_ms": {"render_primal": prim_avg, "render_adjoint": adj_avg},
+        "stages": stage_report,
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "frac_at_loaded_clock": achieved / fp32_peak_loaded,
-                     "traffic": ADJOINT_DRAM_BYTES_PER_LAUNCH,
-                     "flops_per_launch": flops_adj, "work_units": work,
+                     "traffic": DOMINANT_DRAM_BYTES_PER_LAUNCH,
+                     "flops_per_launch": flops.get(dom, 0) / max(dom_launches, 1),
+                     "launch_ms": dom_ms / max(dom_launches, 1),
+                     "work_units_adjoint_pass": work,
                      "peak_note": f"FP32 pipe: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
-                                  f"({peaks['_source']} max clock)",
-                     "primal": {"achieved": flops_prim / (prim_avg / 1000.0) / 1e12, "flops_per_launch": flops_prim}},
-        "memory": {"prb_cache_bytes_per_thread": fp["local_bytes_per_thread"],
-                   "prb_cache_bytes_resident": cache_bytes, "adjoint_registers": fp["registers"],
-                   "threads_per_sm": fp["threads_per_sm"]},
+                                  f"({peaks['_source']} max clock)"},
+        "memory": {"workspace_bytes": dctx.query_workspace(adj),
+                   "prb_cache_bytes": (min(job.num_paths, (1 << 21) // job.spp * job.spp) * job.max_depth * 31 * 4
+                                       if lc[3] == 2 else cache_bytes),
+                   "prb_cache_where": "wavefront workspace" if lc[3] == 2 else "megakernel thread-local memory",
+                   "megakernel_local_bytes_per_thread": fp["local_bytes_per_thread"],
+                   "megakernel_adjoint_registers": fp["registers"]},
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": 2 * K,
+        "gpu_launches": int(sum(n for n, _ in timed.values())),
     }
     if pool is not None:
         result["cpu_baseline"] = oracle_sample(args.cpu_pixels, cpu_procs, {}, pool)
@@ -375,6 +417,8 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--schedule", type=int, default=None, help="0 grid, 1 persistent (default: library default)")
     ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--adj-schedule", type=int, default=None, help="adjoint schedule (default: same as --schedule)")
+    ap.add_argument("--adj-block", type=int, default=None)
     ap.add_argument("--cpu-pixels", type=int, default=4096)
     ap.add_argument("--ref-pixels", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -193,7 +193,9 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* scene, const dp
                                 const dppt_params* params, const float* d_image, const dppt_grads* grads,
                                 void* stream);
 
-/* Device workspace (bytes) the jobs need beyond the caller's buffers. */
+/* Device workspace (bytes) the jobs need beyond the caller's buffers with the
+ * context's current launch shapes: filter buffers, plus the wavefront path
+ * state and per-vertex cache when a wavefront schedule is selected. */
 dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int32_t njobs, size_t* bytes);
 
 /* Schedule for subsequent launches (the autotuner's choice). */
@@ -219,13 +221,13 @@ dppt_status dppt_autotune(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job
 dppt_status dppt_adjoint_footprint(const dppt_ctx* ctx, int32_t max_depth, int64_t out[4]);
 
 /* Work units of the jobs' paths, counted by an instrumented (untimed) instance
- * of the primal megakernel on the same BVH: out[0..7] = paths, surface
+ * of the primal megakernel on the same BVH: out[0..9] = paths, surface
  * vertices, closest-hit rays, shadow rays, BVH nodes visited by closest-hit
- * rays, BVH nodes visited by shadow rays, ray/triangle tests, ray/sphere
- * tests.  Synchronous; writes no image.  Used for the roofline's algorithmic
- * work per launch. */
+ * rays, BVH nodes visited by shadow rays, ray/triangle tests of closest-hit
+ * rays, of shadow rays, ray/sphere tests of closest-hit rays, of shadow rays.
+ * Synchronous; writes no image.  Used for the roofline's algorithmic work. */
 dppt_status dppt_count_work(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* jobs, int32_t njobs,
-                            const dppt_params* params, uint64_t out[8]);
+                            const dppt_params* params, uint64_t out[10]);
 
 /* No counterpart in the paper: an allocation-free variant of
  * dppt_render_primal for callers that must not let the library allocate
@@ -243,6 +245,16 @@ dppt_status dppt_count_work(dppt_ctx* ctx, const dppt_scene* scene, const dppt_j
  * streams) race on it.  Calls no cudaMalloc or cudaFree. */
 dppt_status dppt_render_primal_noalloc(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* job,
                                        const dppt_params* params, float* image, void* stream);
+
+/* Kernel launches per stage since the last reset and, while timing is on,
+ * their summed durations from CUDA events recorded on the launching stream
+ * around each launch.  Stages: 0 primal megakernel, 1 adjoint megakernel,
+ * 2-9 wavefront init, extend (closest hit), shade, shadow (any hit), cache
+ * pass, replay pass, list swap, pixel sums; 10 camera-filter folds.  The call
+ * waits for the recorded events, copies the counters to launches[16] and
+ * ms[16] (either may be NULL), clears them when reset != 0 and then sets
+ * timing on or off for the following launches. */
+dppt_status dppt_stage_stats(dppt_ctx* ctx, int32_t timing, int32_t reset, int64_t launches[16], double ms[16]);
 
 /* Synchronise `stream` and return (then clear) the device status word:
  * DPPT_OK, DPPT_ERR_DEVICE (a traversal stack overflow) or DPPT_ERR_TIMEOUT. */

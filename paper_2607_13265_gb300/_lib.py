@@ -77,6 +77,7 @@ SIGNATURES = {
     "dppt_autotune": (c_i32, [c_vp, c_vp, ctypes.POINTER(Job), c_i32, ctypes.POINTER(Params), c_i32,
                               ctypes.POINTER(Launch), ctypes.POINTER(ctypes.c_float)]),
     "dppt_render_primal_noalloc": (c_i32, [c_vp, c_vp, ctypes.POINTER(Job), ctypes.POINTER(Params), c_vp, c_vp]),
+    "dppt_stage_stats": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_i64), ctypes.POINTER(ctypes.c_double)]),
     "dppt_sync_status": (c_i32, [c_vp, c_vp]),
 }
 

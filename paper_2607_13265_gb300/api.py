@@ -82,6 +82,22 @@ class Context:
         _check(self.h, self.lib.dppt_adjoint_footprint(self.h, max_depth, out), "dppt_adjoint_footprint")
         return {"local_bytes_per_thread": out[0], "registers": out[1], "threads_per_sm": out[2], "sms": out[3]}
 
+    STAGES = ("primal", "adjoint", "wf_init", "wf_extend", "wf_shade", "wf_shadow", "wf_cache", "wf_replay",
+              "wf_swap", "wf_pixels", "filter")
+
+    def stage_stats(self, timing: bool = False, reset: bool = True) -> dict:
+        """{stage: (launches, ms)} since the last reset; then switches event timing on/off."""
+        n = (ctypes.c_int64 * 16)()
+        ms = (ctypes.c_double * 16)()
+        _check(self.h, self.lib.dppt_stage_stats(self.h, int(timing), int(reset), n, ms), "dppt_stage_stats")
+        return {name: (int(n[k]), float(ms[k])) for k, name in enumerate(self.STAGES)}
+
+    def query_workspace(self, batch: "JobBatch") -> int:
+        b = ctypes.c_size_t()
+        _check(self.h, self.lib.dppt_query_workspace(self.h, batch.c_jobs, batch.n, ctypes.byref(b)),
+               "dppt_query_workspace")
+        return int(b.value)
+
     def sync_status(self, stream=None):
         _check(self.h, self.lib.dppt_sync_status(self.h, _stream_ptr(stream)), "dppt_sync_status")
 
@@ -201,12 +217,13 @@ def render_primal(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict, ima
     return image
 
 
-WORK_KEYS = ("paths", "vertices", "rays", "shadow_rays", "nodes", "shadow_nodes", "tri_tests", "sph_tests")
+WORK_KEYS = ("paths", "vertices", "rays", "shadow_rays", "nodes", "shadow_nodes", "tri_tests", "shadow_tri_tests",
+             "sph_tests", "shadow_sph_tests")
 
 
 def count_work(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict) -> dict:
     """Work units of the jobs' paths (instrumented primal on the same BVH; untimed)."""
-    out = (ctypes.c_uint64 * 8)()
+    out = (ctypes.c_uint64 * 10)()
     cp = _c_params(params)
     _check(ctx.h, ctx.lib.dppt_count_work(ctx.h, gs.h, batch.c_jobs, batch.n, ctypes.byref(cp), out),
            "dppt_count_work")

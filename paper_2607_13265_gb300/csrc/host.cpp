@@ -22,6 +22,7 @@ struct dppt_ctx {
     unsigned* d_status = nullptr;
     unsigned long long* d_counter = nullptr;
     dppt_launch launch{DPPT_SCHED_GRID, 128, 0, DPPT_SCHED_GRID, 128, 0};
+    StageLog log;
 };
 
 struct dppt_scene {
@@ -647,7 +648,7 @@ dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_jo
         if (wave) {
             for (int k = 0; k < T.njobs; ++k) {
                 cudaError_t e = run_wavefront(0, s->d, P, G, T, k, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
-                                              shape.block, ctx->d_status, cs);
+                                              shape.block, ctx->d_status, cs, &ctx->log);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront primal");
             }
             continue;
@@ -659,14 +660,18 @@ dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_jo
             cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), cs);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
         }
+        int tok = ctx->log.begin(kStagePrimal, cs);
         cudaError_t e = launch_trace(bucket, 0, s->d, P, G, T, L, ctx->d_counter, ctx->d_status, nullptr, cs);
+        ctx->log.end(tok, cs);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "primal launch");
     }
     for (int i = 0; i < njobs; ++i) {
         if (!plan[i].filtered) continue;
         const float* raw = reinterpret_cast<const float*>(static_cast<char*>(ctx->ws) + plan[i].ws_a);
+        int tok = ctx->log.begin(kStageFilter, cs);
         cudaError_t e = launch_apply_filter(raw, image + jobs[i].out_offset, (int)plan[i].npix, jobs[i].filter,
                                             params->theta + jobs[i].theta_offset, plan[i].nang, cs);
+        ctx->log.end(tok, cs);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "filter launch");
     }
     return DPPT_OK;
@@ -704,9 +709,11 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
             if (plan[i].filtered) {
                 float* dS = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_a);
                 float* Sa = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_b);
+                int tok = ctx->log.begin(kStageFilter, cs);
                 cudaError_t e = launch_filter_adjoint_input(d_image + jobs[i].out_offset, dS, (int)plan[i].npix,
                                                             jobs[i].filter, params->theta + jobs[i].theta_offset,
                                                             plan[i].nang, cs);
+                ctx->log.end(tok, cs);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "filter adjoint launch");
                 J.dS = dS;
                 J.raw = grads->theta ? Sa : nullptr;
@@ -722,7 +729,7 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
         if (wave) {
             for (int k = 0; k < T.njobs; ++k) {
                 cudaError_t e = run_wavefront(1, s->d, P, G, T, k, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
-                                              shape.block, ctx->d_status, cs);
+                                              shape.block, ctx->d_status, cs, &ctx->log);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront adjoint");
             }
             continue;
@@ -734,16 +741,20 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
             cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), cs);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
         }
+        int tok = ctx->log.begin(kStageAdjoint, cs);
         cudaError_t e = launch_trace(bucket, 1, s->d, P, G, T, L, ctx->d_counter, ctx->d_status, nullptr, cs);
+        ctx->log.end(tok, cs);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
     }
     if (grads->theta) {
         for (int i = 0; i < njobs; ++i) {
             if (!plan[i].filtered) continue;
             const float* Sa = reinterpret_cast<const float*>(static_cast<char*>(ctx->ws) + plan[i].ws_b);
+            int tok = ctx->log.begin(kStageFilter, cs);
             cudaError_t e = launch_theta_grad(d_image + jobs[i].out_offset, Sa, (int)plan[i].npix, jobs[i].filter,
                                               params->theta + jobs[i].theta_offset, plan[i].nang,
                                               grads->theta + jobs[i].theta_offset, cs);
+            ctx->log.end(tok, cs);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "theta-gradient launch");
         }
     }
@@ -751,7 +762,7 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
 }
 
 dppt_status dppt_count_work(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
-                            const dppt_params* params, uint64_t out[8]) {
+                            const dppt_params* params, uint64_t out[10]) {
     if (!ctx || !s || !out) return fail(ctx, DPPT_ERR_INVALID_ARG, "null argument");
     cudaSetDevice(ctx->device);
     std::vector<JobPlan> plan;
@@ -759,9 +770,9 @@ dppt_status dppt_count_work(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* 
     dppt_status st = check_jobs(ctx, s, jobs, njobs, params, false, plan, ws);
     if (st != DPPT_OK) return st;
     unsigned long long* d_work = nullptr;
-    cudaError_t e = cudaMalloc(&d_work, 8 * sizeof(unsigned long long));
+    cudaError_t e = cudaMalloc(&d_work, 10 * sizeof(unsigned long long));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "work counters");
-    cudaMemset(d_work, 0, 8 * sizeof(unsigned long long));
+    cudaMemset(d_work, 0, 10 * sizeof(unsigned long long));
     std::vector<int> first, maxd;
     std::vector<JobTable> tables;
     build_tables(jobs, njobs, plan, 128, first, tables, maxd);
@@ -775,11 +786,11 @@ dppt_status dppt_count_work(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* 
         if (e != cudaSuccess) break;
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    unsigned long long h[8] = {0};
+    unsigned long long h[10] = {0};
     if (e == cudaSuccess) e = cudaMemcpy(h, d_work, sizeof h, cudaMemcpyDeviceToHost);
     cudaFree(d_work);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "work count");
-    for (int k = 0; k < 8; ++k) out[k] = h[k];
+    for (int k = 0; k < 10; ++k) out[k] = h[k];
     return DPPT_OK;
 }
 
@@ -789,6 +800,8 @@ dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int3
     for (int i = 0; i < njobs; ++i)
         if (jobs[i].filter != DPPT_FILTER_NONE)
             b = align256(b + 2 * (size_t)jobs[i].width * jobs[i].height * 12 * sizeof(float));
+    if (njobs > 0 && (ctx->launch.schedule == DPPT_SCHED_WAVEFRONT || ctx->launch.adj_schedule == DPPT_SCHED_WAVEFRONT))
+        b += wavefront_bytes(wave_paths(jobs, njobs), max_depth_of(jobs, njobs));
     *bytes = b;
     return DPPT_OK;
 }
@@ -888,6 +901,21 @@ dppt_status dppt_autotune(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jo
     *best = ctx->launch;
     if (result == DPPT_OK) ctx->err.clear();
     return result;
+}
+
+dppt_status dppt_stage_stats(dppt_ctx* ctx, int32_t timing, int32_t reset, int64_t launches[16], double ms[16]) {
+    if (!ctx) return DPPT_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    ctx->log.collect();
+    for (int k = 0; k < 16; ++k) {
+        if (launches) launches[k] = k < kStageCount ? ctx->log.launches[k] : 0;
+        if (ms) ms[k] = k < kStageCount ? ctx->log.ms[k] : 0.0;
+    }
+    if (reset) {
+        for (int k = 0; k < kStageCount; ++k) { ctx->log.launches[k] = 0; ctx->log.ms[k] = 0.0; }
+    }
+    ctx->log.timing = timing != 0;
+    return DPPT_OK;
 }
 
 dppt_status dppt_sync_status(dppt_ctx* ctx, void* stream) {

@@ -1,6 +1,7 @@
 // Structures shared by the host side of the library and its kernels.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "dppt.h"
@@ -81,6 +82,50 @@ struct LaunchCfg {
     int schedule, block, grid;
 };
 
+// Kernel launches per stage, and (when timing is on) CUDA events recorded on
+// the launching stream around every launch.
+enum Stage {
+    kStagePrimal = 0, kStageAdjoint, kStageWfInit, kStageWfExtend, kStageWfShade, kStageWfShadow,
+    kStageWfCache, kStageWfReplay, kStageWfSwap, kStageWfPixels, kStageFilter, kStageCount
+};
+struct StageLog {
+    int64_t launches[kStageCount] = {0};
+    double ms[kStageCount] = {0};
+    bool timing = false;
+    struct Rec { int stage; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> spare;
+    cudaEvent_t take() {
+        if (spare.empty()) { cudaEvent_t e = nullptr; cudaEventCreate(&e); return e; }
+        cudaEvent_t e = spare.back(); spare.pop_back(); return e;
+    }
+    int begin(int stage, cudaStream_t st) {
+        launches[stage]++;
+        if (!timing) return -1;
+        Rec r{stage, take(), take()};
+        cudaEventRecord(r.a, st);
+        recs.push_back(r);
+        return (int)recs.size() - 1;
+    }
+    void end(int tok, cudaStream_t st) {
+        if (tok >= 0) cudaEventRecord(recs[tok].b, st);
+    }
+    void collect() {
+        for (Rec& r : recs) {
+            cudaEventSynchronize(r.b);
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.stage] += t;
+            spare.push_back(r.a);
+            spare.push_back(r.b);
+        }
+        recs.clear();
+    }
+    ~StageLog() {
+        for (Rec& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (cudaEvent_t e : spare) cudaEventDestroy(e);
+    }
+};
+
 // megakernel entry points, one set per cache-depth bucket (trace_d<B>.cu);
 // mode 0 primal, 1 adjoint, 2 instrumented primal (work counts, no image)
 #define DPPT_DECLARE_BUCKET(B)                                                                                   \
@@ -100,7 +145,8 @@ DPPT_DECLARE_BUCKET(64)
 // a cache of `cap` vertices, and the run of one job of a table
 size_t wavefront_bytes(long long Q, int cap);
 cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T, int job,
-                          void* ws, long long Q, int cap, int block, unsigned* status, cudaStream_t st);
+                          void* ws, long long Q, int cap, int block, unsigned* status, cudaStream_t st,
+                          StageLog* log);
 
 // read-only views of the opaque context and scene (host.cpp), for entry points
 // implemented in other translation units

@@ -38,7 +38,7 @@ struct HitRec { float t; int prim, slot; float b1, b2; };
 
 // work units of one path, gathered only by the instrumented primal instance
 struct WorkCount {
-    unsigned vertices, rays, shadow_rays, nodes, shadow_nodes, tri_tests, sph_tests;
+    unsigned vertices, rays, shadow_rays, nodes, shadow_nodes, tri_tests, shadow_tri_tests, sph_tests, shadow_sph_tests;
 };
 
 __device__ __forceinline__ void child_slabs(float4 n0, float4 n1, float4 n2, f3 inv, f3 oi, float tmax,
@@ -146,7 +146,7 @@ __device__ bool trace_closest(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* 
 
 template <bool COUNT>
 __device__ bool trace_any(const DScene& S, f3 o, f3 d, float tmax, unsigned* status, WorkCount* wc) {
-    if (COUNT) { wc->shadow_rays++; wc->sph_tests += S.num_spheres; }
+    if (COUNT) { wc->shadow_rays++; wc->shadow_sph_tests += S.num_spheres; }
     if (S.num_tris > 0) {
         f3 inv = safe_inv(d);
         f3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
@@ -170,7 +170,7 @@ __device__ bool trace_any(const DScene& S, f3 o, f3 d, float tmax, unsigned* sta
             } else {
                 unsigned v = ~(unsigned)ref;
                 int first = (int)(v & 0x1FFFFFFu), cnt = (int)(v >> 25);
-                if (COUNT) wc->tri_tests += cnt;
+                if (COUNT) wc->shadow_tri_tests += cnt;
                 for (int i = first; i < first + cnt; ++i) {
                     float b1, b2;
                     float t = tri_test(S.tris, i, o, d, b1, b2);
@@ -927,7 +927,7 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
     for (int k = threadIdx.x; k < nscal; k += blockDim.x) sgrad[k] = 0.0f;
     float cE[MAXD][12];
     float cW[MAXD][19];
-    WorkCount wc = {0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    WorkCount wc = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     unsigned long long paths_done = 0;
     long long chunk = blockIdx.x;
     for (;;) {
@@ -1002,7 +1002,9 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
         atomicAdd(work + 4, (unsigned long long)wc.nodes);
         atomicAdd(work + 5, (unsigned long long)wc.shadow_nodes);
         atomicAdd(work + 6, (unsigned long long)wc.tri_tests);
-        atomicAdd(work + 7, (unsigned long long)wc.sph_tests);
+        atomicAdd(work + 7, (unsigned long long)wc.shadow_tri_tests);
+        atomicAdd(work + 8, (unsigned long long)wc.sph_tests);
+        atomicAdd(work + 9, (unsigned long long)wc.shadow_sph_tests);
     }
     if (MODE == 1) {
         __syncthreads();

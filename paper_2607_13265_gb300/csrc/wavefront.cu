@@ -232,7 +232,8 @@ size_t wavefront_bytes(long long Q, int cap) {
 // Renders (mode 0) or differentiates (mode 1) job `job` of the table in waves of
 // at most Q paths (whole pixels), writing the per-pixel raw image to J.raw.
 cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T, int job,
-                          void* ws, long long Q, int cap, int block, unsigned* status, cudaStream_t st) {
+                          void* ws, long long Q, int cap, int block, unsigned* status, cudaStream_t st,
+                          StageLog* log) {
     const DJob& J = T.job[job];
     char* p = static_cast<char*>(ws);
     WfPath* paths = reinterpret_cast<WfPath*>(p); p += align_up(sizeof(WfPath) * Q);
@@ -254,26 +255,41 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
         WfLists A{lists[0], lists[1], lists[2], lists[3], lists[4], count};
         cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 8, st);
         if (e != cudaSuccess) return e;
+        int tok = log->begin(kStageWfInit, st);
         k_wf_init<<<grid, block, 0, st>>>(S, T, job, pix0 * J.spp, nq, paths, A);
+        log->end(tok, st);
         for (int it = 0; it < passes * J.depth; ++it) {
             // lists alternate between two buffer pairs: the next lists of one iteration are the
             // live lists of the following one (k_wf_swap moves the counts)
             WfLists L = (it & 1) ? WfLists{lists[2], lists[3], lists[0], lists[1], lists[4], count} : A;
             unsigned* sg = J.sig ? J.sig + pix0 * J.spp : nullptr;
+            tok = log->begin(kStageWfExtend, st);
             k_wf_extend<<<grid, block, 0, st>>>(S, paths, vtx, hits, L, status);
+            log->end(tok, st);
+            tok = log->begin(kStageWfShade, st);
             k_wf_shade<<<grid, block, 0, st>>>(S, P, T, paths, vtx, hits, L);
+            log->end(tok, st);
+            tok = log->begin(kStageWfShadow, st);
             k_wf_shadow<<<grid, block, 0, st>>>(S, vtx, L, status);
-            if (mode == 0) {
-                k_wf_finish<0><<<grid, block, 0, st>>>(S, P, G, T, paths, vtx, cache, Q, cap, L, 0, rawp, sg);
-            } else {
-                k_wf_finish<1><<<grid, block, 0, st>>>(S, P, G, T, paths, vtx, cache, Q, cap, L, 0, rawp, sg);
+            log->end(tok, st);
+            tok = log->begin(kStageWfCache, st);
+            if (mode == 0) k_wf_finish<0><<<grid, block, 0, st>>>(S, P, G, T, paths, vtx, cache, Q, cap, L, 0, rawp, sg);
+            else k_wf_finish<1><<<grid, block, 0, st>>>(S, P, G, T, paths, vtx, cache, Q, cap, L, 0, rawp, sg);
+            log->end(tok, st);
+            if (mode == 1) {
+                tok = log->begin(kStageWfReplay, st);
                 k_wf_finish<1><<<grid, block, smem, st>>>(S, P, G, T, paths, vtx, cache, Q, cap, L, 1, rawp, sg);
+                log->end(tok, st);
             }
+            tok = log->begin(kStageWfSwap, st);
             k_wf_swap<<<1, 32, 0, st>>>(L);
+            log->end(tok, st);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         if (J.raw) {
+            tok = log->begin(kStageWfPixels, st);
             k_wf_pixels<<<(int)((wp + 127) / 128), 128, 0, st>>>(rawp, J.spp, wp, J.raw + pix0 * 12);
+            log->end(tok, st);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }
