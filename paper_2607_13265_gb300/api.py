@@ -300,6 +300,26 @@ class PolarizedRender(torch.autograd.Function):
         return (None, None, None, None, grads["tex"], grads["ior"], grads["le"], grads["sheet"], grads["theta"])
 
 
+class ImageL2(torch.autograd.Function):
+    """mean((I - T)^2) without image-sized temporaries in the forward; the backward
+    returns dg/dI = 2 (I - T) / N, the adjoint image render_adjoint consumes."""
+
+    @staticmethod
+    def forward(fctx, img, target):
+        fctx.save_for_backward(img, target)
+        acc = torch.zeros((), dtype=torch.float64, device=img.device)
+        step = 1 << 24
+        for c in range(0, img.numel(), step):
+            d = img[c:c + step] - target[c:c + step]
+            acc += (d * d).sum(dtype=torch.float64)
+        return (acc / img.numel()).to(img.dtype)
+
+    @staticmethod
+    def backward(fctx, g):
+        img, target = fctx.saved_tensors
+        return torch.sub(img, target).mul_(2.0 / img.numel()).mul_(g), None
+
+
 def adjoint_jobs(jobs, pass_id: int = 1):
     """Copies of the jobs with another pass id (decorrelated paths for the adjoint)."""
     import copy

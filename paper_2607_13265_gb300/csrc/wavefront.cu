@@ -1,30 +1,108 @@
 // Wavefront schedule of the same path tracer: the megakernel's per-vertex work
 // split into stage kernels over compacted lists of live paths,
-//   extend  (closest hit)  ->  shade (surface data, light and BSDF samples)
-//   -> shadow (any hit of the light samples) -> finish (per-vertex action,
-//   next ray), the finish stage launched once per pass so that cache passes
-//   and dual-number replays run in separate, coherent kernels.
-// Path state, hits and the per-vertex cache of E_i / W_i live in the context
-// workspace ([vertex][component][path] for the cache, so that a warp's loads
-// are contiguous).  The replay re-traces the path with the same stage code
-// and Philox counters as the cache pass.  Every stage reads its list length
-// from device memory, so a wave is a fixed sequence of launches.
+//   extend (closest hit) -> shade (surface data, light and BSDF samples)
+//   -> shadow (any hit of the light samples) -> cache / replay (per-vertex
+//   action, next ray),
+// the last stage as two kernels so that cache passes and dual-number replays
+// run separately.  Path state lives in the context workspace as arrays of
+// 16-byte-aligned records that a thread moves with float4 loads and stores:
+// the walk (64 B), path bookkeeping (16 B), the vertex handed from shade to
+// finish (96 B), the hit (16 B), the adjoint row (48 B), the raw Stokes
+// value (48 B); the per-vertex cache of E_i / W_i is laid out
+// [vertex][component][path] so that a warp's accesses are contiguous.  The
+// replay re-traces the path with the same stage code and Philox counters as
+// the cache pass.  Every stage reads its list length from device memory and
+// loops over it with a grid stride, so a wave is a fixed sequence of launches.
 #include "trace.cuh"
+
+// resident 128-thread blocks per SM the finish kernels' register allocation must allow
+// (4 -> at most 128 registers per thread, 3 -> at most 168)
+#ifndef DPPT_WF_CACHE_MIN_BLOCKS
+#define DPPT_WF_CACHE_MIN_BLOCKS 4
+#endif
+#ifndef DPPT_WF_REPLAY_MIN_BLOCKS
+#define DPPT_WF_REPLAY_MIN_BLOCKS 3
+#endif
 
 namespace dppt {
 
-struct __align__(16) WfPath {
-    Walk w;
-    unsigned long long pid;
-    float a[3][4];
-    float raw[12];
-    int job, phase, n, i;
+struct __align__(16) WfWalk { float4 a, b, c, d; };   // (o, prev_pdf) (d, sig) (xprev, v|nv|delta) (d1, -)
+struct __align__(16) WfMeta { unsigned lo, hi; int job, pni; };  // pid, job, phase | n << 8 | i << 16
+struct __align__(16) WfVtx { float4 x_tu, ng_tv, wi_pdf, wl_d2, misc; int4 ids; };
+struct __align__(16) WfRay { float4 o_tmax, dir; };
+
+enum : unsigned {
+    kFEmit = 1u, kFOutside = 2u, kFOk = 4u, kFTerminal = 8u, kFDelta = 16u, kFHit = 32u,
+    kEvShift = 6, kNeeShift = 8
 };
-struct __align__(16) WfVertex {
-    VCtx vc;
-    NeePending ne;
-    Shade sh;
-    int hit, visible;
+constexpr int kMissCode = (int)0x80000000;
+
+__device__ __forceinline__ void put_walk(WfWalk* p, const Walk& w) {
+    WfWalk r;
+    r.a = make_float4(w.o.x, w.o.y, w.o.z, w.prev_pdf);
+    r.b = make_float4(w.d.x, w.d.y, w.d.z, __uint_as_float(w.sig));
+    r.c = make_float4(w.xprev.x, w.xprev.y, w.xprev.z,
+                      __int_as_float(w.v | (w.nv << 8) | ((w.prev_delta ? 1 : 0) << 16)));
+    r.d = make_float4(w.d1.x, w.d1.y, w.d1.z, 0.0f);
+    *p = r;
+}
+__device__ __forceinline__ void get_walk(const WfWalk* p, Walk& w) {
+    WfWalk r = *p;
+    w.o = {r.a.x, r.a.y, r.a.z}; w.prev_pdf = r.a.w;
+    w.d = {r.b.x, r.b.y, r.b.z}; w.sig = __float_as_uint(r.b.w);
+    w.xprev = {r.c.x, r.c.y, r.c.z};
+    int bits = __float_as_int(r.c.w);
+    w.v = bits & 0xff; w.nv = (bits >> 8) & 0xff; w.prev_delta = (bits >> 16) & 1;
+    w.d1 = {r.d.x, r.d.y, r.d.z};
+}
+
+__device__ __forceinline__ void put_vertex(WfVtx* p, const VCtx& vc, const NeePending& ne, const Shade& sh) {
+    WfVtx r;
+    r.x_tu = make_float4(vc.x.x, vc.x.y, vc.x.z, vc.tu);
+    r.ng_tv = make_float4(vc.ng.x, vc.ng.y, vc.ng.z, vc.tv);
+    r.wi_pdf = make_float4(sh.wi.x, sh.wi.y, sh.wi.z, sh.pdf);
+    r.wl_d2 = make_float4(ne.wl.x, ne.wl.y, ne.wl.z, ne.dist2);
+    r.misc = make_float4(ne.cl, ne.cx, vc.w_emit, vc.p_event);
+    unsigned f = kFHit | (vc.emit ? kFEmit : 0u) | (vc.outside ? kFOutside : 0u) | (sh.ok ? kFOk : 0u) |
+                 (sh.terminal ? kFTerminal : 0u) | (sh.delta ? kFDelta : 0u) | (sh.ev << kEvShift) |
+                 ((unsigned)ne.state << kNeeShift);
+    r.ids = make_int4(vc.prim, (vc.mat & 0xffff) | (ne.l << 16), vc.light, (int)f);
+    *p = r;
+}
+__device__ __forceinline__ bool get_vertex(const WfVtx* p, const Walk& w, VCtx& vc, NeePending& ne, Shade& sh) {
+    WfVtx r = *p;
+    unsigned f = (unsigned)r.ids.w;
+    if (!(f & kFHit)) return false;
+    vc.x = {r.x_tu.x, r.x_tu.y, r.x_tu.z}; vc.tu = r.x_tu.w;
+    vc.ng = {r.ng_tv.x, r.ng_tv.y, r.ng_tv.z}; vc.tv = r.ng_tv.w;
+    vc.wo = -w.d;
+    vc.n = dot(vc.ng, vc.wo) >= 0.0f ? vc.ng : -vc.ng;
+    vc.prim = r.ids.x; vc.mat = r.ids.y & 0xffff; vc.light = r.ids.z;
+    vc.emit = f & kFEmit; vc.outside = f & kFOutside;
+    vc.w_emit = r.misc.z; vc.p_event = r.misc.w;
+    vc.event = 0; vc.pdf = 1.0f; vc.nee = false; vc.scatter = false; vc.nee_light = -1; vc.nee_w = 0.0f;
+    vc.wl = f3{0.f, 0.f, 0.f}; vc.wi = vc.wl;
+    sh.wi = {r.wi_pdf.x, r.wi_pdf.y, r.wi_pdf.z}; sh.pdf = r.wi_pdf.w;
+    sh.ok = f & kFOk; sh.terminal = f & kFTerminal; sh.delta = f & kFDelta; sh.ev = (f >> kEvShift) & 3u;
+    ne.state = (int)((f >> kNeeShift) & 3u);
+    ne.l = r.ids.y >> 16;
+    ne.wl = {r.wl_d2.x, r.wl_d2.y, r.wl_d2.z}; ne.dist2 = r.wl_d2.w;
+    ne.cl = r.misc.x; ne.cx = r.misc.y;
+    return true;
+}
+
+struct WfState {
+    WfWalk* walk;
+    WfMeta* meta;
+    WfVtx* vtx;
+    float4* hit;        // (t, b1, b2, BVH slot | -(sphere + 1) | miss code)
+    WfRay* ray;         // shadow rays
+    int* visible;
+    float4* arow;       // adjoint rows, 3 per path
+    float4* raw;        // raw Stokes per path, 3 per path
+    float* cache;
+    long long Q;
+    int cap;
 };
 
 struct WfLists {
@@ -36,116 +114,174 @@ struct WfLists {
     int* count;   // [0] n0, [1] n1, [2] next0, [3] next1, [4] shadow
 };
 
-__device__ __forceinline__ int list_at(const WfLists& L, int idx) {
-    int n0 = L.count[0];
+__device__ __forceinline__ int list_at(const WfLists& L, int n0, int idx) {
     return idx < n0 ? L.l0[idx] : L.l1[idx - n0];
 }
 
 __global__ void k_wf_init(const DScene S, const __grid_constant__ JobTable T, int job, long long p0, int nq,
-                          WfPath* paths, WfLists L) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nq) return;
-    const DJob& J = T.job[job];
-    WfPath& st = paths[q];
-    st.pid = (unsigned long long)(p0 + q);
-    st.job = job;
-    st.phase = 0;
-    st.n = 0;
-    st.i = 0;
-    walk_begin(S, J, st.pid, (long long)(st.pid / J.spp), st.w);
-    L.l0[q] = q;
-    if (q == 0) { L.count[0] = nq; L.count[1] = 0; }
+                          WfState W, WfLists L) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
+        const DJob& J = T.job[job];
+        const unsigned long long pid = (unsigned long long)(p0 + q);
+        Walk w;
+        walk_begin(S, J, pid, (long long)(pid / J.spp), w);
+        put_walk(W.walk + q, w);
+        W.meta[q] = WfMeta{(unsigned)pid, (unsigned)(pid >> 32), job, 0};
+        L.l0[q] = q;
+        if (q == 0) { L.count[0] = nq; L.count[1] = 0; }
+    }
 }
 
-__global__ void k_wf_extend(const DScene S, WfPath* paths, WfVertex* vtx, HitRec* hits, WfLists L, unsigned* status) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= L.count[0] + L.count[1]) return;
-    int q = list_at(L, idx);
-    const Walk& w = paths[q].w;
-    HitRec h;
-    vtx[q].hit = trace_closest<false>(S, w.o, w.d, h, status, nullptr) ? 1 : 0;
-    hits[q] = h;
+__global__ void k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
+    const int n0 = L.count[0], n = n0 + L.count[1];
+    const int stride = gridDim.x * blockDim.x;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
+        const int q = list_at(L, n0, idx);
+        const float4 a = W.walk[q].a, b = W.walk[q].b;
+        HitRec h;
+        float4 out;
+        if (trace_closest<false>(S, f3{a.x, a.y, a.z}, f3{b.x, b.y, b.z}, h, status, nullptr)) {
+            int code = h.prim < S.num_tris ? h.slot : -(h.prim - S.num_tris + 1);
+            out = make_float4(h.t, h.b1, h.b2, __int_as_float(code));
+        } else {
+            out = make_float4(0.f, 0.f, 0.f, __int_as_float(kMissCode));
+        }
+        W.hit[q] = out;
+    }
 }
 
-__global__ void k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfPath* paths,
-                           WfVertex* vtx, const HitRec* hits, WfLists L) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= L.count[0] + L.count[1]) return;
-    int q = list_at(L, idx);
-    WfVertex& V = vtx[q];
-    if (!V.hit) return;
-    const WfPath& st = paths[q];
-    walk_shade(S, P, T.job[st.job], st.pid, st.w, hits[q], V.vc, V.ne, V.sh);
-    V.visible = 0;
-    if (V.ne.state == 1) L.shadow[atomicAdd(L.count + 4, 1)] = q;
+__global__ void k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfState W, WfLists L) {
+    const int n0 = L.count[0], n = n0 + L.count[1];
+    const int stride = gridDim.x * blockDim.x;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
+        const int q = list_at(L, n0, idx);
+        const float4 hv = W.hit[q];
+        const int code = __float_as_int(hv.w);
+        if (code == kMissCode) {
+            W.vtx[q].ids = make_int4(0, 0, 0, 0);
+            continue;
+        }
+        HitRec h;
+        h.t = hv.x; h.b1 = hv.y; h.b2 = hv.z;
+        if (code >= 0) { h.slot = code; h.prim = __float_as_int(__ldg(&S.tris[3 * code].w)); }
+        else { h.slot = -1; h.prim = S.num_tris + (-code - 1); }
+        Walk w;
+        get_walk(W.walk + q, w);
+        const WfMeta m = W.meta[q];
+        const unsigned long long pid = (unsigned long long)m.lo | ((unsigned long long)m.hi << 32);
+        VCtx vc;
+        NeePending ne;
+        Shade sh;
+        walk_shade(S, P, T.job[m.job], pid, w, h, vc, ne, sh);
+        put_vertex(W.vtx + q, vc, ne, sh);
+        if (ne.state == 1) {
+            W.ray[q] = WfRay{make_float4(ne.o2.x, ne.o2.y, ne.o2.z, ne.tmax), make_float4(ne.dir.x, ne.dir.y, ne.dir.z, 0.f)};
+            L.shadow[atomicAdd(L.count + 4, 1)] = q;
+        }
+        W.visible[q] = 0;
+    }
 }
 
-__global__ void k_wf_shadow(const DScene S, WfVertex* vtx, WfLists L, unsigned* status) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= L.count[4]) return;
-    int q = L.shadow[idx];
-    const NeePending& ne = vtx[q].ne;
-    vtx[q].visible = trace_any<false>(S, ne.o2, ne.dir, ne.tmax, status, nullptr) ? 0 : 1;
+__global__ void k_wf_shadow(const DScene S, WfState W, WfLists L, unsigned* status) {
+    const int n = L.count[4];
+    const int stride = gridDim.x * blockDim.x;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
+        const int q = L.shadow[idx];
+        const WfRay r = W.ray[q];
+        W.visible[q] = trace_any<false>(S, f3{r.o_tmax.x, r.o_tmax.y, r.o_tmax.z}, f3{r.dir.x, r.dir.y, r.dir.z},
+                                        r.o_tmax.w, status, nullptr) ? 0 : 1;
+    }
 }
 
-// Finish stage for the paths of one pass (phase 0: cache pass, phase 1: replay).
-template <int MODE>
-__global__ void k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_constant__ JobTable T,
-                            WfPath* paths, WfVertex* vtx, float* cache, long long Q, int cap, WfLists L, int phase,
-                            float* rawp, unsigned* sig) {
+__device__ __forceinline__ void flush_scalars(const DScene& S, const DGrads& G, float* sgrad, int nscal) {
+    __syncthreads();
+    float* gdst[3] = {G.ior, G.sheet, G.le};
+    const int nI = S.num_ior, nS = S.num_sheets;
+    for (int k = threadIdx.x; k < nscal; k += blockDim.x) {
+        float v = sgrad[k];
+        if (v == 0.0f) continue;
+        float* base;
+        int off;
+        if (k < nI) { base = gdst[0]; off = k; }
+        else if (k < nI + nS) { base = gdst[1]; off = k - nI; }
+        else { base = gdst[2]; off = k - nI - nS; }
+        if (base) atomicAdd(base + off, v);
+    }
+}
+
+// Per-vertex action of one pass.  PHASE 0 (cache pass): cache E_i / W_i; at the
+// end of the walk fold the cache, store the path's raw Stokes value and, for the
+// adjoint (MODE 1), start the replay.  PHASE 1: the replay (MODE 1 only).
+template <int MODE, int PHASE>
+__global__ void __launch_bounds__(128, PHASE == 1 ? DPPT_WF_REPLAY_MIN_BLOCKS : DPPT_WF_CACHE_MIN_BLOCKS)
+k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_constant__ JobTable T, WfState W, WfLists L,
+            unsigned* sig) {
     extern __shared__ float sgrad[];
-    const int nscal = (MODE == 1 && phase == 1) ? S.num_ior + S.num_sheets + 12 * S.num_lights : 0;
-    for (int k = threadIdx.x; k < nscal; k += blockDim.x) sgrad[k] = 0.0f;
-    if (nscal) __syncthreads();
-    const int count = phase == 0 ? L.count[0] : L.count[1];
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < count) {
-        const int q = phase == 0 ? L.l0[idx] : L.l1[idx];
-        WfPath& st = paths[q];
-        const DJob& J = T.job[st.job];
+    const int nscal = PHASE == 1 ? S.num_ior + S.num_sheets + 12 * S.num_lights : 0;
+    if (PHASE == 1) {
+        for (int k = threadIdx.x; k < nscal; k += blockDim.x) sgrad[k] = 0.0f;
+        __syncthreads();
+    }
+    const int count = PHASE == 0 ? L.count[0] : L.count[1];
+    const int stride = gridDim.x * blockDim.x;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += stride) {
+        const int q = PHASE == 0 ? L.l0[idx] : L.l1[idx];
+        const WfMeta m = W.meta[q];
+        const DJob& J = T.job[m.job];
+        Walk w;
+        get_walk(W.walk + q, w);
         PathVis<GlobalCache> vis;
         vis.S = &S; vis.P = &P; vis.G = &G; vis.sgrad = sgrad;
-        vis.C.base = cache; vis.C.Q = Q; vis.C.q = q; vis.C.cap = cap;
-        vis.n = st.n; vis.i = st.i; vis.phase = st.phase;
-        if (phase == 1) {
+        vis.C.base = W.cache; vis.C.Q = W.Q; vis.C.q = q; vis.C.cap = W.cap;
+        vis.n = (m.pni >> 8) & 0xff; vis.i = (m.pni >> 16) & 0xff; vis.phase = PHASE;
+        if (PHASE == 1) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) vis.a[c][k] = st.a[c][k];
+            for (int c = 0; c < 3; ++c) {
+                float4 r = W.arow[3 * (long long)q + c];
+                vis.a[c][0] = r.x; vis.a[c][1] = r.y; vis.a[c][2] = r.z; vis.a[c][3] = r.w;
+            }
         }
-        WfVertex& V = vtx[q];
+        VCtx vc;
+        NeePending ne;
+        Shade sh;
         bool cont = false;
-        if (V.hit) cont = walk_finish(S, P, st.w, V.vc, V.ne, V.visible != 0, V.sh, vis);
+        if (get_vertex(W.vtx + q, w, vc, ne, sh)) cont = walk_finish(S, P, w, vc, ne, W.visible[q] != 0, sh, vis);
         bool done = false;
+        int phase = PHASE;
         if (cont) {
-            if (phase == 0) L.next0[atomicAdd(L.count + 2, 1)] = q;
+            if (PHASE == 0) L.next0[atomicAdd(L.count + 2, 1)] = q;
             else L.next1[atomicAdd(L.count + 3, 1)] = q;
-        } else if (phase == 0) {
+        } else if (PHASE == 0) {
             float L0[12];
             vis.fold(L0);
-            Rot<float> Rc = camera_rot(S.cams[J.cam], st.w.d1);
+            Rot<float> Rc = camera_rot(S.cams[J.cam], w.d1);
             const float inv = 1.0f / (float)J.spp;
+            float rv[12];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 float v[4] = {L0[4 * c], L0[4 * c + 1], L0[4 * c + 2], L0[4 * c + 3]};
                 rot_apply(Rc, v);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) st.raw[4 * c + k] = v[k] * inv;
+                for (int k = 0; k < 4; ++k) rv[4 * c + k] = v[k] * inv;
             }
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                W.raw[3 * (long long)q + c] = make_float4(rv[4 * c], rv[4 * c + 1], rv[4 * c + 2], rv[4 * c + 3]);
             if (MODE == 1 && vis.n > 0) {
-                const long long pix = (long long)(st.pid / J.spp);
+                const unsigned long long pid = (unsigned long long)m.lo | ((unsigned long long)m.hi << 32);
+                const long long pix = (long long)(pid / J.spp);
                 const float* ds = J.dS + pix * 12;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     float av[4] = {__ldg(ds + 4 * c) * inv, __ldg(ds + 4 * c + 1) * inv,
                                    __ldg(ds + 4 * c + 2) * inv, __ldg(ds + 4 * c + 3) * inv};
                     rot_apply_row(Rc, av);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) vis.a[c][k] = av[k];
+                    W.arow[3 * (long long)q + c] = make_float4(av[0], av[1], av[2], av[3]);
                 }
-                vis.phase = 1;
+                phase = 1;
                 vis.i = 0;
-                walk_begin(S, J, st.pid, pix, st.w);
+                walk_begin(S, J, pid, pix, w);
                 L.next1[atomicAdd(L.count + 3, 1)] = q;
             } else {
                 done = true;
@@ -153,39 +289,19 @@ __global__ void k_wf_finish(const DScene S, const DParams P, const DGrads G, con
         } else {
             done = true;
         }
-        st.n = vis.n; st.i = vis.i; st.phase = vis.phase;
-        if (MODE == 1 && vis.phase == 1) {
+        if (PHASE == 1 && !done) {
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) st.a[c][k] = vis.a[c][k];
+                W.arow[3 * (long long)q + c] = make_float4(vis.a[c][0], vis.a[c][1], vis.a[c][2], vis.a[c][3]);
         }
-        if (done) {
-            float4* o = reinterpret_cast<float4*>(rawp + (long long)q * 12);
-            o[0] = make_float4(st.raw[0], st.raw[1], st.raw[2], st.raw[3]);
-            o[1] = make_float4(st.raw[4], st.raw[5], st.raw[6], st.raw[7]);
-            o[2] = make_float4(st.raw[8], st.raw[9], st.raw[10], st.raw[11]);
-            if (sig) sig[q] = fnv(st.w.sig, (unsigned)st.w.nv);
-        }
+        W.meta[q].pni = phase | (vis.n << 8) | (vis.i << 16);
+        put_walk(W.walk + q, w);
+        if (done && sig) sig[q] = fnv(w.sig, (unsigned)w.nv);
     }
-    if (nscal) {
-        __syncthreads();
-        float* gdst[3] = {G.ior, G.sheet, G.le};
-        const int nI = S.num_ior, nS = S.num_sheets;
-        for (int k = threadIdx.x; k < nscal; k += blockDim.x) {
-            float v = sgrad[k];
-            if (v == 0.0f) continue;
-            float* base;
-            int off;
-            if (k < nI) { base = gdst[0]; off = k; }
-            else if (k < nI + nS) { base = gdst[1]; off = k - nI; }
-            else { base = gdst[2]; off = k - nI - nS; }
-            if (base) atomicAdd(base + off, v);
-        }
-    }
+    if (PHASE == 1) flush_scalars(S, G, sgrad, nscal);
 }
 
-// next lists become the live lists; the paths' raw values of a finished wave are summed per pixel
+// the next lists become the live lists
 __global__ void k_wf_swap(WfLists L) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         L.count[0] = L.count[2];
@@ -196,34 +312,35 @@ __global__ void k_wf_swap(WfLists L) {
     }
 }
 
-__global__ void k_wf_pixels(const float* rawp, int spp, long long npix, float* dst) {
+// sums the spp paths of each pixel of a finished wave (deterministic order)
+__global__ void k_wf_pixels(const float4* raw, int spp, long long npix, float* dst) {
     long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (pix >= npix) return;
-    float acc[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = 0.0f;
+    float4 acc[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
     for (int s = 0; s < spp; ++s) {
-        const float4* r = reinterpret_cast<const float4*>(rawp + (pix * spp + s) * 12);
-        for (int qd = 0; qd < 3; ++qd) {
-            float4 t = r[qd];
-            acc[4 * qd] += t.x; acc[4 * qd + 1] += t.y; acc[4 * qd + 2] += t.z; acc[4 * qd + 3] += t.w;
+        const float4* r = raw + 3 * (pix * spp + s);
+        for (int c = 0; c < 3; ++c) {
+            float4 t = r[c];
+            acc[c].x += t.x; acc[c].y += t.y; acc[c].z += t.z; acc[c].w += t.w;
         }
     }
     float4* o = reinterpret_cast<float4*>(dst + pix * 12);
-    o[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    o[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-    o[2] = make_float4(acc[8], acc[9], acc[10], acc[11]);
+    o[0] = acc[0]; o[1] = acc[1]; o[2] = acc[2];
 }
 
 static size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t wavefront_bytes(long long Q, int cap) {
     size_t b = 0;
-    b += align_up(sizeof(WfPath) * Q);
-    b += align_up(sizeof(WfVertex) * Q);
-    b += align_up(sizeof(HitRec) * Q);
-    b += align_up(sizeof(float) * 12 * Q);            // raw per path
-    b += 5 * align_up(sizeof(int) * Q);               // lists
+    b += align_up(sizeof(WfWalk) * Q);
+    b += align_up(sizeof(WfMeta) * Q);
+    b += align_up(sizeof(WfVtx) * Q);
+    b += align_up(sizeof(float4) * Q);          // hits
+    b += align_up(sizeof(WfRay) * Q);
+    b += align_up(sizeof(int) * Q);             // visible
+    b += align_up(sizeof(float4) * 3 * Q);      // adjoint rows
+    b += align_up(sizeof(float4) * 3 * Q);      // raw per path
+    b += 5 * align_up(sizeof(int) * Q);         // lists
     b += align_up(sizeof(int) * 8);
     b += align_up(sizeof(float) * 31 * (size_t)cap * Q);
     return b;
@@ -236,14 +353,24 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                           StageLog* log) {
     const DJob& J = T.job[job];
     char* p = static_cast<char*>(ws);
-    WfPath* paths = reinterpret_cast<WfPath*>(p); p += align_up(sizeof(WfPath) * Q);
-    WfVertex* vtx = reinterpret_cast<WfVertex*>(p); p += align_up(sizeof(WfVertex) * Q);
-    HitRec* hits = reinterpret_cast<HitRec*>(p); p += align_up(sizeof(HitRec) * Q);
-    float* rawp = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * 12 * Q);
+    WfState W;
+    W.walk = reinterpret_cast<WfWalk*>(p); p += align_up(sizeof(WfWalk) * Q);
+    W.meta = reinterpret_cast<WfMeta*>(p); p += align_up(sizeof(WfMeta) * Q);
+    W.vtx = reinterpret_cast<WfVtx*>(p); p += align_up(sizeof(WfVtx) * Q);
+    W.hit = reinterpret_cast<float4*>(p); p += align_up(sizeof(float4) * Q);
+    W.ray = reinterpret_cast<WfRay*>(p); p += align_up(sizeof(WfRay) * Q);
+    W.visible = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * Q);
+    W.arow = reinterpret_cast<float4*>(p); p += align_up(sizeof(float4) * 3 * Q);
+    W.raw = reinterpret_cast<float4*>(p); p += align_up(sizeof(float4) * 3 * Q);
     int* lists[5];
     for (int k = 0; k < 5; ++k) { lists[k] = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * Q); }
     int* count = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * 8);
-    float* cache = reinterpret_cast<float*>(p);
+    W.cache = reinterpret_cast<float*>(p);
+    W.Q = Q;
+    W.cap = cap;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long npix = (long long)J.W * J.H;
     const long long pix_per_wave = std::max(1LL, Q / J.spp);
     const int passes = mode == 1 ? 2 : 1;
@@ -251,34 +378,36 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
     for (long long pix0 = 0; pix0 < npix; pix0 += pix_per_wave) {
         const long long wp = std::min(pix_per_wave, npix - pix0);
         const int nq = (int)(wp * J.spp);
-        const int grid = (nq + block - 1) / block;
+        // stage kernels stride over their lists: a few resident waves of blocks at most
+        const int grid = (int)std::min<long long>((nq + block - 1) / block, (long long)sms * (2048 / block));
+        const int fgrid = (int)std::min<long long>((nq + 127) / 128, (long long)sms * DPPT_WF_CACHE_MIN_BLOCKS * 2);
         WfLists A{lists[0], lists[1], lists[2], lists[3], lists[4], count};
         cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 8, st);
         if (e != cudaSuccess) return e;
         int tok = log->begin(kStageWfInit, st);
-        k_wf_init<<<grid, block, 0, st>>>(S, T, job, pix0 * J.spp, nq, paths, A);
+        k_wf_init<<<grid, block, 0, st>>>(S, T, job, pix0 * J.spp, nq, W, A);
         log->end(tok, st);
+        unsigned* sg = J.sig ? J.sig + pix0 * J.spp : nullptr;
         for (int it = 0; it < passes * J.depth; ++it) {
             // lists alternate between two buffer pairs: the next lists of one iteration are the
             // live lists of the following one (k_wf_swap moves the counts)
             WfLists L = (it & 1) ? WfLists{lists[2], lists[3], lists[0], lists[1], lists[4], count} : A;
-            unsigned* sg = J.sig ? J.sig + pix0 * J.spp : nullptr;
             tok = log->begin(kStageWfExtend, st);
-            k_wf_extend<<<grid, block, 0, st>>>(S, paths, vtx, hits, L, status);
+            k_wf_extend<<<grid, block, 0, st>>>(S, W, L, status);
             log->end(tok, st);
             tok = log->begin(kStageWfShade, st);
-            k_wf_shade<<<grid, block, 0, st>>>(S, P, T, paths, vtx, hits, L);
+            k_wf_shade<<<grid, block, 0, st>>>(S, P, T, W, L);
             log->end(tok, st);
             tok = log->begin(kStageWfShadow, st);
-            k_wf_shadow<<<grid, block, 0, st>>>(S, vtx, L, status);
+            k_wf_shadow<<<grid, block, 0, st>>>(S, W, L, status);
             log->end(tok, st);
             tok = log->begin(kStageWfCache, st);
-            if (mode == 0) k_wf_finish<0><<<grid, block, 0, st>>>(S, P, G, T, paths, vtx, cache, Q, cap, L, 0, rawp, sg);
-            else k_wf_finish<1><<<grid, block, 0, st>>>(S, P, G, T, paths, vtx, cache, Q, cap, L, 0, rawp, sg);
+            if (mode == 0) k_wf_finish<0, 0><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+            else k_wf_finish<1, 0><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
             log->end(tok, st);
             if (mode == 1) {
                 tok = log->begin(kStageWfReplay, st);
-                k_wf_finish<1><<<grid, block, smem, st>>>(S, P, G, T, paths, vtx, cache, Q, cap, L, 1, rawp, sg);
+                k_wf_finish<1, 1><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
                 log->end(tok, st);
             }
             tok = log->begin(kStageWfSwap, st);
@@ -288,7 +417,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
         }
         if (J.raw) {
             tok = log->begin(kStageWfPixels, st);
-            k_wf_pixels<<<(int)((wp + 127) / 128), 128, 0, st>>>(rawp, J.spp, wp, J.raw + pix0 * 12);
+            k_wf_pixels<<<(int)((wp + 127) / 128), 128, 0, st>>>(W.raw, J.spp, wp, J.raw + pix0 * 12);
             log->end(tok, st);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }

@@ -335,6 +335,10 @@ class Perlin:
 
 def displaced_sphere(freq: int, amplitude: float, seed: int, radius: float = 1.0,
                      center=(0, 0, 0), base_freq: float = 2.0):
+    """Displaced geodesic sphere with spherical UVs.  Every triangle gets its own three
+    vertices so that a triangle crossing the u = 0/1 seam can carry u values on one side
+    of it (u + 1 for the small ones; textures wrap), instead of interpolating across the
+    whole texture."""
     v, f = geodesic_sphere(freq)
     d = Perlin(seed).fbm(v, octaves=3, base_freq=base_freq)
     v = v * (radius * (1.0 + amplitude * d))[:, None] + np.asarray(center, np.float64)
@@ -342,7 +346,13 @@ def displaced_sphere(freq: int, amplitude: float, seed: int, radius: float = 1.0
     n /= np.linalg.norm(n, axis=1, keepdims=True)
     uv = np.stack([np.arctan2(n[:, 2], n[:, 0]) / (2 * np.pi) + 0.5,
                    np.arccos(np.clip(n[:, 1], -1, 1)) / np.pi], 1)
-    return v, f, uv
+    tv = v[f].reshape(-1, 3)
+    tuv = uv[f].copy()                       # [F, 3, 2]
+    u = tuv[:, :, 0]
+    seam = (u.max(1) - u.min(1)) > 0.5
+    u[seam] = np.where(u[seam] < 0.5, u[seam] + 1.0, u[seam])
+    tf = np.arange(3 * len(f), dtype=np.int64).reshape(-1, 3)
+    return tv, tf, tuv.reshape(-1, 2)
 
 
 # ============================================================ workloads
