@@ -588,7 +588,7 @@ static void build_tables(const dppt_job* jobs, int njobs, const std::vector<JobP
     }
 }
 
-constexpr long long kWaveCap = 1LL << 21;   // paths per wave of the wavefront schedule
+constexpr long long kWaveCap = 1LL << 22;   // paths per wave of the wavefront schedule
 
 static long long wave_paths(const dppt_job* jobs, int njobs) {
     long long q = 0;

@@ -92,6 +92,14 @@ __device__ __forceinline__ float sphere_test(float4 s, f3 o, f3 d, float tmax) {
 
 __device__ __forceinline__ f3 safe_inv(f3 d) { return {1.0f / d.x, 1.0f / d.y, 1.0f / d.z}; }
 
+// BVH traversal in the while-while form with postponed leaves (Aila & Laine,
+// "Understanding the efficiency of ray traversal on GPUs", HPG 2009): a lane
+// descends inner nodes until it has found a leaf, keeps descending while other
+// lanes of its warp have not, and the warp then tests leaves together.
+constexpr int kTravDone = 0x7fffffff;   // stack sentinel: traversal finished
+
+__device__ __forceinline__ int trav_pop(const int* stack, int& sp) { return sp > 0 ? stack[--sp] : kTravDone; }
+
 // closest hit; ties in t go to the lower primitive id (triangles before spheres)
 template <bool COUNT>
 __device__ bool trace_closest(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* status, WorkCount* wc) {
@@ -102,8 +110,10 @@ __device__ bool trace_closest(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* 
         f3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
         int stack[kBvhStack];
         int sp = 0, ref = 0;
-        for (;;) {
-            if (ref >= 0) {
+        while (ref != kTravDone) {
+            int leaf = kTravDone;
+            // inner nodes until this lane (and, while it waits, its warp) has a leaf
+            while (ref >= 0 && ref != kTravDone) {
                 const float4* nd = S.nodes + 4 * ref;
                 float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
                 float tl, tr; bool hl, hr;
@@ -113,14 +123,18 @@ __device__ bool trace_closest(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* 
                 if (hl && hr) {
                     int nr = cl, fr = cr;
                     if (tr < tl) { nr = cr; fr = cl; }
-                    if (sp >= kBvhStack) { atomicOr(status, kStatusStackOverflow); break; }
+                    if (sp >= kBvhStack) { atomicOr(status, kStatusStackOverflow); ref = kTravDone; break; }
                     stack[sp++] = fr;
                     ref = nr;
                 } else if (hl) ref = cl;
                 else if (hr) ref = cr;
-                else { if (sp == 0) break; ref = stack[--sp]; }
-            } else {
-                unsigned v = ~(unsigned)ref;
+                else ref = trav_pop(stack, sp);
+                if (ref < 0 && leaf == kTravDone) { leaf = ref; ref = trav_pop(stack, sp); }
+                if (!__any_sync(__activemask(), leaf == kTravDone)) break;
+            }
+            // leaves, including further leaves met on the stack
+            while (leaf != kTravDone) {
+                unsigned v = ~(unsigned)leaf;
                 int first = (int)(v & 0x1FFFFFFu), cnt = (int)(v >> 25);
                 if (COUNT) wc->tri_tests += cnt;
                 for (int i = first; i < first + cnt; ++i) {
@@ -131,8 +145,8 @@ __device__ bool trace_closest(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* 
                         if (t < h.t || id < h.prim) { h.t = t; h.prim = id; h.slot = i; h.b1 = b1; h.b2 = b2; }
                     }
                 }
-                if (sp == 0) break;
-                ref = stack[--sp];
+                leaf = kTravDone;
+                if (ref < 0) { leaf = ref; ref = trav_pop(stack, sp); }
             }
         }
     }
@@ -144,16 +158,22 @@ __device__ bool trace_closest(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* 
     return h.prim >= 0;
 }
 
+// any hit in (0, tmax)
 template <bool COUNT>
 __device__ bool trace_any(const DScene& S, f3 o, f3 d, float tmax, unsigned* status, WorkCount* wc) {
     if (COUNT) { wc->shadow_rays++; wc->shadow_sph_tests += S.num_spheres; }
+    for (int k = 0; k < S.num_spheres; ++k) {
+        float t = sphere_test(__ldg(S.spheres + k), o, d, tmax);
+        if (t > 0.0f && t < tmax) return true;
+    }
     if (S.num_tris > 0) {
         f3 inv = safe_inv(d);
         f3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
         int stack[kBvhStack];
         int sp = 0, ref = 0;
-        for (;;) {
-            if (ref >= 0) {
+        while (ref != kTravDone) {
+            int leaf = kTravDone;
+            while (ref >= 0 && ref != kTravDone) {
                 const float4* nd = S.nodes + 4 * ref;
                 float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
                 float tl, tr; bool hl, hr;
@@ -166,9 +186,12 @@ __device__ bool trace_any(const DScene& S, f3 o, f3 d, float tmax, unsigned* sta
                     ref = cl;
                 } else if (hl) ref = cl;
                 else if (hr) ref = cr;
-                else { if (sp == 0) break; ref = stack[--sp]; }
-            } else {
-                unsigned v = ~(unsigned)ref;
+                else ref = trav_pop(stack, sp);
+                if (ref < 0 && leaf == kTravDone) { leaf = ref; ref = trav_pop(stack, sp); }
+                if (!__any_sync(__activemask(), leaf == kTravDone)) break;
+            }
+            while (leaf != kTravDone) {
+                unsigned v = ~(unsigned)leaf;
                 int first = (int)(v & 0x1FFFFFFu), cnt = (int)(v >> 25);
                 if (COUNT) wc->shadow_tri_tests += cnt;
                 for (int i = first; i < first + cnt; ++i) {
@@ -176,21 +199,24 @@ __device__ bool trace_any(const DScene& S, f3 o, f3 d, float tmax, unsigned* sta
                     float t = tri_test(S.tris, i, o, d, b1, b2);
                     if (t > 0.0f && t < tmax) return true;
                 }
-                if (sp == 0) break;
-                ref = stack[--sp];
+                leaf = kTravDone;
+                if (ref < 0) { leaf = ref; ref = trav_pop(stack, sp); }
             }
         }
-    }
-    for (int k = 0; k < S.num_spheres; ++k) {
-        float t = sphere_test(__ldg(S.spheres + k), o, d, tmax);
-        if (t > 0.0f && t < tmax) return true;
     }
     return false;
 }
 
 // ================================================================== textures
 struct Taps { long long idx[4]; float w[4]; };
-__device__ __forceinline__ int wrapi(int a, int n) { int m = a % n; return m < 0 ? m + n : m; }
+// a mod n in [0, n); texel coordinates are nearly always within one period of the range
+__device__ __forceinline__ int wrapi(int a, int n) {
+    if ((unsigned)a < (unsigned)n) return a;
+    if (a < 0 && a >= -n) return a + n;
+    if (a >= n && a < 2 * n) return a - n;
+    int m = a % n;
+    return m < 0 ? m + n : m;
+}
 __device__ __forceinline__ Taps tex_taps(const DTex& t, float u, float v) {
     float x = u * (float)t.w - 0.5f, y = v * (float)t.h - 0.5f;
     float fx0 = floorf(x), fy0 = floorf(y);
@@ -220,6 +246,7 @@ __device__ __forceinline__ float tex_lookup(const DScene& S, const float* data, 
 struct VCtx {
     f3 x, ng, n, wo, wl, wi;
     float tu, tv, w_emit, nee_w, pdf, p_event;
+    float alpha, alb[3], pspec;   // material values at the vertex, looked up once
     int prim, mat, light, nee_light, event;
     bool emit, nee, scatter, outside;
 };
@@ -230,31 +257,35 @@ __device__ __forceinline__ float ggx_pdf(float alpha, f3 n, f3 wo, f3 wi) {
     if (ch <= 0.0f || oh <= 0.0f) return 0.0f;
     return ggx_D<float>(ch, alpha) * ch / (4.0f * oh);
 }
-__device__ __forceinline__ float mean_albedo(const DScene& S, const DParams& P, const DMat& m, float u, float v) {
-    if (m.albedo_tex < 0) return 1.0f;
-    DTex t = S.tex[m.albedo_tex];
-    Taps tp = tex_taps(t, u, v);
-    float a = 0.0f;
-    for (int c = 0; c < 3; ++c) a += tex_value(P.tex, tp, min(c, t.ch - 1));
-    return a / 3.0f;
-}
-__device__ __forceinline__ float plastic_pspec(const DScene& S, const DParams& P, const DMat& m, const VCtx& vc) {
-    float eta = __ldg(P.ior + m.ior_index);
-    float fs = fresnel_unpolarized(dot(vc.wo, vc.n), 1.0f, eta);
-    float fd = mean_albedo(S, P, m, vc.tu, vc.tv);
-    float tot = fs + fd;
-    return tot > 0.0f ? fs / tot : 0.5f;
+// Roughness, albedo (tint) and the rough dielectric's specular-lobe probability at the
+// vertex: looked up once and reused by sampling, pdfs and the Mueller evaluation.
+__device__ __forceinline__ void material_values(const DScene& S, const DParams& P, const DMat& m, VCtx& vc) {
+    if (m.albedo_tex >= 0) {
+        DTex t = S.tex[m.albedo_tex];
+        Taps tp = tex_taps(t, vc.tu, vc.tv);
+        for (int c = 0; c < 3; ++c) vc.alb[c] = tex_value(P.tex, tp, min(c, t.ch - 1));
+    } else {
+        vc.alb[0] = vc.alb[1] = vc.alb[2] = 1.0f;
+    }
+    vc.alpha = 0.0f;
+    vc.pspec = 0.0f;
+    if (m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX)
+        vc.alpha = tex_lookup(S, P.tex, m.rough_tex, 0, vc.tu, vc.tv);
+    if (m.type == DPPT_MAT_PLASTIC_GGX) {
+        float eta = __ldg(P.ior + m.ior_index);
+        float fs = fresnel_unpolarized(dot(vc.wo, vc.n), 1.0f, eta);
+        float fd = (vc.alb[0] + vc.alb[1] + vc.alb[2]) / 3.0f;
+        float tot = fs + fd;
+        vc.pspec = tot > 0.0f ? fs / tot : 0.5f;
+    }
 }
 __device__ __forceinline__ float bsdf_pdf(const DScene& S, const DParams& P, const DMat& m, const VCtx& vc, f3 wi) {
     float ci = dot(wi, vc.n);
     if (ci <= 0.0f) return 0.0f;
     if (m.type == DPPT_MAT_DIFFUSE) return ci * kInvPi;
-    float al = tex_lookup(S, P.tex, m.rough_tex, 0, vc.tu, vc.tv);
-    if (m.type == DPPT_MAT_CONDUCTOR_GGX) return ggx_pdf(al, vc.n, vc.wo, wi);
-    if (m.type == DPPT_MAT_PLASTIC_GGX) {
-        float ps = plastic_pspec(S, P, m, vc);
-        return ps * ggx_pdf(al, vc.n, vc.wo, wi) + (1.0f - ps) * ci * kInvPi;
-    }
+    if (m.type == DPPT_MAT_CONDUCTOR_GGX) return ggx_pdf(vc.alpha, vc.n, vc.wo, wi);
+    if (m.type == DPPT_MAT_PLASTIC_GGX)
+        return vc.pspec * ggx_pdf(vc.alpha, vc.n, vc.wo, wi) + (1.0f - vc.pspec) * ci * kInvPi;
     return 0.0f;
 }
 
@@ -328,9 +359,7 @@ __device__ void bsdf_compact(const DScene& S, const DParams& P, const DMat& m, c
     if (ci <= 0.0f || co <= 0.0f) return;
     T alb[3];
     if (m.albedo_tex >= 0) {
-        DTex t = S.tex[m.albedo_tex];
-        Taps tp = tex_taps(t, vc.tu, vc.tv);
-        for (int c = 0; c < 3; ++c) alb[c] = seeded<T>(tex_value(P.tex, tp, min(c, t.ch - 1)), 2);
+        for (int c = 0; c < 3; ++c) alb[c] = seeded<T>(vc.alb[c], 2);
     } else {
         for (int c = 0; c < 3; ++c) alb[c] = T(1.0f);
     }
@@ -340,7 +369,7 @@ __device__ void bsdf_compact(const DScene& S, const DParams& P, const DMat& m, c
     }
     f3 h = normalize(vc.wo + wi);
     float ch = dot(h, vc.n), oh = dot(vc.wo, h), ih = dot(wi, h);
-    T al = seeded<T>(tex_lookup(S, P.tex, m.rough_tex, 0, vc.tu, vc.tv), 0);
+    T al = seeded<T>(vc.alpha, 0);
     T k = ggx_D<T>(ch, al) * ggx_G1<T>(co, oh, al) * ggx_G1<T>(ci, ih, al) / (4.0f * co * ci);
     ABCS<T> F;
     if (m.type == DPPT_MAT_CONDUCTOR_GGX) {
@@ -497,7 +526,7 @@ __device__ __forceinline__ void walk_begin(const DScene& S, const DJob& J, unsig
 // action, next ray).  walk_step chains them for the megakernel.
 struct NeePending {
     f3 o2, dir, wl;
-    float tmax, dist2, cl, cx;
+    float tmax, pl, cx;   // pl: solid-angle pdf of the light sample
     int l;
     int state;   // 2: no light sample at this vertex, 0: sample facing away, 1: shadow ray pending
 };
@@ -560,6 +589,7 @@ __device__ __forceinline__ void walk_shade(const DScene& S, const DParams& P, co
     sh.delta = m.type == DPPT_MAT_SMOOTH_DIELECTRIC || m.type == DPPT_MAT_POLARIZER_SHEET ||
                m.type == DPPT_MAT_RETARDER_SHEET;
     if (sh.terminal) return;
+    material_values(S, P, m, vc);
     U8 U = draw8(J.k0, J.k1, pid, (unsigned)w.v);
     if (!sh.delta && nL > 0) {
         int l = min((int)(U.u[4] * (float)nL), nL - 1);
@@ -578,8 +608,7 @@ __device__ __forceinline__ void walk_shade(const DScene& S, const DParams& P, co
             ne.dir = dd * (1.0f / dl);
             ne.tmax = dl * (1.0f - 1e-4f);
             ne.wl = wl;
-            ne.dist2 = dist2;
-            ne.cl = cl;
+            ne.pl = dist2 / (cl * L.area * (float)nL);
             ne.cx = cx;
             ne.l = l;
             ne.state = 1;
@@ -589,14 +618,14 @@ __device__ __forceinline__ void walk_shade(const DScene& S, const DParams& P, co
     f3 wi = {0.f, 0.f, 0.f};
     if (m.type == DPPT_MAT_DIFFUSE || m.type == DPPT_MAT_PLASTIC_GGX || m.type == DPPT_MAT_CONDUCTOR_GGX) {
         bool spec = m.type == DPPT_MAT_CONDUCTOR_GGX;
-        if (m.type == DPPT_MAT_PLASTIC_GGX) { spec = U.u[0] < plastic_pspec(S, P, m, vc); sh.ev = spec ? 1u : 2u; }
+        if (m.type == DPPT_MAT_PLASTIC_GGX) { spec = U.u[0] < vc.pspec; sh.ev = spec ? 1u : 2u; }
         f3 t1 = onb_t1(vc.n), t2 = onb_t2(vc.n);
         if (!spec) {
             float r = sqrtf(U.u[1]), sph, cph;
             sincosf(2.0f * kPi * U.u[2], &sph, &cph);
             wi = t1 * (r * cph) + t2 * (r * sph) + vc.n * sqrtf(fmaxf(0.0f, 1.0f - U.u[1]));
         } else {
-            float al = tex_lookup(S, P.tex, m.rough_tex, 0, vc.tu, vc.tv);
+            const float al = vc.alpha;
             float tan2 = al * al * U.u[1] / (1.0f - U.u[1]);
             float ch = 1.0f / sqrtf(1.0f + tan2);
             float shv = sqrtf(fmaxf(0.0f, 1.0f - ch * ch));
@@ -648,8 +677,7 @@ __device__ __forceinline__ bool walk_finish(const DScene& S, const DParams& P, W
             neeflag = 0u;
             if (ne.state == 1 && visible) {
                 const DMat m = S.mats[vc.mat];
-                DLight L = load_light(S, ne.l);
-                float pl = ne.dist2 / (ne.cl * L.area * (float)S.num_lights);
+                float pl = ne.pl;
                 float pb = bsdf_pdf(S, P, m, vc, ne.wl);
                 float wm = pl * pl / (pl * pl + pb * pb);
                 vc.nee = true; vc.nee_light = ne.l; vc.wl = ne.wl;

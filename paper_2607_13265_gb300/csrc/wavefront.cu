@@ -7,7 +7,7 @@
 // run separately.  Path state lives in the context workspace as arrays of
 // 16-byte-aligned records that a thread moves with float4 loads and stores:
 // the walk (64 B), path bookkeeping (16 B), the vertex handed from shade to
-// finish (96 B), the hit (16 B), the adjoint row (48 B), the raw Stokes
+// finish (112 B), the hit (16 B), the adjoint row (48 B), the raw Stokes
 // value (48 B); the per-vertex cache of E_i / W_i is laid out
 // [vertex][component][path] so that a warp's accesses are contiguous.  The
 // replay re-traces the path with the same stage code and Philox counters as
@@ -28,7 +28,7 @@ namespace dppt {
 
 struct __align__(16) WfWalk { float4 a, b, c, d; };   // (o, prev_pdf) (d, sig) (xprev, v|nv|delta) (d1, -)
 struct __align__(16) WfMeta { unsigned lo, hi; int job, pni; };  // pid, job, phase | n << 8 | i << 16
-struct __align__(16) WfVtx { float4 x_tu, ng_tv, wi_pdf, wl_d2, misc; int4 ids; };
+struct __align__(16) WfVtx { float4 x_tu, ng_tv, wi_pdf, wl_ps, misc, mat; int4 ids; };
 struct __align__(16) WfRay { float4 o_tmax, dir; };
 
 enum : unsigned {
@@ -61,8 +61,9 @@ __device__ __forceinline__ void put_vertex(WfVtx* p, const VCtx& vc, const NeePe
     r.x_tu = make_float4(vc.x.x, vc.x.y, vc.x.z, vc.tu);
     r.ng_tv = make_float4(vc.ng.x, vc.ng.y, vc.ng.z, vc.tv);
     r.wi_pdf = make_float4(sh.wi.x, sh.wi.y, sh.wi.z, sh.pdf);
-    r.wl_d2 = make_float4(ne.wl.x, ne.wl.y, ne.wl.z, ne.dist2);
-    r.misc = make_float4(ne.cl, ne.cx, vc.w_emit, vc.p_event);
+    r.wl_ps = make_float4(ne.wl.x, ne.wl.y, ne.wl.z, vc.pspec);
+    r.misc = make_float4(ne.pl, ne.cx, vc.w_emit, vc.p_event);
+    r.mat = make_float4(vc.alpha, vc.alb[0], vc.alb[1], vc.alb[2]);
     unsigned f = kFHit | (vc.emit ? kFEmit : 0u) | (vc.outside ? kFOutside : 0u) | (sh.ok ? kFOk : 0u) |
                  (sh.terminal ? kFTerminal : 0u) | (sh.delta ? kFDelta : 0u) | (sh.ev << kEvShift) |
                  ((unsigned)ne.state << kNeeShift);
@@ -86,8 +87,9 @@ __device__ __forceinline__ bool get_vertex(const WfVtx* p, const Walk& w, VCtx& 
     sh.ok = f & kFOk; sh.terminal = f & kFTerminal; sh.delta = f & kFDelta; sh.ev = (f >> kEvShift) & 3u;
     ne.state = (int)((f >> kNeeShift) & 3u);
     ne.l = r.ids.y >> 16;
-    ne.wl = {r.wl_d2.x, r.wl_d2.y, r.wl_d2.z}; ne.dist2 = r.wl_d2.w;
-    ne.cl = r.misc.x; ne.cx = r.misc.y;
+    ne.wl = {r.wl_ps.x, r.wl_ps.y, r.wl_ps.z}; vc.pspec = r.wl_ps.w;
+    ne.pl = r.misc.x; ne.cx = r.misc.y;
+    vc.alpha = r.mat.x; vc.alb[0] = r.mat.y; vc.alb[1] = r.mat.z; vc.alb[2] = r.mat.w;
     return true;
 }
 
