@@ -756,8 +756,11 @@ struct GlobalCache {
     __device__ __forceinline__ float& w(int v, int k) const { return base[((long long)v * 31 + 12 + k) * Q + q]; }
 };
 
-// Pass 0 caches E_v (overwritten later by the suffix L[v]) and the compact W_v;
-// pass 1 (adjoint only) replays the vertex with dual numbers.
+// Pass 0 caches E_v and the compact W_v of every vertex after which the path goes on
+// (the last vertex has L[n] = E_n, so its W is never needed and its E stays in
+// registers); the backward fold overwrites E_v with the suffix L[v] where the replay
+// will read it (the adjoint's vertices 1..n-1).  Pass 1 (adjoint only) replays the
+// vertex with dual numbers.
 template <class Cache>
 struct PathVis {
     const DScene* S;
@@ -766,7 +769,9 @@ struct PathVis {
     float* sgrad;       // shared scalar-gradient accumulators [ior | sheet | le]
     Cache C;
     float a[3][4];      // adjoint row a^T = dI^T C R_cam W_1 ... W_{v-1}
+    float lastE[12];    // emission at the path's last vertex
     int n, i, phase;
+    bool has_last, adjoint;
 
     __device__ __forceinline__ void operator()(const VCtx& vc) {
         if (phase == 0) {
@@ -774,6 +779,15 @@ struct PathVis {
             float E[3][4];
             Compact<float> W;
             eval_vertex<float>(*S, *P, vc, E, W, nullptr);
+            if (!vc.scatter) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) lastE[4 * c + k] = E[c][k];
+                has_last = true;
+                ++n;
+                return;
+            }
 #pragma unroll
             for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -796,8 +810,15 @@ struct PathVis {
     __device__ __forceinline__ void fold(float L0[12]) {
         float L[12];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) L[k] = 0.0f;
-        for (int v = n - 1; v >= 0; --v) {
+        for (int k = 0; k < 12; ++k) L[k] = has_last ? lastE[k] : 0.0f;
+        int v = n - 1;
+        if (has_last) {
+            if (adjoint && v >= 1)
+#pragma unroll
+                for (int k = 0; k < 12; ++k) C.e(v, k) = L[k];
+            --v;
+        }
+        for (; v >= 0; --v) {
             Compact<float> W;
             W.ri = {C.w(v, 0), C.w(v, 1)}; W.ro = {C.w(v, 2), C.w(v, 3)};
 #pragma unroll
@@ -812,8 +833,9 @@ struct PathVis {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) L[4 * c + k] = C.e(v, 4 * c + k) + y[k];
             }
+            if (adjoint && v >= 1)
 #pragma unroll
-            for (int k = 0; k < 12; ++k) C.e(v, k) = L[k];
+                for (int k = 0; k < 12; ++k) C.e(v, k) = L[k];
         }
 #pragma unroll
         for (int k = 0; k < 12; ++k) L0[k] = L[k];
@@ -977,7 +999,7 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
             PathVis<LocalCache<MAXD>> vis;
             vis.S = &S; vis.P = &P; vis.G = &G; vis.sgrad = sgrad;
             vis.C.cE = cE; vis.C.cW = cW;
-            vis.n = 0; vis.i = 0;
+            vis.n = 0; vis.i = 0; vis.has_last = false; vis.adjoint = MODE == 1;
             Walk w;
             const int passes = MODE == 1 ? 2 : 1;
             // pass 0 caches E_i and W_i; pass 1 replays the same path through the same call site

@@ -237,6 +237,8 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
         vis.S = &S; vis.P = &P; vis.G = &G; vis.sgrad = sgrad;
         vis.C.base = W.cache; vis.C.Q = W.Q; vis.C.q = q; vis.C.cap = W.cap;
         vis.n = (m.pni >> 8) & 0xff; vis.i = (m.pni >> 16) & 0xff; vis.phase = PHASE;
+        vis.has_last = false;          // set, and consumed by the fold, within this launch
+        vis.adjoint = MODE == 1;
         if (PHASE == 1) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -296,9 +298,12 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
             for (int c = 0; c < 3; ++c)
                 W.arow[3 * (long long)q + c] = make_float4(vis.a[c][0], vis.a[c][1], vis.a[c][2], vis.a[c][3]);
         }
-        W.meta[q].pni = phase | (vis.n << 8) | (vis.i << 16);
-        put_walk(W.walk + q, w);
-        if (done && sig) sig[q] = fnv(w.sig, (unsigned)w.nv);
+        if (done) {
+            if (sig) sig[q] = fnv(w.sig, (unsigned)w.nv);
+        } else {
+            W.meta[q].pni = phase | (vis.n << 8) | (vis.i << 16);
+            put_walk(W.walk + q, w);
+        }
     }
     if (PHASE == 1) flush_scalars(S, G, sgrad, nscal);
 }
