@@ -70,6 +70,23 @@ def _env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value over all ranks (the slowest rank's time); x itself when world == 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(paths_per_step: int, world: int, steps: int, max_total_ms: float) -> float:
+    """Whole-job paths/s: every rank traced paths_per_step paths per step; the job took
+    as long as its slowest rank."""
+    return paths_per_step * world * steps / (max_total_ms / 1000.0)
+
+
 def load_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -265,13 +282,9 @@ def run_native(args):
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     prim_ms = [e[0].elapsed_time(e[1]) for e in ev]
     adj_ms = [e[2].elapsed_time(e[3]) for e in ev]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     paths_per_step = 2 * job.num_paths
-    value = paths_per_step * world * K / (total_ms / 1000.0)
+    value = weak_scaling_value(paths_per_step, world, K, total_ms)
 
     # ---- end to end through the public autograd API with host buffers
     e2e = None
@@ -419,7 +432,7 @@ def main():
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--adj-schedule", type=int, default=None, help="adjoint schedule (default: same as --schedule)")
     ap.add_argument("--adj-block", type=int, default=None)
-    ap.add_argument("--cpu-pixels", type=int, default=4096)
+    ap.add_argument("--cpu-pixels", type=int, default=16384)
     ap.add_argument("--ref-pixels", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--width", type=int, default=None, help="smaller image (profiling captures only)")
