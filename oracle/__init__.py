@@ -12,6 +12,8 @@ Functions follow the paper as stated in ``oracle.cpp``'s header:
     sampling, either by conventional taped AD (``mode='tape'``, the "Conv. AD"
     reference of Sec. 5.1) or by cached suffix replay (``mode='replay'``,
     Sec. 4.3 / Fig. 2);
+  * ``gradient(..., mode='pprb')`` -- basic polarized PRB with noise-regularized
+    inversion (Sec. 4.1-4.2), the baseline whose failure Sec. 4.1 analyses;
   * ``render(..., params_live=...)`` -- the frozen-sampling estimator used for
     central finite differences.
 """
@@ -56,6 +58,8 @@ def lib():
             L.orc_render.argtypes = [P, P, P, i64, P, P, P, P, P, P]
             L.orc_gradient.restype = i32
             L.orc_gradient.argtypes = [P, P, P, i64, P, P, P, P, i32]
+            L.orc_gradient_pprb.restype = i32
+            L.orc_gradient_pprb.argtypes = [P, P, P, i64, P, P, P, P, dbl, i32]
             L.orc_philox.argtypes = [P, P, P]
             L.orc_uniforms.argtypes = [ctypes.c_uint64] * 5 + [P]
             L.orc_fresnel_reflect.argtypes = [dbl, dbl, dbl, dbl, P]
@@ -159,15 +163,24 @@ class OracleScene:
         assert rc == 0
         return (out, pout, sig) if paths else out
 
-    def gradient(self, job, params: dict, dI: np.ndarray, pixels=None, mode: str = "replay") -> dict:
-        """Gradient of sum(dI * I) w.r.t. {tex, ior, le, sheet, theta}."""
+    def gradient(self, job, params: dict, dI: np.ndarray, pixels=None, mode: str = "replay",
+                 sigma: float = 1e-3, primal_noise: bool = True, single: bool = False) -> dict:
+        """Gradient of sum(dI * I) w.r.t. {tex, ior, le, sheet, theta}: mode 'tape'
+        (conventional AD), 'replay' (cached suffix replay) or 'pprb' (basic polarized PRB
+        with noise-regularized inversion, the failing baseline of Sec. 4.1-4.2: noise of
+        deviation ``sigma`` in the primal too when ``primal_noise``, fold and recovery in
+        single precision when ``single``)."""
         pix = self._pixels(job, pixels)
         P, lay = flat_params(params, job)
         dI = np.ascontiguousarray(dI, np.float64).reshape(job.num_angles, len(pix), 3, 4)
         g = np.zeros_like(P)
         j = job_array(job)
-        rc = lib().orc_gradient(self.h, _p(j), _p(pix), len(pix), _p(P), _p(lay), _p(dI), _p(g),
-                                {"tape": 0, "replay": 1}[mode])
+        if mode == "pprb":
+            rc = lib().orc_gradient_pprb(self.h, _p(j), _p(pix), len(pix), _p(P), _p(lay), _p(dI), _p(g),
+                                         float(sigma), int(primal_noise) | (2 if single else 0))
+        else:
+            rc = lib().orc_gradient(self.h, _p(j), _p(pix), len(pix), _p(P), _p(lay), _p(dI), _p(g),
+                                    {"tape": 0, "replay": 1}[mode])
         assert rc == 0
         return unflat(g, lay)
 

@@ -1169,6 +1169,140 @@ int orc_gradient(void* sc, const int64_t* job, const int64_t* pixels, int64_t np
     return 0;
 }
 
+}  // extern "C"
+
+// Basic polarized PRB (P-PRB, Sec. 4.1 with the noise regularization of Sec. 4.2): the
+// baseline the paper shows to fail for rank-deficient, polarization-aware operators, kept
+// here to demonstrate that failure against the exact routes.  The replay knows only the
+// path's total L[1] and recovers each suffix by removing the vertex,
+//     L[v+1] = (W_v + u_v I)^-1 (L[v] - E_v),   u_v ~ N(0, sigma),
+// u_v drawn per (path, vertex) from Philox (key seed ^ 0x5bd1e995, pass 3) by Box-Muller.
+// flags bit 0: the noise also enters the primal fold and the adjoint's throughput (the
+// paper's reading: the same u in both phases); clear, only the inversion is regularized.
+// flags bit 1: the fold and the recovery run in single precision (the precision of a
+// GPU renderer); the local derivative itself is taken in double either way.
+template <typename T>
+static bool solve4(T m[4][5], T x[4]) {
+    for (int c = 0; c < 4; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 4; ++r) if (std::fabs(m[r][c]) > std::fabs(m[piv][c])) piv = r;
+        if (m[piv][c] == T(0)) return false;
+        if (piv != c) for (int j = 0; j < 5; ++j) std::swap(m[c][j], m[piv][j]);
+        for (int r = 0; r < 4; ++r) {
+            if (r == c) continue;
+            T f = m[r][c] / m[c][c];
+            for (int j = c; j < 5; ++j) m[r][j] -= f * m[c][j];
+        }
+    }
+    for (int i = 0; i < 4; ++i) x[i] = m[i][4] / m[i][i];
+    return true;
+}
+
+template <typename T>
+static void pprb_path(const Scene& s, const Params<double>& pd, const Params<Var>& pvar, const Layout& lay,
+                      const JobDesc& J, int A, int64_t ip, int64_t npix, int64_t pix, int smp, const double* dI,
+                      double* grad, double sigma, bool primal_noise) {
+    Path path = sample_path(s, pd, J, pix, smp);
+    int n = (int)path.vs.size();
+    M4<double> Rc = camera_rot(s, J.cam, path.d1);
+    const double inv_spp = 1.0 / J.spp;
+    uint64_t pid = (uint64_t)(pix * J.spp + smp);
+    std::vector<VEval<double>> ev(n);
+    std::vector<double> u(n);
+    for (int v = 0; v < n; ++v) {
+        ev[v] = eval_vertex<double>(s, pd, path.vs[v]);
+        Uniforms un = draw(J.seed ^ 0x5bd1e995ULL, 3, J.stream, pid, (uint64_t)v);
+        u[v] = sigma * std::sqrt(-2.0 * std::log(std::max(un.u[0], 1e-300))) * std::cos(2.0 * M_PI * un.u[1]);
+    }
+    const double up = primal_noise ? 1.0 : 0.0;
+    // phase 1: the path's total, folded from the light end
+    T L[3][4] = {};
+    for (int v = n - 1; v >= 0; --v)
+        for (int c = 0; c < 3; ++c) {
+            T nx[4];
+            for (int k = 0; k < 4; ++k) {
+                T acc = (T)ev[v].E[c].s[k] + (T)(up * u[v]) * L[c][k];
+                for (int j = 0; j < 4; ++j) acc += (T)ev[v].W[c].m[k][j] * L[c][j];
+                nx[k] = acc;
+            }
+            for (int k = 0; k < 4; ++k) L[c][k] = nx[k];
+        }
+    // camera: the filter's own derivative and the adjoint row entering the first vertex
+    double arow[3][4] = {};
+    for (int a = 0; a < A; ++a) {
+        g_tape.clear();
+        Var th = J.filter == FILTER_NONE ? Var(0.0) : pvar.at(lay.theta + a);
+        M4<Var> Cv = camera_filter<Var>(J.filter, th);
+        Var Jt(0.0);
+        for (int c = 0; c < 3; ++c) {
+            S4<double> tot;
+            for (int k = 0; k < 4; ++k) tot.s[k] = (double)L[c][k];
+            S4<Var> o = mvec(Cv, mvec(Rc, tot));
+            for (int k = 0; k < 4; ++k) {
+                double w = dI[((a * npix + ip) * 3 + c) * 4 + k] * inv_spp;
+                if (w == 0.0) continue;
+                Jt = Jt + o.s[k] * w;
+                for (int j = 0; j < 4; ++j) {
+                    double crj = 0.0;
+                    for (int q = 0; q < 4; ++q) crj += Cv.m[k][q].v * Rc.m[q][j];
+                    arow[c][j] += w * crj;
+                }
+            }
+        }
+        tape_backward(Jt, 1.0, grad);
+        g_tape.clear();
+    }
+    // phase 2: replay, recovering each suffix by inversion
+    for (int v = 0; v < n; ++v) {
+        S4<double> Ln[3];
+        for (int c = 0; c < 3; ++c) {
+            T m[4][5], x[4];
+            for (int k = 0; k < 4; ++k) {
+                for (int j = 0; j < 4; ++j) m[k][j] = (T)ev[v].W[c].m[k][j] + (k == j ? (T)u[v] : T(0));
+                m[k][4] = L[c][k] - (T)ev[v].E[c].s[k];
+            }
+            if (!solve4(m, x)) for (int k = 0; k < 4; ++k) x[k] = T(0);
+            for (int k = 0; k < 4; ++k) { L[c][k] = x[k]; Ln[c].s[k] = (double)x[k]; }
+        }
+        g_tape.clear();
+        VEval<Var> e = eval_vertex<Var>(s, pvar, path.vs[v]);
+        Var Jv(0.0);
+        for (int c = 0; c < 3; ++c) {
+            S4<Var> wl = mvec(e.W[c], Ln[c]);
+            for (int k = 0; k < 4; ++k)
+                if (arow[c][k] != 0.0) Jv = Jv + (e.E[c].s[k] + wl.s[k]) * arow[c][k];
+        }
+        tape_backward(Jv, 1.0, grad);
+        g_tape.clear();
+        double na[3][4];
+        for (int c = 0; c < 3; ++c)
+            for (int j = 0; j < 4; ++j) {
+                double acc = arow[c][j] * up * u[v];
+                for (int k = 0; k < 4; ++k) acc += arow[c][k] * ev[v].W[c].m[k][j];
+                na[c][j] = acc;
+            }
+        std::memcpy(arow, na, sizeof(na));
+    }
+}
+
+extern "C" {
+int orc_gradient_pprb(void* sc, const int64_t* job, const int64_t* pixels, int64_t npix, const double* Pd,
+                      const int64_t* layout, const double* dI, double* grad, double sigma, int flags) {
+    const Scene& s = *(const Scene*)sc;
+    JobDesc J = job_from(job);
+    Layout lay = layout_from(layout);
+    Params<double> pd{Pd, lay};
+    Params<Var> pvar{Pd, lay};
+    int A = J.filter == FILTER_NONE ? 1 : J.nang;
+    bool primal_noise = flags & 1, single = flags & 2;
+    for (int64_t ip = 0; ip < npix; ++ip)
+        for (int smp = 0; smp < J.spp; ++smp) {
+            if (single) pprb_path<float>(s, pd, pvar, lay, J, A, ip, npix, pixels[ip], smp, dI, grad, sigma, primal_noise);
+            else pprb_path<double>(s, pd, pvar, lay, J, A, ip, npix, pixels[ip], smp, dI, grad, sigma, primal_noise);
+        }
+    return 0;
+}
+
 // ---------------------------------------------------------------- unit probes
 void orc_philox(const uint64_t* ctr, const uint64_t* key, uint64_t* out) { philox4x64_10(ctr, key, out); }
 void orc_uniforms(uint64_t seed, uint64_t pass, uint64_t stream, uint64_t path, uint64_t vertex, double* u) {

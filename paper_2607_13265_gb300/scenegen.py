@@ -514,6 +514,22 @@ def malus_scene(alpha: float, le: float = 2.0) -> tuple[Scene, Job]:
     return s, job
 
 
+def polarizer_stack_scene(angles, le=2.0, spacing: float = 0.05) -> tuple[Scene, Job]:
+    """Camera looking down -z through a stack of linear-polarizer sheets (sheet k at
+    z = -k * spacing, axis at angles[k]) at a large quad light; polarizer camera filter at
+    0 rad; depth len(angles) + 1 (every camera path crosses the whole stack)."""
+    s = Scene()
+    for k, a in enumerate(angles):
+        s.sheet.append(float(a))
+        m = s.add_material(Material(MAT_POLARIZER_SHEET, sheet_index=k, t1=(1, 0, 0), t2=(0, 1, 0)))
+        s.add_quad((-1, -1, -k * spacing), (2, 0, 0), (0, 2, 0), m)
+    s.add_light((-2, -2, -len(angles) * spacing - 1), (4, 0, 0), (0, 4, 0), le)
+    s.add_camera((0, 0, 2), (0, 0, 0), (0, 1, 0), 0.01)
+    job = Job(camera=0, width=2, height=2, spp=4, max_depth=len(angles) + 1, filter=FILTER_POLARIZER,
+              thetas=[0.0])
+    return s, job
+
+
 def retarder_scene(alpha: float, phi: float, le: float = 2.0) -> tuple[Scene, Job]:
     """Unpolarized light through a polarizer sheet at alpha, then a quarter-wave sheet with
     fast axis phi, seen by an unfiltered camera (depth 3)."""
