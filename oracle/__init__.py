@@ -14,6 +14,7 @@ Functions follow the paper as stated in ``oracle.cpp``'s header:
     Sec. 4.3 / Fig. 2);
   * ``gradient(..., mode='pprb')`` -- basic polarized PRB with noise-regularized
     inversion (Sec. 4.1-4.2), the baseline whose failure Sec. 4.1 analyses;
+  * :meth:`OracleScene.gradient_hybrid` -- hybrid cached replay (Sec. 4.4);
   * ``render(..., params_live=...)`` -- the frozen-sampling estimator used for
     central finite differences.
 """
@@ -60,6 +61,8 @@ def lib():
             L.orc_gradient.argtypes = [P, P, P, i64, P, P, P, P, i32]
             L.orc_gradient_pprb.restype = i32
             L.orc_gradient_pprb.argtypes = [P, P, P, i64, P, P, P, P, dbl, i32]
+            L.orc_gradient_hybrid.restype = i32
+            L.orc_gradient_hybrid.argtypes = [P, P, P, i64, P, P, P, P, i32, dbl, dbl, P]
             L.orc_philox.argtypes = [P, P, P]
             L.orc_uniforms.argtypes = [ctypes.c_uint64] * 5 + [P]
             L.orc_fresnel_reflect.argtypes = [dbl, dbl, dbl, dbl, P]
@@ -184,6 +187,22 @@ class OracleScene:
         assert rc == 0
         return unflat(g, lay)
 
+    def gradient_hybrid(self, job, params: dict, dI: np.ndarray, k: int, gamma: float, eps: float,
+                        pixels=None) -> tuple[dict, dict]:
+        """Gradient by hybrid cached replay (Sec. 4.4): suffixes cached every k vertices, the
+        others recovered by scalar PRB (DI < gamma), inversion (|det| > eps) or
+        recomputation.  Returns (gradient, channel-vertices per route)."""
+        pix = self._pixels(job, pixels)
+        P, lay = flat_params(params, job)
+        dI = np.ascontiguousarray(dI, np.float64).reshape(job.num_angles, len(pix), 3, 4)
+        g = np.zeros_like(P)
+        routes = np.zeros(4)
+        j = job_array(job)
+        rc = lib().orc_gradient_hybrid(self.h, _p(j), _p(pix), len(pix), _p(P), _p(lay), _p(dI), _p(g),
+                                       int(k), float(gamma), float(eps), _p(routes))
+        assert rc == 0
+        return unflat(g, lay), dict(zip(["cached", "scalar", "inverse", "recompute"], routes.tolist()))
+
     def closest(self, o, d, brute=False):
         o = np.ascontiguousarray(o, np.float64)
         d = np.ascontiguousarray(d, np.float64)
@@ -193,9 +212,10 @@ class OracleScene:
 
 
 def stats(reset: bool = True) -> dict:
-    out = np.zeros(8)
+    out = np.zeros(9)
     lib().orc_stats(_p(out), int(reset))
-    keys = ["rays", "shadow_rays", "vertices", "bvh_nodes", "tri_tests", "sph_tests", "paths", "tape_peak_nodes"]
+    keys = ["rays", "shadow_rays", "vertices", "bvh_nodes", "tri_tests", "sph_tests", "paths", "tape_peak_nodes",
+            "tape_total_nodes"]
     return dict(zip(keys, out.tolist()))
 
 

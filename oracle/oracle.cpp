@@ -78,6 +78,7 @@ Uniforms draw(uint64_t seed, uint64_t pass, uint64_t stream, uint64_t path, uint
 struct TNode { int a, b; double da, db; };
 thread_local std::vector<TNode> g_tape;
 thread_local size_t g_tape_peak = 0;
+thread_local double g_tape_total = 0;   // nodes of all whole-path tapes (conventional AD)
 
 struct Var {
     double v; int i;
@@ -1102,6 +1103,7 @@ int orc_gradient(void* sc, const int64_t* job, const int64_t* pixels, int64_t np
                         }
                     }
                 }
+                g_tape_total += (double)g_tape.size();
                 tape_backward(J0, 1.0, grad);
                 g_tape.clear();
             } else {
@@ -1303,6 +1305,171 @@ int orc_gradient_pprb(void* sc, const int64_t* job, const int64_t* pixels, int64
     return 0;
 }
 
+// Hybrid cached replay (Sec. 4.4, Eq. hybrid_decision).  The primal pass keeps the suffix
+// L[c] only at checkpoints c = 0, k, 2k, ... (L[n] = 0).  The replay of a block starting at
+// checkpoint c carries the detached block throughput bt = W_c ... W_v and the block's
+// emitted part eb = sum_{j=c..v} W_c ... W_{j-1} E_j, so that L[c] = eb + bt L[v+1].  A
+// suffix L[v+1] that is not a checkpoint is recovered per colour channel, in this order:
+//   DI(bt) < gamma            : scalar PRB, s0 = (L[c] - eb)_0 / bt_00, polarization dropped;
+//   |det bt| > eps            : bt^-1 (L[c] - eb);
+//   otherwise                 : recomputation -- the vertices v+1 .. (next checkpoint - 1)
+//                               are evaluated again and folded onto the next checkpoint.
+// DI is the depolarization index of Gil and Bernabeu, sqrt(sum m_ij^2 - m_00^2) /
+// (sqrt(3) m_00): 0 for an ideal depolarizer, 1 for a non-depolarizing operator.
+// routes[0..3] += channel-vertices served from a checkpoint, by scalar PRB, by inversion,
+// by recomputation.
+static double depol_index(const M4<double>& m) {
+    if (!(m.m[0][0] > 0.0)) return HUGE_VAL;
+    double s2 = 0.0;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) s2 += m.m[i][j] * m.m[i][j];
+    return std::sqrt(std::max(0.0, s2 - m.m[0][0] * m.m[0][0])) / (std::sqrt(3.0) * m.m[0][0]);
+}
+static double det4(const M4<double>& A) {
+    double m[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) m[i][j] = A.m[i][j];
+    double d = 1.0;
+    for (int c = 0; c < 4; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 4; ++r) if (std::fabs(m[r][c]) > std::fabs(m[piv][c])) piv = r;
+        if (m[piv][c] == 0.0) return 0.0;
+        if (piv != c) { for (int j = 0; j < 4; ++j) std::swap(m[c][j], m[piv][j]); d = -d; }
+        d *= m[c][c];
+        for (int r = c + 1; r < 4; ++r) {
+            double f = m[r][c] / m[c][c];
+            for (int j = c; j < 4; ++j) m[r][j] -= f * m[c][j];
+        }
+    }
+    return d;
+}
+
+extern "C" int orc_gradient_hybrid(void* sc, const int64_t* job, const int64_t* pixels, int64_t npix,
+                                   const double* Pd, const int64_t* layout, const double* dI, double* grad,
+                                   int k, double gamma, double eps, double* routes) {
+    const Scene& s = *(const Scene*)sc;
+    if (k < 1) return -1;
+    JobDesc J = job_from(job);
+    Layout lay = layout_from(layout);
+    Params<double> pd{Pd, lay};
+    Params<Var> pvar{Pd, lay};
+    int A = J.filter == FILTER_NONE ? 1 : J.nang;
+    for (int64_t ip = 0; ip < npix; ++ip) {
+        int64_t pix = pixels[ip];
+        for (int smp = 0; smp < J.spp; ++smp) {
+            Path path = sample_path(s, pd, J, pix, smp);
+            int n = (int)path.vs.size();
+            M4<double> Rc = camera_rot(s, J.cam, path.d1);
+            const double inv_spp = 1.0 / J.spp;
+            // primal pass: fold, keeping the suffix only at the checkpoints
+            int nck = n / k + 2;
+            std::vector<std::array<S4<double>, 3>> Lck(nck);
+            for (auto& a : Lck) for (int c = 0; c < 3; ++c) a[c] = szero<double>();
+            {
+                S4<double> L[3] = {szero<double>(), szero<double>(), szero<double>()};
+                for (int v = n - 1; v >= 0; --v) {
+                    VEval<double> e = eval_vertex<double>(s, pd, path.vs[v]);
+                    for (int c = 0; c < 3; ++c) {
+                        S4<double> wl = mvec(e.W[c], L[c]);
+                        for (int q = 0; q < 4; ++q) L[c].s[q] = e.E[c].s[q] + wl.s[q];
+                    }
+                    if (v % k == 0) for (int c = 0; c < 3; ++c) Lck[v / k][c] = L[c];
+                }
+            }
+            auto suffix_at_ck = [&](int idx, int c) -> S4<double> {   // L[idx], idx a checkpoint or n
+                return idx >= n ? szero<double>() : Lck[idx / k][c];
+            };
+            // camera-filter term and the initial adjoint row
+            double arow[3][4] = {};
+            for (int a = 0; a < A; ++a) {
+                g_tape.clear();
+                Var th = J.filter == FILTER_NONE ? Var(0.0) : pvar.at(lay.theta + a);
+                M4<Var> Cv = camera_filter<Var>(J.filter, th);
+                Var Jt(0.0);
+                for (int c = 0; c < 3; ++c) {
+                    S4<Var> o = mvec(Cv, mvec(Rc, suffix_at_ck(0, c)));
+                    for (int q = 0; q < 4; ++q) {
+                        double w = dI[((a * npix + ip) * 3 + c) * 4 + q] * inv_spp;
+                        if (w == 0.0) continue;
+                        Jt = Jt + o.s[q] * w;
+                        for (int j = 0; j < 4; ++j) {
+                            double crj = 0.0;
+                            for (int r = 0; r < 4; ++r) crj += Cv.m[q][r].v * Rc.m[r][j];
+                            arow[c][j] += w * crj;
+                        }
+                    }
+                }
+                tape_backward(Jt, 1.0, grad);
+                g_tape.clear();
+            }
+            // replay
+            M4<double> bt[3];
+            S4<double> eb[3], Lblk[3];
+            for (int v = 0; v < n; ++v) {
+                if (v % k == 0)
+                    for (int c = 0; c < 3; ++c) { bt[c] = M4<double>::ident(); eb[c] = szero<double>(); Lblk[c] = suffix_at_ck(v, c); }
+                VEval<double> ev = eval_vertex<double>(s, pd, path.vs[v]);
+                for (int c = 0; c < 3; ++c) {
+                    S4<double> be = mvec(bt[c], ev.E[c]);
+                    for (int q = 0; q < 4; ++q) eb[c].s[q] += be.s[q];
+                    bt[c] = mmul(bt[c], ev.W[c]);
+                }
+                S4<double> Ln[3];
+                const int next = (v / k + 1) * k;
+                for (int c = 0; c < 3; ++c) {
+                    if (v + 1 == next || v + 1 >= n) { Ln[c] = suffix_at_ck(v + 1, c); routes[0] += 1; continue; }
+                    S4<double> r;
+                    for (int q = 0; q < 4; ++q) r.s[q] = Lblk[c].s[q] - eb[c].s[q];
+                    double di = depol_index(bt[c]);
+                    if (di < gamma) {
+                        Ln[c] = szero<double>();
+                        Ln[c].s[0] = r.s[0] / bt[c].m[0][0];
+                        routes[1] += 1;
+                    } else if (std::fabs(det4(bt[c])) > eps) {
+                        double m[4][5], x[4];
+                        for (int i = 0; i < 4; ++i) { for (int j = 0; j < 4; ++j) m[i][j] = bt[c].m[i][j]; m[i][4] = r.s[i]; }
+                        solve4(m, x);
+                        for (int q = 0; q < 4; ++q) Ln[c].s[q] = x[q];
+                        routes[2] += 1;
+                    } else {
+                        // trace on to the next checkpoint and fold onto its cached suffix
+                        S4<double> acc = szero<double>();
+                        M4<double> T = M4<double>::ident();
+                        for (int j = v + 1; j < std::min(next, n); ++j) {
+                            VEval<double> ej = eval_vertex<double>(s, pd, path.vs[j]);
+                            S4<double> te = mvec(T, ej.E[c]);
+                            for (int q = 0; q < 4; ++q) acc.s[q] += te.s[q];
+                            T = mmul(T, ej.W[c]);
+                        }
+                        S4<double> tl = mvec(T, suffix_at_ck(next, c));
+                        for (int q = 0; q < 4; ++q) Ln[c].s[q] = acc.s[q] + tl.s[q];
+                        routes[3] += 1;
+                    }
+                }
+                g_tape.clear();
+                VEval<Var> e = eval_vertex<Var>(s, pvar, path.vs[v]);
+                Var Jv(0.0);
+                for (int c = 0; c < 3; ++c) {
+                    S4<Var> wl = mvec(e.W[c], Ln[c]);
+                    for (int q = 0; q < 4; ++q)
+                        if (arow[c][q] != 0.0) Jv = Jv + (e.E[c].s[q] + wl.s[q]) * arow[c][q];
+                }
+                tape_backward(Jv, 1.0, grad);
+                g_tape.clear();
+                double na[3][4];
+                for (int c = 0; c < 3; ++c)
+                    for (int j = 0; j < 4; ++j) {
+                        double acc = 0.0;
+                        for (int q = 0; q < 4; ++q) acc += arow[c][q] * ev.W[c].m[q][j];
+                        na[c][j] = acc;
+                    }
+                std::memcpy(arow, na, sizeof(na));
+            }
+        }
+    }
+    return 0;
+}
+
 // ---------------------------------------------------------------- unit probes
 void orc_philox(const uint64_t* ctr, const uint64_t* key, uint64_t* out) { philox4x64_10(ctr, key, out); }
 void orc_uniforms(uint64_t seed, uint64_t pass, uint64_t stream, uint64_t path, uint64_t vertex, double* u) {
@@ -1348,7 +1515,8 @@ int orc_closest(void* sc, const double* o, const double* d, int brute, double* t
 void orc_stats(double* out, int reset) {
     out[0] = g_stats.rays; out[1] = g_stats.shadow_rays; out[2] = g_stats.vertices; out[3] = g_stats.nodes;
     out[4] = g_stats.tri_tests; out[5] = g_stats.sph_tests; out[6] = g_stats.paths; out[7] = (double)g_tape_peak;
-    if (reset) { g_stats = Stats{}; g_tape_peak = 0; }
+    out[8] = g_tape_total;
+    if (reset) { g_stats = Stats{}; g_tape_peak = 0; g_tape_total = 0; }
 }
 
 }  // extern "C"

@@ -500,6 +500,43 @@ def large_scene(num_meshes: int = 10, freq: int = 50, tex_res: int = 1024, width
     return s, job
 
 
+def deep_stack_scene(num_sheets: int = 85, width: int = 1280, height: int = 720, spp: int = 1,
+                     depth: int = 128, freq: int = 20, tex_res: int = 256) -> tuple[Scene, Job]:
+    """Deep-path workload: a closed diffuse room (every wall albedo 0.8, the floor a
+    differentiable tex_res^2x3 map ~ U[0.6,0.9], seed 9) lit by a ceiling quad light of
+    radiance 10, holding a rough-conductor displaced sphere (20*freq^2 triangles, eta =
+    0.2+3.0i, roughness 0.2) and, between it and the camera, a stack of num_sheets linear
+    polarizers (0.6 x 0.6, spacing 0.004) whose axes twist from 0 to 90 deg.  The room is
+    closed, so every path runs to max_depth; a path through the stack spends num_sheets
+    vertices in it.  Camera polarizer at 0 deg; 1280x720, 1 spp."""
+    s = Scene()
+    floor_alb = np.random.default_rng(9).uniform(0.6, 0.9, (tex_res, tex_res, 3))
+    tf = s.add_texture(floor_alb, differentiable=True)
+    tw = s.add_const_texture([0.8, 0.8, 0.8])
+    troughness = s.add_const_texture([0.2])
+    talb = s.add_const_texture([0.9, 0.9, 0.9])
+    wall = s.add_material(Material(MAT_DIFFUSE, albedo_tex=tw))
+    floor = s.add_material(Material(MAT_DIFFUSE, albedo_tex=tf))
+    s.add_quad((-1, -1, -1), (0, 0, 2), (2, 0, 0), floor)   # floor, normal +y
+    s.add_quad((-1, 1, -1), (2, 0, 0), (0, 0, 2), wall)     # ceiling, normal -y
+    s.add_quad((-1, -1, -1), (2, 0, 0), (0, 2, 0), wall)    # back, normal +z
+    s.add_quad((-1, -1, -1), (0, 2, 0), (0, 0, 2), wall)    # left, normal +x
+    s.add_quad((1, -1, -1), (0, 0, 2), (0, 2, 0), wall)     # right, normal -x
+    s.add_quad((-1, -1, 1), (0, 2, 0), (2, 0, 0), wall)     # front, normal -z
+    s.add_light((-0.3, 0.999, -0.3), (0.6, 0, 0), (0, 0, 0.6), 10.0)
+    cond = s.add_material(Material(MAT_CONDUCTOR_GGX, albedo_tex=talb, rough_tex=troughness, eta_re=0.2, eta_im=3.0))
+    v, f, uv = displaced_sphere(freq, 0.05, seed=1, radius=0.35, center=(0.0, -0.5, -0.4))
+    s.add_mesh(v, f, cond, uv)
+    for k in range(num_sheets):
+        s.sheet.append(0.5 * math.pi * k / max(1, num_sheets - 1))
+        m = s.add_material(Material(MAT_POLARIZER_SHEET, sheet_index=k, t1=(1, 0, 0), t2=(0, 1, 0)))
+        s.add_quad((-0.3, -0.4, 0.3 - 0.004 * k), (0.6, 0, 0), (0, 0.6, 0), m)
+    s.add_camera((0, 0, 0.95), (0, -0.1, -1), (0, 1, 0), 60.0)
+    job = Job(camera=0, width=width, height=height, spp=spp, max_depth=depth, seed=0,
+              filter=FILTER_POLARIZER, thetas=[0.0])
+    return s, job
+
+
 # ============================================================ closed-form test scenes
 def malus_scene(alpha: float, le: float = 2.0) -> tuple[Scene, Job]:
     """Camera looking down -z through a linear-polarizer sheet (axis at alpha from +x toward
