@@ -110,7 +110,8 @@ typedef struct {
 } dppt_scene_desc;
 
 /* One render job: a camera view rendered at width x height with spp paths per
- * pixel and at most max_depth surface vertices per path, seen through the
+ * pixel and at most max_depth surface vertices per path (1 <= max_depth <= 128;
+ * the cache of a path holds 124 bytes per vertex), seen through the
  * camera filter at num_angles polarizer angles params.theta[theta_offset + a].
  * Path p = pixel * spp + sample draws its randoms from Philox4x64-10 with key
  * (seed ^ pass * 0x9E3779B97F4A7C15, stream) and counter (p, vertex, 0, 0);
@@ -195,7 +196,9 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* scene, const dp
 
 /* Device workspace (bytes) the jobs need beyond the caller's buffers with the
  * context's current launch shapes: filter buffers, plus the wavefront path
- * state and per-vertex cache when a wavefront schedule is selected. */
+ * state and per-vertex cache when a wavefront schedule is selected.  The
+ * wavefront runs in waves of at most 4,194,304 paths (whole pixels), fewer
+ * when the wave's state and cache would pass 8 GiB (deep paths). */
 dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int32_t njobs, size_t* bytes);
 
 /* Schedule for subsequent launches (the autotuner's choice). */
@@ -213,6 +216,28 @@ dppt_status dppt_get_launch(const dppt_ctx* ctx, dppt_launch* launch);
  * produced while tuning are discarded.  Synchronous. */
 dppt_status dppt_autotune(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* jobs, int32_t njobs,
                           const dppt_params* params, int32_t reps, dppt_launch* best, float* times_ms);
+
+/* Hybrid cached replay (Sec. 4.4, Eq. hybrid_decision) for subsequent
+ * render_adjoint calls.  checkpoint_interval k = 1 (the default) caches the
+ * suffix at every vertex (Sec. 4.3).  k = 4, 8 or 16 keeps it only at every
+ * k-th vertex; the replay recovers the others from the detached throughput bt
+ * of the vertices since the last checkpoint: by the scalar PRB update (s0
+ * only, polarization dropped) when its depolarization index
+ * DI(bt) = sqrt(sum m_ij^2 - m_00^2) / (sqrt(3) m_00) is below gamma, by
+ * bt^-1 applied to the checkpoint's suffix minus the block's emission when
+ * |det bt| > eps, and otherwise by tracing the block again up to the next
+ * checkpoint.  gamma = 0 never takes the scalar route; eps = +inf never
+ * inverts (then the result is exact).  k > 1 runs on the grid and persistent
+ * adjoint schedules only (render_adjoint returns DPPT_ERR_UNSUPPORTED with the
+ * wavefront schedule).  Errors: INVALID_ARG for another k, a negative or NaN
+ * threshold. */
+typedef struct {
+    int32_t checkpoint_interval;
+    float gamma;
+    float eps;
+} dppt_replay;
+dppt_status dppt_set_replay(dppt_ctx* ctx, const dppt_replay* replay);
+dppt_status dppt_get_replay(const dppt_ctx* ctx, dppt_replay* replay);
 
 /* Per-thread local cache bytes and registers of the adjoint kernel used for
  * max_depth, and the resident threads per SM for the current launch shape:

@@ -56,6 +56,10 @@ class Launch(ctypes.Structure):
                 ("adj_schedule", c_i32), ("adj_block_size", c_i32), ("adj_blocks_per_sm", c_i32)]
 
 
+class Replay(ctypes.Structure):
+    _fields_ = [("checkpoint_interval", c_i32), ("gamma", c_f32), ("eps", c_f32)]
+
+
 # every symbol include/dppt.h declares, with (restype, argtypes)
 SIGNATURES = {
     "dppt_create": (c_i32, [ctypes.POINTER(c_vp), ctypes.c_int]),
@@ -72,6 +76,8 @@ SIGNATURES = {
     "dppt_set_launch": (c_i32, [c_vp, ctypes.POINTER(Launch)]),
     "dppt_get_launch": (c_i32, [c_vp, ctypes.POINTER(Launch)]),
     "dppt_adjoint_footprint": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_i64)]),
+    "dppt_set_replay": (c_i32, [c_vp, ctypes.POINTER(Replay)]),
+    "dppt_get_replay": (c_i32, [c_vp, ctypes.POINTER(Replay)]),
     "dppt_count_work": (c_i32, [c_vp, c_vp, ctypes.POINTER(Job), c_i32, ctypes.POINTER(Params),
                                 ctypes.POINTER(ctypes.c_uint64)]),
     "dppt_autotune": (c_i32, [c_vp, c_vp, ctypes.POINTER(Job), c_i32, ctypes.POINTER(Params), c_i32,

@@ -77,6 +77,18 @@ class Context:
         _check(self.h, self.lib.dppt_get_launch(self.h, ctypes.byref(l)), "dppt_get_launch")
         return (l.schedule, l.block_size, l.blocks_per_sm, l.adj_schedule, l.adj_block_size, l.adj_blocks_per_sm)
 
+    def set_replay(self, checkpoint_interval: int = 1, gamma: float = 0.0, eps: float = float("inf")):
+        """Suffix replay of render_adjoint: checkpoint_interval 1 caches every vertex's suffix
+        (Sec. 4.3); 4, 8 or 16 is the hybrid cached replay of Sec. 4.4 with thresholds gamma
+        (depolarization index, scalar route) and eps (|det|, inversion route)."""
+        r = L.Replay(int(checkpoint_interval), float(gamma), float(eps))
+        _check(self.h, self.lib.dppt_set_replay(self.h, ctypes.byref(r)), "dppt_set_replay")
+
+    def get_replay(self) -> tuple:
+        r = L.Replay()
+        _check(self.h, self.lib.dppt_get_replay(self.h, ctypes.byref(r)), "dppt_get_replay")
+        return (r.checkpoint_interval, r.gamma, r.eps)
+
     def adjoint_footprint(self, max_depth: int) -> dict:
         out = (ctypes.c_int64 * 4)()
         _check(self.h, self.lib.dppt_adjoint_footprint(self.h, max_depth, out), "dppt_adjoint_footprint")

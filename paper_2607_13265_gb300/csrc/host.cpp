@@ -22,6 +22,7 @@ struct dppt_ctx {
     unsigned* d_status = nullptr;
     unsigned long long* d_counter = nullptr;
     dppt_launch launch{DPPT_SCHED_GRID, 128, 0, DPPT_SCHED_GRID, 128, 0};
+    dppt_replay replay{1, 0.0f, 0.0f};
     StageLog log;
 };
 
@@ -203,7 +204,7 @@ int red_mode(int spp) {
 }
 
 int depth_bucket(int max_depth) {
-    for (int b : {4, 8, 16, 32, 64})
+    for (int b : {4, 8, 16, 32, 64, 128})
         if (max_depth <= b) return b;
     return -1;
 }
@@ -217,6 +218,7 @@ cudaError_t launch_trace(int bucket, int mode, const DScene& S, const DParams& P
         case 16: return launch_trace_16(mode, S, P, G, T, L, counter, status, work, st);
         case 32: return launch_trace_32(mode, S, P, G, T, L, counter, status, work, st);
         case 64: return launch_trace_64(mode, S, P, G, T, L, counter, status, work, st);
+        case 128: return launch_trace_128(mode, S, P, G, T, L, counter, status, work, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -227,6 +229,7 @@ cudaError_t trace_attributes(int bucket, int mode, cudaFuncAttributes* a) {
         case 16: return trace_attributes_16(mode, a);
         case 32: return trace_attributes_32(mode, a);
         case 64: return trace_attributes_64(mode, a);
+        case 128: return trace_attributes_128(mode, a);
     }
     return cudaErrorInvalidValue;
 }
@@ -237,6 +240,36 @@ int trace_occupancy(int bucket, int mode, int block, size_t smem) {
         case 16: return trace_occupancy_16(mode, block, smem);
         case 32: return trace_occupancy_32(mode, block, smem);
         case 64: return trace_occupancy_64(mode, block, smem);
+        case 128: return trace_occupancy_128(mode, block, smem);
+    }
+    return 0;
+}
+
+// hybrid cached replay kernels: interval k in {4, 8, 16}, depth buckets 8..128
+int hybrid_bucket(int max_depth) { return std::max(8, depth_bucket(max_depth)); }
+cudaError_t launch_hybrid(int k, int bucket, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T,
+                          const LaunchCfg& L, unsigned long long* counter, unsigned* status, HybridCfg hc,
+                          cudaStream_t st) {
+    switch (k) {
+        case 4: return launch_hybrid_4(bucket, S, P, G, T, L, counter, status, hc, st);
+        case 8: return launch_hybrid_8(bucket, S, P, G, T, L, counter, status, hc, st);
+        case 16: return launch_hybrid_16(bucket, S, P, G, T, L, counter, status, hc, st);
+    }
+    return cudaErrorInvalidValue;
+}
+cudaError_t hybrid_attributes(int k, int bucket, cudaFuncAttributes* a) {
+    switch (k) {
+        case 4: return hybrid_attributes_4(bucket, a);
+        case 8: return hybrid_attributes_8(bucket, a);
+        case 16: return hybrid_attributes_16(bucket, a);
+    }
+    return cudaErrorInvalidValue;
+}
+int hybrid_occupancy(int k, int bucket, int block, size_t smem) {
+    switch (k) {
+        case 4: return hybrid_occupancy_4(bucket, block, smem);
+        case 8: return hybrid_occupancy_8(bucket, block, smem);
+        case 16: return hybrid_occupancy_16(bucket, block, smem);
     }
     return 0;
 }
@@ -270,7 +303,7 @@ dppt_status check_jobs(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs,
         if (j.camera < 0 || j.camera >= s->num_cameras) return bad("camera index out of range");
         if (j.width < 1 || j.height < 1 || (int64_t)j.width * j.height > (1LL << 31) - 1) return bad("bad image size");
         if (j.spp < 1 || j.spp > (1 << 20)) return bad("spp out of range [1, 2^20]");
-        if (j.max_depth < 1 || j.max_depth > 64) return bad("max_depth out of range [1, 64]");
+        if (j.max_depth < 1 || j.max_depth > kMaxDepth) return bad("max_depth out of range [1, 128]");
         if (j.filter < DPPT_FILTER_NONE || j.filter > DPPT_FILTER_QWP_POLARIZER) return bad("unknown filter");
         if (j.out_offset < 0) return bad("negative out_offset");
         if ((j.out_offset & 3) != 0) return bad("out_offset must be a multiple of 4 floats");
@@ -588,22 +621,25 @@ static void build_tables(const dppt_job* jobs, int njobs, const std::vector<JobP
     }
 }
 
-constexpr long long kWaveCap = 1LL << 22;   // paths per wave of the wavefront schedule
-
-static long long wave_paths(const dppt_job* jobs, int njobs) {
-    long long q = 0;
-    for (int i = 0; i < njobs; ++i) {
-        long long n = (long long)jobs[i].width * jobs[i].height * jobs[i].spp;
-        long long cap = std::max<long long>(jobs[i].spp, (kWaveCap / jobs[i].spp) * jobs[i].spp);
-        q = std::max(q, std::min(n, cap));
-    }
-    return q;
-}
+constexpr long long kWaveCap = 1LL << 22;        // paths per wave of the wavefront schedule
+constexpr long long kWaveBytes = 8LL << 30;      // wave state + cache budget (deep paths take smaller waves)
 
 static int max_depth_of(const dppt_job* jobs, int njobs) {
     int d = 1;
     for (int i = 0; i < njobs; ++i) d = std::max(d, jobs[i].max_depth);
     return d;
+}
+
+static long long wave_paths(const dppt_job* jobs, int njobs) {
+    const long long per_path = (long long)(wavefront_bytes(1LL << 20, max_depth_of(jobs, njobs)) >> 20) + 1;
+    const long long limit = std::min(kWaveCap, std::max(1LL, kWaveBytes / per_path));
+    long long q = 0;
+    for (int i = 0; i < njobs; ++i) {
+        long long n = (long long)jobs[i].width * jobs[i].height * jobs[i].spp;
+        long long cap = std::max<long long>(jobs[i].spp, (limit / jobs[i].spp) * jobs[i].spp);
+        q = std::max(q, std::min(n, cap));
+    }
+    return q;
 }
 
 static size_t scalar_smem(const dppt_scene* s) {
@@ -690,6 +726,8 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
     if (st != DPPT_OK) return st;
     const Shape shape = shape_of(ctx, 1);
     const bool wave = shape.schedule == DPPT_SCHED_WAVEFRONT;
+    if (wave && ctx->replay.checkpoint_interval > 1)
+        return fail(ctx, DPPT_ERR_UNSUPPORTED, "hybrid cached replay runs on the grid and persistent schedules");
     const long long Q = wave ? wave_paths(jobs, njobs) : 0;
     const int cap = max_depth_of(jobs, njobs);
     const size_t ws_jobs = ws;
@@ -732,6 +770,31 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
                                               shape.block, ctx->d_status, cs, &ctx->log);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront adjoint");
             }
+            continue;
+        }
+        if (ctx->replay.checkpoint_interval > 1) {
+            // hybrid cached replay: checkpoints every k vertices
+            const int k = ctx->replay.checkpoint_interval, hb = hybrid_bucket(maxd[g]);
+            cudaFuncAttributes fa;
+            cudaError_t e = hybrid_attributes(k, hb, &fa);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel attributes");
+            if (shape.block > fa.maxThreadsPerBlock)
+                return fail(ctx, DPPT_ERR_INVALID_ARG, "block_size exceeds the hybrid kernel's limit of " +
+                                                           std::to_string(fa.maxThreadsPerBlock) + " threads");
+            LaunchCfg L;
+            L.schedule = shape.schedule;
+            L.block = shape.block;
+            int occ = std::max(1, hybrid_occupancy(k, hb, L.block, scalar_smem(s)));
+            L.grid = ctx->sm_count * (shape.bps > 0 ? std::min(shape.bps, occ) : occ);
+            if (L.schedule == DPPT_SCHED_PERSISTENT) {
+                e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), cs);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+            }
+            int tok = ctx->log.begin(kStageAdjoint, cs);
+            e = launch_hybrid(k, hb, s->d, P, G, T, L, ctx->d_counter, ctx->d_status,
+                              HybridCfg{ctx->replay.gamma, ctx->replay.eps}, cs);
+            ctx->log.end(tok, cs);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "hybrid adjoint launch");
             continue;
         }
         const int bucket = depth_bucket(maxd[g]);
@@ -825,14 +888,33 @@ dppt_status dppt_get_launch(const dppt_ctx* ctx, dppt_launch* l) {
 }
 
 dppt_status dppt_adjoint_footprint(const dppt_ctx* ctx, int32_t max_depth, int64_t out[4]) {
-    if (!ctx || !out || max_depth < 1 || max_depth > 64) return DPPT_ERR_INVALID_ARG;
-    const int bucket = depth_bucket(max_depth);
+    if (!ctx || !out || max_depth < 1 || max_depth > kMaxDepth) return DPPT_ERR_INVALID_ARG;
+    const int k = ctx->replay.checkpoint_interval, blk = ctx->launch.adj_block_size;
+    const int bucket = k > 1 ? hybrid_bucket(max_depth) : depth_bucket(max_depth);
     cudaFuncAttributes a;
-    if (trace_attributes(bucket, 1, &a) != cudaSuccess) return DPPT_ERR_CUDA;
+    if ((k > 1 ? hybrid_attributes(k, bucket, &a) : trace_attributes(bucket, 1, &a)) != cudaSuccess)
+        return DPPT_ERR_CUDA;
     out[0] = (int64_t)a.localSizeBytes;
     out[1] = a.numRegs;
-    out[2] = (int64_t)trace_occupancy(bucket, 1, ctx->launch.adj_block_size, 1024) * ctx->launch.adj_block_size;
+    out[2] = (int64_t)(k > 1 ? hybrid_occupancy(k, bucket, blk, 1024) : trace_occupancy(bucket, 1, blk, 1024)) * blk;
     out[3] = ctx->sm_count;
+    return DPPT_OK;
+}
+
+dppt_status dppt_set_replay(dppt_ctx* ctx, const dppt_replay* r) {
+    if (!ctx || !r) return fail(ctx, DPPT_ERR_INVALID_ARG, "null argument");
+    const int k = r->checkpoint_interval;
+    if (k != 1 && k != 4 && k != 8 && k != 16)
+        return fail(ctx, DPPT_ERR_INVALID_ARG, "checkpoint_interval must be 1, 4, 8 or 16");
+    if (!(r->gamma >= 0.0f) || !(r->eps >= 0.0f))
+        return fail(ctx, DPPT_ERR_INVALID_ARG, "gamma and eps must be >= 0");
+    ctx->replay = *r;
+    return DPPT_OK;
+}
+
+dppt_status dppt_get_replay(const dppt_ctx* ctx, dppt_replay* r) {
+    if (!ctx || !r) return DPPT_ERR_INVALID_ARG;
+    *r = ctx->replay;
     return DPPT_OK;
 }
 

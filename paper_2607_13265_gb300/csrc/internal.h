@@ -10,6 +10,7 @@ namespace dppt {
 
 constexpr int kMaxJobsPerLaunch = 64;
 constexpr int kBvhStack = 64;
+constexpr int kMaxDepth = 128;      // surface vertices per path (largest cache bucket)
 
 struct DMat {
     int type, albedo_tex, rough_tex, ior_index, sheet_index;
@@ -139,7 +140,22 @@ DPPT_DECLARE_BUCKET(8)
 DPPT_DECLARE_BUCKET(16)
 DPPT_DECLARE_BUCKET(32)
 DPPT_DECLARE_BUCKET(64)
+DPPT_DECLARE_BUCKET(128)
 #undef DPPT_DECLARE_BUCKET
+
+// hybrid cached replay (hybrid_k<K>.cu): adjoint megakernels with checkpoint interval K
+// for depth buckets 8..128
+struct HybridCfg { float gamma, eps; };
+#define DPPT_DECLARE_HYBRID(K)                                                                                     \
+    cudaError_t launch_hybrid_##K(int bucket, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T, \
+                                  const LaunchCfg& L, unsigned long long* counter, unsigned* status, HybridCfg hc, \
+                                  cudaStream_t st);                                                               \
+    cudaError_t hybrid_attributes_##K(int bucket, cudaFuncAttributes* a);                                         \
+    int hybrid_occupancy_##K(int bucket, int block, size_t smem);
+DPPT_DECLARE_HYBRID(4)
+DPPT_DECLARE_HYBRID(8)
+DPPT_DECLARE_HYBRID(16)
+#undef DPPT_DECLARE_HYBRID
 
 // wavefront schedule (wavefront.cu): workspace bytes for waves of Q paths with
 // a cache of `cap` vertices, and the run of one job of a table

@@ -51,6 +51,7 @@ cudaError_t launch_bucket(int bucket, const DScene& S, const DParams& P, const D
         case 16: return launch_trace_16(0, S, P, G, T, L, nullptr, status, nullptr, st);
         case 32: return launch_trace_32(0, S, P, G, T, L, nullptr, status, nullptr, st);
         case 64: return launch_trace_64(0, S, P, G, T, L, nullptr, status, nullptr, st);
+        case 128: return launch_trace_128(0, S, P, G, T, L, nullptr, status, nullptr, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -76,7 +77,7 @@ extern "C" dppt_status dppt_render_primal_noalloc(dppt_ctx* ctx, const dppt_scen
     const dppt_job& j = *job;
     const DScene& S = *scene_view(scene);
     if (j.camera < 0 || j.camera >= scene_num_cameras(scene)) return bad(ctx, DPPT_ERR_INVALID_ARG, "camera index out of range");
-    if (j.width < 1 || j.height < 1 || j.spp < 1 || j.spp > (1 << 20) || j.max_depth < 1 || j.max_depth > 64)
+    if (j.width < 1 || j.height < 1 || j.spp < 1 || j.spp > (1 << 20) || j.max_depth < 1 || j.max_depth > kMaxDepth)
         return bad(ctx, DPPT_ERR_INVALID_ARG, "bad image size, spp or max_depth");
     if (j.filter < DPPT_FILTER_NONE || j.filter > DPPT_FILTER_QWP_POLARIZER) return bad(ctx, DPPT_ERR_INVALID_ARG, "unknown filter");
     if (j.out_offset < 0 || (j.out_offset & 3) != 0) return bad(ctx, DPPT_ERR_INVALID_ARG, "out_offset must be a non-negative multiple of 4");
@@ -116,8 +117,8 @@ extern "C" dppt_status dppt_render_primal_noalloc(dppt_ctx* ctx, const dppt_scen
         e = cudaMemsetAsync(J.raw, 0, (size_t)npix * 12 * sizeof(float), st);
         if (e != cudaSuccess) return bad(ctx, DPPT_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(e));
     }
-    int bucket = 64;
-    for (int b : {4, 8, 16, 32, 64})
+    int bucket = kMaxDepth;
+    for (int b : {4, 8, 16, 32, 64, 128})
         if (j.max_depth <= b) { bucket = b; break; }
     DParams P{params->tex, params->ior, params->le, params->sheet, params->theta};
     DGrads G{nullptr, nullptr, nullptr, nullptr};

@@ -756,6 +756,92 @@ struct GlobalCache {
     __device__ __forceinline__ float& w(int v, int k) const { return base[((long long)v * 31 + 12 + k) * Q + q]; }
 };
 
+// The replayed vertex's local vector-Jacobian product: J_c = a_c^T (E_c + W_c L_c) with
+// dual numbers (W and the NEE operator f from eval_vertex<D3>, Ln the suffix L[v+1]),
+// scattered into the gradients; then the adjoint row advances, a^T <- a^T W_v.
+__device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, const DGrads& G_, float* sgrad,
+                                           const VCtx& vc, const Compact<D3>& W, const Compact<D3>& f,
+                                           const float Ln[3][4], float a[3][4]) {
+    const DScene* S = &S_;
+    const DParams* P = &P_;
+    const DGrads* G = &G_;
+    const DMat m = S->mats[vc.mat];
+    // local vector-Jacobian products: J_c = a_c^T (E_c + W_c L_c) with dual numbers
+    float g_slot0 = 0.0f, g_eta = 0.0f, g_alb[3];
+    Compact<float> fv;
+    if (vc.nee) fv = compact_value(f);
+    Rot<float> Rle = {1.0f, 0.0f};
+    if (vc.nee) Rle = emitter_rot(load_light(*S, vc.nee_light), -vc.wl);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        D3 x[4] = {D3(Ln[c][0]), D3(Ln[c][1]), D3(Ln[c][2]), D3(Ln[c][3])};
+        D3 y[4];
+        compact_apply(W, c, x, y);
+        D3 J = y[0] * a[c][0] + y[1] * a[c][1] + y[2] * a[c][2] + y[3] * a[c][3];
+        if (vc.nee) {
+            const float* le = P->le + 12 * vc.nee_light + 4 * c;
+            float lv[4] = {__ldg(le), __ldg(le + 1), __ldg(le + 2), __ldg(le + 3)};
+            rot_apply(Rle, lv);
+            D3 xe[4] = {D3(lv[0] * vc.nee_w), D3(lv[1] * vc.nee_w), D3(lv[2] * vc.nee_w), D3(lv[3] * vc.nee_w)};
+            D3 ye[4];
+            compact_apply(f, c, xe, ye);
+            J = J + ye[0] * a[c][0] + ye[1] * a[c][1] + ye[2] * a[c][2] + ye[3] * a[c][3];
+        }
+        g_slot0 += J.d0;
+        g_eta += J.d1;
+        g_alb[c] = J.d2;
+    }
+    // emitter Stokes gradients (linear): w R^T a for a hit, nee_w R^T f^T a for NEE
+    if (vc.emit || vc.nee) {
+        const int base = S->num_ior + S->num_sheets;
+        Rot<float> Re = {1.0f, 0.0f};
+        if (vc.emit) Re = emitter_rot(load_light(*S, vc.light), vc.wo);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (vc.emit) {
+                float g[4] = {a[c][0], a[c][1], a[c][2], a[c][3]};
+                rot_apply_row(Re, g);
+                for (int k = 0; k < 4; ++k)
+                    if (g[k] != 0.0f) atomicAdd(sgrad + base + 12 * vc.light + 4 * c + k, g[k] * vc.w_emit);
+            }
+            if (vc.nee) {
+                float g[4] = {a[c][0], a[c][1], a[c][2], a[c][3]};
+                compact_row(fv, c, g);
+                rot_apply_row(Rle, g);
+                for (int k = 0; k < 4; ++k)
+                    if (g[k] != 0.0f) atomicAdd(sgrad + base + 12 * vc.nee_light + 4 * c + k, g[k] * vc.nee_w);
+            }
+        }
+    }
+    // parameter scatter
+    if (m.type == DPPT_MAT_SMOOTH_DIELECTRIC || m.type == DPPT_MAT_PLASTIC_GGX) {
+        if (g_eta != 0.0f) atomicAdd(sgrad + m.ior_index, g_eta);
+    }
+    if (m.type == DPPT_MAT_POLARIZER_SHEET || m.type == DPPT_MAT_RETARDER_SHEET) {
+        if (g_slot0 != 0.0f) atomicAdd(sgrad + S->num_ior + m.sheet_index, g_slot0);
+    }
+    if (G->tex) {
+        if ((m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.rough_tex].pad) {
+            Taps tp = tex_taps(S->tex[m.rough_tex], vc.tu, vc.tv);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomic_add_agg(G->tex, tp.idx[k], g_slot0 * tp.w[k]);
+        }
+        if (m.albedo_tex >= 0 && (m.type == DPPT_MAT_DIFFUSE || m.type == DPPT_MAT_CONDUCTOR_GGX ||
+                                  m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.albedo_tex].pad) {
+            DTex t = S->tex[m.albedo_tex];
+            Taps tp = tex_taps(t, vc.tu, vc.tv);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) atomic_add_agg(G->tex, tp.idx[k] + min(c, t.ch - 1), g_alb[c] * tp.w[k]);
+        }
+    }
+    // advance the adjoint row through the value of W_i
+    Compact<float> Wv = compact_value(W);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) compact_row(Wv, c, a[c]);
+}
+
 // Pass 0 caches E_v and the compact W_v of every vertex after which the path goes on
 // (the last vertex has L[n] = E_n, so its W is never needed and its E stays in
 // registers); the backward fold overwrites E_v with the suffix L[v] where the replay
@@ -842,7 +928,6 @@ struct PathVis {
     }
 
     __device__ void replay_vertex(const VCtx& vc) {
-        const DMat m = S->mats[vc.mat];
         float E[3][4];
         Compact<D3> W, f;
         eval_vertex<D3>(*S, *P, vc, E, W, &f);
@@ -854,80 +939,7 @@ struct PathVis {
 #pragma unroll
             for (int k = 0; k < 12; ++k) Ln[k >> 2][k & 3] = 0.0f;
         }
-        // local vector-Jacobian products: J_c = a_c^T (E_c + W_c L_c) with dual numbers
-        float g_slot0 = 0.0f, g_eta = 0.0f, g_alb[3];
-        Compact<float> fv;
-        if (vc.nee) fv = compact_value(f);
-        Rot<float> Rle = {1.0f, 0.0f};
-        if (vc.nee) Rle = emitter_rot(load_light(*S, vc.nee_light), -vc.wl);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            D3 x[4] = {D3(Ln[c][0]), D3(Ln[c][1]), D3(Ln[c][2]), D3(Ln[c][3])};
-            D3 y[4];
-            compact_apply(W, c, x, y);
-            D3 J = y[0] * a[c][0] + y[1] * a[c][1] + y[2] * a[c][2] + y[3] * a[c][3];
-            if (vc.nee) {
-                const float* le = P->le + 12 * vc.nee_light + 4 * c;
-                float lv[4] = {__ldg(le), __ldg(le + 1), __ldg(le + 2), __ldg(le + 3)};
-                rot_apply(Rle, lv);
-                D3 xe[4] = {D3(lv[0] * vc.nee_w), D3(lv[1] * vc.nee_w), D3(lv[2] * vc.nee_w), D3(lv[3] * vc.nee_w)};
-                D3 ye[4];
-                compact_apply(f, c, xe, ye);
-                J = J + ye[0] * a[c][0] + ye[1] * a[c][1] + ye[2] * a[c][2] + ye[3] * a[c][3];
-            }
-            g_slot0 += J.d0;
-            g_eta += J.d1;
-            g_alb[c] = J.d2;
-        }
-        // emitter Stokes gradients (linear): w R^T a for a hit, nee_w R^T f^T a for NEE
-        if (vc.emit || vc.nee) {
-            const int base = S->num_ior + S->num_sheets;
-            Rot<float> Re = {1.0f, 0.0f};
-            if (vc.emit) Re = emitter_rot(load_light(*S, vc.light), vc.wo);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if (vc.emit) {
-                    float g[4] = {a[c][0], a[c][1], a[c][2], a[c][3]};
-                    rot_apply_row(Re, g);
-                    for (int k = 0; k < 4; ++k)
-                        if (g[k] != 0.0f) atomicAdd(sgrad + base + 12 * vc.light + 4 * c + k, g[k] * vc.w_emit);
-                }
-                if (vc.nee) {
-                    float g[4] = {a[c][0], a[c][1], a[c][2], a[c][3]};
-                    compact_row(fv, c, g);
-                    rot_apply_row(Rle, g);
-                    for (int k = 0; k < 4; ++k)
-                        if (g[k] != 0.0f) atomicAdd(sgrad + base + 12 * vc.nee_light + 4 * c + k, g[k] * vc.nee_w);
-                }
-            }
-        }
-        // parameter scatter
-        if (m.type == DPPT_MAT_SMOOTH_DIELECTRIC || m.type == DPPT_MAT_PLASTIC_GGX) {
-            if (g_eta != 0.0f) atomicAdd(sgrad + m.ior_index, g_eta);
-        }
-        if (m.type == DPPT_MAT_POLARIZER_SHEET || m.type == DPPT_MAT_RETARDER_SHEET) {
-            if (g_slot0 != 0.0f) atomicAdd(sgrad + S->num_ior + m.sheet_index, g_slot0);
-        }
-        if (G->tex) {
-            if ((m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.rough_tex].pad) {
-                Taps tp = tex_taps(S->tex[m.rough_tex], vc.tu, vc.tv);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) atomic_add_agg(G->tex, tp.idx[k], g_slot0 * tp.w[k]);
-            }
-            if (m.albedo_tex >= 0 && (m.type == DPPT_MAT_DIFFUSE || m.type == DPPT_MAT_CONDUCTOR_GGX ||
-                                      m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.albedo_tex].pad) {
-                DTex t = S->tex[m.albedo_tex];
-                Taps tp = tex_taps(t, vc.tu, vc.tv);
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) atomic_add_agg(G->tex, tp.idx[k] + min(c, t.ch - 1), g_alb[c] * tp.w[k]);
-            }
-        }
-        // advance the adjoint row through the value of W_i
-        Compact<float> Wv = compact_value(W);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) compact_row(Wv, c, a[c]);
+        replay_vjp(*S, *P, *G, sgrad, vc, W, f, Ln, a);
     }
 };
 

@@ -1,0 +1,6 @@
+// Kernels of the depth-128 cache bucket (paths of at most 128 vertices).
+#include "trace.cuh"
+
+namespace dppt {
+DPPT_TRACE_BUCKET(128)
+}  // namespace dppt

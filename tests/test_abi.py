@@ -44,8 +44,8 @@ def test_struct_layouts_match_header():
 #include <stdio.h>
 #include "dppt.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(dppt_material), sizeof(dppt_scene_desc), sizeof(dppt_job),
-         sizeof(dppt_params), sizeof(dppt_grads), sizeof(dppt_launch));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dppt_material), sizeof(dppt_scene_desc), sizeof(dppt_job),
+         sizeof(dppt_params), sizeof(dppt_grads), sizeof(dppt_launch), sizeof(dppt_replay));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -54,7 +54,8 @@ int main(void) {
         open(c, "w").write(src)
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         sizes = [int(x) for x in subprocess.check_output([exe]).split()]
-    mine = [ctypes.sizeof(t) for t in (_lib.Material, _lib.SceneDesc, _lib.Job, _lib.Params, _lib.Grads, _lib.Launch)]
+    mine = [ctypes.sizeof(t) for t in (_lib.Material, _lib.SceneDesc, _lib.Job, _lib.Params, _lib.Grads, _lib.Launch,
+                                      _lib.Replay)]
     assert sizes == mine
 
 

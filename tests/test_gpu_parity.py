@@ -34,6 +34,8 @@ def small_scenes():
     out["icosphere"] = (s, j)
     s, j = sg.rocks_scene(freq=4, num_rocks=3, tex_res=16, width=20, spp=4, depth=16)
     out["rocks"] = (s, j)
+    # 85 stacked polarizers in a closed room: paths of up to 128 vertices (largest cache bucket)
+    out["deep"] = sg.deep_stack_scene(num_sheets=85, width=12, height=8, spp=2, depth=128, freq=6, tex_res=16)
     return out
 
 
@@ -131,7 +133,7 @@ def test_furnace_on_gpu(env):
     api, dctx, _ = env
     scene, job = sg.furnace_scene(0.6, 1.5)
     gs = api.GpuScene(dctx, scene)
-    for depth in (1, 3, 7):
+    for depth in (1, 3, 7, 100, 128):
         job.max_depth = depth
         (img,), _, _ = gpu_image(api, dctx, gs, [job])
         assert np.allclose(img[..., 0], 1.5 * sum(0.6**k for k in range(depth)), rtol=2e-6)
@@ -223,7 +225,7 @@ def test_empty_and_invalid(env):
     batch = api.pack_jobs([])
     P = api.device_params(scene, api.pack_jobs([job]))
     api.render_primal(dctx, gs, batch, P, image=torch.zeros(1, device="cuda"))   # no jobs: no-op
-    for field, value in [("camera", 5), ("max_depth", 0), ("max_depth", 65), ("spp", 0), ("filter", 9)]:
+    for field, value in [("camera", 5), ("max_depth", 0), ("max_depth", 129), ("spp", 0), ("filter", 9)]:
         bad = api.pack_jobs([job])
         setattr(bad.c_jobs[0], field, value)
         with pytest.raises(_lib.DpptError):
