@@ -501,14 +501,15 @@ def large_scene(num_meshes: int = 10, freq: int = 50, tex_res: int = 1024, width
 
 
 def deep_stack_scene(num_sheets: int = 85, width: int = 1280, height: int = 720, spp: int = 1,
-                     depth: int = 128, freq: int = 20, tex_res: int = 256) -> tuple[Scene, Job]:
+                     depth: int = 128, freq: int = 20, tex_res: int = 256, mesh: bool = True) -> tuple[Scene, Job]:
     """Deep-path workload: a closed diffuse room (every wall albedo 0.8, the floor a
     differentiable tex_res^2x3 map ~ U[0.6,0.9], seed 9) lit by a ceiling quad light of
     radiance 10, holding a rough-conductor displaced sphere (20*freq^2 triangles, eta =
     0.2+3.0i, roughness 0.2) and, between it and the camera, a stack of num_sheets linear
     polarizers (0.6 x 0.6, spacing 0.004) whose axes twist from 0 to 90 deg.  The room is
     closed, so every path runs to max_depth; a path through the stack spends num_sheets
-    vertices in it.  Camera polarizer at 0 deg; 1280x720, 1 spp."""
+    vertices in it.  Camera polarizer at 0 deg; 1280x720, 1 spp.  mesh=False leaves out the
+    conductor (flat surfaces only: long paths then stay identical between FP32 and FP64)."""
     s = Scene()
     floor_alb = np.random.default_rng(9).uniform(0.6, 0.9, (tex_res, tex_res, 3))
     tf = s.add_texture(floor_alb, differentiable=True)
@@ -524,9 +525,11 @@ def deep_stack_scene(num_sheets: int = 85, width: int = 1280, height: int = 720,
     s.add_quad((1, -1, -1), (0, 0, 2), (0, 2, 0), wall)     # right, normal -x
     s.add_quad((-1, -1, 1), (0, 2, 0), (2, 0, 0), wall)     # front, normal -z
     s.add_light((-0.3, 0.999, -0.3), (0.6, 0, 0), (0, 0, 0.6), 10.0)
-    cond = s.add_material(Material(MAT_CONDUCTOR_GGX, albedo_tex=talb, rough_tex=troughness, eta_re=0.2, eta_im=3.0))
-    v, f, uv = displaced_sphere(freq, 0.05, seed=1, radius=0.35, center=(0.0, -0.5, -0.4))
-    s.add_mesh(v, f, cond, uv)
+    if mesh:
+        cond = s.add_material(Material(MAT_CONDUCTOR_GGX, albedo_tex=talb, rough_tex=troughness, eta_re=0.2,
+                                       eta_im=3.0))
+        v, f, uv = displaced_sphere(freq, 0.05, seed=1, radius=0.35, center=(0.0, -0.5, -0.4))
+        s.add_mesh(v, f, cond, uv)
     for k in range(num_sheets):
         s.sheet.append(0.5 * math.pi * k / max(1, num_sheets - 1))
         m = s.add_material(Material(MAT_POLARIZER_SHEET, sheet_index=k, t1=(1, 0, 0), t2=(0, 1, 0)))

@@ -47,3 +47,20 @@ def flat(view: np.ndarray) -> np.ndarray:
 def grad_rel(g: np.ndarray, o: np.ndarray) -> float:
     n = np.linalg.norm(o)
     return float(np.linalg.norm(g - o) / n) if n > 0 else float(np.linalg.norm(g))
+
+
+def identical_path_pixels(api, dctx, gs, job, oracle_scene, params_np):
+    """Signatures of the job's paths (its own pass id) on both sides: returns the fraction
+    of identical paths and a per-pixel mask of the pixels whose paths are all identical.
+    A path whose FP32 and FP64 walks part (a grazing ray on a neighbouring triangle after
+    many bounces) is a different sample, not a wrong one: comparisons use the mask."""
+    import torch
+    sig = torch.zeros(job.num_paths, dtype=torch.int32, device="cuda")
+    batch = api.pack_jobs([job], path_sig=sig)
+    P = api.device_params(gs.scene, batch, params_np)
+    api.render_primal(dctx, gs, batch, P)
+    dctx.sync_status()
+    sg = sig.cpu().numpy().view(np.uint32)
+    _, _, so = oracle_scene.render(job, params_np if params_np is not None else gs.scene.params(), paths=True)
+    same = sg == so
+    return float(same.mean()), same.reshape(-1, job.spp).all(1)

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from paper_2607_13265_gb300 import scenegen as sg
-from parity import GRAD_TOL, grad_rel
+from parity import GRAD_TOL, grad_rel, identical_path_pixels
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +31,7 @@ def env(oracle_mod):
 
 
 def _scenes():
-    out = {"deep": sg.deep_stack_scene(num_sheets=85, width=12, height=8, spp=2, depth=128, freq=6, tex_res=16),
+    out = {"deep": sg.deep_stack_scene(num_sheets=85, width=12, height=8, spp=2, depth=128, tex_res=16, mesh=False),
            "mixed": sg.mixed_scene(width=16, spp=4, depth=6)}
     s, j = sg.rocks_scene(freq=4, num_rocks=3, tex_res=16, width=16, spp=4, depth=16)
     out["rocks"] = (s, j)
@@ -40,6 +40,14 @@ def _scenes():
 
 SCENES = _scenes()
 CONFIGS = [(4, 0.0, INF), (8, 0.0, 1e-3), (16, 0.0, INF)]
+
+
+def _adjoint_input(api, dctx, scene, job, O, seed):
+    """Seeded dI restricted to pixels whose adjoint paths are identical on both sides."""
+    gs = api.GpuScene(dctx, scene)
+    frac, keep = identical_path_pixels(api, dctx, gs, job, O.OracleScene(scene), None)
+    assert frac >= 0.97, frac
+    return np.random.default_rng(seed).normal(size=(job.num_angles, job.num_pixels, 3, 4)) * keep[None, :, None, None]
 
 
 def _gpu_grad(api, dctx, scene, job, dI, sched, k, gamma, eps):
@@ -87,7 +95,7 @@ def test_hybrid_matches_oracle(env, name, cfg, sched):
     scene, job = SCENES[name]
     job.pass_id = 1
     try:
-        dI = np.random.default_rng(7).normal(size=(job.num_angles, job.num_pixels, 3, 4))
+        dI = _adjoint_input(api, dctx, scene, job, O, 7)
         got = _gpu_grad(api, dctx, scene, job, dI, sched, *cfg)
         ref, routes = O.OracleScene(scene).gradient_hybrid(job, scene.params(), dI, *cfg)
     finally:
@@ -102,7 +110,7 @@ def test_hybrid_exact_routes_equal_cached_replay(env):
     scene, job = SCENES["deep"]
     job.pass_id = 1
     try:
-        dI = np.random.default_rng(3).normal(size=(job.num_angles, job.num_pixels, 3, 4))
+        dI = _adjoint_input(api, dctx, scene, job, O, 3)
         got = _gpu_grad(api, dctx, scene, job, dI, 0, 8, 0.0, INF)
         ref = O.OracleScene(scene).gradient(job, scene.params(), dI, mode="replay")
     finally:
