@@ -100,61 +100,98 @@ constexpr int kTravDone = 0x7fffffff;   // stack sentinel: traversal finished
 
 __device__ __forceinline__ int trav_pop(const int* stack, int& sp) { return sp > 0 ? stack[--sp] : kTravDone; }
 
+// Traversal state of one ray, kept in registers between rounds (the stack is the
+// caller's thread-local array).  t: best hit so far (closest) or the ray's tmax (any);
+// prim: closest primitive id so far, or 1 once an any-hit query has found a blocker.
+struct Trav {
+    f3 o, d, inv, oi;
+    float t, b1, b2;
+    int prim, slot, sp, ref;
+};
+
+__device__ __forceinline__ void trav_begin(Trav& r, f3 o, f3 d, float t) {
+    r.o = o; r.d = d;
+    r.inv = safe_inv(d);
+    r.oi = {o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z};
+    r.t = t; r.b1 = r.b2 = 0.0f;
+    r.prim = -1; r.slot = -1; r.sp = 0; r.ref = 0;
+}
+
+// One round of the while-while loop with postponed leaves: inner nodes until this lane
+// (and, while it waits, every lane of the warp in the round) has a leaf, then the leaves,
+// including further leaves met on the stack.  ANY: stop at the first hit in (0, t).
+// Returns true when the ray's traversal is complete.
+template <bool ANY, bool COUNT>
+__device__ __forceinline__ bool trav_round(const DScene& S, Trav& r, int* stack, unsigned* status, WorkCount* wc) {
+    int leaf = kTravDone;
+    while (r.ref >= 0 && r.ref != kTravDone) {
+        const float4* nd = S.nodes + 4 * r.ref;
+        float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+        float tl, tr; bool hl, hr;
+        if (COUNT) { if (ANY) wc->shadow_nodes++; else wc->nodes++; }
+        child_slabs(n0, n1, n2, r.inv, r.oi, r.t, tl, tr, hl, hr);
+        int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+        if (hl && hr) {
+            int nr = cl, fr = cr;
+            if (!ANY && tr < tl) { nr = cr; fr = cl; }
+            if (r.sp >= kBvhStack) { atomicOr(status, kStatusStackOverflow); r.ref = kTravDone; return true; }
+            stack[r.sp++] = fr;
+            r.ref = nr;
+        } else if (hl) r.ref = cl;
+        else if (hr) r.ref = cr;
+        else r.ref = trav_pop(stack, r.sp);
+        if (r.ref < 0 && leaf == kTravDone) { leaf = r.ref; r.ref = trav_pop(stack, r.sp); }
+        if (!__any_sync(__activemask(), leaf == kTravDone)) break;
+    }
+    while (leaf != kTravDone) {
+        unsigned v = ~(unsigned)leaf;
+        int first = (int)(v & 0x1FFFFFFu), cnt = (int)(v >> 25);
+        if (COUNT) { if (ANY) wc->shadow_tri_tests += cnt; else wc->tri_tests += cnt; }
+        for (int i = first; i < first + cnt; ++i) {
+            float b1, b2;
+            float t = tri_test(S.tris, i, r.o, r.d, b1, b2);
+            if (ANY) {
+                if (t > 0.0f && t < r.t) { r.prim = 1; r.ref = kTravDone; return true; }
+            } else if (t > 0.0f && t <= r.t) {
+                int id = __float_as_int(__ldg(&S.tris[3 * i].w));
+                if (t < r.t || id < r.prim) { r.t = t; r.prim = id; r.slot = i; r.b1 = b1; r.b2 = b2; }
+            }
+        }
+        leaf = kTravDone;
+        if (r.ref < 0) { leaf = r.ref; r.ref = trav_pop(stack, r.sp); }
+    }
+    return r.ref == kTravDone;
+}
+
+// spheres after the triangles: ties in t go to the lower primitive id (triangles first)
+__device__ __forceinline__ void trav_spheres_closest(const DScene& S, Trav& r) {
+    for (int k = 0; k < S.num_spheres; ++k) {
+        float t = sphere_test(__ldg(S.spheres + k), r.o, r.d, FLT_MAX);
+        int id = S.num_tris + k;
+        if (t > 0.0f && (t < r.t || (t == r.t && id < r.prim))) { r.t = t; r.prim = id; r.slot = -1; }
+    }
+}
+__device__ __forceinline__ bool trav_spheres_any(const DScene& S, f3 o, f3 d, float tmax) {
+    for (int k = 0; k < S.num_spheres; ++k) {
+        float t = sphere_test(__ldg(S.spheres + k), o, d, tmax);
+        if (t > 0.0f && t < tmax) return true;
+    }
+    return false;
+}
+
 // closest hit; ties in t go to the lower primitive id (triangles before spheres)
 template <bool COUNT>
 __device__ bool trace_closest(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* status, WorkCount* wc) {
     if (COUNT) { wc->rays++; wc->sph_tests += S.num_spheres; }
-    h.t = FLT_MAX; h.prim = -1; h.slot = -1; h.b1 = h.b2 = 0.0f;
+    Trav r;
+    trav_begin(r, o, d, FLT_MAX);
     if (S.num_tris > 0) {
-        f3 inv = safe_inv(d);
-        f3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
         int stack[kBvhStack];
-        int sp = 0, ref = 0;
-        while (ref != kTravDone) {
-            int leaf = kTravDone;
-            // inner nodes until this lane (and, while it waits, its warp) has a leaf
-            while (ref >= 0 && ref != kTravDone) {
-                const float4* nd = S.nodes + 4 * ref;
-                float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
-                float tl, tr; bool hl, hr;
-                if (COUNT) wc->nodes++;
-                child_slabs(n0, n1, n2, inv, oi, h.t, tl, tr, hl, hr);
-                int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
-                if (hl && hr) {
-                    int nr = cl, fr = cr;
-                    if (tr < tl) { nr = cr; fr = cl; }
-                    if (sp >= kBvhStack) { atomicOr(status, kStatusStackOverflow); ref = kTravDone; break; }
-                    stack[sp++] = fr;
-                    ref = nr;
-                } else if (hl) ref = cl;
-                else if (hr) ref = cr;
-                else ref = trav_pop(stack, sp);
-                if (ref < 0 && leaf == kTravDone) { leaf = ref; ref = trav_pop(stack, sp); }
-                if (!__any_sync(__activemask(), leaf == kTravDone)) break;
-            }
-            // leaves, including further leaves met on the stack
-            while (leaf != kTravDone) {
-                unsigned v = ~(unsigned)leaf;
-                int first = (int)(v & 0x1FFFFFFu), cnt = (int)(v >> 25);
-                if (COUNT) wc->tri_tests += cnt;
-                for (int i = first; i < first + cnt; ++i) {
-                    float b1, b2;
-                    float t = tri_test(S.tris, i, o, d, b1, b2);
-                    if (t > 0.0f && t <= h.t) {
-                        int id = __float_as_int(__ldg(&S.tris[3 * i].w));
-                        if (t < h.t || id < h.prim) { h.t = t; h.prim = id; h.slot = i; h.b1 = b1; h.b2 = b2; }
-                    }
-                }
-                leaf = kTravDone;
-                if (ref < 0) { leaf = ref; ref = trav_pop(stack, sp); }
-            }
+        while (!trav_round<false, COUNT>(S, r, stack, status, wc)) {
         }
     }
-    for (int k = 0; k < S.num_spheres; ++k) {
-        float t = sphere_test(__ldg(S.spheres + k), o, d, FLT_MAX);
-        int id = S.num_tris + k;
-        if (t > 0.0f && (t < h.t || (t == h.t && id < h.prim))) { h.t = t; h.prim = id; }
-    }
+    trav_spheres_closest(S, r);
+    h.t = r.t; h.prim = r.prim; h.slot = r.slot; h.b1 = r.b1; h.b2 = r.b2;
     return h.prim >= 0;
 }
 
@@ -162,49 +199,14 @@ __device__ bool trace_closest(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* 
 template <bool COUNT>
 __device__ bool trace_any(const DScene& S, f3 o, f3 d, float tmax, unsigned* status, WorkCount* wc) {
     if (COUNT) { wc->shadow_rays++; wc->shadow_sph_tests += S.num_spheres; }
-    for (int k = 0; k < S.num_spheres; ++k) {
-        float t = sphere_test(__ldg(S.spheres + k), o, d, tmax);
-        if (t > 0.0f && t < tmax) return true;
+    if (trav_spheres_any(S, o, d, tmax)) return true;
+    if (S.num_tris == 0) return false;
+    Trav r;
+    trav_begin(r, o, d, tmax);
+    int stack[kBvhStack];
+    while (!trav_round<true, COUNT>(S, r, stack, status, wc)) {
     }
-    if (S.num_tris > 0) {
-        f3 inv = safe_inv(d);
-        f3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
-        int stack[kBvhStack];
-        int sp = 0, ref = 0;
-        while (ref != kTravDone) {
-            int leaf = kTravDone;
-            while (ref >= 0 && ref != kTravDone) {
-                const float4* nd = S.nodes + 4 * ref;
-                float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
-                float tl, tr; bool hl, hr;
-                if (COUNT) wc->shadow_nodes++;
-                child_slabs(n0, n1, n2, inv, oi, tmax, tl, tr, hl, hr);
-                int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
-                if (hl && hr) {
-                    if (sp >= kBvhStack) { atomicOr(status, kStatusStackOverflow); return false; }
-                    stack[sp++] = cr;
-                    ref = cl;
-                } else if (hl) ref = cl;
-                else if (hr) ref = cr;
-                else ref = trav_pop(stack, sp);
-                if (ref < 0 && leaf == kTravDone) { leaf = ref; ref = trav_pop(stack, sp); }
-                if (!__any_sync(__activemask(), leaf == kTravDone)) break;
-            }
-            while (leaf != kTravDone) {
-                unsigned v = ~(unsigned)leaf;
-                int first = (int)(v & 0x1FFFFFFu), cnt = (int)(v >> 25);
-                if (COUNT) wc->shadow_tri_tests += cnt;
-                for (int i = first; i < first + cnt; ++i) {
-                    float b1, b2;
-                    float t = tri_test(S.tris, i, o, d, b1, b2);
-                    if (t > 0.0f && t < tmax) return true;
-                }
-                leaf = kTravDone;
-                if (ref < 0) { leaf = ref; ref = trav_pop(stack, sp); }
-            }
-        }
-    }
-    return false;
+    return r.prim >= 0;
 }
 
 // ================================================================== textures

@@ -135,6 +135,7 @@ __global__ void k_wf_init(const DScene S, const __grid_constant__ JobTable T, in
     }
 }
 
+// Closest hits of the live paths, one ray per thread in a grid-stride loop.
 __global__ void k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
     const int n0 = L.count[0], n = n0 + L.count[1];
     const int stride = gridDim.x * blockDim.x;

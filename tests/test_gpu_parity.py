@@ -39,8 +39,11 @@ def small_scenes():
     return out
 
 
-# fraction of paths that must be identical between FP32 and FP64 (longer paths part more often)
-MIN_IDENTICAL = {"deep": 0.97}
+# fraction of paths that must be identical between FP32 and FP64.  Position errors grow
+# along a path (a bounce at incidence cosine c scales the error parallel to the wall by
+# ~1/c), so long paths in a closed room part more often: about 6% of the 128-vertex paths
+# of the deep scene (and 22% in the same room without the stack) versus < 1% at depth 16.
+MIN_IDENTICAL = {"deep": 0.85}
 
 
 SCENES = small_scenes()
