@@ -41,6 +41,19 @@ struct WorkCount {
     unsigned vertices, rays, shadow_rays, nodes, shadow_nodes, tri_tests, shadow_tri_tests, sph_tests, shadow_sph_tests;
 };
 
+// three-operand minimum / maximum (PTX min.f32 / max.f32 with three sources, sm_100+);
+// like fminf / fmaxf they return the other operands when one is NaN
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 __device__ __forceinline__ void child_slabs(float4 n0, float4 n1, float4 n2, f3 inv, f3 oi, float tmax,
                                             float& tl, float& tr, bool& hl, bool& hr) {
     float lx0 = fmaf(n0.x, inv.x, -oi.x), lx1 = fmaf(n0.y, inv.x, -oi.x);
@@ -49,10 +62,10 @@ __device__ __forceinline__ void child_slabs(float4 n0, float4 n1, float4 n2, f3 
     float rx0 = fmaf(n1.x, inv.x, -oi.x), rx1 = fmaf(n1.y, inv.x, -oi.x);
     float ry0 = fmaf(n1.z, inv.y, -oi.y), ry1 = fmaf(n1.w, inv.y, -oi.y);
     float rz0 = fmaf(n2.z, inv.z, -oi.z), rz1 = fmaf(n2.w, inv.z, -oi.z);
-    float ln = fmaxf(fmaxf(fminf(lx0, lx1), fminf(ly0, ly1)), fmaxf(fminf(lz0, lz1), 0.0f));
-    float lf = fminf(fminf(fmaxf(lx0, lx1), fmaxf(ly0, ly1)), fminf(fmaxf(lz0, lz1), tmax));
-    float rn = fmaxf(fmaxf(fminf(rx0, rx1), fminf(ry0, ry1)), fmaxf(fminf(rz0, rz1), 0.0f));
-    float rf = fminf(fminf(fmaxf(rx0, rx1), fmaxf(ry0, ry1)), fminf(fmaxf(rz0, rz1), tmax));
+    float ln = fmax3(fminf(lx0, lx1), fminf(ly0, ly1), fmaxf(fminf(lz0, lz1), 0.0f));
+    float lf = fmin3(fmaxf(lx0, lx1), fmaxf(ly0, ly1), fminf(fmaxf(lz0, lz1), tmax));
+    float rn = fmax3(fminf(rx0, rx1), fminf(ry0, ry1), fmaxf(fminf(rz0, rz1), 0.0f));
+    float rf = fmin3(fmaxf(rx0, rx1), fmaxf(ry0, ry1), fminf(fmaxf(rz0, rz1), tmax));
     hl = ln <= lf; hr = rn <= rf; tl = ln; tr = rn;
 }
 

@@ -15,6 +15,11 @@
 // loops over it with a grid stride, so a wave is a fixed sequence of launches.
 #include "trace.cuh"
 
+// resident threads per SM the traversal kernels' register allocation must allow (as blocks
+// of the largest wavefront block size, 512)
+#ifndef DPPT_WF_TRAVERSE_MIN_BLOCKS
+#define DPPT_WF_TRAVERSE_MIN_BLOCKS 2
+#endif
 // resident 128-thread blocks per SM the finish kernels' register allocation must allow
 // (4 -> at most 128 registers per thread, 3 -> at most 168)
 #ifndef DPPT_WF_CACHE_MIN_BLOCKS
@@ -136,7 +141,8 @@ __global__ void k_wf_init(const DScene S, const __grid_constant__ JobTable T, in
 }
 
 // Closest hits of the live paths, one ray per thread in a grid-stride loop.
-__global__ void k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
+__global__ void __launch_bounds__(512, DPPT_WF_TRAVERSE_MIN_BLOCKS)
+k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
     const int n0 = L.count[0], n = n0 + L.count[1];
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
@@ -186,7 +192,8 @@ __global__ void k_wf_shade(const DScene S, const DParams P, const __grid_constan
     }
 }
 
-__global__ void k_wf_shadow(const DScene S, WfState W, WfLists L, unsigned* status) {
+__global__ void __launch_bounds__(512, DPPT_WF_TRAVERSE_MIN_BLOCKS)
+k_wf_shadow(const DScene S, WfState W, WfLists L, unsigned* status) {
     const int n = L.count[4];
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
