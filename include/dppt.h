@@ -194,6 +194,27 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* scene, const dp
                                 const dppt_params* params, const float* d_image, const dppt_grads* grads,
                                 void* stream);
 
+/* Fused mean-squared-error loss on the camera-filtered images: a
+ * differentiable image loss g(I(pi)) of the problem statement (Sec. 3.1),
+ * here g = scale * sum_jobs sum_a sum_pix |C(theta_a) raw_pix - T_a,pix|^2, folded
+ * into the camera filter so that no per-angle image is ever stored (no
+ * counterpart call in the paper).  raw is the unfiltered image of the jobs'
+ * primal paths, [H][W][3][4] float32 per job at raw_offsets[i] floats (host
+ * array, multiples of 4) -- render_primal of the same jobs with filter NONE
+ * writes it; target is in the image layout of the jobs (job.out_offset).
+ * dppt_loss_l2 overwrites *loss (device double).  dppt_render_adjoint_l2 is
+ * render_adjoint with dg/dI = 2 scale (C_a raw - T_a) formed per pixel:
+ * gradients are ADDED into grads; workspace: 12 floats per pixel for the
+ * adjoint input and, for filtered jobs, 12 more for the adjoint paths' raw
+ * image.  Errors: INVALID_ARG for null buffers or bad offsets, as
+ * render_primal / render_adjoint otherwise. */
+dppt_status dppt_loss_l2(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* jobs, int32_t njobs,
+                         const dppt_params* params, const float* raw, const int64_t* raw_offsets,
+                         const float* target, double scale, double* loss, void* stream);
+dppt_status dppt_render_adjoint_l2(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* jobs, int32_t njobs,
+                                   const dppt_params* params, const float* raw, const int64_t* raw_offsets,
+                                   const float* target, float scale, const dppt_grads* grads, void* stream);
+
 /* Device workspace (bytes) the jobs need beyond the caller's buffers with the
  * context's current launch shapes: filter buffers, plus the wavefront path
  * state and per-vertex cache when a wavefront schedule is selected.  The

@@ -72,6 +72,10 @@ SIGNATURES = {
     "dppt_render_primal": (c_i32, [c_vp, c_vp, ctypes.POINTER(Job), c_i32, ctypes.POINTER(Params), c_vp, c_vp]),
     "dppt_render_adjoint": (c_i32, [c_vp, c_vp, ctypes.POINTER(Job), c_i32, ctypes.POINTER(Params), c_vp,
                                     ctypes.POINTER(Grads), c_vp]),
+    "dppt_loss_l2": (c_i32, [c_vp, c_vp, ctypes.POINTER(Job), c_i32, ctypes.POINTER(Params), c_vp,
+                             ctypes.POINTER(c_i64), c_vp, ctypes.c_double, c_vp, c_vp]),
+    "dppt_render_adjoint_l2": (c_i32, [c_vp, c_vp, ctypes.POINTER(Job), c_i32, ctypes.POINTER(Params), c_vp,
+                                       ctypes.POINTER(c_i64), c_vp, c_f32, ctypes.POINTER(Grads), c_vp]),
     "dppt_query_workspace": (c_i32, [c_vp, ctypes.POINTER(Job), c_i32, ctypes.POINTER(ctypes.c_size_t)]),
     "dppt_set_launch": (c_i32, [c_vp, ctypes.POINTER(Launch)]),
     "dppt_get_launch": (c_i32, [c_vp, ctypes.POINTER(Launch)]),

@@ -278,6 +278,48 @@ def render_adjoint(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict, d_
     return grads
 
 
+def raw_batch(batch: JobBatch) -> JobBatch:
+    """The batch's jobs without their camera filter: render_primal of this batch writes each
+    job's raw (unfiltered) image [H][W][3][4], back to back; the paths are the same."""
+    import copy
+    jobs = []
+    for j in batch.jobs:
+        k = copy.copy(j)
+        k.filter, k.thetas = FILTER_NONE, []
+        jobs.append(k)
+    return pack_jobs(jobs)
+
+
+def loss_l2(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict, raw: torch.Tensor, raw_offsets,
+            target: torch.Tensor, scale: float, loss: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """scale * sum |C(theta_a) raw - T_a|^2 over the batch's jobs, angles and pixels (device double)."""
+    if loss is None:
+        loss = torch.empty((), dtype=torch.float64, device=raw.device)
+    cp = _c_params(params)
+    offs = np.ascontiguousarray(raw_offsets, np.int64)
+    _check(ctx.h, ctx.lib.dppt_loss_l2(ctx.h, gs.h, batch.c_jobs, batch.n, ctypes.byref(cp), _ptr(raw),
+                                       offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(target),
+                                       float(scale), _ptr(loss), _stream_ptr(stream)), "dppt_loss_l2")
+    return loss
+
+
+def render_adjoint_l2(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict, raw: torch.Tensor, raw_offsets,
+                      target: torch.Tensor, scale: float, grads: dict | None = None, stream=None) -> dict:
+    """render_adjoint with the adjoint input of the fused L2 loss formed per pixel: ADDS
+    the gradient of scale * sum |C_a raw - T_a|^2 into `grads` and returns it."""
+    if grads is None:
+        grads = zero_grads(params)
+    cp = _c_params(params)
+    cg = L.Grads(_ptr(grads.get("tex")), _ptr(grads.get("ior")), _ptr(grads.get("le")), _ptr(grads.get("sheet")),
+                 _ptr(grads.get("theta")))
+    offs = np.ascontiguousarray(raw_offsets, np.int64)
+    _check(ctx.h, ctx.lib.dppt_render_adjoint_l2(ctx.h, gs.h, batch.c_jobs, batch.n, ctypes.byref(cp), _ptr(raw),
+                                                 offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(target),
+                                                 float(scale), ctypes.byref(cg), _stream_ptr(stream)),
+           "dppt_render_adjoint_l2")
+    return grads
+
+
 def image_views(batch: JobBatch, image: torch.Tensor) -> list:
     """Per-job views [angles][H][W][3][4] of a packed image buffer."""
     out = []
@@ -310,6 +352,37 @@ class PolarizedRender(torch.autograd.Function):
                   "theta": theta.detach()}
         grads = render_adjoint(fctx.dctx, fctx.gs, fctx.adj_batch, params, d_image.contiguous())
         return (None, None, None, None, grads["tex"], grads["ior"], grads["le"], grads["sheet"], grads["theta"])
+
+
+class PolarizedL2(torch.autograd.Function):
+    """mean((I(pi) - T)^2) over all jobs and angles, fused into the camera filter: the
+    forward keeps only the raw image (12 floats per pixel, whatever the number of angles)
+    and the backward forms the adjoint input per pixel (dppt_render_adjoint_l2).
+
+    forward(ctx_obj, gscene, batch, adjoint_batch, target, tex, ior, le, sheet, theta) -> loss."""
+
+    @staticmethod
+    def forward(fctx, dctx, gs, batch, adj_batch, target, tex, ior, le, sheet, theta):
+        params = {"tex": tex.detach(), "ior": ior.detach(), "le": le.detach(), "sheet": sheet.detach(),
+                  "theta": theta.detach()}
+        rb = raw_batch(batch)
+        raw = render_primal(dctx, gs, rb, params)
+        n = target.numel()
+        loss = loss_l2(dctx, gs, batch, params, raw, rb.offsets, target, 1.0 / n)
+        fctx.dctx, fctx.gs, fctx.adj_batch, fctx.raw_offsets, fctx.n = dctx, gs, adj_batch, rb.offsets, n
+        fctx.save_for_backward(tex, ior, le, sheet, theta, raw, target)
+        return loss.to(torch.float32)
+
+    @staticmethod
+    def backward(fctx, g):
+        tex, ior, le, sheet, theta, raw, target = fctx.saved_tensors
+        params = {"tex": tex.detach(), "ior": ior.detach(), "le": le.detach(), "sheet": sheet.detach(),
+                  "theta": theta.detach()}
+        grads = render_adjoint_l2(fctx.dctx, fctx.gs, fctx.adj_batch, params, raw, fctx.raw_offsets, target,
+                                  1.0 / fctx.n)
+        for v in grads.values():
+            v.mul_(g)
+        return (None, None, None, None, None, grads["tex"], grads["ior"], grads["le"], grads["sheet"], grads["theta"])
 
 
 class ImageL2(torch.autograd.Function):

@@ -10,8 +10,12 @@ in [0, 180) deg; 16 spp, depth 8; L2 loss to a seeded target (perturbed albedo).
 * plain: one call per (view, angle), i.e. 512 render_primal + 512 render_adjoint calls,
   each tracing the view's paths again.
 
-Both run through the autograd Function for the memory comparison (peak device memory of
-forward + backward, plus the library's workspace).  Prints one JSON line.
+* batched, fused L2: the same batch with the loss folded into the camera filter
+  (PolarizedL2 / dppt_loss_l2 + dppt_render_adjoint_l2): only the raw image (12 floats per
+  pixel) is kept instead of one image per angle, captured in a CUDA graph as well.
+
+All forms run through their autograd Functions for the memory comparison (peak device
+memory of forward + backward, plus the library's workspace).  Prints one JSON line.
 
   python -m paper_2607_13265_gb300.batch_bench [--replays 50] [--angles 64] [--views 8]
 """
@@ -104,6 +108,39 @@ def main(argv=None):
     graph_vs_eager = max(float((grads[k] - grads_eager[k]).abs().max() / (grads_eager[k].abs().max() + 1e-30))
                          for k in ("tex", "theta"))
 
+    # the same step with the L2 loss fused into the camera filter (12 floats per pixel kept)
+    rb = api.raw_batch(batch)
+    raw_buf = torch.empty(rb.image_floats, dtype=torch.float32, device="cuda")
+    loss_buf = torch.empty((), dtype=torch.float64, device="cuda")
+    grads_f = api.zero_grads(P)
+
+    def step_fused():
+        api.render_primal(dctx, gs, rb, P, image=raw_buf, stream=stream)
+        api.loss_l2(dctx, gs, batch, P, raw_buf, rb.offsets, target, 1.0 / N, loss=loss_buf, stream=stream)
+        for g in grads_f.values():
+            g.zero_()
+        api.render_adjoint_l2(dctx, gs, adj, P, raw_buf, rb.offsets, target, 1.0 / N, grads_f, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            step_fused()
+    stream.synchronize()
+    fused_vs_image = max(float((grads_f[k] - grads_eager[k]).abs().max() / (grads_eager[k].abs().max() + 1e-30))
+                         for k in ("tex", "theta"))
+    graph_f = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_f, stream=stream):
+        step_fused()
+    lat_f = []
+    for _ in range(args.replays):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            graph_f.replay()
+            b.record(stream)
+        b.synchronize()
+        lat_f.append(a.elapsed_time(b))
+    dctx.sync_status(stream)
+
     traced = sum(2 * j.num_paths for j in jobs)                       # primal + adjoint paths traced
     effective = sum(2 * j.num_paths * j.num_angles for j in jobs)     # (view, angle) path samples produced
     p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
@@ -182,8 +219,14 @@ def main(argv=None):
             loss = loss + api.ImageL2.apply(img, t) * (img.numel() / N)
         loss.backward()
 
+    def fused_autograd():
+        loss = api.PolarizedL2.apply(dctx, gs, batch, adj, target, leaf["tex"], leaf["ior"], leaf["le"],
+                                     leaf["sheet"], leaf["theta"])
+        loss.backward()
+
     mem_batched = peak(batched_autograd)
     ws_batched = dctx.query_workspace(adj)
+    mem_fused = peak(fused_autograd)
     mem_plain = peak(plain_autograd)
     ws_plain = max(dctx.query_workspace(pa) for pa in plain_adj[:: max(1, args.angles)])
 
@@ -198,10 +241,18 @@ def main(argv=None):
                     "effective_paths_per_s": effective / (p50 / 1000.0),
                     "graph_vs_eager_grad_rel": graph_vs_eager,
                     "peak_autograd_bytes": int(mem_batched), "workspace_bytes": int(ws_batched)},
+        "batched_fused_l2": {"graph_p50_ms": float(np.percentile(lat_f, 50)),
+                             "graph_p99_ms": float(np.percentile(lat_f, 99)),
+                             "traced_paths_per_s": traced / (float(np.percentile(lat_f, 50)) / 1000.0),
+                             "effective_paths_per_s": effective / (float(np.percentile(lat_f, 50)) / 1000.0),
+                             "grad_rel_vs_image_form": fused_vs_image,
+                             "peak_autograd_bytes": int(mem_fused)},
         "plain": {"calls": 2 * len(plain_jobs), "ms": plain_ms, "traced_paths_per_s": plain_traced / (plain_ms / 1000.0),
                   "effective_paths_per_s": effective / (plain_ms / 1000.0),
                   "peak_autograd_bytes": int(mem_plain), "workspace_bytes": int(ws_plain)},
         "speedup_effective": plain_ms / p50,
+        "gradient_memory_vs_plain": {"batched_image_form": mem_batched / max(1, mem_plain),
+                                     "batched_fused_l2": mem_fused / max(1, mem_plain)},
         "per_view_gradients": per_view,
         "tuning": tuning,
     }

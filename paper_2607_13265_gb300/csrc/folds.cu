@@ -131,6 +131,136 @@ __global__ void k_theta_grad(const float* __restrict__ dimage, const float* __re
         if (sacc[a] != 0.0f) atomicAdd(dtheta + a, sacc[a]);
 }
 
+// ================================================================== fused L2 loss folds
+// The loss scale * sum_a sum_pix |C_a raw - T_a|^2 of a job and its derivatives, with the
+// residual C_a raw - T_a formed per pixel and never stored (raw [pix][12], target in the
+// image layout [a][pix][12]).  An unfiltered job (filter none) has one "angle" with C = I.
+__device__ __forceinline__ void load12(const float* p, float v[12]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    for (int k = 0; k < 3; ++k) { float4 t = __ldg(q + k); v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w; }
+}
+__device__ __forceinline__ void filter_or_identity(int filter, const float* theta, int a, float C[16], float dC[16]) {
+    if (filter == DPPT_FILTER_NONE) {
+        for (int k = 0; k < 16; ++k) { C[k] = (k % 5 == 0) ? 1.0f : 0.0f; dC[k] = 0.0f; }
+    } else {
+        filter_matrix(filter, __ldg(theta + a), C, dC);
+    }
+}
+// residual of channel c at angle a: d = C v - t
+__device__ __forceinline__ void residual4(const float* C, const float* v, const float* t, float d[4]) {
+    for (int i = 0; i < 4; ++i) d[i] = C[4 * i] * v[0] + C[4 * i + 1] * v[1] + C[4 * i + 2] * v[2] + C[4 * i + 3] * v[3] - t[i];
+}
+
+__global__ void k_l2_loss(const float* __restrict__ raw, const float* __restrict__ target, int npix, int filter,
+                          const float* __restrict__ theta, int nang, double scale, double* loss) {
+    extern __shared__ float sC[];
+    __shared__ double swarp[32];
+    for (int a = threadIdx.x; a < nang; a += blockDim.x) {
+        float C[16], dC[16];
+        filter_or_identity(filter, theta, a, C, dC);
+        for (int k = 0; k < 16; ++k) sC[16 * a + k] = C[k];
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix; pix += (long long)gridDim.x * blockDim.x) {
+        float r[12], t[12];
+        load12(raw + pix * 12, r);
+        float part = 0.0f;
+        for (int a = 0; a < nang; ++a) {
+            load12(target + ((long long)a * npix + pix) * 12, t);
+            for (int c = 0; c < 3; ++c) {
+                float d[4];
+                residual4(sC + 16 * a, r + 4 * c, t + 4 * c, d);
+                part += d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3];
+            }
+        }
+        acc += (double)part;
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) swarp[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += swarp[w];
+        if (b != 0.0) atomicAdd(loss, b * scale);
+    }
+}
+
+// dS = 2 scale sum_a C_a^T (C_a raw - T_a)
+__global__ void k_l2_adjoint_input(const float* __restrict__ raw, const float* __restrict__ target, float* __restrict__ dS,
+                                   int npix, int filter, const float* __restrict__ theta, int nang, float scale2) {
+    extern __shared__ float sC[];
+    for (int a = threadIdx.x; a < nang; a += blockDim.x) {
+        float C[16], dC[16];
+        filter_or_identity(filter, theta, a, C, dC);
+        for (int k = 0; k < 16; ++k) sC[16 * a + k] = C[k];
+    }
+    __syncthreads();
+    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix; pix += (long long)gridDim.x * blockDim.x) {
+        float r[12], t[12], acc[12];
+        load12(raw + pix * 12, r);
+        for (int k = 0; k < 12; ++k) acc[k] = 0.0f;
+        for (int a = 0; a < nang; ++a) {
+            const float* C = sC + 16 * a;
+            load12(target + ((long long)a * npix + pix) * 12, t);
+            for (int c = 0; c < 3; ++c) {
+                float d[4];
+                residual4(C, r + 4 * c, t + 4 * c, d);
+                for (int j = 0; j < 4; ++j)
+                    acc[4 * c + j] += C[j] * d[0] + C[4 + j] * d[1] + C[8 + j] * d[2] + C[12 + j] * d[3];
+            }
+        }
+        float4* o = reinterpret_cast<float4*>(dS + pix * 12);
+        for (int q = 0; q < 3; ++q)
+            o[q] = make_float4(scale2 * acc[4 * q], scale2 * acc[4 * q + 1], scale2 * acc[4 * q + 2], scale2 * acc[4 * q + 3]);
+    }
+}
+
+// dtheta_a += 2 scale sum_pix (C_a raw - T_a)^T dC_a S_adj
+__global__ void k_l2_theta_grad(const float* __restrict__ raw, const float* __restrict__ target,
+                                const float* __restrict__ S_adj, int npix, int filter, const float* __restrict__ theta,
+                                int nang, float scale2, float* __restrict__ dtheta) {
+    extern __shared__ float sm[];
+    float* sC = sm;                 // [nang][16]
+    float* sdC = sm + 16 * nang;    // [nang][16]
+    float* sacc = sm + 32 * nang;   // [nang]
+    for (int a = threadIdx.x; a < nang; a += blockDim.x) {
+        float C[16], dC[16];
+        filter_matrix(filter, __ldg(theta + a), C, dC);
+        for (int k = 0; k < 16; ++k) { sC[16 * a + k] = C[k]; sdC[16 * a + k] = dC[k]; }
+        sacc[a] = 0.0f;
+    }
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long rounds = (npix + stride - 1) / stride;
+    for (long long it = 0; it < rounds; ++it) {
+        const long long pix = first + it * stride;
+        const bool act = pix < npix;
+        float r[12], s[12], t[12];
+        for (int k = 0; k < 12; ++k) { r[k] = 0.0f; s[k] = 0.0f; }
+        if (act) { load12(raw + pix * 12, r); load12(S_adj + pix * 12, s); }
+        for (int a = 0; a < nang; ++a) {
+            float v = 0.0f;
+            if (act) {
+                load12(target + ((long long)a * npix + pix) * 12, t);
+                const float* dC = sdC + 16 * a;
+                for (int c = 0; c < 3; ++c) {
+                    float d[4];
+                    residual4(sC + 16 * a, r + 4 * c, t + 4 * c, d);
+                    for (int i = 0; i < 4; ++i)
+                        v += d[i] * (dC[4 * i] * s[4 * c] + dC[4 * i + 1] * s[4 * c + 1] + dC[4 * i + 2] * s[4 * c + 2] +
+                                     dC[4 * i + 3] * s[4 * c + 3]);
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(sacc + a, v * scale2);
+        }
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < nang; a += blockDim.x)
+        if (sacc[a] != 0.0f) atomicAdd(dtheta + a, sacc[a]);
+}
 
 static int fold_grid(int npix, int block) {
     long long g = ((long long)npix + block - 1) / block;
@@ -149,6 +279,30 @@ cudaError_t launch_filter_adjoint_input(const float* dimage, float* dS, int npix
 cudaError_t launch_theta_grad(const float* dimage, const float* S_adj, int npix, int filter, const float* theta,
                               int nang, float* dtheta, cudaStream_t st) {
     k_theta_grad<<<fold_grid(npix, 256), 256, sizeof(float) * 17 * nang, st>>>(dimage, S_adj, npix, filter, theta, nang, dtheta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l2_loss(const float* raw, const float* target, int npix, int filter, const float* theta, int nang,
+                           double scale, double* loss, cudaStream_t st) {
+    k_l2_loss<<<fold_grid(npix, 256), 256, sizeof(float) * 16 * nang, st>>>(raw, target, npix, filter, theta, nang,
+                                                                              scale, loss);
+    return cudaGetLastError();
+}
+cudaError_t launch_l2_adjoint_input(const float* raw, const float* target, float* dS, int npix, int filter,
+                                    const float* theta, int nang, float scale2, cudaStream_t st) {
+    k_l2_adjoint_input<<<fold_grid(npix, 256), 256, sizeof(float) * 16 * nang, st>>>(raw, target, dS, npix, filter,
+                                                                                       theta, nang, scale2);
+    return cudaGetLastError();
+}
+cudaError_t launch_l2_theta_grad(const float* raw, const float* target, const float* S_adj, int npix, int filter,
+                                 const float* theta, int nang, float scale2, float* dtheta, cudaStream_t st) {
+    const size_t smem = sizeof(float) * 33 * nang;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_l2_theta_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_l2_theta_grad<<<fold_grid(npix, 256), 256, smem, st>>>(raw, target, S_adj, npix, filter, theta, nang, scale2,
+                                                              dtheta);
     return cudaGetLastError();
 }
 

@@ -284,7 +284,8 @@ struct JobPlan {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 dppt_status check_jobs(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
-                       const dppt_params* p, bool adjoint, std::vector<JobPlan>& plan, size_t& ws_bytes) {
+                       const dppt_params* p, bool adjoint, std::vector<JobPlan>& plan, size_t& ws_bytes,
+                       bool l2 = false) {
     if (njobs < 0 || (njobs > 0 && !jobs)) return fail(ctx, DPPT_ERR_INVALID_ARG, "jobs: null or negative count");
     if (!p) return fail(ctx, DPPT_ERR_INVALID_ARG, "params is null");
     if (s->tex_size > 0 && !p->tex) return fail(ctx, DPPT_ERR_INVALID_ARG, "params.tex is null");
@@ -323,10 +324,21 @@ dppt_status check_jobs(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs,
                 q.ws_b = ws_bytes;
                 ws_bytes = align256(ws_bytes + (size_t)q.npix * 12 * sizeof(float));
             }
+        } else if (l2) {
+            q.ws_a = ws_bytes;   // the fused loss's adjoint input of an unfiltered job
+            ws_bytes = align256(ws_bytes + (size_t)q.npix * 12 * sizeof(float));
         }
     }
     return DPPT_OK;
 }
+
+// The fused mean-squared-error loss of dppt_loss_l2 / dppt_render_adjoint_l2.
+struct L2Spec {
+    const float* raw;
+    const int64_t* raw_offsets;
+    const float* target;
+    float scale;
+};
 
 dppt_status ensure_ws(dppt_ctx* ctx, size_t bytes) {
     if (bytes <= ctx->ws_size) return DPPT_OK;
@@ -713,16 +725,20 @@ dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_jo
     return DPPT_OK;
 }
 
-dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
-                                const dppt_params* params, const float* d_image, const dppt_grads* grads,
-                                void* stream) {
+}  // extern "C"
+
+// Phases 2+3 for the adjoint input dg/dI given as an image (l2 == nullptr) or formed from
+// the fused L2 loss's residual (l2 != nullptr, d_image unused).
+static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
+                                const dppt_params* params, const float* d_image, const L2Spec* l2,
+                                const dppt_grads* grads, void* stream) {
     if (!ctx || !s) return fail(ctx, DPPT_ERR_INVALID_ARG, "null context or scene");
     if (!grads) return fail(ctx, DPPT_ERR_INVALID_ARG, "grads is null");
-    if (!d_image && njobs > 0) return fail(ctx, DPPT_ERR_INVALID_ARG, "d_image is null");
+    if (!l2 && !d_image && njobs > 0) return fail(ctx, DPPT_ERR_INVALID_ARG, "d_image is null");
     cudaSetDevice(ctx->device);
     std::vector<JobPlan> plan;
     size_t ws = 0;
-    dppt_status st = check_jobs(ctx, s, jobs, njobs, params, true, plan, ws);
+    dppt_status st = check_jobs(ctx, s, jobs, njobs, params, true, plan, ws, l2 != nullptr);
     if (st != DPPT_OK) return st;
     const Shape shape = shape_of(ctx, 1);
     const bool wave = shape.schedule == DPPT_SCHED_WAVEFRONT;
@@ -748,9 +764,14 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
                 float* dS = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_a);
                 float* Sa = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_b);
                 int tok = ctx->log.begin(kStageFilter, cs);
-                cudaError_t e = launch_filter_adjoint_input(d_image + jobs[i].out_offset, dS, (int)plan[i].npix,
-                                                            jobs[i].filter, params->theta + jobs[i].theta_offset,
-                                                            plan[i].nang, cs);
+                cudaError_t e =
+                    l2 ? launch_l2_adjoint_input(l2->raw + l2->raw_offsets[i], l2->target + jobs[i].out_offset, dS,
+                                                 (int)plan[i].npix, jobs[i].filter,
+                                                 params->theta + jobs[i].theta_offset, plan[i].nang,
+                                                 2.0f * l2->scale, cs)
+                       : launch_filter_adjoint_input(d_image + jobs[i].out_offset, dS, (int)plan[i].npix,
+                                                     jobs[i].filter, params->theta + jobs[i].theta_offset,
+                                                     plan[i].nang, cs);
                 ctx->log.end(tok, cs);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "filter adjoint launch");
                 J.dS = dS;
@@ -759,6 +780,16 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
                     e = cudaMemsetAsync(J.raw, 0, (size_t)plan[i].npix * 12 * sizeof(float), cs);
                     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
                 }
+            } else if (l2) {
+                float* dS = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_a);
+                int tok = ctx->log.begin(kStageFilter, cs);
+                cudaError_t e = launch_l2_adjoint_input(l2->raw + l2->raw_offsets[i], l2->target + jobs[i].out_offset,
+                                                        dS, (int)plan[i].npix, DPPT_FILTER_NONE, nullptr, 1,
+                                                        2.0f * l2->scale, cs);
+                ctx->log.end(tok, cs);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "L2 adjoint input launch");
+                J.dS = dS;
+                J.raw = nullptr;
             } else {
                 J.dS = d_image + jobs[i].out_offset;
                 J.raw = nullptr;
@@ -814,12 +845,68 @@ dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
             if (!plan[i].filtered) continue;
             const float* Sa = reinterpret_cast<const float*>(static_cast<char*>(ctx->ws) + plan[i].ws_b);
             int tok = ctx->log.begin(kStageFilter, cs);
-            cudaError_t e = launch_theta_grad(d_image + jobs[i].out_offset, Sa, (int)plan[i].npix, jobs[i].filter,
-                                              params->theta + jobs[i].theta_offset, plan[i].nang,
-                                              grads->theta + jobs[i].theta_offset, cs);
+            cudaError_t e =
+                l2 ? launch_l2_theta_grad(l2->raw + l2->raw_offsets[i], l2->target + jobs[i].out_offset, Sa,
+                                          (int)plan[i].npix, jobs[i].filter, params->theta + jobs[i].theta_offset,
+                                          plan[i].nang, 2.0f * l2->scale, grads->theta + jobs[i].theta_offset, cs)
+                   : launch_theta_grad(d_image + jobs[i].out_offset, Sa, (int)plan[i].npix, jobs[i].filter,
+                                       params->theta + jobs[i].theta_offset, plan[i].nang,
+                                       grads->theta + jobs[i].theta_offset, cs);
             ctx->log.end(tok, cs);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "theta-gradient launch");
         }
+    }
+    return DPPT_OK;
+}
+
+static dppt_status check_l2(dppt_ctx* ctx, const dppt_job* jobs, int32_t njobs, const float* raw,
+                            const int64_t* raw_offsets, const float* target) {
+    if (njobs > 0 && (!raw || !raw_offsets || !target))
+        return fail(ctx, DPPT_ERR_INVALID_ARG, "raw, raw_offsets and target must not be null");
+    for (int i = 0; i < njobs; ++i)
+        if (raw_offsets[i] < 0 || (raw_offsets[i] & 3) != 0)
+            return fail(ctx, DPPT_ERR_INVALID_ARG, "raw_offsets must be >= 0 and multiples of 4 floats");
+    return DPPT_OK;
+}
+
+extern "C" {
+
+dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
+                                const dppt_params* params, const float* d_image, const dppt_grads* grads,
+                                void* stream) {
+    return adjoint_impl(ctx, s, jobs, njobs, params, d_image, nullptr, grads, stream);
+}
+
+dppt_status dppt_render_adjoint_l2(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
+                                   const dppt_params* params, const float* raw, const int64_t* raw_offsets,
+                                   const float* target, float scale, const dppt_grads* grads, void* stream) {
+    if (!ctx) return DPPT_ERR_INVALID_ARG;
+    dppt_status st = check_l2(ctx, jobs, njobs, raw, raw_offsets, target);
+    if (st != DPPT_OK) return st;
+    const L2Spec l2{raw, raw_offsets, target, scale};
+    return adjoint_impl(ctx, s, jobs, njobs, params, nullptr, &l2, grads, stream);
+}
+
+dppt_status dppt_loss_l2(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
+                         const dppt_params* params, const float* raw, const int64_t* raw_offsets,
+                         const float* target, double scale, double* loss, void* stream) {
+    if (!ctx || !s || !loss) return fail(ctx, DPPT_ERR_INVALID_ARG, "null context, scene or loss");
+    cudaSetDevice(ctx->device);
+    std::vector<JobPlan> plan;
+    size_t ws = 0;
+    dppt_status st = check_jobs(ctx, s, jobs, njobs, params, false, plan, ws);
+    if (st != DPPT_OK) return st;
+    if ((st = check_l2(ctx, jobs, njobs, raw, raw_offsets, target)) != DPPT_OK) return st;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), cs);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+    for (int i = 0; i < njobs; ++i) {
+        int tok = ctx->log.begin(kStageFilter, cs);
+        e = launch_l2_loss(raw + raw_offsets[i], target + jobs[i].out_offset, (int)plan[i].npix, jobs[i].filter,
+                           plan[i].filtered ? params->theta + jobs[i].theta_offset : nullptr, plan[i].nang, scale,
+                           loss, cs);
+        ctx->log.end(tok, cs);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "L2 loss launch");
     }
     return DPPT_OK;
 }

@@ -181,4 +181,11 @@ cudaError_t launch_filter_adjoint_input(const float* dimage, float* dS, int npix
                                         const float* theta, int nang, cudaStream_t st);
 cudaError_t launch_theta_grad(const float* dimage, const float* S_adj, int npix, int filter, const float* theta,
                               int nang, float* dtheta, cudaStream_t st);
+// fused mean-squared-error folds (residual C_a raw - T_a formed per pixel)
+cudaError_t launch_l2_loss(const float* raw, const float* target, int npix, int filter, const float* theta, int nang,
+                           double scale, double* loss, cudaStream_t st);
+cudaError_t launch_l2_adjoint_input(const float* raw, const float* target, float* dS, int npix, int filter,
+                                    const float* theta, int nang, float scale2, cudaStream_t st);
+cudaError_t launch_l2_theta_grad(const float* raw, const float* target, const float* S_adj, int npix, int filter,
+                                 const float* theta, int nang, float scale2, float* dtheta, cudaStream_t st);
 }  // namespace dppt

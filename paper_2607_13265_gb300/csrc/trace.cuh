@@ -368,7 +368,8 @@ __device__ __forceinline__ f3 s_axis(f3 a, f3 b) {
 
 // pBRDF value f(wo, wi) without the cosine, as a compact operator.
 template <class T>
-__device__ void bsdf_compact(const DScene& S, const DParams& P, const DMat& m, const VCtx& vc, f3 wi, Compact<T>& f) {
+__device__ __forceinline__ void bsdf_compact(const DScene& S, const DParams& P, const DMat& m, const VCtx& vc, f3 wi,
+                                             Compact<T>& f) {
     compact_zero(f);
     float ci = dot(wi, vc.n), co = dot(vc.wo, vc.n);
     if (ci <= 0.0f || co <= 0.0f) return;
@@ -416,11 +417,20 @@ __device__ __forceinline__ Rot<float> emitter_rot(const DLight& L, f3 p) {
     return rot_between(p, xe, onb_t1(p));
 }
 
+// The material of a vertex; MT >= 0 states its type at compile time (kernels specialized
+// to one material type), so that the other types' code folds away.
+template <int MT>
+__device__ __forceinline__ DMat load_mat(const DScene& S, int mat) {
+    DMat m = S.mats[mat];
+    if (MT >= 0) m.type = MT;
+    return m;
+}
+
 // E_v (per channel, float) and W_v (compact, T) for one vertex.
-template <class T>
+template <class T, int MT = -1>
 __device__ void eval_vertex(const DScene& S, const DParams& P, const VCtx& vc, float E[3][4], Compact<T>& W,
                             Compact<T>* fnee) {
-    const DMat m = S.mats[vc.mat];
+    const DMat m = load_mat<MT>(S, vc.mat);
     for (int c = 0; c < 3; ++c) E[c][0] = E[c][1] = E[c][2] = E[c][3] = 0.0f;
     if (vc.emit) {
         DLight L = load_light(S, vc.light);
@@ -774,13 +784,14 @@ struct GlobalCache {
 // The replayed vertex's local vector-Jacobian product: J_c = a_c^T (E_c + W_c L_c) with
 // dual numbers (W and the NEE operator f from eval_vertex<D3>, Ln the suffix L[v+1]),
 // scattered into the gradients; then the adjoint row advances, a^T <- a^T W_v.
+template <int MT = -1>
 __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, const DGrads& G_, float* sgrad,
                                            const VCtx& vc, const Compact<D3>& W, const Compact<D3>& f,
                                            const float Ln[3][4], float a[3][4]) {
     const DScene* S = &S_;
     const DParams* P = &P_;
     const DGrads* G = &G_;
-    const DMat m = S->mats[vc.mat];
+    const DMat m = load_mat<MT>(S_, vc.mat);
     // local vector-Jacobian products: J_c = a_c^T (E_c + W_c L_c) with dual numbers
     float g_slot0 = 0.0f, g_eta = 0.0f, g_alb[3];
     Compact<float> fv;
@@ -862,7 +873,7 @@ __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, 
 // registers); the backward fold overwrites E_v with the suffix L[v] where the replay
 // will read it (the adjoint's vertices 1..n-1).  Pass 1 (adjoint only) replays the
 // vertex with dual numbers.
-template <class Cache>
+template <class Cache, int MT = -1>
 struct PathVis {
     const DScene* S;
     const DParams* P;
@@ -879,7 +890,7 @@ struct PathVis {
             if (n >= C.cap) return;
             float E[3][4];
             Compact<float> W;
-            eval_vertex<float>(*S, *P, vc, E, W, nullptr);
+            eval_vertex<float, MT>(*S, *P, vc, E, W, nullptr);
             if (!vc.scatter) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
@@ -945,7 +956,7 @@ struct PathVis {
     __device__ void replay_vertex(const VCtx& vc) {
         float E[3][4];
         Compact<D3> W, f;
-        eval_vertex<D3>(*S, *P, vc, E, W, &f);
+        eval_vertex<D3, MT>(*S, *P, vc, E, W, &f);
         float Ln[3][4];
         if (i + 1 < n) {
 #pragma unroll
@@ -954,7 +965,7 @@ struct PathVis {
 #pragma unroll
             for (int k = 0; k < 12; ++k) Ln[k >> 2][k & 3] = 0.0f;
         }
-        replay_vjp(*S, *P, *G, sgrad, vc, W, f, Ln, a);
+        replay_vjp<MT>(*S, *P, *G, sgrad, vc, W, f, Ln, a);
     }
 };
 

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared_symbols():
     src = open(os.path.join(ROOT, "include", "dppt.h")).read()
-    return sorted(set(re.findall(r"\b(dppt_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(dppt_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")

@@ -14,5 +14,58 @@ def test_batched_graph_and_plain_form():
                             "--depth", "4", "--no-tune"])
     assert out["batched"]["graph_vs_eager_grad_rel"] < 1e-4
     assert out["speedup_effective"] > 1.0
+    assert out["batched_fused_l2"]["grad_rel_vs_image_form"] < 1e-4
+    assert out["batched_fused_l2"]["peak_autograd_bytes"] < out["plain"]["peak_autograd_bytes"]
     assert len(out["per_view_gradients"]) == 3
     assert all(v["dtheta_l2"] > 0 for v in out["per_view_gradients"])
+
+
+def test_fused_l2_equals_image_form():
+    """PolarizedL2 (loss folded into the camera filter) gives the loss and every gradient of
+    PolarizedRender + ImageL2 on the same paths -- views with 8 polarizer angles each, plus
+    an unfiltered job -- while keeping 12 floats per pixel instead of one image per angle."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import copy
+    import numpy as np
+    from paper_2607_13265_gb300 import api, build, scenegen as sg
+    build.build()
+    dctx = api.Context(0)
+    scene, jobs = sg.cornell_views(3, 8, 4, 4, (24, 40, 32))
+    plain = copy.copy(jobs[0])
+    plain.filter, plain.thetas, plain.stream = sg.FILTER_NONE, [], 7
+    jobs = jobs + [plain]
+    gs = api.GpuScene(dctx, scene)
+    batch = api.pack_jobs(jobs)
+    adj = api.pack_jobs(api.adjoint_jobs(jobs))
+    P = api.device_params(scene, batch)
+    tp = scene.params()
+    tp["tex"] = np.clip(tp["tex"] * 0.8 + 0.05, 0.0, 1.0)
+    tp["theta"] = batch.theta + 0.1
+    target = api.render_primal(dctx, gs, batch, api.device_params(scene, batch, tp)).clone()
+
+    def grads(fused):
+        leaf = {k: v.clone().requires_grad_(True) for k, v in P.items()}
+        args = (leaf["tex"], leaf["ior"], leaf["le"], leaf["sheet"], leaf["theta"])
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        if fused:
+            loss = api.PolarizedL2.apply(dctx, gs, batch, adj, target, *args)
+        else:
+            loss = api.ImageL2.apply(api.PolarizedRender.apply(dctx, gs, batch, adj, *args), target)
+        loss.backward()
+        torch.cuda.synchronize()
+        dctx.sync_status()
+        peak = torch.cuda.max_memory_allocated() - base
+        return float(loss), {k: v.grad.double().cpu().numpy() for k, v in leaf.items()}, peak
+
+    l_img, g_img, m_img = grads(False)
+    l_fus, g_fus, m_fus = grads(True)
+    assert l_fus == pytest.approx(l_img, rel=1e-5)
+    for k in ("tex", "theta", "ior", "le"):
+        n = np.linalg.norm(g_img[k])
+        assert n > 0, k
+        assert np.linalg.norm(g_fus[k] - g_img[k]) <= 1e-4 * n, (k, np.linalg.norm(g_fus[k] - g_img[k]) / n)
+    assert m_fus < 0.5 * m_img, (m_fus, m_img)
