@@ -48,6 +48,14 @@ F_VERTEX_ADJOINT = 2 * F_SHADE + F_CACHE + F_REPLAY
 DOMINANT_DRAM_BYTES_PER_LAUNCH = None
 
 
+def wave_paths(job) -> int:
+    """Paths per wavefront wave: at most 4,194,304 whole pixels and at most 8 GiB of path
+    state (~400 B) plus cache (124 B per vertex) per wave, as the library sizes them."""
+    per_path = 400 + 124 * job.max_depth
+    cap = min(1 << 22, (8 << 30) // per_path)
+    return min(job.num_paths, max(job.spp, cap // job.spp * job.spp))
+
+
 def stage_flops(w: dict, passes: int) -> dict:
     """Algorithmic flops of each stage for one launch of the work counted in `w`."""
     closest = F_NODE * w["nodes"] + F_TRI * w["tri_tests"] + F_SPH * w["sph_tests"]
@@ -122,6 +130,34 @@ def _oracle_task(pixels):
     aj.pass_id = 1
     o.gradient(aj, P, np.ones_like(img), pixels=pix, mode="replay")
     return time.perf_counter() - t0, 2 * len(pix) * job.spp
+
+
+def _oracle_tape_task(pixels):
+    """Conventional taped AD of the workload's paths on a few pixels: the tape's nodes (one
+    per parameter-dependent scalar operation, all kept until the reverse sweep) and the
+    vertices they cover."""
+    import copy
+    import numpy as np
+    import oracle
+    o, scene, job = _W["o"], _W["scene"], _W["job"]
+    pix = np.asarray(pixels, np.int64)
+    P = scene.params()
+    aj = copy.copy(job)
+    aj.pass_id = 1
+    img = o.render(aj, P, pixels=pix)
+    oracle.stats(reset=True)
+    o.gradient(aj, P, np.ones_like(img), pixels=pix, mode="tape")
+    st = oracle.stats(reset=True)
+    return st["tape_total_nodes"], st["vertices"]
+
+
+def tape_model(pool, num_pixels: int = 64) -> dict:
+    """Tape nodes per path vertex of conventional AD on an evenly strided pixel sample."""
+    import numpy as np
+    pix = np.linspace(0, 256 * 256 - 1, num_pixels).astype(np.int64)
+    res = pool.map(_oracle_tape_task, [pix[i:i + 8].tolist() for i in range(0, len(pix), 8)])
+    nodes, verts = sum(r[0] for r in res), sum(r[1] for r in res)
+    return {"tape_nodes_per_vertex": nodes / max(verts, 1), "sample": f"{num_pixels} pixels x 64 spp, FP64 oracle tape"}
 
 
 def oracle_sample(num_pixels: int, procs: int, workload_kw: dict, pool=None):
@@ -367,14 +403,18 @@ def run_native(args):
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "frac_at_loaded_clock": achieved / fp32_peak_loaded,
                      "traffic": DOMINANT_DRAM_BYTES_PER_LAUNCH,
+                     "hbm": ({"achieved_gbs": DOMINANT_DRAM_BYTES_PER_LAUNCH / (dom_ms / max(dom_launches, 1) / 1e3) / 1e9,
+                              "peak_gbs": float(peaks.get("hbm_gbs") or 6800.0),
+                              "frac": DOMINANT_DRAM_BYTES_PER_LAUNCH / (dom_ms / max(dom_launches, 1) / 1e3) / 1e9
+                                      / float(peaks.get("hbm_gbs") or 6800.0)}
+                             if DOMINANT_DRAM_BYTES_PER_LAUNCH else None),
                      "flops_per_launch": flops.get(dom, 0) / max(dom_launches, 1),
                      "launch_ms": dom_ms / max(dom_launches, 1),
                      "work_units_adjoint_pass": work,
                      "peak_note": f"FP32 pipe: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
                                   f"({peaks['_source']} max clock)"},
         "memory": {"workspace_bytes": dctx.query_workspace(adj),
-                   "prb_cache_bytes": (min(job.num_paths, (1 << 21) // job.spp * job.spp) * job.max_depth * 31 * 4
-                                       if lc[3] == 2 else cache_bytes),
+                   "prb_cache_bytes": (wave_paths(job) * job.max_depth * 31 * 4 if lc[3] == 2 else cache_bytes),
                    "prb_cache_where": "wavefront workspace" if lc[3] == 2 else "megakernel thread-local memory",
                    "megakernel_local_bytes_per_thread": fp["local_bytes_per_thread"],
                    "megakernel_adjoint_registers": fp["registers"]},
@@ -384,6 +424,14 @@ def run_native(args):
     }
     if pool is not None:
         result["cpu_baseline"] = oracle_sample(args.cpu_pixels, cpu_procs, {}, pool)
+        tm = tape_model(pool)
+        # conventional AD keeps every path's tape at once: nodes/vertex x vertices of the
+        # gradient pass, at 16 B per node (FP32 partials + 32-bit operand indices) and 4 B
+        # (one FP32 value: a lower bound for any tape)
+        nv = tm["tape_nodes_per_vertex"] * work["vertices"]
+        result["memory"]["tape_ad_model"] = {"bytes_16B_per_node": int(16 * nv), "bytes_4B_lower_bound": int(4 * nv),
+                                             **tm}
+        result["memory"]["prb_cache_vs_tape_ad"] = result["memory"]["prb_cache_bytes"] / max(1.0, 16 * nv)
         pool.close()
         pool.join()
     if rank == 0:

@@ -59,7 +59,7 @@ def test_fused_l2_equals_image_form():
         torch.cuda.synchronize()
         dctx.sync_status()
         peak = torch.cuda.max_memory_allocated() - base
-        return float(loss), {k: v.grad.double().cpu().numpy() for k, v in leaf.items()}, peak
+        return float(loss.detach()), {k: v.grad.double().cpu().numpy() for k, v in leaf.items()}, peak
 
     l_img, g_img, m_img = grads(False)
     l_fus, g_fus, m_fus = grads(True)
