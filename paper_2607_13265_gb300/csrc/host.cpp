@@ -180,6 +180,67 @@ struct Builder {
     }
 };
 
+// Collapses the binary BVH into a 4-wide one: a node's children are found by replacing,
+// while fewer than four, the inner child of largest surface area by its two children.
+// Node layout (8 float4, one 128-byte line): the four children's lo.x, hi.x, lo.y, hi.y,
+// lo.z, hi.z (one float4 each), their references (leaf references as in the binary tree),
+// then the child count.  Returns the 4-wide node index of binary node `ref`.
+struct Collapser {
+    const std::vector<float4>& bin;
+    std::vector<float4> out;
+    int max_depth = 0;
+    explicit Collapser(const std::vector<float4>& b) : bin(b) {}
+
+    struct Child { float lo[3], hi[3]; int ref; };
+    void children_of(int ref, Child& l, Child& r) const {
+        const float4* n = &bin[4 * ref];
+        l = Child{{n[0].x, n[0].z, n[2].x}, {n[0].y, n[0].w, n[2].y}, 0};
+        r = Child{{n[1].x, n[1].z, n[2].z}, {n[1].y, n[1].w, n[2].w}, 0};
+        std::memcpy(&l.ref, &n[3].x, 4);
+        std::memcpy(&r.ref, &n[3].y, 4);
+    }
+    static float area(const Child& c) {
+        float d[3];
+        for (int k = 0; k < 3; ++k) d[k] = std::max(0.0f, c.hi[k] - c.lo[k]);
+        return d[0] * d[1] + d[1] * d[2] + d[2] * d[0];
+    }
+    int collapse(int ref, int depth) {
+        max_depth = std::max(max_depth, depth);
+        Child c[4];
+        int n = 2;
+        children_of(ref, c[0], c[1]);
+        while (n < 4) {
+            int best = -1;
+            for (int k = 0; k < n; ++k)
+                if (c[k].ref >= 0 && (best < 0 || area(c[k]) > area(c[best]))) best = k;
+            if (best < 0) break;
+            Child a, b;
+            children_of(c[best].ref, a, b);
+            c[best] = a;
+            c[n++] = b;
+        }
+        const int id = (int)(out.size() / 8);
+        out.resize(out.size() + 8);
+        int refs[4] = {~0, ~0, ~0, ~0};
+        for (int k = 0; k < n; ++k) refs[k] = c[k].ref >= 0 ? collapse(c[k].ref, depth + 1) : c[k].ref;
+        float v[6][4];
+        for (int k = 0; k < 4; ++k)
+            for (int a = 0; a < 3; ++a) {
+                v[2 * a][k] = k < n ? c[k].lo[a] : 0.0f;
+                v[2 * a + 1][k] = k < n ? c[k].hi[a] : 0.0f;
+            }
+        for (int r = 0; r < 6; ++r) out[8 * id + r] = make_float4(v[r][0], v[r][1], v[r][2], v[r][3]);
+        float4 rf;
+        std::memcpy(&rf.x, &refs[0], 4); std::memcpy(&rf.y, &refs[1], 4);
+        std::memcpy(&rf.z, &refs[2], 4); std::memcpy(&rf.w, &refs[3], 4);
+        out[8 * id + 6] = rf;
+        float4 meta = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        std::memcpy(&meta.x, &n, 4);
+        out[8 * id + 7] = meta;
+        return id;
+    }
+};
+
 template <class T>
 bool upload(dppt_scene* s, const T* host, size_t count, const T** dst, cudaError_t& err) {
     *dst = nullptr;
@@ -534,6 +595,13 @@ dppt_status dppt_scene_upload(dppt_ctx* ctx, const dppt_scene_desc* d, dppt_scen
         depth = B.max_depth + 1;
         if (depth >= kBvhStack) return fail(ctx, DPPT_ERR_UNSUPPORTED, "BVH deeper than the traversal stack");
     }
+    Collapser C4(B.nodes);
+    if (F > 0) {
+        C4.collapse(0, 1);
+        // a 4-wide node pushes up to three children
+        if (3 * C4.max_depth + 1 >= kBvhStack)
+            return fail(ctx, DPPT_ERR_UNSUPPORTED, "4-wide BVH deeper than the traversal stack");
+    }
     std::vector<float4> tris(3 * F);
     std::vector<float> tri_uv(6 * F, 0.0f);
     for (int64_t s = 0; s < F; ++s) {
@@ -559,6 +627,7 @@ dppt_status dppt_scene_upload(dppt_ctx* ctx, const dppt_scene_desc* d, dppt_scen
     cudaError_t e = cudaSuccess;
     DScene& D = s->d;
     bool ok = upload(s, B.nodes.data(), B.nodes.size(), &D.nodes, e) &&
+              upload(s, C4.out.data(), C4.out.size(), &D.nodes4, e) &&
               upload(s, tris.data(), tris.size(), &D.tris, e) &&
               upload(s, d->tri_material, (size_t)F, &D.tri_mat, e) &&
               upload(s, d->tri_light, (size_t)F, &D.tri_light, e) &&

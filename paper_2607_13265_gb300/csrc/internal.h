@@ -10,7 +10,11 @@ namespace dppt {
 
 constexpr int kMaxJobsPerLaunch = 64;
 constexpr int kBvhStack = 64;
-constexpr int kMaxDepth = 128;      // surface vertices per path (largest cache bucket)
+constexpr int kMaxDepth = 128;
+// traversal of the 4-wide BVH (1) or of the binary one (0)
+#ifndef DPPT_BVH4
+#define DPPT_BVH4 1
+#endif      // surface vertices per path (largest cache bucket)
 
 struct DMat {
     int type, albedo_tex, rough_tex, ior_index, sheet_index;
@@ -26,7 +30,8 @@ struct DCam { float org[3], fwd[3], right[3], up[3], tanh; };
 //   ref < 0 is a leaf ~(first | count << 25) over the BVH-ordered triangles.
 // Triangles (3 x float4 = 48 B, BVH order): (v0, original id), (e1, 0), (e2, 0).
 struct DScene {
-    const float4* nodes;
+    const float4* nodes;    // binary BVH: 4 float4 per node
+    const float4* nodes4;   // the same tree collapsed to 4 children per node: 8 float4 per node
     const float4* tris;
     int num_tris;
     int num_nodes;

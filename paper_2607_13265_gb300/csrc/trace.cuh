@@ -176,6 +176,88 @@ __device__ __forceinline__ bool trav_round(const DScene& S, Trav& r, int* stack,
     return r.ref == kTravDone;
 }
 
+// One round over the 4-wide BVH, with the same while-while structure: a node's four
+// child boxes are tested together, the nearest hit child is descended and the other hits
+// are pushed far to near (for any-hit queries in node order).  COUNT counts a node visit
+// as two units of two child boxes, the unit of the binary tree.
+__device__ __forceinline__ void cswap(float& ta, int& ra, float& tb, int& rb) {
+    if (tb < ta) { float t = ta; ta = tb; tb = t; int r = ra; ra = rb; rb = r; }
+}
+template <bool ANY, bool COUNT>
+__device__ __forceinline__ bool trav4_round(const DScene& S, Trav& r, int* stack, unsigned* status, WorkCount* wc) {
+    int leaf = kTravDone;
+    while (r.ref >= 0 && r.ref != kTravDone) {
+        const float4* nd = S.nodes4 + 8 * r.ref;
+        const float4 lx = __ldg(nd), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
+        const float4 lz = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
+        const int cnt = __float_as_int(__ldg(&nd[7].x));
+        if (COUNT) { if (ANY) wc->shadow_nodes += 2; else wc->nodes += 2; }
+        const float blx[4] = {lx.x, lx.y, lx.z, lx.w}, bhx[4] = {hx.x, hx.y, hx.z, hx.w};
+        const float bly[4] = {ly.x, ly.y, ly.z, ly.w}, bhy[4] = {hy.x, hy.y, hy.z, hy.w};
+        const float blz[4] = {lz.x, lz.y, lz.z, lz.w}, bhz[4] = {hz.x, hz.y, hz.z, hz.w};
+        const int cr[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
+        float t[4];
+        int c[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float x0 = fmaf(blx[k], r.inv.x, -r.oi.x), x1 = fmaf(bhx[k], r.inv.x, -r.oi.x);
+            const float y0 = fmaf(bly[k], r.inv.y, -r.oi.y), y1 = fmaf(bhy[k], r.inv.y, -r.oi.y);
+            const float z0 = fmaf(blz[k], r.inv.z, -r.oi.z), z1 = fmaf(bhz[k], r.inv.z, -r.oi.z);
+            const float tn = fmax3(fminf(x0, x1), fminf(y0, y1), fmaxf(fminf(z0, z1), 0.0f));
+            const float tf = fmin3(fmaxf(x0, x1), fmaxf(y0, y1), fminf(fmaxf(z0, z1), r.t));
+            const bool hit = k < cnt && tn <= tf;
+            t[k] = hit ? tn : INFINITY;
+            c[k] = hit ? cr[k] : kTravDone;
+        }
+        if (!ANY) {
+            // sorting network on (t, ref): nearest first
+            cswap(t[0], c[0], t[1], c[1]);
+            cswap(t[2], c[2], t[3], c[3]);
+            cswap(t[0], c[0], t[2], c[2]);
+            cswap(t[1], c[1], t[3], c[3]);
+            cswap(t[1], c[1], t[2], c[2]);
+        }
+        int next = kTravDone;
+#pragma unroll
+        for (int k = 3; k >= 0; --k) {
+            if (c[k] == kTravDone) continue;
+            if (next != kTravDone) {
+                if (r.sp >= kBvhStack) { atomicOr(status, kStatusStackOverflow); r.ref = kTravDone; return true; }
+                stack[r.sp++] = next;
+            }
+            next = c[k];
+        }
+        r.ref = next != kTravDone ? next : trav_pop(stack, r.sp);
+        if (r.ref < 0 && leaf == kTravDone) { leaf = r.ref; r.ref = trav_pop(stack, r.sp); }
+        if (!__any_sync(__activemask(), leaf == kTravDone)) break;
+    }
+    while (leaf != kTravDone) {
+        unsigned v = ~(unsigned)leaf;
+        int first = (int)(v & 0x1FFFFFFu), cnt = (int)(v >> 25);
+        if (COUNT) { if (ANY) wc->shadow_tri_tests += cnt; else wc->tri_tests += cnt; }
+        for (int i = first; i < first + cnt; ++i) {
+            float b1, b2;
+            float tt = tri_test(S.tris, i, r.o, r.d, b1, b2);
+            if (ANY) {
+                if (tt > 0.0f && tt < r.t) { r.prim = 1; r.ref = kTravDone; return true; }
+            } else if (tt > 0.0f && tt <= r.t) {
+                int id = __float_as_int(__ldg(&S.tris[3 * i].w));
+                if (tt < r.t || id < r.prim) { r.t = tt; r.prim = id; r.slot = i; r.b1 = b1; r.b2 = b2; }
+            }
+        }
+        leaf = kTravDone;
+        if (r.ref < 0) { leaf = r.ref; r.ref = trav_pop(stack, r.sp); }
+    }
+    return r.ref == kTravDone;
+}
+
+// the traversal of the build's BVH layout
+template <bool ANY, bool COUNT>
+__device__ __forceinline__ bool trav_step(const DScene& S, Trav& r, int* stack, unsigned* status, WorkCount* wc) {
+    if (DPPT_BVH4) return trav4_round<ANY, COUNT>(S, r, stack, status, wc);
+    return trav_round<ANY, COUNT>(S, r, stack, status, wc);
+}
+
 // spheres after the triangles: ties in t go to the lower primitive id (triangles first)
 __device__ __forceinline__ void trav_spheres_closest(const DScene& S, Trav& r) {
     for (int k = 0; k < S.num_spheres; ++k) {
@@ -200,7 +282,7 @@ __device__ bool trace_closest(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* 
     trav_begin(r, o, d, FLT_MAX);
     if (S.num_tris > 0) {
         int stack[kBvhStack];
-        while (!trav_round<false, COUNT>(S, r, stack, status, wc)) {
+        while (!trav_step<false, COUNT>(S, r, stack, status, wc)) {
         }
     }
     trav_spheres_closest(S, r);
@@ -217,7 +299,7 @@ __device__ bool trace_any(const DScene& S, f3 o, f3 d, float tmax, unsigned* sta
     Trav r;
     trav_begin(r, o, d, tmax);
     int stack[kBvhStack];
-    while (!trav_round<true, COUNT>(S, r, stack, status, wc)) {
+    while (!trav_step<true, COUNT>(S, r, stack, status, wc)) {
     }
     return r.prim >= 0;
 }
@@ -744,22 +826,48 @@ __device__ __forceinline__ bool walk_step(const DScene& S, const DParams& P, con
     return walk_finish(S, P, w, vc, ne, visible, sh, vis);
 }
 
-// Warp-aggregated scatter-add: lanes adding to the same element combine their
-// values first, then one lane issues the atomic.
-__device__ __forceinline__ void atomic_add_agg(float* base, long long idx, float val) {
+// Gradient scatter of texel derivatives.  DPPT_GRAD_AGG 2 (default): once per vertex and
+// texture, two integer warp reductions tell whether a full warp sits on the same base
+// texel (then its four bilinear taps agree too, e.g. the samples of one pixel at their
+// first vertex); such a warp sums each value with shuffles and one lane issues the atomic,
+// any other warp issues one atomic per lane.  1: lanes adding to the same element are
+// grouped with __match_any_sync before every atomic.  0: one atomic per lane.
+#ifndef DPPT_GRAD_AGG
+#define DPPT_GRAD_AGG 2
+#endif
+__device__ __forceinline__ void atomic_add_grouped(float* base, long long idx, float val) {
     const unsigned mask = __activemask();
     const unsigned peers = __match_any_sync(mask, (unsigned long long)idx);
     const int lane = threadIdx.x & 31;
-    float sum;
-    if (peers == 0xffffffffu) {
-        sum = val;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-    } else {
-        sum = 0.0f;
-        for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, val, __ffs(m) - 1);
-    }
+    float sum = 0.0f;
+    for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, val, __ffs(m) - 1);
     if (lane == __ffs(peers) - 1 && sum != 0.0f) atomicAdd(base + idx, sum);
+}
+// adds vals[c] * w[k] at tp.idx[k] + min(c, ch - 1) for the NC values and the four taps
+template <int NC>
+__device__ __forceinline__ void scatter_taps(float* g, const Taps& tp, const float* vals, int ch) {
+    const unsigned FULL = 0xffffffffu;
+    bool uniform = false;
+    if (DPPT_GRAD_AGG == 2 && __activemask() == FULL) {
+        const unsigned lo = (unsigned)tp.idx[0], hi = (unsigned)((unsigned long long)tp.idx[0] >> 32);
+        uniform = __reduce_or_sync(FULL, hi) == 0u && __reduce_min_sync(FULL, lo) == __reduce_max_sync(FULL, lo);
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float v = vals[c] * tp.w[k];
+            const long long idx = tp.idx[k] + min(c, ch - 1);
+            if (uniform) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+                if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(g + idx, v);
+            } else if (DPPT_GRAD_AGG == 1) {
+                atomic_add_grouped(g, idx, v);
+            } else if (v != 0.0f) {
+                atomicAdd(g + idx, v);
+            }
+        }
 }
 
 // ================================================================== per-vertex actions
@@ -849,17 +957,13 @@ __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, 
     if (G->tex) {
         if ((m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.rough_tex].pad) {
             Taps tp = tex_taps(S->tex[m.rough_tex], vc.tu, vc.tv);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) atomic_add_agg(G->tex, tp.idx[k], g_slot0 * tp.w[k]);
+            scatter_taps<1>(G->tex, tp, &g_slot0, 1);
         }
         if (m.albedo_tex >= 0 && (m.type == DPPT_MAT_DIFFUSE || m.type == DPPT_MAT_CONDUCTOR_GGX ||
                                   m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.albedo_tex].pad) {
             DTex t = S->tex[m.albedo_tex];
             Taps tp = tex_taps(t, vc.tu, vc.tv);
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) atomic_add_agg(G->tex, tp.idx[k] + min(c, t.ch - 1), g_alb[c] * tp.w[k]);
+            scatter_taps<3>(G->tex, tp, g_alb, t.ch);
         }
     }
     // advance the adjoint row through the value of W_i

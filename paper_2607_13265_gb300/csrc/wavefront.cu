@@ -140,7 +140,8 @@ __global__ void k_wf_init(const DScene S, const __grid_constant__ JobTable T, in
     }
 }
 
-// Closest hits of the live paths, one ray per thread in a grid-stride loop.
+// Closest hits of the live paths, one ray per thread in a grid-stride loop.  The list
+// keeps the samples of a pixel together, so a warp's rays share their origin.
 __global__ void __launch_bounds__(512, DPPT_WF_TRAVERSE_MIN_BLOCKS)
 k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
     const int n0 = L.count[0], n = n0 + L.count[1];
