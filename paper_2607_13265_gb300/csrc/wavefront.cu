@@ -21,12 +21,12 @@
 #define DPPT_WF_TRAVERSE_MIN_BLOCKS 2
 #endif
 // resident 128-thread blocks per SM the finish kernels' register allocation must allow
-// (4 -> at most 128 registers per thread, 3 -> at most 168)
+// (4 -> at most 128 registers per thread, 3 -> at most 168); chosen by measured sweeps
 #ifndef DPPT_WF_CACHE_MIN_BLOCKS
 #define DPPT_WF_CACHE_MIN_BLOCKS 4
 #endif
 #ifndef DPPT_WF_REPLAY_MIN_BLOCKS
-#define DPPT_WF_REPLAY_MIN_BLOCKS 3
+#define DPPT_WF_REPLAY_MIN_BLOCKS 4
 #endif
 
 namespace dppt {

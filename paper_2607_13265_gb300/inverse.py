@@ -5,8 +5,9 @@ rough dielectric pBRDFs, 3 polarizer sheets and 1 retarder sheet, 4 unpolarized 
 lights; 1024x1024, 128 spp, depth 12, camera polarizer at 16 angles (folded exactly).
 Parameters: the 1024^2x3 albedo and 1024^2 roughness textures, optimized with Adam (lr
 1e-2) toward a target rendered from seeded target textures with other random numbers.
-Each iteration is PolarizedRender forward (render_primal) + loss.backward()
-(render_adjoint, cached suffix replay) + Adam.  Prints one JSON line.
+Each iteration is the fused loss PolarizedL2 (render_primal of the raw image + the loss
+folded into the camera filter) + loss.backward() (render_adjoint_l2, cached suffix replay)
++ Adam; --image-loss uses PolarizedRender and mean((I - T)^2) instead.  Prints one JSON line.
 
   python -m paper_2607_13265_gb300.inverse [--iters 10] [--width 1024] [--spp 128]
 """
@@ -31,6 +32,8 @@ def main(argv=None):
     ap.add_argument("--meshes", type=int, default=10)
     ap.add_argument("--freq", type=int, default=50)
     ap.add_argument("--tex", type=int, default=1024)
+    ap.add_argument("--image-loss", action="store_true",
+                    help="PolarizedRender + mean((I - T)^2) instead of the fused PolarizedL2")
     args = ap.parse_args(argv)
 
     import torch
@@ -73,15 +76,22 @@ def main(argv=None):
 
     history = []
     times = []
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    mem0 = torch.cuda.memory_allocated()
     rmse0 = {"albedo": rmse(alb), "roughness": rmse(rough)}
     for it in range(args.iters):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         opt.zero_grad(set_to_none=True)
         adj_it = api.pack_jobs(api.adjoint_jobs([job], pass_id=1 + 2 * it))   # fresh decorrelated paths
-        img = api.PolarizedRender.apply(dctx, gs, batch, adj_it, tex, others["ior"], others["le"], others["sheet"],
-                                        others["theta"])
-        loss = ((img - target) ** 2).mean()
+        if args.image_loss:
+            img = api.PolarizedRender.apply(dctx, gs, batch, adj_it, tex, others["ior"], others["le"],
+                                            others["sheet"], others["theta"])
+            loss = ((img - target) ** 2).mean()
+        else:
+            loss = api.PolarizedL2.apply(dctx, gs, batch, adj_it, target, tex, others["ior"], others["le"],
+                                         others["sheet"], others["theta"])
         loss.backward()
         opt.step()
         with torch.no_grad():
@@ -104,6 +114,8 @@ def main(argv=None):
         "paths_per_iteration": paths, "paths_per_s": paths / (float(np.median(times)) / 1000.0),
         "loss": history, "texture_rmse_before": rmse0,
         "texture_rmse_after": {"albedo": rmse(alb), "roughness": rmse(rough)},
+        "loss_form": "image" if args.image_loss else "fused_l2",
+        "peak_autograd_bytes": int(torch.cuda.max_memory_allocated() - mem0),
         "workspace_bytes": dctx.query_workspace(adj), "tuning": tuning,
     }
     print(json.dumps(out))
