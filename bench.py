@@ -43,9 +43,11 @@ F_SHADE, F_CACHE, F_REPLAY = 60, 358, 620
 F_VERTEX_PRIMAL = F_SHADE + F_CACHE
 F_VERTEX_ADJOINT = 2 * F_SHADE + F_CACHE + F_REPLAY
 
-# DRAM traffic per launch of the dominant kernel from one ncu capture (bytes), or None
-# when the kernel has changed since the counters were taken.
-DOMINANT_DRAM_BYTES_PER_LAUNCH = None
+# DRAM traffic per launch of the dominant kernel (k_wf_extend, the 4-wide BVH traversal)
+# from one ncu capture of this workload: mean of dram__bytes_read.sum + dram__bytes_write.sum
+# over the 24 launches of one timed step (bytes); None once the kernel has changed since.
+DOMINANT_DRAM_BYTES_PER_LAUNCH = 96.23e6
+DOMINANT_KERNEL = "wf_extend"
 
 
 def wave_paths(job) -> int:
@@ -402,12 +404,13 @@ def run_native(args):
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "frac_at_loaded_clock": achieved / fp32_peak_loaded,
-                     "traffic": DOMINANT_DRAM_BYTES_PER_LAUNCH,
+                     "traffic": DOMINANT_DRAM_BYTES_PER_LAUNCH if dom == DOMINANT_KERNEL else None,
                      "hbm": ({"achieved_gbs": DOMINANT_DRAM_BYTES_PER_LAUNCH / (dom_ms / max(dom_launches, 1) / 1e3) / 1e9,
                               "peak_gbs": float(peaks.get("hbm_gbs") or 6800.0),
                               "frac": DOMINANT_DRAM_BYTES_PER_LAUNCH / (dom_ms / max(dom_launches, 1) / 1e3) / 1e9
-                                      / float(peaks.get("hbm_gbs") or 6800.0)}
-                             if DOMINANT_DRAM_BYTES_PER_LAUNCH else None),
+                                      / float(peaks.get("hbm_gbs") or 6800.0),
+                              "note": "ncu DRAM bytes per launch (cold caches) / in-bench launch time"}
+                             if DOMINANT_DRAM_BYTES_PER_LAUNCH and dom == DOMINANT_KERNEL else None),
                      "flops_per_launch": flops.get(dom, 0) / max(dom_launches, 1),
                      "launch_ms": dom_ms / max(dom_launches, 1),
                      "work_units_adjoint_pass": work,
