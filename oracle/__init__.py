@@ -102,7 +102,7 @@ def unflat(vec: np.ndarray, layout: np.ndarray) -> dict:
     return {n: vec[layout[i]:layout[i + 1]].copy() for i, n in enumerate(names)}
 
 
-MAT_I_FIELDS = 5
+MAT_I_FIELDS = 6
 MAT_F_FIELDS = 10
 
 
@@ -125,7 +125,8 @@ class OracleScene:
         tlight = arr(scene.tri_light, np.int32)
         sph = arr(scene.spheres, np.float64)
         smat = arr(scene.sph_mat, np.int32)
-        mi = arr([[m.type, m.albedo_tex, m.rough_tex, m.ior_index, m.sheet_index] for m in scene.materials], np.int32)
+        mi = arr([[m.type, m.albedo_tex, m.rough_tex, m.ior_index, m.sheet_index, m.normal_tex]
+                  for m in scene.materials], np.int32)
         mf = arr([[m.eta_re, m.eta_im, *m.t1, *m.t2, m.retard, m.emission] for m in scene.materials], np.float64)
         lights = arr(scene.lights, np.float64)
         texd = arr(scene.tex_desc, np.int64)

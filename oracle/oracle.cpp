@@ -338,15 +338,16 @@ double fresnel_unpolarized(double cos_i, double eta_i, double eta_t) {
 
 // GGX (Trowbridge-Reitz) distribution and separable Smith masking, Walter et
 // al. 2007, with alpha = roughness (isotropic).
-template <class T> T ggx_D(double cos_h, T alpha) {
-    if (cos_h <= 0.0) return T(0.0);
+// The cosines with the shading normal may carry derivatives too (normal maps): type C.
+template <class T, class C = double> T ggx_D(C cos_h, T alpha) {
+    if (val(cos_h) <= 0.0) return T(0.0);
     T a2 = alpha * alpha;
     T k = (a2 - 1.0) * (cos_h * cos_h) + 1.0;
     return a2 / (k * k * M_PI);
 }
-template <class T> T ggx_G1(double cos_v, double cos_vh, T alpha) {
-    if (cos_vh * cos_v <= 0.0) return T(0.0);
-    double t2 = (1.0 - cos_v * cos_v) / (cos_v * cos_v);
+template <class T, class C = double> T ggx_G1(C cos_v, double cos_vh, T alpha) {
+    if (cos_vh * val(cos_v) <= 0.0) return T(0.0);
+    C t2 = (1.0 - cos_v * cos_v) / (cos_v * cos_v);
     return T(2.0) / (sqrt(alpha * alpha * t2 + 1.0) + 1.0);
 }
 
@@ -356,7 +357,7 @@ enum { MAT_DIFFUSE = 0, MAT_SMOOTH_DIELECTRIC = 1, MAT_CONDUCTOR_GGX = 2, MAT_PL
 enum { FILTER_NONE = 0, FILTER_POLARIZER = 1, FILTER_QWP_POLARIZER = 2 };
 
 struct Mat {
-    int type, albedo_tex, rough_tex, ior_index, sheet_index;
+    int type, albedo_tex, rough_tex, ior_index, sheet_index, normal_tex;
     double eta_re, eta_im, t1[3], t2[3], retard, emission;
 };
 struct Light { V3 o, e1, e2, n; double area; };
@@ -570,6 +571,15 @@ template <class T> T tex_lookup(const Scene& s, const Params<T>& P, int tex, int
     return r;
 }
 
+// Shading normal of a vertex with a normal map (a material's tangent-space map, three
+// channels n_t = 2 c - 1 interpolated bilinearly): normalize(n_t.x T + n_t.y B + n_t.z N)
+// with N the geometric normal on the side of wo, T the triangle's dP/du made normal to N
+// and unit, B = N x T.  Without a normal map it is N.  Evaluated with parameters of type T
+// so that the normal map's texels carry derivatives.
+template <class T> struct N3 { T x, y, z; };
+struct Vtx;
+template <class T> N3<T> shading_normal(const Scene& s, const Params<T>& P, const Vtx& vt);
+
 // ============================================================ path sampling
 // One surface vertex of a sampled path.  Everything here is computed with the
 // detached parameters pi0: directions, lobe and reflect/refract choices, pdfs
@@ -577,11 +587,26 @@ template <class T> T tex_lookup(const Scene& s, const Params<T>& P, int tex, int
 // with the live parameters pi (T = double or Var).
 struct Vtx {
     V3 x, ng, n, wo; double tu, tv; int prim, mat;
+    V3 ngo, tan; bool nmap;   // geometric normal toward wo; normal map: tangent (unit, normal to ngo)
     bool emit_light; int light; double w_emit;
     bool nee; int nee_light; V3 wl; double nee_w;
     bool scatter; V3 wi; double pdf; int event; bool delta;
     double p_event; bool outside;
 };
+
+template <class T> N3<T> shading_normal(const Scene& s, const Params<T>& P, const Vtx& vt) {
+    if (!vt.nmap) return {T(vt.n.x), T(vt.n.y), T(vt.n.z)};
+    const Mat& m = s.mats[vt.mat];
+    T a = tex_lookup<T>(s, P, m.normal_tex, 0, vt.tu, vt.tv) * 2.0 - 1.0;
+    T b = tex_lookup<T>(s, P, m.normal_tex, 1, vt.tu, vt.tv) * 2.0 - 1.0;
+    T c = tex_lookup<T>(s, P, m.normal_tex, 2, vt.tu, vt.tv) * 2.0 - 1.0;
+    V3 N = vt.ngo, Tg = vt.tan, B = cross(N, Tg);
+    T x = a * Tg.x + b * B.x + c * N.x;
+    T y = a * Tg.y + b * B.y + c * N.y;
+    T z = a * Tg.z + b * B.z + c * N.z;
+    T l = sqrt(x * x + y * y + z * z);
+    return {x / l, y / l, z / l};
+}
 
 struct Path {
     std::vector<Vtx> vs;
@@ -690,6 +715,27 @@ Path sample_path(const Scene& s, const Params<double>& P0, const JobDesc& J, int
         }
         vt.n = dot(vt.ng, vt.wo) >= 0.0 ? vt.ng : -vt.ng;
         const Mat& m = s.mats[vt.mat];
+        vt.ngo = vt.n;
+        vt.nmap = false;
+        if (m.normal_tex >= 0 && h.prim < s.F()) {
+            // tangent of the triangle's (u, v) parametrization: dP/du
+            int f = h.prim, i0 = s.idx[3 * f], i1 = s.idx[3 * f + 1], i2 = s.idx[3 * f + 2];
+            V3 dp1 = s.v[i1] - s.v[i0], dp2 = s.v[i2] - s.v[i0];
+            double du1 = s.uv[2 * i1] - s.uv[2 * i0], dv1 = s.uv[2 * i1 + 1] - s.uv[2 * i0 + 1];
+            double du2 = s.uv[2 * i2] - s.uv[2 * i0], dv2 = s.uv[2 * i2 + 1] - s.uv[2 * i0 + 1];
+            double r = du1 * dv2 - du2 * dv1;
+            if (std::fabs(r) > 1e-20) {
+                V3 t = (dp1 * dv2 - dp2 * dv1) * (1.0 / r);
+                t = t - vt.ngo * dot(vt.ngo, t);
+                double tl = length(t);
+                if (tl > 1e-12) {
+                    vt.tan = t * (1.0 / tl);
+                    vt.nmap = true;
+                    N3<double> ns = shading_normal<double>(s, P0, vt);
+                    vt.n = V3{ns.x, ns.y, ns.z};
+                }
+            }
+        }
         // emission reached by BSDF sampling (MIS against light sampling)
         if (vt.light >= 0) {
             const Light& L = s.lights[vt.light];
@@ -724,8 +770,8 @@ Path sample_path(const Scene& s, const Params<double>& P0, const JobDesc& J, int
             V3 wl = dv * (1.0 / dist);
             double cl = -dot(L.n, wl), cx = dot(vt.n, wl);
             neeflag = 0;
-            if (cl > 0.0 && cx > 0.0) {
-                V3 o2 = vt.x + vt.n * s.eps;
+            if (cl > 0.0 && cx > 0.0 && dot(vt.ngo, wl) > 0.0) {
+                V3 o2 = vt.x + vt.ngo * s.eps;
                 V3 dd = y - o2;
                 double dl = length(dd);
                 if (!occluded(s, Ray{o2, dd * (1.0 / dl)}, dl * (1.0 - 1e-4))) {
@@ -760,7 +806,7 @@ Path sample_path(const Scene& s, const Params<double>& P0, const JobDesc& J, int
                 if (oh <= 0.0) ok = false;
                 else wi = hv * (2.0 * oh) - vt.wo;
             }
-            if (ok && dot(wi, vt.n) <= 0.0) ok = false;
+            if (ok && (dot(wi, vt.n) <= 0.0 || dot(wi, vt.ngo) <= 0.0)) ok = false;
             if (ok) { vt.pdf = bsdf_pdf(s, P0, vt, wi); if (!(vt.pdf > 0.0)) ok = false; }
         } else if (m.type == MAT_SMOOTH_DIELECTRIC) {
             double eta = P0.at(P0.lay.ior + m.ior_index);
@@ -821,8 +867,9 @@ M4<double> emitter_rot(const Light& L, V3 p) {
 template <class T> void bsdf_eval(const Scene& s, const Params<T>& P, const Vtx& vt, V3 wi, M4<T> f[3]) {
     const Mat& m = s.mats[vt.mat];
     for (int c = 0; c < 3; ++c) f[c] = M4<T>::zero();
-    double ci = dot(wi, vt.n), co = dot(vt.wo, vt.n);
-    if (ci <= 0.0 || co <= 0.0) return;
+    const N3<T> n = shading_normal<T>(s, P, vt);
+    T ci = n.x * wi.x + n.y * wi.y + n.z * wi.z, co = n.x * vt.wo.x + n.y * vt.wo.y + n.z * vt.wo.z;
+    if (val(ci) <= 0.0 || val(co) <= 0.0) return;
     T alb[3];
     for (int c = 0; c < 3; ++c) alb[c] = m.albedo_tex >= 0 ? tex_lookup<T>(s, P, m.albedo_tex, c, vt.tu, vt.tv) : T(1.0);
     if (m.type == MAT_DIFFUSE) {
@@ -831,10 +878,11 @@ template <class T> void bsdf_eval(const Scene& s, const Params<T>& P, const Vtx&
     }
     // specular microfacet lobe: D G F(h) / (4 cos_o cos_i) with frame rotations
     V3 h = normalize(vt.wo + wi);
-    double ch = dot(h, vt.n), oh = dot(vt.wo, h), ih = dot(wi, h);
+    T ch = n.x * h.x + n.y * h.y + n.z * h.z;
+    double oh = dot(vt.wo, h), ih = dot(wi, h);
     T al = tex_lookup<T>(s, P, m.rough_tex, 0, vt.tu, vt.tv);
-    T DG = ggx_D<T>(ch, al) * ggx_G1<T>(co, oh, al) * ggx_G1<T>(ci, ih, al);
-    T k = DG / (4.0 * co * ci);
+    T DG = ggx_D<T, T>(ch, al) * ggx_G1<T, T>(co, oh, al) * ggx_G1<T, T>(ci, ih, al);
+    T k = DG / (co * ci * 4.0);
     FresnelABCS<T> F;
     if (m.type == MAT_CONDUCTOR_GGX) F = fresnel_reflect<T>(ih, T(1.0), Cx<T>{T(m.eta_re), T(m.eta_im)});
     else F = fresnel_reflect<T>(ih, T(1.0), Cx<T>{P.at(P.lay.ior + m.ior_index), T(0.0)});
@@ -885,11 +933,17 @@ template <class T> VEval<T> eval_vertex(const Scene& s, const Params<T>& P, cons
         M4<double> R = emitter_rot(L, -vt.wl);
         M4<T> f[3];
         bsdf_eval<T>(s, P, vt, vt.wl, f);
+        // nee_w holds the cosine with the detached shading normal: a normal map makes it live
+        T wn = T(vt.nee_w);
+        if (vt.nmap) {
+            const N3<T> n = shading_normal<T>(s, P, vt);
+            wn = (n.x * vt.wl.x + n.y * vt.wl.y + n.z * vt.wl.z) * (vt.nee_w / dot(vt.n, vt.wl));
+        }
         for (int c = 0; c < 3; ++c) {
             S4<T> le = light_le(s, P, vt.nee_light, c);
             S4<T> lr = mvec(to_t<T>(R), le);
             S4<T> e = mvec(f[c], lr);
-            for (int i = 0; i < 4; ++i) r.E[c].s[i] = r.E[c].s[i] + e.s[i] * vt.nee_w;
+            for (int i = 0; i < 4; ++i) r.E[c].s[i] = r.E[c].s[i] + e.s[i] * wn;
         }
     }
     if (!vt.scatter) return r;
@@ -897,8 +951,9 @@ template <class T> VEval<T> eval_vertex(const Scene& s, const Params<T>& P, cons
     if (m.type == MAT_DIFFUSE || m.type == MAT_CONDUCTOR_GGX || m.type == MAT_PLASTIC_GGX) {
         M4<T> f[3];
         bsdf_eval<T>(s, P, vt, wi, f);
-        double w = dot(wi, vt.n) / vt.pdf;
-        for (int c = 0; c < 3; ++c) r.W[c] = mscale(f[c], T(w));
+        const N3<T> n = shading_normal<T>(s, P, vt);
+        T w = (n.x * wi.x + n.y * wi.y + n.z * wi.z) * (1.0 / vt.pdf);
+        for (int c = 0; c < 3; ++c) r.W[c] = mscale(f[c], w);
     } else if (m.type == MAT_SMOOTH_DIELECTRIC) {
         T eta = P.at(P.lay.ior + m.ior_index);
         T eo = vt.outside ? T(1.0) : eta, et = vt.outside ? eta : T(1.0);
@@ -955,7 +1010,7 @@ extern "C" {
 
 void* orc_scene_create(int64_t nv, const double* verts, const double* uvs, int64_t nf, const int32_t* tris,
                        const int32_t* tri_mat, const int32_t* tri_light, int64_t ns, const double* spheres,
-                       const int32_t* sph_mat, int64_t nm, const int32_t* mat_i /*nm x 5*/,
+                       const int32_t* sph_mat, int64_t nm, const int32_t* mat_i /*nm x 6*/,
                        const double* mat_f /*nm x 10*/, int64_t nl, const double* lights /*nl x 9*/,
                        int64_t nt, const int64_t* tex_desc /*nt x 4*/, int64_t nc, const double* cams /*nc x 10*/,
                        double eps) {
@@ -970,8 +1025,8 @@ void* orc_scene_create(int64_t nv, const double* verts, const double* uvs, int64
     s->smat.assign(sph_mat, sph_mat + ns);
     for (int64_t i = 0; i < nm; ++i) {
         Mat m;
-        m.type = mat_i[5 * i]; m.albedo_tex = mat_i[5 * i + 1]; m.rough_tex = mat_i[5 * i + 2];
-        m.ior_index = mat_i[5 * i + 3]; m.sheet_index = mat_i[5 * i + 4];
+        m.type = mat_i[6 * i]; m.albedo_tex = mat_i[6 * i + 1]; m.rough_tex = mat_i[6 * i + 2];
+        m.ior_index = mat_i[6 * i + 3]; m.sheet_index = mat_i[6 * i + 4]; m.normal_tex = mat_i[6 * i + 5];
         const double* f = mat_f + 10 * i;
         m.eta_re = f[0]; m.eta_im = f[1];
         m.t1[0] = f[2]; m.t1[1] = f[3]; m.t1[2] = f[4];

@@ -58,6 +58,7 @@ class Material:
     t1: tuple = (1.0, 0.0, 0.0)
     t2: tuple = (0.0, 1.0, 0.0)
     retard: float = 0.0
+    normal_tex: int = -1      # tangent-space normal map (3 channels, n = 2 c - 1), triangles with UVs
     emission: float = 0.0     # constant unpolarized emission (both sides), not differentiable
 
 
@@ -537,6 +538,53 @@ def deep_stack_scene(num_sheets: int = 85, width: int = 1280, height: int = 720,
     s.add_camera((0, 0, 0.95), (0, -0.1, -1), (0, 1, 0), 60.0)
     job = Job(camera=0, width=width, height=height, spp=spp, max_depth=depth, seed=0,
               filter=FILTER_POLARIZER, thetas=[0.0])
+    return s, job
+
+
+def bump_normal_map(res: int, seed: int, strength: float = 0.6) -> np.ndarray:
+    """Tangent-space normal map [res][res][3] of a seeded height field h(u, v) (a sum of six
+    periodic waves): n = normalize(-s dh/du, -s dh/dv, 1), stored as (n + 1) / 2."""
+    rng = np.random.default_rng(seed)
+    u = (np.arange(res) + 0.5) / res
+    U, V = np.meshgrid(u, u, indexing="xy")           # row = v, column = u
+    hu = np.zeros((res, res))
+    hv = np.zeros((res, res))
+    for _ in range(6):
+        ku, kv = rng.integers(1, 4, 2)
+        ph, a = rng.uniform(0, 2 * math.pi), rng.uniform(0.02, 0.05)
+        arg = 2 * math.pi * (ku * U + kv * V) + ph
+        hu += a * 2 * math.pi * ku * np.cos(arg)
+        hv += a * 2 * math.pi * kv * np.cos(arg)
+    n = np.stack([-strength * hu, -strength * hv, np.ones_like(hu)], -1)
+    n /= np.linalg.norm(n, axis=-1, keepdims=True)
+    return 0.5 * (n + 1.0)
+
+
+def normal_map_scene(width: int = 24, spp: int = 4, depth: int = 4, tex_res: int = 16, flat: bool = False,
+                     freq: int = 3) -> tuple[Scene, Job]:
+    """Normal-mapped pBRDFs: a rough-dielectric ground quad, a diffuse back wall and a
+    rough-conductor geodesic sphere (20*freq^2 triangles), each with its own differentiable
+    tangent-space normal map (seeded bumps; flat=True: n = (0, 0, 1) everywhere); a quad
+    light of radiance 8 and a camera polarizer at 20 deg."""
+    s = Scene()
+    maps = [np.full((tex_res, tex_res, 3), (0.5, 0.5, 1.0)) if flat else bump_normal_map(tex_res, 40 + k)
+            for k in range(3)]
+    tn = [s.add_texture(m_, differentiable=True) for m_ in maps]
+    tr = s.add_const_texture([0.3])
+    ta = s.add_const_texture([0.6, 0.5, 0.4])
+    ground = s.add_material(Material(MAT_PLASTIC_GGX, albedo_tex=ta, rough_tex=tr, ior_index=s.add_ior(1.5),
+                                     normal_tex=tn[0]))
+    wall = s.add_material(Material(MAT_DIFFUSE, albedo_tex=ta, normal_tex=tn[1]))
+    cond = s.add_material(Material(MAT_CONDUCTOR_GGX, albedo_tex=ta, rough_tex=tr, eta_re=0.2, eta_im=3.0,
+                                   normal_tex=tn[2]))
+    s.add_quad((-2, -1, 2), (4, 0, 0), (0, 0, -4), ground)     # normal +y
+    s.add_quad((-2, -1, -2), (4, 0, 0), (0, 3, 0), wall)       # normal +z
+    v, f, uv = displaced_sphere(freq, 0.0, seed=1, radius=0.6, center=(0.0, -0.3, 0.0))
+    s.add_mesh(v, f, cond, uv)
+    s.add_light((-0.7, 2.0, -0.7), (1.4, 0, 0), (0, 0, 1.4), 8.0)
+    s.add_camera((0.0, 0.6, 3.5), (0.0, -0.3, 0.0), (0, 1, 0), 40.0)
+    job = Job(camera=0, width=width, height=width, spp=spp, max_depth=depth, seed=0,
+              filter=FILTER_POLARIZER, thetas=[math.radians(20.0)])
     return s, job
 
 
