@@ -78,6 +78,12 @@ typedef struct {
     int32_t rough_tex;     /* 1-channel GGX roughness texture (alpha), required for GGX types */
     int32_t ior_index;     /* index into params.ior (dielectrics), -1 otherwise */
     int32_t sheet_index;   /* index into params.sheet (sheet axis angle), -1 otherwise */
+    int32_t normal_tex;    /* 3-channel tangent-space normal map, n = 2 c - 1, or -1; diffuse and GGX
+                              types on triangles with UVs only.  Shading normal: normalize(n.x T +
+                              n.y B + n.z N), N the geometric normal facing the viewer, T the
+                              triangle's dP/du made normal to N, B = N x T.  Its texels are
+                              differentiated; the material's albedo, roughness and index of
+                              refraction then are not (their dual-number slots carry n). */
     float eta_re, eta_im;  /* conductor complex index of refraction (constant) */
     float t1[3], t2[3];    /* sheet axis basis: axis = cos(a) t1 + sin(a) t2 */
     float retard;          /* retarder sheet retardance (radians) */

@@ -21,7 +21,7 @@ c_i32, c_i64, c_u64, c_f32, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint
 
 class Material(ctypes.Structure):
     _fields_ = [("type", c_i32), ("albedo_tex", c_i32), ("rough_tex", c_i32), ("ior_index", c_i32),
-                ("sheet_index", c_i32), ("eta_re", c_f32), ("eta_im", c_f32), ("t1", c_f32 * 3), ("t2", c_f32 * 3),
+                ("sheet_index", c_i32), ("normal_tex", c_i32), ("eta_re", c_f32), ("eta_im", c_f32), ("t1", c_f32 * 3), ("t2", c_f32 * 3),
                 ("retard", c_f32), ("emission", c_f32)]
 
 

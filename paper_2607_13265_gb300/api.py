@@ -136,7 +136,8 @@ class GpuScene:
         smat = arr(scene.sph_mat, np.int32)
         mats = (L.Material * len(scene.materials))()
         for i, m in enumerate(scene.materials):
-            mats[i] = L.Material(m.type, m.albedo_tex, m.rough_tex, m.ior_index, m.sheet_index, m.eta_re, m.eta_im,
+            mats[i] = L.Material(m.type, m.albedo_tex, m.rough_tex, m.ior_index, m.sheet_index, m.normal_tex,
+                                 m.eta_re, m.eta_im,
                                  (ctypes.c_float * 3)(*m.t1), (ctypes.c_float * 3)(*m.t2), m.retard, m.emission)
         lights = arr(scene.lights, np.float32)
         texd = arr(scene.tex_desc, np.int64)

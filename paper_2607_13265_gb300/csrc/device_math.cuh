@@ -219,15 +219,16 @@ template <class T> __device__ __forceinline__ ABCS<T> fresnel_transmit(float cos
 }
 
 // ------------------------------------------------------------------ GGX (Walter et al. 2007)
-template <class T> __device__ __forceinline__ T ggx_D(float cos_h, T alpha) {
-    if (cos_h <= 0.0f) return T(0.0f);
+// the cosines with the shading normal carry derivatives under a normal map: type C
+template <class T, class C = float> __device__ __forceinline__ T ggx_D(C cos_h, T alpha) {
+    if (val(cos_h) <= 0.0f) return T(0.0f);
     T a2 = alpha * alpha;
     T k = (a2 - 1.0f) * (cos_h * cos_h) + 1.0f;
     return a2 / (k * k * kPi);
 }
-template <class T> __device__ __forceinline__ T ggx_G1(float cos_v, float cos_vh, T alpha) {
-    if (cos_vh * cos_v <= 0.0f) return T(0.0f);
-    float t2 = (1.0f - cos_v * cos_v) / (cos_v * cos_v);
+template <class T, class C = float> __device__ __forceinline__ T ggx_G1(C cos_v, float cos_vh, T alpha) {
+    if (cos_vh * val(cos_v) <= 0.0f) return T(0.0f);
+    C t2 = (1.0f - cos_v * cos_v) / (cos_v * cos_v);
     return T(2.0f) / (tsqrt(alpha * alpha * t2 + 1.0f) + 1.0f);
 }
 

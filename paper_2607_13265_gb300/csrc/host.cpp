@@ -520,7 +520,7 @@ dppt_status dppt_scene_upload(dppt_ctx* ctx, const dppt_scene_desc* d, dppt_scen
         const dppt_material& m = d->materials[i];
         DMat& o = mats[i];
         o.type = m.type; o.albedo_tex = m.albedo_tex; o.rough_tex = m.rough_tex; o.ior_index = m.ior_index;
-        o.sheet_index = m.sheet_index; o.eta_re = m.eta_re; o.eta_im = m.eta_im;
+        o.sheet_index = m.sheet_index; o.normal_tex = m.normal_tex; o.eta_re = m.eta_re; o.eta_im = m.eta_im;
         for (int k = 0; k < 3; ++k) { o.t1[k] = m.t1[k]; o.t2[k] = m.t2[k]; }
         o.retard = m.retard; o.emission = m.emission;
         if (m.type < DPPT_MAT_DIFFUSE || m.type > DPPT_MAT_EMITTER) return fail(ctx, DPPT_ERR_INVALID_ARG, "unknown material type");
@@ -532,7 +532,19 @@ dppt_status dppt_scene_upload(dppt_ctx* ctx, const dppt_scene_desc* d, dppt_scen
         bool sheet = m.type == DPPT_MAT_POLARIZER_SHEET || m.type == DPPT_MAT_RETARDER_SHEET;
         if (sheet && (m.sheet_index < 0 || m.sheet_index >= d->num_sheets)) return fail(ctx, DPPT_ERR_INVALID_ARG, "sheet_index out of range");
         if (!(m.emission >= 0.0f)) return fail(ctx, DPPT_ERR_INVALID_ARG, "negative emission");
+        if (m.normal_tex != -1) {
+            if (m.normal_tex < 0 || m.normal_tex >= T || tex[m.normal_tex].ch < 3)
+                return fail(ctx, DPPT_ERR_INVALID_ARG, "normal_tex must be a 3-channel texture");
+            if (!(m.type == DPPT_MAT_DIFFUSE || ggx))
+                return fail(ctx, DPPT_ERR_INVALID_ARG, "normal maps are for diffuse and GGX materials");
+            if (!d->uvs) return fail(ctx, DPPT_ERR_INVALID_ARG, "normal maps need triangle UVs");
+        }
     }
+    bool any_normal_map = false;
+    for (int i = 0; i < M; ++i) any_normal_map = any_normal_map || mats[i].normal_tex >= 0;
+    for (int64_t i = 0; i < Sn; ++i)
+        if (mats[d->sphere_material[i]].normal_tex >= 0)
+            return fail(ctx, DPPT_ERR_INVALID_ARG, "normal maps are for triangles, not spheres");
     std::vector<DLight> lights(L);
     for (int l = 0; l < L; ++l) {
         const float* q = d->lights + 9 * l;
@@ -621,6 +633,24 @@ dppt_status dppt_scene_upload(dppt_ctx* ctx, const dppt_scene_desc* d, dppt_scen
                 tri_uv[6 * t + 2 * k] = d->uvs[2 * d->triangles[3 * t + k]];
                 tri_uv[6 * t + 2 * k + 1] = d->uvs[2 * d->triangles[3 * t + k] + 1];
             }
+    // dP/du of every triangle's (u, v) parametrization, for normal maps (zero if degenerate)
+    std::vector<float> tri_tan;
+    if (any_normal_map) {
+        tri_tan.assign(3 * F, 0.0f);
+        for (int64_t t = 0; t < F; ++t) {
+            const int i0 = d->triangles[3 * t], i1 = d->triangles[3 * t + 1], i2 = d->triangles[3 * t + 2];
+            double dp1[3], dp2[3];
+            for (int k = 0; k < 3; ++k) {
+                dp1[k] = (double)d->vertices[3 * i1 + k] - d->vertices[3 * i0 + k];
+                dp2[k] = (double)d->vertices[3 * i2 + k] - d->vertices[3 * i0 + k];
+            }
+            const double du1 = (double)d->uvs[2 * i1] - d->uvs[2 * i0], dv1 = (double)d->uvs[2 * i1 + 1] - d->uvs[2 * i0 + 1];
+            const double du2 = (double)d->uvs[2 * i2] - d->uvs[2 * i0], dv2 = (double)d->uvs[2 * i2 + 1] - d->uvs[2 * i0 + 1];
+            const double r = du1 * dv2 - du2 * dv1;
+            if (std::fabs(r) > 1e-20)
+                for (int k = 0; k < 3; ++k) tri_tan[3 * t + k] = (float)((dp1[k] * dv2 - dp2[k] * dv1) / r);
+        }
+    }
 
     dppt_scene* s = new dppt_scene();
     s->ctx = ctx;
@@ -632,6 +662,7 @@ dppt_status dppt_scene_upload(dppt_ctx* ctx, const dppt_scene_desc* d, dppt_scen
               upload(s, d->tri_material, (size_t)F, &D.tri_mat, e) &&
               upload(s, d->tri_light, (size_t)F, &D.tri_light, e) &&
               upload(s, tri_uv.data(), tri_uv.size(), &D.tri_uv, e) &&
+              upload(s, tri_tan.data(), tri_tan.size(), &D.tri_tan, e) &&
               upload(s, reinterpret_cast<const float4*>(d->spheres), (size_t)Sn, &D.spheres, e) &&
               upload(s, d->sphere_material, (size_t)Sn, &D.sph_mat, e) &&
               upload(s, mats.data(), mats.size(), &D.mats, e) &&

@@ -17,7 +17,7 @@ constexpr int kMaxDepth = 128;
 #endif      // surface vertices per path (largest cache bucket)
 
 struct DMat {
-    int type, albedo_tex, rough_tex, ior_index, sheet_index;
+    int type, albedo_tex, rough_tex, ior_index, sheet_index, normal_tex;
     float eta_re, eta_im, t1[3], t2[3], retard, emission;
 };
 struct DLight { float o[3], e1[3], e2[3], n[3], area; };
@@ -38,6 +38,7 @@ struct DScene {
     const int* tri_mat;     // original triangle order
     const int* tri_light;
     const float* tri_uv;    // [F][6]
+    const float* tri_tan;   // [F][3] dP/du per triangle (original order), or null without normal maps
     const float4* spheres;
     const int* sph_mat;
     int num_spheres;

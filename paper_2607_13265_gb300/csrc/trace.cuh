@@ -16,6 +16,7 @@
 //    call site of walk_step -- and accumulates a^T dE_i + a^T dW_i L[i+1] with
 //    dual numbers before a <- a^T W_i.  No Mueller matrix is inverted.
 #include <cfloat>
+#include <type_traits>
 
 #include "device_math.cuh"
 #include "internal.h"
@@ -448,16 +449,64 @@ __device__ __forceinline__ f3 s_axis(f3 a, f3 b) {
     return sl > 1e-12f ? sx * (1.0f / sl) : onb_t1(a);
 }
 
-// pBRDF value f(wo, wi) without the cosine, as a compact operator.
+// Normal maps: the shading normal normalize(n.x T + n.y B + n.z N) of a triangle vertex,
+// n = 2 c - 1 from the material's tangent-space map (bilinear), N the geometric normal on
+// the side of wo, T the triangle's dP/du made normal to N and unit, B = N x T.  For T = D3
+// the three components of n are the dual-number slots (a normal-mapped material's texel
+// derivatives replace its albedo / roughness / index slots).  Returns false, leaving n,
+// when the vertex has no usable normal map.
+__device__ __forceinline__ bool nmap_frame(const DScene& S, const DMat& m, const VCtx& vc, f3& N, f3& Tg, f3& B) {
+    if (m.normal_tex < 0 || vc.prim >= S.num_tris || !S.tri_tan) return false;
+    N = dot(vc.ng, vc.wo) >= 0.0f ? vc.ng : -vc.ng;
+    f3 t = ld3(S.tri_tan + 3 * (long long)vc.prim);
+    t = t - N * dot(N, t);
+    const float tl = len(t);
+    if (!(tl > 1e-12f)) return false;
+    Tg = t * (1.0f / tl);
+    B = cross(N, Tg);
+    return true;
+}
 template <class T>
+__device__ __forceinline__ bool shading_normal(const DScene& S, const DParams& P, const DMat& m, const VCtx& vc,
+                                               T n[3]) {
+    f3 N, Tg, B;
+    if (!nmap_frame(S, m, vc, N, Tg, B)) return false;
+    const Taps tp = tex_taps(S.tex[m.normal_tex], vc.tu, vc.tv);
+    T a[3];
+    for (int c = 0; c < 3; ++c) a[c] = seeded<T>(2.0f * tex_value(P.tex, tp, c) - 1.0f, c);
+    T x = a[0] * Tg.x + a[1] * B.x + a[2] * N.x;
+    T y = a[0] * Tg.y + a[1] * B.y + a[2] * N.y;
+    T z = a[0] * Tg.z + a[1] * B.z + a[2] * N.z;
+    T l = tsqrt(x * x + y * y + z * z);
+    n[0] = x / l; n[1] = y / l; n[2] = z / l;
+    return true;
+}
+// the vertex's detached shading normal into vc.n (no-op without a normal map)
+__device__ __forceinline__ void apply_normal_map(const DScene& S, const DParams& P, VCtx& vc) {
+    const DMat m = S.mats[vc.mat];
+    float n[3];
+    if (m.normal_tex >= 0 && shading_normal<float>(S, P, m, vc, n)) vc.n = f3{n[0], n[1], n[2]};
+}
+
+// pBRDF value f(wo, wi) without the cosine, as a compact operator.  NM: the shading normal
+// nT carries derivatives (normal map); the material's own parameters are then constants.
+template <class T, bool NM = false>
 __device__ __forceinline__ void bsdf_compact(const DScene& S, const DParams& P, const DMat& m, const VCtx& vc, f3 wi,
-                                             Compact<T>& f) {
+                                             Compact<T>& f, const T* nT = nullptr) {
+    using C = typename std::conditional<NM, T, float>::type;
     compact_zero(f);
-    float ci = dot(wi, vc.n), co = dot(vc.wo, vc.n);
-    if (ci <= 0.0f || co <= 0.0f) return;
+    C ci, co;
+    if constexpr (NM) {
+        ci = nT[0] * wi.x + nT[1] * wi.y + nT[2] * wi.z;
+        co = nT[0] * vc.wo.x + nT[1] * vc.wo.y + nT[2] * vc.wo.z;
+    } else {
+        ci = dot(wi, vc.n);
+        co = dot(vc.wo, vc.n);
+    }
+    if (val(ci) <= 0.0f || val(co) <= 0.0f) return;
     T alb[3];
     if (m.albedo_tex >= 0) {
-        for (int c = 0; c < 3; ++c) alb[c] = seeded<T>(vc.alb[c], 2);
+        for (int c = 0; c < 3; ++c) alb[c] = seeded<T>(vc.alb[c], NM ? -1 : 2);
     } else {
         for (int c = 0; c < 3; ++c) alb[c] = T(1.0f);
     }
@@ -466,15 +515,18 @@ __device__ __forceinline__ void bsdf_compact(const DScene& S, const DParams& P, 
         return;
     }
     f3 h = normalize(vc.wo + wi);
-    float ch = dot(h, vc.n), oh = dot(vc.wo, h), ih = dot(wi, h);
-    T al = seeded<T>(vc.alpha, 0);
-    T k = ggx_D<T>(ch, al) * ggx_G1<T>(co, oh, al) * ggx_G1<T>(ci, ih, al) / (4.0f * co * ci);
+    C ch;
+    if constexpr (NM) ch = nT[0] * h.x + nT[1] * h.y + nT[2] * h.z;
+    else ch = dot(h, vc.n);
+    const float oh = dot(vc.wo, h), ih = dot(wi, h);
+    T al = seeded<T>(vc.alpha, NM ? -1 : 0);
+    T k = ggx_D<T, C>(ch, al) * ggx_G1<T, C>(co, oh, al) * ggx_G1<T, C>(ci, ih, al) / (co * ci * 4.0f);
     ABCS<T> F;
     if (m.type == DPPT_MAT_CONDUCTOR_GGX) {
         ABCS<float> Ff = fresnel_reflect<float>(ih, 1.0f, Cx<float>{m.eta_re, m.eta_im});
         F = {T(Ff.A), T(Ff.B), T(Ff.C), T(Ff.S)};
     } else {
-        F = fresnel_reflect_real<T>(ih, T(1.0f), seeded<T>(__ldg(P.ior + m.ior_index), 1));
+        F = fresnel_reflect_real<T>(ih, T(1.0f), seeded<T>(__ldg(P.ior + m.ior_index), NM ? -1 : 1));
     }
     f3 sax = s_axis(vc.wo, h);
     Rot<float> ri = rot_between(-wi, onb_t1(-wi), sax);
@@ -487,7 +539,7 @@ __device__ __forceinline__ void bsdf_compact(const DScene& S, const DParams& P, 
     }
 }
 
-template <class T> __device__ __forceinline__ void compact_scale(Compact<T>& W, float s) {
+template <class T, class U> __device__ __forceinline__ void compact_scale(Compact<T>& W, U s) {
     for (int c = 0; c < 3; ++c) { W.A[c] = W.A[c] * s; W.B[c] = W.B[c] * s; W.C[c] = W.C[c] * s; W.S[c] = W.S[c] * s; W.D[c] = W.D[c] * s; }
 }
 
@@ -508,8 +560,9 @@ __device__ __forceinline__ DMat load_mat(const DScene& S, int mat) {
     return m;
 }
 
-// E_v (per channel, float) and W_v (compact, T) for one vertex.
-template <class T, int MT = -1>
+// E_v (per channel, float) and W_v (compact, T) for one vertex.  NM = false compiles the
+// normal-map path out (kernels launched for scenes without normal maps).
+template <class T, int MT = -1, bool NM = true>
 __device__ void eval_vertex(const DScene& S, const DParams& P, const VCtx& vc, float E[3][4], Compact<T>& W,
                             Compact<T>* fnee) {
     const DMat m = load_mat<MT>(S, vc.mat);
@@ -526,11 +579,27 @@ __device__ void eval_vertex(const DScene& S, const DParams& P, const VCtx& vc, f
     }
     if (m.emission > 0.0f)
         for (int c = 0; c < 3; ++c) E[c][0] += m.emission;
+    // a normal map's shading normal with derivatives (dual numbers only: detached values
+    // are already in vc.n)
+    T nT[3];
+    bool nm = false;
+    if constexpr (NM && sizeof(T) != sizeof(float))
+        if (m.normal_tex >= 0) nm = shading_normal<T>(S, P, m, vc, nT);
     if (vc.nee) {
         DLight L = load_light(S, vc.nee_light);
         Rot<float> R = emitter_rot(L, -vc.wl);
         Compact<T> f;
-        bsdf_compact<T>(S, P, m, vc, vc.wl, f);
+        if constexpr (NM) {
+            if (nm) {
+                // nee_w holds the cosine with the detached shading normal: the live one replaces it
+                bsdf_compact<T, true>(S, P, m, vc, vc.wl, f, nT);
+                compact_scale(f, (nT[0] * vc.wl.x + nT[1] * vc.wl.y + nT[2] * vc.wl.z) * (1.0f / dot(vc.n, vc.wl)));
+            } else {
+                bsdf_compact<T>(S, P, m, vc, vc.wl, f);
+            }
+        } else {
+            bsdf_compact<T>(S, P, m, vc, vc.wl, f);
+        }
         Compact<float> fv;
         if constexpr (sizeof(T) == sizeof(float)) fv = *reinterpret_cast<Compact<float>*>(&f);
         else fv = compact_value(*reinterpret_cast<Compact<D3>*>(&f));
@@ -548,8 +617,18 @@ __device__ void eval_vertex(const DScene& S, const DParams& P, const VCtx& vc, f
     if (!vc.scatter) return;
     f3 wi = vc.wi;
     if (m.type == DPPT_MAT_DIFFUSE || m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX) {
-        bsdf_compact<T>(S, P, m, vc, wi, W);
-        compact_scale(W, dot(wi, vc.n) / vc.pdf);
+        if constexpr (NM) {
+            if (nm) {
+                bsdf_compact<T, true>(S, P, m, vc, wi, W, nT);
+                compact_scale(W, (nT[0] * wi.x + nT[1] * wi.y + nT[2] * wi.z) * (1.0f / vc.pdf));
+            } else {
+                bsdf_compact<T>(S, P, m, vc, wi, W);
+                compact_scale(W, dot(wi, vc.n) / vc.pdf);
+            }
+        } else {
+            bsdf_compact<T>(S, P, m, vc, wi, W);
+            compact_scale(W, dot(wi, vc.n) / vc.pdf);
+        }
     } else if (m.type == DPPT_MAT_SMOOTH_DIELECTRIC) {
         T eta = seeded<T>(__ldg(P.ior + m.ior_index), 1);
         T eo = vc.outside ? T(1.0f) : eta, et = vc.outside ? eta : T(1.0f);
@@ -644,6 +723,7 @@ struct Shade {
     bool ok, terminal, delta;
 };
 
+template <bool NM = true>
 __device__ __forceinline__ void walk_shade(const DScene& S, const DParams& P, const DJob& J, unsigned long long pid,
                                            const Walk& w, const HitRec& h, VCtx& vc, NeePending& ne, Shade& sh) {
     const int nL = S.num_lights;
@@ -673,7 +753,9 @@ __device__ __forceinline__ void walk_shade(const DScene& S, const DParams& P, co
         vc.light = -1;
     }
     vc.n = dot(vc.ng, vc.wo) >= 0.0f ? vc.ng : -vc.ng;
+    const f3 ngo = vc.n;   // geometric normal on the side of wo
     const DMat m = S.mats[vc.mat];
+    if (NM && m.normal_tex >= 0) apply_normal_map(S, P, vc);
     if (vc.light >= 0) {
         DLight L = load_light(S, vc.light);
         float cl = dot(ld3(L.n), vc.wo);
@@ -707,8 +789,8 @@ __device__ __forceinline__ void walk_shade(const DScene& S, const DParams& P, co
         f3 wl = dv * (1.0f / dist);
         float cl = -dot(ld3(L.n), wl), cx = dot(vc.n, wl);
         ne.state = 0;
-        if (cl > 0.0f && cx > 0.0f) {
-            f3 o2 = vc.x + vc.n * S.eps;
+        if (cl > 0.0f && cx > 0.0f && dot(ngo, wl) > 0.0f) {
+            f3 o2 = vc.x + ngo * S.eps;
             f3 dd = y - o2;
             float dl = len(dd);
             ne.o2 = o2;
@@ -743,7 +825,7 @@ __device__ __forceinline__ void walk_shade(const DScene& S, const DParams& P, co
             if (oh <= 0.0f) ok = false;
             else wi = hv * (2.0f * oh) - vc.wo;
         }
-        if (ok && dot(wi, vc.n) <= 0.0f) ok = false;
+        if (ok && (dot(wi, vc.n) <= 0.0f || dot(wi, ngo) <= 0.0f)) ok = false;
         if (ok) { sh.pdf = bsdf_pdf(S, P, m, vc, wi); if (!(sh.pdf > 0.0f)) ok = false; }
     } else if (m.type == DPPT_MAT_SMOOTH_DIELECTRIC) {
         float eta = __ldg(P.ior + m.ior_index);
@@ -894,7 +976,7 @@ struct GlobalCache {
 // The replayed vertex's local vector-Jacobian product: J_c = a_c^T (E_c + W_c L_c) with
 // dual numbers (W and the NEE operator f from eval_vertex<D3>, Ln the suffix L[v+1]),
 // scattered into the gradients; then the adjoint row advances, a^T <- a^T W_v.
-template <int MT = -1>
+template <int MT = -1, bool NM = true>
 __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, const DGrads& G_, float* sgrad,
                                            const VCtx& vc, const Compact<D3>& W, const Compact<D3>& f,
                                            const float Ln[3][4], float a[3][4]) {
@@ -949,14 +1031,23 @@ __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, 
             }
         }
     }
-    // parameter scatter
-    if (m.type == DPPT_MAT_SMOOTH_DIELECTRIC || m.type == DPPT_MAT_PLASTIC_GGX) {
+    // parameter scatter (a normal-mapped vertex's slots belong to its normal map)
+    f3 nN, nT, nB;
+    const bool nm = NM && m.normal_tex >= 0 && nmap_frame(*S, m, vc, nN, nT, nB);
+    if (!nm && (m.type == DPPT_MAT_SMOOTH_DIELECTRIC || m.type == DPPT_MAT_PLASTIC_GGX)) {
         if (g_eta != 0.0f) atomicAdd(sgrad + m.ior_index, g_eta);
     }
     if (m.type == DPPT_MAT_POLARIZER_SHEET || m.type == DPPT_MAT_RETARDER_SHEET) {
         if (g_slot0 != 0.0f) atomicAdd(sgrad + S->num_ior + m.sheet_index, g_slot0);
     }
-    if (G->tex) {
+    if (nm) {
+        // normal map: the slots are the derivatives w.r.t. the three components of n = 2 c - 1
+        if (G->tex && S->tex[m.normal_tex].pad) {
+            const Taps tp = tex_taps(S->tex[m.normal_tex], vc.tu, vc.tv);
+            const float gn[3] = {2.0f * g_slot0, 2.0f * g_eta, 2.0f * (g_alb[0] + g_alb[1] + g_alb[2])};
+            scatter_taps<3>(G->tex, tp, gn, 3);
+        }
+    } else if (G->tex) {
         if ((m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.rough_tex].pad) {
             Taps tp = tex_taps(S->tex[m.rough_tex], vc.tu, vc.tv);
             scatter_taps<1>(G->tex, tp, &g_slot0, 1);
@@ -979,7 +1070,7 @@ __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, 
 // registers); the backward fold overwrites E_v with the suffix L[v] where the replay
 // will read it (the adjoint's vertices 1..n-1).  Pass 1 (adjoint only) replays the
 // vertex with dual numbers.
-template <class Cache, int MT = -1>
+template <class Cache, int MT = -1, bool NM = true>
 struct PathVis {
     const DScene* S;
     const DParams* P;
@@ -996,7 +1087,7 @@ struct PathVis {
             if (n >= C.cap) return;
             float E[3][4];
             Compact<float> W;
-            eval_vertex<float, MT>(*S, *P, vc, E, W, nullptr);
+            eval_vertex<float, MT, NM>(*S, *P, vc, E, W, nullptr);
             if (!vc.scatter) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
@@ -1062,7 +1153,7 @@ struct PathVis {
     __device__ void replay_vertex(const VCtx& vc) {
         float E[3][4];
         Compact<D3> W, f;
-        eval_vertex<D3, MT>(*S, *P, vc, E, W, &f);
+        eval_vertex<D3, MT, NM>(*S, *P, vc, E, W, &f);
         float Ln[3][4];
         if (i + 1 < n) {
 #pragma unroll
@@ -1071,7 +1162,7 @@ struct PathVis {
 #pragma unroll
             for (int k = 0; k < 12; ++k) Ln[k >> 2][k & 3] = 0.0f;
         }
-        replay_vjp<MT>(*S, *P, *G, sgrad, vc, W, f, Ln, a);
+        replay_vjp<MT, NM>(*S, *P, *G, sgrad, vc, W, f, Ln, a);
     }
 };
 

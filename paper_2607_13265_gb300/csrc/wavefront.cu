@@ -161,6 +161,7 @@ k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
     }
 }
 
+template <bool NM>
 __global__ void k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfState W, WfLists L) {
     const int n0 = L.count[0], n = n0 + L.count[1];
     const int stride = gridDim.x * blockDim.x;
@@ -183,7 +184,7 @@ __global__ void k_wf_shade(const DScene S, const DParams P, const __grid_constan
         VCtx vc;
         NeePending ne;
         Shade sh;
-        walk_shade(S, P, T.job[m.job], pid, w, h, vc, ne, sh);
+        walk_shade<NM>(S, P, T.job[m.job], pid, w, h, vc, ne, sh);
         put_vertex(W.vtx + q, vc, ne, sh);
         if (ne.state == 1) {
             W.ray[q] = WfRay{make_float4(ne.o2.x, ne.o2.y, ne.o2.z, ne.tmax), make_float4(ne.dir.x, ne.dir.y, ne.dir.z, 0.f)};
@@ -224,7 +225,7 @@ __device__ __forceinline__ void flush_scalars(const DScene& S, const DGrads& G, 
 // Per-vertex action of one pass.  PHASE 0 (cache pass): cache E_i / W_i; at the
 // end of the walk fold the cache, store the path's raw Stokes value and, for the
 // adjoint (MODE 1), start the replay.  PHASE 1: the replay (MODE 1 only).
-template <int MODE, int PHASE>
+template <int MODE, int PHASE, bool NM>
 __global__ void __launch_bounds__(128, PHASE == 1 ? DPPT_WF_REPLAY_MIN_BLOCKS : DPPT_WF_CACHE_MIN_BLOCKS)
 k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_constant__ JobTable T, WfState W, WfLists L,
             unsigned* sig) {
@@ -242,7 +243,7 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
         const DJob& J = T.job[m.job];
         Walk w;
         get_walk(W.walk + q, w);
-        PathVis<GlobalCache> vis;
+        PathVis<GlobalCache, -1, NM> vis;
         vis.S = &S; vis.P = &P; vis.G = &G; vis.sgrad = sgrad;
         vis.C.base = W.cache; vis.C.Q = W.Q; vis.C.q = q; vis.C.cap = W.cap;
         vis.n = (m.pni >> 8) & 0xff; vis.i = (m.pni >> 16) & 0xff; vis.phase = PHASE;
@@ -259,7 +260,10 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
         NeePending ne;
         Shade sh;
         bool cont = false;
-        if (get_vertex(W.vtx + q, w, vc, ne, sh)) cont = walk_finish(S, P, w, vc, ne, W.visible[q] != 0, sh, vis);
+        if (get_vertex(W.vtx + q, w, vc, ne, sh)) {
+            if (NM) apply_normal_map(S, P, vc);
+            cont = walk_finish(S, P, w, vc, ne, W.visible[q] != 0, sh, vis);
+        }
         bool done = false;
         int phase = PHASE;
         if (cont) {
@@ -389,6 +393,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long npix = (long long)J.W * J.H;
     const long long pix_per_wave = std::max(1LL, Q / J.spp);
+    const bool nmaps = S.tri_tan != nullptr;   // the scene has normal maps: kernels with that path
     const int passes = mode == 1 ? 2 : 1;
     const size_t smem = mode == 1 ? sizeof(float) * (size_t)(S.num_ior + S.num_sheets + 12 * S.num_lights) : 0;
     for (long long pix0 = 0; pix0 < npix; pix0 += pix_per_wave) {
@@ -412,18 +417,25 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
             k_wf_extend<<<grid, block, 0, st>>>(S, W, L, status);
             log->end(tok, st);
             tok = log->begin(kStageWfShade, st);
-            k_wf_shade<<<grid, block, 0, st>>>(S, P, T, W, L);
+            if (nmaps) k_wf_shade<true><<<grid, block, 0, st>>>(S, P, T, W, L);
+            else k_wf_shade<false><<<grid, block, 0, st>>>(S, P, T, W, L);
             log->end(tok, st);
             tok = log->begin(kStageWfShadow, st);
             k_wf_shadow<<<grid, block, 0, st>>>(S, W, L, status);
             log->end(tok, st);
             tok = log->begin(kStageWfCache, st);
-            if (mode == 0) k_wf_finish<0, 0><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
-            else k_wf_finish<1, 0><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+            if (mode == 0) {
+                if (nmaps) k_wf_finish<0, 0, true><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+                else k_wf_finish<0, 0, false><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+            } else {
+                if (nmaps) k_wf_finish<1, 0, true><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+                else k_wf_finish<1, 0, false><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+            }
             log->end(tok, st);
             if (mode == 1) {
                 tok = log->begin(kStageWfReplay, st);
-                k_wf_finish<1, 1><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                if (nmaps) k_wf_finish<1, 1, true><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                else k_wf_finish<1, 1, false><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
                 log->end(tok, st);
             }
             tok = log->begin(kStageWfSwap, st);
