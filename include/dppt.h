@@ -256,12 +256,21 @@ dppt_status dppt_autotune(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job
  * checkpoint.  gamma = 0 never takes the scalar route; eps = +inf never
  * inverts (then the result is exact).  k > 1 runs on the grid and persistent
  * adjoint schedules only (render_adjoint returns DPPT_ERR_UNSUPPORTED with the
- * wavefront schedule).  Errors: INVALID_ARG for another k, a negative or NaN
- * threshold. */
+ * wavefront schedule).  method DPPT_REPLAY_PPRB selects instead the basic
+ * polarized PRB the paper analyses and rejects (Sec. 4.1-4.2): no cache; the
+ * replay recovers L[v+1] = (W_v + u_v I)^-1 (L[v] - E_v) with noise u_v ~
+ * N(0, sigma) that also enters the primal throughput (Philox key (seed ^
+ * 0x5bd1e995) ^ 3 * 0x9E3779B97F4A7C15 and the job's stream, counter (path,
+ * vertex), Box-Muller).  It is exact only where every factor is invertible;
+ * it exists to measure that baseline (grid and persistent schedules).  Errors:
+ * INVALID_ARG for another method or k, a negative or NaN threshold or sigma. */
+enum { DPPT_REPLAY_CACHED = 0, DPPT_REPLAY_PPRB = 1 };
 typedef struct {
-    int32_t checkpoint_interval;
-    float gamma;
-    float eps;
+    int32_t method;                /* DPPT_REPLAY_CACHED (default) or DPPT_REPLAY_PPRB (below) */
+    int32_t checkpoint_interval;   /* cached: 1, 4, 8 or 16 */
+    float gamma;                   /* cached, k > 1: DI threshold of the scalar route */
+    float eps;                     /* cached, k > 1: |det| threshold of the inversion route */
+    float sigma;                   /* P-PRB: deviation of the diagonal noise u ~ N(0, sigma) */
 } dppt_replay;
 dppt_status dppt_set_replay(dppt_ctx* ctx, const dppt_replay* replay);
 dppt_status dppt_get_replay(const dppt_ctx* ctx, dppt_replay* replay);

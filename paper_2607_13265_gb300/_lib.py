@@ -57,7 +57,8 @@ class Launch(ctypes.Structure):
 
 
 class Replay(ctypes.Structure):
-    _fields_ = [("checkpoint_interval", c_i32), ("gamma", c_f32), ("eps", c_f32)]
+    _fields_ = [("method", c_i32), ("checkpoint_interval", c_i32), ("gamma", c_f32), ("eps", c_f32),
+                ("sigma", c_f32)]
 
 
 # every symbol include/dppt.h declares, with (restype, argtypes)

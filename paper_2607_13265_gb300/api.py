@@ -77,17 +77,20 @@ class Context:
         _check(self.h, self.lib.dppt_get_launch(self.h, ctypes.byref(l)), "dppt_get_launch")
         return (l.schedule, l.block_size, l.blocks_per_sm, l.adj_schedule, l.adj_block_size, l.adj_blocks_per_sm)
 
-    def set_replay(self, checkpoint_interval: int = 1, gamma: float = 0.0, eps: float = float("inf")):
+    def set_replay(self, checkpoint_interval: int = 1, gamma: float = 0.0, eps: float = float("inf"),
+                   method: str = "cached", sigma: float = 0.0):
         """Suffix replay of render_adjoint: checkpoint_interval 1 caches every vertex's suffix
         (Sec. 4.3); 4, 8 or 16 is the hybrid cached replay of Sec. 4.4 with thresholds gamma
-        (depolarization index, scalar route) and eps (|det|, inversion route)."""
-        r = L.Replay(int(checkpoint_interval), float(gamma), float(eps))
+        (depolarization index, scalar route) and eps (|det|, inversion route).  method 'pprb'
+        selects the basic polarized PRB baseline with diagonal noise of deviation sigma."""
+        r = L.Replay({"cached": 0, "pprb": 1}[method], int(checkpoint_interval), float(gamma), float(eps), float(sigma))
         _check(self.h, self.lib.dppt_set_replay(self.h, ctypes.byref(r)), "dppt_set_replay")
 
     def get_replay(self) -> tuple:
+        """(checkpoint_interval, gamma, eps, method, sigma)"""
         r = L.Replay()
         _check(self.h, self.lib.dppt_get_replay(self.h, ctypes.byref(r)), "dppt_get_replay")
-        return (r.checkpoint_interval, r.gamma, r.eps)
+        return (r.checkpoint_interval, r.gamma, r.eps, ("cached", "pprb")[r.method], r.sigma)
 
     def adjoint_footprint(self, max_depth: int) -> dict:
         out = (ctypes.c_int64 * 4)()

@@ -22,7 +22,7 @@ struct dppt_ctx {
     unsigned* d_status = nullptr;
     unsigned long long* d_counter = nullptr;
     dppt_launch launch{DPPT_SCHED_GRID, 128, 0, DPPT_SCHED_GRID, 128, 0};
-    dppt_replay replay{1, 0.0f, 0.0f};
+    dppt_replay replay{DPPT_REPLAY_CACHED, 1, 0.0f, 0.0f, 0.0f};
     StageLog log;
 };
 
@@ -719,6 +719,7 @@ static void build_tables(const dppt_job* jobs, int njobs, const std::vector<JobP
             J.cam = j.camera; J.W = j.width; J.H = j.height; J.spp = j.spp; J.depth = j.max_depth;
             J.red_mode = red_mode(j.spp);
             J.k0 = j.seed ^ ((unsigned long long)(uint32_t)j.pass * 0x9E3779B97F4A7C15ULL);
+            J.kn = (j.seed ^ 0x5bd1e995ULL) ^ (3ULL * 0x9E3779B97F4A7C15ULL);
             J.k1 = j.stream;
             J.npaths = (long long)plan[b + k].npix * j.spp;
             J.chunk_begin = chunks;
@@ -842,8 +843,8 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
     if (st != DPPT_OK) return st;
     const Shape shape = shape_of(ctx, 1);
     const bool wave = shape.schedule == DPPT_SCHED_WAVEFRONT;
-    if (wave && ctx->replay.checkpoint_interval > 1)
-        return fail(ctx, DPPT_ERR_UNSUPPORTED, "hybrid cached replay runs on the grid and persistent schedules");
+    if (wave && (ctx->replay.checkpoint_interval > 1 || ctx->replay.method == DPPT_REPLAY_PPRB))
+        return fail(ctx, DPPT_ERR_UNSUPPORTED, "hybrid replay and P-PRB run on the grid and persistent schedules");
     const long long Q = wave ? wave_paths(jobs, njobs) : 0;
     const int cap = max_depth_of(jobs, njobs);
     const size_t ws_jobs = ws;
@@ -901,6 +902,29 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
                                               shape.block, ctx->d_status, cs, &ctx->log);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront adjoint");
             }
+            continue;
+        }
+        if (ctx->replay.method == DPPT_REPLAY_PPRB) {
+            // basic polarized PRB: no cache, suffixes recovered by noise-regularized inversion
+            cudaFuncAttributes fa;
+            cudaError_t e = pprb_attributes(&fa);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel attributes");
+            if (shape.block > fa.maxThreadsPerBlock)
+                return fail(ctx, DPPT_ERR_INVALID_ARG, "block_size exceeds the P-PRB kernel's limit of " +
+                                                           std::to_string(fa.maxThreadsPerBlock) + " threads");
+            LaunchCfg L;
+            L.schedule = shape.schedule;
+            L.block = shape.block;
+            int occ = std::max(1, pprb_occupancy(L.block, scalar_smem(s)));
+            L.grid = ctx->sm_count * (shape.bps > 0 ? std::min(shape.bps, occ) : occ);
+            if (L.schedule == DPPT_SCHED_PERSISTENT) {
+                e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), cs);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+            }
+            int tok = ctx->log.begin(kStageAdjoint, cs);
+            e = launch_pprb(s->d, P, G, T, L, ctx->d_counter, ctx->d_status, ctx->replay.sigma, cs);
+            ctx->log.end(tok, cs);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "P-PRB adjoint launch");
             continue;
         }
         if (ctx->replay.checkpoint_interval > 1) {
@@ -1077,24 +1101,31 @@ dppt_status dppt_get_launch(const dppt_ctx* ctx, dppt_launch* l) {
 dppt_status dppt_adjoint_footprint(const dppt_ctx* ctx, int32_t max_depth, int64_t out[4]) {
     if (!ctx || !out || max_depth < 1 || max_depth > kMaxDepth) return DPPT_ERR_INVALID_ARG;
     const int k = ctx->replay.checkpoint_interval, blk = ctx->launch.adj_block_size;
+    const bool pprb = ctx->replay.method == DPPT_REPLAY_PPRB;
     const int bucket = k > 1 ? hybrid_bucket(max_depth) : depth_bucket(max_depth);
     cudaFuncAttributes a;
-    if ((k > 1 ? hybrid_attributes(k, bucket, &a) : trace_attributes(bucket, 1, &a)) != cudaSuccess)
-        return DPPT_ERR_CUDA;
+    cudaError_t e = pprb ? pprb_attributes(&a) : k > 1 ? hybrid_attributes(k, bucket, &a) : trace_attributes(bucket, 1, &a);
+    if (e != cudaSuccess) return DPPT_ERR_CUDA;
     out[0] = (int64_t)a.localSizeBytes;
     out[1] = a.numRegs;
-    out[2] = (int64_t)(k > 1 ? hybrid_occupancy(k, bucket, blk, 1024) : trace_occupancy(bucket, 1, blk, 1024)) * blk;
+    out[2] = (int64_t)(pprb     ? pprb_occupancy(blk, 1024)
+                       : k > 1 ? hybrid_occupancy(k, bucket, blk, 1024)
+                               : trace_occupancy(bucket, 1, blk, 1024)) * blk;
     out[3] = ctx->sm_count;
     return DPPT_OK;
 }
 
 dppt_status dppt_set_replay(dppt_ctx* ctx, const dppt_replay* r) {
     if (!ctx || !r) return fail(ctx, DPPT_ERR_INVALID_ARG, "null argument");
+    if (r->method != DPPT_REPLAY_CACHED && r->method != DPPT_REPLAY_PPRB)
+        return fail(ctx, DPPT_ERR_INVALID_ARG, "unknown replay method");
     const int k = r->checkpoint_interval;
     if (k != 1 && k != 4 && k != 8 && k != 16)
         return fail(ctx, DPPT_ERR_INVALID_ARG, "checkpoint_interval must be 1, 4, 8 or 16");
     if (!(r->gamma >= 0.0f) || !(r->eps >= 0.0f))
         return fail(ctx, DPPT_ERR_INVALID_ARG, "gamma and eps must be >= 0");
+    if (!(r->sigma >= 0.0f) || !(r->sigma < INFINITY))
+        return fail(ctx, DPPT_ERR_INVALID_ARG, "sigma must be finite and >= 0");
     ctx->replay = *r;
     return DPPT_OK;
 }

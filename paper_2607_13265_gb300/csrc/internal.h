@@ -71,6 +71,7 @@ struct DGrads {
 struct DJob {
     int cam, W, H, spp, depth, red_mode;
     unsigned long long k0, k1;
+    unsigned long long kn;   // key of the basic polarized PRB's noise stream (seed ^ 0x5bd1e995, pass 3)
     long long npaths;
     long long chunk_begin;
     float* raw;            // mean raw sensor-frame Stokes per pixel [H*W][12] (primal: image or
@@ -158,6 +159,11 @@ struct HybridCfg { float gamma, eps; };
                                   cudaStream_t st);                                                               \
     cudaError_t hybrid_attributes_##K(int bucket, cudaFuncAttributes* a);                                         \
     int hybrid_occupancy_##K(int bucket, int block, size_t smem);
+// basic polarized PRB (pprb.cu): the cache-free adjoint megakernel of Sec. 4.1-4.2
+cudaError_t launch_pprb(const DScene& S, const DParams& P, const DGrads& G, const JobTable& T, const LaunchCfg& L,
+                        unsigned long long* counter, unsigned* status, float sigma, cudaStream_t st);
+cudaError_t pprb_attributes(cudaFuncAttributes* a);
+int pprb_occupancy(int block, size_t smem);
 DPPT_DECLARE_HYBRID(4)
 DPPT_DECLARE_HYBRID(8)
 DPPT_DECLARE_HYBRID(16)

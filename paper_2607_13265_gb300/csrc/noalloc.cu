@@ -106,6 +106,7 @@ extern "C" dppt_status dppt_render_primal_noalloc(dppt_ctx* ctx, const dppt_scen
     const bool pow2 = (j.spp & (j.spp - 1)) == 0;
     J.red_mode = pow2 && j.spp <= 32 ? 0 : (pow2 ? 1 : 2);
     J.k0 = j.seed ^ ((unsigned long long)(uint32_t)j.pass * 0x9E3779B97F4A7C15ULL);
+    J.kn = (j.seed ^ 0x5bd1e995ULL) ^ (3ULL * 0x9E3779B97F4A7C15ULL);
     J.k1 = j.stream;
     J.npaths = npix * j.spp;
     J.chunk_begin = 0;

@@ -7,7 +7,7 @@ vertices in it.  For each max_depth and each schedule the module times render_pr
 render_adjoint (cached suffix replay) with CUDA events on the launching stream, after a
 warm-up call, and reports the memory the adjoint holds for its cache (for the fully cached
 replay and, with --hybrid k.., for the hybrid cached replay of Sec. 4.4 with checkpoints
-every k vertices):
+every k vertices; with --pprb, for the basic polarized PRB baseline, which keeps no cache):
   * megakernel schedules: the per-thread local cache (bytes per thread, from the compiled
     kernel) times the threads resident on the GPU -- independent of the image size;
   * wavefront schedule: the library workspace (path state + per-vertex cache of one wave,
@@ -16,6 +16,7 @@ The loss is a seeded linear functional of the image.  Prints one JSON line per
 (schedule, depth) and a final summary line.
 
   python -m paper_2607_13265_gb300.deep_bench [--depths 4 8 16 32 64 128] [--reps 3] [--hybrid 4 8 16]
+      [--pprb 0.01]
 """
 from __future__ import annotations
 
@@ -40,6 +41,8 @@ def main(argv=None):
     ap.add_argument("--hybrid", type=int, nargs="*", default=[], help="checkpoint intervals k of hybrid replay runs")
     ap.add_argument("--gamma", type=float, default=0.0)
     ap.add_argument("--eps", type=float, default=float("inf"))
+    ap.add_argument("--pprb", type=float, default=None,
+                    help="also time the basic polarized PRB baseline with this noise deviation")
     args = ap.parse_args(argv)
 
     import torch
@@ -51,10 +54,12 @@ def main(argv=None):
     gs = api.GpuScene(dctx, scene)
     stream = torch.cuda.Stream()
     rows = []
-    runs = [(s_, 1) for s_ in args.schedules] + [("grid", k) for k in args.hybrid]
-    for sched, kint in runs:
-        dctx.set_replay(kint, args.gamma, args.eps)
-        label = sched if kint == 1 else f"grid/hybrid-k{kint}"
+    runs = [(s_, 1, "cached") for s_ in args.schedules] + [("grid", k, "cached") for k in args.hybrid]
+    if args.pprb is not None:
+        runs.append(("grid", 1, "pprb"))
+    for sched, kint, method in runs:
+        dctx.set_replay(kint, args.gamma, args.eps, method=method, sigma=args.pprb or 0.0)
+        label = "grid/pprb" if method == "pprb" else sched if kint == 1 else f"grid/hybrid-k{kint}"
         for d in args.depths:
             job = copy.copy(job0)
             job.max_depth = d
@@ -95,7 +100,8 @@ def main(argv=None):
                    "primal_ms": float(np.median(tp)), "adjoint_ms": float(np.median(ta)),
                    "adjoint_vertices_per_s": work["vertices"] / (float(np.median(ta)) / 1e3),
                    "cache_bytes": int(ws if sched == "wavefront" else mega_cache),
-                   "replay": {"checkpoint_interval": kint, "gamma": args.gamma, "eps": args.eps},
+                   "replay": {"method": method, "checkpoint_interval": kint, "gamma": args.gamma, "eps": args.eps,
+                              "sigma": args.pprb if method == "pprb" else None},
                    "workspace_bytes": int(ws), "local_bytes_per_thread": int(fp["local_bytes_per_thread"]),
                    "resident_threads": int(fp["threads_per_sm"] * fp["sms"]),
                    "device_bytes_grown_first_call": int(grown),

@@ -618,6 +618,22 @@ def polarizer_stack_scene(angles, le=2.0, spacing: float = 0.05) -> tuple[Scene,
     return s, job
 
 
+def retarder_pair_scene() -> tuple[Scene, Job]:
+    """A polarized emitter (Stokes 2, 0.8, 0.9, 0.3) behind a quarter-wave and a sixth-wave
+    retarder sheet (axes 0.3 and 1.0 rad), polarizer camera filter at 0.2 rad: every
+    operator on the path is invertible."""
+    s = Scene()
+    s.sheet += [0.3, 1.0]
+    q = s.add_material(Material(MAT_RETARDER_SHEET, sheet_index=0, retard=math.pi / 2))
+    h = s.add_material(Material(MAT_RETARDER_SHEET, sheet_index=1, retard=math.pi / 3))
+    s.add_quad((-1, -1, 0), (2, 0, 0), (0, 2, 0), q)
+    s.add_quad((-1, -1, -0.05), (2, 0, 0), (0, 2, 0), h)
+    s.add_light((-2, -2, -1), (4, 0, 0), (0, 4, 0), np.array([2.0, 0.8, 0.9, 0.3]))
+    s.add_camera((0, 0, 2), (0, 0, 0), (0, 1, 0), 0.01)
+    job = Job(camera=0, width=2, height=2, spp=4, max_depth=3, filter=FILTER_POLARIZER, thetas=[0.2])
+    return s, job
+
+
 def retarder_scene(alpha: float, phi: float, le: float = 2.0) -> tuple[Scene, Job]:
     """Unpolarized light through a polarizer sheet at alpha, then a quarter-wave sheet with
     fast axis phi, seen by an unfiltered camera (depth 3)."""

@@ -32,21 +32,6 @@ def _setup(oracle_mod, scene, job, seed=1):
     return o, P, dI
 
 
-def _retarder_pair():
-    """A polarized emitter behind two retarder sheets (quarter- and sixth-wave), polarizer
-    camera filter: every scene operator is invertible."""
-    s = sg.Scene()
-    s.sheet += [0.3, 1.0]
-    q = s.add_material(sg.Material(sg.MAT_RETARDER_SHEET, sheet_index=0, retard=np.pi / 2))
-    h = s.add_material(sg.Material(sg.MAT_RETARDER_SHEET, sheet_index=1, retard=np.pi / 3))
-    s.add_quad((-1, -1, 0), (2, 0, 0), (0, 2, 0), q)
-    s.add_quad((-1, -1, -0.05), (2, 0, 0), (0, 2, 0), h)
-    s.add_light((-2, -2, -1), (4, 0, 0), (0, 4, 0), np.array([2.0, 0.8, 0.9, 0.3]))
-    s.add_camera((0, 0, 2), (0, 0, 0), (0, 1, 0), 0.01)
-    job = sg.Job(camera=0, width=2, height=2, spp=4, max_depth=3, filter=sg.FILTER_POLARIZER, thetas=[0.2])
-    return s, job
-
-
 def test_polarizer_stack_breaks_pprb_for_every_sigma(oracle_mod):
     """Five linear polarizers: the sheet-angle gradients need the polarization state behind
     each sheet, which a rank-deficient factor does not carry."""
@@ -89,7 +74,7 @@ def test_camera_filter_angle_survives_pprb(oracle_mod):
 @pytest.mark.parametrize("single", [False, True])
 def test_retarders_are_invertible_so_pprb_converges(oracle_mod, single):
     """Case 1 of Sec. 4.1: with invertible factors the P-PRB error is the noise's, O(sigma)."""
-    s, job = _retarder_pair()
+    s, job = sg.retarder_pair_scene()
     o, P, dI = _setup(oracle_mod, s, job)
     tape = o.gradient(job, P, dI, mode="tape")["sheet"]
     assert _rel(o.gradient(job, P, dI, mode="replay")["sheet"], tape) < 1e-12
