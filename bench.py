@@ -273,7 +273,7 @@ def run_native(args):
     if args.schedule is not None:
         adj_s = args.schedule if args.adj_schedule is None else args.adj_schedule
         adj_b = args.block if args.adj_block is None else args.adj_block
-        dctx.set_launch(args.schedule, args.block, 0, adj_s, adj_b, 0)
+        dctx.set_launch(args.schedule, args.block, 0, adj_s, adj_b, 0, args.adj_scatter)
     else:
         # the library's autotuner picks schedule and block size for each call (untimed)
         tuning = api.autotune(dctx, gs, adj, P, reps=2)
@@ -397,6 +397,7 @@ def run_native(args):
                    "paths_per_step": paths_per_step, "grads": "albedo 128x128x3 + roughness 128x128",
                    "l2": "flushed between timed steps (512 MiB write)",
                    "schedule": {"primal": [api.SCHEDULE_NAMES[lc[0]], lc[1]], "adjoint": [api.SCHEDULE_NAMES[lc[3]], lc[4]],
+                                "adjoint_texel_scatter": ("warp", "lane")[lc[6]],
                                 "chosen_by": "autotuner" if tuning else "command line"},
                    "parallelism": f"replicas{world}"},
         "calls_ms": {"render_primal": prim_avg, "render_adjoint": adj_avg},
@@ -483,6 +484,8 @@ def main():
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--adj-schedule", type=int, default=None, help="adjoint schedule (default: same as --schedule)")
     ap.add_argument("--adj-block", type=int, default=None)
+    ap.add_argument("--adj-scatter", type=int, default=0, choices=[0, 1],
+                    help="with --schedule: texel gradients per warp group (0) or per lane (1)")
     ap.add_argument("--cpu-pixels", type=int, default=16384)
     ap.add_argument("--ref-pixels", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -163,7 +163,13 @@ typedef struct {
     int32_t adj_schedule;       /* the same three for render_adjoint */
     int32_t adj_block_size;
     int32_t adj_blocks_per_sm;
+    int32_t adj_scatter;        /* texel-gradient scatter of render_adjoint: DPPT_SCATTER_WARP
+                                   (default; lanes of a warp adding to the same texel combine
+                                   first, one atomic per group) or DPPT_SCATTER_LANE (one atomic
+                                   per lane) -- which is faster depends on how many warps hit the
+                                   same texels; the autotuner measures both */
 } dppt_launch;
+enum { DPPT_SCATTER_WARP = 0, DPPT_SCATTER_LANE = 1 };
 
 /* Create a context on CUDA device `device` (made current for the call). */
 dppt_status dppt_create(dppt_ctx** out, int device);
@@ -233,7 +239,8 @@ dppt_status dppt_set_launch(dppt_ctx* ctx, const dppt_launch* launch);
 dppt_status dppt_get_launch(const dppt_ctx* ctx, dppt_launch* launch);
 
 /* Autotuner: times render_primal and render_adjoint of the given jobs for
- * every schedule (grid, persistent, wavefront) and block size (64, 128, 256)
+ * every schedule (grid, persistent, wavefront) and block size (64, 128, 256),
+ * then the adjoint's fastest shape with the other texel-gradient scatter
  * with CUDA events on `stream` (one warm-up call and `reps` timed calls per
  * candidate), keeps the fastest shape for each of the two calls in the
  * context and returns it in *best.  times_ms (nullable) receives the

@@ -53,7 +53,8 @@ class Grads(ctypes.Structure):
 
 class Launch(ctypes.Structure):
     _fields_ = [("schedule", c_i32), ("block_size", c_i32), ("blocks_per_sm", c_i32),
-                ("adj_schedule", c_i32), ("adj_block_size", c_i32), ("adj_blocks_per_sm", c_i32)]
+                ("adj_schedule", c_i32), ("adj_block_size", c_i32), ("adj_blocks_per_sm", c_i32),
+                ("adj_scatter", c_i32)]
 
 
 class Replay(ctypes.Structure):

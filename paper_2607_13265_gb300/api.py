@@ -63,19 +63,24 @@ class Context:
             pass
 
     def set_launch(self, schedule: int, block_size: int, blocks_per_sm: int = 0, adj_schedule: int | None = None,
-                   adj_block_size: int | None = None, adj_blocks_per_sm: int | None = None):
-        """Launch shape of render_primal (and of render_adjoint; same as the primal unless given)."""
+                   adj_block_size: int | None = None, adj_blocks_per_sm: int | None = None,
+                   adj_scatter: int | None = None):
+        """Launch shape of render_primal (and of render_adjoint; same as the primal unless given).
+        adj_scatter: 0 texel gradients combined per warp group, 1 one atomic per lane (unchanged
+        when None)."""
         l = L.Launch(schedule, block_size, blocks_per_sm,
                      schedule if adj_schedule is None else adj_schedule,
                      block_size if adj_block_size is None else adj_block_size,
-                     blocks_per_sm if adj_blocks_per_sm is None else adj_blocks_per_sm)
+                     blocks_per_sm if adj_blocks_per_sm is None else adj_blocks_per_sm,
+                     self.get_launch()[6] if adj_scatter is None else adj_scatter)
         _check(self.h, self.lib.dppt_set_launch(self.h, ctypes.byref(l)), "dppt_set_launch")
 
     def get_launch(self) -> tuple:
-        """(schedule, block, blocks_per_sm, adj_schedule, adj_block, adj_blocks_per_sm)"""
+        """(schedule, block, blocks_per_sm, adj_schedule, adj_block, adj_blocks_per_sm, adj_scatter)"""
         l = L.Launch()
         _check(self.h, self.lib.dppt_get_launch(self.h, ctypes.byref(l)), "dppt_get_launch")
-        return (l.schedule, l.block_size, l.blocks_per_sm, l.adj_schedule, l.adj_block_size, l.adj_blocks_per_sm)
+        return (l.schedule, l.block_size, l.blocks_per_sm, l.adj_schedule, l.adj_block_size, l.adj_blocks_per_sm,
+                l.adj_scatter)
 
     def set_replay(self, checkpoint_interval: int = 1, gamma: float = 0.0, eps: float = float("inf"),
                    method: str = "cached", sigma: float = 0.0):
@@ -262,7 +267,8 @@ def autotune(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict, reps: in
             k = 3 * si + bi
             table[f"{SCHEDULE_NAMES[si]}/{b}"] = {"primal_ms": times[2 * k], "adjoint_ms": times[2 * k + 1]}
     return {"primal": (SCHEDULE_NAMES[best.schedule], best.block_size),
-            "adjoint": (SCHEDULE_NAMES[best.adj_schedule], best.adj_block_size), "times_ms": table}
+            "adjoint": (SCHEDULE_NAMES[best.adj_schedule], best.adj_block_size),
+            "adjoint_scatter": ("warp", "lane")[best.adj_scatter], "times_ms": table}
 
 
 def zero_grads(params: dict) -> dict:

@@ -21,7 +21,7 @@ struct dppt_ctx {
     size_t ws_size = 0;
     unsigned* d_status = nullptr;
     unsigned long long* d_counter = nullptr;
-    dppt_launch launch{DPPT_SCHED_GRID, 128, 0, DPPT_SCHED_GRID, 128, 0};
+    dppt_launch launch{DPPT_SCHED_GRID, 128, 0, DPPT_SCHED_GRID, 128, 0, DPPT_SCATTER_WARP};
     dppt_replay replay{DPPT_REPLAY_CACHED, 1, 0.0f, 0.0f, 0.0f};
     StageLog log;
 };
@@ -834,6 +834,8 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
                                 const dppt_params* params, const float* d_image, const L2Spec* l2,
                                 const dppt_grads* grads, void* stream) {
     if (!ctx || !s) return fail(ctx, DPPT_ERR_INVALID_ARG, "null context or scene");
+    DScene Sd = s->d;   // the adjoint launches' copy, with the texel-gradient scatter of the launch shape
+    Sd.scatter_lane = ctx->launch.adj_scatter == DPPT_SCATTER_LANE ? 1 : 0;
     if (!grads) return fail(ctx, DPPT_ERR_INVALID_ARG, "grads is null");
     if (!l2 && !d_image && njobs > 0) return fail(ctx, DPPT_ERR_INVALID_ARG, "d_image is null");
     cudaSetDevice(ctx->device);
@@ -898,7 +900,7 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
         }
         if (wave) {
             for (int k = 0; k < T.njobs; ++k) {
-                cudaError_t e = run_wavefront(1, s->d, P, G, T, k, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
+                cudaError_t e = run_wavefront(1, Sd, P, G, T, k, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
                                               shape.block, ctx->d_status, cs, &ctx->log);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront adjoint");
             }
@@ -922,7 +924,7 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
             }
             int tok = ctx->log.begin(kStageAdjoint, cs);
-            e = launch_pprb(s->d, P, G, T, L, ctx->d_counter, ctx->d_status, ctx->replay.sigma, cs);
+            e = launch_pprb(Sd, P, G, T, L, ctx->d_counter, ctx->d_status, ctx->replay.sigma, cs);
             ctx->log.end(tok, cs);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "P-PRB adjoint launch");
             continue;
@@ -946,7 +948,7 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
             }
             int tok = ctx->log.begin(kStageAdjoint, cs);
-            e = launch_hybrid(k, hb, s->d, P, G, T, L, ctx->d_counter, ctx->d_status,
+            e = launch_hybrid(k, hb, Sd, P, G, T, L, ctx->d_counter, ctx->d_status,
                               HybridCfg{ctx->replay.gamma, ctx->replay.eps}, cs);
             ctx->log.end(tok, cs);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "hybrid adjoint launch");
@@ -960,7 +962,7 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
             if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
         }
         int tok = ctx->log.begin(kStageAdjoint, cs);
-        cudaError_t e = launch_trace(bucket, 1, s->d, P, G, T, L, ctx->d_counter, ctx->d_status, nullptr, cs);
+        cudaError_t e = launch_trace(bucket, 1, Sd, P, G, T, L, ctx->d_counter, ctx->d_status, nullptr, cs);
         ctx->log.end(tok, cs);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
     }
@@ -1088,6 +1090,8 @@ dppt_status dppt_set_launch(dppt_ctx* ctx, const dppt_launch* l) {
     if (!block_ok(l->block_size) || !block_ok(l->adj_block_size))
         return fail(ctx, DPPT_ERR_INVALID_ARG, "block_size must be 64, 128, 256 or 512");
     if (l->blocks_per_sm < 0 || l->adj_blocks_per_sm < 0) return fail(ctx, DPPT_ERR_INVALID_ARG, "negative blocks_per_sm");
+    if (l->adj_scatter != DPPT_SCATTER_WARP && l->adj_scatter != DPPT_SCATTER_LANE)
+        return fail(ctx, DPPT_ERR_INVALID_ARG, "unknown adj_scatter");
     ctx->launch = *l;
     return DPPT_OK;
 }
@@ -1172,7 +1176,7 @@ dppt_status dppt_autotune(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jo
     dppt_status result = DPPT_OK;
     for (int si = 0; si < 3 && result == DPPT_OK; ++si)
         for (int bi = 0; bi < 3 && result == DPPT_OK; ++bi) {
-            ctx->launch = dppt_launch{scheds[si], blocks[bi], 0, scheds[si], blocks[bi], 0};
+            ctx->launch = dppt_launch{scheds[si], blocks[bi], 0, scheds[si], blocks[bi], 0, DPPT_SCATTER_WARP};
             float t[2] = {INFINITY, INFINITY};
             for (int mode = 0; mode < 2; ++mode) {
                 auto call = [&]() {
@@ -1194,6 +1198,24 @@ dppt_status dppt_autotune(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jo
             if (t[0] < best_t[0]) { best_t[0] = t[0]; pick.schedule = scheds[si]; pick.block_size = blocks[bi]; pick.blocks_per_sm = 0; }
             if (t[1] < best_t[1]) { best_t[1] = t[1]; pick.adj_schedule = scheds[si]; pick.adj_block_size = blocks[bi]; pick.adj_blocks_per_sm = 0; }
         }
+    // the adjoint's fastest shape once more with one atomic per lane for texel gradients
+    pick.adj_scatter = DPPT_SCATTER_WARP;
+    if (result == DPPT_OK && std::isfinite(best_t[1])) {
+        ctx->launch = pick;
+        ctx->launch.adj_scatter = DPPT_SCATTER_LANE;
+        auto call = [&]() { return dppt_render_adjoint(ctx, s, jobs, njobs, params, dimage, &G, st); };
+        if (call() == DPPT_OK) {
+            cudaEventRecord(a, st);
+            bool ok = true;
+            for (int r = 0; r < reps && ok; ++r) ok = call() == DPPT_OK;
+            cudaEventRecord(b, st);
+            if (cudaEventSynchronize(b) == cudaSuccess && ok) {
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, a, b);
+                if (ms / reps < best_t[1]) pick.adj_scatter = DPPT_SCATTER_LANE;
+            }
+        }
+    }
     cudaStreamSynchronize(st);
     cudaEventDestroy(a); cudaEventDestroy(b); cudaStreamDestroy(st);
     cudaFree(image); cudaFree(dimage); cudaFree(g);

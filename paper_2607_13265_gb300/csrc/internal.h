@@ -48,7 +48,8 @@ struct DScene {
     const DTex* tex;
     const DCam* cams;
     float eps;
-    int num_ior, num_sheets, pad;
+    int num_ior, num_sheets;
+    int scatter_lane;       // adjoint: texel gradients one atomic per lane (1) or per warp group (0)
 };
 
 struct DParams {

@@ -908,48 +908,40 @@ __device__ __forceinline__ bool walk_step(const DScene& S, const DParams& P, con
     return walk_finish(S, P, w, vc, ne, visible, sh, vis);
 }
 
-// Gradient scatter of texel derivatives.  DPPT_GRAD_AGG 0 (default): one atomic per lane;
-// the lanes of one atomic instruction that add to the same element are combined by the
-// memory system, and on this workload that measured faster than either software
-// aggregation.  2: once per vertex and texture, two integer warp reductions tell whether a
-// full warp sits on the same base texel (then its four bilinear taps agree too, e.g. the
-// samples of one pixel at their first vertex); such a warp sums each value with shuffles
-// and one lane issues the atomic.  1: lanes adding to the same element are grouped with
-// __match_any_sync before every atomic.
-#ifndef DPPT_GRAD_AGG
-#define DPPT_GRAD_AGG 0
-#endif
+// Gradient scatter of texel derivatives, chosen per launch (DScene::scatter_lane): either
+// the lanes of a warp that add to the same element are grouped with __match_any_sync and
+// one lane per group issues the atomic (the default: it keeps many warps that hit the same
+// texels from serializing on them), or every lane issues its own atomic (faster when few
+// lanes share texels, since the memory system already combines the lanes of one atomic
+// instruction that hit the same address).
 __device__ __forceinline__ void atomic_add_grouped(float* base, long long idx, float val) {
     const unsigned mask = __activemask();
     const unsigned peers = __match_any_sync(mask, (unsigned long long)idx);
     const int lane = threadIdx.x & 31;
-    float sum = 0.0f;
-    for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, val, __ffs(m) - 1);
+    float sum;
+    if (peers == 0xffffffffu) {
+        sum = val;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    } else {
+        sum = 0.0f;
+        for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, val, __ffs(m) - 1);
+    }
     if (lane == __ffs(peers) - 1 && sum != 0.0f) atomicAdd(base + idx, sum);
 }
 // adds vals[c] * w[k] at tp.idx[k] + min(c, ch - 1) for the NC values and the four taps
 template <int NC>
-__device__ __forceinline__ void scatter_taps(float* g, const Taps& tp, const float* vals, int ch) {
-    const unsigned FULL = 0xffffffffu;
-    bool uniform = false;
-    if (DPPT_GRAD_AGG == 2 && __activemask() == FULL) {
-        const unsigned lo = (unsigned)tp.idx[0], hi = (unsigned)((unsigned long long)tp.idx[0] >> 32);
-        uniform = __reduce_or_sync(FULL, hi) == 0u && __reduce_min_sync(FULL, lo) == __reduce_max_sync(FULL, lo);
-    }
+__device__ __forceinline__ void scatter_taps(float* g, const Taps& tp, const float* vals, int ch, bool per_lane) {
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            float v = vals[c] * tp.w[k];
+            const float v = vals[c] * tp.w[k];
             const long long idx = tp.idx[k] + min(c, ch - 1);
-            if (uniform) {
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
-                if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(g + idx, v);
-            } else if (DPPT_GRAD_AGG == 1) {
+            if (per_lane) {
+                if (v != 0.0f) atomicAdd(g + idx, v);
+            } else {
                 atomic_add_grouped(g, idx, v);
-            } else if (v != 0.0f) {
-                atomicAdd(g + idx, v);
             }
         }
 }
@@ -1045,18 +1037,18 @@ __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, 
         if (G->tex && S->tex[m.normal_tex].pad) {
             const Taps tp = tex_taps(S->tex[m.normal_tex], vc.tu, vc.tv);
             const float gn[3] = {2.0f * g_slot0, 2.0f * g_eta, 2.0f * (g_alb[0] + g_alb[1] + g_alb[2])};
-            scatter_taps<3>(G->tex, tp, gn, 3);
+            scatter_taps<3>(G->tex, tp, gn, 3, S->scatter_lane != 0);
         }
     } else if (G->tex) {
         if ((m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.rough_tex].pad) {
             Taps tp = tex_taps(S->tex[m.rough_tex], vc.tu, vc.tv);
-            scatter_taps<1>(G->tex, tp, &g_slot0, 1);
+            scatter_taps<1>(G->tex, tp, &g_slot0, 1, S->scatter_lane != 0);
         }
         if (m.albedo_tex >= 0 && (m.type == DPPT_MAT_DIFFUSE || m.type == DPPT_MAT_CONDUCTOR_GGX ||
                                   m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.albedo_tex].pad) {
             DTex t = S->tex[m.albedo_tex];
             Taps tp = tex_taps(t, vc.tu, vc.tv);
-            scatter_taps<3>(G->tex, tp, g_alb, t.ch);
+            scatter_taps<3>(G->tex, tp, g_alb, t.ch, S->scatter_lane != 0);
         }
     }
     // advance the adjoint row through the value of W_i

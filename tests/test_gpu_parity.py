@@ -270,3 +270,26 @@ def test_full_size_workload_sampled_pixels(env):
     assert same.mean() >= 0.9
     err = image_rel_err(gp, o)
     assert float(err[:, same].max()) <= 10 * IMG_TOL_P999
+
+
+@pytest.mark.parametrize("sched", [0, 2], ids=["grid", "wavefront"])
+def test_texel_scatter_modes_agree(env, sched):
+    """Texel gradients combined per warp group or issued one atomic per lane: the same sums
+    in another order."""
+    import torch
+    api, dctx, _ = env
+    scene, job = SCENES["icosphere"]
+    gs = api.GpuScene(dctx, scene)
+    adj = api.pack_jobs(api.adjoint_jobs([job]))
+    P = api.device_params(scene, adj)
+    d = torch.as_tensor(np.random.default_rng(3).normal(size=adj.image_floats), dtype=torch.float32, device="cuda")
+    prev = dctx.get_launch()
+    out = []
+    try:
+        for scatter in (0, 1):
+            dctx.set_launch(sched, 128, 0, sched, 128, 0, scatter)
+            out.append(api.render_adjoint(dctx, gs, adj, P, d)["tex"].double().cpu().numpy())
+    finally:
+        dctx.set_launch(*prev)
+    assert np.linalg.norm(out[0]) > 0
+    assert np.linalg.norm(out[0] - out[1]) <= 1e-5 * np.linalg.norm(out[0])
