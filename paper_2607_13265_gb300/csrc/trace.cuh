@@ -930,11 +930,24 @@ __device__ __forceinline__ void atomic_add_grouped(float* base, long long idx, f
     if (lane == __ffs(peers) - 1 && sum != 0.0f) atomicAdd(base + idx, sum);
 }
 // adds vals[c] * w[k] at tp.idx[k] + min(c, ch - 1) for the NC values and the four taps
+// (kept as a loop: the replay kernel is bound by instruction fetch, and sixteen inlined
+// copies of the grouping code would enlarge it)
+#ifndef DPPT_SCATTER_UNROLL
+#define DPPT_SCATTER_UNROLL 0
+#endif
 template <int NC>
 __device__ __forceinline__ void scatter_taps(float* g, const Taps& tp, const float* vals, int ch, bool per_lane) {
+#if DPPT_SCATTER_UNROLL
 #pragma unroll
+#else
+#pragma unroll 1
+#endif
     for (int c = 0; c < NC; ++c)
+#if DPPT_SCATTER_UNROLL
 #pragma unroll
+#else
+#pragma unroll 1
+#endif
         for (int k = 0; k < 4; ++k) {
             const float v = vals[c] * tp.w[k];
             const long long idx = tp.idx[k] + min(c, ch - 1);
