@@ -540,6 +540,9 @@ dppt_status dppt_scene_upload(dppt_ctx* ctx, const dppt_scene_desc* d, dppt_scen
             if (!d->uvs) return fail(ctx, DPPT_ERR_INVALID_ARG, "normal maps need triangle UVs");
         }
     }
+    int mat_types = 0;
+    for (int64_t i = 0; i < F; ++i) mat_types |= 1 << mats[d->tri_material[i]].type;
+    for (int64_t i = 0; i < Sn; ++i) mat_types |= 1 << mats[d->sphere_material[i]].type;
     bool any_normal_map = false;
     for (int i = 0; i < M; ++i) any_normal_map = any_normal_map || mats[i].normal_tex >= 0;
     for (int64_t i = 0; i < Sn; ++i)
@@ -678,6 +681,7 @@ dppt_status dppt_scene_upload(dppt_ctx* ctx, const dppt_scene_desc* d, dppt_scen
     D.num_spheres = (int)Sn;
     D.num_lights = L;
     D.eps = d->ray_eps;
+    D.mat_types = mat_types;
     D.num_ior = d->num_ior;
     D.num_sheets = d->num_sheets;
     s->num_nodes = D.num_nodes;

@@ -50,6 +50,7 @@ struct DScene {
     float eps;
     int num_ior, num_sheets;
     int scatter_lane;       // adjoint: texel gradients one atomic per lane (1) or per warp group (0)
+    int mat_types;          // bit t set when a triangle or sphere uses a material of type t
 };
 
 struct DParams {

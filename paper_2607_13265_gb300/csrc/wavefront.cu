@@ -118,8 +118,19 @@ struct WfLists {
     int* next0;
     int* next1;
     int* shadow;
-    int* count;   // [0] n0, [1] n1, [2] next0, [3] next1, [4] shadow
+    int* count;   // [0] n0, [1] n1, [2] next0, [3] next1, [4] shadow, [8 + b] replay bin b
+    int* bins;    // replay paths binned by the material type of their vertex: bin b at bins + b * Q
+    int binQ;
 };
+
+// Replay bins: the material types with a replay kernel of their own (diffuse, rough
+// conductor, rough dielectric), and one bin for everything else (smooth dielectrics,
+// sheets, emitter hits, paths that left the scene).
+constexpr int kBinOther = 7;
+constexpr unsigned kBinnedTypes = (1u << DPPT_MAT_DIFFUSE) | (1u << DPPT_MAT_CONDUCTOR_GGX) | (1u << DPPT_MAT_PLASTIC_GGX);
+#ifndef DPPT_WF_BIN_REPLAY
+#define DPPT_WF_BIN_REPLAY 1
+#endif
 
 __device__ __forceinline__ int list_at(const WfLists& L, int n0, int idx) {
     return idx < n0 ? L.l0[idx] : L.l1[idx - n0];
@@ -206,6 +217,29 @@ k_wf_shadow(const DScene S, WfState W, WfLists L, unsigned* status) {
     }
 }
 
+// Sorts the replay list into per-material bins.  Appends are warp-aggregated: the lanes
+// of a warp going to the same bin take consecutive slots with one atomic.
+__global__ void k_wf_bin(const DScene S, WfState W, WfLists L) {
+    const int n = L.count[1];
+    const int stride = gridDim.x * blockDim.x;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
+        const int q = L.l1[idx];
+        const int4 ids = W.vtx[q].ids;
+        int b = kBinOther;
+        if ((unsigned)ids.w & kFHit) {
+            const int t = __ldg(&S.mats[ids.y & 0xffff].type);
+            if ((kBinnedTypes >> t) & 1u) b = t;
+        }
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, b);
+        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(L.count + 8 + b, __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        L.bins[(long long)b * L.binQ + base + __popc(peers & ((1u << lane) - 1u))] = q;
+    }
+}
+
 __device__ __forceinline__ void flush_scalars(const DScene& S, const DGrads& G, float* sgrad, int nscal) {
     __syncthreads();
     float* gdst[3] = {G.ior, G.sheet, G.le};
@@ -225,7 +259,7 @@ __device__ __forceinline__ void flush_scalars(const DScene& S, const DGrads& G, 
 // Per-vertex action of one pass.  PHASE 0 (cache pass): cache E_i / W_i; at the
 // end of the walk fold the cache, store the path's raw Stokes value and, for the
 // adjoint (MODE 1), start the replay.  PHASE 1: the replay (MODE 1 only).
-template <int MODE, int PHASE, bool NM>
+template <int MODE, int PHASE, bool NM, int MT = -1, int BIN = -1>
 __global__ void __launch_bounds__(128, PHASE == 1 ? DPPT_WF_REPLAY_MIN_BLOCKS : DPPT_WF_CACHE_MIN_BLOCKS)
 k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_constant__ JobTable T, WfState W, WfLists L,
             unsigned* sig) {
@@ -235,15 +269,17 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
         for (int k = threadIdx.x; k < nscal; k += blockDim.x) sgrad[k] = 0.0f;
         __syncthreads();
     }
-    const int count = PHASE == 0 ? L.count[0] : L.count[1];
+    // the pass's list: the cache list, the replay list, or one replay bin
+    const int* list = PHASE == 0 ? L.l0 : BIN < 0 ? L.l1 : L.bins + (long long)BIN * L.binQ;
+    const int count = PHASE == 0 ? L.count[0] : BIN < 0 ? L.count[1] : L.count[8 + (BIN < 0 ? 0 : BIN)];
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += stride) {
-        const int q = PHASE == 0 ? L.l0[idx] : L.l1[idx];
+        const int q = list[idx];
         const WfMeta m = W.meta[q];
         const DJob& J = T.job[m.job];
         Walk w;
         get_walk(W.walk + q, w);
-        PathVis<GlobalCache, -1, NM> vis;
+        PathVis<GlobalCache, MT, NM> vis;
         vis.S = &S; vis.P = &P; vis.G = &G; vis.sgrad = sgrad;
         vis.C.base = W.cache; vis.C.Q = W.Q; vis.C.q = q; vis.C.cap = W.cap;
         vis.n = (m.pni >> 8) & 0xff; vis.i = (m.pni >> 16) & 0xff; vis.phase = PHASE;
@@ -329,6 +365,7 @@ __global__ void k_wf_swap(WfLists L) {
         L.count[2] = 0;
         L.count[3] = 0;
         L.count[4] = 0;
+        for (int b = 8; b < 16; ++b) L.count[b] = 0;
     }
 }
 
@@ -361,7 +398,8 @@ size_t wavefront_bytes(long long Q, int cap) {
     b += align_up(sizeof(float4) * 3 * Q);      // adjoint rows
     b += align_up(sizeof(float4) * 3 * Q);      // raw per path
     b += 5 * align_up(sizeof(int) * Q);         // lists
-    b += align_up(sizeof(int) * 8);
+    b += align_up(sizeof(int) * 16);
+    b += align_up(sizeof(int) * 8 * Q);         // replay bins
     b += align_up(sizeof(float) * 31 * (size_t)cap * Q);
     return b;
 }
@@ -384,7 +422,8 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
     W.raw = reinterpret_cast<float4*>(p); p += align_up(sizeof(float4) * 3 * Q);
     int* lists[5];
     for (int k = 0; k < 5; ++k) { lists[k] = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * Q); }
-    int* count = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * 8);
+    int* count = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * 16);
+    int* bins = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * 8 * Q);
     W.cache = reinterpret_cast<float*>(p);
     W.Q = Q;
     W.cap = cap;
@@ -394,6 +433,8 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
     const long long npix = (long long)J.W * J.H;
     const long long pix_per_wave = std::max(1LL, Q / J.spp);
     const bool nmaps = S.tri_tan != nullptr;   // the scene has normal maps: kernels with that path
+    const unsigned types = (unsigned)S.mat_types;
+    const bool binned = DPPT_WF_BIN_REPLAY && (types & kBinnedTypes) != 0;
     const int passes = mode == 1 ? 2 : 1;
     const size_t smem = mode == 1 ? sizeof(float) * (size_t)(S.num_ior + S.num_sheets + 12 * S.num_lights) : 0;
     for (long long pix0 = 0; pix0 < npix; pix0 += pix_per_wave) {
@@ -402,8 +443,8 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
         // stage kernels stride over their lists: a few resident waves of blocks at most
         const int grid = (int)std::min<long long>((nq + block - 1) / block, (long long)sms * (2048 / block));
         const int fgrid = (int)std::min<long long>((nq + 127) / 128, (long long)sms * DPPT_WF_CACHE_MIN_BLOCKS * 2);
-        WfLists A{lists[0], lists[1], lists[2], lists[3], lists[4], count};
-        cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 8, st);
+        WfLists A{lists[0], lists[1], lists[2], lists[3], lists[4], count, bins, (int)Q};
+        cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 16, st);
         if (e != cudaSuccess) return e;
         int tok = log->begin(kStageWfInit, st);
         k_wf_init<<<grid, block, 0, st>>>(S, T, job, pix0 * J.spp, nq, W, A);
@@ -412,7 +453,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
         for (int it = 0; it < passes * J.depth; ++it) {
             // lists alternate between two buffer pairs: the next lists of one iteration are the
             // live lists of the following one (k_wf_swap moves the counts)
-            WfLists L = (it & 1) ? WfLists{lists[2], lists[3], lists[0], lists[1], lists[4], count} : A;
+            WfLists L = (it & 1) ? WfLists{lists[2], lists[3], lists[0], lists[1], lists[4], count, bins, (int)Q} : A;
             tok = log->begin(kStageWfExtend, st);
             k_wf_extend<<<grid, block, 0, st>>>(S, W, L, status);
             log->end(tok, st);
@@ -434,8 +475,28 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
             log->end(tok, st);
             if (mode == 1) {
                 tok = log->begin(kStageWfReplay, st);
-                if (nmaps) k_wf_finish<1, 1, true><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
-                else k_wf_finish<1, 1, false><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                if (binned) {
+                    // one replay kernel per material type present, then the rest
+                    k_wf_bin<<<grid, block, 0, st>>>(S, W, L);
+                    if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) {
+                        if (nmaps) k_wf_finish<1, 1, true, DPPT_MAT_CONDUCTOR_GGX, DPPT_MAT_CONDUCTOR_GGX><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                        else k_wf_finish<1, 1, false, DPPT_MAT_CONDUCTOR_GGX, DPPT_MAT_CONDUCTOR_GGX><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                    }
+                    if (types & (1u << DPPT_MAT_PLASTIC_GGX)) {
+                        if (nmaps) k_wf_finish<1, 1, true, DPPT_MAT_PLASTIC_GGX, DPPT_MAT_PLASTIC_GGX><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                        else k_wf_finish<1, 1, false, DPPT_MAT_PLASTIC_GGX, DPPT_MAT_PLASTIC_GGX><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                    }
+                    if (types & (1u << DPPT_MAT_DIFFUSE)) {
+                        if (nmaps) k_wf_finish<1, 1, true, DPPT_MAT_DIFFUSE, DPPT_MAT_DIFFUSE><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                        else k_wf_finish<1, 1, false, DPPT_MAT_DIFFUSE, DPPT_MAT_DIFFUSE><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                    }
+                    if (nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                    else k_wf_finish<1, 1, false, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                } else if (nmaps) {
+                    k_wf_finish<1, 1, true><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                } else {
+                    k_wf_finish<1, 1, false><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                }
                 log->end(tok, st);
             }
             tok = log->begin(kStageWfSwap, st);
