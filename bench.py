@@ -37,25 +37,47 @@ WORKLOAD = "icosphere50k_256x256_64spp_depth8"
 # light-sample setup 60 (shade stage); the Mueller evaluation and cache store 358
 # (rotations 12, Fresnel 60, GGX D*G 40, next-event estimation 150, fold 96); the
 # replay 620 (dual-number derivatives of the 262-flop evaluation, ~2x = 524, and the
-# adjoint row update a^T W = 96).  The megakernels do the same work in one kernel.
+# adjoint row update a^T W = 96).  The megakernels do the same work in one kernel and trace
+# every ray again in the replay; the wavefront's replay reads the cache pass's hits instead.
 F_NODE, F_TRI, F_SPH = 24, 30, 20
 F_SHADE, F_CACHE, F_REPLAY = 60, 358, 620
 F_VERTEX_PRIMAL = F_SHADE + F_CACHE
 F_VERTEX_ADJOINT = 2 * F_SHADE + F_CACHE + F_REPLAY
 
-# DRAM traffic per launch of the dominant kernel (k_wf_extend, the 4-wide BVH traversal)
-# from one ncu capture of this workload: mean of dram__bytes_read.sum + dram__bytes_write.sum
-# over the 24 launches of one timed step (bytes); None once the kernel has changed since.
-DOMINANT_DRAM_BYTES_PER_LAUNCH = 96.23e6
-DOMINANT_KERNEL = "wf_extend"
+# Algorithmic DRAM bytes of the cache pass (k_wf_finish<MODE, 0>, HBM-bound), per unit:
+# per traced ray (a live path of the pass) the list index, bookkeeping, walk and the vertex
+# record's ids (4 + 16 + 64 + 16); per surface vertex the rest of the vertex record and the
+# visibility (96 + 4), the cache write (124 B of E_v / W_v, + 4 B visibility in the adjoint),
+# the walk, bookkeeping and next-list writes (64 + 4 + 4), and the fold's read of the cache
+# (124); per finished path the raw Stokes write (48) and, in the adjoint, the image adjoint
+# read, the adjoint row write and the replay's start (48 + 48 + 64 + 4 + 4).
+B_CACHE_RAY = 100
+B_CACHE_VERTEX_PRIMAL, B_CACHE_VERTEX_ADJOINT = 420, 424
+B_CACHE_PATH_PRIMAL, B_CACHE_PATH_ADJOINT = 48, 216
+
+# DRAM traffic per launch (bytes) from one ncu capture of this workload: mean of
+# dram__bytes_read.sum + dram__bytes_write.sum over the launches of one timed step;
+# None for a kernel changed since its capture.
+DRAM_BYTES_PER_LAUNCH = {"wf_extend": 63.00e6, "wf_cache": 330.8e6}
+
+
+# floats per vertex of the wavefront cache: E_v 12, compact W_v 19, the hit 4, visibility 1
+WF_CACHE_FLOATS = 36
 
 
 def wave_paths(job) -> int:
     """Paths per wavefront wave: at most 4,194,304 whole pixels and at most 8 GiB of path
-    state (~400 B) plus cache (124 B per vertex) per wave, as the library sizes them."""
-    per_path = 400 + 124 * job.max_depth
+    state (~400 B) plus cache (144 B per vertex) per wave, as the library sizes them."""
+    per_path = 400 + 4 * WF_CACHE_FLOATS * job.max_depth
     cap = min(1 << 22, (8 << 30) // per_path)
     return min(job.num_paths, max(job.spp, cap // job.spp * job.spp))
+
+
+def cache_pass_bytes(w: dict, passes: int) -> float:
+    """Algorithmic DRAM bytes of the cache pass over the work counted in `w`."""
+    if passes == 2:
+        return B_CACHE_RAY * w["rays"] + B_CACHE_VERTEX_ADJOINT * w["vertices"] + B_CACHE_PATH_ADJOINT * w["paths"]
+    return B_CACHE_RAY * w["rays"] + B_CACHE_VERTEX_PRIMAL * w["vertices"] + B_CACHE_PATH_PRIMAL * w["paths"]
 
 
 def stage_flops(w: dict, passes: int) -> dict:
@@ -63,7 +85,7 @@ def stage_flops(w: dict, passes: int) -> dict:
     closest = F_NODE * w["nodes"] + F_TRI * w["tri_tests"] + F_SPH * w["sph_tests"]
     shadow = F_NODE * w["shadow_nodes"] + F_TRI * w["shadow_tri_tests"] + F_SPH * w["shadow_sph_tests"]
     V = w["vertices"]
-    out = {"wf_extend": passes * closest, "wf_shadow": passes * shadow, "wf_shade": passes * V * F_SHADE,
+    out = {"wf_extend": closest, "wf_shadow": shadow, "wf_shade": passes * V * F_SHADE,
            "wf_cache": V * F_CACHE}
     if passes == 2:
         out["wf_replay"] = V * F_REPLAY
@@ -387,6 +409,37 @@ def run_native(args):
     stage_report = {k: {"launches": n, "ms_per_step": ms / K,
                         "tflops": (flops[k] / (ms / 1000.0) / 1e12) if k in flops and ms > 0 else None}
                     for k, (n, ms) in timed.items()}
+    if "wf_cache" in stage_report and timed["wf_cache"][1] > 0:
+        cb = (cache_pass_bytes(work, 2) + (cache_pass_bytes(pw, 1) if lc[0] == 2 else 0)) * K
+        stage_report["wf_cache"]["gbs"] = cb / (timed["wf_cache"][1] / 1000.0) / 1e9
+
+    # the dominant kernel's roofline: the cache pass moves records (HBM-bound); traversal and
+    # the dual-number replay are bound by FP32 arithmetic issued under divergence
+    hbm_peak = float(peaks.get("hbm_gbs") or 6800.0)
+    launch_s = dom_ms / max(dom_launches, 1) / 1e3
+    traffic = DRAM_BYTES_PER_LAUNCH.get(dom)
+    if dom == "wf_cache":
+        byt = (cache_pass_bytes(work, 2) + (cache_pass_bytes(pw, 1) if lc[0] == 2 else 0)) * K
+        ach = byt / max(dom_launches, 1) / launch_s / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": ach / hbm_peak, "traffic": traffic,
+                    "bytes_per_launch": byt / max(dom_launches, 1), "launch_ms": launch_s * 1e3,
+                    "work_units_adjoint_pass": work,
+                    "peak_note": f"{peaks['_source']} HBM copy bandwidth"}
+    else:
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                    "frac_at_loaded_clock": achieved / fp32_peak_loaded,
+                    "traffic": traffic,
+                    "hbm": ({"achieved_gbs": traffic / launch_s / 1e9, "peak_gbs": hbm_peak,
+                             "frac": traffic / launch_s / 1e9 / hbm_peak,
+                             "note": "ncu DRAM bytes per launch (cold caches) / in-bench launch time"}
+                            if traffic else None),
+                    "flops_per_launch": flops.get(dom, 0) / max(dom_launches, 1),
+                    "launch_ms": launch_s * 1e3,
+                    "work_units_adjoint_pass": work,
+                    "peak_note": f"FP32 pipe: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
+                                 f"({peaks['_source']} max clock)"}
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -402,23 +455,9 @@ def run_native(args):
                    "parallelism": f"replicas{world}"},
         "calls_ms": {"render_primal": prim_avg, "render_adjoint": adj_avg},
         "stages": stage_report,
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "frac_at_loaded_clock": achieved / fp32_peak_loaded,
-                     "traffic": DOMINANT_DRAM_BYTES_PER_LAUNCH if dom == DOMINANT_KERNEL else None,
-                     "hbm": ({"achieved_gbs": DOMINANT_DRAM_BYTES_PER_LAUNCH / (dom_ms / max(dom_launches, 1) / 1e3) / 1e9,
-                              "peak_gbs": float(peaks.get("hbm_gbs") or 6800.0),
-                              "frac": DOMINANT_DRAM_BYTES_PER_LAUNCH / (dom_ms / max(dom_launches, 1) / 1e3) / 1e9
-                                      / float(peaks.get("hbm_gbs") or 6800.0),
-                              "note": "ncu DRAM bytes per launch (cold caches) / in-bench launch time"}
-                             if DOMINANT_DRAM_BYTES_PER_LAUNCH and dom == DOMINANT_KERNEL else None),
-                     "flops_per_launch": flops.get(dom, 0) / max(dom_launches, 1),
-                     "launch_ms": dom_ms / max(dom_launches, 1),
-                     "work_units_adjoint_pass": work,
-                     "peak_note": f"FP32 pipe: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
-                                  f"({peaks['_source']} max clock)"},
+        "roofline": roofline,
         "memory": {"workspace_bytes": dctx.query_workspace(adj),
-                   "prb_cache_bytes": (wave_paths(job) * job.max_depth * 31 * 4 if lc[3] == 2 else cache_bytes),
+                   "prb_cache_bytes": (wave_paths(job) * job.max_depth * WF_CACHE_FLOATS * 4 if lc[3] == 2 else cache_bytes),
                    "prb_cache_where": "wavefront workspace" if lc[3] == 2 else "megakernel thread-local memory",
                    "megakernel_local_bytes_per_thread": fp["local_bytes_per_thread"],
                    "megakernel_adjoint_registers": fp["registers"]},

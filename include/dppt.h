@@ -117,7 +117,8 @@ typedef struct {
 
 /* One render job: a camera view rendered at width x height with spp paths per
  * pixel and at most max_depth surface vertices per path (1 <= max_depth <= 128;
- * the cache of a path holds 124 bytes per vertex), seen through the
+ * the cache of a path holds 124 bytes per vertex in the megakernels, 144 in
+ * the wavefront, whose replay reads each vertex's hit from it), seen through the
  * camera filter at num_angles polarizer angles params.theta[theta_offset + a].
  * Path p = pixel * spp + sample draws its randoms from Philox4x64-10 with key
  * (seed ^ pass * 0x9E3779B97F4A7C15, stream) and counter (p, vertex, 0, 0);

@@ -960,22 +960,98 @@ __device__ __forceinline__ void scatter_taps(float* g, const Taps& tp, const flo
 }
 
 // ================================================================== per-vertex actions
-// Where a path's cached E_v / compact W_v live: thread-local arrays (megakernel)
-// or global memory laid out [vertex][component][path] (wavefront).
+// Where a path's cached E_v / compact W_v live: thread-local arrays (megakernel) or one
+// record per (vertex, path) in global memory (wavefront).  Both hold W_v as 19 floats in
+// the order ri.c, ri.s, ro.c, ro.s, A[3], B[3], C[3], S[3], D[3].
+__device__ __forceinline__ void pack_w(const Compact<float>& W, float o[20]) {
+    o[0] = W.ri.c; o[1] = W.ri.s; o[2] = W.ro.c; o[3] = W.ro.s;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        o[4 + c] = W.A[c]; o[7 + c] = W.B[c]; o[10 + c] = W.C[c]; o[13 + c] = W.S[c]; o[16 + c] = W.D[c];
+    }
+    o[19] = 0.0f;
+}
+__device__ __forceinline__ void unpack_w(const float o[19], Compact<float>& W) {
+    W.ri = {o[0], o[1]}; W.ro = {o[2], o[3]};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        W.A[c] = o[4 + c]; W.B[c] = o[7 + c]; W.C[c] = o[10 + c]; W.S[c] = o[13 + c]; W.D[c] = o[16 + c];
+    }
+}
+
 template <int MAXD>
 struct LocalCache {
     float (*cE)[12];
     float (*cW)[19];
     static constexpr int cap = MAXD;
-    __device__ __forceinline__ float& e(int v, int k) const { return cE[v][k]; }
-    __device__ __forceinline__ float& w(int v, int k) const { return cW[v][k]; }
+    __device__ __forceinline__ void put(int v, const float E[12], const Compact<float>& W) const {
+        float o[20];
+        pack_w(W, o);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) cE[v][k] = E[k];
+#pragma unroll
+        for (int k = 0; k < 19; ++k) cW[v][k] = o[k];
+    }
+    __device__ __forceinline__ void get_w(int v, Compact<float>& W) const { unpack_w(cW[v], W); }
+    __device__ __forceinline__ void get_e(int v, float e[12]) const {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) e[k] = cE[v][k];
+    }
+    __device__ __forceinline__ void put_e(int v, const float e[12]) const {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) cE[v][k] = e[k];
+    }
 };
+
+// A vertex of the wavefront's global cache: one 144-byte record per (vertex, path), so a
+// path's record stays whole however sparse the live paths of an iteration become (nine
+// float4s: E_v 12 floats, compact W_v 19, the visibility of the vertex's light sample 1,
+// the closest hit of the ray that made the vertex: t, b1, b2, code).  The replay reads the
+// hit and the visibility instead of tracing the ray and the shadow ray again (it would
+// find exactly the same hits).
+constexpr int kWfCacheComps = 36;
+constexpr int kWfVisComp = 31;
+constexpr int kWfHitComp = 32;
 struct GlobalCache {
     float* base;
     long long Q, q;
     int cap;
-    __device__ __forceinline__ float& e(int v, int k) const { return base[((long long)v * 31 + k) * Q + q]; }
-    __device__ __forceinline__ float& w(int v, int k) const { return base[((long long)v * 31 + 12 + k) * Q + q]; }
+    __device__ __forceinline__ float4* rec(int v) const {
+        return reinterpret_cast<float4*>(base + ((long long)v * Q + q) * kWfCacheComps);
+    }
+    // writes E_v and W_v (and a zero visibility, which the caller sets afterwards)
+    __device__ __forceinline__ void put(int v, const float E[12], const Compact<float>& W) const {
+        float o[20];
+        pack_w(W, o);
+        float4* r = rec(v);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r[k] = make_float4(E[4 * k], E[4 * k + 1], E[4 * k + 2], E[4 * k + 3]);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) r[3 + k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+    }
+    __device__ __forceinline__ void get_w(int v, Compact<float>& W) const {
+        const float4* r = rec(v);
+        float o[20];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const float4 t = r[3 + k];
+            o[4 * k] = t.x; o[4 * k + 1] = t.y; o[4 * k + 2] = t.z; o[4 * k + 3] = t.w;
+        }
+        unpack_w(o, W);
+    }
+    __device__ __forceinline__ void get_e(int v, float e[12]) const {
+        const float4* r = rec(v);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 t = r[k];
+            e[4 * k] = t.x; e[4 * k + 1] = t.y; e[4 * k + 2] = t.z; e[4 * k + 3] = t.w;
+        }
+    }
+    __device__ __forceinline__ void put_e(int v, const float e[12]) const {
+        float4* r = rec(v);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r[k] = make_float4(e[4 * k], e[4 * k + 1], e[4 * k + 2], e[4 * k + 3]);
+    }
 };
 
 // The replayed vertex's local vector-Jacobian product: J_c = a_c^T (E_c + W_c L_c) with
@@ -1102,16 +1178,7 @@ struct PathVis {
                 ++n;
                 return;
             }
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) C.e(n, 4 * c + k) = E[c][k];
-            C.w(n, 0) = W.ri.c; C.w(n, 1) = W.ri.s; C.w(n, 2) = W.ro.c; C.w(n, 3) = W.ro.s;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                C.w(n, 4 + c) = W.A[c]; C.w(n, 7 + c) = W.B[c]; C.w(n, 10 + c) = W.C[c];
-                C.w(n, 13 + c) = W.S[c]; C.w(n, 16 + c) = W.D[c];
-            }
+            C.put(n, &E[0][0], W);
             ++n;
             return;
         }
@@ -1127,29 +1194,22 @@ struct PathVis {
         for (int k = 0; k < 12; ++k) L[k] = has_last ? lastE[k] : 0.0f;
         int v = n - 1;
         if (has_last) {
-            if (adjoint && v >= 1)
-#pragma unroll
-                for (int k = 0; k < 12; ++k) C.e(v, k) = L[k];
+            if (adjoint && v >= 1) C.put_e(v, L);
             --v;
         }
         for (; v >= 0; --v) {
             Compact<float> W;
-            W.ri = {C.w(v, 0), C.w(v, 1)}; W.ro = {C.w(v, 2), C.w(v, 3)};
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                W.A[c] = C.w(v, 4 + c); W.B[c] = C.w(v, 7 + c); W.C[c] = C.w(v, 10 + c);
-                W.S[c] = C.w(v, 13 + c); W.D[c] = C.w(v, 16 + c);
-            }
+            C.get_w(v, W);
+            float e[12];
+            C.get_e(v, e);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 float y[4];
                 compact_apply(W, c, &L[4 * c], y);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) L[4 * c + k] = C.e(v, 4 * c + k) + y[k];
+                for (int k = 0; k < 4; ++k) L[4 * c + k] = e[4 * c + k] + y[k];
             }
-            if (adjoint && v >= 1)
-#pragma unroll
-                for (int k = 0; k < 12; ++k) C.e(v, k) = L[k];
+            if (adjoint && v >= 1) C.put_e(v, L);
         }
 #pragma unroll
         for (int k = 0; k < 12; ++k) L0[k] = L[k];
@@ -1161,8 +1221,7 @@ struct PathVis {
         eval_vertex<D3, MT, NM>(*S, *P, vc, E, W, &f);
         float Ln[3][4];
         if (i + 1 < n) {
-#pragma unroll
-            for (int k = 0; k < 12; ++k) Ln[k >> 2][k & 3] = C.e(i + 1, k);
+            C.get_e(i + 1, &Ln[0][0]);
         } else {
 #pragma unroll
             for (int k = 0; k < 12; ++k) Ln[k >> 2][k & 3] = 0.0f;

@@ -8,10 +8,11 @@
 // 16-byte-aligned records that a thread moves with float4 loads and stores:
 // the walk (64 B), path bookkeeping (16 B), the vertex handed from shade to
 // finish (112 B), the hit (16 B), the adjoint row (48 B), the raw Stokes
-// value (48 B); the per-vertex cache of E_i / W_i is laid out
-// [vertex][component][path] so that a warp's accesses are contiguous.  The
-// replay re-traces the path with the same stage code and Philox counters as
-// the cache pass.  Every stage reads its list length from device memory and
+// value (48 B); the per-vertex cache holds one 144-byte record per (vertex,
+// path), whole whatever fraction of the wave's paths is still live.  The
+// replay walks the path again with the same stage code and Philox counters as
+// the cache pass, but reads each vertex's closest hit and light-sample
+// visibility from the cache instead of tracing its two rays again.  Every stage reads its list length from device memory and
 // loops over it with a grid stride, so a wave is a fixed sequence of launches.
 #include "trace.cuh"
 
@@ -75,10 +76,13 @@ __device__ __forceinline__ void put_vertex(WfVtx* p, const VCtx& vc, const NeePe
     r.ids = make_int4(vc.prim, (vc.mat & 0xffff) | (ne.l << 16), vc.light, (int)f);
     *p = r;
 }
+// (the ids first: a path whose ray missed reads 16 of the record's 112 bytes)
 __device__ __forceinline__ bool get_vertex(const WfVtx* p, const Walk& w, VCtx& vc, NeePending& ne, Shade& sh) {
-    WfVtx r = *p;
+    WfVtx r;
+    r.ids = p->ids;
     unsigned f = (unsigned)r.ids.w;
     if (!(f & kFHit)) return false;
+    r.x_tu = p->x_tu; r.ng_tv = p->ng_tv; r.wi_pdf = p->wi_pdf; r.wl_ps = p->wl_ps; r.misc = p->misc; r.mat = p->mat;
     vc.x = {r.x_tu.x, r.x_tu.y, r.x_tu.z}; vc.tu = r.x_tu.w;
     vc.ng = {r.ng_tv.x, r.ng_tv.y, r.ng_tv.z}; vc.tv = r.ng_tv.w;
     vc.wo = -w.d;
@@ -152,13 +156,14 @@ __global__ void k_wf_init(const DScene S, const __grid_constant__ JobTable T, in
 }
 
 // Closest hits of the live paths, one ray per thread in a grid-stride loop.  The list
-// keeps the samples of a pixel together, so a warp's rays share their origin.
+// keeps the samples of a pixel together, so a warp's rays share their origin.  Only the
+// cache pass traces: replayed paths read their hits from the cache (kWfHitComp).
 __global__ void __launch_bounds__(512, DPPT_WF_TRAVERSE_MIN_BLOCKS)
 k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
-    const int n0 = L.count[0], n = n0 + L.count[1];
+    const int n = L.count[0];
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        const int q = list_at(L, n0, idx);
+        const int q = L.l0[idx];
         const float4 a = W.walk[q].a, b = W.walk[q].b;
         HitRec h;
         float4 out;
@@ -172,16 +177,46 @@ k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
     }
 }
 
+// Appends path q to replay bin b.  Appends are warp-aggregated: the lanes of a warp going
+// to the same bin take consecutive slots with one atomic.
+__device__ __forceinline__ void bin_append(const WfLists& L, int b, int q) {
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, b);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(L.count + 8 + b, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    L.bins[(long long)b * L.binQ + base + __popc(peers & ((1u << lane) - 1u))] = q;
+}
+
+enum : int { kShadeStoreHits = 1, kShadeBinReplay = 2 };
+
+// Surface data, light sample and BSDF sample of each live path's new vertex.  In the
+// adjoint (kShadeStoreHits), a cache-pass path stores its hit in the cache at its vertex
+// slot and a replayed path takes its hit and its light sample's visibility from there;
+// with kShadeBinReplay each replayed path is appended to the bin of its vertex's material
+// type (kBinOther for misses and the types without a replay kernel of their own).
 template <bool NM>
-__global__ void k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfState W, WfLists L) {
+__global__ void k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfState W, WfLists L,
+                           int flags) {
     const int n0 = L.count[0], n = n0 + L.count[1];
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
         const int q = list_at(L, n0, idx);
-        const float4 hv = W.hit[q];
+        const bool replay = idx >= n0;
+        const int v = __float_as_int(W.walk[q].c.w) & 0xff;     // the vertex's slot (see put_walk)
+        float* rec = W.cache + ((long long)(v - 1) * W.Q + q) * kWfCacheComps;
+        float4 hv;
+        if (replay) {
+            hv = *reinterpret_cast<const float4*>(rec + kWfHitComp);
+        } else {
+            hv = W.hit[q];
+            if (flags & kShadeStoreHits) *reinterpret_cast<float4*>(rec + kWfHitComp) = hv;
+        }
         const int code = __float_as_int(hv.w);
         if (code == kMissCode) {
             W.vtx[q].ids = make_int4(0, 0, 0, 0);
+            if (replay && (flags & kShadeBinReplay)) bin_append(L, kBinOther, q);
             continue;
         }
         HitRec h;
@@ -197,6 +232,14 @@ __global__ void k_wf_shade(const DScene S, const DParams P, const __grid_constan
         Shade sh;
         walk_shade<NM>(S, P, T.job[m.job], pid, w, h, vc, ne, sh);
         put_vertex(W.vtx + q, vc, ne, sh);
+        if (replay) {
+            W.visible[q] = __float_as_int(rec[kWfVisComp]);
+            if (flags & kShadeBinReplay) {
+                const int t = __ldg(&S.mats[vc.mat].type);
+                bin_append(L, (kBinnedTypes >> t) & 1u ? t : kBinOther, q);
+            }
+            continue;
+        }
         if (ne.state == 1) {
             W.ray[q] = WfRay{make_float4(ne.o2.x, ne.o2.y, ne.o2.z, ne.tmax), make_float4(ne.dir.x, ne.dir.y, ne.dir.z, 0.f)};
             L.shadow[atomicAdd(L.count + 4, 1)] = q;
@@ -214,29 +257,6 @@ k_wf_shadow(const DScene S, WfState W, WfLists L, unsigned* status) {
         const WfRay r = W.ray[q];
         W.visible[q] = trace_any<false>(S, f3{r.o_tmax.x, r.o_tmax.y, r.o_tmax.z}, f3{r.dir.x, r.dir.y, r.dir.z},
                                         r.o_tmax.w, status, nullptr) ? 0 : 1;
-    }
-}
-
-// Sorts the replay list into per-material bins.  Appends are warp-aggregated: the lanes
-// of a warp going to the same bin take consecutive slots with one atomic.
-__global__ void k_wf_bin(const DScene S, WfState W, WfLists L) {
-    const int n = L.count[1];
-    const int stride = gridDim.x * blockDim.x;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        const int q = L.l1[idx];
-        const int4 ids = W.vtx[q].ids;
-        int b = kBinOther;
-        if ((unsigned)ids.w & kFHit) {
-            const int t = __ldg(&S.mats[ids.y & 0xffff].type);
-            if ((kBinnedTypes >> t) & 1u) b = t;
-        }
-        const unsigned act = __activemask();
-        const unsigned peers = __match_any_sync(act, b);
-        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(L.count + 8 + b, __popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        L.bins[(long long)b * L.binQ + base + __popc(peers & ((1u << lane) - 1u))] = q;
     }
 }
 
@@ -285,20 +305,26 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
         vis.n = (m.pni >> 8) & 0xff; vis.i = (m.pni >> 16) & 0xff; vis.phase = PHASE;
         vis.has_last = false;          // set, and consumed by the fold, within this launch
         vis.adjoint = MODE == 1;
-        if (PHASE == 1) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float4 r = W.arow[3 * (long long)q + c];
-                vis.a[c][0] = r.x; vis.a[c][1] = r.y; vis.a[c][2] = r.z; vis.a[c][3] = r.w;
-            }
-        }
         VCtx vc;
         NeePending ne;
         Shade sh;
         bool cont = false;
         if (get_vertex(W.vtx + q, w, vc, ne, sh)) {
+            if (PHASE == 1) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float4 r = W.arow[3 * (long long)q + c];
+                    vis.a[c][0] = r.x; vis.a[c][1] = r.y; vis.a[c][2] = r.z; vis.a[c][3] = r.w;
+                }
+            }
             if (NM) apply_normal_map(S, P, vc);
-            cont = walk_finish(S, P, w, vc, ne, W.visible[q] != 0, sh, vis);
+            const int visible = W.visible[q];
+            const int slot = w.v - 1;
+            cont = walk_finish(S, P, w, vc, ne, visible != 0, sh, vis);
+            // the replay of this vertex reads it back (k_wf_shade); stored after walk_finish,
+            // whose cache write zeroes it
+            if (MODE == 1 && PHASE == 0)
+                W.cache[((long long)slot * W.Q + q) * kWfCacheComps + kWfVisComp] = __int_as_float(visible);
         }
         bool done = false;
         int phase = PHASE;
@@ -400,7 +426,7 @@ size_t wavefront_bytes(long long Q, int cap) {
     b += 5 * align_up(sizeof(int) * Q);         // lists
     b += align_up(sizeof(int) * 16);
     b += align_up(sizeof(int) * 8 * Q);         // replay bins
-    b += align_up(sizeof(float) * 31 * (size_t)cap * Q);
+    b += align_up(sizeof(float) * kWfCacheComps * (size_t)cap * Q);
     return b;
 }
 
@@ -458,8 +484,9 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
             k_wf_extend<<<grid, block, 0, st>>>(S, W, L, status);
             log->end(tok, st);
             tok = log->begin(kStageWfShade, st);
-            if (nmaps) k_wf_shade<true><<<grid, block, 0, st>>>(S, P, T, W, L);
-            else k_wf_shade<false><<<grid, block, 0, st>>>(S, P, T, W, L);
+            const int sflags = (mode == 1 ? kShadeStoreHits : 0) | (mode == 1 && binned ? kShadeBinReplay : 0);
+            if (nmaps) k_wf_shade<true><<<grid, block, 0, st>>>(S, P, T, W, L, sflags);
+            else k_wf_shade<false><<<grid, block, 0, st>>>(S, P, T, W, L, sflags);
             log->end(tok, st);
             tok = log->begin(kStageWfShadow, st);
             k_wf_shadow<<<grid, block, 0, st>>>(S, W, L, status);
@@ -476,8 +503,8 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
             if (mode == 1) {
                 tok = log->begin(kStageWfReplay, st);
                 if (binned) {
-                    // one replay kernel per material type present, then the rest
-                    k_wf_bin<<<grid, block, 0, st>>>(S, W, L);
+                    // one replay kernel per material type present (k_wf_shade binned the
+                    // replay list), then the rest
                     if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) {
                         if (nmaps) k_wf_finish<1, 1, true, DPPT_MAT_CONDUCTOR_GGX, DPPT_MAT_CONDUCTOR_GGX><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
                         else k_wf_finish<1, 1, false, DPPT_MAT_CONDUCTOR_GGX, DPPT_MAT_CONDUCTOR_GGX><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
