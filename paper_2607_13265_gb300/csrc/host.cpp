@@ -759,9 +759,7 @@ static long long wave_paths(const dppt_job* jobs, int njobs) {
     return q;
 }
 
-static size_t scalar_smem(const dppt_scene* s) {
-    return sizeof(float) * (size_t)(s->d.num_ior + s->d.num_sheets + 12 * s->d.num_lights);
-}
+static size_t scalar_smem(const dppt_scene* s) { return sgrad_bytes(sgrad_scalars(s->d)); }
 
 dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
                                const dppt_params* params, float* image, void* stream) {

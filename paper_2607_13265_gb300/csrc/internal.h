@@ -10,11 +10,11 @@ namespace dppt {
 
 constexpr int kMaxJobsPerLaunch = 64;
 constexpr int kBvhStack = 64;
-constexpr int kMaxDepth = 128;
+constexpr int kMaxDepth = 128;      // surface vertices per path (largest cache bucket)
 // traversal of the 4-wide BVH (1) or of the binary one (0)
 #ifndef DPPT_BVH4
 #define DPPT_BVH4 1
-#endif      // surface vertices per path (largest cache bucket)
+#endif
 
 struct DMat {
     int type, albedo_tex, rough_tex, ior_index, sheet_index, normal_tex;
@@ -52,6 +52,16 @@ struct DScene {
     int scatter_lane;       // adjoint: texel gradients one atomic per lane (1) or per warp group (0)
     int mat_types;          // bit t set when a triangle or sphere uses a material of type t
 };
+
+// Scalar gradients (indices of refraction, sheet angles, emitter Stokes vectors) are summed
+// per block in shared memory and flushed with one global atomic per block and scalar.  Each
+// scalar has 32 copies when they fit in 16 KB: lane l of a warp adds to copy l, so the lanes
+// of a warp adding to one scalar use 32 banks instead of serialising on one address.
+inline __host__ __device__ int sgrad_scalars(const DScene& S) { return S.num_ior + S.num_sheets + 12 * S.num_lights; }
+inline __host__ __device__ int sgrad_copies(int nscal) { return nscal * 32 * (int)sizeof(float) <= 16384 ? 32 : 1; }
+inline __host__ __device__ size_t sgrad_bytes(int nscal) {
+    return sizeof(float) * (size_t)nscal * (size_t)sgrad_copies(nscal);
+}
 
 struct DParams {
     const float* tex;

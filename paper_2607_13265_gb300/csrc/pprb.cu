@@ -97,8 +97,7 @@ k_pprb(const DScene S, const DParams P, const DGrads G, const __grid_constant__ 
        unsigned long long* counter, unsigned* status, int persistent, float sigma) {
     extern __shared__ float sgrad[];
     __shared__ long long s_chunk;
-    const int nscal = S.num_ior + S.num_sheets + 12 * S.num_lights;
-    for (int k = threadIdx.x; k < nscal; k += blockDim.x) sgrad[k] = 0.0f;
+    sgrad_zero(sgrad, sgrad_scalars(S));
     float beta[48];
     WorkCount wc = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     long long chunk = blockIdx.x;
@@ -156,19 +155,7 @@ k_pprb(const DScene S, const DParams P, const DGrads G, const __grid_constant__ 
         }
         if (!persistent) break;
     }
-    __syncthreads();
-    float* gdst[3] = {G.ior, G.sheet, G.le};
-    const int nI = S.num_ior, nS = S.num_sheets;
-    for (int k = threadIdx.x; k < nscal; k += blockDim.x) {
-        float v = sgrad[k];
-        if (v == 0.0f) continue;
-        float* base;
-        int off;
-        if (k < nI) { base = gdst[0]; off = k; }
-        else if (k < nI + nS) { base = gdst[1]; off = k - nI; }
-        else { base = gdst[2]; off = k - nI - nS; }
-        if (base) atomicAdd(base + off, v);
-    }
+    sgrad_flush(S, G, sgrad);
 }
 
 cudaError_t launch_pprb(const DScene& S, const DParams& P, const DGrads& G, const JobTable& T, const LaunchCfg& L,
@@ -177,7 +164,7 @@ cudaError_t launch_pprb(const DScene& S, const DParams& P, const DGrads& G, cons
     long long g = pers ? L.grid : T.total_chunks;
     if (g <= 0) return cudaSuccess;
     if (g > 0x7fffffffLL) g = 0x7fffffffLL;
-    size_t sm = sizeof(float) * (size_t)(S.num_ior + S.num_sheets + 12 * S.num_lights);
+    const size_t sm = sgrad_bytes(sgrad_scalars(S));
     k_pprb<<<(int)g, L.block, sm, st>>>(S, P, G, T, counter, status, pers, sigma);
     return cudaGetLastError();
 }

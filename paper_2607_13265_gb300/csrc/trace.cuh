@@ -929,6 +929,36 @@ __device__ __forceinline__ void atomic_add_grouped(float* base, long long idx, f
     }
     if (lane == __ffs(peers) - 1 && sum != 0.0f) atomicAdd(base + idx, sum);
 }
+// The block's scalar-gradient accumulators (sgrad_copies copies of each scalar), zeroed by
+// all threads of the block at its start.
+__device__ __forceinline__ void sgrad_zero(float* sg, int nscal) {
+    const int n = nscal * sgrad_copies(nscal);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) sg[k] = 0.0f;
+    __syncthreads();
+}
+__device__ __forceinline__ void sgrad_add(const DScene& S, float* sg, int k, float v) {
+    const int copies = sgrad_copies(sgrad_scalars(S));
+    atomicAdd(sg + k * copies + (threadIdx.x & (copies - 1)), v);
+}
+// after the block's last addition: sums the copies (read in a rotated order, one bank per
+// lane) and adds each nonzero scalar to its gradient with one global atomic
+__device__ __forceinline__ void sgrad_flush(const DScene& S, const DGrads& G, const float* sg) {
+    __syncthreads();
+    const int nscal = sgrad_scalars(S), copies = sgrad_copies(nscal);
+    const int nI = S.num_ior, nS = S.num_sheets;
+    for (int k = threadIdx.x; k < nscal; k += blockDim.x) {
+        float v = 0.0f;
+        for (int c = 0; c < copies; ++c) v += sg[k * copies + ((c + k) & (copies - 1))];
+        if (v == 0.0f) continue;
+        float* base;
+        int off;
+        if (k < nI) { base = G.ior; off = k; }
+        else if (k < nI + nS) { base = G.sheet; off = k - nI; }
+        else { base = G.le; off = k - nI - nS; }
+        if (base) atomicAdd(base + off, v);
+    }
+}
+
 // adds vals[c] * w[k] at tp.idx[k] + min(c, ch - 1) for the NC values and the four taps
 // (kept as a loop: the replay kernel is bound by instruction fetch, and sixteen inlined
 // copies of the grouping code would enlarge it)
@@ -1101,14 +1131,14 @@ __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, 
                 float g[4] = {a[c][0], a[c][1], a[c][2], a[c][3]};
                 rot_apply_row(Re, g);
                 for (int k = 0; k < 4; ++k)
-                    if (g[k] != 0.0f) atomicAdd(sgrad + base + 12 * vc.light + 4 * c + k, g[k] * vc.w_emit);
+                    if (g[k] != 0.0f) sgrad_add(*S, sgrad, base + 12 * vc.light + 4 * c + k, g[k] * vc.w_emit);
             }
             if (vc.nee) {
                 float g[4] = {a[c][0], a[c][1], a[c][2], a[c][3]};
                 compact_row(fv, c, g);
                 rot_apply_row(Rle, g);
                 for (int k = 0; k < 4; ++k)
-                    if (g[k] != 0.0f) atomicAdd(sgrad + base + 12 * vc.nee_light + 4 * c + k, g[k] * vc.nee_w);
+                    if (g[k] != 0.0f) sgrad_add(*S, sgrad, base + 12 * vc.nee_light + 4 * c + k, g[k] * vc.nee_w);
             }
         }
     }
@@ -1116,10 +1146,10 @@ __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, 
     f3 nN, nT, nB;
     const bool nm = NM && m.normal_tex >= 0 && nmap_frame(*S, m, vc, nN, nT, nB);
     if (!nm && (m.type == DPPT_MAT_SMOOTH_DIELECTRIC || m.type == DPPT_MAT_PLASTIC_GGX)) {
-        if (g_eta != 0.0f) atomicAdd(sgrad + m.ior_index, g_eta);
+        if (g_eta != 0.0f) sgrad_add(*S, sgrad, m.ior_index, g_eta);
     }
     if (m.type == DPPT_MAT_POLARIZER_SHEET || m.type == DPPT_MAT_RETARDER_SHEET) {
-        if (g_slot0 != 0.0f) atomicAdd(sgrad + S->num_ior + m.sheet_index, g_slot0);
+        if (g_slot0 != 0.0f) sgrad_add(*S, sgrad, S->num_ior + m.sheet_index, g_slot0);
     }
     if (nm) {
         // normal map: the slots are the derivatives w.r.t. the three components of n = 2 c - 1
@@ -1272,8 +1302,7 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
         unsigned long long* counter, unsigned* status, int persistent, unsigned long long* work) {
     extern __shared__ float sgrad[];
     __shared__ long long s_chunk;
-    const int nscal = MODE == 1 ? S.num_ior + S.num_sheets + 12 * S.num_lights : 0;
-    for (int k = threadIdx.x; k < nscal; k += blockDim.x) sgrad[k] = 0.0f;
+    if (MODE == 1) sgrad_zero(sgrad, sgrad_scalars(S));
     float cE[MAXD][12];
     float cW[MAXD][19];
     WorkCount wc = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
@@ -1355,21 +1384,7 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
         atomicAdd(work + 8, (unsigned long long)wc.sph_tests);
         atomicAdd(work + 9, (unsigned long long)wc.shadow_sph_tests);
     }
-    if (MODE == 1) {
-        __syncthreads();
-        float* gdst[3] = {G.ior, G.sheet, G.le};
-        const int nI = S.num_ior, nS = S.num_sheets;
-        for (int k = threadIdx.x; k < nscal; k += blockDim.x) {
-            float v = sgrad[k];
-            if (v == 0.0f) continue;
-            float* base;
-            int off;
-            if (k < nI) { base = gdst[0]; off = k; }
-            else if (k < nI + nS) { base = gdst[1]; off = k - nI; }
-            else { base = gdst[2]; off = k - nI - nS; }
-            if (base) atomicAdd(base + off, v);
-        }
-    }
+    if (MODE == 1) sgrad_flush(S, G, sgrad);
 }
 
 // one translation unit per cache depth instantiates its kernels and launchers
@@ -1384,7 +1399,7 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
         if (mode == 0)                                                                                           \
             k_trace<B, 0, false><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, nullptr);         \
         else if (mode == 1) {                                                                                    \
-            size_t sm = sizeof(float) * (size_t)(S.num_ior + S.num_sheets + 12 * S.num_lights);                 \
+            size_t sm = sgrad_bytes(sgrad_scalars(S));                                                          \
             k_trace<B, 1, false><<<(int)g, L.block, sm, st>>>(S, P, G, T, counter, status, pers, nullptr);        \
         } else                                                                                                   \
             k_trace<B, 0, true><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, work);             \

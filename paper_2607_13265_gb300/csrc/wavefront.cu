@@ -260,22 +260,6 @@ k_wf_shadow(const DScene S, WfState W, WfLists L, unsigned* status) {
     }
 }
 
-__device__ __forceinline__ void flush_scalars(const DScene& S, const DGrads& G, float* sgrad, int nscal) {
-    __syncthreads();
-    float* gdst[3] = {G.ior, G.sheet, G.le};
-    const int nI = S.num_ior, nS = S.num_sheets;
-    for (int k = threadIdx.x; k < nscal; k += blockDim.x) {
-        float v = sgrad[k];
-        if (v == 0.0f) continue;
-        float* base;
-        int off;
-        if (k < nI) { base = gdst[0]; off = k; }
-        else if (k < nI + nS) { base = gdst[1]; off = k - nI; }
-        else { base = gdst[2]; off = k - nI - nS; }
-        if (base) atomicAdd(base + off, v);
-    }
-}
-
 // Per-vertex action of one pass.  PHASE 0 (cache pass): cache E_i / W_i; at the
 // end of the walk fold the cache, store the path's raw Stokes value and, for the
 // adjoint (MODE 1), start the replay.  PHASE 1: the replay (MODE 1 only).
@@ -284,11 +268,7 @@ __global__ void __launch_bounds__(128, PHASE == 1 ? DPPT_WF_REPLAY_MIN_BLOCKS : 
 k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_constant__ JobTable T, WfState W, WfLists L,
             unsigned* sig) {
     extern __shared__ float sgrad[];
-    const int nscal = PHASE == 1 ? S.num_ior + S.num_sheets + 12 * S.num_lights : 0;
-    if (PHASE == 1) {
-        for (int k = threadIdx.x; k < nscal; k += blockDim.x) sgrad[k] = 0.0f;
-        __syncthreads();
-    }
+    if (PHASE == 1) sgrad_zero(sgrad, sgrad_scalars(S));
     // the pass's list: the cache list, the replay list, or one replay bin
     const int* list = PHASE == 0 ? L.l0 : BIN < 0 ? L.l1 : L.bins + (long long)BIN * L.binQ;
     const int count = PHASE == 0 ? L.count[0] : BIN < 0 ? L.count[1] : L.count[8 + (BIN < 0 ? 0 : BIN)];
@@ -380,7 +360,7 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
             put_walk(W.walk + q, w);
         }
     }
-    if (PHASE == 1) flush_scalars(S, G, sgrad, nscal);
+    if (PHASE == 1) sgrad_flush(S, G, sgrad);
 }
 
 // the next lists become the live lists
@@ -462,7 +442,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
     const unsigned types = (unsigned)S.mat_types;
     const bool binned = DPPT_WF_BIN_REPLAY && (types & kBinnedTypes) != 0;
     const int passes = mode == 1 ? 2 : 1;
-    const size_t smem = mode == 1 ? sizeof(float) * (size_t)(S.num_ior + S.num_sheets + 12 * S.num_lights) : 0;
+    const size_t smem = mode == 1 ? sgrad_bytes(sgrad_scalars(S)) : 0;
     for (long long pix0 = 0; pix0 < npix; pix0 += pix_per_wave) {
         const long long wp = std::min(pix_per_wave, npix - pix0);
         const int nq = (int)(wp * J.spp);
