@@ -104,7 +104,9 @@ __device__ __forceinline__ float sphere_test(float4 s, f3 o, f3 d, float tmax) {
     return -1.0f;
 }
 
-__device__ __forceinline__ f3 safe_inv(f3 d) { return {1.0f / d.x, 1.0f / d.y, 1.0f / d.z}; }
+// 1 / d with components of magnitude below 1e-20 replaced by +-1e-20 (finite slab distances)
+__device__ __forceinline__ float safe_rcp(float x) { return 1.0f / (fabsf(x) > 1e-20f ? x : copysignf(1e-20f, x)); }
+__device__ __forceinline__ f3 safe_inv(f3 d) { return {safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z)}; }
 
 // BVH traversal in the while-while form with postponed leaves (Aila & Laine,
 // "Understanding the efficiency of ray traversal on GPUs", HPG 2009): a lane
@@ -121,12 +123,16 @@ struct Trav {
     f3 o, d, inv, oi;
     float t, b1, b2;
     int prim, slot, sp, ref;
+    int nx, ny, nz;     // 4-wide nodes: float4 offsets of the near planes per axis (far = near ^ 1)
 };
 
 __device__ __forceinline__ void trav_begin(Trav& r, f3 o, f3 d, float t) {
     r.o = o; r.d = d;
     r.inv = safe_inv(d);
     r.oi = {o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z};
+    r.nx = r.inv.x < 0.0f ? 1 : 0;
+    r.ny = r.inv.y < 0.0f ? 3 : 2;
+    r.nz = r.inv.z < 0.0f ? 5 : 4;
     r.t = t; r.b1 = r.b2 = 0.0f;
     r.prim = -1; r.slot = -1; r.sp = 0; r.ref = 0;
 }
@@ -179,8 +185,11 @@ __device__ __forceinline__ bool trav_round(const DScene& S, Trav& r, int* stack,
 
 // One round over the 4-wide BVH, with the same while-while structure: a node's four
 // child boxes are tested together, the nearest hit child is descended and the other hits
-// are pushed far to near (for any-hit queries in node order).  COUNT counts a node visit
-// as two units of two child boxes, the unit of the binary tree.
+// are pushed far to near (for any-hit queries in node order).  The slab test reads each
+// axis's near and far planes by the sign of the ray direction (Williams et al., "An
+// efficient and robust ray-box intersection algorithm", 2005), so no min/max of the two
+// plane distances is needed.  COUNT counts a node visit as two units of two child boxes,
+// the unit of the binary tree.
 __device__ __forceinline__ void cswap(float& ta, int& ra, float& tb, int& rb) {
     if (tb < ta) { float t = ta; ta = tb; tb = t; int r = ra; ra = rb; rb = r; }
 }
@@ -189,23 +198,24 @@ __device__ __forceinline__ bool trav4_round(const DScene& S, Trav& r, int* stack
     int leaf = kTravDone;
     while (r.ref >= 0 && r.ref != kTravDone) {
         const float4* nd = S.nodes4 + 8 * r.ref;
-        const float4 lx = __ldg(nd), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
-        const float4 lz = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
+        const float4 nx = __ldg(nd + r.nx), fx = __ldg(nd + (r.nx ^ 1));
+        const float4 ny = __ldg(nd + r.ny), fy = __ldg(nd + (r.ny ^ 1));
+        const float4 nz = __ldg(nd + r.nz), fz = __ldg(nd + (r.nz ^ 1)), rf = __ldg(nd + 6);
         const int cnt = __float_as_int(__ldg(&nd[7].x));
         if (COUNT) { if (ANY) wc->shadow_nodes += 2; else wc->nodes += 2; }
-        const float blx[4] = {lx.x, lx.y, lx.z, lx.w}, bhx[4] = {hx.x, hx.y, hx.z, hx.w};
-        const float bly[4] = {ly.x, ly.y, ly.z, ly.w}, bhy[4] = {hy.x, hy.y, hy.z, hy.w};
-        const float blz[4] = {lz.x, lz.y, lz.z, lz.w}, bhz[4] = {hz.x, hz.y, hz.z, hz.w};
+        const float bnx[4] = {nx.x, nx.y, nx.z, nx.w}, bfx[4] = {fx.x, fx.y, fx.z, fx.w};
+        const float bny[4] = {ny.x, ny.y, ny.z, ny.w}, bfy[4] = {fy.x, fy.y, fy.z, fy.w};
+        const float bnz[4] = {nz.x, nz.y, nz.z, nz.w}, bfz[4] = {fz.x, fz.y, fz.z, fz.w};
         const int cr[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
         float t[4];
         int c[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float x0 = fmaf(blx[k], r.inv.x, -r.oi.x), x1 = fmaf(bhx[k], r.inv.x, -r.oi.x);
-            const float y0 = fmaf(bly[k], r.inv.y, -r.oi.y), y1 = fmaf(bhy[k], r.inv.y, -r.oi.y);
-            const float z0 = fmaf(blz[k], r.inv.z, -r.oi.z), z1 = fmaf(bhz[k], r.inv.z, -r.oi.z);
-            const float tn = fmax3(fminf(x0, x1), fminf(y0, y1), fmaxf(fminf(z0, z1), 0.0f));
-            const float tf = fmin3(fmaxf(x0, x1), fmaxf(y0, y1), fminf(fmaxf(z0, z1), r.t));
+            const float x0 = fmaf(bnx[k], r.inv.x, -r.oi.x), x1 = fmaf(bfx[k], r.inv.x, -r.oi.x);
+            const float y0 = fmaf(bny[k], r.inv.y, -r.oi.y), y1 = fmaf(bfy[k], r.inv.y, -r.oi.y);
+            const float z0 = fmaf(bnz[k], r.inv.z, -r.oi.z), z1 = fmaf(bfz[k], r.inv.z, -r.oi.z);
+            const float tn = fmax3(x0, y0, fmaxf(z0, 0.0f));
+            const float tf = fmin3(x1, y1, fminf(z1, r.t));
             const bool hit = k < cnt && tn <= tf;
             t[k] = hit ? tn : INFINITY;
             c[k] = hit ? cr[k] : kTravDone;
