@@ -122,7 +122,12 @@ struct WfLists {
     int* next0;
     int* next1;
     int* shadow;
-    int* count;   // [0] n0, [1] n1, [2] next0, [3] next1, [4] shadow, [8 + b] replay bin b
+    // counts of this iteration: [0] n0, [1] n1, [4] shadow, [8 + b] replay bin b; nxt[0], nxt[1]:
+    // the next lists' lengths.  The two 16-int halves of the count array alternate between
+    // iterations (the next counts of one are the live counts of the following one), and each
+    // iteration's k_wf_extend zeroes the counts the iteration appends to.
+    int* cur;
+    int* nxt;
     int* bins;    // replay paths binned by the material type of their vertex: bin b at bins + b * Q
     int binQ;
 };
@@ -151,7 +156,7 @@ __global__ void k_wf_init(const DScene S, const __grid_constant__ JobTable T, in
         put_walk(W.walk + q, w);
         W.meta[q] = WfMeta{(unsigned)pid, (unsigned)(pid >> 32), job, 0};
         L.l0[q] = q;
-        if (q == 0) { L.count[0] = nq; L.count[1] = 0; }
+        if (q == 0) { L.cur[0] = nq; L.cur[1] = 0; }
     }
 }
 
@@ -160,7 +165,11 @@ __global__ void k_wf_init(const DScene S, const __grid_constant__ JobTable T, in
 // cache pass traces: replayed paths read their hits from the cache (kWfHitComp).
 __global__ void __launch_bounds__(512, DPPT_WF_TRAVERSE_MIN_BLOCKS)
 k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
-    const int n = L.count[0];
+    const int n = L.cur[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        L.nxt[0] = 0; L.nxt[1] = 0; L.cur[4] = 0;
+        for (int b = 8; b < 16; ++b) L.cur[b] = 0;
+    }
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
         const int q = L.l0[idx];
@@ -184,7 +193,7 @@ __device__ __forceinline__ void bin_append(const WfLists& L, int b, int q) {
     const unsigned peers = __match_any_sync(act, b);
     const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
     int base = 0;
-    if (lane == leader) base = atomicAdd(L.count + 8 + b, __popc(peers));
+    if (lane == leader) base = atomicAdd(L.cur + 8 + b, __popc(peers));
     base = __shfl_sync(peers, base, leader);
     L.bins[(long long)b * L.binQ + base + __popc(peers & ((1u << lane) - 1u))] = q;
 }
@@ -199,7 +208,7 @@ enum : int { kShadeStoreHits = 1, kShadeBinReplay = 2 };
 template <bool NM>
 __global__ void k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfState W, WfLists L,
                            int flags) {
-    const int n0 = L.count[0], n = n0 + L.count[1];
+    const int n0 = L.cur[0], n = n0 + L.cur[1];
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
         const int q = list_at(L, n0, idx);
@@ -242,7 +251,7 @@ __global__ void k_wf_shade(const DScene S, const DParams P, const __grid_constan
         }
         if (ne.state == 1) {
             W.ray[q] = WfRay{make_float4(ne.o2.x, ne.o2.y, ne.o2.z, ne.tmax), make_float4(ne.dir.x, ne.dir.y, ne.dir.z, 0.f)};
-            L.shadow[atomicAdd(L.count + 4, 1)] = q;
+            L.shadow[atomicAdd(L.cur + 4, 1)] = q;
         }
         W.visible[q] = 0;
     }
@@ -250,7 +259,7 @@ __global__ void k_wf_shade(const DScene S, const DParams P, const __grid_constan
 
 __global__ void __launch_bounds__(512, DPPT_WF_TRAVERSE_MIN_BLOCKS)
 k_wf_shadow(const DScene S, WfState W, WfLists L, unsigned* status) {
-    const int n = L.count[4];
+    const int n = L.cur[4];
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
         const int q = L.shadow[idx];
@@ -271,7 +280,7 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
     if (PHASE == 1) sgrad_zero(sgrad, sgrad_scalars(S));
     // the pass's list: the cache list, the replay list, or one replay bin
     const int* list = PHASE == 0 ? L.l0 : BIN < 0 ? L.l1 : L.bins + (long long)BIN * L.binQ;
-    const int count = PHASE == 0 ? L.count[0] : BIN < 0 ? L.count[1] : L.count[8 + (BIN < 0 ? 0 : BIN)];
+    const int count = PHASE == 0 ? L.cur[0] : BIN < 0 ? L.cur[1] : L.cur[8 + (BIN < 0 ? 0 : BIN)];
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += stride) {
         const int q = list[idx];
@@ -309,8 +318,8 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
         bool done = false;
         int phase = PHASE;
         if (cont) {
-            if (PHASE == 0) L.next0[atomicAdd(L.count + 2, 1)] = q;
-            else L.next1[atomicAdd(L.count + 3, 1)] = q;
+            if (PHASE == 0) L.next0[atomicAdd(L.nxt + 0, 1)] = q;
+            else L.next1[atomicAdd(L.nxt + 1, 1)] = q;
         } else if (PHASE == 0) {
             float L0[12];
             vis.fold(L0);
@@ -341,7 +350,7 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
                 phase = 1;
                 vis.i = 0;
                 walk_begin(S, J, pid, pix, w);
-                L.next1[atomicAdd(L.count + 3, 1)] = q;
+                L.next1[atomicAdd(L.nxt + 1, 1)] = q;
             } else {
                 done = true;
             }
@@ -361,18 +370,6 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
         }
     }
     if (PHASE == 1) sgrad_flush(S, G, sgrad);
-}
-
-// the next lists become the live lists
-__global__ void k_wf_swap(WfLists L) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        L.count[0] = L.count[2];
-        L.count[1] = L.count[3];
-        L.count[2] = 0;
-        L.count[3] = 0;
-        L.count[4] = 0;
-        for (int b = 8; b < 16; ++b) L.count[b] = 0;
-    }
 }
 
 // sums the spp paths of each pixel of a finished wave (deterministic order)
@@ -404,10 +401,30 @@ size_t wavefront_bytes(long long Q, int cap) {
     b += align_up(sizeof(float4) * 3 * Q);      // adjoint rows
     b += align_up(sizeof(float4) * 3 * Q);      // raw per path
     b += 5 * align_up(sizeof(int) * Q);         // lists
-    b += align_up(sizeof(int) * 16);
+    b += align_up(sizeof(int) * 32);
     b += align_up(sizeof(int) * 8 * Q);         // replay bins
     b += align_up(sizeof(float) * kWfCacheComps * (size_t)cap * Q);
     return b;
+}
+
+// The replay of bin MT with the kernel compiled for that material type.
+struct ReplayArgs {
+    const DScene& S;
+    const DParams& P;
+    const DGrads& G;
+    const JobTable& T;
+    const WfState& W;
+    const WfLists& L;
+    unsigned* sg;
+    int grid;
+    size_t smem;
+    cudaStream_t st;
+    bool nmaps;
+};
+template <int MT>
+static void replay_bin(const ReplayArgs& a) {
+    if (a.nmaps) k_wf_finish<1, 1, true, MT, MT><<<a.grid, 128, a.smem, a.st>>>(a.S, a.P, a.G, a.T, a.W, a.L, a.sg);
+    else k_wf_finish<1, 1, false, MT, MT><<<a.grid, 128, a.smem, a.st>>>(a.S, a.P, a.G, a.T, a.W, a.L, a.sg);
 }
 
 // Renders (mode 0) or differentiates (mode 1) job `job` of the table in waves of
@@ -428,7 +445,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
     W.raw = reinterpret_cast<float4*>(p); p += align_up(sizeof(float4) * 3 * Q);
     int* lists[5];
     for (int k = 0; k < 5; ++k) { lists[k] = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * Q); }
-    int* count = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * 16);
+    int* count = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * 32);
     int* bins = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * 8 * Q);
     W.cache = reinterpret_cast<float*>(p);
     W.Q = Q;
@@ -449,17 +466,18 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
         // stage kernels stride over their lists: a few resident waves of blocks at most
         const int grid = (int)std::min<long long>((nq + block - 1) / block, (long long)sms * (2048 / block));
         const int fgrid = (int)std::min<long long>((nq + 127) / 128, (long long)sms * DPPT_WF_CACHE_MIN_BLOCKS * 2);
-        WfLists A{lists[0], lists[1], lists[2], lists[3], lists[4], count, bins, (int)Q};
-        cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 16, st);
+        WfLists A{lists[0], lists[1], lists[2], lists[3], lists[4], count, count + 16, bins, (int)Q};
+        cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 32, st);
         if (e != cudaSuccess) return e;
         int tok = log->begin(kStageWfInit, st);
         k_wf_init<<<grid, block, 0, st>>>(S, T, job, pix0 * J.spp, nq, W, A);
         log->end(tok, st);
         unsigned* sg = J.sig ? J.sig + pix0 * J.spp : nullptr;
         for (int it = 0; it < passes * J.depth; ++it) {
-            // lists alternate between two buffer pairs: the next lists of one iteration are the
-            // live lists of the following one (k_wf_swap moves the counts)
-            WfLists L = (it & 1) ? WfLists{lists[2], lists[3], lists[0], lists[1], lists[4], count, bins, (int)Q} : A;
+            // lists and counts alternate between two buffers: the next lists of one iteration
+            // are the live lists of the following one
+            WfLists L = (it & 1) ? WfLists{lists[2], lists[3], lists[0], lists[1], lists[4], count + 16, count, bins, (int)Q}
+                                 : A;
             tok = log->begin(kStageWfExtend, st);
             k_wf_extend<<<grid, block, 0, st>>>(S, W, L, status);
             log->end(tok, st);
@@ -485,18 +503,10 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                 if (binned) {
                     // one replay kernel per material type present (k_wf_shade binned the
                     // replay list), then the rest
-                    if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) {
-                        if (nmaps) k_wf_finish<1, 1, true, DPPT_MAT_CONDUCTOR_GGX, DPPT_MAT_CONDUCTOR_GGX><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
-                        else k_wf_finish<1, 1, false, DPPT_MAT_CONDUCTOR_GGX, DPPT_MAT_CONDUCTOR_GGX><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
-                    }
-                    if (types & (1u << DPPT_MAT_PLASTIC_GGX)) {
-                        if (nmaps) k_wf_finish<1, 1, true, DPPT_MAT_PLASTIC_GGX, DPPT_MAT_PLASTIC_GGX><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
-                        else k_wf_finish<1, 1, false, DPPT_MAT_PLASTIC_GGX, DPPT_MAT_PLASTIC_GGX><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
-                    }
-                    if (types & (1u << DPPT_MAT_DIFFUSE)) {
-                        if (nmaps) k_wf_finish<1, 1, true, DPPT_MAT_DIFFUSE, DPPT_MAT_DIFFUSE><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
-                        else k_wf_finish<1, 1, false, DPPT_MAT_DIFFUSE, DPPT_MAT_DIFFUSE><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
-                    }
+                    const ReplayArgs ra{S, P, G, T, W, L, sg, fgrid, smem, st, nmaps};
+                    if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) replay_bin<DPPT_MAT_CONDUCTOR_GGX>(ra);
+                    if (types & (1u << DPPT_MAT_PLASTIC_GGX)) replay_bin<DPPT_MAT_PLASTIC_GGX>(ra);
+                    if (types & (1u << DPPT_MAT_DIFFUSE)) replay_bin<DPPT_MAT_DIFFUSE>(ra);
                     if (nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
                     else k_wf_finish<1, 1, false, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
                 } else if (nmaps) {
@@ -506,9 +516,6 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                 }
                 log->end(tok, st);
             }
-            tok = log->begin(kStageWfSwap, st);
-            k_wf_swap<<<1, 32, 0, st>>>(L);
-            log->end(tok, st);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         if (J.raw) {
