@@ -29,6 +29,11 @@
 #ifndef DPPT_WF_REPLAY_MIN_BLOCKS
 #define DPPT_WF_REPLAY_MIN_BLOCKS 4
 #endif
+// resident 512-thread blocks per SM the shade kernel's register allocation must allow
+// (2 -> at most 64 registers per thread)
+#ifndef DPPT_WF_SHADE_MIN_BLOCKS
+#define DPPT_WF_SHADE_MIN_BLOCKS 2
+#endif
 
 namespace dppt {
 
@@ -133,10 +138,12 @@ struct WfLists {
 };
 
 // Replay bins: the material types with a replay kernel of their own (diffuse, rough
-// conductor, rough dielectric), and one bin for everything else (smooth dielectrics,
-// sheets, emitter hits, paths that left the scene).
+// conductor, rough dielectric, polarizer and retarder sheets), and one bin for everything
+// else (smooth dielectrics, emitter hits, paths that left the scene).
 constexpr int kBinOther = 7;
-constexpr unsigned kBinnedTypes = (1u << DPPT_MAT_DIFFUSE) | (1u << DPPT_MAT_CONDUCTOR_GGX) | (1u << DPPT_MAT_PLASTIC_GGX);
+constexpr unsigned kBinnedTypes = (1u << DPPT_MAT_DIFFUSE) | (1u << DPPT_MAT_CONDUCTOR_GGX) |
+                                  (1u << DPPT_MAT_PLASTIC_GGX) | (1u << DPPT_MAT_POLARIZER_SHEET) |
+                                  (1u << DPPT_MAT_RETARDER_SHEET);
 #ifndef DPPT_WF_BIN_REPLAY
 #define DPPT_WF_BIN_REPLAY 1
 #endif
@@ -206,8 +213,8 @@ enum : int { kShadeStoreHits = 1, kShadeBinReplay = 2 };
 // with kShadeBinReplay each replayed path is appended to the bin of its vertex's material
 // type (kBinOther for misses and the types without a replay kernel of their own).
 template <bool NM>
-__global__ void k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfState W, WfLists L,
-                           int flags) {
+__global__ void __launch_bounds__(512, DPPT_WF_SHADE_MIN_BLOCKS)
+k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfState W, WfLists L, int flags) {
     const int n0 = L.cur[0], n = n0 + L.cur[1];
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
@@ -507,6 +514,8 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                     if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) replay_bin<DPPT_MAT_CONDUCTOR_GGX>(ra);
                     if (types & (1u << DPPT_MAT_PLASTIC_GGX)) replay_bin<DPPT_MAT_PLASTIC_GGX>(ra);
                     if (types & (1u << DPPT_MAT_DIFFUSE)) replay_bin<DPPT_MAT_DIFFUSE>(ra);
+                    if (types & (1u << DPPT_MAT_POLARIZER_SHEET)) replay_bin<DPPT_MAT_POLARIZER_SHEET>(ra);
+                    if (types & (1u << DPPT_MAT_RETARDER_SHEET)) replay_bin<DPPT_MAT_RETARDER_SHEET>(ra);
                     if (nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
                     else k_wf_finish<1, 1, false, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
                 } else if (nmaps) {
