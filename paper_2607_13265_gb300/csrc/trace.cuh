@@ -733,7 +733,7 @@ struct Shade {
     bool ok, terminal, delta;
 };
 
-template <bool NM = true>
+template <bool NM = true, int MT = -1>
 __device__ __forceinline__ void walk_shade(const DScene& S, const DParams& P, const DJob& J, unsigned long long pid,
                                            const Walk& w, const HitRec& h, VCtx& vc, NeePending& ne, Shade& sh) {
     const int nL = S.num_lights;
@@ -764,7 +764,7 @@ __device__ __forceinline__ void walk_shade(const DScene& S, const DParams& P, co
     }
     vc.n = dot(vc.ng, vc.wo) >= 0.0f ? vc.ng : -vc.ng;
     const f3 ngo = vc.n;   // geometric normal on the side of wo
-    const DMat m = S.mats[vc.mat];
+    const DMat m = load_mat<MT>(S, vc.mat);
     if (NM && m.normal_tex >= 0) apply_normal_map(S, P, vc);
     if (vc.light >= 0) {
         DLight L = load_light(S, vc.light);

@@ -1,19 +1,18 @@
-// Wavefront schedule of the same path tracer: the megakernel's per-vertex work
-// split into stage kernels over compacted lists of live paths,
+// Wavefront schedule of the same path tracer: the megakernel's per-vertex work split into
+// stage kernels over compacted lists of live paths.  A cache-pass iteration runs
 //   extend (closest hit) -> shade (surface data, light and BSDF samples)
-//   -> shadow (any hit of the light samples) -> cache / replay (per-vertex
-//   action, next ray),
-// the last stage as two kernels so that cache passes and dual-number replays
-// run separately.  Path state lives in the context workspace as arrays of
-// 16-byte-aligned records that a thread moves with float4 loads and stores:
-// the walk (64 B), path bookkeeping (16 B), the vertex handed from shade to
-// finish (112 B), the hit (16 B), the adjoint row (48 B), the raw Stokes
-// value (48 B); the per-vertex cache holds one 144-byte record per (vertex,
-// path), whole whatever fraction of the wave's paths is still live.  The
-// replay walks the path again with the same stage code and Philox counters as
-// the cache pass, but reads each vertex's closest hit and light-sample
-// visibility from the cache instead of tracing its two rays again.  Every stage reads its list length from device memory and
-// loops over it with a grid stride, so a wave is a fixed sequence of launches.
+//   -> shadow (any hit of the light samples) -> cache (per-vertex action, next ray);
+// the replay runs in the same iterations as one kernel per material type, over the paths
+// binned by the type of their next vertex: it shades that vertex itself from the hit and
+// light-sample visibility the cache pass stored (no traversal, no vertex record) and
+// evaluates it with dual numbers, with the same code and Philox counters as the cache
+// pass.  Path state lives in the context workspace as arrays of 16-byte-aligned records
+// that a thread moves with float4 loads and stores: the walk (64 B), path bookkeeping
+// (16 B), the vertex handed from shade to cache (112 B), the hit (16 B), the adjoint row
+// (48 B), the raw Stokes value (48 B); the per-vertex cache holds one 144-byte record per
+// (vertex, path), whole whatever fraction of the wave's paths is still live.  Every stage
+// reads its list length from device memory and loops over it with a grid stride, so a
+// wave is a fixed sequence of launches.
 #include "trace.cuh"
 
 // resident threads per SM the traversal kernels' register allocation must allow (as blocks
@@ -122,18 +121,19 @@ struct WfState {
 };
 
 struct WfLists {
-    int* l0;      // live paths in the cache pass
-    int* l1;      // live paths in the replay pass
+    int* l0;      // live paths of the cache pass
     int* next0;
-    int* next1;
     int* shadow;
-    // counts of this iteration: [0] n0, [1] n1, [4] shadow, [8 + b] replay bin b; nxt[0], nxt[1]:
-    // the next lists' lengths.  The two 16-int halves of the count array alternate between
-    // iterations (the next counts of one are the live counts of the following one), and each
-    // iteration's k_wf_extend zeroes the counts the iteration appends to.
+    // counts of this iteration: [0] cache-pass paths, [4] shadow rays, [8 + b] replay bin b;
+    // nxt: the same for the next iteration ([0] and [8 + b] are appended to).  The two
+    // 16-int halves of the count array alternate between iterations, and each iteration's
+    // k_wf_extend zeroes the counts the iteration appends to.
     int* cur;
     int* nxt;
-    int* bins;    // replay paths binned by the material type of their vertex: bin b at bins + b * Q
+    // replayed paths binned by the material type of their vertex: bin b at bins + b * binQ
+    // (this iteration) and nbins + b * binQ (the next one)
+    int* bins;
+    int* nbins;
     int binQ;
 };
 
@@ -144,13 +144,6 @@ constexpr int kBinOther = 7;
 constexpr unsigned kBinnedTypes = (1u << DPPT_MAT_DIFFUSE) | (1u << DPPT_MAT_CONDUCTOR_GGX) |
                                   (1u << DPPT_MAT_PLASTIC_GGX) | (1u << DPPT_MAT_POLARIZER_SHEET) |
                                   (1u << DPPT_MAT_RETARDER_SHEET);
-#ifndef DPPT_WF_BIN_REPLAY
-#define DPPT_WF_BIN_REPLAY 1
-#endif
-
-__device__ __forceinline__ int list_at(const WfLists& L, int n0, int idx) {
-    return idx < n0 ? L.l0[idx] : L.l1[idx - n0];
-}
 
 __global__ void k_wf_init(const DScene S, const __grid_constant__ JobTable T, int job, long long p0, int nq,
                           WfState W, WfLists L) {
@@ -163,19 +156,19 @@ __global__ void k_wf_init(const DScene S, const __grid_constant__ JobTable T, in
         put_walk(W.walk + q, w);
         W.meta[q] = WfMeta{(unsigned)pid, (unsigned)(pid >> 32), job, 0};
         L.l0[q] = q;
-        if (q == 0) { L.cur[0] = nq; L.cur[1] = 0; }
+        if (q == 0) L.cur[0] = nq;
     }
 }
 
 // Closest hits of the live paths, one ray per thread in a grid-stride loop.  The list
 // keeps the samples of a pixel together, so a warp's rays share their origin.  Only the
-// cache pass traces: replayed paths read their hits from the cache (kWfHitComp).
+// cache pass traces: the replay reads its hits from the cache (kWfHitComp).
 __global__ void __launch_bounds__(512, DPPT_WF_TRAVERSE_MIN_BLOCKS)
 k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
     const int n = L.cur[0];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        L.nxt[0] = 0; L.nxt[1] = 0; L.cur[4] = 0;
-        for (int b = 8; b < 16; ++b) L.cur[b] = 0;
+        L.nxt[0] = 0; L.cur[4] = 0;
+        for (int b = 8; b < 16; ++b) L.nxt[b] = 0;
     }
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
@@ -193,46 +186,48 @@ k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
     }
 }
 
-// Appends path q to replay bin b.  Appends are warp-aggregated: the lanes of a warp going
-// to the same bin take consecutive slots with one atomic.
+// Appends path q to the next iteration's replay bin b.  Appends are warp-aggregated: the
+// lanes of a warp going to the same bin take consecutive slots with one atomic.
 __device__ __forceinline__ void bin_append(const WfLists& L, int b, int q) {
     const unsigned act = __activemask();
     const unsigned peers = __match_any_sync(act, b);
     const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
     int base = 0;
-    if (lane == leader) base = atomicAdd(L.cur + 8 + b, __popc(peers));
+    if (lane == leader) base = atomicAdd(L.nxt + 8 + b, __popc(peers));
     base = __shfl_sync(peers, base, leader);
-    L.bins[(long long)b * L.binQ + base + __popc(peers & ((1u << lane) - 1u))] = q;
+    L.nbins[(long long)b * L.binQ + base + __popc(peers & ((1u << lane) - 1u))] = q;
 }
 
-enum : int { kShadeStoreHits = 1, kShadeBinReplay = 2 };
+// The replay bin of path q's vertex in cache slot v: the material type of its cached hit
+// when that type has a replay kernel of its own, else kBinOther (misses included).
+__device__ __forceinline__ int replay_bin_of(const DScene& S, const WfState& W, int q, int v) {
+    const int code = __float_as_int(W.cache[((long long)v * W.Q + q) * kWfCacheComps + kWfHitComp + 3]);
+    if (code == kMissCode) return kBinOther;
+    const int mat = code >= 0 ? __ldg(S.tri_mat + __float_as_int(__ldg(&S.tris[3 * code].w)))
+                              : __ldg(S.sph_mat + (-code - 1));
+    const int t = __ldg(&S.mats[mat].type);
+    return (kBinnedTypes >> t) & 1u ? t : kBinOther;
+}
 
-// Surface data, light sample and BSDF sample of each live path's new vertex.  In the
-// adjoint (kShadeStoreHits), a cache-pass path stores its hit in the cache at its vertex
-// slot and a replayed path takes its hit and its light sample's visibility from there;
-// with kShadeBinReplay each replayed path is appended to the bin of its vertex's material
-// type (kBinOther for misses and the types without a replay kernel of their own).
+// Surface data, light sample and BSDF sample of each cache-pass path's new vertex; in the
+// adjoint (store_hits) the hit is also stored in the cache at the vertex's slot for the
+// replay.
 template <bool NM>
 __global__ void __launch_bounds__(512, DPPT_WF_SHADE_MIN_BLOCKS)
-k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfState W, WfLists L, int flags) {
-    const int n0 = L.cur[0], n = n0 + L.cur[1];
+k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfState W, WfLists L,
+           int store_hits) {
+    const int n = L.cur[0];
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        const int q = list_at(L, n0, idx);
-        const bool replay = idx >= n0;
-        const int v = __float_as_int(W.walk[q].c.w) & 0xff;     // the vertex's slot (see put_walk)
-        float* rec = W.cache + ((long long)(v - 1) * W.Q + q) * kWfCacheComps;
-        float4 hv;
-        if (replay) {
-            hv = *reinterpret_cast<const float4*>(rec + kWfHitComp);
-        } else {
-            hv = W.hit[q];
-            if (flags & kShadeStoreHits) *reinterpret_cast<float4*>(rec + kWfHitComp) = hv;
+        const int q = L.l0[idx];
+        const float4 hv = W.hit[q];
+        if (store_hits) {
+            const int v = __float_as_int(W.walk[q].c.w) & 0xff;     // the vertex's slot (see put_walk)
+            *reinterpret_cast<float4*>(W.cache + ((long long)(v - 1) * W.Q + q) * kWfCacheComps + kWfHitComp) = hv;
         }
         const int code = __float_as_int(hv.w);
         if (code == kMissCode) {
             W.vtx[q].ids = make_int4(0, 0, 0, 0);
-            if (replay && (flags & kShadeBinReplay)) bin_append(L, kBinOther, q);
             continue;
         }
         HitRec h;
@@ -248,14 +243,6 @@ k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
         Shade sh;
         walk_shade<NM>(S, P, T.job[m.job], pid, w, h, vc, ne, sh);
         put_vertex(W.vtx + q, vc, ne, sh);
-        if (replay) {
-            W.visible[q] = __float_as_int(rec[kWfVisComp]);
-            if (flags & kShadeBinReplay) {
-                const int t = __ldg(&S.mats[vc.mat].type);
-                bin_append(L, (kBinnedTypes >> t) & 1u ? t : kBinOther, q);
-            }
-            continue;
-        }
         if (ne.state == 1) {
             W.ray[q] = WfRay{make_float4(ne.o2.x, ne.o2.y, ne.o2.z, ne.tmax), make_float4(ne.dir.x, ne.dir.y, ne.dir.z, 0.f)};
             L.shadow[atomicAdd(L.cur + 4, 1)] = q;
@@ -276,18 +263,22 @@ k_wf_shadow(const DScene S, WfState W, WfLists L, unsigned* status) {
     }
 }
 
-// Per-vertex action of one pass.  PHASE 0 (cache pass): cache E_i / W_i; at the
-// end of the walk fold the cache, store the path's raw Stokes value and, for the
-// adjoint (MODE 1), start the replay.  PHASE 1: the replay (MODE 1 only).
+// Per-vertex action of one pass.  PHASE 0 (cache pass): cache E_i / W_i; at the end of
+// the walk fold the cache, store the path's raw Stokes value and, for the adjoint (MODE
+// 1), start the replay.  PHASE 1: the replay of replay bin BIN (MODE 1 only), compiled for
+// material type MT (-1: any).  It shades its vertex itself from the cached hit and light-
+// sample visibility (no vertex record, no traversal) and appends each continuing path to
+// the bin of its next vertex.
 template <int MODE, int PHASE, bool NM, int MT = -1, int BIN = -1>
 __global__ void __launch_bounds__(128, PHASE == 1 ? DPPT_WF_REPLAY_MIN_BLOCKS : DPPT_WF_CACHE_MIN_BLOCKS)
 k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_constant__ JobTable T, WfState W, WfLists L,
             unsigned* sig) {
     extern __shared__ float sgrad[];
     if (PHASE == 1) sgrad_zero(sgrad, sgrad_scalars(S));
-    // the pass's list: the cache list, the replay list, or one replay bin
-    const int* list = PHASE == 0 ? L.l0 : BIN < 0 ? L.l1 : L.bins + (long long)BIN * L.binQ;
-    const int count = PHASE == 0 ? L.cur[0] : BIN < 0 ? L.cur[1] : L.cur[8 + (BIN < 0 ? 0 : BIN)];
+    static_assert(PHASE == 0 || BIN >= 0, "the replay runs over one bin");
+    // the pass's list: the cache list or one replay bin
+    const int* list = PHASE == 0 ? L.l0 : L.bins + (long long)(BIN < 0 ? 0 : BIN) * L.binQ;
+    const int count = PHASE == 0 ? L.cur[0] : L.cur[8 + (BIN < 0 ? 0 : BIN)];
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += stride) {
         const int q = list[idx];
@@ -305,28 +296,41 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
         NeePending ne;
         Shade sh;
         bool cont = false;
-        if (get_vertex(W.vtx + q, w, vc, ne, sh)) {
-            if (PHASE == 1) {
+        if (PHASE == 0) {
+            if (get_vertex(W.vtx + q, w, vc, ne, sh)) {
+                if (NM) apply_normal_map(S, P, vc);
+                const int visible = W.visible[q];
+                const int slot = w.v - 1;
+                cont = walk_finish(S, P, w, vc, ne, visible != 0, sh, vis);
+                // the replay of this vertex reads it back; stored after walk_finish, whose
+                // cache write zeroes it
+                if (MODE == 1)
+                    W.cache[((long long)slot * W.Q + q) * kWfCacheComps + kWfVisComp] = __int_as_float(visible);
+            }
+        } else {
+            const float* rec = W.cache + ((long long)(w.v - 1) * W.Q + q) * kWfCacheComps;
+            const float4 hv = *reinterpret_cast<const float4*>(rec + kWfHitComp);
+            const int code = __float_as_int(hv.w);
+            if (code != kMissCode) {
+                HitRec h;
+                h.t = hv.x; h.b1 = hv.y; h.b2 = hv.z;
+                if (code >= 0) { h.slot = code; h.prim = __float_as_int(__ldg(&S.tris[3 * code].w)); }
+                else { h.slot = -1; h.prim = S.num_tris + (-code - 1); }
+                const unsigned long long pid = (unsigned long long)m.lo | ((unsigned long long)m.hi << 32);
+                walk_shade<NM, MT>(S, P, J, pid, w, h, vc, ne, sh);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     float4 r = W.arow[3 * (long long)q + c];
                     vis.a[c][0] = r.x; vis.a[c][1] = r.y; vis.a[c][2] = r.z; vis.a[c][3] = r.w;
                 }
+                cont = walk_finish(S, P, w, vc, ne, __float_as_int(rec[kWfVisComp]) != 0, sh, vis);
             }
-            if (NM) apply_normal_map(S, P, vc);
-            const int visible = W.visible[q];
-            const int slot = w.v - 1;
-            cont = walk_finish(S, P, w, vc, ne, visible != 0, sh, vis);
-            // the replay of this vertex reads it back (k_wf_shade); stored after walk_finish,
-            // whose cache write zeroes it
-            if (MODE == 1 && PHASE == 0)
-                W.cache[((long long)slot * W.Q + q) * kWfCacheComps + kWfVisComp] = __int_as_float(visible);
         }
         bool done = false;
         int phase = PHASE;
         if (cont) {
             if (PHASE == 0) L.next0[atomicAdd(L.nxt + 0, 1)] = q;
-            else L.next1[atomicAdd(L.nxt + 1, 1)] = q;
+            else bin_append(L, replay_bin_of(S, W, q, w.v - 1), q);
         } else if (PHASE == 0) {
             float L0[12];
             vis.fold(L0);
@@ -357,7 +361,7 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
                 phase = 1;
                 vis.i = 0;
                 walk_begin(S, J, pid, pix, w);
-                L.next1[atomicAdd(L.nxt + 1, 1)] = q;
+                bin_append(L, replay_bin_of(S, W, q, 0), q);
             } else {
                 done = true;
             }
@@ -407,9 +411,9 @@ size_t wavefront_bytes(long long Q, int cap) {
     b += align_up(sizeof(int) * Q);             // visible
     b += align_up(sizeof(float4) * 3 * Q);      // adjoint rows
     b += align_up(sizeof(float4) * 3 * Q);      // raw per path
-    b += 5 * align_up(sizeof(int) * Q);         // lists
+    b += 3 * align_up(sizeof(int) * Q);         // lists
     b += align_up(sizeof(int) * 32);
-    b += align_up(sizeof(int) * 8 * Q);         // replay bins
+    b += 2 * align_up(sizeof(int) * 8 * Q);     // replay bins of this and the next iteration
     b += align_up(sizeof(float) * kWfCacheComps * (size_t)cap * Q);
     return b;
 }
@@ -450,10 +454,11 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
     W.visible = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * Q);
     W.arow = reinterpret_cast<float4*>(p); p += align_up(sizeof(float4) * 3 * Q);
     W.raw = reinterpret_cast<float4*>(p); p += align_up(sizeof(float4) * 3 * Q);
-    int* lists[5];
-    for (int k = 0; k < 5; ++k) { lists[k] = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * Q); }
+    int* lists[3];
+    for (int k = 0; k < 3; ++k) { lists[k] = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * Q); }
     int* count = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * 32);
-    int* bins = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * 8 * Q);
+    int* bins[2];
+    for (int k = 0; k < 2; ++k) { bins[k] = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * 8 * Q); }
     W.cache = reinterpret_cast<float*>(p);
     W.Q = Q;
     W.cap = cap;
@@ -464,7 +469,6 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
     const long long pix_per_wave = std::max(1LL, Q / J.spp);
     const bool nmaps = S.tri_tan != nullptr;   // the scene has normal maps: kernels with that path
     const unsigned types = (unsigned)S.mat_types;
-    const bool binned = DPPT_WF_BIN_REPLAY && (types & kBinnedTypes) != 0;
     const int passes = mode == 1 ? 2 : 1;
     const size_t smem = mode == 1 ? sgrad_bytes(sgrad_scalars(S)) : 0;
     for (long long pix0 = 0; pix0 < npix; pix0 += pix_per_wave) {
@@ -473,7 +477,8 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
         // stage kernels stride over their lists: a few resident waves of blocks at most
         const int grid = (int)std::min<long long>((nq + block - 1) / block, (long long)sms * (2048 / block));
         const int fgrid = (int)std::min<long long>((nq + 127) / 128, (long long)sms * DPPT_WF_CACHE_MIN_BLOCKS * 2);
-        WfLists A{lists[0], lists[1], lists[2], lists[3], lists[4], count, count + 16, bins, (int)Q};
+        const WfLists A{lists[0], lists[1], lists[2], count, count + 16, bins[0], bins[1], (int)Q};
+        const WfLists B{lists[1], lists[0], lists[2], count + 16, count, bins[1], bins[0], (int)Q};
         cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 32, st);
         if (e != cudaSuccess) return e;
         int tok = log->begin(kStageWfInit, st);
@@ -481,17 +486,15 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
         log->end(tok, st);
         unsigned* sg = J.sig ? J.sig + pix0 * J.spp : nullptr;
         for (int it = 0; it < passes * J.depth; ++it) {
-            // lists and counts alternate between two buffers: the next lists of one iteration
-            // are the live lists of the following one
-            WfLists L = (it & 1) ? WfLists{lists[2], lists[3], lists[0], lists[1], lists[4], count + 16, count, bins, (int)Q}
-                                 : A;
+            // lists, counts and bins alternate between two buffers: the next ones of an
+            // iteration are the live ones of the following iteration
+            const WfLists& L = (it & 1) ? B : A;
             tok = log->begin(kStageWfExtend, st);
             k_wf_extend<<<grid, block, 0, st>>>(S, W, L, status);
             log->end(tok, st);
             tok = log->begin(kStageWfShade, st);
-            const int sflags = (mode == 1 ? kShadeStoreHits : 0) | (mode == 1 && binned ? kShadeBinReplay : 0);
-            if (nmaps) k_wf_shade<true><<<grid, block, 0, st>>>(S, P, T, W, L, sflags);
-            else k_wf_shade<false><<<grid, block, 0, st>>>(S, P, T, W, L, sflags);
+            if (nmaps) k_wf_shade<true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1);
+            else k_wf_shade<false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1);
             log->end(tok, st);
             tok = log->begin(kStageWfShadow, st);
             k_wf_shadow<<<grid, block, 0, st>>>(S, W, L, status);
@@ -507,22 +510,15 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
             log->end(tok, st);
             if (mode == 1) {
                 tok = log->begin(kStageWfReplay, st);
-                if (binned) {
-                    // one replay kernel per material type present (k_wf_shade binned the
-                    // replay list), then the rest
-                    const ReplayArgs ra{S, P, G, T, W, L, sg, fgrid, smem, st, nmaps};
-                    if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) replay_bin<DPPT_MAT_CONDUCTOR_GGX>(ra);
-                    if (types & (1u << DPPT_MAT_PLASTIC_GGX)) replay_bin<DPPT_MAT_PLASTIC_GGX>(ra);
-                    if (types & (1u << DPPT_MAT_DIFFUSE)) replay_bin<DPPT_MAT_DIFFUSE>(ra);
-                    if (types & (1u << DPPT_MAT_POLARIZER_SHEET)) replay_bin<DPPT_MAT_POLARIZER_SHEET>(ra);
-                    if (types & (1u << DPPT_MAT_RETARDER_SHEET)) replay_bin<DPPT_MAT_RETARDER_SHEET>(ra);
-                    if (nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
-                    else k_wf_finish<1, 1, false, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
-                } else if (nmaps) {
-                    k_wf_finish<1, 1, true><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
-                } else {
-                    k_wf_finish<1, 1, false><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
-                }
+                // one replay kernel per binned material type present, then the other bin
+                const ReplayArgs ra{S, P, G, T, W, L, sg, fgrid, smem, st, nmaps};
+                if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) replay_bin<DPPT_MAT_CONDUCTOR_GGX>(ra);
+                if (types & (1u << DPPT_MAT_PLASTIC_GGX)) replay_bin<DPPT_MAT_PLASTIC_GGX>(ra);
+                if (types & (1u << DPPT_MAT_DIFFUSE)) replay_bin<DPPT_MAT_DIFFUSE>(ra);
+                if (types & (1u << DPPT_MAT_POLARIZER_SHEET)) replay_bin<DPPT_MAT_POLARIZER_SHEET>(ra);
+                if (types & (1u << DPPT_MAT_RETARDER_SHEET)) replay_bin<DPPT_MAT_RETARDER_SHEET>(ra);
+                if (nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                else k_wf_finish<1, 1, false, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
                 log->end(tok, st);
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
