@@ -1045,10 +1045,10 @@ struct LocalCache {
 
 // A vertex of the wavefront's global cache: one 144-byte record per (vertex, path), so a
 // path's record stays whole however sparse the live paths of an iteration become (nine
-// float4s: E_v 12 floats, compact W_v 19, the visibility of the vertex's light sample 1,
-// the closest hit of the ray that made the vertex: t, b1, b2, code).  The replay reads the
-// hit and the visibility instead of tracing the ray and the shadow ray again (it would
-// find exactly the same hits).
+// float4s: E_v 12 floats, compact W_v 19, one word with the visibility of the vertex's
+// light sample and the vertex's replay bin, the closest hit of the ray that made the
+// vertex: t, b1, b2, code).  The replay reads the hit and the visibility instead of
+// tracing the ray and the shadow ray again (it would find exactly the same hits).
 constexpr int kWfCacheComps = 36;
 constexpr int kWfVisComp = 31;
 constexpr int kWfHitComp = 32;

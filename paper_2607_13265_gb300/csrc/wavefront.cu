@@ -198,15 +198,15 @@ __device__ __forceinline__ void bin_append(const WfLists& L, int b, int q) {
     L.nbins[(long long)b * L.binQ + base + __popc(peers & ((1u << lane) - 1u))] = q;
 }
 
-// The replay bin of path q's vertex in cache slot v: the material type of its cached hit
-// when that type has a replay kernel of its own, else kBinOther (misses included).
-__device__ __forceinline__ int replay_bin_of(const DScene& S, const WfState& W, int q, int v) {
-    const int code = __float_as_int(W.cache[((long long)v * W.Q + q) * kWfCacheComps + kWfHitComp + 3]);
-    if (code == kMissCode) return kBinOther;
-    const int mat = code >= 0 ? __ldg(S.tri_mat + __float_as_int(__ldg(&S.tris[3 * code].w)))
-                              : __ldg(S.sph_mat + (-code - 1));
+// The cache record's visibility word (kWfVisComp) holds, as an int, the light sample's
+// visibility in bit 0 and the vertex's replay bin above it: the material type when that
+// type has a replay kernel of its own, else kBinOther (misses included).
+__device__ __forceinline__ int replay_bin(const DScene& S, int mat) {
     const int t = __ldg(&S.mats[mat].type);
     return (kBinnedTypes >> t) & 1u ? t : kBinOther;
+}
+__device__ __forceinline__ int replay_bin_of(const WfState& W, int q, int v) {
+    return __float_as_int(W.cache[((long long)v * W.Q + q) * kWfCacheComps + kWfVisComp]) >> 1;
 }
 
 // Surface data, light sample and BSDF sample of each cache-pass path's new vertex; in the
@@ -221,11 +221,13 @@ k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
         const int q = L.l0[idx];
         const float4 hv = W.hit[q];
+        const int code = __float_as_int(hv.w);
         if (store_hits) {
             const int v = __float_as_int(W.walk[q].c.w) & 0xff;     // the vertex's slot (see put_walk)
-            *reinterpret_cast<float4*>(W.cache + ((long long)(v - 1) * W.Q + q) * kWfCacheComps + kWfHitComp) = hv;
+            float* rec = W.cache + ((long long)(v - 1) * W.Q + q) * kWfCacheComps;
+            *reinterpret_cast<float4*>(rec + kWfHitComp) = hv;
+            if (code == kMissCode) rec[kWfVisComp] = __int_as_float(kBinOther << 1);
         }
-        const int code = __float_as_int(hv.w);
         if (code == kMissCode) {
             W.vtx[q].ids = make_int4(0, 0, 0, 0);
             continue;
@@ -302,10 +304,10 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
                 const int visible = W.visible[q];
                 const int slot = w.v - 1;
                 cont = walk_finish(S, P, w, vc, ne, visible != 0, sh, vis);
-                // the replay of this vertex reads it back; stored after walk_finish, whose
-                // cache write zeroes it
+                // the replay reads it back; stored after walk_finish, whose cache write zeroes it
                 if (MODE == 1)
-                    W.cache[((long long)slot * W.Q + q) * kWfCacheComps + kWfVisComp] = __int_as_float(visible);
+                    W.cache[((long long)slot * W.Q + q) * kWfCacheComps + kWfVisComp] =
+                        __int_as_float(replay_bin(S, vc.mat) << 1 | (visible != 0 ? 1 : 0));
             }
         } else {
             const float* rec = W.cache + ((long long)(w.v - 1) * W.Q + q) * kWfCacheComps;
@@ -323,14 +325,14 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
                     float4 r = W.arow[3 * (long long)q + c];
                     vis.a[c][0] = r.x; vis.a[c][1] = r.y; vis.a[c][2] = r.z; vis.a[c][3] = r.w;
                 }
-                cont = walk_finish(S, P, w, vc, ne, __float_as_int(rec[kWfVisComp]) != 0, sh, vis);
+                cont = walk_finish(S, P, w, vc, ne, (__float_as_int(rec[kWfVisComp]) & 1) != 0, sh, vis);
             }
         }
         bool done = false;
         int phase = PHASE;
         if (cont) {
             if (PHASE == 0) L.next0[atomicAdd(L.nxt + 0, 1)] = q;
-            else bin_append(L, replay_bin_of(S, W, q, w.v - 1), q);
+            else bin_append(L, replay_bin_of(W, q, w.v - 1), q);
         } else if (PHASE == 0) {
             float L0[12];
             vis.fold(L0);
@@ -361,7 +363,7 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
                 phase = 1;
                 vis.i = 0;
                 walk_begin(S, J, pid, pix, w);
-                bin_append(L, replay_bin_of(S, W, q, 0), q);
+                bin_append(L, replay_bin_of(W, q, 0), q);
             } else {
                 done = true;
             }
@@ -433,7 +435,7 @@ struct ReplayArgs {
     bool nmaps;
 };
 template <int MT>
-static void replay_bin(const ReplayArgs& a) {
+static void launch_replay_bin(const ReplayArgs& a) {
     if (a.nmaps) k_wf_finish<1, 1, true, MT, MT><<<a.grid, 128, a.smem, a.st>>>(a.S, a.P, a.G, a.T, a.W, a.L, a.sg);
     else k_wf_finish<1, 1, false, MT, MT><<<a.grid, 128, a.smem, a.st>>>(a.S, a.P, a.G, a.T, a.W, a.L, a.sg);
 }
@@ -512,11 +514,11 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                 tok = log->begin(kStageWfReplay, st);
                 // one replay kernel per binned material type present, then the other bin
                 const ReplayArgs ra{S, P, G, T, W, L, sg, fgrid, smem, st, nmaps};
-                if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) replay_bin<DPPT_MAT_CONDUCTOR_GGX>(ra);
-                if (types & (1u << DPPT_MAT_PLASTIC_GGX)) replay_bin<DPPT_MAT_PLASTIC_GGX>(ra);
-                if (types & (1u << DPPT_MAT_DIFFUSE)) replay_bin<DPPT_MAT_DIFFUSE>(ra);
-                if (types & (1u << DPPT_MAT_POLARIZER_SHEET)) replay_bin<DPPT_MAT_POLARIZER_SHEET>(ra);
-                if (types & (1u << DPPT_MAT_RETARDER_SHEET)) replay_bin<DPPT_MAT_RETARDER_SHEET>(ra);
+                if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) launch_replay_bin<DPPT_MAT_CONDUCTOR_GGX>(ra);
+                if (types & (1u << DPPT_MAT_PLASTIC_GGX)) launch_replay_bin<DPPT_MAT_PLASTIC_GGX>(ra);
+                if (types & (1u << DPPT_MAT_DIFFUSE)) launch_replay_bin<DPPT_MAT_DIFFUSE>(ra);
+                if (types & (1u << DPPT_MAT_POLARIZER_SHEET)) launch_replay_bin<DPPT_MAT_POLARIZER_SHEET>(ra);
+                if (types & (1u << DPPT_MAT_RETARDER_SHEET)) launch_replay_bin<DPPT_MAT_RETARDER_SHEET>(ra);
                 if (nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
                 else k_wf_finish<1, 1, false, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
                 log->end(tok, st);
