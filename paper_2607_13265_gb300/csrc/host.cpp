@@ -759,7 +759,8 @@ static long long wave_paths(const dppt_job* jobs, int njobs) {
     return q;
 }
 
-static size_t scalar_smem(const dppt_scene* s) { return sgrad_bytes(sgrad_scalars(s->d)); }
+// shared memory of the megakernel adjoints' scalar-gradient accumulators (one copy each)
+static size_t scalar_smem(const dppt_scene* s) { return sgrad_bytes(s->d); }
 
 dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
                                const dppt_params* params, float* image, void* stream) {
@@ -838,6 +839,7 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
     if (!ctx || !s) return fail(ctx, DPPT_ERR_INVALID_ARG, "null context or scene");
     DScene Sd = s->d;   // the adjoint launches' copy, with the texel-gradient scatter of the launch shape
     Sd.scatter_lane = ctx->launch.adj_scatter == DPPT_SCATTER_LANE ? 1 : 0;
+    Sd.sgrad_lanes = ctx->launch.adj_schedule == DPPT_SCHED_WAVEFRONT ? 1 : 0;
     if (!grads) return fail(ctx, DPPT_ERR_INVALID_ARG, "grads is null");
     if (!l2 && !d_image && njobs > 0) return fail(ctx, DPPT_ERR_INVALID_ARG, "d_image is null");
     cudaSetDevice(ctx->device);

@@ -239,7 +239,7 @@ k_hybrid(const DScene S, const DParams P, const DGrads G, const __grid_constant_
          unsigned long long* counter, unsigned* status, int persistent, HybridCfg hc) {
     extern __shared__ float sgrad[];
     __shared__ long long s_chunk;
-    sgrad_zero(sgrad, sgrad_scalars(S));
+    sgrad_zero(S, sgrad);
     constexpr int NB = HybVis<MAXD, K>::NB;
     float ck[NB][60];
     unsigned char route[MAXD];
@@ -326,7 +326,7 @@ cudaError_t launch_hybrid_t(const DScene& S, const DParams& P, const DGrads& G, 
     long long g = pers ? L.grid : T.total_chunks;
     if (g <= 0) return cudaSuccess;
     if (g > 0x7fffffffLL) g = 0x7fffffffLL;
-    const size_t sm = sgrad_bytes(sgrad_scalars(S));
+    const size_t sm = sgrad_bytes(S);
     k_hybrid<MAXD, K><<<(int)g, L.block, sm, st>>>(S, P, G, T, counter, status, pers, hc);
     return cudaGetLastError();
 }

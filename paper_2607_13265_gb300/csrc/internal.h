@@ -50,17 +50,22 @@ struct DScene {
     float eps;
     int num_ior, num_sheets;
     int scatter_lane;       // adjoint: texel gradients one atomic per lane (1) or per warp group (0)
+    int sgrad_lanes;        // adjoint: scalar-gradient accumulators with a copy per lane (1) or one (0)
     int mat_types;          // bit t set when a triangle or sphere uses a material of type t
 };
 
 // Scalar gradients (indices of refraction, sheet angles, emitter Stokes vectors) are summed
-// per block in shared memory and flushed with one global atomic per block and scalar.  Each
-// scalar has 32 copies when they fit in 16 KB: lane l of a warp adds to copy l, so the lanes
-// of a warp adding to one scalar use 32 banks instead of serialising on one address.
+// per block in shared memory and flushed with one global atomic per block and scalar.  With
+// sgrad_lanes (the wavefront replay) each scalar has 32 copies when they fit in 16 KB: lane
+// l of a warp adds to copy l, so the lanes of a warp adding to one scalar use 32 banks
+// instead of serialising on one address.  The megakernels keep one copy: their thread-local
+// caches live in L1, which a larger shared-memory carveout would shrink.
 inline __host__ __device__ int sgrad_scalars(const DScene& S) { return S.num_ior + S.num_sheets + 12 * S.num_lights; }
-inline __host__ __device__ int sgrad_copies(int nscal) { return nscal * 32 * (int)sizeof(float) <= 16384 ? 32 : 1; }
-inline __host__ __device__ size_t sgrad_bytes(int nscal) {
-    return sizeof(float) * (size_t)nscal * (size_t)sgrad_copies(nscal);
+inline __host__ __device__ int sgrad_copies(const DScene& S) {
+    return S.sgrad_lanes && sgrad_scalars(S) * 32 * (int)sizeof(float) <= 16384 ? 32 : 1;
+}
+inline __host__ __device__ size_t sgrad_bytes(const DScene& S) {
+    return sizeof(float) * (size_t)sgrad_scalars(S) * (size_t)sgrad_copies(S);
 }
 
 struct DParams {

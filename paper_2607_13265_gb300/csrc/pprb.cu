@@ -97,7 +97,7 @@ k_pprb(const DScene S, const DParams P, const DGrads G, const __grid_constant__ 
        unsigned long long* counter, unsigned* status, int persistent, float sigma) {
     extern __shared__ float sgrad[];
     __shared__ long long s_chunk;
-    sgrad_zero(sgrad, sgrad_scalars(S));
+    sgrad_zero(S, sgrad);
     float beta[48];
     WorkCount wc = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     long long chunk = blockIdx.x;
@@ -164,7 +164,7 @@ cudaError_t launch_pprb(const DScene& S, const DParams& P, const DGrads& G, cons
     long long g = pers ? L.grid : T.total_chunks;
     if (g <= 0) return cudaSuccess;
     if (g > 0x7fffffffLL) g = 0x7fffffffLL;
-    const size_t sm = sgrad_bytes(sgrad_scalars(S));
+    const size_t sm = sgrad_bytes(S);
     k_pprb<<<(int)g, L.block, sm, st>>>(S, P, G, T, counter, status, pers, sigma);
     return cudaGetLastError();
 }

@@ -941,20 +941,20 @@ __device__ __forceinline__ void atomic_add_grouped(float* base, long long idx, f
 }
 // The block's scalar-gradient accumulators (sgrad_copies copies of each scalar), zeroed by
 // all threads of the block at its start.
-__device__ __forceinline__ void sgrad_zero(float* sg, int nscal) {
-    const int n = nscal * sgrad_copies(nscal);
+__device__ __forceinline__ void sgrad_zero(const DScene& S, float* sg) {
+    const int n = sgrad_scalars(S) * sgrad_copies(S);
     for (int k = threadIdx.x; k < n; k += blockDim.x) sg[k] = 0.0f;
     __syncthreads();
 }
 __device__ __forceinline__ void sgrad_add(const DScene& S, float* sg, int k, float v) {
-    const int copies = sgrad_copies(sgrad_scalars(S));
+    const int copies = sgrad_copies(S);
     atomicAdd(sg + k * copies + (threadIdx.x & (copies - 1)), v);
 }
 // after the block's last addition: sums the copies (read in a rotated order, one bank per
 // lane) and adds each nonzero scalar to its gradient with one global atomic
 __device__ __forceinline__ void sgrad_flush(const DScene& S, const DGrads& G, const float* sg) {
     __syncthreads();
-    const int nscal = sgrad_scalars(S), copies = sgrad_copies(nscal);
+    const int nscal = sgrad_scalars(S), copies = sgrad_copies(S);
     const int nI = S.num_ior, nS = S.num_sheets;
     for (int k = threadIdx.x; k < nscal; k += blockDim.x) {
         float v = 0.0f;
@@ -969,34 +969,39 @@ __device__ __forceinline__ void sgrad_flush(const DScene& S, const DGrads& G, co
     }
 }
 
-// adds vals[c] * w[k] at tp.idx[k] + min(c, ch - 1) for the NC values and the four taps
-// (kept as a loop: the replay kernel is bound by instruction fetch, and sixteen inlined
-// copies of the grouping code would enlarge it)
-#ifndef DPPT_SCATTER_UNROLL
-#define DPPT_SCATTER_UNROLL 0
-#endif
-template <int NC>
+// adds vals[c] * w[k] at tp.idx[k] + min(c, ch - 1) for the NC values and the four taps.
+// UNROLL = false keeps the sixteen sites as a loop: the wavefront replay kernels are bound by
+// instruction fetch, and sixteen inlined copies of the grouping code would enlarge them.
+// The megakernels are bound by their thread-local cache and run faster unrolled.
+template <int NC, bool UNROLL>
 __device__ __forceinline__ void scatter_taps(float* g, const Taps& tp, const float* vals, int ch, bool per_lane) {
-#if DPPT_SCATTER_UNROLL
+    if (UNROLL) {
 #pragma unroll
-#else
-#pragma unroll 1
-#endif
-    for (int c = 0; c < NC; ++c)
-#if DPPT_SCATTER_UNROLL
+        for (int c = 0; c < NC; ++c)
 #pragma unroll
-#else
-#pragma unroll 1
-#endif
-        for (int k = 0; k < 4; ++k) {
-            const float v = vals[c] * tp.w[k];
-            const long long idx = tp.idx[k] + min(c, ch - 1);
-            if (per_lane) {
-                if (v != 0.0f) atomicAdd(g + idx, v);
-            } else {
-                atomic_add_grouped(g, idx, v);
+            for (int k = 0; k < 4; ++k) {
+                const float v = vals[c] * tp.w[k];
+                const long long idx = tp.idx[k] + min(c, ch - 1);
+                if (per_lane) {
+                    if (v != 0.0f) atomicAdd(g + idx, v);
+                } else {
+                    atomic_add_grouped(g, idx, v);
+                }
             }
-        }
+    } else {
+#pragma unroll 1
+        for (int c = 0; c < NC; ++c)
+#pragma unroll 1
+            for (int k = 0; k < 4; ++k) {
+                const float v = vals[c] * tp.w[k];
+                const long long idx = tp.idx[k] + min(c, ch - 1);
+                if (per_lane) {
+                    if (v != 0.0f) atomicAdd(g + idx, v);
+                } else {
+                    atomic_add_grouped(g, idx, v);
+                }
+            }
+    }
 }
 
 // ================================================================== per-vertex actions
@@ -1024,6 +1029,7 @@ struct LocalCache {
     float (*cE)[12];
     float (*cW)[19];
     static constexpr int cap = MAXD;
+    static constexpr bool kUnrollScatter = true;
     __device__ __forceinline__ void put(int v, const float E[12], const Compact<float>& W) const {
         float o[20];
         pack_w(W, o);
@@ -1056,6 +1062,7 @@ struct GlobalCache {
     float* base;
     long long Q, q;
     int cap;
+    static constexpr bool kUnrollScatter = false;
     __device__ __forceinline__ float4* rec(int v) const {
         return reinterpret_cast<float4*>(base + ((long long)v * Q + q) * kWfCacheComps);
     }
@@ -1097,7 +1104,7 @@ struct GlobalCache {
 // The replayed vertex's local vector-Jacobian product: J_c = a_c^T (E_c + W_c L_c) with
 // dual numbers (W and the NEE operator f from eval_vertex<D3>, Ln the suffix L[v+1]),
 // scattered into the gradients; then the adjoint row advances, a^T <- a^T W_v.
-template <int MT = -1, bool NM = true>
+template <int MT = -1, bool NM = true, bool UNROLL = true>
 __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, const DGrads& G_, float* sgrad,
                                            const VCtx& vc, const Compact<D3>& W, const Compact<D3>& f,
                                            const float Ln[3][4], float a[3][4]) {
@@ -1166,18 +1173,18 @@ __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, 
         if (G->tex && S->tex[m.normal_tex].pad) {
             const Taps tp = tex_taps(S->tex[m.normal_tex], vc.tu, vc.tv);
             const float gn[3] = {2.0f * g_slot0, 2.0f * g_eta, 2.0f * (g_alb[0] + g_alb[1] + g_alb[2])};
-            scatter_taps<3>(G->tex, tp, gn, 3, S->scatter_lane != 0);
+            scatter_taps<3, UNROLL>(G->tex, tp, gn, 3, S->scatter_lane != 0);
         }
     } else if (G->tex) {
         if ((m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.rough_tex].pad) {
             Taps tp = tex_taps(S->tex[m.rough_tex], vc.tu, vc.tv);
-            scatter_taps<1>(G->tex, tp, &g_slot0, 1, S->scatter_lane != 0);
+            scatter_taps<1, UNROLL>(G->tex, tp, &g_slot0, 1, S->scatter_lane != 0);
         }
         if (m.albedo_tex >= 0 && (m.type == DPPT_MAT_DIFFUSE || m.type == DPPT_MAT_CONDUCTOR_GGX ||
                                   m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.albedo_tex].pad) {
             DTex t = S->tex[m.albedo_tex];
             Taps tp = tex_taps(t, vc.tu, vc.tv);
-            scatter_taps<3>(G->tex, tp, g_alb, t.ch, S->scatter_lane != 0);
+            scatter_taps<3, UNROLL>(G->tex, tp, g_alb, t.ch, S->scatter_lane != 0);
         }
     }
     // advance the adjoint row through the value of W_i
@@ -1266,7 +1273,7 @@ struct PathVis {
 #pragma unroll
             for (int k = 0; k < 12; ++k) Ln[k >> 2][k & 3] = 0.0f;
         }
-        replay_vjp<MT, NM>(*S, *P, *G, sgrad, vc, W, f, Ln, a);
+        replay_vjp<MT, NM, Cache::kUnrollScatter>(*S, *P, *G, sgrad, vc, W, f, Ln, a);
     }
 };
 
@@ -1312,7 +1319,7 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
         unsigned long long* counter, unsigned* status, int persistent, unsigned long long* work) {
     extern __shared__ float sgrad[];
     __shared__ long long s_chunk;
-    if (MODE == 1) sgrad_zero(sgrad, sgrad_scalars(S));
+    if (MODE == 1) sgrad_zero(S, sgrad);
     float cE[MAXD][12];
     float cW[MAXD][19];
     WorkCount wc = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
@@ -1409,7 +1416,7 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
         if (mode == 0)                                                                                           \
             k_trace<B, 0, false><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, nullptr);         \
         else if (mode == 1) {                                                                                    \
-            size_t sm = sgrad_bytes(sgrad_scalars(S));                                                          \
+            size_t sm = sgrad_bytes(S);                                                                         \
             k_trace<B, 1, false><<<(int)g, L.block, sm, st>>>(S, P, G, T, counter, status, pers, nullptr);        \
         } else                                                                                                   \
             k_trace<B, 0, true><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, work);             \

@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(128, PHASE == 1 ? DPPT_WF_REPLAY_MIN_BLOCKS : 
 k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_constant__ JobTable T, WfState W, WfLists L,
             unsigned* sig) {
     extern __shared__ float sgrad[];
-    if (PHASE == 1) sgrad_zero(sgrad, sgrad_scalars(S));
+    if (PHASE == 1) sgrad_zero(S, sgrad);
     static_assert(PHASE == 0 || BIN >= 0, "the replay runs over one bin");
     // the pass's list: the cache list or one replay bin
     const int* list = PHASE == 0 ? L.l0 : L.bins + (long long)(BIN < 0 ? 0 : BIN) * L.binQ;
@@ -472,7 +472,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
     const bool nmaps = S.tri_tan != nullptr;   // the scene has normal maps: kernels with that path
     const unsigned types = (unsigned)S.mat_types;
     const int passes = mode == 1 ? 2 : 1;
-    const size_t smem = mode == 1 ? sgrad_bytes(sgrad_scalars(S)) : 0;
+    const size_t smem = mode == 1 ? sgrad_bytes(S) : 0;
     for (long long pix0 = 0; pix0 < npix; pix0 += pix_per_wave) {
         const long long wp = std::min(pix_per_wave, npix - pix0);
         const int nq = (int)(wp * J.spp);

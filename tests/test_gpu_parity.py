@@ -38,6 +38,15 @@ def small_scenes():
     out["deep"] = sg.deep_stack_scene(num_sheets=85, width=12, height=8, spp=2, depth=128, tex_res=16, mesh=False)
     # normal maps on a rough dielectric, a diffuse and a rough conductor surface
     out["nmap"] = sg.normal_map_scene(width=20, spp=4, depth=4, tex_res=16)
+    # thirteen polarized lights: 156 scalar gradients, more than the 32 shared-memory copies
+    # per scalar fit in 16 KB, so the kernels keep one copy of each
+    s, j = sg.cornell_box()
+    for k in range(12):
+        a = 2.0 * np.pi * k / 12
+        s.add_light((0.7 * np.cos(a) - 0.06, 0.998, 0.7 * np.sin(a) - 0.06), (0.12, 0, 0), (0, 0, 0.12),
+                    [[4.0, 1.0, 0.5, 0.2]] * 3)
+    j.width = j.height = 24
+    out["lights13"] = (s, j)
     return out
 
 
