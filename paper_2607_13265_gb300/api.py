@@ -103,7 +103,7 @@ class Context:
         return {"local_bytes_per_thread": out[0], "registers": out[1], "threads_per_sm": out[2], "sms": out[3]}
 
     STAGES = ("primal", "adjoint", "wf_init", "wf_extend", "wf_shade", "wf_shadow", "wf_cache", "wf_replay",
-              "wf_swap", "wf_pixels", "filter")
+              "reserved", "wf_pixels", "filter")
 
     def stage_stats(self, timing: bool = False, reset: bool = True) -> dict:
         """{stage: (launches, ms)} since the last reset; then switches event timing on/off."""

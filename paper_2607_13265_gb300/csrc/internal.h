@@ -111,7 +111,7 @@ struct LaunchCfg {
 // the launching stream around every launch.
 enum Stage {
     kStagePrimal = 0, kStageAdjoint, kStageWfInit, kStageWfExtend, kStageWfShade, kStageWfShadow,
-    kStageWfCache, kStageWfReplay, kStageWfSwap, kStageWfPixels, kStageFilter, kStageCount
+    kStageWfCache, kStageWfReplay, kStageReserved, kStageWfPixels, kStageFilter, kStageCount
 };
 struct StageLog {
     int64_t launches[kStageCount] = {0};
