@@ -30,6 +30,10 @@
 #endif
 // resident 512-thread blocks per SM the shade kernel's register allocation must allow
 // (2 -> at most 64 registers per thread)
+// extend and shade fused in one kernel (1) or as two launches (0)
+#ifndef DPPT_WF_FUSE_SHADE
+#define DPPT_WF_FUSE_SHADE 1
+#endif
 #ifndef DPPT_WF_SHADE_MIN_BLOCKS
 #define DPPT_WF_SHADE_MIN_BLOCKS 2
 #endif
@@ -238,6 +242,57 @@ k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
         else { h.slot = -1; h.prim = S.num_tris + (-code - 1); }
         Walk w;
         get_walk(W.walk + q, w);
+        const WfMeta m = W.meta[q];
+        const unsigned long long pid = (unsigned long long)m.lo | ((unsigned long long)m.hi << 32);
+        VCtx vc;
+        NeePending ne;
+        Shade sh;
+        walk_shade<NM>(S, P, T.job[m.job], pid, w, h, vc, ne, sh);
+        put_vertex(W.vtx + q, vc, ne, sh);
+        if (ne.state == 1) {
+            W.ray[q] = WfRay{make_float4(ne.o2.x, ne.o2.y, ne.o2.z, ne.tmax), make_float4(ne.dir.x, ne.dir.y, ne.dir.z, 0.f)};
+            L.shadow[atomicAdd(L.cur + 4, 1)] = q;
+        }
+        W.visible[q] = 0;
+    }
+}
+
+// Extend and shade in one kernel: the closest hit of each cache-pass path and, from it in
+// registers, the vertex's surface data and samples.  The launch's block 0 zeroes the
+// counts the iteration appends to after this kernel and the next iteration's shadow
+// count (this kernel appends to this iteration's, zeroed one iteration earlier).
+template <bool NM>
+__global__ void __launch_bounds__(512, DPPT_WF_TRAVERSE_MIN_BLOCKS)
+k_wf_extend_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfState W, WfLists L,
+                  int store_hits, unsigned* status) {
+    const int n = L.cur[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        L.nxt[0] = 0; L.nxt[4] = 0;
+        for (int b = 8; b < 16; ++b) L.nxt[b] = 0;
+    }
+    const int stride = gridDim.x * blockDim.x;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
+        const int q = L.l0[idx];
+        HitRec h;
+        bool hit;
+        {
+            const float4 a = W.walk[q].a, b = W.walk[q].b;
+            hit = trace_closest<false>(S, f3{a.x, a.y, a.z}, f3{b.x, b.y, b.z}, h, status, nullptr);
+        }
+        Walk w;
+        get_walk(W.walk + q, w);
+        if (store_hits) {
+            float* rec = W.cache + ((long long)(w.v - 1) * W.Q + q) * kWfCacheComps;
+            const int code = !hit ? kMissCode : h.prim < S.num_tris ? h.slot : -(h.prim - S.num_tris + 1);
+            *reinterpret_cast<float4*>(rec + kWfHitComp) =
+                hit ? make_float4(h.t, h.b1, h.b2, __int_as_float(code)) : make_float4(0.f, 0.f, 0.f, __int_as_float(kMissCode));
+            if (!hit) rec[kWfVisComp] = __int_as_float(kBinOther << 1);
+        }
+        if (!hit) {
+            W.vtx[q].ids = make_int4(0, 0, 0, 0);
+            continue;
+        }
+        if (h.prim >= S.num_tris) h.slot = -1;
         const WfMeta m = W.meta[q];
         const unsigned long long pid = (unsigned long long)m.lo | ((unsigned long long)m.hi << 32);
         VCtx vc;
@@ -491,6 +546,12 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
             // lists, counts and bins alternate between two buffers: the next ones of an
             // iteration are the live ones of the following iteration
             const WfLists& L = (it & 1) ? B : A;
+#if DPPT_WF_FUSE_SHADE
+            tok = log->begin(kStageWfExtend, st);
+            if (nmaps) k_wf_extend_shade<true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status);
+            else k_wf_extend_shade<false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status);
+            log->end(tok, st);
+#else
             tok = log->begin(kStageWfExtend, st);
             k_wf_extend<<<grid, block, 0, st>>>(S, W, L, status);
             log->end(tok, st);
@@ -498,6 +559,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
             if (nmaps) k_wf_shade<true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1);
             else k_wf_shade<false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1);
             log->end(tok, st);
+#endif
             tok = log->begin(kStageWfShadow, st);
             k_wf_shadow<<<grid, block, 0, st>>>(S, W, L, status);
             log->end(tok, st);
