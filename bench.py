@@ -58,7 +58,7 @@ B_CACHE_PATH_PRIMAL, B_CACHE_PATH_ADJOINT = 48, 216
 # DRAM traffic per launch (bytes) from one ncu capture of this workload: mean of
 # dram__bytes_read.sum + dram__bytes_write.sum over the launches of one timed step;
 # None for a kernel changed since its capture.
-DRAM_BYTES_PER_LAUNCH = {"wf_extend": None, "wf_cache": None}
+DRAM_BYTES_PER_LAUNCH = {"wf_extend": 178.89e6, "wf_cache": 330.85e6}
 
 
 # floats per vertex of the wavefront cache: E_v 12, compact W_v 19, the hit 4, visibility 1
@@ -67,8 +67,8 @@ WF_CACHE_FLOATS = 36
 
 def wave_paths(job) -> int:
     """Paths per wavefront wave: at most 4,194,304 whole pixels and at most 8 GiB of path
-    state (~400 B) plus cache (144 B per vertex) per wave, as the library sizes them."""
-    per_path = 400 + 4 * WF_CACHE_FLOATS * job.max_depth
+    state (416 B) plus cache (144 B per vertex) per wave, as the library sizes them."""
+    per_path = 416 + 4 * WF_CACHE_FLOATS * job.max_depth
     cap = min(1 << 22, (8 << 30) // per_path)
     return min(job.num_paths, max(job.spp, cap // job.spp * job.spp))
 

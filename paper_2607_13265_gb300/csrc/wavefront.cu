@@ -1,7 +1,8 @@
 // Wavefront schedule of the same path tracer: the megakernel's per-vertex work split into
 // stage kernels over compacted lists of live paths.  A cache-pass iteration runs
-//   extend (closest hit) -> shade (surface data, light and BSDF samples)
-//   -> shadow (any hit of the light samples) -> cache (per-vertex action, next ray);
+//   extend + shade (closest hit, then surface data, light and BSDF samples; one kernel,
+//   or two with DPPT_WF_FUSE_SHADE=0) -> shadow (any hit of the light samples)
+//   -> cache (per-vertex action, next ray);
 // the replay runs in the same iterations as one kernel per material type, over the paths
 // binned by the type of their next vertex: it shades that vertex itself from the hit and
 // light-sample visibility the cache pass stored (no traversal, no vertex record) and
