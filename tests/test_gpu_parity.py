@@ -230,6 +230,39 @@ def test_schedules_agree(env, schedule, block):
         assert np.array_equal(ref, got)
 
 
+def test_wavefront_waves_match_megakernel(env):
+    """A job of 7.84 M paths runs as two wavefront waves (at most 4,194,304 paths each, whole
+    pixels): image and gradients equal the grid megakernel's, which has no waves, up to
+    summation order.  A gradient element sums millions of FP32 atomic additions in an order
+    that differs between the schedules (about sqrt(N) * 6e-8 ~ 2e-4 relative at N = 8e6);
+    a lost or repeated wave would be an O(1) error."""
+    import torch
+    api, dctx, _ = env
+    scene, job = sg.cornell_box()
+    job.width = job.height = 700
+    job.spp, job.max_depth = 16, 4
+    assert job.num_paths > 4194304
+    gs = api.GpuScene(dctx, scene)
+    prev = dctx.get_launch()
+    out = []
+    try:
+        for sched in (0, 2):
+            dctx.set_launch(sched, 128, 0, sched, 128, 0)
+            (img,), batch, P = gpu_image(api, dctx, gs, [job])
+            dI = torch.as_tensor(np.random.default_rng(5).normal(size=img.size), dtype=torch.float32, device="cuda")
+            g = api.render_adjoint(dctx, gs, batch, P, dI)
+            dctx.sync_status()
+            out.append((img, {k: v.double().cpu().numpy() for k, v in g.items()}))
+    finally:
+        dctx.set_launch(*prev)
+    (ri, rg), (wi, wg) = out
+    assert np.abs(ri).max() > 0
+    assert np.allclose(ri, wi, rtol=1e-5, atol=1e-6 * np.abs(ri).max())
+    for k in ("tex", "ior", "le", "theta"):
+        assert np.linalg.norm(rg[k]) > 0, k
+        assert grad_rel(wg[k], rg[k]) <= GRAD_TOL, (k, grad_rel(wg[k], rg[k]))
+
+
 @pytest.mark.parametrize("w,h,spp", [(37, 23, 3), (19, 5, 64), (1, 1, 1), (7, 9, 33)])
 def test_ragged_sizes(env, sched, oracle_mod, w, h, spp):
     api, dctx, O = env
