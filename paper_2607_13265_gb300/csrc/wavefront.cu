@@ -547,33 +547,40 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
             // lists, counts and bins alternate between two buffers: the next ones of an
             // iteration are the live ones of the following iteration
             const WfLists& L = (it & 1) ? B : A;
-#if DPPT_WF_FUSE_SHADE
-            tok = log->begin(kStageWfExtend, st);
-            if (nmaps) k_wf_extend_shade<true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status);
-            else k_wf_extend_shade<false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status);
-            log->end(tok, st);
-#else
-            tok = log->begin(kStageWfExtend, st);
-            k_wf_extend<<<grid, block, 0, st>>>(S, W, L, status);
-            log->end(tok, st);
-            tok = log->begin(kStageWfShade, st);
-            if (nmaps) k_wf_shade<true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1);
-            else k_wf_shade<false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1);
-            log->end(tok, st);
-#endif
-            tok = log->begin(kStageWfShadow, st);
-            k_wf_shadow<<<grid, block, 0, st>>>(S, W, L, status);
-            log->end(tok, st);
-            tok = log->begin(kStageWfCache, st);
-            if (mode == 0) {
-                if (nmaps) k_wf_finish<0, 0, true><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
-                else k_wf_finish<0, 0, false><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+            // a path's cache pass ends by iteration depth - 1 (one vertex per iteration), and no
+            // path replays before iteration 1: the launches with nothing to do are skipped
+            if (it >= J.depth) {
+                // what the extend launch would have zeroed: the counts appended to next
+                if ((e = cudaMemsetAsync(L.nxt, 0, sizeof(int) * 16, st)) != cudaSuccess) return e;
             } else {
-                if (nmaps) k_wf_finish<1, 0, true><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
-                else k_wf_finish<1, 0, false><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+#if DPPT_WF_FUSE_SHADE
+                tok = log->begin(kStageWfExtend, st);
+                if (nmaps) k_wf_extend_shade<true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status);
+                else k_wf_extend_shade<false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status);
+                log->end(tok, st);
+#else
+                tok = log->begin(kStageWfExtend, st);
+                k_wf_extend<<<grid, block, 0, st>>>(S, W, L, status);
+                log->end(tok, st);
+                tok = log->begin(kStageWfShade, st);
+                if (nmaps) k_wf_shade<true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1);
+                else k_wf_shade<false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1);
+                log->end(tok, st);
+#endif
+                tok = log->begin(kStageWfShadow, st);
+                k_wf_shadow<<<grid, block, 0, st>>>(S, W, L, status);
+                log->end(tok, st);
+                tok = log->begin(kStageWfCache, st);
+                if (mode == 0) {
+                    if (nmaps) k_wf_finish<0, 0, true><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+                    else k_wf_finish<0, 0, false><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+                } else {
+                    if (nmaps) k_wf_finish<1, 0, true><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+                    else k_wf_finish<1, 0, false><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+                }
+                log->end(tok, st);
             }
-            log->end(tok, st);
-            if (mode == 1) {
+            if (mode == 1 && it > 0) {
                 tok = log->begin(kStageWfReplay, st);
                 // one replay kernel per binned material type present, then the other bin
                 const ReplayArgs ra{S, P, G, T, W, L, sg, fgrid, smem, st, nmaps};
