@@ -261,27 +261,40 @@ k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
 // Extend and shade in one kernel: the closest hit of each cache-pass path and, from it in
 // registers, the vertex's surface data and samples.  The launch's block 0 zeroes the
 // counts the iteration appends to after this kernel and the next iteration's shadow
-// count (this kernel appends to this iteration's, zeroed one iteration earlier).
-template <bool NM>
+// count (this kernel appends to this iteration's, zeroed one iteration earlier).  The
+// first iteration of a wave (FIRST) starts the wave's nq paths p0 .. p0 + nq - 1 of job
+// `job` itself: camera rays, path records and the identity cache-pass list.
+template <bool NM, bool FIRST>
 __global__ void __launch_bounds__(512, DPPT_WF_TRAVERSE_MIN_BLOCKS)
 k_wf_extend_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfState W, WfLists L,
-                  int store_hits, unsigned* status) {
-    const int n = L.cur[0];
+                  int store_hits, unsigned* status, int job, long long p0, int nq) {
+    const int n = FIRST ? nq : L.cur[0];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         L.nxt[0] = 0; L.nxt[4] = 0;
         for (int b = 8; b < 16; ++b) L.nxt[b] = 0;
+        if (FIRST) L.cur[0] = nq;
     }
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        const int q = L.l0[idx];
+        const int q = FIRST ? idx : L.l0[idx];
         HitRec h;
         bool hit;
-        {
-            const float4 a = W.walk[q].a, b = W.walk[q].b;
-            hit = trace_closest<false>(S, f3{a.x, a.y, a.z}, f3{b.x, b.y, b.z}, h, status, nullptr);
-        }
         Walk w;
-        get_walk(W.walk + q, w);
+        if (FIRST) {
+            const unsigned long long pid = (unsigned long long)(p0 + q);
+            const DJob& J = T.job[job];
+            walk_begin(S, J, pid, (long long)(pid / J.spp), w);
+            put_walk(W.walk + q, w);
+            W.meta[q] = WfMeta{(unsigned)pid, (unsigned)(pid >> 32), job, 0};
+            L.l0[q] = q;
+            hit = trace_closest<false>(S, w.o, w.d, h, status, nullptr);
+        } else {
+            {
+                const float4 a = W.walk[q].a, b = W.walk[q].b;
+                hit = trace_closest<false>(S, f3{a.x, a.y, a.z}, f3{b.x, b.y, b.z}, h, status, nullptr);
+            }
+            get_walk(W.walk + q, w);
+        }
         if (store_hits) {
             float* rec = W.cache + ((long long)(w.v - 1) * W.Q + q) * kWfCacheComps;
             const int code = !hit ? kMissCode : h.prim < S.num_tris ? h.slot : -(h.prim - S.num_tris + 1);
@@ -539,9 +552,12 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
         const WfLists B{lists[1], lists[0], lists[2], count + 16, count, bins[1], bins[0], (int)Q};
         cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 32, st);
         if (e != cudaSuccess) return e;
-        int tok = log->begin(kStageWfInit, st);
+        int tok = 0;
+#if !DPPT_WF_FUSE_SHADE
+        tok = log->begin(kStageWfInit, st);
         k_wf_init<<<grid, block, 0, st>>>(S, T, job, pix0 * J.spp, nq, W, A);
         log->end(tok, st);
+#endif
         unsigned* sg = J.sig ? J.sig + pix0 * J.spp : nullptr;
         for (int it = 0; it < passes * J.depth; ++it) {
             // lists, counts and bins alternate between two buffers: the next ones of an
@@ -555,8 +571,15 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
             } else {
 #if DPPT_WF_FUSE_SHADE
                 tok = log->begin(kStageWfExtend, st);
-                if (nmaps) k_wf_extend_shade<true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status);
-                else k_wf_extend_shade<false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status);
+                // the first iteration also starts the wave's paths
+                const long long p0 = pix0 * J.spp;
+                if (it == 0) {
+                    if (nmaps) k_wf_extend_shade<true, true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, job, p0, nq);
+                    else k_wf_extend_shade<false, true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, job, p0, nq);
+                } else {
+                    if (nmaps) k_wf_extend_shade<true, false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, job, p0, nq);
+                    else k_wf_extend_shade<false, false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, job, p0, nq);
+                }
                 log->end(tok, st);
 #else
                 tok = log->begin(kStageWfExtend, st);
