@@ -52,6 +52,13 @@ dppt_status cuda_fail(dppt_ctx* ctx, cudaError_t e, const char* what) {
 }
 
 // ------------------------------------------------------------------ BVH (binned SAH)
+// SAH: centroid bins per axis, and the cost of visiting a node relative to one triangle test
+#ifndef DPPT_SAH_BINS
+#define DPPT_SAH_BINS 16
+#endif
+#ifndef DPPT_SAH_TRAV
+#define DPPT_SAH_TRAV 1.0
+#endif
 struct Box {
     float lo[3] = {INFINITY, INFINITY, INFINITY};
     float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -75,7 +82,7 @@ struct Builder {
     std::vector<float4> nodes;
     float pad;
     int max_depth = 0;
-    static constexpr int kBins = 16;
+    static constexpr int kBins = DPPT_SAH_BINS;
     static constexpr int kMaxLeaf = 8;
 
     Builder(const std::vector<Box>& b, const std::vector<float>& c, std::vector<int>& o, float p)
@@ -145,7 +152,7 @@ struct Builder {
             }
         }
         float leaf_cost = nb.area() * n;
-        if (best_axis < 0 || (best_cost * 1.0f + nb.area() * 1.0f >= leaf_cost && n <= kMaxLeaf)) {
+        if (best_axis < 0 || (best_cost * 1.0f + nb.area() * (float)DPPT_SAH_TRAV >= leaf_cost && n <= kMaxLeaf)) {
             if (n <= kMaxLeaf) return -1;
             if (best_axis < 0) return b + n / 2;
         }
