@@ -230,6 +230,42 @@ def test_schedules_agree(env, schedule, block):
         assert np.array_equal(ref, got)
 
 
+@pytest.mark.parametrize("depth", [1, 2])
+def test_shallow_paths(env, sched, depth):
+    """Depth 1 (emitter hits only, no light samples) and depth 2: the edge cases of the
+    wavefront's iteration count and of the replay's first and last vertex."""
+    import torch
+    api, dctx, O = env
+    scene, job = sg.cornell_box()
+    job.width = job.height = 24
+    job.max_depth = depth
+    job.pass_id = 1
+    try:
+        gs = api.GpuScene(dctx, scene)
+        batch = api.pack_jobs([job])
+        P = api.device_params(scene, batch)
+        frac, keep = identical_path_pixels(api, dctx, gs, job, O.OracleScene(scene), None)
+        assert frac >= 0.99, frac
+        (g_img,), _, _ = gpu_image(api, dctx, gs, [job])
+        o_img = O.OracleScene(scene).render(job, scene.params())
+        dI = np.random.default_rng(11).normal(size=(job.num_angles, job.num_pixels, 3, 4)) * keep[None, :, None, None]
+        grads = api.render_adjoint(dctx, gs, batch, P, torch.as_tensor(dI.ravel(), dtype=torch.float32, device="cuda"))
+        dctx.sync_status()
+        ref = O.OracleScene(scene).gradient(job, scene.params(), dI, mode="replay")
+    finally:
+        job.pass_id = 0
+    err = image_rel_err(flat(g_img), o_img)[:, keep]
+    assert float(np.quantile(err, 0.999)) <= IMG_TOL_P999
+    got = {k: v.double().cpu().numpy() for k, v in grads.items()}
+    keys = ("le", "theta") if depth == 1 else ("tex", "le", "theta")
+    for k in keys:
+        o = ref[k]
+        assert np.linalg.norm(o) > 0, k
+        assert grad_rel(got[k][:o.size], o) <= GRAD_TOL, (k, grad_rel(got[k][:o.size], o))
+    if depth == 1:      # nothing scatters at depth 1: no texture or index-of-refraction gradient
+        assert np.all(got["tex"] == 0.0) and np.all(ref["tex"] == 0.0)
+
+
 def test_wavefront_waves_match_megakernel(env):
     """A job of 7.84 M paths runs as two wavefront waves (at most 4,194,304 paths each, whole
     pixels): image and gradients equal the grid megakernel's, which has no waves, up to
