@@ -219,10 +219,17 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "200"],
+                                          "-i", str(self.index), "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+        if self.proc is not None:
+            # the timed region starts once the sampler runs; its first line, taken before the
+            # region, is not counted
+            import select
+            ready, _, _ = select.select([self.proc.stdout], [], [], 10.0)
+            if ready:
+                self.proc.stdout.readline()
         return self
 
     def __exit__(self, *exc):
@@ -318,11 +325,11 @@ def run_native(args):
 
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    dctx.stage_stats(timing=True, reset=True)      # per-stage CUDA events on the launching stream
-    with ClockSampler(local) as clk:
+    with ClockSampler(local) as clk:                # clocks sampled from here to the end of the region
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        dctx.stage_stats(timing=True, reset=True)  # per-stage CUDA events on the launching stream
         for k in range(K):
             flush.zero_()                               # L2 flush between timed steps (outside the events)
             e0, e1, e2, e3 = ev[k]
