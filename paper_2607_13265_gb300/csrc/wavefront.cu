@@ -146,6 +146,9 @@ struct WfLists {
 // conductor, rough dielectric, polarizer and retarder sheets), and one bin for everything
 // else (smooth dielectrics, emitter hits, paths that left the scene).
 constexpr int kBinOther = 7;
+// the bin word of a cache slot whose ray left the scene: the replay of a path ends at the
+// vertex before it, with no launch for the miss
+constexpr int kBinMiss = 15;
 constexpr unsigned kBinnedTypes = (1u << DPPT_MAT_DIFFUSE) | (1u << DPPT_MAT_CONDUCTOR_GGX) |
                                   (1u << DPPT_MAT_PLASTIC_GGX) | (1u << DPPT_MAT_POLARIZER_SHEET) |
                                   (1u << DPPT_MAT_RETARDER_SHEET);
@@ -205,7 +208,7 @@ __device__ __forceinline__ void bin_append(const WfLists& L, int b, int q) {
 
 // The cache record's visibility word (kWfVisComp) holds, as an int, the light sample's
 // visibility in bit 0 and the vertex's replay bin above it: the material type when that
-// type has a replay kernel of its own, else kBinOther (misses included).
+// type has a replay kernel of its own, kBinMiss when the ray left the scene, else kBinOther.
 __device__ __forceinline__ int replay_bin(const DScene& S, int mat) {
     const int t = __ldg(&S.mats[mat].type);
     return (kBinnedTypes >> t) & 1u ? t : kBinOther;
@@ -231,7 +234,7 @@ k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
             const int v = __float_as_int(W.walk[q].c.w) & 0xff;     // the vertex's slot (see put_walk)
             float* rec = W.cache + ((long long)(v - 1) * W.Q + q) * kWfCacheComps;
             *reinterpret_cast<float4*>(rec + kWfHitComp) = hv;
-            if (code == kMissCode) rec[kWfVisComp] = __int_as_float(kBinOther << 1);
+            if (code == kMissCode) rec[kWfVisComp] = __int_as_float(kBinMiss << 1);
         }
         if (code == kMissCode) {
             W.vtx[q].ids = make_int4(0, 0, 0, 0);
@@ -300,7 +303,7 @@ k_wf_extend_shade(const DScene S, const DParams P, const __grid_constant__ JobTa
             const int code = !hit ? kMissCode : h.prim < S.num_tris ? h.slot : -(h.prim - S.num_tris + 1);
             *reinterpret_cast<float4*>(rec + kWfHitComp) =
                 hit ? make_float4(h.t, h.b1, h.b2, __int_as_float(code)) : make_float4(0.f, 0.f, 0.f, __int_as_float(kMissCode));
-            if (!hit) rec[kWfVisComp] = __int_as_float(kBinOther << 1);
+            if (!hit) rec[kWfVisComp] = __int_as_float(kBinMiss << 1);
         }
         if (!hit) {
             W.vtx[q].ids = make_int4(0, 0, 0, 0);
@@ -399,9 +402,12 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
         }
         bool done = false;
         int phase = PHASE;
-        if (cont) {
-            if (PHASE == 0) L.next0[atomicAdd(L.nxt + 0, 1)] = q;
-            else bin_append(L, replay_bin_of(W, q, w.v - 1), q);
+        if (cont && PHASE == 1) {
+            const int b = replay_bin_of(W, q, w.v - 1);
+            if (b == kBinMiss) done = true;     // the next ray left the scene: nothing to replay
+            else bin_append(L, b, q);
+        } else if (cont) {
+            L.next0[atomicAdd(L.nxt + 0, 1)] = q;
         } else if (PHASE == 0) {
             float L0[12];
             vis.fold(L0);
