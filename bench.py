@@ -58,7 +58,7 @@ B_CACHE_PATH_PRIMAL, B_CACHE_PATH_ADJOINT = 48, 216
 # DRAM traffic per launch (bytes) from one ncu capture of this workload: mean of
 # dram__bytes_read.sum + dram__bytes_write.sum over the launches of one timed step;
 # None for a kernel changed since its capture.
-DRAM_BYTES_PER_LAUNCH = {"wf_extend": 269.19e6, "wf_cache": 496.14e6}
+DRAM_BYTES_PER_LAUNCH = {"wf_extend": 269.25e6, "wf_cache": 496.24e6}
 
 
 # floats per vertex of the wavefront cache: E_v 12, compact W_v 19, the hit 4, visibility 1
