@@ -69,6 +69,7 @@ def lib():
             L.orc_fresnel_transmit.argtypes = [dbl, dbl, dbl, P]
             L.orc_camera_filter.argtypes = [i32, dbl, P]
             L.orc_csqrt.argtypes = [dbl, dbl, P]
+            L.orc_ggx.argtypes = [dbl, dbl, dbl, dbl, P]
             L.orc_closest.restype = i32
             L.orc_closest.argtypes = [P, P, P, i32, P]
             L.orc_stats.argtypes = [P, i32]
@@ -250,6 +251,13 @@ def camera_filter(filter_type: int, theta: float) -> np.ndarray:
     o = np.zeros(16)
     lib().orc_camera_filter(filter_type, theta, _p(o))
     return o.reshape(4, 4)
+
+
+def ggx(cos_h: float, cos_v: float, cos_vh: float, alpha: float) -> tuple[float, float]:
+    """The oracle's GGX D(cos_h) and Smith G1(cos_v, cos_vh) for roughness alpha."""
+    o = np.zeros(2)
+    lib().orc_ggx(float(cos_h), float(cos_v), float(cos_vh), float(alpha), _p(o))
+    return float(o[0]), float(o[1])
 
 
 def csqrt(z: complex) -> complex:

@@ -1544,6 +1544,11 @@ void orc_camera_filter(int filter, double theta, double* m16) {
     M4<double> C = camera_filter<double>(filter, theta);
     for (int i = 0; i < 4; ++i) for (int j = 0; j < 4; ++j) m16[4 * i + j] = C.m[i][j];
 }
+// GGX normal distribution D(cos_h) and Smith masking G1(cos_v, cos_vh) (Walter et al. 2007)
+void orc_ggx(double cos_h, double cos_v, double cos_vh, double alpha, double* out) {
+    out[0] = ggx_D<double>(cos_h, alpha);
+    out[1] = ggx_G1<double>(cos_v, cos_vh, alpha);
+}
 void orc_csqrt(double re, double im, double* out) {
     Cx<double> r = csqrt(Cx<double>{re, im});
     out[0] = r.re; out[1] = r.im;

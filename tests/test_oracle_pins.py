@@ -2,7 +2,8 @@
 
 Each test names the fact it checks.  Together they are chosen so that a dropped term, a
 wrong sign or index, or a transposed operand in the oracle fails at least one of them:
-Malus's law and its derivative (polarizer, frame rotations, camera filter), the quarter-wave
+Malus's law and its derivative (polarizer, frame rotations, camera filter), the GGX
+normalization and Smith masking identities (pBRDF lobes), the quarter-wave
 conversion to circular light (retarder block), Brewster's angle (Fresnel s/p split and the
 s/p frame), energy conservation and textbook closed forms of the Fresnel coefficients,
 exact depolarization after a diffuse bounce (Sec. 4.1 case 2), the white furnace (sampling
@@ -95,6 +96,37 @@ def test_fresnel_total_internal_reflection_is_a_retarder(oracle_mod):
         s2 = 1 - ci * ci
         d = 2 * math.atan(ci * math.sqrt(s2 - 1 / n**2) / s2)
         assert abs(math.cos(d)) == pytest.approx(abs(C), abs=1e-12)
+
+
+@pytest.mark.parametrize("alpha", [0.05, 0.2, 0.5, 1.0])
+def test_ggx_projected_area_and_masking_identities(oracle_mod, alpha):
+    """Two identities of the GGX microfacet model (Walter et al. 2007; Heitz 2014, "Understanding
+    the masking-shadowing function"), fixed by geometry rather than by the oracle:
+    the microfacet normals cover the macro-surface exactly once,
+        int D(h) cos(theta_h) dw_h = 2 pi int_0^1 D(mu) mu dmu = 1,
+    and the Smith masking G1 normalizes the visible projected area for every direction o,
+        G1(o) int max(0, o.h) D(h) dw_h = cos(theta_o).
+    A missing 1/pi, a squared or unsquared alpha, or a wrong exponent in D or G1 breaks one."""
+    integrate = pytest.importorskip("scipy.integrate")
+    D = lambda mu: oracle_mod.ggx(mu, 1.0, 1.0, alpha)[0]
+    # D peaks within ~alpha of mu = 1: split the range there for the quadrature
+    knots = [0.0, max(0.0, 1.0 - 4.0 * alpha * alpha), 1.0]
+    area = sum(integrate.quad(lambda m: D(m) * m, a, b, epsabs=1e-13, epsrel=1e-11, limit=400)[0]
+               for a, b in zip(knots[:-1], knots[1:]) if b > a)
+    assert 2.0 * math.pi * area == pytest.approx(1.0, rel=1e-8)
+    for theta_o in (0.0, 0.5, 1.0, 1.3):
+        o = np.array([math.sin(theta_o), 0.0, math.cos(theta_o)])
+
+        def visible(phi, mu):
+            s = math.sqrt(max(0.0, 1.0 - mu * mu))
+            return max(0.0, o[0] * s * math.cos(phi) + o[2] * mu) * D(mu)
+
+        # the phi integrand is even: integrate over [0, pi] and double
+        inner = lambda mu: integrate.quad(lambda ph: visible(ph, mu), 0.0, math.pi, epsabs=1e-12, limit=200)[0]
+        proj = 2.0 * sum(integrate.quad(inner, a, b, epsabs=1e-10, epsrel=1e-8, limit=200)[0]
+                         for a, b in zip(knots[:-1], knots[1:]) if b > a)
+        g1 = oracle_mod.ggx(1.0, math.cos(theta_o), 1.0, alpha)[1]
+        assert g1 * proj == pytest.approx(math.cos(theta_o), rel=1e-6), (alpha, theta_o)
 
 
 def test_conductor_normal_incidence(oracle_mod):
