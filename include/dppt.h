@@ -318,9 +318,10 @@ dppt_status dppt_render_primal_noalloc(dppt_ctx* ctx, const dppt_scene* scene, c
 /* Kernel launches per stage since the last reset and, while timing is on,
  * their summed durations from CUDA events recorded on the launching stream
  * around each launch.  Stages: 0 primal megakernel, 1 adjoint megakernel,
- * 2-7 wavefront init, extend (closest hit), shade, shadow (any hit), cache
- * pass, replay pass; 8 reserved (no launches); 9 wavefront pixel sums; 10
- * camera-filter folds.  The call
+ * 2-7 wavefront init, extend (closest hit; with the default build it also
+ * shades the vertex and starts a wave's paths, so stages 2 and 4 have no
+ * launches), shade, shadow (any hit), cache pass, replay pass; 8 reserved (no
+ * launches); 9 wavefront pixel sums; 10 camera-filter folds.  The call
  * waits for the recorded events, copies the counters to launches[16] and
  * ms[16] (either may be NULL), clears them when reset != 0 and then sets
  * timing on or off for the following launches. */
