@@ -31,6 +31,10 @@
 #endif
 // resident 512-thread blocks per SM the shade kernel's register allocation must allow
 // (2 -> at most 64 registers per thread)
+// resident 512-thread blocks per SM the fused extend + shade kernel's registers must allow
+#ifndef DPPT_WF_EXTEND_SHADE_MIN_BLOCKS
+#define DPPT_WF_EXTEND_SHADE_MIN_BLOCKS 2
+#endif
 // extend and shade fused in one kernel (1) or as two launches (0)
 #ifndef DPPT_WF_FUSE_SHADE
 #define DPPT_WF_FUSE_SHADE 1
@@ -268,7 +272,7 @@ k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
 // first iteration of a wave (FIRST) starts the wave's nq paths p0 .. p0 + nq - 1 of job
 // `job` itself: camera rays, path records and the identity cache-pass list.
 template <bool NM, bool FIRST>
-__global__ void __launch_bounds__(512, DPPT_WF_TRAVERSE_MIN_BLOCKS)
+__global__ void __launch_bounds__(512, DPPT_WF_EXTEND_SHADE_MIN_BLOCKS)
 k_wf_extend_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfState W, WfLists L,
                   int store_hits, unsigned* status, int job, long long p0, int nq) {
     const int n = FIRST ? nq : L.cur[0];
