@@ -66,10 +66,10 @@ WF_CACHE_FLOATS = 36
 
 
 def wave_paths(job) -> int:
-    """Paths per wavefront wave: at most 4,194,304 whole pixels and at most 8 GiB of path
+    """Paths per wavefront wave: at most 4,194,304 whole pixels and at most 32 GiB of path
     state (416 B) plus cache (144 B per vertex) per wave, as the library sizes them."""
     per_path = 416 + 4 * WF_CACHE_FLOATS * job.max_depth
-    cap = min(1 << 22, (8 << 30) // per_path)
+    cap = min(1 << 22, (32 << 30) // per_path)
     return min(job.num_paths, max(job.spp, cap // job.spp * job.spp))
 
 

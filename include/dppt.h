@@ -232,7 +232,7 @@ dppt_status dppt_render_adjoint_l2(dppt_ctx* ctx, const dppt_scene* scene, const
  * context's current launch shapes: filter buffers, plus the wavefront path
  * state and per-vertex cache when a wavefront schedule is selected.  The
  * wavefront runs in waves of at most 4,194,304 paths (whole pixels), fewer
- * when the wave's state and cache would pass 8 GiB (deep paths). */
+ * when the wave's state and cache would pass 32 GiB (deep paths). */
 dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int32_t njobs, size_t* bytes);
 
 /* Schedule for subsequent launches (the autotuner's choice). */

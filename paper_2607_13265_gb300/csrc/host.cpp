@@ -746,7 +746,12 @@ static void build_tables(const dppt_job* jobs, int njobs, const std::vector<JobP
 }
 
 constexpr long long kWaveCap = 1LL << 22;        // paths per wave of the wavefront schedule
-constexpr long long kWaveBytes = 8LL << 30;      // wave state + cache budget (deep paths take smaller waves)
+// a wave's state and cache budget: 32 GiB, an eighth of GB300's HBM, holds one wave of the
+// 1280x720 deep-path workload at depth 128 (17 GB; 8 GiB made three waves, 1.5x the time)
+#ifndef DPPT_WF_WAVE_GIB
+#define DPPT_WF_WAVE_GIB 32
+#endif
+constexpr long long kWaveBytes = (long long)DPPT_WF_WAVE_GIB << 30;   // wave state + cache budget (deep paths take smaller waves)
 
 static int max_depth_of(const dppt_job* jobs, int njobs) {
     int d = 1;

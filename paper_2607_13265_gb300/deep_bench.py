@@ -11,7 +11,7 @@ every k vertices; with --pprb, for the basic polarized PRB baseline, which keeps
   * megakernel schedules: the per-thread local cache (bytes per thread, from the compiled
     kernel) times the threads resident on the GPU -- independent of the image size;
   * wavefront schedule: the library workspace (path state + per-vertex cache of one wave,
-    waves capped at 8 GiB).
+    waves capped at 32 GiB).
 The loss is a seeded linear functional of the image.  Prints one JSON line per
 (schedule, depth) and a final summary line.
 
