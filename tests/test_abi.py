@@ -59,6 +59,33 @@ int main(void) {
     assert sizes == mine
 
 
+def test_field_offsets_match_header():
+    """Every field of every ctypes mirror sits at the offset the C compiler gives the
+    field of the same name (the Python name `pass_` mirrors the C field `pass`)."""
+    from paper_2607_13265_gb300 import _lib
+    import subprocess
+    import tempfile
+    mirrors = {"dppt_material": _lib.Material, "dppt_scene_desc": _lib.SceneDesc, "dppt_job": _lib.Job,
+               "dppt_params": _lib.Params, "dppt_grads": _lib.Grads, "dppt_launch": _lib.Launch,
+               "dppt_replay": _lib.Replay}
+    lines, expect = [], []
+    for cname, t in mirrors.items():
+        for f in t._fields_:
+            name = f[0]
+            cfield = "pass" if name == "pass_" else name
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {cfield}));')
+            expect.append(getattr(t, name).offset)
+    src = "#include <stdio.h>\n#include <stddef.h>\n#include \"dppt.h\"\nint main(void) {\n" + "\n".join(lines) + \
+          "\n  return 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "o.c")
+        exe = os.path.join(d, "o")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        got = [int(x) for x in subprocess.check_output([exe]).split()]
+    assert got == expect
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_2607_13265_gb300 import _lib
     saved = _lib._lib
