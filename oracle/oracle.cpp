@@ -23,9 +23,10 @@
 //   * a frozen-sampling estimator F(pi) (sampling from pi0, values from pi)
 //     whose central differences check both derivative routes.
 //
-// Conventions that the paper leaves to its host renderer are fixed here and
-// listed in the design notes; they are implemented again, independently, in
-// the CUDA library.
+// Conventions that the paper leaves to its host renderer (Stokes frames and the
+// rotation sign, the signs of the Fresnel blocks' C and S terms, the depth and
+// MIS conventions) are fixed here and implemented again, independently, in the
+// CUDA library.
 #include <algorithm>
 #include <array>
 #include <cmath>
