@@ -44,37 +44,46 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def _configure(L):
+    P = ctypes.c_void_p
+    i64, dbl, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    L.orc_scene_create.restype = P
+    L.orc_scene_create.argtypes = [i64, P, P, i64, P, P, P, i64, P, P, i64, P, P, i64, P, i64, P, i64, P, dbl]
+    L.orc_scene_destroy.argtypes = [P]
+    L.orc_render.restype = i32
+    L.orc_render.argtypes = [P, P, P, i64, P, P, P, P, P, P]
+    L.orc_gradient.restype = i32
+    L.orc_gradient.argtypes = [P, P, P, i64, P, P, P, P, i32]
+    L.orc_gradient_pprb.restype = i32
+    L.orc_gradient_pprb.argtypes = [P, P, P, i64, P, P, P, P, dbl, i32]
+    L.orc_gradient_hybrid.restype = i32
+    L.orc_gradient_hybrid.argtypes = [P, P, P, i64, P, P, P, P, i32, dbl, dbl, P]
+    L.orc_philox.argtypes = [P, P, P]
+    L.orc_uniforms.argtypes = [ctypes.c_uint64] * 5 + [P]
+    L.orc_fresnel_reflect.argtypes = [dbl, dbl, dbl, dbl, P]
+    L.orc_fresnel_transmit.argtypes = [dbl, dbl, dbl, P]
+    L.orc_camera_filter.argtypes = [i32, dbl, P]
+    L.orc_csqrt.argtypes = [dbl, dbl, P]
+    L.orc_ggx.argtypes = [dbl, dbl, dbl, dbl, P]
+    L.orc_closest.restype = i32
+    L.orc_closest.argtypes = [P, P, P, i32, P]
+    L.orc_stats.argtypes = [P, i32]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_SO)
-            P = ctypes.c_void_p
-            i64, dbl, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int
-            L.orc_scene_create.restype = P
-            L.orc_scene_create.argtypes = [i64, P, P, i64, P, P, P, i64, P, P, i64, P, P, i64, P, i64, P, i64, P, dbl]
-            L.orc_scene_destroy.argtypes = [P]
-            L.orc_render.restype = i32
-            L.orc_render.argtypes = [P, P, P, i64, P, P, P, P, P, P]
-            L.orc_gradient.restype = i32
-            L.orc_gradient.argtypes = [P, P, P, i64, P, P, P, P, i32]
-            L.orc_gradient_pprb.restype = i32
-            L.orc_gradient_pprb.argtypes = [P, P, P, i64, P, P, P, P, dbl, i32]
-            L.orc_gradient_hybrid.restype = i32
-            L.orc_gradient_hybrid.argtypes = [P, P, P, i64, P, P, P, P, i32, dbl, dbl, P]
-            L.orc_philox.argtypes = [P, P, P]
-            L.orc_uniforms.argtypes = [ctypes.c_uint64] * 5 + [P]
-            L.orc_fresnel_reflect.argtypes = [dbl, dbl, dbl, dbl, P]
-            L.orc_fresnel_transmit.argtypes = [dbl, dbl, dbl, P]
-            L.orc_camera_filter.argtypes = [i32, dbl, P]
-            L.orc_csqrt.argtypes = [dbl, dbl, P]
-            L.orc_ggx.argtypes = [dbl, dbl, dbl, dbl, P]
-            L.orc_closest.restype = i32
-            L.orc_closest.argtypes = [P, P, P, i32, P]
-            L.orc_stats.argtypes = [P, i32]
-            _lib = L
+            _lib = _configure(ctypes.CDLL(_SO))
     return _lib
+
+
+def load(path: str):
+    """A separate build of the oracle at `path` (the tests build copies of oracle.cpp with
+    one planted mistake and check that the pins catch it); pass it to OracleScene."""
+    return _configure(ctypes.CDLL(os.path.abspath(path)))
 
 
 def _p(a):
@@ -110,8 +119,8 @@ MAT_F_FIELDS = 10
 class OracleScene:
     """The oracle's own copy of a scene (built from the seeded generator's arrays)."""
 
-    def __init__(self, scene):
-        L = lib()
+    def __init__(self, scene, library=None):
+        L = self._lib = library if library is not None else lib()
         self._keep = []
 
         def arr(a, dt):
@@ -140,7 +149,7 @@ class OracleScene:
 
     def __del__(self):
         try:
-            lib().orc_scene_destroy(self.h)
+            self._lib.orc_scene_destroy(self.h)
         except Exception:
             pass
 
@@ -164,7 +173,7 @@ class OracleScene:
         pout = np.zeros((len(pix) * job.spp, 3, 4)) if paths else None
         sig = np.zeros(len(pix) * job.spp, np.uint32) if paths else None
         j = job_array(job)
-        rc = lib().orc_render(self.h, _p(j), _p(pix), len(pix), _p(P0), _p(Pv), _p(lay), _p(out), _p(pout), _p(sig))
+        rc = self._lib.orc_render(self.h, _p(j), _p(pix), len(pix), _p(P0), _p(Pv), _p(lay), _p(out), _p(pout), _p(sig))
         assert rc == 0
         return (out, pout, sig) if paths else out
 
@@ -181,10 +190,10 @@ class OracleScene:
         g = np.zeros_like(P)
         j = job_array(job)
         if mode == "pprb":
-            rc = lib().orc_gradient_pprb(self.h, _p(j), _p(pix), len(pix), _p(P), _p(lay), _p(dI), _p(g),
+            rc = self._lib.orc_gradient_pprb(self.h, _p(j), _p(pix), len(pix), _p(P), _p(lay), _p(dI), _p(g),
                                          float(sigma), int(primal_noise) | (2 if single else 0))
         else:
-            rc = lib().orc_gradient(self.h, _p(j), _p(pix), len(pix), _p(P), _p(lay), _p(dI), _p(g),
+            rc = self._lib.orc_gradient(self.h, _p(j), _p(pix), len(pix), _p(P), _p(lay), _p(dI), _p(g),
                                     {"tape": 0, "replay": 1}[mode])
         assert rc == 0
         return unflat(g, lay)
@@ -200,7 +209,7 @@ class OracleScene:
         g = np.zeros_like(P)
         routes = np.zeros(4)
         j = job_array(job)
-        rc = lib().orc_gradient_hybrid(self.h, _p(j), _p(pix), len(pix), _p(P), _p(lay), _p(dI), _p(g),
+        rc = self._lib.orc_gradient_hybrid(self.h, _p(j), _p(pix), len(pix), _p(P), _p(lay), _p(dI), _p(g),
                                        int(k), float(gamma), float(eps), _p(routes))
         assert rc == 0
         return unflat(g, lay), dict(zip(["cached", "scalar", "inverse", "recompute"], routes.tolist()))
@@ -209,7 +218,7 @@ class OracleScene:
         o = np.ascontiguousarray(o, np.float64)
         d = np.ascontiguousarray(d, np.float64)
         t = np.zeros(1)
-        prim = lib().orc_closest(self.h, _p(o), _p(d), int(brute), _p(t))
+        prim = self._lib.orc_closest(self.h, _p(o), _p(d), int(brute), _p(t))
         return prim, float(t[0])
 
 

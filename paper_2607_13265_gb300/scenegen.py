@@ -564,14 +564,15 @@ def normal_map_scene(width: int = 24, spp: int = 4, depth: int = 4, tex_res: int
                      freq: int = 3) -> tuple[Scene, Job]:
     """Normal-mapped pBRDFs: a rough-dielectric ground quad, a diffuse back wall and a
     rough-conductor geodesic sphere (20*freq^2 triangles), each with its own differentiable
-    tangent-space normal map (seeded bumps; flat=True: n = (0, 0, 1) everywhere); a quad
-    light of radiance 8 and a camera polarizer at 20 deg."""
+    tangent-space normal map (seeded bumps; flat=True: n = (0, 0, 1) everywhere) and a
+    shared differentiable 8x8 albedo texture ~ U[0.3, 0.8] (seed 43) and roughness texture
+    ~ U[0.15, 0.45] (seed 44); a quad light of radiance 8 and a camera polarizer at 20 deg."""
     s = Scene()
     maps = [np.full((tex_res, tex_res, 3), (0.5, 0.5, 1.0)) if flat else bump_normal_map(tex_res, 40 + k)
             for k in range(3)]
     tn = [s.add_texture(m_, differentiable=True) for m_ in maps]
-    tr = s.add_const_texture([0.3])
-    ta = s.add_const_texture([0.6, 0.5, 0.4])
+    tr = s.add_texture(np.random.default_rng(44).uniform(0.15, 0.45, (8, 8)), differentiable=True)
+    ta = s.add_texture(np.random.default_rng(43).uniform(0.3, 0.8, (8, 8, 3)), differentiable=True)
     ground = s.add_material(Material(MAT_PLASTIC_GGX, albedo_tex=ta, rough_tex=tr, ior_index=s.add_ior(1.5),
                                      normal_tex=tn[0]))
     wall = s.add_material(Material(MAT_DIFFUSE, albedo_tex=ta, normal_tex=tn[1]))
@@ -671,6 +672,107 @@ def brewster_scene(ior: float = 1.5, le: float = 1.0, dielectric: bool = True) -
     s.add_light(o, e1, e2, le)
     s.add_camera((0, 3 * math.cos(tb), -3 * math.sin(tb)), (0, 0, 0), (0, 1, 0), 0.01)
     job = Job(camera=0, width=2, height=2, spp=64, max_depth=2)
+    return s, job
+
+
+def polygon_light_scene(albedo=(0.6, 0.5, 0.4), le=(5.0, 3.0), surface_emission: bool = False,
+                        spp: int = 4096) -> tuple[Scene, Job]:
+    """A diffuse floor (y = 0, normal +y) of constant albedo seen at the origin by a camera
+    with a tiny field of view, lit by two one-sided parallelogram lights of unpolarized
+    radiance le[0] and le[1]: a tilted one above the origin and a small upright one near
+    the horizon, so that the cosines at the two ends of a light sample differ.  Depth 2
+    (direct light only), no camera filter.  With surface_emission the lights are replaced
+    by two-sided emitting diffuse quads of zero albedo at the same places: there is then no
+    light to sample, and only BSDF sampling reaches them.  The light quads, as (o, e1, e2),
+    are LIGHT_QUADS."""
+    s = Scene()
+    ta = s.add_const_texture(list(albedo), differentiable=True)
+    floor = s.add_material(Material(MAT_DIFFUSE, albedo_tex=ta))
+    s.add_quad((-5, 0, 5), (10, 0, 0), (0, 0, -10), floor)          # normal +y
+    black = s.add_const_texture([0.0, 0.0, 0.0])
+    for (o, e1, e2), L in zip(LIGHT_QUADS, le):
+        if surface_emission:
+            s.add_quad(o, e1, e2, s.add_material(Material(MAT_DIFFUSE, albedo_tex=black, emission=float(L))))
+        else:
+            s.add_light(np.array(o, np.float64), np.array(e1, np.float64), np.array(e2, np.float64), float(L))
+    s.add_camera((0, 2.0, 2.0), (0, 0, 0), (0, 1, 0), 0.01)
+    job = Job(camera=0, width=2, height=2, spp=spp, max_depth=2, seed=5)
+    return s, job
+
+
+# (o, e1, e2) of the two lights of polygon_light_scene; each emits toward e1 x e2, which faces
+# the origin: one above, tilted (normal (0, -0.6, 0.6)), one upright near the horizon (normal -x)
+LIGHT_QUADS = (((-0.6, 1.5, -0.9), (1.0, 0.0, 0.0), (0.0, 0.6, 0.6)),
+               ((1.5, 0.2, -0.4), (0.0, 0.0, 0.8), (0.0, 0.5, 0.0)))
+
+
+def _yawed(v, yaw_deg: float) -> np.ndarray:
+    """v rotated by yaw_deg about the y axis (so that no direction of a test scene lies in a
+    coordinate plane, where reference-frame tangents degenerate to the axes)."""
+    c, s_ = math.cos(math.radians(yaw_deg)), math.sin(math.radians(yaw_deg))
+    v = np.asarray(v, np.float64)
+    return np.array([c * v[0] + s_ * v[2], v[1], -s_ * v[0] + c * v[2]])
+
+
+def glass_interface_scene(ior: float = 1.5, theta_deg: float = 35.0, camera_inside: bool = False,
+                          slab: float = 0.0, le: float = 1.0, spp: int = 256, yaw_deg: float = 30.0
+                          ) -> tuple[Scene, Job]:
+    """A smooth-dielectric plane (y = 0) between a camera above it, looking at the origin at
+    theta_deg from the normal in the y-z plane (its right vector is the s axis of the
+    interface), and a large one-sided unpolarized light below, facing up.  The plane's
+    normal faces the camera (the camera is in air) or, with camera_inside, the light (the
+    camera is on the side of the medium).  slab > 0 adds a second, parallel interface of the
+    same index at y = -slab whose normal faces down: a glass slab seen from air.  The
+    camera's plane of incidence is turned by yaw_deg about the normal.  Depth 2 (3 with the
+    slab), no camera filter."""
+    s = Scene()
+    glass = s.add_material(Material(MAT_SMOOTH_DIELECTRIC, ior_index=s.add_ior(ior)))
+    if camera_inside:
+        s.add_quad((-50, 0, 50), (0, 0, -100), (100, 0, 0), glass)    # normal -y
+    else:
+        s.add_quad((-50, 0, 50), (100, 0, 0), (0, 0, -100), glass)    # normal +y
+    if slab > 0.0:
+        s.add_quad((-50, -slab, 50), (0, 0, -100), (100, 0, 0), glass)
+    s.add_light(np.array([-50.0, -1.0 - slab, 50.0]), np.array([100.0, 0, 0]), np.array([0, 0, -100.0]), le)
+    t = math.radians(theta_deg)
+    s.add_camera(_yawed((0, 3 * math.cos(t), -3 * math.sin(t)), yaw_deg), (0, 0, 0), (0, 1, 0), 0.01)
+    job = Job(camera=0, width=2, height=2, spp=spp, max_depth=3 if slab > 0.0 else 2, seed=9)
+    return s, job
+
+
+def specular_limit_scene(kind: str, theta_deg: float, roughness: float = 0.01, le=(1.0, 0.3, 0.5, 0.2),
+                         ior: float = 1.5, eta=(0.2, 3.0), spp: int = 1024, light_size: float = 8.0,
+                         yaw_deg: float = 30.0) -> tuple[Scene, Job]:
+    """A plane (y = 0, normal +y) seen at theta_deg from its normal by a camera in the y-z
+    plane (right vector = the s axis), with a large quad light in the mirror direction whose
+    Stokes radiance le is given in the light's frame, its x axis (the first edge) along the
+    s axis.  The light is a square of side light_size at distance 10; the plane of
+    incidence is turned by yaw_deg about the normal.  kind: 'conductor'
+    (GGX, complex index eta, white tint), 'plastic' (GGX rough dielectric of index ior with
+    a black diffuse lobe, so only the specular lobe is sampled), or 'smooth' (smooth
+    dielectric of index ior).  The GGX kinds take a constant roughness.  Depth 2, no camera
+    filter."""
+    s = Scene()
+    if kind == "smooth":
+        m = s.add_material(Material(MAT_SMOOTH_DIELECTRIC, ior_index=s.add_ior(ior)))
+    else:
+        tr = s.add_const_texture([roughness], differentiable=True)
+        if kind == "conductor":
+            m = s.add_material(Material(MAT_CONDUCTOR_GGX, rough_tex=tr, eta_re=eta[0], eta_im=eta[1]))
+        else:
+            tb = s.add_const_texture([0.0, 0.0, 0.0])
+            m = s.add_material(Material(MAT_PLASTIC_GGX, albedo_tex=tb, rough_tex=tr, ior_index=s.add_ior(ior)))
+    s.add_quad((-50, 0, 50), (100, 0, 0), (0, 0, -100), m)
+    t = math.radians(theta_deg)
+    d = 10.0
+    c = _yawed((0.0, d * math.cos(t), d * math.sin(t)), yaw_deg)
+    n = -c / np.linalg.norm(c)
+    sx = _yawed((1.0, 0.0, 0.0), yaw_deg)             # the s axis of the plane of incidence
+    e1 = light_size * sx
+    e2 = light_size * np.cross(n, sx)                 # e1 x e2 along n: the light faces the origin
+    s.add_light(c - 0.5 * e1 - 0.5 * e2, e1, e2, np.asarray(le, np.float64))
+    s.add_camera(_yawed((0, 3 * math.cos(t), -3 * math.sin(t)), yaw_deg), (0, 0, 0), (0, 1, 0), 0.01)
+    job = Job(camera=0, width=2, height=2, spp=spp, max_depth=2, seed=13)
     return s, job
 
 

@@ -1,0 +1,293 @@
+"""Closed-form pins of the oracle's light transport: next-event estimation with multiple
+importance sampling, smooth-dielectric transmission with its radiance scaling, and the
+frame rotations of the Fresnel and GGX pBRDF operators.
+
+Each check compares the FP64 oracle with a result that radiometry and optics fix, not
+with the oracle's own formulas:
+  * a Lambertian floor lit by two one-sided parallelogram lights: the pixel equals
+    (albedo / pi) * sum_l L_l * Phi_l, where Phi_l is the cosine-weighted solid angle of
+    light l from Lambert's polygon formula (itself checked against quadrature).  The
+    estimator of Eq. 2 with NEE + power-heuristic MIS and the BSDF-sampling-only estimator
+    (the same quads as emitting surfaces) must both reach it within a Monte Carlo bound;
+  * one smooth interface seen from either side: every transmitted path carries exactly
+    L (eta_cam / eta_light)^2 (radiance scales with the squared index of the medium it
+    enters) and the s/p split of the textbook transmittances T_s = 1 - |r_s|^2,
+    T_p = 1 - |r_p|^2; a glass slab carries the product of two such transmissions;
+  * specular reflection of polarized light: every reflected path of a smooth dielectric
+    carries M(r_s, r_p) Le / F exactly, and rough GGX lobes (conductor, and a rough
+    dielectric at Brewster's angle) approach the same Mueller matrix as the roughness
+    goes to 0.01 -- with the light's Stokes vector given in a frame that shares its x
+    axis with the s axis, so that every frame rotation on the way must cancel.
+
+test_planted_mistake_is_caught builds copies of oracle.cpp with one line changed (a
+dropped term, a swapped operand, an inverted rotation or factor, a wrong sign) and
+requires the check named for each to fail on it.
+"""
+import concurrent.futures
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2607_13265_gb300 import scenegen as sg
+
+ORACLE_CPP = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "oracle.cpp")
+
+
+# ---------------------------------------------------------------- textbook optics
+def polygon_phi(x, n, corners) -> float:
+    """Cosine-weighted solid angle int cos(theta) dw of a planar polygon seen from x with
+    normal n (Lambert's formula: half the sum over edges of the edge's angle times the
+    normal's component along the edge plane's normal); the polygon must lie above x's
+    horizon.  Irradiance from a uniform Lambertian emitter of radiance L is L * Phi."""
+    u = [(np.asarray(c, float) - x) / np.linalg.norm(np.asarray(c, float) - x) for c in corners]
+    tot = 0.0
+    for i in range(len(u)):
+        a, b = u[i], u[(i + 1) % len(u)]
+        cr = np.cross(a, b)
+        tot += math.acos(float(np.clip(a @ b, -1.0, 1.0))) * float(n @ cr) / float(np.linalg.norm(cr))
+    return abs(tot) / 2.0
+
+
+def fresnel_rs_rp(cos_i: float, n1: float, n2: complex):
+    """Fresnel amplitude coefficients (Born & Wolf) from index n1 into n2 (complex for a
+    conductor), principal root for the refracted cosine."""
+    cos_t = np.sqrt(1.0 - (n1 / n2) ** 2 * (1.0 - cos_i * cos_i) + 0j)
+    rs = (n1 * cos_i - n2 * cos_t) / (n1 * cos_i + n2 * cos_t)
+    rp = (n2 * cos_i - n1 * cos_t) / (n2 * cos_i + n1 * cos_t)
+    return complex(rs), complex(rp)
+
+
+def reflection_mueller(rs: complex, rp: complex) -> np.ndarray:
+    """Mueller matrix of a reflection in the s/p frames: A, B from |r_s|^2, |r_p|^2 and
+    C + iS = r_s conj(r_p), in the block form the method's frames are stated with."""
+    A = (abs(rs) ** 2 + abs(rp) ** 2) / 2
+    B = (abs(rs) ** 2 - abs(rp) ** 2) / 2
+    z = rs * np.conj(rp)
+    return np.array([[A, B, 0, 0], [B, A, 0, 0], [0, 0, z.real, z.imag], [0, 0, -z.imag, z.real]])
+
+
+def test_lambert_polygon_formula_matches_quadrature():
+    """The closed form used below against a midpoint quadrature of cos cos / r^2 dA."""
+    x, n = np.zeros(3), np.array([0.0, 1.0, 0.0])
+    for o, e1, e2 in sg.LIGHT_QUADS:
+        o, e1, e2 = (np.asarray(v, float) for v in (o, e1, e2))
+        N = 400
+        s = (np.arange(N) + 0.5) / N
+        area = np.linalg.norm(np.cross(e1, e2))
+        nl = np.cross(e1, e2) / area
+        P = o + s[:, None, None] * e1 + s[None, :, None] * e2
+        d = x - P
+        r2 = (d * d).sum(-1)
+        quad = float(((d @ nl) * (-(d @ n)) / r2 ** 2).mean() * area)
+        assert polygon_phi(x, n, [o, o + e1, o + e1 + e2, o + e2]) == pytest.approx(quad, rel=1e-6)
+
+
+# ---------------------------------------------------------------- checks (raise AssertionError)
+def check_nee_mis(make, surface_emission=False):
+    """Direct light on a Lambertian floor from two one-sided parallelogram lights: NEE with
+    the power heuristic (or, with surface_emission, BSDF sampling alone) against
+    (a / pi) sum_l L_l Phi_l, 5 standard errors of the path mean (10^6 paths) plus 0.02% for
+    the camera's footprint."""
+    albedo, le = np.array([0.6, 0.5, 0.4]), (5.0, 3.0)
+    s, job = sg.polygon_light_scene(tuple(albedo), le, surface_emission=surface_emission,
+                                    spp=262144)
+    _, paths, _ = make(s).render(job, s.params(), paths=True)
+    x, n = np.zeros(3), np.array([0.0, 1.0, 0.0])
+    E = 0.0
+    for (o, e1, e2), L in zip(sg.LIGHT_QUADS, le):
+        o, e1, e2 = (np.asarray(v, float) for v in (o, e1, e2))
+        E += L * polygon_phi(x, n, [o, o + e1, o + e1 + e2, o + e2])
+    expect = albedo / math.pi * E
+    s0 = paths[:, :, 0]
+    mean, sem = s0.mean(0), s0.std(0) / math.sqrt(s0.shape[0])
+    assert np.all(np.abs(mean - expect) <= 5 * sem + 2e-4 * expect), (mean, expect, sem)
+    assert np.all(paths[:, :, 1:] == 0.0)
+
+
+def check_transmission(make, camera_inside, theta=35.0, ior=1.5, L=1.3):
+    """One smooth interface between the camera and an unpolarized light: every transmitted
+    path carries s0 = L (eta_cam / eta_light)^2 and s1 / s0 = (T_s - T_p) / (T_s + T_p) with
+    x along s (s2 = s3 = 0); the transmitted fraction is the unpolarized transmittance."""
+    s, job = sg.glass_interface_scene(ior, theta, camera_inside=camera_inside, le=L, spp=4096)
+    _, paths, _ = make(s).render(job, s.params(), paths=True)
+    n_cam, n_light = (ior, 1.0) if camera_inside else (1.0, ior)
+    rs, rp = fresnel_rs_rp(math.cos(math.radians(theta)), n_cam, n_light)
+    Ts, Tp = 1 - abs(rs) ** 2, 1 - abs(rp) ** 2
+    v = paths[:, 0]
+    hit = v[:, 0] != 0.0
+    assert np.allclose(v[hit, 0], L * (n_cam / n_light) ** 2, rtol=1e-9)
+    # the 0.01 deg field of view spreads the incidence angle by ~1e-4 rad
+    assert np.allclose(v[hit, 1] / v[hit, 0], (Ts - Tp) / (Ts + Tp), atol=1e-4)
+    assert np.allclose(v[hit, 2:], 0.0, atol=1e-4 * L)
+    T = (Ts + Tp) / 2
+    assert abs(hit.mean() - T) <= 5 * math.sqrt(T * (1 - T) / hit.size)
+
+
+def check_slab(make, theta=40.0, ior=1.5, L=1.0):
+    """A glass slab (two parallel interfaces) in front of an unpolarized light: the
+    (eta)^2 factors of entering and leaving cancel, and each path transmitted twice
+    carries the product of the two transmissions over the two unpolarized sampling
+    probabilities: s0 = L (1 + b^2), s1 = 2 L b with b = (T_s - T_p) / (T_s + T_p)."""
+    s, job = sg.glass_interface_scene(ior, theta, slab=0.2, le=L, spp=4096)
+    _, paths, _ = make(s).render(job, s.params(), paths=True)
+    rs, rp = fresnel_rs_rp(math.cos(math.radians(theta)), 1.0, ior)
+    Ts, Tp = 1 - abs(rs) ** 2, 1 - abs(rp) ** 2
+    b = (Ts - Tp) / (Ts + Tp)
+    v = paths[:, 0]
+    hit = v[:, 0] != 0.0
+    assert np.allclose(v[hit, 0], L * (1 + b * b), atol=1e-5 * L)
+    assert np.allclose(v[hit, 1], 2 * L * b, atol=1e-4 * L)
+    T = (Ts + Tp) / 2
+    assert abs(hit.mean() - T * T) <= 5 * math.sqrt(T * T * (1 - T * T) / hit.size)
+
+
+LE_POL = np.array([1.0, 0.3, 0.5, 0.2])
+
+
+def check_smooth_reflection(make, theta=40.0, ior=1.5):
+    """Polarized light reflected by a smooth dielectric: every reflected path carries
+    M(r_s, r_p) Le / F with F = (|r_s|^2 + |r_p|^2) / 2, the light's x axis being the s axis."""
+    s, job = sg.specular_limit_scene("smooth", theta, ior=ior, le=LE_POL, spp=2048)
+    _, paths, _ = make(s).render(job, s.params(), paths=True)
+    M = reflection_mueller(*fresnel_rs_rp(math.cos(math.radians(theta)), 1.0, ior))
+    v = paths[:, 0]
+    hit = v[:, 0] != 0.0
+    assert hit.sum() > 20
+    assert np.allclose(v[hit], (M @ LE_POL) / M[0, 0], atol=1e-3)
+
+
+def check_rough_limit(make, kind, theta, light_size=8.0, s0_tol=0.05):
+    """A GGX lobe of roughness 0.01 reflects polarized light as its smooth limit does: the
+    pixel's Stokes ratios s_k / s0 match (M Le)_k / (M Le)_0 to 0.02 (M the reflection
+    Mueller matrix at the mirror angle), and with a light covering the lobe s0 matches
+    (M Le)_0 to s0_tol.  A small light (light_size 0.4 at distance 10) leaves a large part
+    of the estimate to next-event estimation."""
+    s, job = sg.specular_limit_scene(kind, theta, roughness=0.01, le=LE_POL, spp=16384, light_size=light_size)
+    img = make(s).render(job, s.params())[0]
+    n2 = complex(0.2, 3.0) if kind == "conductor" else 1.5
+    ref = reflection_mueller(*fresnel_rs_rp(math.cos(math.radians(theta)), 1.0, n2)) @ LE_POL
+    px = img[:, 0, :].mean(0)
+    assert px[0] > 0
+    assert np.allclose(px / px[0], ref / ref[0], atol=0.02), (px / px[0], ref / ref[0])
+    if s0_tol is not None:
+        assert px[0] == pytest.approx(ref[0], rel=s0_tol), (px[0], ref[0])
+
+
+def _real(oracle_mod):
+    return lambda s: oracle_mod.OracleScene(s)
+
+
+def test_nee_mis_matches_polygon_irradiance(oracle_mod):
+    check_nee_mis(_real(oracle_mod))
+
+
+def test_bsdf_sampling_matches_polygon_irradiance(oracle_mod):
+    check_nee_mis(_real(oracle_mod), surface_emission=True)
+
+
+@pytest.mark.parametrize("inside", [False, True])
+def test_transmission_radiance_and_polarization(oracle_mod, inside):
+    check_transmission(_real(oracle_mod), inside)
+
+
+def test_glass_slab(oracle_mod):
+    check_slab(_real(oracle_mod))
+
+
+def test_smooth_reflection_of_polarized_light(oracle_mod):
+    check_smooth_reflection(_real(oracle_mod))
+
+
+@pytest.mark.parametrize("kind,theta,size", [("conductor", 50.0, 8.0), ("conductor", 50.0, 0.4),
+                                             ("plastic", math.degrees(math.atan(1.5)), 8.0)])
+def test_rough_lobe_specular_limit(oracle_mod, kind, theta, size):
+    check_rough_limit(_real(oracle_mod), kind, theta, light_size=size, s0_tol=0.05 if size > 1 else None)
+
+
+def test_rough_dielectric_at_brewster_is_s_polarized(oracle_mod):
+    """Brewster's angle with the specular lobe alone: whatever the light's polarization,
+    the reflected light is polarized along s (s1 = s0), as for a smooth interface."""
+    s, job = sg.specular_limit_scene("plastic", math.degrees(math.atan(1.5)), roughness=0.01, le=LE_POL,
+                                     spp=16384)
+    px = oracle_mod.OracleScene(s).render(job, s.params())[0][:, 0, :].mean(0)
+    assert px[1] / px[0] == pytest.approx(1.0, abs=2e-3)
+    assert abs(px[2]) < 2e-3 * px[0] and abs(px[3]) < 2e-3 * px[0]
+
+
+# ---------------------------------------------------------------- planted mistakes
+# (name, text in oracle.cpp, replacement, which occurrence, the check that must catch it)
+_NEE = lambda m: check_nee_mis(m)
+MUTANTS = [
+    ("emit_pdf_drops_light_count", "double pl = dist2 / (cl * L.area * nL);", "double pl = dist2 / (cl * L.area);", 0, _NEE),
+    ("nee_pdf_drops_light_count", "double pl = dist2 / (cl * L.area * nL);", "double pl = dist2 / (cl * L.area);", 1, _NEE),
+    ("nee_pdf_cosine_at_receiver", "double pl = dist2 / (cl * L.area * nL);", "double pl = dist2 / (cx * L.area * nL);", 1, _NEE),
+    ("nee_mis_weight_swapped", "double wmis = pl * pl / (pl * pl + pb * pb);", "double wmis = pb * pb / (pl * pl + pb * pb);", 0, _NEE),
+    ("emit_mis_weight_swapped", "vt.w_emit = prev_pdf * prev_pdf / (prev_pdf * prev_pdf + pl * pl);",
+     "vt.w_emit = pl * pl / (prev_pdf * prev_pdf + pl * pl);", 0, _NEE),
+    ("nee_cosine_dropped", "vt.nee_w = cx / pl * wmis;", "vt.nee_w = 1.0 / pl * wmis;", 0, _NEE),
+    ("transmit_radiance_inverted", "T sc = (eo / et) * (eo / et);", "T sc = (et / eo) * (et / eo);", 0,
+     lambda m: check_transmission(m, False)),
+    ("transmit_radiance_dropped", "T sc = (eo / et) * (eo / et);", "T sc = T(1.0);", 0,
+     lambda m: check_transmission(m, True)),
+    ("transmit_split_sign", "fac * (ts * ts - tp * tp) * 0.5", "fac * (tp * tp - ts * ts) * 0.5", 0,
+     lambda m: check_transmission(m, False)),
+    ("transmit_cosine_ratio_inverted", "T fac = (eta_t * cos_t) / (eta_i * cos_i);",
+     "T fac = (eta_i * cos_i) / (eta_t * cos_t);", 0, lambda m: check_transmission(m, False)),
+    ("fresnel_phase_conjugated", "Cx<T> rsp = cmul(rs, Cx<T>{rp.re, -rp.im});",
+     "Cx<T> rsp = cmul(Cx<T>{rs.re, -rs.im}, rp);", 0, lambda m: check_rough_limit(m, "conductor", 50.0)),
+    ("ggx_rin_inverted", "M4<double> Rin = rot_fixed(-wi, onb_t1(-wi), sax);",
+     "M4<double> Rin = rot_fixed(-wi, sax, onb_t1(-wi));", 0, lambda m: check_rough_limit(m, "conductor", 50.0)),
+    ("ggx_rin_reversed_propagation", "M4<double> Rin = rot_fixed(-wi, onb_t1(-wi), sax);",
+     "M4<double> Rin = rot_fixed(wi, onb_t1(wi), sax);", 0, lambda m: check_rough_limit(m, "conductor", 50.0)),
+    ("ggx_rout_inverted", "M4<double> Rout = rot_fixed(vt.wo, sax, onb_t1(vt.wo));",
+     "M4<double> Rout = rot_fixed(vt.wo, onb_t1(vt.wo), sax);", 0,
+     lambda m: check_rough_limit(m, "plastic", math.degrees(math.atan(1.5)))),
+    ("smooth_rin_inverted", "M4<double> Rin = rot_fixed(-wi, onb_t1(-wi), sax);",
+     "M4<double> Rin = rot_fixed(-wi, sax, onb_t1(-wi));", 1, lambda m: check_smooth_reflection(m)),
+    ("smooth_rout_inverted", "M4<double> Rout = rot_fixed(vt.wo, sax, onb_t1(vt.wo));",
+     "M4<double> Rout = rot_fixed(vt.wo, onb_t1(vt.wo), sax);", 1, lambda m: check_smooth_reflection(m)),
+    ("emitter_frame_reversed_for_hits", "M4<double> R = emitter_rot(L, vt.wo);", "M4<double> R = emitter_rot(L, -vt.wo);",
+     0, lambda m: check_smooth_reflection(m)),
+    ("emitter_frame_reversed_for_nee", "M4<double> R = emitter_rot(L, -vt.wl);", "M4<double> R = emitter_rot(L, vt.wl);",
+     0, lambda m: check_rough_limit(m, "conductor", 50.0, light_size=0.4, s0_tol=None)),
+]
+
+
+def _replace_nth(text: str, old: str, new: str, k: int) -> str:
+    pos = -1
+    for _ in range(k + 1):
+        pos = text.index(old, pos + 1)
+    return text[:pos] + new + text[pos + len(old):]
+
+
+@pytest.fixture(scope="module")
+def mutant_libs(tmp_path_factory, oracle_mod):
+    src = open(ORACLE_CPP).read()
+    out = tmp_path_factory.mktemp("oracle_mutants")
+    jobs = {}
+    for name, old, new, k, _ in MUTANTS:
+        assert src.count(old) > k, f"{name}: the oracle no longer contains {old!r}"
+        cpp = out / f"{name}.cpp"
+        cpp.write_text(_replace_nth(src, old, new, k))
+        jobs[name] = (cpp, out / f"{name}.so")
+
+    def compile_one(item):
+        cpp, so = item
+        subprocess.check_call(["g++", "-std=c++17", "-O1", "-shared", "-fPIC", "-o", str(so), str(cpp)])
+        return str(so)
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        built = dict(zip(jobs, ex.map(compile_one, jobs.values())))
+    return {name: oracle_mod.load(path) for name, path in built.items()}
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(oracle_mod, mutant_libs, name):
+    check = {m[0]: m[4] for m in MUTANTS}[name]
+    check(_real(oracle_mod))                      # the unmodified oracle passes the check
+    library = mutant_libs[name]
+    with pytest.raises(AssertionError):
+        check(lambda s: oracle_mod.OracleScene(s, library=library))

@@ -5,10 +5,13 @@ N and B = N x T) and of its texel derivatives.
 * A flat map (n_t = (0, 0, 1) everywhere) reproduces the renderer without normal maps,
   path by path (paths that part by a rounding-level near-edge hit are excluded).
 * The cached suffix replay equals the tape on the normal maps' texel gradients.
-* The texel gradients equal central differences of the frozen-sampling estimator."""
+* The texel gradients equal central differences of the frozen-sampling estimator, and so
+  do the normal-mapped materials' own albedo, roughness and index-of-refraction
+  gradients."""
 import copy
 
 import numpy as np
+import pytest
 
 from paper_2607_13265_gb300 import scenegen as sg
 
@@ -64,3 +67,26 @@ def test_normal_map_gradient_matches_central_differences(oracle_mod):
             return float((dI * o.render(aj, P, params_live=live)).sum())
         fd = (J(h) - J(-h)) / (2 * h)
         assert abs(g[t] - fd) <= 1e-6 * abs(fd), (t, g[t], fd)
+
+
+def test_normal_mapped_material_parameters_match_central_differences(oracle_mod):
+    """On normal-mapped materials the albedo and roughness texels and the index of refraction
+    are differentiated too: both routes against central differences."""
+    s, o, P, aj, dI = _setup(oracle_mod)
+    gt = o.gradient(aj, P, dI, mode="tape")
+    gr = o.gradient(aj, P, dI, mode="replay")
+    (r_off, rw, rh, _), (a_off, aw, ah, ac) = s.tex_desc[3], s.tex_desc[4]
+    checks = [("ior", 0)]
+    for off, n in ((r_off, rw * rh), (a_off, aw * ah * ac)):
+        block = np.abs(gt["tex"][off:off + n])
+        checks += [("tex", int(off + k)) for k in np.argsort(-block)[:3]]
+    h = 1e-5
+    for name, t in checks:
+        def J(d):
+            live = {k: np.array(v, dtype=np.float64, copy=True) for k, v in P.items()}
+            live[name].reshape(-1)[t] += d
+            return float((dI * o.render(aj, P, params_live=live)).sum())
+        fd = (J(h) - J(-h)) / (2 * h)
+        assert gt[name][t] != 0.0, (name, t)
+        assert abs(gt[name][t] - fd) <= 1e-6 * max(1.0, abs(fd)), (name, t, gt[name][t], fd)
+        assert gr[name][t] == pytest.approx(gt[name][t], rel=1e-10, abs=1e-12)
