@@ -82,8 +82,9 @@ typedef struct {
                               types on triangles with UVs only.  Shading normal: normalize(n.x T +
                               n.y B + n.z N), N the geometric normal facing the viewer, T the
                               triangle's dP/du made normal to N, B = N x T.  Its texels are
-                              differentiated; the material's albedo, roughness and index of
-                              refraction then are not (their dual-number slots carry n). */
+                              differentiated, and so are the material's own albedo, roughness
+                              and index of refraction (the replay evaluates a normal-mapped
+                              vertex twice, once per set of three dual-number slots). */
     float eta_re, eta_im;  /* conductor complex index of refraction (constant) */
     float t1[3], t2[3];    /* sheet axis basis: axis = cos(a) t1 + sin(a) t2 */
     float retard;          /* retarder sheet retardance (radians) */
@@ -302,16 +303,22 @@ dppt_status dppt_count_work(dppt_ctx* ctx, const dppt_scene* scene, const dppt_j
  * dppt_render_primal for callers that must not let the library allocate
  * device memory (device memory owned by another allocator or under a fixed
  * budget, loops that must not block in cudaMalloc, work issued while a stream
- * is captured).  Renders ONE job exactly like dppt_render_primal, but a job
- * with a camera filter keeps its raw (unfiltered) image in a fixed 12 MiB
- * device array compiled into the library instead of the context workspace;
- * every GPU that loads the library holds that array until the process exits.
- * Limit: width * height <= 262144 pixels (e.g. 512 x 512); larger jobs get
- * DPPT_ERR_INVALID_ARG.  The first call on a device resolves the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls on a device share the array, which keeps the
- * last call's contents: calls that overlap on the GPU (for instance on two
- * streams) race on it.  Calls no cudaMalloc or cudaFree. */
+ * is captured).  Renders ONE job with the same paths as dppt_render_primal,
+ * always with the grid megakernel at 128-thread blocks whatever launch shape
+ * the context holds (its image equals dppt_render_primal's to rounding; under
+ * another schedule the two sum the paths in another order), and its launches
+ * are not counted by dppt_stage_stats.  A job with a camera filter keeps its
+ * raw (unfiltered) image in a fixed 12 MiB device array compiled into the
+ * library instead of the context workspace; every GPU that loads the library
+ * holds that array until the process exits.  Limit: width * height <= 262144
+ * pixels (e.g. 512 x 512); larger jobs get DPPT_ERR_INVALID_ARG.  Every call
+ * made outside stream capture resolves the array's device address
+ * (cudaGetSymbolAddress) again; a call made while `stream` is being captured
+ * reuses the address of the device's last call outside capture, so make one
+ * call outside capture first (otherwise DPPT_ERR_CUDA).  All calls on a device
+ * share the array, which keeps the last call's contents: calls that overlap on
+ * the GPU (for instance on two streams) race on it.  Calls no cudaMalloc or
+ * cudaFree. */
 dppt_status dppt_render_primal_noalloc(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* job,
                                        const dppt_params* params, float* image, void* stream);
 

@@ -220,10 +220,14 @@ template <class T> __device__ __forceinline__ ABCS<T> fresnel_transmit(float cos
 
 // ------------------------------------------------------------------ GGX (Walter et al. 2007)
 // the cosines with the shading normal carry derivatives under a normal map: type C
-template <class T, class C = float> __device__ __forceinline__ T ggx_D(C cos_h, T alpha) {
+// GGX normal distribution D(h) = a^2 / (pi k^2), k = (a^2 - 1) cos^2 + 1 = sin^2 + a^2 cos^2
+// (Walter et al. 2007).  The caller passes sin^2 of the half vector's angle to the normal as
+// |n x h|^2: near the lobe's peak 1 - cos^2 would cancel in FP32 (for a = 0.01 the peak's k
+// is ~1e-4, and cos_h carries a rounding error of ~1e-7).
+template <class T, class C = float> __device__ __forceinline__ T ggx_D(C cos_h, C sin2_h, T alpha) {
     if (val(cos_h) <= 0.0f) return T(0.0f);
     T a2 = alpha * alpha;
-    T k = (a2 - 1.0f) * (cos_h * cos_h) + 1.0f;
+    T k = a2 * (cos_h * cos_h) + sin2_h;
     return a2 / (k * k * kPi);
 }
 template <class T, class C = float> __device__ __forceinline__ T ggx_G1(C cos_v, float cos_vh, T alpha) {

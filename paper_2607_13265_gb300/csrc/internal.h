@@ -140,6 +140,7 @@ struct StageLog {
             cudaEventSynchronize(r.b);
             float t = 0.0f;
             if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.stage] += t;
+            else cudaGetLastError();   // a failed query must not surface as the next launch's error
             spare.push_back(r.a);
             spare.push_back(r.b);
         }

@@ -363,7 +363,8 @@ __device__ __forceinline__ float ggx_pdf(float alpha, f3 n, f3 wo, f3 wi) {
     f3 h = normalize(wo + wi);
     float ch = dot(h, n), oh = dot(wo, h);
     if (ch <= 0.0f || oh <= 0.0f) return 0.0f;
-    return ggx_D<float>(ch, alpha) * ch / (4.0f * oh);
+    const f3 nh = cross(n, h);
+    return ggx_D<float>(ch, dot(nh, nh), alpha) * ch / (4.0f * oh);
 }
 // Roughness, albedo (tint) and the rough dielectric's specular-lobe probability at the
 // vertex: looked up once and reused by sampling, pdfs and the Mueller evaluation.
@@ -525,12 +526,19 @@ __device__ __forceinline__ void bsdf_compact(const DScene& S, const DParams& P, 
         return;
     }
     f3 h = normalize(vc.wo + wi);
-    C ch;
-    if constexpr (NM) ch = nT[0] * h.x + nT[1] * h.y + nT[2] * h.z;
-    else ch = dot(h, vc.n);
+    C ch, sh2;   // cosine and squared sine (|n x h|^2) of the half vector's angle to the normal
+    if constexpr (NM) {
+        ch = nT[0] * h.x + nT[1] * h.y + nT[2] * h.z;
+        const C cx = nT[1] * h.z - nT[2] * h.y, cy = nT[2] * h.x - nT[0] * h.z, cz = nT[0] * h.y - nT[1] * h.x;
+        sh2 = cx * cx + cy * cy + cz * cz;
+    } else {
+        ch = dot(h, vc.n);
+        const f3 nh = cross(vc.n, h);
+        sh2 = dot(nh, nh);
+    }
     const float oh = dot(vc.wo, h), ih = dot(wi, h);
     T al = seeded<T>(vc.alpha, NM ? -1 : 0);
-    T k = ggx_D<T, C>(ch, al) * ggx_G1<T, C>(co, oh, al) * ggx_G1<T, C>(ci, ih, al) / (co * ci * 4.0f);
+    T k = ggx_D<T, C>(ch, sh2, al) * ggx_G1<T, C>(co, oh, al) * ggx_G1<T, C>(ci, ih, al) / (co * ci * 4.0f);
     ABCS<T> F;
     if (m.type == DPPT_MAT_CONDUCTOR_GGX) {
         ABCS<float> Ff = fresnel_reflect<float>(ih, 1.0f, Cx<float>{m.eta_re, m.eta_im});
@@ -571,8 +579,12 @@ __device__ __forceinline__ DMat load_mat(const DScene& S, int mat) {
 }
 
 // E_v (per channel, float) and W_v (compact, T) for one vertex.  NM = false compiles the
-// normal-map path out (kernels launched for scenes without normal maps).
-template <class T, int MT = -1, bool NM = true>
+// normal-map path out (kernels launched for scenes without normal maps).  With dual numbers
+// the three slots carry the material's own parameters (roughness or sheet angle, index of
+// refraction, channel albedo) and the shading normal is a constant; NSLOTS instead makes
+// them the components of a normal-mapped vertex's map value n, the material's parameters
+// then being constants (replay_vjp runs both evaluations at such a vertex).
+template <class T, int MT = -1, bool NM = true, bool NSLOTS = false>
 __device__ void eval_vertex(const DScene& S, const DParams& P, const VCtx& vc, float E[3][4], Compact<T>& W,
                             Compact<T>* fnee) {
     const DMat m = load_mat<MT>(S, vc.mat);
@@ -589,17 +601,17 @@ __device__ void eval_vertex(const DScene& S, const DParams& P, const VCtx& vc, f
     }
     if (m.emission > 0.0f)
         for (int c = 0; c < 3; ++c) E[c][0] += m.emission;
-    // a normal map's shading normal with derivatives (dual numbers only: detached values
-    // are already in vc.n)
+    // a normal map's shading normal with derivatives (the normal-slot evaluation only:
+    // detached values are already in vc.n)
     T nT[3];
     bool nm = false;
-    if constexpr (NM && sizeof(T) != sizeof(float))
+    if constexpr (NM && NSLOTS && sizeof(T) != sizeof(float))
         if (m.normal_tex >= 0) nm = shading_normal<T>(S, P, m, vc, nT);
     if (vc.nee) {
         DLight L = load_light(S, vc.nee_light);
         Rot<float> R = emitter_rot(L, -vc.wl);
         Compact<T> f;
-        if constexpr (NM) {
+        if constexpr (NM && NSLOTS) {
             if (nm) {
                 // nee_w holds the cosine with the detached shading normal: the live one replaces it
                 bsdf_compact<T, true>(S, P, m, vc, vc.wl, f, nT);
@@ -627,7 +639,7 @@ __device__ void eval_vertex(const DScene& S, const DParams& P, const VCtx& vc, f
     if (!vc.scatter) return;
     f3 wi = vc.wi;
     if (m.type == DPPT_MAT_DIFFUSE || m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX) {
-        if constexpr (NM) {
+        if constexpr (NM && NSLOTS) {
             if (nm) {
                 bsdf_compact<T, true>(S, P, m, vc, wi, W, nT);
                 compact_scale(W, (nT[0] * wi.x + nT[1] * wi.y + nT[2] * wi.z) * (1.0f / vc.pdf));
@@ -827,7 +839,7 @@ __device__ __forceinline__ void walk_shade(const DScene& S, const DParams& P, co
             const float al = vc.alpha;
             float tan2 = al * al * U.u[1] / (1.0f - U.u[1]);
             float ch = 1.0f / sqrtf(1.0f + tan2);
-            float shv = sqrtf(fmaxf(0.0f, 1.0f - ch * ch));
+            float shv = sqrtf(tan2) * ch;     // sin = tan cos: no cancellation near the normal
             float sph, cph;
             sincosf(2.0f * kPi * U.u[2], &sph, &cph);
             f3 hv = t1 * (shv * cph) + t2 * (shv * sph) + vc.n * ch;
@@ -903,7 +915,7 @@ __device__ __forceinline__ bool walk_finish(const DScene& S, const DParams& P, W
 
 // Traces vertex w.v of the path and calls vis(vc) for it.  Returns true when
 // the path continues with vertex w.v + 1.
-template <class Vis, bool COUNT>
+template <class Vis, bool COUNT, bool NM = true>
 __device__ __forceinline__ bool walk_step(const DScene& S, const DParams& P, const DJob& J, unsigned long long pid,
                                           Walk& w, Vis& vis, unsigned* status, WorkCount* wc) {
     HitRec h;
@@ -912,7 +924,7 @@ __device__ __forceinline__ bool walk_step(const DScene& S, const DParams& P, con
     VCtx vc;
     NeePending ne;
     Shade sh;
-    walk_shade(S, P, J, pid, w, h, vc, ne, sh);
+    walk_shade<NM>(S, P, J, pid, w, h, vc, ne, sh);
     bool visible = false;
     if (ne.state == 1) visible = !trace_any<COUNT>(S, ne.o2, ne.dir, ne.tmax, status, wc);
     return walk_finish(S, P, w, vc, ne, visible, sh, vis);
@@ -1101,9 +1113,59 @@ struct GlobalCache {
     }
 };
 
-// The replayed vertex's local vector-Jacobian product: J_c = a_c^T (E_c + W_c L_c) with
-// dual numbers (W and the NEE operator f from eval_vertex<D3>, Ln the suffix L[v+1]),
-// scattered into the gradients; then the adjoint row advances, a^T <- a^T W_v.
+// Local vector-Jacobian products of one dual-number evaluation of a replayed vertex:
+// per channel J_c = a_c^T (W_c L_c + f_c Le_c nee_w) (W and the NEE operator f from
+// eval_vertex<D3>, Ln the suffix L[v+1]); returns the three slots' derivatives, the third
+// per channel.
+__device__ __forceinline__ void local_vjp(const DScene& S, const DParams& P, const VCtx& vc, const Compact<D3>& W,
+                                          const Compact<D3>& f, const Rot<float>& Rle, const float Ln[3][4],
+                                          const float a[3][4], float& g0, float& g1, float g2[3]) {
+    g0 = g1 = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        D3 x[4] = {D3(Ln[c][0]), D3(Ln[c][1]), D3(Ln[c][2]), D3(Ln[c][3])};
+        D3 y[4];
+        compact_apply(W, c, x, y);
+        D3 J = y[0] * a[c][0] + y[1] * a[c][1] + y[2] * a[c][2] + y[3] * a[c][3];
+        if (vc.nee) {
+            const float* le = P.le + 12 * vc.nee_light + 4 * c;
+            float lv[4] = {__ldg(le), __ldg(le + 1), __ldg(le + 2), __ldg(le + 3)};
+            rot_apply(Rle, lv);
+            D3 xe[4] = {D3(lv[0] * vc.nee_w), D3(lv[1] * vc.nee_w), D3(lv[2] * vc.nee_w), D3(lv[3] * vc.nee_w)};
+            D3 ye[4];
+            compact_apply(f, c, xe, ye);
+            J = J + ye[0] * a[c][0] + ye[1] * a[c][1] + ye[2] * a[c][2] + ye[3] * a[c][3];
+        }
+        g0 += J.d0;
+        g1 += J.d1;
+        g2[c] = J.d2;
+    }
+}
+
+// The normal map's texel derivatives at a normal-mapped replayed vertex: a second dual
+// evaluation whose slots carry the three components of n = 2 c - 1.  Not inlined: it runs
+// at normal-mapped vertices only and would otherwise raise the register pressure of every
+// replay kernel that may meet one.
+template <int MT>
+__device__ __noinline__ void normal_map_vjp(const DScene& S, const DParams& P, const DGrads& G, const VCtx& vc,
+                                            const Rot<float> Rle, const float Ln[3][4], const float a[3][4]) {
+    const DMat m = load_mat<MT>(S, vc.mat);
+    f3 nN, nT, nB;
+    if (!nmap_frame(S, m, vc, nN, nT, nB)) return;
+    float En[3][4];
+    Compact<D3> Wn, fn;
+    eval_vertex<D3, MT, true, true>(S, P, vc, En, Wn, &fn);
+    float h0, h1, h2[3];
+    local_vjp(S, P, vc, Wn, fn, Rle, Ln, a, h0, h1, h2);
+    const Taps tp = tex_taps(S.tex[m.normal_tex], vc.tu, vc.tv);
+    const float gn[3] = {2.0f * h0, 2.0f * h1, 2.0f * (h2[0] + h2[1] + h2[2])};
+    scatter_taps<3, false>(G.tex, tp, gn, 3, S.scatter_lane != 0);
+}
+
+// The replayed vertex's local vector-Jacobian product, scattered into the gradients, then
+// the adjoint row's advance a^T <- a^T W_v.  W and f come from eval_vertex<D3> with the
+// material's own slots.  At a normal-mapped vertex a second evaluation, whose slots carry
+// the map value n, gives the normal map's texel derivatives.
 template <int MT = -1, bool NM = true, bool UNROLL = true>
 __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, const DGrads& G_, float* sgrad,
                                            const VCtx& vc, const Compact<D3>& W, const Compact<D3>& f,
@@ -1112,36 +1174,17 @@ __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, 
     const DParams* P = &P_;
     const DGrads* G = &G_;
     const DMat m = load_mat<MT>(S_, vc.mat);
-    // local vector-Jacobian products: J_c = a_c^T (E_c + W_c L_c) with dual numbers
-    float g_slot0 = 0.0f, g_eta = 0.0f, g_alb[3];
-    Compact<float> fv;
-    if (vc.nee) fv = compact_value(f);
     Rot<float> Rle = {1.0f, 0.0f};
     if (vc.nee) Rle = emitter_rot(load_light(*S, vc.nee_light), -vc.wl);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        D3 x[4] = {D3(Ln[c][0]), D3(Ln[c][1]), D3(Ln[c][2]), D3(Ln[c][3])};
-        D3 y[4];
-        compact_apply(W, c, x, y);
-        D3 J = y[0] * a[c][0] + y[1] * a[c][1] + y[2] * a[c][2] + y[3] * a[c][3];
-        if (vc.nee) {
-            const float* le = P->le + 12 * vc.nee_light + 4 * c;
-            float lv[4] = {__ldg(le), __ldg(le + 1), __ldg(le + 2), __ldg(le + 3)};
-            rot_apply(Rle, lv);
-            D3 xe[4] = {D3(lv[0] * vc.nee_w), D3(lv[1] * vc.nee_w), D3(lv[2] * vc.nee_w), D3(lv[3] * vc.nee_w)};
-            D3 ye[4];
-            compact_apply(f, c, xe, ye);
-            J = J + ye[0] * a[c][0] + ye[1] * a[c][1] + ye[2] * a[c][2] + ye[3] * a[c][3];
-        }
-        g_slot0 += J.d0;
-        g_eta += J.d1;
-        g_alb[c] = J.d2;
-    }
+    float g_slot0, g_eta, g_alb[3];
+    local_vjp(S_, P_, vc, W, f, Rle, Ln, a, g_slot0, g_eta, g_alb);
     // emitter Stokes gradients (linear): w R^T a for a hit, nee_w R^T f^T a for NEE
     if (vc.emit || vc.nee) {
         const int base = S->num_ior + S->num_sheets;
         Rot<float> Re = {1.0f, 0.0f};
         if (vc.emit) Re = emitter_rot(load_light(*S, vc.light), vc.wo);
+        Compact<float> fv;
+        if (vc.nee) fv = compact_value(f);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if (vc.emit) {
@@ -1159,23 +1202,14 @@ __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, 
             }
         }
     }
-    // parameter scatter (a normal-mapped vertex's slots belong to its normal map)
-    f3 nN, nT, nB;
-    const bool nm = NM && m.normal_tex >= 0 && nmap_frame(*S, m, vc, nN, nT, nB);
-    if (!nm && (m.type == DPPT_MAT_SMOOTH_DIELECTRIC || m.type == DPPT_MAT_PLASTIC_GGX)) {
+    // parameter scatter
+    if (m.type == DPPT_MAT_SMOOTH_DIELECTRIC || m.type == DPPT_MAT_PLASTIC_GGX) {
         if (g_eta != 0.0f) sgrad_add(*S, sgrad, m.ior_index, g_eta);
     }
     if (m.type == DPPT_MAT_POLARIZER_SHEET || m.type == DPPT_MAT_RETARDER_SHEET) {
         if (g_slot0 != 0.0f) sgrad_add(*S, sgrad, S->num_ior + m.sheet_index, g_slot0);
     }
-    if (nm) {
-        // normal map: the slots are the derivatives w.r.t. the three components of n = 2 c - 1
-        if (G->tex && S->tex[m.normal_tex].pad) {
-            const Taps tp = tex_taps(S->tex[m.normal_tex], vc.tu, vc.tv);
-            const float gn[3] = {2.0f * g_slot0, 2.0f * g_eta, 2.0f * (g_alb[0] + g_alb[1] + g_alb[2])};
-            scatter_taps<3, UNROLL>(G->tex, tp, gn, 3, S->scatter_lane != 0);
-        }
-    } else if (G->tex) {
+    if (G->tex) {
         if ((m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.rough_tex].pad) {
             Taps tp = tex_taps(S->tex[m.rough_tex], vc.tu, vc.tv);
             scatter_taps<1, UNROLL>(G->tex, tp, &g_slot0, 1, S->scatter_lane != 0);
@@ -1186,6 +1220,9 @@ __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, 
             Taps tp = tex_taps(t, vc.tu, vc.tv);
             scatter_taps<3, UNROLL>(G->tex, tp, g_alb, t.ch, S->scatter_lane != 0);
         }
+    }
+    if constexpr (NM) {
+        if (G->tex && m.normal_tex >= 0 && S->tex[m.normal_tex].pad) normal_map_vjp<MT>(S_, P_, G_, vc, Rle, Ln, a);
     }
     // advance the adjoint row through the value of W_i
     Compact<float> Wv = compact_value(W);
@@ -1313,7 +1350,10 @@ __device__ __forceinline__ void pixel_reduce(const DJob& J, float* dst, long lon
 }
 
 // ================================================================== megakernel
-template <int MAXD, int MODE, bool COUNT>
+// NM = false compiles the normal-map code out: the adjoint is launched with it only for
+// scenes that have normal maps (their second dual evaluation would otherwise raise the
+// register pressure of every adjoint).
+template <int MAXD, int MODE, bool COUNT, bool NM = true>
 __global__ void __launch_bounds__(256, MODE == 1 ? DPPT_MIN_BLOCKS_ADJOINT : DPPT_MIN_BLOCKS_PRIMAL)
 k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__ JobTable T,
         unsigned long long* counter, unsigned* status, int persistent, unsigned long long* work) {
@@ -1341,7 +1381,7 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
         for (int k = 0; k < 12; ++k) raw[k] = 0.0f;
         if (active) {
             const long long pix = p / J.spp;
-            PathVis<LocalCache<MAXD>> vis;
+            PathVis<LocalCache<MAXD>, -1, NM> vis;
             vis.S = &S; vis.P = &P; vis.G = &G; vis.sgrad = sgrad;
             vis.C.cE = cE; vis.C.cW = cW;
             vis.n = 0; vis.i = 0; vis.has_last = false; vis.adjoint = MODE == 1;
@@ -1352,7 +1392,8 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
             for (int phase = 0; phase < passes; ++phase) {
                 vis.phase = phase;
                 walk_begin(S, J, (unsigned long long)p, pix, w);
-                while (walk_step<PathVis<LocalCache<MAXD>>, COUNT>(S, P, J, (unsigned long long)p, w, vis, status, &wc)) {
+                while (walk_step<PathVis<LocalCache<MAXD>, -1, NM>, COUNT, NM>(S, P, J, (unsigned long long)p, w, vis,
+                                                                               status, &wc)) {
                 }
                 if (phase == 0) {
                     float L0[12];
@@ -1417,19 +1458,24 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
             k_trace<B, 0, false><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, nullptr);         \
         else if (mode == 1) {                                                                                    \
             size_t sm = sgrad_bytes(S);                                                                         \
-            k_trace<B, 1, false><<<(int)g, L.block, sm, st>>>(S, P, G, T, counter, status, pers, nullptr);        \
+            if (S.tri_tan)                                                                                       \
+                k_trace<B, 1, false, true><<<(int)g, L.block, sm, st>>>(S, P, G, T, counter, status, pers, nullptr); \
+            else                                                                                                 \
+                k_trace<B, 1, false, false><<<(int)g, L.block, sm, st>>>(S, P, G, T, counter, status, pers, nullptr);\
         } else                                                                                                   \
             k_trace<B, 0, true><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, work);             \
         return cudaGetLastError();                                                                               \
     }                                                                                                            \
+    /* the adjoint's attributes are those of the kernel without normal-map code (the same  */                  \
+    /* launch bounds as the one with it)                                                    */                  \
     cudaError_t trace_attributes_##B(int mode, cudaFuncAttributes* a) {                                         \
         return cudaFuncGetAttributes(a, mode == 0 ? reinterpret_cast<const void*>(&k_trace<B, 0, false>)          \
-                                                  : reinterpret_cast<const void*>(&k_trace<B, 1, false>));        \
+                                                  : reinterpret_cast<const void*>(&k_trace<B, 1, false, false>)); \
     }                                                                                                            \
     int trace_occupancy_##B(int mode, int block, size_t smem) {                                                  \
         int nb = 0;                                                                                              \
         const void* f = mode == 0 ? reinterpret_cast<const void*>(&k_trace<B, 0, false>)                          \
-                                  : reinterpret_cast<const void*>(&k_trace<B, 1, false>);                        \
+                                  : reinterpret_cast<const void*>(&k_trace<B, 1, false, false>);                 \
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, smem) != cudaSuccess) return 0;          \
         return nb;                                                                                               \
     }
