@@ -1,22 +1,37 @@
 #!/usr/bin/env python
 """Throughput benchmark of the polarized path tracer (primal + cached-suffix-replay adjoint).
 
-One step = one inverse-rendering gradient evaluation of the 50k-triangle displaced
-icosphere workload (256x256, 64 spp, depth 8, rough conductor + rough dielectric
-pBRDFs, 128^2x3 albedo and 128^2 roughness maps): render_primal (PRB phase 1), the L2
-loss adjoint dI = 2 (I - T) / N, render_adjoint (phases 2+3) into both maps.
-Metric: primal + adjoint paths per second (each step traces 2 x 4,194,304 paths).
+Headline workload (the batched views x angles gradient): the Cornell-box scene (12
+triangles + 2 spheres: diffuse walls, a diffuse and a glass sphere, a quad light) seen by 8
+cameras orbiting +-20 deg with square images of 128, 183, 238, 293, 347, 402, 457 and 512
+pixels (945,372 pixels), each behind a linear polarizer at 64 angles in [0, 180) deg; 16
+spp, depth 8; L2 loss to a seeded target (perturbed albedo, other random numbers).
+
+* One step = one gradient evaluation of the whole batch in its batched autograd form
+  (PolarizedL2: render_primal of the raw image of all views in one launch, the loss
+  folded into the camera filter, render_adjoint_l2 of all views in one call), captured
+  once in a CUDA graph and replayed; the timed region is K replays.
+* Metric: primal + adjoint paths per second, counting every (view, angle, pixel, sample)
+  path of the primal and of the adjoint -- the paths the plain form traces one call at a
+  time (2 x 968,318,976 per step); the batched form traces each view's paths once
+  (2 x 15,125,952) and folds the angles exactly.  The same line reports, measured in the
+  same run: the plain form (512 render_primal + 512 render_adjoint calls, one per view and
+  angle), the traced-path rate of both forms, and the gradient memory (peak device memory
+  of forward + backward through torch.autograd) of the batched and the plain form.
+* "icosphere": the 50k-triangle displaced icosphere (256x256, 64 spp, depth 8, rough
+  conductor + rough dielectric, 128^2x3 albedo and 128^2 roughness maps) as one eager
+  gradient step per iteration, with its stage times and the roofline of its dominant kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
-N > 1 runs under torchrun: every rank renders its own independent view stream (weak
-scaling, no data-path collective); rank 0 prints one JSON line.
+N > 1 runs under torchrun: every rank renders its own independent paths (weak scaling,
+no data-path collective); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
 import argparse
+import copy
 import json
-import math
 import multiprocessing as mp
 import os
 import statistics
@@ -29,7 +44,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "primal+adjoint paths/sec and gradient MB vs plain launch at 1e-3 grad rel-err"
 UNIT = "paths/s"
-WORKLOAD = "icosphere50k_256x256_64spp_depth8"
+VIEW_SIZES = (128, 183, 238, 293, 347, 402, 457, 512)
+NUM_VIEWS, NUM_ANGLES, VIEW_SPP, VIEW_DEPTH = 8, 64, 16, 8
+WORKLOAD = f"cornell_views{NUM_VIEWS}x{NUM_ANGLES}angles_{VIEW_SPP}spp_depth{VIEW_DEPTH}"
+ICO_WORKLOAD = "icosphere50k_256x256_64spp_depth8"
 
 # Algorithmic FP32 work per unit (flops), counted from the operations the method
 # performs: a BVH node visit tests two child boxes (12 FMA = 24 flops), a ray/triangle
@@ -55,11 +73,10 @@ B_CACHE_RAY = 100
 B_CACHE_VERTEX_PRIMAL, B_CACHE_VERTEX_ADJOINT = 420, 424
 B_CACHE_PATH_PRIMAL, B_CACHE_PATH_ADJOINT = 48, 216
 
-# DRAM traffic per launch (bytes) from one ncu capture of this workload: mean of
-# dram__bytes_read.sum + dram__bytes_write.sum over the launches of one timed step;
-# None for a kernel changed since its capture.
-DRAM_BYTES_PER_LAUNCH = {"wf_extend": 269.25e6, "wf_cache": 496.24e6}
-
+# DRAM traffic per launch (bytes) of a workload's dominant kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, stage); absent for a
+# kernel changed since its capture.
+DRAM_BYTES_PER_LAUNCH = {}
 
 # floats per vertex of the wavefront cache: E_v 12, compact W_v 19, the hit 4, visibility 1
 WF_CACHE_FLOATS = 36
@@ -118,6 +135,19 @@ def weak_scaling_value(paths_per_step: int, world: int, steps: int, max_total_ms
     return paths_per_step * world * steps / (max_total_ms / 1000.0)
 
 
+def views_workload(scale: float = 1.0):
+    """The views x angles batch (scale < 1 shrinks the image sides, for tests only)."""
+    from paper_2607_13265_gb300 import scenegen as sg
+    sizes = tuple(max(8, int(round(s * scale))) for s in VIEW_SIZES)
+    return sg.cornell_views(NUM_VIEWS, NUM_ANGLES, VIEW_SPP, VIEW_DEPTH, sizes)
+
+
+def path_counts(jobs) -> tuple[int, int]:
+    """(paths counted by the metric, paths traced by the batched form) per gradient step:
+    primal + adjoint, the former once per polarizer angle."""
+    return (sum(2 * j.num_paths * j.num_angles for j in jobs), sum(2 * j.num_paths for j in jobs))
+
+
 def load_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -132,19 +162,19 @@ def load_peaks() -> dict:
 _W = {}
 
 
-def _oracle_init(workload_kw):
+def _oracle_init(scale: float = 1.0):
     import oracle
-    from paper_2607_13265_gb300 import scenegen as sg
     oracle.build()
-    scene, job = sg.icosphere_scene(**workload_kw)
+    scene, jobs = views_workload(scale)
     _W["o"] = oracle.OracleScene(scene)
-    _W["scene"], _W["job"] = scene, job
+    _W["scene"], _W["jobs"] = scene, jobs
 
 
-def _oracle_task(pixels):
-    import copy
+def _oracle_task(item):
+    """Primal + cached-replay adjoint of the oracle on some pixels of one view, all angles."""
     import numpy as np
-    o, scene, job = _W["o"], _W["scene"], _W["job"]
+    view, pixels = item
+    o, scene, job = _W["o"], _W["scene"], _W["jobs"][view]
     pix = np.asarray(pixels, np.int64)
     P = scene.params()
     t0 = time.perf_counter()
@@ -152,59 +182,44 @@ def _oracle_task(pixels):
     aj = copy.copy(job)
     aj.pass_id = 1
     o.gradient(aj, P, np.ones_like(img), pixels=pix, mode="replay")
-    return time.perf_counter() - t0, 2 * len(pix) * job.spp
+    return time.perf_counter() - t0, 2 * len(pix) * job.spp * job.num_angles, 2 * len(pix) * job.spp
 
 
-def _oracle_tape_task(pixels):
-    """Conventional taped AD of the workload's paths on a few pixels: the tape's nodes (one
-    per parameter-dependent scalar operation, all kept until the reverse sweep) and the
-    vertices they cover."""
-    import copy
+def _sample_items(num_pixels: int, scale: float = 1.0):
+    """num_pixels pixels spread evenly over the views (evenly strided in each), as tasks of
+    at most 32 pixels."""
     import numpy as np
-    import oracle
-    o, scene, job = _W["o"], _W["scene"], _W["job"]
-    pix = np.asarray(pixels, np.int64)
-    P = scene.params()
-    aj = copy.copy(job)
-    aj.pass_id = 1
-    img = o.render(aj, P, pixels=pix)
-    oracle.stats(reset=True)
-    o.gradient(aj, P, np.ones_like(img), pixels=pix, mode="tape")
-    st = oracle.stats(reset=True)
-    return st["tape_total_nodes"], st["vertices"]
+    _, jobs = views_workload(scale)
+    per = max(1, num_pixels // len(jobs))
+    items = []
+    for v, j in enumerate(jobs):
+        pix = np.linspace(0, j.num_pixels - 1, min(per, j.num_pixels)).astype(np.int64)
+        items += [(v, pix[i:i + 32].tolist()) for i in range(0, len(pix), 32)]
+    return items
 
 
-def tape_model(pool, num_pixels: int = 64) -> dict:
-    """Tape nodes per path vertex of conventional AD on an evenly strided pixel sample."""
-    import numpy as np
-    pix = np.linspace(0, 256 * 256 - 1, num_pixels).astype(np.int64)
-    res = pool.map(_oracle_tape_task, [pix[i:i + 8].tolist() for i in range(0, len(pix), 8)])
-    nodes, verts = sum(r[0] for r in res), sum(r[1] for r in res)
-    return {"tape_nodes_per_vertex": nodes / max(verts, 1), "sample": f"{num_pixels} pixels x 64 spp, FP64 oracle tape"}
-
-
-def oracle_sample(num_pixels: int, procs: int, workload_kw: dict, pool=None):
-    """The FP64 oracle (primal + cached-replay adjoint) on an evenly strided pixel
-    sample of the workload, one task per 64 pixels over `procs` worker processes."""
-    import numpy as np
-    npix = 256 * 256
-    pix = np.linspace(0, npix - 1, num_pixels).astype(np.int64)
-    chunks = [pix[i:i + 64].tolist() for i in range(0, len(pix), 64)]
+def oracle_sample(num_pixels: int, procs: int, pool=None, scale: float = 1.0):
+    """The FP64 oracle (primal + cached-replay adjoint, all 64 angles) on an evenly strided
+    pixel sample of the views x angles workload over `procs` worker processes."""
+    items = _sample_items(num_pixels, scale)
     own = pool is None
     if own:
-        pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_init, initargs=(workload_kw,))
-        pool.map(_oracle_task, [chunks[0][:1]] * procs)   # warm every worker
+        pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_init, initargs=(scale,))
+        pool.map(_oracle_task, [(0, [0])] * procs)    # warm every worker
     t0 = time.perf_counter()
-    res = pool.map(_oracle_task, chunks)
+    res = pool.map(_oracle_task, items)
     wall = time.perf_counter() - t0
     if own:
         pool.close()
         pool.join()
     paths = sum(r[1] for r in res)
+    traced = sum(r[2] for r in res)
+    npix = sum(len(p) for _, p in items)
     return {"value": paths / wall, "unit": UNIT, "cores": procs, "kind": "oracle",
-            "sample": f"{num_pixels} evenly strided pixels x 64 spp of the {WORKLOAD} workload "
-                      f"({paths} primal+adjoint paths, FP64, {wall:.2f} s wall on {procs} processes)",
-            "wall_s": wall, "paths": paths}
+            "sample": f"{npix} evenly strided pixels over the 8 views of the {WORKLOAD} workload, 16 spp, "
+                      f"all 64 angles ({traced} primal+adjoint paths traced, {paths} counted as the metric counts "
+                      f"them; FP64, {wall:.2f} s wall on {procs} processes)",
+            "traced_paths_per_s": traced / wall, "wall_s": wall, "paths": paths}
 
 
 # ---------------------------------------------------------------- clocks
@@ -260,9 +275,388 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- roofline
+def roofline_of(stages: dict, flops: dict, cache_bytes: float, props, peaks: dict, clocks: dict,
+                traffic_key: str, work: dict) -> dict:
+    """Roofline of the stage with the most GPU time in `stages` ({stage: (launches, ms)}):
+    the cache pass against HBM (records and cache move through DRAM), every other stage
+    against the FP32 pipe (traversal and dual-number arithmetic under divergence)."""
+    timed = {k: v for k, v in stages.items() if v[0] > 0 and v[1] > 0}
+    dom = max(timed, key=lambda k: timed[k][1])
+    launches, ms = timed[dom]
+    launch_s = ms / launches / 1e3
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    fp32_loaded = props.multi_processor_count * 128 * 2 * (clocks.get("sm_mhz") or sm_max) * 1e6 / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs") or 6800.0)
+    traffic = DRAM_BYTES_PER_LAUNCH.get((traffic_key, dom))
+    if dom == "wf_cache":
+        ach = cache_bytes / launches / launch_s / 1e9
+        return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": traffic, "bytes_per_launch": cache_bytes / launches,
+                "launch_ms": launch_s * 1e3, "launches": launches, "work_units_adjoint_pass": work,
+                "peak_note": f"{peaks['_source']} HBM copy bandwidth"}
+    ach = flops.get(dom, 0) / launches / launch_s / 1e12
+    return {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": ach / fp32_peak, "frac_at_loaded_clock": ach / fp32_loaded, "traffic": traffic,
+            "hbm": ({"achieved_gbs": traffic / launch_s / 1e9, "peak_gbs": hbm_peak,
+                     "frac": traffic / launch_s / 1e9 / hbm_peak,
+                     "note": "ncu DRAM bytes per launch (cold caches) / in-bench launch time"} if traffic else None),
+            "flops_per_launch": flops.get(dom, 0) / launches, "launch_ms": launch_s * 1e3, "launches": launches,
+            "work_units_adjoint_pass": work,
+            "peak_note": f"FP32 pipe: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
+                         f"({peaks['_source']} max clock)"}
+
+
+def workload_flops(work: dict, pwork: dict, launch: tuple, steps: int) -> tuple[dict, float]:
+    """Algorithmic flops per stage and cache-pass bytes of `steps` gradient steps (primal
+    work `pwork`, adjoint work `work`) under the launch shapes `launch`."""
+    flops = {}
+    for name, v in stage_flops(work, 2).items():
+        flops[name] = flops.get(name, 0) + v * steps
+    for name, v in stage_flops(pwork, 1).items():
+        if name == "primal" or launch[0] == 2:
+            flops[name] = flops.get(name, 0) + v * steps
+    # the library shades each cache-pass vertex inside the extend kernel
+    flops["wf_extend"] = flops.get("wf_extend", 0) + flops.pop("wf_shade", 0)
+    cb = (cache_pass_bytes(work, 2) + (cache_pass_bytes(pwork, 1) if launch[0] == 2 else 0)) * steps
+    return flops, cb
+
+
+def stage_report(stages: dict, flops: dict, cache_bytes: float, steps: int) -> dict:
+    out = {}
+    for k, (n, ms) in stages.items():
+        if n == 0:
+            continue
+        r = {"launches_per_step": n / steps, "ms_per_step": ms / steps,
+             "tflops": (flops[k] / (ms / 1000.0) / 1e12) if k in flops and ms > 0 else None}
+        if k == "wf_cache" and ms > 0:
+            r["gbs"] = cache_bytes / (ms / 1000.0) / 1e9
+        out[k] = r
+    return out
+
+
 # ---------------------------------------------------------------- native leg
-def run_native(args):
+def run_views(args, api, dctx, rank, world, dev, clk_index, peaks):
+    """The headline: batched views x angles gradient step in a CUDA graph, the plain form,
+    gradient memory of both, end to end through PolarizedL2 with host buffers."""
     import numpy as np
+    import torch
+    scene, jobs = views_workload(args.scale)
+    for j in jobs:
+        j.stream += 1000 * rank                  # every rank traces its own independent paths
+    gs = api.GpuScene(dctx, scene)
+    batch = api.pack_jobs(jobs)
+    adj = api.pack_jobs(api.adjoint_jobs(jobs))
+    rb = api.raw_batch(batch)
+    P = api.device_params(scene, batch)
+    tuning = None
+    if args.schedule is not None:
+        dctx.set_launch(args.schedule, args.block, 0, args.adj_schedule if args.adj_schedule is not None
+                        else args.schedule, args.adj_block or args.block, 0, args.adj_scatter)
+    else:
+        tuning = api.autotune(dctx, gs, adj, P, reps=1)
+    lc = dctx.get_launch()
+
+    # seeded target: the walls' and the diffuse sphere's albedo perturbed, other random numbers
+    tp = scene.params()
+    rng = np.random.default_rng(21)
+    tp["tex"] = np.clip(tp["tex"] + rng.uniform(-0.15, 0.15, tp["tex"].shape), 0.05, 0.95)
+    tp["theta"] = batch.theta
+    tjobs = [copy.copy(j) for j in jobs]
+    for j in tjobs:
+        j.seed = 777
+    target = api.render_primal(dctx, gs, api.pack_jobs(tjobs), api.device_params(scene, batch, tp)).clone()
+    N = float(target.numel())
+    stream = torch.cuda.Stream(device=dev)
+    raw_buf = torch.empty(rb.image_floats, dtype=torch.float32, device=dev)
+    loss_buf = torch.empty((), dtype=torch.float64, device=dev)
+    grads = api.zero_grads(P)
+
+    def step():
+        # what PolarizedL2's forward and backward run, issued on one stream
+        api.render_primal(dctx, gs, rb, P, image=raw_buf, stream=stream)
+        api.loss_l2(dctx, gs, batch, P, raw_buf, rb.offsets, target, 1.0 / N, loss=loss_buf, stream=stream)
+        for g in grads.values():
+            g.zero_()
+        api.render_adjoint_l2(dctx, gs, adj, P, raw_buf, rb.offsets, target, 1.0 / N, grads, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()                       # the library sizes its workspace here, before the capture
+    stream.synchronize()
+    dctx.sync_status(stream)
+    dctx.stage_stats(timing=False, reset=True)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        step()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            graph.replay()
+    stream.synchronize()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(clk_index) as clk:
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                flush.zero_()                    # L2 flush between timed replays (outside the events)
+                ev[k][0].record(stream)
+                graph.replay()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    dctx.sync_status(stream)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    # per-kernel times: the same step run eagerly (the graph's kernels, launched one by one),
+    # with the CUDA events the library records around each launch on the launching stream
+    KS = min(K, 5)
+    dctx.stage_stats(timing=True, reset=True)
+    with torch.cuda.stream(stream):
+        for _ in range(KS):
+            flush.zero_()
+            step()
+    stream.synchronize()
+    stages = dctx.stage_stats(timing=False, reset=True)
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    counted, traced = path_counts(jobs)
+    value = weak_scaling_value(counted, world, K, total_ms)
+    clocks = clk.summary()
+    loss_val = float(loss_buf)
+
+    # ---- the plain form: one render_primal + one render_adjoint per (view, angle)
+    plain_jobs = []
+    for j in jobs:
+        for t in j.thetas:
+            k = copy.copy(j)
+            k.thetas = [t]
+            plain_jobs.append(k)
+    plain_batches = [api.pack_jobs([k]) for k in plain_jobs]
+    plain_adj = [api.pack_jobs(api.adjoint_jobs([k])) for k in plain_jobs]
+    views = api.image_views(batch, target)
+    plain_targets = [views[vi][a].reshape(-1) for vi, j in enumerate(jobs) for a in range(j.num_angles)]
+    plain_params = []
+    for k in plain_jobs:
+        q = dict(P)
+        q["theta"] = torch.tensor([k.thetas[0]], dtype=torch.float32, device=dev)
+        plain_params.append(q)
+    pg = api.zero_grads(P)
+    theta_scratch = torch.zeros(1, device=dev)
+
+    def plain_all():
+        for pb, pa, q, t in zip(plain_batches, plain_adj, plain_params, plain_targets):
+            img = api.render_primal(dctx, gs, pb, q, stream=stream)
+            d = (img - t).mul_(2.0 / N)
+            gq = {"tex": pg["tex"], "ior": pg["ior"], "le": pg["le"], "sheet": pg["sheet"], "theta": theta_scratch}
+            api.render_adjoint(dctx, gs, pa, q, d, gq, stream=stream)
+
+    with torch.cuda.stream(stream):
+        plain_all()                      # warm-up
+    stream.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        flush.zero_()
+        a.record(stream)
+        plain_all()
+        b.record(stream)
+    b.synchronize()
+    plain_ms = max_over_ranks(a.elapsed_time(b), world, dev)
+    plain_traced = sum(2 * k.num_paths for k in plain_jobs)
+    dctx.sync_status(stream)
+
+    # ---- gradient memory of the autograd forms: peak device memory of forward + backward
+    def peak(fn):
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        fn()
+        torch.cuda.synchronize()
+        return torch.cuda.max_memory_allocated() - base
+
+    leaf = {k: v.clone().requires_grad_(True) for k, v in P.items()}
+
+    def batched_fused():
+        api.PolarizedL2.apply(dctx, gs, batch, adj, target, leaf["tex"], leaf["ior"], leaf["le"], leaf["sheet"],
+                              leaf["theta"]).backward()
+
+    def batched_image():
+        img = api.PolarizedRender.apply(dctx, gs, batch, adj, leaf["tex"], leaf["ior"], leaf["le"], leaf["sheet"],
+                                        leaf["theta"])
+        api.ImageL2.apply(img, target).backward()
+
+    def plain_autograd():
+        loss = 0.0
+        for pb, pa, q, t in zip(plain_batches, plain_adj, plain_params, plain_targets):
+            thq = q["theta"].clone().requires_grad_(True)
+            img = api.PolarizedRender.apply(dctx, gs, pb, pa, leaf["tex"], leaf["ior"], leaf["le"], leaf["sheet"], thq)
+            loss = loss + api.ImageL2.apply(img, t) * (img.numel() / N)
+        loss.backward()
+
+    mem_fused = peak(batched_fused)
+    mem_image = peak(batched_image)
+    mem_plain = peak(plain_autograd)
+    ws_batched = dctx.query_workspace(adj)
+    ws_plain = max(dctx.query_workspace(pa) for pa in plain_adj[::NUM_ANGLES])
+
+    # ---- end to end through the public autograd API, texture from and gradient to pinned host memory
+    host_tex = torch.from_numpy(np.asarray(scene.params()["tex"], np.float32)).pin_memory()
+    host_grad = torch.empty_like(host_tex).pin_memory()
+    host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+    tex_d = P["tex"].clone().requires_grad_(True)
+    others = {k: P[k].clone().requires_grad_(True) for k in ("ior", "le", "sheet", "theta")}
+    cur = torch.cuda.current_stream(dev)
+
+    def e2e_step():
+        tex_d.data.copy_(host_tex, non_blocking=True)
+        tex_d.grad = None
+        loss = api.PolarizedL2.apply(dctx, gs, batch, adj, target, tex_d, others["ior"], others["le"],
+                                     others["sheet"], others["theta"])
+        loss.backward()
+        host_grad.copy_(tex_d.grad, non_blocking=True)
+        host_loss.copy_(loss.detach().view(1), non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(K):
+        flush.zero_()
+        a.record(cur)
+        e2e_step()
+        b.record(cur)
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    e2e = {"value": weak_scaling_value(counted, world, K, e2e_ms), "unit": UNIT,
+           "h2d_bytes_per_step": int(host_tex.numel() * 4), "d2h_bytes_per_step": int(host_grad.numel() * 4 + 4),
+           "ms_per_step": e2e_ms / K, "api": "PolarizedL2.apply + loss.backward()"}
+
+    # ---- roofline of the dominant kernel of the graph replays
+    work = api.count_work(dctx, gs, adj, P)
+    pwork = api.count_work(dctx, gs, rb, P)
+    flops, cbytes = workload_flops(work, pwork, lc, KS)
+    props = torch.cuda.get_device_properties(dev)
+    roofline = roofline_of(stages, flops, cbytes, props, peaks, clocks, WORKLOAD, work)
+
+    result = {
+        "value": value, "ms_per_step": total_ms / K, "clocks": clocks,
+        "config": {"workload": WORKLOAD if args.scale == 1.0 else f"{WORKLOAD} scaled {args.scale}",
+                   "scene": "Cornell box: 12 triangles + 2 spheres, one quad light",
+                   "views": [j.width for j in jobs], "angles": NUM_ANGLES, "spp": VIEW_SPP, "max_depth": VIEW_DEPTH,
+                   "pixels": int(sum(j.num_pixels for j in jobs)),
+                   "paths_counted_per_step": counted, "paths_traced_per_step": traced,
+                   "paths_counted": "every (view, angle, pixel, sample) path of the primal and of the adjoint, "
+                                    "as the plain form traces them; the batched form folds the angles exactly",
+                   "step": "CUDA-graph replay of the batched fused-L2 gradient step (PolarizedL2 forward + backward "
+                           "kernels: render_primal of all views, dppt_loss_l2, dppt_render_adjoint_l2)",
+                   "grads": "albedo textures, IOR, emitter Stokes, 512 polarizer angles",
+                   "l2": "flushed between timed steps (512 MiB write); the 2.9 GB target is read every step",
+                   "schedule": {"primal": [api.SCHEDULE_NAMES[lc[0]], lc[1]],
+                                "adjoint": [api.SCHEDULE_NAMES[lc[3]], lc[4]],
+                                "adjoint_texel_scatter": ("warp", "lane")[lc[6]],
+                                "chosen_by": "autotuner" if tuning else "command line"},
+                   "parallelism": f"replicas{world}"},
+        "batched": {"ms_per_step": total_ms / K, "paths_per_s": value,
+                    "traced_paths_per_s": weak_scaling_value(traced, world, K, total_ms),
+                    "p50_ms": statistics.median(step_ms), "p99_ms": sorted(step_ms)[min(K - 1, int(0.99 * K))],
+                    "loss": loss_val,
+                    "peak_autograd_bytes": int(mem_fused), "workspace_bytes": int(ws_batched),
+                    "image_form_peak_autograd_bytes": int(mem_image)},
+        "plain": {"calls": 2 * len(plain_jobs), "ms_per_step": plain_ms,
+                  "paths_per_s": weak_scaling_value(counted, world, 1, plain_ms),
+                  "traced_paths_per_s": weak_scaling_value(plain_traced, world, 1, plain_ms),
+                  "peak_autograd_bytes": int(mem_plain), "workspace_bytes": int(ws_plain)},
+        "vs_plain": {"paths_per_s": (total_ms / K) and plain_ms / (total_ms / K),
+                     "gradient_mb_batched": mem_fused / 2**20, "gradient_mb_plain": mem_plain / 2**20,
+                     "gradient_memory_ratio": mem_fused / max(1, mem_plain)},
+        "stages": stage_report(stages, flops, cbytes, KS),
+        "stages_note": f"per-kernel times over {KS} eager runs of the captured step (CUDA events the library "
+                       "records around each launch on the launching stream); eager step "
+                       f"{sum(v[1] for v in stages.values()) / KS:.2f} ms of kernel time",
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(sum(n for n, _ in stages.values()) / KS * K),
+        "tuning": tuning,
+    }
+    return result
+
+
+def run_icosphere(args, api, dctx, rank, dev, peaks):
+    """The 50k-triangle icosphere gradient step (eager), its stages and dominant-kernel roofline."""
+    import numpy as np
+    import torch
+    from paper_2607_13265_gb300 import scenegen as sg
+    scene, job = sg.icosphere_scene()
+    job.stream = rank
+    target_scene, tjob = sg.icosphere_scene()
+    tp = target_scene.params()
+    rng = np.random.default_rng(100)
+    for t in (0, 1):
+        off, w, h, ch = target_scene.tex_desc[t]
+        lo, hi = ((0.2, 0.9), (0.05, 0.5))[t]
+        tp["tex"][off:off + w * h * ch] = rng.uniform(lo, hi, w * h * ch)
+    gs = api.GpuScene(dctx, scene)
+    batch = api.pack_jobs([job])
+    adj = api.pack_jobs(api.adjoint_jobs([job]))
+    P = api.device_params(scene, batch)
+    tuning = api.autotune(dctx, gs, adj, P, reps=2)
+    lc = dctx.get_launch()
+    tjob.seed = 12345
+    target = api.render_primal(dctx, gs, api.pack_jobs([tjob]), api.device_params(scene, batch, tp)).clone()
+    N = float(target.numel())
+    grads = api.zero_grads(P)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        img = api.render_primal(dctx, gs, batch, P, stream=stream)
+        dI = (img - target).mul_(2.0 / N)
+        api.render_adjoint(dctx, gs, adj, P, dI, grads, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    dctx.stage_stats(timing=True, reset=True)
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    stages = dctx.stage_stats(timing=False, reset=True)
+    dctx.sync_status()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    paths = 2 * job.num_paths
+    work = api.count_work(dctx, gs, adj, P)
+    pwork = api.count_work(dctx, gs, batch, P)
+    flops, cbytes = workload_flops(work, pwork, lc, K)
+    props = torch.cuda.get_device_properties(dev)
+    fp = dctx.adjoint_footprint(job.max_depth)
+    return {"workload": ICO_WORKLOAD, "paths_per_s": paths * K / (ms / 1000.0), "ms_per_step": ms / K,
+            "paths_per_step": paths,
+            "schedule": {"primal": [api.SCHEDULE_NAMES[lc[0]], lc[1]], "adjoint": [api.SCHEDULE_NAMES[lc[3]], lc[4]],
+                         "adjoint_texel_scatter": ("warp", "lane")[lc[6]], "chosen_by": "autotuner"},
+            "stages": stage_report(stages, flops, cbytes, K),
+            "roofline": roofline_of(stages, flops, cbytes, props, peaks, {}, ICO_WORKLOAD, work),
+            "memory": {"workspace_bytes": dctx.query_workspace(adj),
+                       "prb_cache_bytes": (wave_paths(job) * job.max_depth * WF_CACHE_FLOATS * 4 if lc[3] == 2
+                                           else fp["local_bytes_per_thread"] * fp["threads_per_sm"] * fp["sms"]),
+                       "megakernel_local_bytes_per_thread": fp["local_bytes_per_thread"],
+                       "megakernel_adjoint_registers": fp["registers"]},
+            "gpu_launches": int(sum(n for n, _ in stages.values())),
+            "tuning_times_ms": tuning["times_ms"]}
+
+
+def run_native(args):
     import torch
     import torch.distributed as dist
     rank, world, local = _env_rank()
@@ -270,220 +664,28 @@ def run_native(args):
     cpu_procs = os.cpu_count() or 1
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle's worker processes are spawned before the first CUDA call
-        pool = mp.get_context("spawn").Pool(cpu_procs, initializer=_oracle_init, initargs=({},))
+        pool = mp.get_context("spawn").Pool(cpu_procs, initializer=_oracle_init, initargs=(args.scale,))
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2607_13265_gb300 import api, build, scenegen as sg
+    from paper_2607_13265_gb300 import api, build
     build.build()
     dev = torch.device("cuda", local)
-    kw = {}
-    if args.width:
-        kw["width"] = args.width
-    if args.spp:
-        kw["spp"] = args.spp
-    scene, job = sg.icosphere_scene(**kw)
-    job.stream = rank                      # every rank traces its own independent paths
-    target_scene, tjob = sg.icosphere_scene(**kw)
-    tp = target_scene.params()
-    rng = np.random.default_rng(100)
-    off, w, h, ch = target_scene.tex_desc[0]
-    tp["tex"][off:off + w * h * ch] = rng.uniform(0.2, 0.9, w * h * ch)
-    off, w, h, ch = target_scene.tex_desc[1]
-    tp["tex"][off:off + w * h * ch] = rng.uniform(0.05, 0.5, w * h * ch)
-
-    dctx = api.Context(local)
-    gs = api.GpuScene(dctx, scene)
-    batch = api.pack_jobs([job])
-    adj = api.pack_jobs(api.adjoint_jobs([job]))
-    P = api.device_params(scene, batch)
-    tuning = None
-    if args.schedule is not None:
-        adj_s = args.schedule if args.adj_schedule is None else args.adj_schedule
-        adj_b = args.block if args.adj_block is None else args.adj_block
-        dctx.set_launch(args.schedule, args.block, 0, adj_s, adj_b, 0, args.adj_scatter)
-    else:
-        # the library's autotuner picks schedule and block size for each call (untimed)
-        tuning = api.autotune(dctx, gs, adj, P, reps=2)
-    tjob.seed = 12345
-    target = api.render_primal(dctx, gs, api.pack_jobs([tjob]), api.device_params(scene, batch, tp)).clone()
-    N = float(target.numel())
-    grads = api.zero_grads(P)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-
-    def step():
-        img = api.render_primal(dctx, gs, batch, P, stream=stream)
-        dI = (img - target).mul_(2.0 / N)
-        api.render_adjoint(dctx, gs, adj, P, dI, grads, stream=stream)
-        return img
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    dctx.sync_status()
-
-    K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
-    with ClockSampler(local) as clk:                # clocks sampled from here to the end of the region
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        dctx.stage_stats(timing=True, reset=True)  # per-stage CUDA events on the launching stream
-        for k in range(K):
-            flush.zero_()                               # L2 flush between timed steps (outside the events)
-            e0, e1, e2, e3 = ev[k]
-            e0.record(stream)
-            img = api.render_primal(dctx, gs, batch, P, stream=stream)
-            e1.record(stream)
-            dI = (img - target).mul_(2.0 / N)
-            e2.record(stream)
-            api.render_adjoint(dctx, gs, adj, P, dI, grads, stream=stream)
-            e3.record(stream)
-        torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    stages = dctx.stage_stats(timing=False, reset=True)
-    dctx.sync_status()
-    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
-    prim_ms = [e[0].elapsed_time(e[1]) for e in ev]
-    adj_ms = [e[2].elapsed_time(e[3]) for e in ev]
-    total_ms = max_over_ranks(sum(step_ms), world, dev)
-    paths_per_step = 2 * job.num_paths
-    value = weak_scaling_value(paths_per_step, world, K, total_ms)
-
-    # ---- end to end through the public autograd API with host buffers
-    e2e = None
-    if rank == 0 or world > 1:
-        host_tex = torch.from_numpy(np.asarray(scene.params()["tex"], np.float32)).pin_memory()
-        host_grad = torch.empty_like(host_tex).pin_memory()
-        host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
-        tex_d = P["tex"].clone().requires_grad_(True)
-        others = {k: P[k].clone().requires_grad_(True) for k in ("ior", "le", "sheet", "theta")}
-
-        def e2e_step():
-            tex_d.data.copy_(host_tex, non_blocking=True)
-            tex_d.grad = None
-            img = api.PolarizedRender.apply(dctx, gs, batch, adj, tex_d, others["ior"], others["le"],
-                                            others["sheet"], others["theta"])
-            loss = ((img - target) ** 2).mean()
-            loss.backward()
-            host_grad.copy_(tex_d.grad, non_blocking=True)
-            host_loss.copy_(loss.detach().view(1), non_blocking=True)
-
-        for _ in range(args.warmup):
-            e2e_step()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ms = 0.0
-        for _ in range(K):
-            flush.zero_()
-            a.record(stream)
-            e2e_step()
-            b.record(stream)
-            b.synchronize()
-            ms += a.elapsed_time(b)
-        e2e = {"value": paths_per_step * K / (ms / 1000.0), "unit": UNIT,
-               "h2d_bytes_per_step": int(host_tex.numel() * 4),
-               "d2h_bytes_per_step": int(host_grad.numel() * 4 + 4),
-               "api": "PolarizedRender.apply + loss.backward()"}
-
-    # ---- roofline of the dominant kernel (largest share of the timed region's GPU time)
-    work = api.count_work(dctx, gs, adj, P)
-    pw = api.count_work(dctx, gs, batch, P)
-    lc = dctx.get_launch()
-    flops = {}
-    for name, v in stage_flops(work, 2).items():
-        flops[name] = flops.get(name, 0) + v * K
-    for name, v in stage_flops(pw, 1).items():
-        if name == "primal" or lc[0] == 2:
-            flops[name] = flops.get(name, 0) + v * K
-    timed = {k: v for k, v in stages.items() if v[0] > 0}
-    if "wf_extend" in timed and "wf_shade" not in timed and "wf_shade" in flops:
-        # the library shades each cache-pass vertex inside the extend kernel
-        flops["wf_extend"] = flops.get("wf_extend", 0) + flops.pop("wf_shade")
-    dom = max(timed, key=lambda k: timed[k][1])
-    dom_launches, dom_ms = timed[dom]
-    adj_avg = sum(adj_ms) / K
-    prim_avg = sum(prim_ms) / K
-    props = torch.cuda.get_device_properties(dev)
     peaks = load_peaks()
-    clocks = clk.summary()
-    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
-    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at max clock
-    fp32_peak_loaded = props.multi_processor_count * 128 * 2 * (clocks["sm_mhz"] or sm_max) * 1e6 / 1e12
-    achieved = flops.get(dom, 0) / (dom_ms / 1000.0) / 1e12 if dom_ms > 0 else 0.0
-    fp = dctx.adjoint_footprint(job.max_depth)
-    cache_bytes = fp["local_bytes_per_thread"] * fp["threads_per_sm"] * fp["sms"]
-    stage_report = {k: {"launches": n, "ms_per_step": ms / K,
-                        "tflops": (flops[k] / (ms / 1000.0) / 1e12) if k in flops and ms > 0 else None}
-                    for k, (n, ms) in timed.items()}
-    if "wf_cache" in stage_report and timed["wf_cache"][1] > 0:
-        cb = (cache_pass_bytes(work, 2) + (cache_pass_bytes(pw, 1) if lc[0] == 2 else 0)) * K
-        stage_report["wf_cache"]["gbs"] = cb / (timed["wf_cache"][1] / 1000.0) / 1e9
-
-    # the dominant kernel's roofline: the cache pass moves records (HBM-bound); traversal and
-    # the dual-number replay are bound by FP32 arithmetic issued under divergence
-    hbm_peak = float(peaks.get("hbm_gbs") or 6800.0)
-    launch_s = dom_ms / max(dom_launches, 1) / 1e3
-    traffic = DRAM_BYTES_PER_LAUNCH.get(dom)
-    if dom == "wf_cache":
-        byt = (cache_pass_bytes(work, 2) + (cache_pass_bytes(pw, 1) if lc[0] == 2 else 0)) * K
-        ach = byt / max(dom_launches, 1) / launch_s / 1e9
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": ach / hbm_peak, "traffic": traffic,
-                    "bytes_per_launch": byt / max(dom_launches, 1), "launch_ms": launch_s * 1e3,
-                    "work_units_adjoint_pass": work,
-                    "peak_note": f"{peaks['_source']} HBM copy bandwidth"}
-    else:
-        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
-                    "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                    "frac_at_loaded_clock": achieved / fp32_peak_loaded,
-                    "traffic": traffic,
-                    "hbm": ({"achieved_gbs": traffic / launch_s / 1e9, "peak_gbs": hbm_peak,
-                             "frac": traffic / launch_s / 1e9 / hbm_peak,
-                             "note": "ncu DRAM bytes per launch (cold caches) / in-bench launch time"}
-                            if traffic else None),
-                    "flops_per_launch": flops.get(dom, 0) / max(dom_launches, 1),
-                    "launch_ms": launch_s * 1e3,
-                    "work_units_adjoint_pass": work,
-                    "peak_note": f"FP32 pipe: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
-                                 f"({peaks['_source']} max clock)"}
-
+    dctx = api.Context(local)
+    views = run_views(args, api, dctx, rank, world, dev, local, peaks)
+    ico = None if args.no_icosphere else run_icosphere(args, api, dctx, rank, dev, peaks)
     result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
-        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic (seeded procedural scene, textures and target)",
-        "config": {"workload": WORKLOAD if not kw else f"{WORKLOAD} reduced {kw}", "triangles": int(scene.num_triangles), "width": job.width,
-                   "height": job.height, "spp": job.spp, "max_depth": job.max_depth,
-                   "paths_per_step": paths_per_step, "grads": "albedo 128x128x3 + roughness 128x128",
-                   "l2": "flushed between timed steps (512 MiB write)",
-                   "schedule": {"primal": [api.SCHEDULE_NAMES[lc[0]], lc[1]], "adjoint": [api.SCHEDULE_NAMES[lc[3]], lc[4]],
-                                "adjoint_texel_scatter": ("warp", "lane")[lc[6]],
-                                "chosen_by": "autotuner" if tuning else "command line"},
-                   "parallelism": f"replicas{world}"},
-        "calls_ms": {"render_primal": prim_avg, "render_adjoint": adj_avg},
-        "stages": stage_report,
-        "roofline": roofline,
-        "memory": {"workspace_bytes": dctx.query_workspace(adj),
-                   "prb_cache_bytes": (wave_paths(job) * job.max_depth * WF_CACHE_FLOATS * 4 if lc[3] == 2 else cache_bytes),
-                   "prb_cache_where": "wavefront workspace" if lc[3] == 2 else "megakernel thread-local memory",
-                   "megakernel_local_bytes_per_thread": fp["local_bytes_per_thread"],
-                   "megakernel_adjoint_registers": fp["registers"]},
-        "clocks": clocks,
-        "e2e": e2e,
-        "gpu_launches": int(sum(n for n, _ in timed.values())),
+        "metric": METRIC, "value": views["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": views["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded procedural scene, textures and target)",
+        "config": views["config"], "batched": views["batched"], "plain": views["plain"],
+        "vs_plain": views["vs_plain"], "stages": views["stages"], "stages_note": views["stages_note"],
+        "roofline": views["roofline"], "clocks": views["clocks"], "e2e": views["e2e"],
+        "gpu_launches": views["gpu_launches"], "tuning": views["tuning"], "icosphere": ico,
     }
     if pool is not None:
-        result["cpu_baseline"] = oracle_sample(args.cpu_pixels, cpu_procs, {}, pool)
-        tm = tape_model(pool)
-        # conventional AD keeps every path's tape at once: nodes/vertex x vertices of the
-        # gradient pass, at 16 B per node (FP32 partials + 32-bit operand indices) and 4 B
-        # (one FP32 value: a lower bound for any tape)
-        nv = tm["tape_nodes_per_vertex"] * work["vertices"]
-        result["memory"]["tape_ad_model"] = {"bytes_16B_per_node": int(16 * nv), "bytes_4B_lower_bound": int(4 * nv),
-                                             **tm}
-        result["memory"]["prb_cache_vs_tape_ad"] = result["memory"]["prb_cache_bytes"] / max(1.0, 16 * nv)
+        result["cpu_baseline"] = oracle_sample(args.cpu_pixels, cpu_procs, pool, args.scale)
         pool.close()
         pool.join()
     if rank == 0:
@@ -498,20 +700,21 @@ def run_reference(args):
     if rank != 0:
         return
     procs = os.cpu_count() or 1
-    pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_init, initargs=({},))
-    pool.map(_oracle_task, [[0]] * procs)
+    pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_init, initargs=(args.scale,))
+    pool.map(_oracle_task, [(0, [0])] * procs)
     for _ in range(args.warmup):
-        oracle_sample(args.ref_pixels, procs, {}, pool)
-    vals, walls, paths = [], 0.0, 0
+        oracle_sample(args.ref_pixels, procs, pool, args.scale)
+    walls, paths, traced = 0.0, 0, 0.0
     for _ in range(args.steps):
-        r = oracle_sample(args.ref_pixels, procs, {}, pool)
+        r = oracle_sample(args.ref_pixels, procs, pool, args.scale)
         walls += r["wall_s"]
         paths += r["paths"]
     pool.close()
     pool.join()
     value = paths / walls
-    sample = (f"{args.ref_pixels} evenly strided pixels x 64 spp of the {WORKLOAD} workload per step "
-              f"(FP64 oracle: primal + cached-replay adjoint)")
+    sample = (f"{args.ref_pixels} evenly strided pixels over the 8 views of the {WORKLOAD} workload per step, "
+              f"16 spp, all 64 angles (FP64 oracle: primal + cached-replay adjoint; paths counted as the "
+              f"native arm counts them)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * walls / args.steps,
@@ -528,17 +731,17 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--schedule", type=int, default=None, help="0 grid, 1 persistent (default: library default)")
+    ap.add_argument("--schedule", type=int, default=None, help="0 grid, 1 persistent, 2 wavefront (default: autotuner)")
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--adj-schedule", type=int, default=None, help="adjoint schedule (default: same as --schedule)")
     ap.add_argument("--adj-block", type=int, default=None)
     ap.add_argument("--adj-scatter", type=int, default=0, choices=[0, 1],
                     help="with --schedule: texel gradients per warp group (0) or per lane (1)")
-    ap.add_argument("--cpu-pixels", type=int, default=16384)
-    ap.add_argument("--ref-pixels", type=int, default=2048)
+    ap.add_argument("--cpu-pixels", type=int, default=8192, help="pixels of the CPU-baseline sample")
+    ap.add_argument("--ref-pixels", type=int, default=1024, help="pixels per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--width", type=int, default=None, help="smaller image (profiling captures only)")
-    ap.add_argument("--spp", type=int, default=None, help="fewer samples per pixel (profiling captures only)")
+    ap.add_argument("--no-icosphere", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0, help="image sides scaled (tests and profiling captures only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
