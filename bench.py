@@ -82,12 +82,13 @@ DRAM_BYTES_PER_LAUNCH = {}
 WF_CACHE_FLOATS = 36
 
 
-def wave_paths(job) -> int:
-    """Paths per wavefront wave: at most 4,194,304 whole pixels and at most 32 GiB of path
-    state (416 B) plus cache (144 B per vertex) per wave, as the library sizes them."""
-    per_path = 416 + 4 * WF_CACHE_FLOATS * job.max_depth
+def wave_paths(jobs) -> int:
+    """Path slots of a wavefront wave, as the library sizes them: all the jobs' paths when
+    they fit, else 4,194,304 or fewer when a wave's path state (416 B) plus cache (144 B per
+    vertex) would pass 32 GiB; several jobs share a wave."""
+    per_path = 416 + 4 * WF_CACHE_FLOATS * max(j.max_depth for j in jobs)
     cap = min(1 << 22, (32 << 30) // per_path)
-    return min(job.num_paths, max(job.spp, cap // job.spp * job.spp))
+    return max(max(j.spp for j in jobs), min(sum(j.num_paths for j in jobs), cap))
 
 
 def cache_pass_bytes(w: dict, passes: int) -> float:
@@ -426,6 +427,9 @@ def run_views(args, api, dctx, rank, world, dev, clk_index, peaks):
     stream.synchronize()
     stages = dctx.stage_stats(timing=False, reset=True)
     total_ms = max_over_ranks(sum(step_ms), world, dev)
+    if args.kernels_only:
+        return {"value": weak_scaling_value(path_counts(jobs)[0], world, K, total_ms), "ms_per_step": total_ms / K,
+                "stages": {k: v for k, v in stages.items() if v[0]}}
     counted, traced = path_counts(jobs)
     value = weak_scaling_value(counted, world, K, total_ms)
     clocks = clk.summary()
@@ -648,7 +652,7 @@ def run_icosphere(args, api, dctx, rank, dev, peaks):
             "stages": stage_report(stages, flops, cbytes, K),
             "roofline": roofline_of(stages, flops, cbytes, props, peaks, {}, ICO_WORKLOAD, work),
             "memory": {"workspace_bytes": dctx.query_workspace(adj),
-                       "prb_cache_bytes": (wave_paths(job) * job.max_depth * WF_CACHE_FLOATS * 4 if lc[3] == 2
+                       "prb_cache_bytes": (wave_paths([job]) * job.max_depth * WF_CACHE_FLOATS * 4 if lc[3] == 2
                                            else fp["local_bytes_per_thread"] * fp["threads_per_sm"] * fp["sms"]),
                        "megakernel_local_bytes_per_thread": fp["local_bytes_per_thread"],
                        "megakernel_adjoint_registers": fp["registers"]},
@@ -662,7 +666,7 @@ def run_native(args):
     rank, world, local = _env_rank()
     pool = None
     cpu_procs = os.cpu_count() or 1
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.kernels_only:
         # the oracle's worker processes are spawned before the first CUDA call
         pool = mp.get_context("spawn").Pool(cpu_procs, initializer=_oracle_init, initargs=(args.scale,))
     torch.cuda.set_device(local)
@@ -674,6 +678,10 @@ def run_native(args):
     peaks = load_peaks()
     dctx = api.Context(local)
     views = run_views(args, api, dctx, rank, world, dev, local, peaks)
+    if args.kernels_only:
+        if rank == 0:
+            print(json.dumps(views))
+        return
     ico = None if args.no_icosphere else run_icosphere(args, api, dctx, rank, dev, peaks)
     result = {
         "metric": METRIC, "value": views["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -742,6 +750,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-icosphere", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="image sides scaled (tests and profiling captures only)")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="profiling captures: the batched steps only (no plain form, memory, end to end or CPU leg)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -745,7 +745,11 @@ static void build_tables(const dppt_job* jobs, int njobs, const std::vector<JobP
     }
 }
 
-constexpr long long kWaveCap = 1LL << 22;        // paths per wave of the wavefront schedule
+// path slots per wave of the wavefront schedule
+#ifndef DPPT_WF_WAVE_PATHS
+#define DPPT_WF_WAVE_PATHS (1LL << 22)
+#endif
+constexpr long long kWaveCap = DPPT_WF_WAVE_PATHS;
 // a wave's state and cache budget: 32 GiB, an eighth of GB300's HBM, holds one wave of the
 // 1280x720 deep-path workload at depth 128 (17 GB; 8 GiB made three waves, 1.5x the time)
 #ifndef DPPT_WF_WAVE_GIB
@@ -759,16 +763,18 @@ static int max_depth_of(const dppt_job* jobs, int njobs) {
     return d;
 }
 
+// Path slots of a wavefront wave: all the jobs' paths when they fit, else the cap (4,194,304
+// paths, or fewer when the state and cache of a wave would pass the byte budget); at least
+// one pixel of every job.  Several jobs share a wave.
 static long long wave_paths(const dppt_job* jobs, int njobs) {
     const long long per_path = (long long)(wavefront_bytes(1LL << 20, max_depth_of(jobs, njobs)) >> 20) + 1;
     const long long limit = std::min(kWaveCap, std::max(1LL, kWaveBytes / per_path));
-    long long q = 0;
+    long long total = 0, spp = 1;
     for (int i = 0; i < njobs; ++i) {
-        long long n = (long long)jobs[i].width * jobs[i].height * jobs[i].spp;
-        long long cap = std::max<long long>(jobs[i].spp, (limit / jobs[i].spp) * jobs[i].spp);
-        q = std::max(q, std::min(n, cap));
+        total += (long long)jobs[i].width * jobs[i].height * jobs[i].spp;
+        spp = std::max<long long>(spp, jobs[i].spp);
     }
-    return q;
+    return std::max(spp, std::min(total, limit));
 }
 
 // shared memory of the megakernel adjoints' scalar-gradient accumulators (one copy each)
@@ -810,11 +816,9 @@ dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_jo
             }
         }
         if (wave) {
-            for (int k = 0; k < T.njobs; ++k) {
-                cudaError_t e = run_wavefront(0, s->d, P, G, T, k, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
-                                              shape.block, ctx->d_status, cs, &ctx->log);
-                if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront primal");
-            }
+            cudaError_t e = run_wavefront(0, s->d, P, G, T, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
+                                          shape.block, ctx->d_status, cs, &ctx->log);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront primal");
             continue;
         }
         const int bucket = depth_bucket(maxd[g]);
@@ -915,11 +919,9 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
             }
         }
         if (wave) {
-            for (int k = 0; k < T.njobs; ++k) {
-                cudaError_t e = run_wavefront(1, Sd, P, G, T, k, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
-                                              shape.block, ctx->d_status, cs, &ctx->log);
-                if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront adjoint");
-            }
+            cudaError_t e = run_wavefront(1, Sd, P, G, T, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
+                                          shape.block, ctx->d_status, cs, &ctx->log);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront adjoint");
             continue;
         }
         if (ctx->replay.method == DPPT_REPLAY_PPRB) {

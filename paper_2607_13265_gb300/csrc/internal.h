@@ -188,9 +188,9 @@ DPPT_DECLARE_HYBRID(16)
 #undef DPPT_DECLARE_HYBRID
 
 // wavefront schedule (wavefront.cu): workspace bytes for waves of Q paths with
-// a cache of `cap` vertices, and the run of one job of a table
+// a cache of `cap` vertices, and the run of every job of a table (several jobs share a wave)
 size_t wavefront_bytes(long long Q, int cap);
-cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T, int job,
+cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T,
                           void* ws, long long Q, int cap, int block, unsigned* status, cudaStream_t st,
                           StageLog* log);
 

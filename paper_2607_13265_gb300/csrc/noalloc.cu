@@ -29,15 +29,23 @@ constexpr int kMaxDevices = 256;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
-// Device address of g_noalloc_raw on the current device, resolved once per
-// device (in host code the array's name is only a stand-in for it).
-cudaError_t scratch_address(int device, void** out) {
+// Device address of g_noalloc_raw on the current device (in host code the array's name is
+// only a stand-in for it).  Outside stream capture it is resolved again on every call, so
+// a context torn down and recreated in between (cudaDeviceReset) cannot leave a stale
+// address; a call made while `st` is being captured reuses the address of the device's
+// last call outside capture, and fails if there was none.
+cudaError_t scratch_address(int device, cudaStream_t st, void** out) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[device]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_raw);
+        e = cudaGetSymbolAddress(&p, g_noalloc_raw);
         if (e != cudaSuccess) return e;
         g_addr[device] = p;
+    } else if (!g_addr[device]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_addr[device];
     return cudaSuccess;
@@ -91,12 +99,14 @@ extern "C" dppt_status dppt_render_primal_noalloc(dppt_ctx* ctx, const dppt_scen
     if ((scene_tex_size(scene) > 0 && !params->tex) || (S.num_ior > 0 && !params->ior) ||
         (S.num_lights > 0 && !params->le) || (S.num_sheets > 0 && !params->sheet))
         return bad(ctx, DPPT_ERR_INVALID_ARG, "params pointer is null");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     void* base = nullptr;
     if (filtered) {
-        e = scratch_address(device, &base);
-        if (e != cudaSuccess) return bad(ctx, DPPT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        e = scratch_address(device, st, &base);
+        if (e != cudaSuccess)
+            return bad(ctx, DPPT_ERR_CUDA, std::string("scratch address (make one call outside stream capture first): ") +
+                                               cudaGetErrorString(e));
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int block = 128;
     JobTable T;
     std::memset(&T, 0, sizeof T);

@@ -14,6 +14,9 @@
 // (vertex, path), whole whatever fraction of the wave's paths is still live.  Every stage
 // reads its list length from device memory and loops over it with a grid stride, so a
 // wave is a fixed sequence of launches.
+#include <algorithm>
+#include <vector>
+
 #include "trace.cuh"
 
 // resident threads per SM the traversal kernels' register allocation must allow (as blocks
@@ -146,6 +149,43 @@ struct WfLists {
     int binQ;
 };
 
+// A wave: pieces of one or more jobs (whole pixels each) laid out back to back in the wave's
+// path slots.  Piece k holds pixels pix0 .. pix0 + npix - 1 of job `job`, its paths in slots
+// q0 .. q0 + npix * spp - 1 and its pixels at wave-pixel index qpix0 onward.
+struct WaveSeg { int job, pad; long long pix0, npix, q0, qpix0; };
+struct WaveTable {
+    WaveSeg seg[kMaxJobsPerLaunch];
+    int nseg, depth;          // pieces; the largest max_depth among them
+    long long nq, npix;       // paths and pixels of the wave
+};
+// the piece holding wave slot q (pieces are sorted by q0)
+__device__ __forceinline__ int wave_piece_of_slot(const WaveTable& wt, long long q) {
+    int lo = 0, hi = wt.nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (wt.seg[mid].q0 <= q) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int wave_piece_of_pixel(const WaveTable& wt, long long i) {
+    int lo = 0, hi = wt.nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (wt.seg[mid].qpix0 <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+// starts the path of wave slot q: camera ray, path record, job-local path id
+__device__ __forceinline__ void wave_start_path(const DScene& S, const JobTable& T, const WaveTable& wt, int q,
+                                                WfState& W, Walk& w) {
+    const WaveSeg& sg = wt.seg[wave_piece_of_slot(wt, q)];
+    const DJob& J = T.job[sg.job];
+    const unsigned long long pid = (unsigned long long)(sg.pix0 * J.spp + (q - sg.q0));
+    walk_begin(S, J, pid, (long long)(pid / J.spp), w);
+    put_walk(W.walk + q, w);
+    W.meta[q] = WfMeta{(unsigned)pid, (unsigned)(pid >> 32), sg.job, 0};
+}
+
 // Replay bins: the material types with a replay kernel of their own (diffuse, rough
 // conductor, rough dielectric, polarizer and retarder sheets), and one bin for everything
 // else (smooth dielectrics, emitter hits, paths that left the scene).
@@ -157,16 +197,13 @@ constexpr unsigned kBinnedTypes = (1u << DPPT_MAT_DIFFUSE) | (1u << DPPT_MAT_CON
                                   (1u << DPPT_MAT_PLASTIC_GGX) | (1u << DPPT_MAT_POLARIZER_SHEET) |
                                   (1u << DPPT_MAT_RETARDER_SHEET);
 
-__global__ void k_wf_init(const DScene S, const __grid_constant__ JobTable T, int job, long long p0, int nq,
+__global__ void k_wf_init(const DScene S, const __grid_constant__ JobTable T, const __grid_constant__ WaveTable wt,
                           WfState W, WfLists L) {
     const int stride = gridDim.x * blockDim.x;
+    const int nq = (int)wt.nq;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
-        const DJob& J = T.job[job];
-        const unsigned long long pid = (unsigned long long)(p0 + q);
         Walk w;
-        walk_begin(S, J, pid, (long long)(pid / J.spp), w);
-        put_walk(W.walk + q, w);
-        W.meta[q] = WfMeta{(unsigned)pid, (unsigned)(pid >> 32), job, 0};
+        wave_start_path(S, T, wt, q, W, w);
         L.l0[q] = q;
         if (q == 0) L.cur[0] = nq;
     }
@@ -269,12 +306,13 @@ k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
 // registers, the vertex's surface data and samples.  The launch's block 0 zeroes the
 // counts the iteration appends to after this kernel and the next iteration's shadow
 // count (this kernel appends to this iteration's, zeroed one iteration earlier).  The
-// first iteration of a wave (FIRST) starts the wave's nq paths p0 .. p0 + nq - 1 of job
-// `job` itself: camera rays, path records and the identity cache-pass list.
+// first iteration of a wave (FIRST) starts the wave's paths itself (camera rays, path
+// records and the identity cache-pass list), from the wave's pieces of jobs.
 template <bool NM, bool FIRST>
 __global__ void __launch_bounds__(512, DPPT_WF_EXTEND_SHADE_MIN_BLOCKS)
 k_wf_extend_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, WfState W, WfLists L,
-                  int store_hits, unsigned* status, int job, long long p0, int nq) {
+                  int store_hits, unsigned* status, const __grid_constant__ WaveTable wt) {
+    const int nq = (int)wt.nq;
     const int n = FIRST ? nq : L.cur[0];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         L.nxt[0] = 0; L.nxt[4] = 0;
@@ -288,11 +326,7 @@ k_wf_extend_shade(const DScene S, const DParams P, const __grid_constant__ JobTa
         bool hit;
         Walk w;
         if (FIRST) {
-            const unsigned long long pid = (unsigned long long)(p0 + q);
-            const DJob& J = T.job[job];
-            walk_begin(S, J, pid, (long long)(pid / J.spp), w);
-            put_walk(W.walk + q, w);
-            W.meta[q] = WfMeta{(unsigned)pid, (unsigned)(pid >> 32), job, 0};
+            wave_start_path(S, T, wt, q, W, w);
             L.l0[q] = q;
             hit = trace_closest<false>(S, w.o, w.d, h, status, nullptr);
         } else {
@@ -349,8 +383,7 @@ k_wf_shadow(const DScene S, WfState W, WfLists L, unsigned* status) {
 // the bin of its next vertex.
 template <int MODE, int PHASE, bool NM, int MT = -1, int BIN = -1>
 __global__ void __launch_bounds__(128, PHASE == 1 ? DPPT_WF_REPLAY_MIN_BLOCKS : DPPT_WF_CACHE_MIN_BLOCKS)
-k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_constant__ JobTable T, WfState W, WfLists L,
-            unsigned* sig) {
+k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_constant__ JobTable T, WfState W, WfLists L) {
     extern __shared__ float sgrad[];
     if (PHASE == 1) sgrad_zero(S, sgrad);
     static_assert(PHASE == 0 || BIN >= 0, "the replay runs over one bin");
@@ -455,7 +488,7 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
                 W.arow[3 * (long long)q + c] = make_float4(vis.a[c][0], vis.a[c][1], vis.a[c][2], vis.a[c][3]);
         }
         if (done) {
-            if (sig) sig[q] = fnv(w.sig, (unsigned)w.nv);
+            if (J.sig) J.sig[(unsigned long long)m.lo | ((unsigned long long)m.hi << 32)] = fnv(w.sig, (unsigned)w.nv);
         } else {
             W.meta[q].pni = phase | (vis.n << 8) | (vis.i << 16);
             put_walk(W.walk + q, w);
@@ -464,19 +497,23 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
     if (PHASE == 1) sgrad_flush(S, G, sgrad);
 }
 
-// sums the spp paths of each pixel of a finished wave (deterministic order)
-__global__ void k_wf_pixels(const float4* raw, int spp, long long npix, float* dst) {
-    long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (pix >= npix) return;
+// sums the spp paths of each pixel of a finished wave (deterministic order) into the raw
+// image of the pixel's job, when it has one
+__global__ void k_wf_pixels(const float4* raw, const __grid_constant__ JobTable T, const __grid_constant__ WaveTable wt) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= wt.npix) return;
+    const WaveSeg& sg = wt.seg[wave_piece_of_pixel(wt, i)];
+    const DJob& J = T.job[sg.job];
+    if (!J.raw) return;
+    const long long local = i - sg.qpix0;
+    const float4* r = raw + 3 * (sg.q0 + local * J.spp);
     float4 acc[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-    for (int s = 0; s < spp; ++s) {
-        const float4* r = raw + 3 * (pix * spp + s);
+    for (int s = 0; s < J.spp; ++s)
         for (int c = 0; c < 3; ++c) {
-            float4 t = r[c];
+            const float4 t = r[3 * s + c];
             acc[c].x += t.x; acc[c].y += t.y; acc[c].z += t.z; acc[c].w += t.w;
         }
-    }
-    float4* o = reinterpret_cast<float4*>(dst + pix * 12);
+    float4* o = reinterpret_cast<float4*>(J.raw + (sg.pix0 + local) * 12);
     o[0] = acc[0]; o[1] = acc[1]; o[2] = acc[2];
 }
 
@@ -507,7 +544,6 @@ struct ReplayArgs {
     const JobTable& T;
     const WfState& W;
     const WfLists& L;
-    unsigned* sg;
     int grid;
     size_t smem;
     cudaStream_t st;
@@ -515,16 +551,44 @@ struct ReplayArgs {
 };
 template <int MT>
 static void launch_replay_bin(const ReplayArgs& a) {
-    if (a.nmaps) k_wf_finish<1, 1, true, MT, MT><<<a.grid, 128, a.smem, a.st>>>(a.S, a.P, a.G, a.T, a.W, a.L, a.sg);
-    else k_wf_finish<1, 1, false, MT, MT><<<a.grid, 128, a.smem, a.st>>>(a.S, a.P, a.G, a.T, a.W, a.L, a.sg);
+    if (a.nmaps) k_wf_finish<1, 1, true, MT, MT><<<a.grid, 128, a.smem, a.st>>>(a.S, a.P, a.G, a.T, a.W, a.L);
+    else k_wf_finish<1, 1, false, MT, MT><<<a.grid, 128, a.smem, a.st>>>(a.S, a.P, a.G, a.T, a.W, a.L);
 }
 
-// Renders (mode 0) or differentiates (mode 1) job `job` of the table in waves of
-// at most Q paths (whole pixels), writing the per-pixel raw image to J.raw.
-cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T, int job,
+// The waves of a table's jobs: the jobs in order, each cut at pixel boundaries into pieces
+// that fill waves of at most Q paths (a wave closes when the next pixel does not fit or it
+// holds kMaxJobsPerLaunch pieces).  Q must hold one pixel of every job.
+static std::vector<WaveTable> plan_waves(const JobTable& T, long long Q) {
+    std::vector<WaveTable> waves;
+    WaveTable cur{};
+    for (int k = 0; k < T.njobs; ++k) {
+        const DJob& J = T.job[k];
+        const long long npix = (long long)J.W * J.H;
+        long long pix = 0;
+        while (pix < npix) {
+            long long room = (Q - cur.nq) / J.spp;
+            if (room == 0 || cur.nseg == kMaxJobsPerLaunch) {
+                waves.push_back(cur);
+                cur = WaveTable{};
+                room = Q / J.spp;
+            }
+            const long long take = std::min(room, npix - pix);
+            cur.seg[cur.nseg++] = WaveSeg{k, 0, pix, take, cur.nq, cur.npix};
+            cur.nq += take * J.spp;
+            cur.npix += take;
+            cur.depth = std::max(cur.depth, J.depth);
+            pix += take;
+        }
+    }
+    if (cur.nseg > 0) waves.push_back(cur);
+    return waves;
+}
+
+// Renders (mode 0) or differentiates (mode 1) every job of the table in waves of at most Q
+// paths, several jobs sharing a wave, and writes each job's per-pixel raw image to J.raw.
+cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T,
                           void* ws, long long Q, int cap, int block, unsigned* status, cudaStream_t st,
                           StageLog* log) {
-    const DJob& J = T.job[job];
     char* p = static_cast<char*>(ws);
     WfState W;
     W.walk = reinterpret_cast<WfWalk*>(p); p += align_up(sizeof(WfWalk) * Q);
@@ -546,15 +610,12 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long npix = (long long)J.W * J.H;
-    const long long pix_per_wave = std::max(1LL, Q / J.spp);
     const bool nmaps = S.tri_tan != nullptr;   // the scene has normal maps: kernels with that path
     const unsigned types = (unsigned)S.mat_types;
     const int passes = mode == 1 ? 2 : 1;
     const size_t smem = mode == 1 ? sgrad_bytes(S) : 0;
-    for (long long pix0 = 0; pix0 < npix; pix0 += pix_per_wave) {
-        const long long wp = std::min(pix_per_wave, npix - pix0);
-        const int nq = (int)(wp * J.spp);
+    for (const WaveTable& wt : plan_waves(T, Q)) {
+        const int nq = (int)wt.nq;
         // stage kernels stride over their lists: a few resident waves of blocks at most
         const int grid = (int)std::min<long long>((nq + block - 1) / block, (long long)sms * (2048 / block));
         const int fgrid = (int)std::min<long long>((nq + 127) / 128, (long long)sms * DPPT_WF_CACHE_MIN_BLOCKS * 2);
@@ -565,30 +626,28 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
         int tok = 0;
 #if !DPPT_WF_FUSE_SHADE
         tok = log->begin(kStageWfInit, st);
-        k_wf_init<<<grid, block, 0, st>>>(S, T, job, pix0 * J.spp, nq, W, A);
+        k_wf_init<<<grid, block, 0, st>>>(S, T, wt, W, A);
         log->end(tok, st);
 #endif
-        unsigned* sg = J.sig ? J.sig + pix0 * J.spp : nullptr;
-        for (int it = 0; it < passes * J.depth; ++it) {
+        for (int it = 0; it < passes * wt.depth; ++it) {
             // lists, counts and bins alternate between two buffers: the next ones of an
             // iteration are the live ones of the following iteration
             const WfLists& L = (it & 1) ? B : A;
             // a path's cache pass ends by iteration depth - 1 (one vertex per iteration), and no
             // path replays before iteration 1: the launches with nothing to do are skipped
-            if (it >= J.depth) {
+            if (it >= wt.depth) {
                 // what the extend launch would have zeroed: the counts appended to next
                 if ((e = cudaMemsetAsync(L.nxt, 0, sizeof(int) * 16, st)) != cudaSuccess) return e;
             } else {
 #if DPPT_WF_FUSE_SHADE
                 tok = log->begin(kStageWfExtend, st);
                 // the first iteration also starts the wave's paths
-                const long long p0 = pix0 * J.spp;
                 if (it == 0) {
-                    if (nmaps) k_wf_extend_shade<true, true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, job, p0, nq);
-                    else k_wf_extend_shade<false, true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, job, p0, nq);
+                    if (nmaps) k_wf_extend_shade<true, true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, wt);
+                    else k_wf_extend_shade<false, true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, wt);
                 } else {
-                    if (nmaps) k_wf_extend_shade<true, false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, job, p0, nq);
-                    else k_wf_extend_shade<false, false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, job, p0, nq);
+                    if (nmaps) k_wf_extend_shade<true, false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, wt);
+                    else k_wf_extend_shade<false, false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, wt);
                 }
                 log->end(tok, st);
 #else
@@ -605,35 +664,33 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                 log->end(tok, st);
                 tok = log->begin(kStageWfCache, st);
                 if (mode == 0) {
-                    if (nmaps) k_wf_finish<0, 0, true><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
-                    else k_wf_finish<0, 0, false><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+                    if (nmaps) k_wf_finish<0, 0, true><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L);
+                    else k_wf_finish<0, 0, false><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L);
                 } else {
-                    if (nmaps) k_wf_finish<1, 0, true><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
-                    else k_wf_finish<1, 0, false><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L, sg);
+                    if (nmaps) k_wf_finish<1, 0, true><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L);
+                    else k_wf_finish<1, 0, false><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L);
                 }
                 log->end(tok, st);
             }
             if (mode == 1 && it > 0) {
                 tok = log->begin(kStageWfReplay, st);
                 // one replay kernel per binned material type present, then the other bin
-                const ReplayArgs ra{S, P, G, T, W, L, sg, fgrid, smem, st, nmaps};
+                const ReplayArgs ra{S, P, G, T, W, L, fgrid, smem, st, nmaps};
                 if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) launch_replay_bin<DPPT_MAT_CONDUCTOR_GGX>(ra);
                 if (types & (1u << DPPT_MAT_PLASTIC_GGX)) launch_replay_bin<DPPT_MAT_PLASTIC_GGX>(ra);
                 if (types & (1u << DPPT_MAT_DIFFUSE)) launch_replay_bin<DPPT_MAT_DIFFUSE>(ra);
                 if (types & (1u << DPPT_MAT_POLARIZER_SHEET)) launch_replay_bin<DPPT_MAT_POLARIZER_SHEET>(ra);
                 if (types & (1u << DPPT_MAT_RETARDER_SHEET)) launch_replay_bin<DPPT_MAT_RETARDER_SHEET>(ra);
-                if (nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
-                else k_wf_finish<1, 1, false, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L, sg);
+                if (nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L);
+                else k_wf_finish<1, 1, false, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L);
                 log->end(tok, st);
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        if (J.raw) {
-            tok = log->begin(kStageWfPixels, st);
-            k_wf_pixels<<<(int)((wp + 127) / 128), 128, 0, st>>>(W.raw, J.spp, wp, J.raw + pix0 * 12);
-            log->end(tok, st);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
+        tok = log->begin(kStageWfPixels, st);
+        k_wf_pixels<<<(int)((wt.npix + 127) / 128), 128, 0, st>>>(W.raw, T, wt);
+        log->end(tok, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

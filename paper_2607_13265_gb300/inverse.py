@@ -58,8 +58,8 @@ def main(argv=None):
     # seeded target textures and image (other random numbers than the optimization's)
     tgt = scene.params()
     (a_off, aw, ah, ach), (r_off, rw, rh, _) = scene.tex_desc[0], scene.tex_desc[1]
-    tgt["tex"][a_off:a_off + aw * ah * ach] = np.random.default_rng(30).uniform(0.2, 0.9, aw * ah * ach)
-    tgt["tex"][r_off:r_off + rw * rh] = np.random.default_rng(31).uniform(0.05, 0.5, rw * rh)
+    tgt["tex"][a_off:a_off + aw * ah * ach] = sg.smooth_texture(aw, 0.2, 0.9, 30, ach).ravel()
+    tgt["tex"][r_off:r_off + rw * rh] = sg.smooth_texture(rw, 0.05, 0.5, 31).ravel()
     tjob = copy.copy(job)
     tjob.seed = 4242
     target = api.render_primal(dctx, gs, api.pack_jobs([tjob]), api.device_params(scene, batch, tgt)).clone()

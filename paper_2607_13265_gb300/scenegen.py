@@ -460,14 +460,32 @@ def rocks_scene(freq: int = 25, num_rocks: int = 8, tex_res: int = 512, width: i
     return s, job
 
 
+def smooth_texture(res: int, lo: float, hi: float, seed: int, channels: int = 1, cells: int = 16) -> np.ndarray:
+    """Seeded value noise [res][res] (or [res][res][channels]): a cells x cells grid of
+    U[lo, hi] values, bilinearly interpolated with wrap-around at texel centres, so the
+    texture varies smoothly (one cell spans res / cells texels) and tiles seamlessly."""
+    g = np.random.default_rng(seed).uniform(lo, hi, (cells, cells, channels))
+    x = (np.arange(res) + 0.5) * cells / res - 0.5
+    i0 = np.floor(x).astype(np.int64)
+    f = x - i0
+    a, b = i0 % cells, (i0 + 1) % cells
+    rows = g[a] * (1 - f)[:, None, None] + g[b] * f[:, None, None]          # [res][cells][ch]
+    out = rows[:, a] * (1 - f)[None, :, None] + rows[:, b] * f[None, :, None]  # [res][res][ch]
+    return out[:, :, 0] if channels == 1 else out
+
+
 def large_scene(num_meshes: int = 10, freq: int = 50, tex_res: int = 1024, width: int = 1024,
                 spp: int = 128, depth: int = 12, num_angles: int = 16) -> tuple[Scene, Job]:
     """Large workload: 10 displaced meshes (seeds 10..19) mixing diffuse, rough conductor and
     rough dielectric pBRDFs, 3 polarizer sheets and 1 retarder sheet, 4 unpolarized lights,
-    1024^2x3 albedo + 1024^2 roughness maps, camera polarizer swept over 16 angles."""
+    1024^2x3 albedo (value noise in [0.2, 0.9], seed 7) + 1024^2 roughness (value noise in
+    [0.05, 0.5], seed 8) maps, camera polarizer swept over 16 angles.  The maps vary smoothly
+    (smooth_texture): a white-noise roughness map at this resolution changes the roughness
+    by up to 0.45 between texels 4e-3 scene units apart, which makes every GGX value, and so
+    the FP32 gradients, hypersensitive to the hit position."""
     s = Scene()
-    albedo = np.random.default_rng(7).uniform(0.2, 0.9, (tex_res, tex_res, 3))
-    rough = np.random.default_rng(8).uniform(0.05, 0.5, (tex_res, tex_res))
+    albedo = smooth_texture(tex_res, 0.2, 0.9, 7, 3)
+    rough = smooth_texture(tex_res, 0.05, 0.5, 8)
     ta = s.add_texture(albedo, differentiable=True)
     tr = s.add_texture(rough, differentiable=True)
     mats = [s.add_material(Material(MAT_DIFFUSE, albedo_tex=ta)),
