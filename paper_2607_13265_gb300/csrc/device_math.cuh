@@ -80,6 +80,40 @@ __device__ __forceinline__ float val(float a) { return a; }
 __device__ __forceinline__ float val(D3 a) { return a.v; }
 __device__ __forceinline__ D3 tcos(D3 a) { float s, c; sincosf(a.v, &s, &c); return {c, -s * a.d0, -s * a.d1, -s * a.d2}; }
 __device__ __forceinline__ D3 tsin(D3 a) { float s, c; sincosf(a.v, &s, &c); return {s, c * a.d0, c * a.d1, c * a.d2}; }
+// One-slot dual number: a value and its derivative with respect to one parameter (the
+// replay of a diffuse vertex, whose only differentiable material value is its albedo).
+struct D1 {
+    float v, d;
+    __device__ __forceinline__ D1() {}
+    __device__ __forceinline__ D1(float x) : v(x), d(0.f) {}
+    __device__ __forceinline__ D1(float x, float a) : v(x), d(a) {}
+};
+__device__ __forceinline__ D1 operator+(D1 a, D1 b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ D1 operator-(D1 a, D1 b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ D1 operator-(D1 a) { return {-a.v, -a.d}; }
+__device__ __forceinline__ D1 operator*(D1 a, D1 b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+__device__ __forceinline__ D1 operator*(D1 a, float s) { return {a.v * s, a.d * s}; }
+__device__ __forceinline__ D1 operator*(float s, D1 a) { return a * s; }
+__device__ __forceinline__ D1 operator+(D1 a, float s) { return {a.v + s, a.d}; }
+__device__ __forceinline__ D1 operator+(float s, D1 a) { return a + s; }
+__device__ __forceinline__ D1 operator-(D1 a, float s) { return {a.v - s, a.d}; }
+__device__ __forceinline__ D1 operator-(float s, D1 a) { return {s - a.v, -a.d}; }
+__device__ __forceinline__ D1 operator/(D1 a, D1 b) {
+    float r = 1.0f / b.v, q = a.v * r;
+    return {q, (a.d - q * b.d) * r};
+}
+__device__ __forceinline__ D1 operator/(D1 a, float s) { return a * (1.0f / s); }
+__device__ __forceinline__ D1 operator/(float s, D1 b) {
+    float r = 1.0f / b.v, q = s * r;
+    return {q, -q * b.d * r};
+}
+__device__ __forceinline__ D1 tsqrt(D1 a) {
+    float s = sqrtf(a.v);
+    return {s, a.d * (0.5f / s)};
+}
+__device__ __forceinline__ float val(D1 a) { return a.v; }
+__device__ __forceinline__ D1 tcos(D1 a) { float s, c; sincosf(a.v, &s, &c); return {c, -s * a.d}; }
+__device__ __forceinline__ D1 tsin(D1 a) { float s, c; sincosf(a.v, &s, &c); return {s, c * a.d}; }
 __device__ __forceinline__ float tcos(float a) { return cosf(a); }
 __device__ __forceinline__ float tsin(float a) { return sinf(a); }
 

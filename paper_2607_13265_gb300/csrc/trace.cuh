@@ -438,6 +438,12 @@ template <class V> __device__ __forceinline__ void compact_row(const Compact<flo
     a[3] = u[2] * W.S[c] + u[3] * W.C[c];
     rot_apply_row(W.ri, a);
 }
+__device__ __forceinline__ Compact<float> compact_value(const Compact<D1>& W) {
+    Compact<float> r;
+    r.ri = {W.ri.c.v, W.ri.s.v}; r.ro = {W.ro.c.v, W.ro.s.v};
+    for (int c = 0; c < 3; ++c) { r.A[c] = W.A[c].v; r.B[c] = W.B[c].v; r.C[c] = W.C[c].v; r.S[c] = W.S[c].v; r.D[c] = W.D[c].v; }
+    return r;
+}
 __device__ __forceinline__ Compact<float> compact_value(const Compact<D3>& W) {
     Compact<float> r;
     r.ri = {W.ri.c.v, W.ri.s.v}; r.ro = {W.ro.c.v, W.ro.s.v};
@@ -451,6 +457,15 @@ template <class T> __device__ __forceinline__ T seeded(float v, int slot) {
 template <> __device__ __forceinline__ D3 seeded<D3>(float v, int slot) {
     return D3(v, slot == 0 ? 1.0f : 0.0f, slot == 1 ? 1.0f : 0.0f, slot == 2 ? 1.0f : 0.0f);
 }
+// D1 carries slot 2 (the channel albedo) alone
+template <> __device__ __forceinline__ D1 seeded<D1>(float v, int slot) { return D1(v, slot == 2 ? 1.0f : 0.0f); }
+// the derivatives of the three slots (roughness or sheet angle, index of refraction, albedo)
+__device__ __forceinline__ float dslot0(const D3& x) { return x.d0; }
+__device__ __forceinline__ float dslot1(const D3& x) { return x.d1; }
+__device__ __forceinline__ float dslot2(const D3& x) { return x.d2; }
+__device__ __forceinline__ float dslot0(const D1&) { return 0.0f; }
+__device__ __forceinline__ float dslot1(const D1&) { return 0.0f; }
+__device__ __forceinline__ float dslot2(const D1& x) { return x.d; }
 
 // s axis of a reflection/refraction: normal to the plane of (a, b), or any
 // axis normal to a when the plane degenerates
@@ -623,8 +638,8 @@ __device__ void eval_vertex(const DScene& S, const DParams& P, const VCtx& vc, f
             bsdf_compact<T>(S, P, m, vc, vc.wl, f);
         }
         Compact<float> fv;
-        if constexpr (sizeof(T) == sizeof(float)) fv = *reinterpret_cast<Compact<float>*>(&f);
-        else fv = compact_value(*reinterpret_cast<Compact<D3>*>(&f));
+        if constexpr (std::is_same<T, float>::value) fv = f;
+        else fv = compact_value(f);
         for (int c = 0; c < 3; ++c) {
             const float* le = P.le + 12 * vc.nee_light + 4 * c;
             float v[4] = {__ldg(le), __ldg(le + 1), __ldg(le + 2), __ldg(le + 3)};
@@ -986,7 +1001,15 @@ __device__ __forceinline__ void sgrad_flush(const DScene& S, const DGrads& G, co
 // instruction fetch, and sixteen inlined copies of the grouping code would enlarge them.
 // The megakernels are bound by their thread-local cache and run faster unrolled.
 template <int NC, bool UNROLL>
-__device__ __forceinline__ void scatter_taps(float* g, const Taps& tp, const float* vals, int ch, bool per_lane) {
+__device__ __forceinline__ void scatter_taps(float* g, const Taps& tp0, const float* vals, int ch, bool per_lane) {
+    // taps on the same texel (a texture one or two texels wide, wrapped) are merged first,
+    // and a zero value issues no atomic
+    Taps tp = tp0;
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < k; ++j)
+            if (tp.w[k] != 0.0f && tp.idx[k] == tp.idx[j]) { tp.w[j] += tp.w[k]; tp.w[k] = 0.0f; }
     if (UNROLL) {
 #pragma unroll
         for (int c = 0; c < NC; ++c)
@@ -994,11 +1017,9 @@ __device__ __forceinline__ void scatter_taps(float* g, const Taps& tp, const flo
             for (int k = 0; k < 4; ++k) {
                 const float v = vals[c] * tp.w[k];
                 const long long idx = tp.idx[k] + min(c, ch - 1);
-                if (per_lane) {
-                    if (v != 0.0f) atomicAdd(g + idx, v);
-                } else {
-                    atomic_add_grouped(g, idx, v);
-                }
+                if (v == 0.0f) continue;
+                if (per_lane) atomicAdd(g + idx, v);
+                else atomic_add_grouped(g, idx, v);
             }
     } else {
 #pragma unroll 1
@@ -1007,11 +1028,9 @@ __device__ __forceinline__ void scatter_taps(float* g, const Taps& tp, const flo
             for (int k = 0; k < 4; ++k) {
                 const float v = vals[c] * tp.w[k];
                 const long long idx = tp.idx[k] + min(c, ch - 1);
-                if (per_lane) {
-                    if (v != 0.0f) atomicAdd(g + idx, v);
-                } else {
-                    atomic_add_grouped(g, idx, v);
-                }
+                if (v == 0.0f) continue;
+                if (per_lane) atomicAdd(g + idx, v);
+                else atomic_add_grouped(g, idx, v);
             }
     }
 }
@@ -1117,28 +1136,29 @@ struct GlobalCache {
 // per channel J_c = a_c^T (W_c L_c + f_c Le_c nee_w) (W and the NEE operator f from
 // eval_vertex<D3>, Ln the suffix L[v+1]); returns the three slots' derivatives, the third
 // per channel.
-__device__ __forceinline__ void local_vjp(const DScene& S, const DParams& P, const VCtx& vc, const Compact<D3>& W,
-                                          const Compact<D3>& f, const Rot<float>& Rle, const float Ln[3][4],
+template <class DT>
+__device__ __forceinline__ void local_vjp(const DScene& S, const DParams& P, const VCtx& vc, const Compact<DT>& W,
+                                          const Compact<DT>& f, const Rot<float>& Rle, const float Ln[3][4],
                                           const float a[3][4], float& g0, float& g1, float g2[3]) {
     g0 = g1 = 0.0f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        D3 x[4] = {D3(Ln[c][0]), D3(Ln[c][1]), D3(Ln[c][2]), D3(Ln[c][3])};
-        D3 y[4];
+        DT x[4] = {DT(Ln[c][0]), DT(Ln[c][1]), DT(Ln[c][2]), DT(Ln[c][3])};
+        DT y[4];
         compact_apply(W, c, x, y);
-        D3 J = y[0] * a[c][0] + y[1] * a[c][1] + y[2] * a[c][2] + y[3] * a[c][3];
+        DT J = y[0] * a[c][0] + y[1] * a[c][1] + y[2] * a[c][2] + y[3] * a[c][3];
         if (vc.nee) {
             const float* le = P.le + 12 * vc.nee_light + 4 * c;
             float lv[4] = {__ldg(le), __ldg(le + 1), __ldg(le + 2), __ldg(le + 3)};
             rot_apply(Rle, lv);
-            D3 xe[4] = {D3(lv[0] * vc.nee_w), D3(lv[1] * vc.nee_w), D3(lv[2] * vc.nee_w), D3(lv[3] * vc.nee_w)};
-            D3 ye[4];
+            DT xe[4] = {DT(lv[0] * vc.nee_w), DT(lv[1] * vc.nee_w), DT(lv[2] * vc.nee_w), DT(lv[3] * vc.nee_w)};
+            DT ye[4];
             compact_apply(f, c, xe, ye);
             J = J + ye[0] * a[c][0] + ye[1] * a[c][1] + ye[2] * a[c][2] + ye[3] * a[c][3];
         }
-        g0 += J.d0;
-        g1 += J.d1;
-        g2[c] = J.d2;
+        g0 += dslot0(J);
+        g1 += dslot1(J);
+        g2[c] = dslot2(J);
     }
 }
 
@@ -1166,9 +1186,9 @@ __device__ __noinline__ void normal_map_vjp(const DScene& S, const DParams& P, c
 // the adjoint row's advance a^T <- a^T W_v.  W and f come from eval_vertex<D3> with the
 // material's own slots.  At a normal-mapped vertex a second evaluation, whose slots carry
 // the map value n, gives the normal map's texel derivatives.
-template <int MT = -1, bool NM = true, bool UNROLL = true>
+template <int MT = -1, bool NM = true, bool UNROLL = true, class DT = D3>
 __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, const DGrads& G_, float* sgrad,
-                                           const VCtx& vc, const Compact<D3>& W, const Compact<D3>& f,
+                                           const VCtx& vc, const Compact<DT>& W, const Compact<DT>& f,
                                            const float Ln[3][4], float a[3][4]) {
     const DScene* S = &S_;
     const DParams* P = &P_;
@@ -1300,9 +1320,11 @@ struct PathVis {
     }
 
     __device__ void replay_vertex(const VCtx& vc) {
+        // a diffuse vertex has one differentiable material value (its albedo): a one-slot dual
+        using DT = typename std::conditional<MT == DPPT_MAT_DIFFUSE, D1, D3>::type;
         float E[3][4];
-        Compact<D3> W, f;
-        eval_vertex<D3, MT, NM>(*S, *P, vc, E, W, &f);
+        Compact<DT> W, f;
+        eval_vertex<DT, MT, NM>(*S, *P, vc, E, W, &f);
         float Ln[3][4];
         if (i + 1 < n) {
             C.get_e(i + 1, &Ln[0][0]);
@@ -1310,7 +1332,7 @@ struct PathVis {
 #pragma unroll
             for (int k = 0; k < 12; ++k) Ln[k >> 2][k & 3] = 0.0f;
         }
-        replay_vjp<MT, NM, Cache::kUnrollScatter>(*S, *P, *G, sgrad, vc, W, f, Ln, a);
+        replay_vjp<MT, NM, Cache::kUnrollScatter, DT>(*S, *P, *G, sgrad, vc, W, f, Ln, a);
     }
 };
 

@@ -32,6 +32,15 @@
 #ifndef DPPT_WF_REPLAY_MIN_BLOCKS
 #define DPPT_WF_REPLAY_MIN_BLOCKS 4
 #endif
+// the same for the replay kernel of diffuse vertices, the simplest material (5 -> at most
+// 102 registers)
+#ifndef DPPT_WF_REPLAY_DIFFUSE_MIN_BLOCKS
+#define DPPT_WF_REPLAY_DIFFUSE_MIN_BLOCKS 4
+#endif
+// the replay prefetches into L2 the records it reads after shading its vertex (1) or not (0)
+#ifndef DPPT_WF_PREFETCH
+#define DPPT_WF_PREFETCH 1
+#endif
 // resident 512-thread blocks per SM the shade kernel's register allocation must allow
 // (2 -> at most 64 registers per thread)
 // resident 512-thread blocks per SM the fused extend + shade kernel's registers must allow
@@ -235,6 +244,11 @@ k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
     }
 }
 
+// Hints the memory system to bring the 32-byte sector at p into L2 (no register is written).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Appends path q to the next iteration's replay bin b.  Appends are warp-aggregated: the
 // lanes of a warp going to the same bin take consecutive slots with one atomic.
 __device__ __forceinline__ void bin_append(const WfLists& L, int b, int q) {
@@ -382,7 +396,9 @@ k_wf_shadow(const DScene S, WfState W, WfLists L, unsigned* status) {
 // sample visibility (no vertex record, no traversal) and appends each continuing path to
 // the bin of its next vertex.
 template <int MODE, int PHASE, bool NM, int MT = -1, int BIN = -1>
-__global__ void __launch_bounds__(128, PHASE == 1 ? DPPT_WF_REPLAY_MIN_BLOCKS : DPPT_WF_CACHE_MIN_BLOCKS)
+__global__ void __launch_bounds__(128, PHASE == 0 ? DPPT_WF_CACHE_MIN_BLOCKS
+                                                  : MT == DPPT_MAT_DIFFUSE ? DPPT_WF_REPLAY_DIFFUSE_MIN_BLOCKS
+                                                                           : DPPT_WF_REPLAY_MIN_BLOCKS)
 k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_constant__ JobTable T, WfState W, WfLists L) {
     extern __shared__ float sgrad[];
     if (PHASE == 1) sgrad_zero(S, sgrad);
@@ -397,6 +413,20 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
         const DJob& J = T.job[m.job];
         Walk w;
         get_walk(W.walk + q, w);
+        if (PHASE == 1 && DPPT_WF_PREFETCH) {
+            // what the replay reads once it has shaded its vertex: the vertex's hit and
+            // visibility, the adjoint row, and the next vertex's cached suffix L[v+1]
+            const char* rec = reinterpret_cast<const char*>(W.cache + ((long long)(w.v - 1) * W.Q + q) * kWfCacheComps);
+            prefetch_l2(rec + 4 * kWfVisComp);
+            prefetch_l2(rec + 4 * kWfHitComp);
+            prefetch_l2(reinterpret_cast<const char*>(W.arow + 3 * (long long)q));
+            prefetch_l2(reinterpret_cast<const char*>(W.arow + 3 * (long long)q) + 32);
+            if (w.v < W.cap) {
+                const char* nxt = reinterpret_cast<const char*>(W.cache + ((long long)w.v * W.Q + q) * kWfCacheComps);
+                prefetch_l2(nxt);
+                prefetch_l2(nxt + 32);
+            }
+        }
         PathVis<GlobalCache, MT, NM> vis;
         vis.S = &S; vis.P = &P; vis.G = &G; vis.sgrad = sgrad;
         vis.C.base = W.cache; vis.C.Q = W.Q; vis.C.q = q; vis.C.cap = W.cap;
