@@ -428,8 +428,13 @@ def run_views(args, api, dctx, rank, world, dev, clk_index, peaks):
     stages = dctx.stage_stats(timing=False, reset=True)
     total_ms = max_over_ranks(sum(step_ms), world, dev)
     if args.kernels_only:
+        # work units of one step's adjoint and primal passes and the number of steps the
+        # process ran (warm-up, capture warm-up, timed, staged): what a profiler's per-launch
+        # counters are divided by to give per-unit figures
         return {"value": weak_scaling_value(path_counts(jobs)[0], world, K, total_ms), "ms_per_step": total_ms / K,
-                "stages": {k: v for k, v in stages.items() if v[0]}}
+                "stages": {k: v for k, v in stages.items() if v[0]}, "launch": list(lc),
+                "steps_run": 2 * args.warmup + K + KS, "work_adjoint": api.count_work(dctx, gs, adj, P),
+                "work_primal": api.count_work(dctx, gs, rb, P)}
     counted, traced = path_counts(jobs)
     value = weak_scaling_value(counted, world, K, total_ms)
     clocks = clk.summary()
@@ -597,9 +602,10 @@ def run_icosphere(args, api, dctx, rank, dev, peaks):
     import numpy as np
     import torch
     from paper_2607_13265_gb300 import scenegen as sg
-    scene, job = sg.icosphere_scene()
+    kw = {"width": max(8, int(round(256 * args.scale)))} if args.scale != 1.0 else {}
+    scene, job = sg.icosphere_scene(**kw)
     job.stream = rank
-    target_scene, tjob = sg.icosphere_scene()
+    target_scene, tjob = sg.icosphere_scene(**kw)
     tp = target_scene.params()
     rng = np.random.default_rng(100)
     for t in (0, 1):
@@ -610,7 +616,12 @@ def run_icosphere(args, api, dctx, rank, dev, peaks):
     batch = api.pack_jobs([job])
     adj = api.pack_jobs(api.adjoint_jobs([job]))
     P = api.device_params(scene, batch)
-    tuning = api.autotune(dctx, gs, adj, P, reps=2)
+    tuning = None
+    if args.schedule is not None:
+        dctx.set_launch(args.schedule, args.block, 0, args.adj_schedule if args.adj_schedule is not None
+                        else args.schedule, args.adj_block or args.block, 0, args.adj_scatter)
+    else:
+        tuning = api.autotune(dctx, gs, adj, P, reps=2)
     lc = dctx.get_launch()
     tjob.seed = 12345
     target = api.render_primal(dctx, gs, api.pack_jobs([tjob]), api.device_params(scene, batch, tp)).clone()
@@ -648,7 +659,8 @@ def run_icosphere(args, api, dctx, rank, dev, peaks):
     return {"workload": ICO_WORKLOAD, "paths_per_s": paths * K / (ms / 1000.0), "ms_per_step": ms / K,
             "paths_per_step": paths,
             "schedule": {"primal": [api.SCHEDULE_NAMES[lc[0]], lc[1]], "adjoint": [api.SCHEDULE_NAMES[lc[3]], lc[4]],
-                         "adjoint_texel_scatter": ("warp", "lane")[lc[6]], "chosen_by": "autotuner"},
+                         "adjoint_texel_scatter": ("warp", "lane")[lc[6]],
+                         "chosen_by": "autotuner" if tuning else "command line"},
             "stages": stage_report(stages, flops, cbytes, K),
             "roofline": roofline_of(stages, flops, cbytes, props, peaks, {}, ICO_WORKLOAD, work),
             "memory": {"workspace_bytes": dctx.query_workspace(adj),
@@ -657,7 +669,7 @@ def run_icosphere(args, api, dctx, rank, dev, peaks):
                        "megakernel_local_bytes_per_thread": fp["local_bytes_per_thread"],
                        "megakernel_adjoint_registers": fp["registers"]},
             "gpu_launches": int(sum(n for n, _ in stages.values())),
-            "tuning_times_ms": tuning["times_ms"]}
+            "tuning_times_ms": tuning["times_ms"] if tuning else None}
 
 
 def run_native(args):
@@ -677,11 +689,15 @@ def run_native(args):
     dev = torch.device("cuda", local)
     peaks = load_peaks()
     dctx = api.Context(local)
-    views = run_views(args, api, dctx, rank, world, dev, local, peaks)
     if args.kernels_only:
+        out = run_views(args, api, dctx, rank, world, dev, local, peaks) if args.only != "icosphere" else {}
+        if not args.no_icosphere and args.only != "views":
+            ico = run_icosphere(args, api, dctx, rank, dev, peaks)
+            out["icosphere"] = {k: ico[k] for k in ("paths_per_s", "ms_per_step", "stages", "schedule")}
         if rank == 0:
-            print(json.dumps(views))
+            print(json.dumps(out))
         return
+    views = run_views(args, api, dctx, rank, world, dev, local, peaks)
     ico = None if args.no_icosphere else run_icosphere(args, api, dctx, rank, dev, peaks)
     result = {
         "metric": METRIC, "value": views["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -751,7 +767,9 @@ def main():
     ap.add_argument("--no-icosphere", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="image sides scaled (tests and profiling captures only)")
     ap.add_argument("--kernels-only", action="store_true",
-                    help="profiling captures: the batched steps only (no plain form, memory, end to end or CPU leg)")
+                    help="profiling captures: the timed steps only (no plain form, memory, end to end or CPU leg)")
+    ap.add_argument("--only", choices=["views", "icosphere"], default=None,
+                    help="with --kernels-only: one workload (--scale shrinks the icosphere's image too)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -114,6 +114,40 @@ __device__ __forceinline__ D1 tsqrt(D1 a) {
 __device__ __forceinline__ float val(D1 a) { return a.v; }
 __device__ __forceinline__ D1 tcos(D1 a) { float s, c; sincosf(a.v, &s, &c); return {c, -s * a.d}; }
 __device__ __forceinline__ D1 tsin(D1 a) { float s, c; sincosf(a.v, &s, &c); return {s, c * a.d}; }
+// Two-slot dual number: derivatives with respect to slots 0 and 2 (the replay of a rough
+// conductor: roughness and albedo tint; its complex index of refraction is a constant).
+struct D2 {
+    float v, d0, d2;
+    __device__ __forceinline__ D2() {}
+    __device__ __forceinline__ D2(float x) : v(x), d0(0.f), d2(0.f) {}
+    __device__ __forceinline__ D2(float x, float a, float c) : v(x), d0(a), d2(c) {}
+};
+__device__ __forceinline__ D2 operator+(D2 a, D2 b) { return {a.v + b.v, a.d0 + b.d0, a.d2 + b.d2}; }
+__device__ __forceinline__ D2 operator-(D2 a, D2 b) { return {a.v - b.v, a.d0 - b.d0, a.d2 - b.d2}; }
+__device__ __forceinline__ D2 operator-(D2 a) { return {-a.v, -a.d0, -a.d2}; }
+__device__ __forceinline__ D2 operator*(D2 a, D2 b) { return {a.v * b.v, a.d0 * b.v + a.v * b.d0, a.d2 * b.v + a.v * b.d2}; }
+__device__ __forceinline__ D2 operator*(D2 a, float s) { return {a.v * s, a.d0 * s, a.d2 * s}; }
+__device__ __forceinline__ D2 operator*(float s, D2 a) { return a * s; }
+__device__ __forceinline__ D2 operator+(D2 a, float s) { return {a.v + s, a.d0, a.d2}; }
+__device__ __forceinline__ D2 operator+(float s, D2 a) { return a + s; }
+__device__ __forceinline__ D2 operator-(D2 a, float s) { return {a.v - s, a.d0, a.d2}; }
+__device__ __forceinline__ D2 operator-(float s, D2 a) { return {s - a.v, -a.d0, -a.d2}; }
+__device__ __forceinline__ D2 operator/(D2 a, D2 b) {
+    float r = 1.0f / b.v, q = a.v * r;
+    return {q, (a.d0 - q * b.d0) * r, (a.d2 - q * b.d2) * r};
+}
+__device__ __forceinline__ D2 operator/(D2 a, float s) { return a * (1.0f / s); }
+__device__ __forceinline__ D2 operator/(float s, D2 b) {
+    float r = 1.0f / b.v, q = s * r;
+    return {q, -q * b.d0 * r, -q * b.d2 * r};
+}
+__device__ __forceinline__ D2 tsqrt(D2 a) {
+    float s = sqrtf(a.v), h = 0.5f / s;
+    return {s, a.d0 * h, a.d2 * h};
+}
+__device__ __forceinline__ float val(D2 a) { return a.v; }
+__device__ __forceinline__ D2 tcos(D2 a) { float s, c; sincosf(a.v, &s, &c); return {c, -s * a.d0, -s * a.d2}; }
+__device__ __forceinline__ D2 tsin(D2 a) { float s, c; sincosf(a.v, &s, &c); return {s, c * a.d0, c * a.d2}; }
 __device__ __forceinline__ float tcos(float a) { return cosf(a); }
 __device__ __forceinline__ float tsin(float a) { return sinf(a); }
 

@@ -114,7 +114,36 @@ __device__ __forceinline__ f3 safe_inv(f3 d) { return {safe_rcp(d.x), safe_rcp(d
 // lanes of its warp have not, and the warp then tests leaves together.
 constexpr int kTravDone = 0x7fffffff;   // stack sentinel: traversal finished
 
-__device__ __forceinline__ int trav_pop(const int* stack, int& sp) { return sp > 0 ? stack[--sp] : kTravDone; }
+// Traversal stacks.  LocalStack keeps all kBvhStack entries in thread-local memory.
+// SharedStack keeps the top kShStack entries in the block's shared memory -- entry j of
+// thread t at sh[j * blockDim.x], sh pointing at the thread's column, so the lanes of a warp
+// use consecutive banks -- and the deeper ones in thread-local memory; the wavefront's
+// traversal kernels use it when DPPT_TRAV_SHARED_STACK > 0.  Measured on the icosphere
+// workload, 16 or 8 shared entries made the fused extend + shade stage slower (5.22 vs 4.95
+// ms per step: the shared memory takes L1 capacity from the node fetches), so it is off.
+#ifndef DPPT_TRAV_SHARED_STACK
+#define DPPT_TRAV_SHARED_STACK 0
+#endif
+constexpr int kShStack = DPPT_TRAV_SHARED_STACK > 0 ? DPPT_TRAV_SHARED_STACK : 1;
+struct LocalStack {
+    int s[kBvhStack];
+    __device__ __forceinline__ void put(int i, int v) { s[i] = v; }
+    __device__ __forceinline__ int get(int i) const { return s[i]; }
+};
+struct SharedStack {
+    int* sh;
+    int loc[kBvhStack - kShStack];
+    __device__ __forceinline__ void put(int i, int v) {
+        if (i < kShStack) sh[i * blockDim.x] = v;
+        else loc[i - kShStack] = v;
+    }
+    __device__ __forceinline__ int get(int i) const { return i < kShStack ? sh[i * blockDim.x] : loc[i - kShStack]; }
+};
+// dynamic shared memory of a traversal kernel launched with `block` threads
+inline size_t trav_stack_smem(int block) { return DPPT_TRAV_SHARED_STACK > 0 ? sizeof(int) * kShStack * (size_t)block : 0; }
+
+template <class St>
+__device__ __forceinline__ int trav_pop(const St& st, int& sp) { return sp > 0 ? st.get(--sp) : kTravDone; }
 
 // Traversal state of one ray, kept in registers between rounds (the stack is the
 // caller's thread-local array).  t: best hit so far (closest) or the ray's tmax (any);
@@ -141,8 +170,8 @@ __device__ __forceinline__ void trav_begin(Trav& r, f3 o, f3 d, float t) {
 // (and, while it waits, every lane of the warp in the round) has a leaf, then the leaves,
 // including further leaves met on the stack.  ANY: stop at the first hit in (0, t).
 // Returns true when the ray's traversal is complete.
-template <bool ANY, bool COUNT>
-__device__ __forceinline__ bool trav_round(const DScene& S, Trav& r, int* stack, unsigned* status, WorkCount* wc) {
+template <bool ANY, bool COUNT, class St>
+__device__ __forceinline__ bool trav_round(const DScene& S, Trav& r, St& stack, unsigned* status, WorkCount* wc) {
     int leaf = kTravDone;
     while (r.ref >= 0 && r.ref != kTravDone) {
         const float4* nd = S.nodes + 4 * r.ref;
@@ -155,7 +184,7 @@ __device__ __forceinline__ bool trav_round(const DScene& S, Trav& r, int* stack,
             int nr = cl, fr = cr;
             if (!ANY && tr < tl) { nr = cr; fr = cl; }
             if (r.sp >= kBvhStack) { atomicOr(status, kStatusStackOverflow); r.ref = kTravDone; return true; }
-            stack[r.sp++] = fr;
+            stack.put(r.sp++, fr);
             r.ref = nr;
         } else if (hl) r.ref = cl;
         else if (hr) r.ref = cr;
@@ -193,8 +222,8 @@ __device__ __forceinline__ bool trav_round(const DScene& S, Trav& r, int* stack,
 __device__ __forceinline__ void cswap(float& ta, int& ra, float& tb, int& rb) {
     if (tb < ta) { float t = ta; ta = tb; tb = t; int r = ra; ra = rb; rb = r; }
 }
-template <bool ANY, bool COUNT>
-__device__ __forceinline__ bool trav4_round(const DScene& S, Trav& r, int* stack, unsigned* status, WorkCount* wc) {
+template <bool ANY, bool COUNT, class St>
+__device__ __forceinline__ bool trav4_round(const DScene& S, Trav& r, St& stack, unsigned* status, WorkCount* wc) {
     int leaf = kTravDone;
     while (r.ref >= 0 && r.ref != kTravDone) {
         const float4* nd = S.nodes4 + 8 * r.ref;
@@ -234,7 +263,7 @@ __device__ __forceinline__ bool trav4_round(const DScene& S, Trav& r, int* stack
             if (c[k] == kTravDone) continue;
             if (next != kTravDone) {
                 if (r.sp >= kBvhStack) { atomicOr(status, kStatusStackOverflow); r.ref = kTravDone; return true; }
-                stack[r.sp++] = next;
+                stack.put(r.sp++, next);
             }
             next = c[k];
         }
@@ -263,8 +292,8 @@ __device__ __forceinline__ bool trav4_round(const DScene& S, Trav& r, int* stack
 }
 
 // the traversal of the build's BVH layout
-template <bool ANY, bool COUNT>
-__device__ __forceinline__ bool trav_step(const DScene& S, Trav& r, int* stack, unsigned* status, WorkCount* wc) {
+template <bool ANY, bool COUNT, class St>
+__device__ __forceinline__ bool trav_step(const DScene& S, Trav& r, St& stack, unsigned* status, WorkCount* wc) {
     if (DPPT_BVH4) return trav4_round<ANY, COUNT>(S, r, stack, status, wc);
     return trav_round<ANY, COUNT>(S, r, stack, status, wc);
 }
@@ -285,14 +314,14 @@ __device__ __forceinline__ bool trav_spheres_any(const DScene& S, f3 o, f3 d, fl
     return false;
 }
 
-// closest hit; ties in t go to the lower primitive id (triangles before spheres)
-template <bool COUNT>
-__device__ bool trace_closest(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* status, WorkCount* wc) {
+// closest hit; ties in t go to the lower primitive id (triangles before spheres).  St: the
+// traversal stack (LocalStack, or SharedStack in kernels that provide shared memory for it).
+template <bool COUNT, class St>
+__device__ bool trace_closest_with(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* status, WorkCount* wc, St& stack) {
     if (COUNT) { wc->rays++; wc->sph_tests += S.num_spheres; }
     Trav r;
     trav_begin(r, o, d, FLT_MAX);
     if (S.num_tris > 0) {
-        int stack[kBvhStack];
         while (!trav_step<false, COUNT>(S, r, stack, status, wc)) {
         }
     }
@@ -300,19 +329,28 @@ __device__ bool trace_closest(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* 
     h.t = r.t; h.prim = r.prim; h.slot = r.slot; h.b1 = r.b1; h.b2 = r.b2;
     return h.prim >= 0;
 }
+template <bool COUNT>
+__device__ bool trace_closest(const DScene& S, f3 o, f3 d, HitRec& h, unsigned* status, WorkCount* wc) {
+    LocalStack stack;
+    return trace_closest_with<COUNT>(S, o, d, h, status, wc, stack);
+}
 
 // any hit in (0, tmax)
-template <bool COUNT>
-__device__ bool trace_any(const DScene& S, f3 o, f3 d, float tmax, unsigned* status, WorkCount* wc) {
+template <bool COUNT, class St>
+__device__ bool trace_any_with(const DScene& S, f3 o, f3 d, float tmax, unsigned* status, WorkCount* wc, St& stack) {
     if (COUNT) { wc->shadow_rays++; wc->shadow_sph_tests += S.num_spheres; }
     if (trav_spheres_any(S, o, d, tmax)) return true;
     if (S.num_tris == 0) return false;
     Trav r;
     trav_begin(r, o, d, tmax);
-    int stack[kBvhStack];
     while (!trav_step<true, COUNT>(S, r, stack, status, wc)) {
     }
     return r.prim >= 0;
+}
+template <bool COUNT>
+__device__ bool trace_any(const DScene& S, f3 o, f3 d, float tmax, unsigned* status, WorkCount* wc) {
+    LocalStack stack;
+    return trace_any_with<COUNT>(S, o, d, tmax, status, wc, stack);
 }
 
 // ================================================================== textures
@@ -444,6 +482,12 @@ __device__ __forceinline__ Compact<float> compact_value(const Compact<D1>& W) {
     for (int c = 0; c < 3; ++c) { r.A[c] = W.A[c].v; r.B[c] = W.B[c].v; r.C[c] = W.C[c].v; r.S[c] = W.S[c].v; r.D[c] = W.D[c].v; }
     return r;
 }
+__device__ __forceinline__ Compact<float> compact_value(const Compact<D2>& W) {
+    Compact<float> r;
+    r.ri = {W.ri.c.v, W.ri.s.v}; r.ro = {W.ro.c.v, W.ro.s.v};
+    for (int c = 0; c < 3; ++c) { r.A[c] = W.A[c].v; r.B[c] = W.B[c].v; r.C[c] = W.C[c].v; r.S[c] = W.S[c].v; r.D[c] = W.D[c].v; }
+    return r;
+}
 __device__ __forceinline__ Compact<float> compact_value(const Compact<D3>& W) {
     Compact<float> r;
     r.ri = {W.ri.c.v, W.ri.s.v}; r.ro = {W.ro.c.v, W.ro.s.v};
@@ -457,8 +501,11 @@ template <class T> __device__ __forceinline__ T seeded(float v, int slot) {
 template <> __device__ __forceinline__ D3 seeded<D3>(float v, int slot) {
     return D3(v, slot == 0 ? 1.0f : 0.0f, slot == 1 ? 1.0f : 0.0f, slot == 2 ? 1.0f : 0.0f);
 }
-// D1 carries slot 2 (the channel albedo) alone
+// D1 carries slot 2 (the channel albedo) alone, D2 slots 0 and 2
 template <> __device__ __forceinline__ D1 seeded<D1>(float v, int slot) { return D1(v, slot == 2 ? 1.0f : 0.0f); }
+template <> __device__ __forceinline__ D2 seeded<D2>(float v, int slot) {
+    return D2(v, slot == 0 ? 1.0f : 0.0f, slot == 2 ? 1.0f : 0.0f);
+}
 // the derivatives of the three slots (roughness or sheet angle, index of refraction, albedo)
 __device__ __forceinline__ float dslot0(const D3& x) { return x.d0; }
 __device__ __forceinline__ float dslot1(const D3& x) { return x.d1; }
@@ -466,6 +513,9 @@ __device__ __forceinline__ float dslot2(const D3& x) { return x.d2; }
 __device__ __forceinline__ float dslot0(const D1&) { return 0.0f; }
 __device__ __forceinline__ float dslot1(const D1&) { return 0.0f; }
 __device__ __forceinline__ float dslot2(const D1& x) { return x.d; }
+__device__ __forceinline__ float dslot0(const D2& x) { return x.d0; }
+__device__ __forceinline__ float dslot1(const D2&) { return 0.0f; }
+__device__ __forceinline__ float dslot2(const D2& x) { return x.d2; }
 
 // s axis of a reflection/refraction: normal to the plane of (a, b), or any
 // axis normal to a when the plane degenerates
@@ -1320,8 +1370,10 @@ struct PathVis {
     }
 
     __device__ void replay_vertex(const VCtx& vc) {
-        // a diffuse vertex has one differentiable material value (its albedo): a one-slot dual
-        using DT = typename std::conditional<MT == DPPT_MAT_DIFFUSE, D1, D3>::type;
+        // a diffuse vertex has one differentiable material value (its albedo), a rough
+        // conductor two (roughness and albedo tint): duals with only those slots
+        using DT = typename std::conditional<MT == DPPT_MAT_DIFFUSE, D1,
+                   typename std::conditional<MT == DPPT_MAT_CONDUCTOR_GGX, D2, D3>::type>::type;
         float E[3][4];
         Compact<DT> W, f;
         eval_vertex<DT, MT, NM>(*S, *P, vc, E, W, &f);

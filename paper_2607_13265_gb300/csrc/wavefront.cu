@@ -218,6 +218,16 @@ __global__ void k_wf_init(const DScene S, const __grid_constant__ JobTable T, co
     }
 }
 
+// The traversal stack of the wavefront's traversal kernels: its top in shared memory (the
+// launch passes trav_stack_smem(block) bytes of dynamic shared memory), unless
+// DPPT_TRAV_SHARED_STACK is 0.
+using WfStack = std::conditional<(DPPT_TRAV_SHARED_STACK > 0), SharedStack, LocalStack>::type;
+__device__ __forceinline__ void stack_init(LocalStack&) {}
+__device__ __forceinline__ void stack_init(SharedStack& st) {
+    extern __shared__ int trav_sh[];
+    st.sh = trav_sh + threadIdx.x;
+}
+
 // Closest hits of the live paths, one ray per thread in a grid-stride loop.  The list
 // keeps the samples of a pixel together, so a warp's rays share their origin.  Only the
 // cache pass traces: the replay reads its hits from the cache (kWfHitComp).
@@ -234,7 +244,9 @@ k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
         const float4 a = W.walk[q].a, b = W.walk[q].b;
         HitRec h;
         float4 out;
-        if (trace_closest<false>(S, f3{a.x, a.y, a.z}, f3{b.x, b.y, b.z}, h, status, nullptr)) {
+        WfStack stk;
+        stack_init(stk);
+        if (trace_closest_with<false>(S, f3{a.x, a.y, a.z}, f3{b.x, b.y, b.z}, h, status, nullptr, stk)) {
             int code = h.prim < S.num_tris ? h.slot : -(h.prim - S.num_tris + 1);
             out = make_float4(h.t, h.b1, h.b2, __int_as_float(code));
         } else {
@@ -339,14 +351,16 @@ k_wf_extend_shade(const DScene S, const DParams P, const __grid_constant__ JobTa
         HitRec h;
         bool hit;
         Walk w;
+        WfStack stk;
+        stack_init(stk);
         if (FIRST) {
             wave_start_path(S, T, wt, q, W, w);
             L.l0[q] = q;
-            hit = trace_closest<false>(S, w.o, w.d, h, status, nullptr);
+            hit = trace_closest_with<false>(S, w.o, w.d, h, status, nullptr, stk);
         } else {
             {
                 const float4 a = W.walk[q].a, b = W.walk[q].b;
-                hit = trace_closest<false>(S, f3{a.x, a.y, a.z}, f3{b.x, b.y, b.z}, h, status, nullptr);
+                hit = trace_closest_with<false>(S, f3{a.x, a.y, a.z}, f3{b.x, b.y, b.z}, h, status, nullptr, stk);
             }
             get_walk(W.walk + q, w);
         }
@@ -384,8 +398,10 @@ k_wf_shadow(const DScene S, WfState W, WfLists L, unsigned* status) {
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
         const int q = L.shadow[idx];
         const WfRay r = W.ray[q];
-        W.visible[q] = trace_any<false>(S, f3{r.o_tmax.x, r.o_tmax.y, r.o_tmax.z}, f3{r.dir.x, r.dir.y, r.dir.z},
-                                        r.o_tmax.w, status, nullptr) ? 0 : 1;
+        WfStack stk;
+        stack_init(stk);
+        W.visible[q] = trace_any_with<false>(S, f3{r.o_tmax.x, r.o_tmax.y, r.o_tmax.z}, f3{r.dir.x, r.dir.y, r.dir.z},
+                                             r.o_tmax.w, status, nullptr, stk) ? 0 : 1;
     }
 }
 
@@ -644,6 +660,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
     const unsigned types = (unsigned)S.mat_types;
     const int passes = mode == 1 ? 2 : 1;
     const size_t smem = mode == 1 ? sgrad_bytes(S) : 0;
+    const size_t tsm = trav_stack_smem(block);   // the traversal kernels' shared stack tops
     for (const WaveTable& wt : plan_waves(T, Q)) {
         const int nq = (int)wt.nq;
         // stage kernels stride over their lists: a few resident waves of blocks at most
@@ -673,16 +690,16 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                 tok = log->begin(kStageWfExtend, st);
                 // the first iteration also starts the wave's paths
                 if (it == 0) {
-                    if (nmaps) k_wf_extend_shade<true, true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, wt);
-                    else k_wf_extend_shade<false, true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, wt);
+                    if (nmaps) k_wf_extend_shade<true, true><<<grid, block, tsm, st>>>(S, P, T, W, L, mode == 1, status, wt);
+                    else k_wf_extend_shade<false, true><<<grid, block, tsm, st>>>(S, P, T, W, L, mode == 1, status, wt);
                 } else {
-                    if (nmaps) k_wf_extend_shade<true, false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, wt);
-                    else k_wf_extend_shade<false, false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1, status, wt);
+                    if (nmaps) k_wf_extend_shade<true, false><<<grid, block, tsm, st>>>(S, P, T, W, L, mode == 1, status, wt);
+                    else k_wf_extend_shade<false, false><<<grid, block, tsm, st>>>(S, P, T, W, L, mode == 1, status, wt);
                 }
                 log->end(tok, st);
 #else
                 tok = log->begin(kStageWfExtend, st);
-                k_wf_extend<<<grid, block, 0, st>>>(S, W, L, status);
+                k_wf_extend<<<grid, block, tsm, st>>>(S, W, L, status);
                 log->end(tok, st);
                 tok = log->begin(kStageWfShade, st);
                 if (nmaps) k_wf_shade<true><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1);
@@ -690,7 +707,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                 log->end(tok, st);
 #endif
                 tok = log->begin(kStageWfShadow, st);
-                k_wf_shadow<<<grid, block, 0, st>>>(S, W, L, status);
+                k_wf_shadow<<<grid, block, tsm, st>>>(S, W, L, status);
                 log->end(tok, st);
                 tok = log->begin(kStageWfCache, st);
                 if (mode == 0) {
