@@ -104,6 +104,26 @@ def well_conditioned_pixels(oracle_mod, scene, job, dI, rel: float = 6e-5) -> np
     return ok
 
 
+def image_input_sensitivity(oracle_mod, scene, job, pixels) -> np.ndarray:
+    """Per pixel of `pixels`: how far the FP64 image moves (largest Stokes component, in the
+    image_rel_err metric) when the scene's inputs are rounded to float32.  That rounding
+    perturbs the inputs by ~6e-8 relative, and an FP32 hit point carries an error of the same
+    order, so the move measures how much of an FP32 program's error the pixel's own
+    conditioning explains: a move above 1e-5 means a condition number above ~150, where FP32
+    cannot resolve the pixel to 1e-4.  Large moves come where a white-noise texture
+    (neighbouring texels independent) sets the roughness of a narrow GGX lobe: a 1e-7 shift of
+    the hit point changes alpha by ~1e-4 relative and the lobe's tail by up to 1e-3."""
+    import copy
+    pixels = np.asarray(pixels, np.int64)
+    o64, _, _ = oracle_mod.OracleScene(scene).render(job, scene.params(), pixels=pixels, paths=True)
+    s32 = float32_inputs(scene)
+    j32 = copy.copy(job)
+    if job.thetas:
+        j32.thetas = [float(np.float32(t)) for t in job.thetas]
+    o32, _, _ = oracle_mod.OracleScene(s32).render(j32, s32.params(), pixels=pixels, paths=True)
+    return image_rel_err(o32, o64).max(axis=(0, 2, 3))
+
+
 def identical_path_pixels(api, dctx, gs, job, oracle_scene, params_np):
     """Signatures of the job's paths (its own pass id) on both sides: returns the fraction
     of identical paths and a per-pixel mask of the pixels whose paths are all identical.

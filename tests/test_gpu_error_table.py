@@ -1,0 +1,228 @@
+"""FP32 (GPU) versus FP64 (oracle) error of every result of the five workloads, measured on
+the same seeded inputs and paths, at the workloads' full sizes.
+
+* 'cornell' -- the plain small workload: 64x64, 16 spp, depth 4, camera polarizer at 30 deg;
+  image of every pixel; gradient (theta, diffuse albedo, index of refraction) of the L2
+  loss to the image rendered at 60 deg with other random numbers.
+* 'icosphere' -- 256x256, 64 spp, depth 8: 256 sampled pixels of the image; gradient of a
+  seeded linear loss on a 16x16 crop (albedo and roughness maps).
+* 'rocks' -- 512x512, 32 spp, depth 16, quarter-wave plate + polarizer: 256 sampled pixels;
+  gradient on an 8x8 crop (albedo map, emitter Stokes vector, filter angle).
+* 'views' -- 8 views x 64 angles, 16 spp, depth 8: 8 sampled pixels per view; gradient of a
+  linear loss on 4 pixels per view (albedo, index, emitter, 512 filter angles).
+* 'large' -- 500k triangles, 1024x1024, 128 spp, depth 12, 16 angles: 24 sampled pixels;
+  gradient of a nonnegative intensity loss on an 8x8 crop (the 1024^2 maps on 32x32-texel
+  block sums, as in test_gpu_workloads).
+
+Images: the per-pixel relative error of tests/parity.py (p99.9 and max) over pixels whose
+paths are all identical in FP32 and FP64, once over all of them and once over the
+well-conditioned ones, whose FP64 image moves by at most 1e-5 when the inputs are rounded to
+float32 (parity.image_input_sensitivity).  Asserted: p99.9 <= 1e-4 over the well-conditioned
+pixels, and at every identical-path pixel an error of at most 1e-3 + 16 x its own move.  The
+icosphere and the rocks carry white-noise texture maps, whose texel-to-texel jumps turn the
+~1e-7 error of an FP32 hit point into up to ~4e-3 on a few pixels; the oracle's own move under
+input rounding is of the same size there (the measured ratio of the two stays below 8), so
+no FP32 program can resolve them.  Gradients: relative
+L2 error per group, over the same pixels.  With DPPT_ERROR_TABLE set to a file name the
+measured table is written there as JSON.
+"""
+import copy
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2607_13265_gb300 import scenegen as sg
+from parity import GRAD_TOL, IMG_TOL_P999, flat, grad_rel, image_rel_err, image_input_sensitivity
+
+pytestmark = pytest.mark.gpu
+
+TABLE = {}
+COND_MOVE = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env(oracle_mod):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_13265_gb300 import build, api
+    build.build()
+    yield torch, api, api.Context(0), oracle_mod
+    out = os.environ.get("DPPT_ERROR_TABLE")
+    if out and TABLE:
+        with open(out, "w") as f:
+            json.dump(TABLE, f, indent=1)
+
+
+def _primal(torch, api, dctx, gs, jobs, P):
+    sig = torch.zeros(sum(j.num_paths for j in jobs), dtype=torch.int32, device="cuda")
+    img = api.render_primal(dctx, gs, api.pack_jobs(jobs, path_sig=sig), P)
+    dctx.sync_status()
+    return img, sig.cpu().numpy().view(np.uint32)
+
+
+def _np_views(api, batch, img):
+    return [v.double().cpu().numpy() for v in api.image_views(batch, img)]
+
+
+def _image_errors(views, sigs, jobs, O, scene, pixels, oracle_mod):
+    """p99.9 and max of the per-pixel relative error over identical-path pixels, all of them
+    and the well-conditioned ones."""
+    errs, errs_c, excess, same_frac, cond_frac = [], [], [], [], []
+    for view, sig, j, pix in zip(views, sigs, jobs, pixels):
+        o, _, so = O.render(j, scene.params(), pixels=pix, paths=True)
+        same = (sig.reshape(-1, j.spp)[pix].ravel() == so).reshape(-1, j.spp).all(1)
+        move = image_input_sensitivity(oracle_mod, scene, j, pix)
+        cond = move <= COND_MOVE
+        same_frac.append(same.mean())
+        cond_frac.append(cond[same].mean())
+        e = image_rel_err(flat(view)[:, pix], o)
+        errs.append(e[:, same].reshape(-1, 12))
+        errs_c.append(e[:, same & cond].reshape(-1, 12))
+        excess.append((e.max(axis=(0, 2, 3)) / (10 * IMG_TOL_P999 + 16 * move))[same])
+    e, ec = np.concatenate(errs).ravel(), np.concatenate(errs_c).ravel()
+    return {"p999": float(np.quantile(ec, 0.999)), "max": float(ec.max()), "pixels_compared": int(ec.size // 12),
+            "all_identical_p999": float(np.quantile(e, 0.999)), "all_identical_max": float(e.max()),
+            "all_identical_pixels": int(e.size // 12), "max_err_over_allowance": float(np.concatenate(excess).max()),
+            "identical_pixel_fraction": float(np.mean(same_frac)),
+            "well_conditioned_fraction": float(np.mean(cond_frac))}
+
+
+def _keep(asig, j, pix, O, scene):
+    _, _, so = O.render(j, scene.params(), pixels=pix, paths=True)
+    return (asig.reshape(-1, j.spp)[pix].ravel() == so).reshape(-1, j.spp).all(1)
+
+
+def _grad_errors(got, ref, scene, block_maps=False):
+    out = {}
+    for t, (off, w, h, ch) in enumerate(scene.tex_desc):
+        if not scene.tex_differentiable[t]:
+            continue
+        o, g = ref["tex"][off:off + w * h * ch], got["tex"][off:off + w * h * ch]
+        if block_maps:
+            o = o.reshape(h // 32, 32, w // 32, 32, ch).sum((1, 3))
+            g = g.reshape(h // 32, 32, w // 32, 32, ch).sum((1, 3))
+        if np.linalg.norm(o) > 0:
+            out[f"tex{t}" + ("_32x32_blocks" if block_maps else "")] = grad_rel(g, o)
+    for k in ("ior", "le", "sheet", "theta"):
+        o = ref[k]
+        if o.size and np.linalg.norm(o) > 0:
+            out[k] = grad_rel(got[k][:o.size], o)
+    return out
+
+
+def _record(name, image, grads):
+    TABLE[name] = {"image": image, "gradient_rel_err": grads}
+    assert image["p999"] <= IMG_TOL_P999, (name, image)
+    assert image["max_err_over_allowance"] <= 1.0, (name, image)
+    assert image["pixels_compared"] >= 20, (name, image)
+    assert all(v <= GRAD_TOL for v in grads.values()), (name, grads)
+
+
+def test_cornell(env):
+    torch, api, dctx, O = env
+    scene, job = sg.cornell_box()
+    gs = api.GpuScene(dctx, scene)
+    P = api.device_params(scene, api.pack_jobs([job]))
+    img, sig = _primal(torch, api, dctx, gs, [job], P)
+    batch = api.pack_jobs([job])
+    Os = O.OracleScene(scene)
+    image = _image_errors(_np_views(api, batch, img), [sig], [job], Os, scene, [np.arange(job.num_pixels)], O)
+    tjob = copy.copy(job)
+    tjob.thetas, tjob.seed = [np.radians(60.0)], 91
+    target = api.render_primal(dctx, gs, api.pack_jobs([tjob]), api.device_params(scene, api.pack_jobs([tjob])))
+    aj = api.adjoint_jobs([job])[0]
+    ai, asig = _primal(torch, api, dctx, gs, [aj], P)
+    keep = _keep(asig, aj, np.arange(job.num_pixels), Os, scene)
+    dI = ((img - target) * (2.0 / img.numel())).double().cpu().numpy().reshape(1, -1, 3, 4) * keep[None, :, None, None]
+    got = {k: v.double().cpu().numpy() for k, v in api.render_adjoint(
+        dctx, gs, api.pack_jobs([aj]), P, torch.as_tensor(dI.ravel(), dtype=torch.float32, device="cuda")).items()}
+    dctx.sync_status()
+    ref = Os.gradient(aj, scene.params(), dI, mode="replay")
+    _record("cornell", image, _grad_errors(got, ref, scene))
+
+
+def _crop(job, x0, y0, n):
+    return np.array([(y0 + dy) * job.width + x0 + dx for dy in range(n) for dx in range(n)], np.int64)
+
+
+def _sampled_and_crop(env, name, scene, job, npix, crop, nonneg=False, block_maps=False, seed=0):
+    torch, api, dctx, O = env
+    gs = api.GpuScene(dctx, scene)
+    P = api.device_params(scene, api.pack_jobs([job]))
+    img, sig = _primal(torch, api, dctx, gs, [job], P)
+    Os = O.OracleScene(scene)
+    pix = np.sort(np.random.default_rng(seed).choice(job.num_pixels, npix, replace=False))
+    image = _image_errors(_np_views(api, api.pack_jobs([job]), img), [sig], [job], Os, scene, [pix], O)
+    aj = api.adjoint_jobs([job])[0]
+    _, asig = _primal(torch, api, dctx, gs, [aj], P)
+    keep = _keep(asig, aj, crop, Os, scene)
+    rng = np.random.default_rng(seed + 1)
+    w = np.zeros((job.num_angles, len(crop), 3, 4))
+    if nonneg:
+        w[..., 0] = rng.uniform(0.5, 1.5, (job.num_angles, len(crop), 3))
+    else:
+        w = rng.normal(size=w.shape)
+    w *= keep[None, :, None, None]
+    W = torch.zeros(job.num_angles * job.num_pixels * 12, dtype=torch.float32, device="cuda")
+    W.view(job.num_angles, -1, 3, 4)[:, torch.as_tensor(crop, device="cuda")] = torch.as_tensor(
+        w, dtype=torch.float32, device="cuda")
+    got = {k: v.double().cpu().numpy() for k, v in api.render_adjoint(dctx, gs, api.pack_jobs([aj]), P, W).items()}
+    dctx.sync_status()
+    ref = Os.gradient(aj, scene.params(), w, pixels=crop, mode="replay")
+    _record(name, image, _grad_errors(got, ref, scene, block_maps))
+
+
+def test_icosphere(env):
+    scene, job = sg.icosphere_scene()
+    _sampled_and_crop(env, "icosphere", scene, job, 256, _crop(job, 120, 120, 16), seed=3)
+
+
+def test_rocks(env):
+    scene, job = sg.rocks_scene()
+    _sampled_and_crop(env, "rocks", scene, job, 256, _crop(job, 300, 220, 8), seed=5)
+
+
+def test_large(env):
+    scene, job = sg.large_scene()
+    _sampled_and_crop(env, "large", scene, job, 24, _crop(job, 480, 560, 8), nonneg=True, block_maps=True, seed=23)
+
+
+def test_views(env):
+    torch, api, dctx, O = env
+    scene, jobs = sg.cornell_views(8, 64, 16, 8)
+    gs = api.GpuScene(dctx, scene)
+    P = api.device_params(scene, api.pack_jobs(jobs))
+    img, sig = _primal(torch, api, dctx, gs, jobs, P)
+    batch = api.pack_jobs(jobs)
+    rng = np.random.default_rng(41)
+    pixels = [np.sort(rng.choice(j.num_pixels, 8, replace=False)) for j in jobs]
+    sigs, base = [], 0
+    for j in jobs:
+        sigs.append(sig[base:base + j.num_paths])
+        base += j.num_paths
+    Os = O.OracleScene(scene)
+    image = _image_errors(_np_views(api, batch, img), sigs, jobs, Os, scene, pixels, O)
+    ajobs = api.adjoint_jobs(jobs)
+    _, asig = _primal(torch, api, dctx, gs, ajobs, P)
+    adj = api.pack_jobs(ajobs)
+    W = torch.zeros(adj.image_floats, dtype=torch.float32, device="cuda")
+    ref, theta_ref, base = None, [], 0
+    from parity import well_conditioned_pixels
+    for j, off in zip(ajobs, adj.offsets):
+        pix = np.sort(rng.choice(j.num_pixels, 4, replace=False))
+        keep = _keep(asig[base:base + j.num_paths], j, pix, Os, scene)
+        base += j.num_paths
+        full = np.zeros((j.num_angles, j.num_pixels, 3, 4))
+        full[:, pix] = rng.normal(size=(j.num_angles, len(pix), 3, 4)) * keep[None, :, None, None]
+        full *= well_conditioned_pixels(O, scene, j, full)[None, :, None, None]
+        W[off:off + full.size] = torch.as_tensor(full.ravel(), dtype=torch.float32, device="cuda")
+        r = Os.gradient(j, scene.params(), full[:, pix], pixels=pix, mode="replay")
+        theta_ref.append(r["theta"][:j.num_angles])
+        ref = r if ref is None else {k: ref[k] + r[k] if k != "theta" else ref[k] for k in ref}
+    got = {k: v.double().cpu().numpy() for k, v in api.render_adjoint(dctx, gs, adj, P, W).items()}
+    dctx.sync_status()
+    ref["theta"] = np.concatenate(theta_ref)
+    _record("views", image, _grad_errors(got, ref, scene))
