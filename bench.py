@@ -73,10 +73,18 @@ B_CACHE_RAY = 100
 B_CACHE_VERTEX_PRIMAL, B_CACHE_VERTEX_ADJOINT = 420, 424
 B_CACHE_PATH_PRIMAL, B_CACHE_PATH_ADJOINT = 48, 216
 
-# DRAM traffic per launch (bytes) of a workload's dominant kernel from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, stage); absent for a
-# kernel changed since its capture.
-DRAM_BYTES_PER_LAUNCH = {}
+# DRAM traffic per launch (bytes; dram__bytes_read.sum + dram__bytes_write.sum, cold caches)
+# keyed by (workload, stage), a "launch" counted as the stage statistics count it (one replay
+# record = the bin kernels of one iteration).  Captured on the views workload with every image
+# side halved, whose per-launch work equals the full size's (one wave of 3.78M against 4.19M
+# paths: 2.09M vertices per cache launch, 1.12M per replay iteration at both sizes), and
+# scaled by the vertices processed: 93 B per primal vertex, 850 B per cache-pass vertex, 815 B
+# per replayed vertex.  Absent for a kernel changed since its capture.
+DRAM_BYTES_PER_LAUNCH = {
+    ("cornell_views8x64angles_16spp_depth8", "primal"): 6.256e9,
+    ("cornell_views8x64angles_16spp_depth8", "wf_cache"): 1.781e9,
+    ("cornell_views8x64angles_16spp_depth8", "wf_replay"): 0.910e9,
+}
 
 # floats per vertex of the wavefront cache: E_v 12, compact W_v 19, the hit 4, visibility 1
 WF_CACHE_FLOATS = 36
@@ -761,8 +769,8 @@ def main():
     ap.add_argument("--adj-block", type=int, default=None)
     ap.add_argument("--adj-scatter", type=int, default=0, choices=[0, 1],
                     help="with --schedule: texel gradients per warp group (0) or per lane (1)")
-    ap.add_argument("--cpu-pixels", type=int, default=8192, help="pixels of the CPU-baseline sample")
-    ap.add_argument("--ref-pixels", type=int, default=1024, help="pixels per step of the reference arm")
+    ap.add_argument("--cpu-pixels", type=int, default=98304, help="pixels of the CPU-baseline sample")
+    ap.add_argument("--ref-pixels", type=int, default=4096, help="pixels per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-icosphere", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="image sides scaled (tests and profiling captures only)")
