@@ -78,23 +78,23 @@ B_CACHE_PATH_PRIMAL, B_CACHE_PATH_ADJOINT = 48, 216
 # record = the bin kernels of one iteration).  Captured on the views workload with every image
 # side halved, whose per-launch work equals the full size's (one wave of 3.78M against 4.19M
 # paths: 2.09M vertices per cache launch, 1.12M per replay iteration at both sizes), and
-# scaled by the vertices processed: 93 B per primal vertex, 850 B per cache-pass vertex, 815 B
+# scaled by the vertices processed: 93 B per primal vertex, 865 B per cache-pass vertex, 548 B
 # per replayed vertex.  Absent for a kernel changed since its capture.
 DRAM_BYTES_PER_LAUNCH = {
     ("cornell_views8x64angles_16spp_depth8", "primal"): 6.256e9,
-    ("cornell_views8x64angles_16spp_depth8", "wf_cache"): 1.781e9,
-    ("cornell_views8x64angles_16spp_depth8", "wf_replay"): 0.910e9,
+    ("cornell_views8x64angles_16spp_depth8", "wf_cache"): 1.813e9,
+    ("cornell_views8x64angles_16spp_depth8", "wf_replay"): 0.613e9,
 }
 
-# floats per vertex of the wavefront cache: E_v 12, compact W_v 19, the hit 4, visibility 1
+# floats per vertex of the wavefront cache: E_v 12, compact W_v 19, visibility 1, the hit 4
 WF_CACHE_FLOATS = 36
 
 
 def wave_paths(jobs) -> int:
     """Path slots of a wavefront wave, as the library sizes them: all the jobs' paths when
-    they fit, else 4,194,304 or fewer when a wave's path state (416 B) plus cache (144 B per
+    they fit, else 4,194,304 or fewer when a wave's path state (432 B) plus cache (144 B per
     vertex) would pass 32 GiB; several jobs share a wave."""
-    per_path = 416 + 4 * WF_CACHE_FLOATS * max(j.max_depth for j in jobs)
+    per_path = 432 + 4 * WF_CACHE_FLOATS * max(j.max_depth for j in jobs)
     cap = min(1 << 22, (32 << 30) // per_path)
     return max(max(j.spp for j in jobs), min(sum(j.num_paths for j in jobs), cap))
 

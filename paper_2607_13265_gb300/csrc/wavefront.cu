@@ -7,13 +7,15 @@
 // binned by the type of their next vertex: it shades that vertex itself from the hit and
 // light-sample visibility the cache pass stored (no traversal, no vertex record) and
 // evaluates it with dual numbers, with the same code and Philox counters as the cache
-// pass.  Path state lives in the context workspace as arrays of 16-byte-aligned records
-// that a thread moves with float4 loads and stores: the walk (64 B), path bookkeeping
-// (16 B), the vertex handed from shade to cache (112 B), the hit (16 B), the adjoint row
-// (48 B), the raw Stokes value (48 B); the per-vertex cache holds one 144-byte record per
-// (vertex, path), whole whatever fraction of the wave's paths is still live.  Every stage
-// reads its list length from device memory and loops over it with a grid stride, so a
-// wave is a fixed sequence of launches.
+// pass.  Path state lives in the context workspace as per-path records that one thread
+// moves with float4 loads and stores, each aligned so that it fills whole 64-byte blocks:
+// the lists' order scatters a warp's paths over the wave, so a thread's record, not a
+// warp's, is the unit of memory traffic.  The path's state (walk 64 B, adjoint row 48 B,
+// bookkeeping 16 B) is one 128-byte record, the vertex handed from shade to cache another;
+// the per-vertex cache holds one 144-byte record per (vertex, path), whole whatever
+// fraction of the wave's paths is still live.  Every stage reads its list length from
+// device memory and loops over it with a grid stride, so a wave is a fixed sequence of
+// launches.
 #include <algorithm>
 #include <vector>
 
@@ -37,13 +39,6 @@
 #ifndef DPPT_WF_REPLAY_DIFFUSE_MIN_BLOCKS
 #define DPPT_WF_REPLAY_DIFFUSE_MIN_BLOCKS 4
 #endif
-// the replay prefetches into L2 the records it reads after shading its vertex: not at all
-// (0), as the sectors holding each record's first bytes (1), or as exactly the bytes it
-// reads, with bulk prefetches (2).  Measured on the views x angles workload: 63.8, 65.3 and
-// 64.7 ms per step.
-#ifndef DPPT_WF_PREFETCH
-#define DPPT_WF_PREFETCH 0
-#endif
 // resident 512-thread blocks per SM the shade kernel's register allocation must allow
 // (2 -> at most 64 registers per thread)
 // resident 512-thread blocks per SM the fused extend + shade kernel's registers must allow
@@ -60,34 +55,34 @@
 
 namespace dppt {
 
-struct __align__(16) WfWalk { float4 a, b, c, d; };   // (o, prev_pdf) (d, sig) (xprev, v|nv|delta) (d1, -)
 struct __align__(16) WfMeta { unsigned lo, hi; int job, pni; };  // pid, job, phase | n << 8 | i << 16
-struct __align__(16) WfVtx { float4 x_tu, ng_tv, wi_pdf, wl_ps, misc, mat; int4 ids; };
+// a path's state: walk (o, prev_pdf) (d, sig) (xprev, v | nv | delta) (d1, -), adjoint row
+// (3 channels), bookkeeping
+struct __align__(128) WfPath { float4 a, b, c, d; float4 arow[3]; WfMeta meta; };
+struct __align__(128) WfVtx { float4 x_tu, ng_tv, wi_pdf, wl_ps, misc, mat; int4 ids; float4 pad; };
 struct __align__(16) WfRay { float4 o_tmax, dir; };
+static_assert(sizeof(WfPath) == 128 && sizeof(WfVtx) == 128, "one 128-byte record per path");
 
 enum : unsigned {
     kFEmit = 1u, kFOutside = 2u, kFOk = 4u, kFTerminal = 8u, kFDelta = 16u, kFHit = 32u,
     kEvShift = 6, kNeeShift = 8
 };
-constexpr int kMissCode = (int)0x80000000;
 
-__device__ __forceinline__ void put_walk(WfWalk* p, const Walk& w) {
-    WfWalk r;
-    r.a = make_float4(w.o.x, w.o.y, w.o.z, w.prev_pdf);
-    r.b = make_float4(w.d.x, w.d.y, w.d.z, __uint_as_float(w.sig));
-    r.c = make_float4(w.xprev.x, w.xprev.y, w.xprev.z,
-                      __int_as_float(w.v | (w.nv << 8) | ((w.prev_delta ? 1 : 0) << 16)));
-    r.d = make_float4(w.d1.x, w.d1.y, w.d1.z, 0.0f);
-    *p = r;
+__device__ __forceinline__ void put_walk(WfPath* p, const Walk& w) {
+    p->a = make_float4(w.o.x, w.o.y, w.o.z, w.prev_pdf);
+    p->b = make_float4(w.d.x, w.d.y, w.d.z, __uint_as_float(w.sig));
+    p->c = make_float4(w.xprev.x, w.xprev.y, w.xprev.z,
+                       __int_as_float(w.v | (w.nv << 8) | ((w.prev_delta ? 1 : 0) << 16)));
+    p->d = make_float4(w.d1.x, w.d1.y, w.d1.z, 0.0f);
 }
-__device__ __forceinline__ void get_walk(const WfWalk* p, Walk& w) {
-    WfWalk r = *p;
-    w.o = {r.a.x, r.a.y, r.a.z}; w.prev_pdf = r.a.w;
-    w.d = {r.b.x, r.b.y, r.b.z}; w.sig = __float_as_uint(r.b.w);
-    w.xprev = {r.c.x, r.c.y, r.c.z};
-    int bits = __float_as_int(r.c.w);
+__device__ __forceinline__ void get_walk(const WfPath* p, Walk& w) {
+    const float4 a = p->a, b = p->b, c = p->c, d = p->d;
+    w.o = {a.x, a.y, a.z}; w.prev_pdf = a.w;
+    w.d = {b.x, b.y, b.z}; w.sig = __float_as_uint(b.w);
+    w.xprev = {c.x, c.y, c.z};
+    int bits = __float_as_int(c.w);
     w.v = bits & 0xff; w.nv = (bits >> 8) & 0xff; w.prev_delta = (bits >> 16) & 1;
-    w.d1 = {r.d.x, r.d.y, r.d.z};
+    w.d1 = {d.x, d.y, d.z};
 }
 
 __device__ __forceinline__ void put_vertex(WfVtx* p, const VCtx& vc, const NeePending& ne, const Shade& sh) {
@@ -102,6 +97,7 @@ __device__ __forceinline__ void put_vertex(WfVtx* p, const VCtx& vc, const NeePe
                  (sh.terminal ? kFTerminal : 0u) | (sh.delta ? kFDelta : 0u) | (sh.ev << kEvShift) |
                  ((unsigned)ne.state << kNeeShift);
     r.ids = make_int4(vc.prim, (vc.mat & 0xffff) | (ne.l << 16), vc.light, (int)f);
+    r.pad = make_float4(0.f, 0.f, 0.f, 0.f);
     *p = r;
 }
 // (the ids first: a path whose ray missed reads 16 of the record's 112 bytes)
@@ -130,19 +126,31 @@ __device__ __forceinline__ bool get_vertex(const WfVtx* p, const Walk& w, VCtx& 
     return true;
 }
 
+constexpr int kMissCode = (int)0x80000000;
+
 struct WfState {
-    WfWalk* walk;
-    WfMeta* meta;
+    WfPath* path;
     WfVtx* vtx;
-    float4* hit;        // (t, b1, b2, BVH slot | -(sphere + 1) | miss code)
+    float4* hit;        // (t, b1, b2, BVH slot | -(sphere + 1) | kMissCode)
     WfRay* ray;         // shadow rays
     int* visible;
-    float4* arow;       // adjoint rows, 3 per path
     float4* raw;        // raw Stokes per path, 3 per path
     float* cache;
     long long Q;
     int cap;
+    __device__ __forceinline__ float* rec(int v, int q) const { return cache + ((long long)v * Q + q) * kWfCacheComps; }
 };
+// the code of a traversal's result: the BVH slot of a triangle, -(sphere + 1), or kMissCode
+__device__ __forceinline__ int code_of(const DScene& S, bool hit, const HitRec& h) {
+    return !hit ? kMissCode : h.prim < S.num_tris ? h.slot : -(h.prim - S.num_tris + 1);
+}
+// the hit of a code (not a miss)
+__device__ __forceinline__ void decode_hit(const DScene& S, const float4& hv, HitRec& h) {
+    const int code = __float_as_int(hv.w);
+    h.t = hv.x; h.b1 = hv.y; h.b2 = hv.z;
+    if (code >= 0) { h.slot = code; h.prim = __float_as_int(__ldg(&S.tris[3 * code].w)); }
+    else { h.slot = -1; h.prim = S.num_tris + (-code - 1); }
+}
 
 struct WfLists {
     int* l0;      // live paths of the cache pass
@@ -194,8 +202,8 @@ __device__ __forceinline__ void wave_start_path(const DScene& S, const JobTable&
     const DJob& J = T.job[sg.job];
     const unsigned long long pid = (unsigned long long)(sg.pix0 * J.spp + (q - sg.q0));
     walk_begin(S, J, pid, (long long)(pid / J.spp), w);
-    put_walk(W.walk + q, w);
-    W.meta[q] = WfMeta{(unsigned)pid, (unsigned)(pid >> 32), sg.job, 0};
+    put_walk(W.path + q, w);
+    W.path[q].meta = WfMeta{(unsigned)pid, (unsigned)(pid >> 32), sg.job, 0};
 }
 
 // Replay bins: the material types with a replay kernel of their own (diffuse, rough
@@ -244,29 +252,16 @@ k_wf_extend(const DScene S, WfState W, WfLists L, unsigned* status) {
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
         const int q = L.l0[idx];
-        const float4 a = W.walk[q].a, b = W.walk[q].b;
+        const float4 a = W.path[q].a, b = W.path[q].b;
         HitRec h;
-        float4 out;
         WfStack stk;
         stack_init(stk);
-        if (trace_closest_with<false>(S, f3{a.x, a.y, a.z}, f3{b.x, b.y, b.z}, h, status, nullptr, stk)) {
-            int code = h.prim < S.num_tris ? h.slot : -(h.prim - S.num_tris + 1);
-            out = make_float4(h.t, h.b1, h.b2, __int_as_float(code));
-        } else {
-            out = make_float4(0.f, 0.f, 0.f, __int_as_float(kMissCode));
-        }
-        W.hit[q] = out;
+        const bool hit = trace_closest_with<false>(S, f3{a.x, a.y, a.z}, f3{b.x, b.y, b.z}, h, status, nullptr, stk);
+        W.hit[q] = hit ? make_float4(h.t, h.b1, h.b2, __int_as_float(code_of(S, true, h)))
+                       : make_float4(0.f, 0.f, 0.f, __int_as_float(code_of(S, false, h)));
     }
 }
 
-// Hints the memory system to bring the 32-byte sector at p into L2 (no register is written).
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-// Brings the `bytes` bytes at p into L2 (p 16-byte aligned, bytes a multiple of 16).
-__device__ __forceinline__ void prefetch_l2_bytes(const void* p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
 
 // Appends path q to the next iteration's replay bin b.  Appends are warp-aggregated: the
 // lanes of a warp going to the same bin take consecutive slots with one atomic.
@@ -288,7 +283,7 @@ __device__ __forceinline__ int replay_bin(const DScene& S, int mat) {
     return (kBinnedTypes >> t) & 1u ? t : kBinOther;
 }
 __device__ __forceinline__ int replay_bin_of(const WfState& W, int q, int v) {
-    return __float_as_int(W.cache[((long long)v * W.Q + q) * kWfCacheComps + kWfVisComp]) >> 1;
+    return __float_as_int(W.rec(v, q)[kWfVisComp]) >> 1;
 }
 
 // Surface data, light sample and BSDF sample of each cache-pass path's new vertex; in the
@@ -303,24 +298,22 @@ k_wf_shade(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
         const int q = L.l0[idx];
         const float4 hv = W.hit[q];
-        const int code = __float_as_int(hv.w);
+        const bool miss = __float_as_int(hv.w) == kMissCode;
         if (store_hits) {
-            const int v = __float_as_int(W.walk[q].c.w) & 0xff;     // the vertex's slot (see put_walk)
-            float* rec = W.cache + ((long long)(v - 1) * W.Q + q) * kWfCacheComps;
+            const int v = __float_as_int(W.path[q].c.w) & 0xff;     // the vertex's slot (see put_walk)
+            float* rec = W.rec(v - 1, q);
             *reinterpret_cast<float4*>(rec + kWfHitComp) = hv;
-            if (code == kMissCode) rec[kWfVisComp] = __int_as_float(kBinMiss << 1);
+            if (miss) rec[kWfVisComp] = __int_as_float(kBinMiss << 1);
         }
-        if (code == kMissCode) {
+        if (miss) {
             W.vtx[q].ids = make_int4(0, 0, 0, 0);
             continue;
         }
         HitRec h;
-        h.t = hv.x; h.b1 = hv.y; h.b2 = hv.z;
-        if (code >= 0) { h.slot = code; h.prim = __float_as_int(__ldg(&S.tris[3 * code].w)); }
-        else { h.slot = -1; h.prim = S.num_tris + (-code - 1); }
+        decode_hit(S, hv, h);
         Walk w;
-        get_walk(W.walk + q, w);
-        const WfMeta m = W.meta[q];
+        get_walk(W.path + q, w);
+        const WfMeta m = W.path[q].meta;
         const unsigned long long pid = (unsigned long long)m.lo | ((unsigned long long)m.hi << 32);
         VCtx vc;
         NeePending ne;
@@ -366,16 +359,16 @@ k_wf_extend_shade(const DScene S, const DParams P, const __grid_constant__ JobTa
             hit = trace_closest_with<false>(S, w.o, w.d, h, status, nullptr, stk);
         } else {
             {
-                const float4 a = W.walk[q].a, b = W.walk[q].b;
+                const float4 a = W.path[q].a, b = W.path[q].b;
                 hit = trace_closest_with<false>(S, f3{a.x, a.y, a.z}, f3{b.x, b.y, b.z}, h, status, nullptr, stk);
             }
-            get_walk(W.walk + q, w);
+            get_walk(W.path + q, w);
         }
         if (store_hits) {
-            float* rec = W.cache + ((long long)(w.v - 1) * W.Q + q) * kWfCacheComps;
-            const int code = !hit ? kMissCode : h.prim < S.num_tris ? h.slot : -(h.prim - S.num_tris + 1);
+            float* rec = W.rec(w.v - 1, q);
+            const int code = code_of(S, hit, h);
             *reinterpret_cast<float4*>(rec + kWfHitComp) =
-                hit ? make_float4(h.t, h.b1, h.b2, __int_as_float(code)) : make_float4(0.f, 0.f, 0.f, __int_as_float(kMissCode));
+                hit ? make_float4(h.t, h.b1, h.b2, __int_as_float(code)) : make_float4(0.f, 0.f, 0.f, __int_as_float(code));
             if (!hit) rec[kWfVisComp] = __int_as_float(kBinMiss << 1);
         }
         if (!hit) {
@@ -383,7 +376,7 @@ k_wf_extend_shade(const DScene S, const DParams P, const __grid_constant__ JobTa
             continue;
         }
         if (h.prim >= S.num_tris) h.slot = -1;
-        const WfMeta m = W.meta[q];
+        const WfMeta m = W.path[q].meta;
         const unsigned long long pid = (unsigned long long)m.lo | ((unsigned long long)m.hi << 32);
         VCtx vc;
         NeePending ne;
@@ -432,33 +425,10 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += stride) {
         const int q = list[idx];
-        const WfMeta m = W.meta[q];
+        const WfMeta m = W.path[q].meta;
         const DJob& J = T.job[m.job];
         Walk w;
-        get_walk(W.walk + q, w);
-        if (PHASE == 1 && DPPT_WF_PREFETCH == 2) {
-            // what the replay reads once it has shaded its vertex, exactly: the vertex's
-            // visibility word and hit (the record's last 32 bytes), the adjoint row (48), and
-            // the next vertex's cached suffix L[v+1] (the record's first 48)
-            const char* rec = reinterpret_cast<const char*>(W.cache + ((long long)(w.v - 1) * W.Q + q) * kWfCacheComps);
-            prefetch_l2_bytes(rec + 4 * (kWfVisComp - 3), 32);
-            prefetch_l2_bytes(W.arow + 3 * (long long)q, 48);
-            if (w.v < W.cap)
-                prefetch_l2_bytes(W.cache + ((long long)w.v * W.Q + q) * kWfCacheComps, 48);
-        } else if (PHASE == 1 && DPPT_WF_PREFETCH) {
-            // what the replay reads once it has shaded its vertex: the vertex's hit and
-            // visibility, the adjoint row, and the next vertex's cached suffix L[v+1]
-            const char* rec = reinterpret_cast<const char*>(W.cache + ((long long)(w.v - 1) * W.Q + q) * kWfCacheComps);
-            prefetch_l2(rec + 4 * kWfVisComp);
-            prefetch_l2(rec + 4 * kWfHitComp);
-            prefetch_l2(reinterpret_cast<const char*>(W.arow + 3 * (long long)q));
-            prefetch_l2(reinterpret_cast<const char*>(W.arow + 3 * (long long)q) + 32);
-            if (w.v < W.cap) {
-                const char* nxt = reinterpret_cast<const char*>(W.cache + ((long long)w.v * W.Q + q) * kWfCacheComps);
-                prefetch_l2(nxt);
-                prefetch_l2(nxt + 32);
-            }
-        }
+        get_walk(W.path + q, w);
         PathVis<GlobalCache, MT, NM> vis;
         vis.S = &S; vis.P = &P; vis.G = &G; vis.sgrad = sgrad;
         vis.C.base = W.cache; vis.C.Q = W.Q; vis.C.q = q; vis.C.cap = W.cap;
@@ -477,23 +447,19 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
                 cont = walk_finish(S, P, w, vc, ne, visible != 0, sh, vis);
                 // the replay reads it back; stored after walk_finish, whose cache write zeroes it
                 if (MODE == 1)
-                    W.cache[((long long)slot * W.Q + q) * kWfCacheComps + kWfVisComp] =
-                        __int_as_float(replay_bin(S, vc.mat) << 1 | (visible != 0 ? 1 : 0));
+                    W.rec(slot, q)[kWfVisComp] = __int_as_float(replay_bin(S, vc.mat) << 1 | (visible != 0 ? 1 : 0));
             }
         } else {
-            const float* rec = W.cache + ((long long)(w.v - 1) * W.Q + q) * kWfCacheComps;
+            const float* rec = W.rec(w.v - 1, q);
             const float4 hv = *reinterpret_cast<const float4*>(rec + kWfHitComp);
-            const int code = __float_as_int(hv.w);
-            if (code != kMissCode) {
+            if (__float_as_int(hv.w) != kMissCode) {
                 HitRec h;
-                h.t = hv.x; h.b1 = hv.y; h.b2 = hv.z;
-                if (code >= 0) { h.slot = code; h.prim = __float_as_int(__ldg(&S.tris[3 * code].w)); }
-                else { h.slot = -1; h.prim = S.num_tris + (-code - 1); }
+                decode_hit(S, hv, h);
                 const unsigned long long pid = (unsigned long long)m.lo | ((unsigned long long)m.hi << 32);
                 walk_shade<NM, MT>(S, P, J, pid, w, h, vc, ne, sh);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    float4 r = W.arow[3 * (long long)q + c];
+                    float4 r = W.path[q].arow[c];
                     vis.a[c][0] = r.x; vis.a[c][1] = r.y; vis.a[c][2] = r.z; vis.a[c][3] = r.w;
                 }
                 cont = walk_finish(S, P, w, vc, ne, (__float_as_int(rec[kWfVisComp]) & 1) != 0, sh, vis);
@@ -532,7 +498,7 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
                     float av[4] = {__ldg(ds + 4 * c) * inv, __ldg(ds + 4 * c + 1) * inv,
                                    __ldg(ds + 4 * c + 2) * inv, __ldg(ds + 4 * c + 3) * inv};
                     rot_apply_row(Rc, av);
-                    W.arow[3 * (long long)q + c] = make_float4(av[0], av[1], av[2], av[3]);
+                    W.path[q].arow[c] = make_float4(av[0], av[1], av[2], av[3]);
                 }
                 phase = 1;
                 vis.i = 0;
@@ -547,13 +513,13 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
         if (PHASE == 1 && !done) {
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                W.arow[3 * (long long)q + c] = make_float4(vis.a[c][0], vis.a[c][1], vis.a[c][2], vis.a[c][3]);
+                W.path[q].arow[c] = make_float4(vis.a[c][0], vis.a[c][1], vis.a[c][2], vis.a[c][3]);
         }
         if (done) {
             if (J.sig) J.sig[(unsigned long long)m.lo | ((unsigned long long)m.hi << 32)] = fnv(w.sig, (unsigned)w.nv);
         } else {
-            W.meta[q].pni = phase | (vis.n << 8) | (vis.i << 16);
-            put_walk(W.walk + q, w);
+            W.path[q].meta.pni = phase | (vis.n << 8) | (vis.i << 16);
+            put_walk(W.path + q, w);
         }
     }
     if (PHASE == 1) sgrad_flush(S, G, sgrad);
@@ -583,13 +549,11 @@ static size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t wavefront_bytes(long long Q, int cap) {
     size_t b = 0;
-    b += align_up(sizeof(WfWalk) * Q);
-    b += align_up(sizeof(WfMeta) * Q);
+    b += align_up(sizeof(WfPath) * Q);
     b += align_up(sizeof(WfVtx) * Q);
     b += align_up(sizeof(float4) * Q);          // hits
     b += align_up(sizeof(WfRay) * Q);
     b += align_up(sizeof(int) * Q);             // visible
-    b += align_up(sizeof(float4) * 3 * Q);      // adjoint rows
     b += align_up(sizeof(float4) * 3 * Q);      // raw per path
     b += 3 * align_up(sizeof(int) * Q);         // lists
     b += align_up(sizeof(int) * 32);
@@ -653,13 +617,11 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                           StageLog* log) {
     char* p = static_cast<char*>(ws);
     WfState W;
-    W.walk = reinterpret_cast<WfWalk*>(p); p += align_up(sizeof(WfWalk) * Q);
-    W.meta = reinterpret_cast<WfMeta*>(p); p += align_up(sizeof(WfMeta) * Q);
+    W.path = reinterpret_cast<WfPath*>(p); p += align_up(sizeof(WfPath) * Q);
     W.vtx = reinterpret_cast<WfVtx*>(p); p += align_up(sizeof(WfVtx) * Q);
     W.hit = reinterpret_cast<float4*>(p); p += align_up(sizeof(float4) * Q);
     W.ray = reinterpret_cast<WfRay*>(p); p += align_up(sizeof(WfRay) * Q);
     W.visible = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * Q);
-    W.arow = reinterpret_cast<float4*>(p); p += align_up(sizeof(float4) * 3 * Q);
     W.raw = reinterpret_cast<float4*>(p); p += align_up(sizeof(float4) * 3 * Q);
     int* lists[3];
     for (int k = 0; k < 3; ++k) { lists[k] = reinterpret_cast<int*>(p); p += align_up(sizeof(int) * Q); }
