@@ -230,10 +230,12 @@ dppt_status dppt_render_adjoint_l2(dppt_ctx* ctx, const dppt_scene* scene, const
                                    const float* target, float scale, const dppt_grads* grads, void* stream);
 
 /* Device workspace (bytes) the jobs need beyond the caller's buffers with the
- * context's current launch shapes: filter buffers, plus the wavefront path
- * state and per-vertex cache when a wavefront schedule is selected.  The
- * wavefront runs in waves of at most 4,194,304 paths (whole pixels), fewer
- * when the wave's state and cache would pass 32 GiB (deep paths). */
+ * context's current launch shapes and replay: filter buffers, plus the
+ * wavefront path state and per-vertex cache (with the hybrid replay, k > 1:
+ * each vertex's hit and the checkpoint data instead) when a wavefront
+ * schedule is selected.  The wavefront runs in waves of at most 4,194,304
+ * paths (whole pixels), fewer when the wave's state and cache would pass
+ * 32 GiB (deep paths). */
 dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int32_t njobs, size_t* bytes);
 
 /* Schedule for subsequent launches (the autotuner's choice). */
@@ -263,15 +265,18 @@ dppt_status dppt_autotune(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job
  * bt^-1 applied to the checkpoint's suffix minus the block's emission when
  * |det bt| > eps, and otherwise by tracing the block again up to the next
  * checkpoint.  gamma = 0 never takes the scalar route; eps = +inf never
- * inverts (then the result is exact).  k > 1 runs on the grid and persistent
- * adjoint schedules only (render_adjoint returns DPPT_ERR_UNSUPPORTED with the
- * wavefront schedule).  method DPPT_REPLAY_PPRB selects instead the basic
+ * inverts (then the result is exact).  k > 1 runs on every schedule: the
+ * megakernels trace a recomputed block again; the wavefront keeps each
+ * vertex's hit (16 B) and re-shades the block from those hits, and its primal
+ * waves then also fold over blocks instead of keeping a per-vertex cache (the
+ * image is the same to rounding).  method DPPT_REPLAY_PPRB selects instead the basic
  * polarized PRB the paper analyses and rejects (Sec. 4.1-4.2): no cache; the
  * replay recovers L[v+1] = (W_v + u_v I)^-1 (L[v] - E_v) with noise u_v ~
  * N(0, sigma) that also enters the primal throughput (Philox key (seed ^
  * 0x5bd1e995) ^ 3 * 0x9E3779B97F4A7C15 and the job's stream, counter (path,
  * vertex), Box-Muller).  It is exact only where every factor is invertible;
- * it exists to measure that baseline (grid and persistent schedules).  Errors:
+ * it exists to measure that baseline (grid and persistent schedules;
+ * render_adjoint returns DPPT_ERR_UNSUPPORTED with the wavefront).  Errors:
  * INVALID_ARG for another method or k, a negative or NaN threshold or sigma. */
 enum { DPPT_REPLAY_CACHED = 0, DPPT_REPLAY_PPRB = 1 };
 typedef struct {

@@ -13,8 +13,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdppt.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["trace_d4.cu", "trace_d8.cu", "trace_d16.cu", "trace_d32.cu", "trace_d64.cu", "trace_d128.cu", "hybrid_k4.cu", "hybrid_k8.cu", "hybrid_k16.cu", "pprb.cu", "wavefront.cu", "folds.cu", "noalloc.cu", "host.cpp"]
-HEADERS = ["device_math.cuh", "internal.h", "trace.cuh", "hybrid.cuh"]
+SOURCES = ["trace_d4.cu", "trace_d8.cu", "trace_d16.cu", "trace_d32.cu", "trace_d64.cu", "trace_d128.cu", "hybrid_k4.cu", "hybrid_k8.cu", "hybrid_k16.cu", "pprb.cu", "wavefront.cu", "wf_hybrid.cu", "folds.cu", "noalloc.cu", "host.cpp"]
+HEADERS = ["device_math.cuh", "internal.h", "trace.cuh", "hybrid.cuh", "wavefront.cuh"]
 
 
 def _nvcc() -> str:

@@ -766,8 +766,8 @@ static int max_depth_of(const dppt_job* jobs, int njobs) {
 // Path slots of a wavefront wave: all the jobs' paths when they fit, else the cap (4,194,304
 // paths, or fewer when the state and cache of a wave would pass the byte budget); at least
 // one pixel of every job.  Several jobs share a wave.
-static long long wave_paths(const dppt_job* jobs, int njobs) {
-    const long long per_path = (long long)(wavefront_bytes(1LL << 20, max_depth_of(jobs, njobs)) >> 20) + 1;
+static long long wave_paths(const dppt_job* jobs, int njobs, int k) {
+    const long long per_path = (long long)(wavefront_bytes(1LL << 20, max_depth_of(jobs, njobs), k) >> 20) + 1;
     const long long limit = std::min(kWaveCap, std::max(1LL, kWaveBytes / per_path));
     long long total = 0, spp = 1;
     for (int i = 0; i < njobs; ++i) {
@@ -775,6 +775,14 @@ static long long wave_paths(const dppt_job* jobs, int njobs) {
         spp = std::max<long long>(spp, jobs[i].spp);
     }
     return std::max(spp, std::min(total, limit));
+}
+
+// the wavefront's replay: the hybrid's checkpoint interval, or 1 for the fully cached replay
+// (P-PRB has no wavefront form); the primal's waves follow it, so that neither pass keeps a
+// per-vertex cache when the hybrid is chosen
+static WfHybrid wf_hybrid(const dppt_ctx* ctx) {
+    const bool h = ctx->replay.method != DPPT_REPLAY_PPRB && ctx->replay.checkpoint_interval > 1;
+    return WfHybrid{h ? ctx->replay.checkpoint_interval : 1, ctx->replay.gamma, ctx->replay.eps};
 }
 
 // shared memory of the megakernel adjoints' scalar-gradient accumulators (one copy each)
@@ -791,10 +799,11 @@ dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_jo
     if (st != DPPT_OK) return st;
     const Shape shape = shape_of(ctx, 0);
     const bool wave = shape.schedule == DPPT_SCHED_WAVEFRONT;
-    const long long Q = wave ? wave_paths(jobs, njobs) : 0;
+    const WfHybrid hy = wf_hybrid(ctx);
+    const long long Q = wave ? wave_paths(jobs, njobs, hy.k) : 0;
     const int cap = max_depth_of(jobs, njobs);
     const size_t ws_jobs = ws;
-    if (wave) ws = ws_jobs + wavefront_bytes(Q, cap);
+    if (wave) ws = ws_jobs + wavefront_bytes(Q, cap, hy.k);
     if ((st = ensure_ws(ctx, ws)) != DPPT_OK) return st;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     std::vector<int> first, maxd;
@@ -817,7 +826,7 @@ dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_jo
         }
         if (wave) {
             cudaError_t e = run_wavefront(0, s->d, P, G, T, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
-                                          shape.block, ctx->d_status, cs, &ctx->log);
+                                          shape.block, hy, ctx->d_status, cs, &ctx->log);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront primal");
             continue;
         }
@@ -865,12 +874,13 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
     if (st != DPPT_OK) return st;
     const Shape shape = shape_of(ctx, 1);
     const bool wave = shape.schedule == DPPT_SCHED_WAVEFRONT;
-    if (wave && (ctx->replay.checkpoint_interval > 1 || ctx->replay.method == DPPT_REPLAY_PPRB))
-        return fail(ctx, DPPT_ERR_UNSUPPORTED, "hybrid replay and P-PRB run on the grid and persistent schedules");
-    const long long Q = wave ? wave_paths(jobs, njobs) : 0;
+    if (wave && ctx->replay.method == DPPT_REPLAY_PPRB)
+        return fail(ctx, DPPT_ERR_UNSUPPORTED, "P-PRB runs on the grid and persistent schedules");
+    const WfHybrid hy = wf_hybrid(ctx);
+    const long long Q = wave ? wave_paths(jobs, njobs, hy.k) : 0;
     const int cap = max_depth_of(jobs, njobs);
     const size_t ws_jobs = ws;
-    if (wave) ws = ws_jobs + wavefront_bytes(Q, cap);
+    if (wave) ws = ws_jobs + wavefront_bytes(Q, cap, hy.k);
     if ((st = ensure_ws(ctx, ws)) != DPPT_OK) return st;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     std::vector<int> first, maxd;
@@ -920,7 +930,7 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
         }
         if (wave) {
             cudaError_t e = run_wavefront(1, Sd, P, G, T, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
-                                          shape.block, ctx->d_status, cs, &ctx->log);
+                                          shape.block, hy, ctx->d_status, cs, &ctx->log);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront adjoint");
             continue;
         }
@@ -1095,7 +1105,7 @@ dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int3
         if (jobs[i].filter != DPPT_FILTER_NONE)
             b = align256(b + 2 * (size_t)jobs[i].width * jobs[i].height * 12 * sizeof(float));
     if (njobs > 0 && (ctx->launch.schedule == DPPT_SCHED_WAVEFRONT || ctx->launch.adj_schedule == DPPT_SCHED_WAVEFRONT))
-        b += wavefront_bytes(wave_paths(jobs, njobs), max_depth_of(jobs, njobs));
+        b += wavefront_bytes(wave_paths(jobs, njobs, wf_hybrid(ctx).k), max_depth_of(jobs, njobs), wf_hybrid(ctx).k);
     *bytes = b;
     return DPPT_OK;
 }

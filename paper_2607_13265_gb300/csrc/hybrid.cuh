@@ -14,7 +14,9 @@
 //     traced again (detached) from the saved walk state up to the next checkpoint, its
 //     E/W folded onto that checkpoint's suffix.
 // Per-thread memory: (MAXD/K + 2) x 60 floats of block data, K x 31 floats of look-ahead,
-// MAXD route bytes -- instead of the MAXD x 31 floats of the fully cached replay.
+// MAXD route bytes -- instead of the MAXD x 31 floats of the fully cached replay.  The
+// visitor works on whatever memory its pointers give it: the megakernel's thread-local
+// arrays, or a path's records in the wavefront's workspace (wf_hybrid.cu).
 #pragma once
 
 #include "trace.cuh"
@@ -84,6 +86,7 @@ struct HybVis {
     float a[3][4];
     float gamma, eps;
     int n, i, phase, la, blk_base;
+    int cap;                // vertices cached at most (MAXD in the megakernel, the wave's depth in the wavefront)
 
     __device__ __forceinline__ bool flagged(int b) const { return (flags[b >> 5] >> (b & 31)) & 1u; }
 
@@ -96,7 +99,7 @@ struct HybVis {
     }
 
     __device__ void cache_vertex(const VCtx& vc) {
-        if (n >= MAXD) return;
+        if (n >= cap) return;
         float E[3][4];
         Compact<float> W;
         eval_vertex<float>(*S, *P, vc, E, W, nullptr);
@@ -267,7 +270,7 @@ k_hybrid(const DScene S, const DParams P, const DGrads G, const __grid_constant_
             vis.S = &S; vis.P = &P; vis.G = &G; vis.sgrad = sgrad;
             vis.ck = ck; vis.route = route; vis.blk = blk; vis.bt = bt; vis.ebr = ebr; vis.flags = flags;
             vis.gamma = hc.gamma; vis.eps = hc.eps;
-            vis.n = 0; vis.i = 0; vis.la = 0; vis.blk_base = 0;
+            vis.n = 0; vis.i = 0; vis.la = 0; vis.blk_base = 0; vis.cap = MAXD;
             for (int k = 0; k < (NB + 31) / 32; ++k) flags[k] = 0u;
             Walk w;
             vis.phase = 0;

@@ -187,12 +187,14 @@ DPPT_DECLARE_HYBRID(8)
 DPPT_DECLARE_HYBRID(16)
 #undef DPPT_DECLARE_HYBRID
 
-// wavefront schedule (wavefront.cu): workspace bytes for waves of Q paths with
-// a cache of `cap` vertices, and the run of every job of a table (several jobs share a wave)
-size_t wavefront_bytes(long long Q, int cap);
+// wavefront schedule (wavefront.cu): workspace bytes for waves of Q paths with a cache of
+// `cap` vertices (k > 1: the hybrid replay's checkpoints every k vertices instead of the
+// per-vertex cache), and the run of every job of a table (several jobs share a wave)
+struct WfHybrid { int k; float gamma, eps; };   // k = 1: the fully cached replay
+size_t wavefront_bytes(long long Q, int cap, int k);
 cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T,
-                          void* ws, long long Q, int cap, int block, unsigned* status, cudaStream_t st,
-                          StageLog* log);
+                          void* ws, long long Q, int cap, int block, const WfHybrid& hy, unsigned* status,
+                          cudaStream_t st, StageLog* log);
 
 // read-only views of the opaque context and scene (host.cpp), for entry points
 // implemented in other translation units

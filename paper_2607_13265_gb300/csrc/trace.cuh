@@ -15,6 +15,8 @@
 //    and the same machine code, because both passes run through the single
 //    call site of walk_step -- and accumulates a^T dE_i + a^T dW_i L[i+1] with
 //    dual numbers before a <- a^T W_i.  No Mueller matrix is inverted.
+#pragma once
+
 #include <cfloat>
 #include <type_traits>
 

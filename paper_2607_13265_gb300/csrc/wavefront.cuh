@@ -1,0 +1,226 @@
+// The wavefront schedule's path records, lists and wave tables, shared by the stage kernels
+// (wavefront.cu) and the hybrid-replay cache and replay kernels (wf_hybrid.cu).
+#pragma once
+
+#include "trace.cuh"
+
+namespace dppt {
+
+struct __align__(16) WfMeta { unsigned lo, hi; int job, pni; };  // pid, job, phase | n << 8 | i << 16
+// a path's state: walk (o, prev_pdf) (d, sig) (xprev, v | nv | delta) (d1, -), adjoint row
+// (3 channels), bookkeeping
+struct __align__(128) WfPath { float4 a, b, c, d; float4 arow[3]; WfMeta meta; };
+struct __align__(128) WfVtx { float4 x_tu, ng_tv, wi_pdf, wl_ps, misc, mat; int4 ids; float4 pad; };
+struct __align__(16) WfRay { float4 o_tmax, dir; };
+static_assert(sizeof(WfPath) == 128 && sizeof(WfVtx) == 128, "one 128-byte record per path");
+
+enum : unsigned {
+    kFEmit = 1u, kFOutside = 2u, kFOk = 4u, kFTerminal = 8u, kFDelta = 16u, kFHit = 32u,
+    kEvShift = 6, kNeeShift = 8
+};
+
+__device__ __forceinline__ void put_walk(WfPath* p, const Walk& w) {
+    p->a = make_float4(w.o.x, w.o.y, w.o.z, w.prev_pdf);
+    p->b = make_float4(w.d.x, w.d.y, w.d.z, __uint_as_float(w.sig));
+    p->c = make_float4(w.xprev.x, w.xprev.y, w.xprev.z,
+                       __int_as_float(w.v | (w.nv << 8) | ((w.prev_delta ? 1 : 0) << 16)));
+    p->d = make_float4(w.d1.x, w.d1.y, w.d1.z, 0.0f);
+}
+__device__ __forceinline__ void get_walk(const WfPath* p, Walk& w) {
+    const float4 a = p->a, b = p->b, c = p->c, d = p->d;
+    w.o = {a.x, a.y, a.z}; w.prev_pdf = a.w;
+    w.d = {b.x, b.y, b.z}; w.sig = __float_as_uint(b.w);
+    w.xprev = {c.x, c.y, c.z};
+    int bits = __float_as_int(c.w);
+    w.v = bits & 0xff; w.nv = (bits >> 8) & 0xff; w.prev_delta = (bits >> 16) & 1;
+    w.d1 = {d.x, d.y, d.z};
+}
+
+__device__ __forceinline__ void put_vertex(WfVtx* p, const VCtx& vc, const NeePending& ne, const Shade& sh) {
+    WfVtx r;
+    r.x_tu = make_float4(vc.x.x, vc.x.y, vc.x.z, vc.tu);
+    r.ng_tv = make_float4(vc.ng.x, vc.ng.y, vc.ng.z, vc.tv);
+    r.wi_pdf = make_float4(sh.wi.x, sh.wi.y, sh.wi.z, sh.pdf);
+    r.wl_ps = make_float4(ne.wl.x, ne.wl.y, ne.wl.z, vc.pspec);
+    r.misc = make_float4(ne.pl, ne.cx, vc.w_emit, vc.p_event);
+    r.mat = make_float4(vc.alpha, vc.alb[0], vc.alb[1], vc.alb[2]);
+    unsigned f = kFHit | (vc.emit ? kFEmit : 0u) | (vc.outside ? kFOutside : 0u) | (sh.ok ? kFOk : 0u) |
+                 (sh.terminal ? kFTerminal : 0u) | (sh.delta ? kFDelta : 0u) | (sh.ev << kEvShift) |
+                 ((unsigned)ne.state << kNeeShift);
+    r.ids = make_int4(vc.prim, (vc.mat & 0xffff) | (ne.l << 16), vc.light, (int)f);
+    r.pad = make_float4(0.f, 0.f, 0.f, 0.f);
+    *p = r;
+}
+// (the ids first: a path whose ray missed reads 16 of the record's 112 bytes)
+__device__ __forceinline__ bool get_vertex(const WfVtx* p, const Walk& w, VCtx& vc, NeePending& ne, Shade& sh) {
+    WfVtx r;
+    r.ids = p->ids;
+    unsigned f = (unsigned)r.ids.w;
+    if (!(f & kFHit)) return false;
+    r.x_tu = p->x_tu; r.ng_tv = p->ng_tv; r.wi_pdf = p->wi_pdf; r.wl_ps = p->wl_ps; r.misc = p->misc; r.mat = p->mat;
+    vc.x = {r.x_tu.x, r.x_tu.y, r.x_tu.z}; vc.tu = r.x_tu.w;
+    vc.ng = {r.ng_tv.x, r.ng_tv.y, r.ng_tv.z}; vc.tv = r.ng_tv.w;
+    vc.wo = -w.d;
+    vc.n = dot(vc.ng, vc.wo) >= 0.0f ? vc.ng : -vc.ng;
+    vc.prim = r.ids.x; vc.mat = r.ids.y & 0xffff; vc.light = r.ids.z;
+    vc.emit = f & kFEmit; vc.outside = f & kFOutside;
+    vc.w_emit = r.misc.z; vc.p_event = r.misc.w;
+    vc.event = 0; vc.pdf = 1.0f; vc.nee = false; vc.scatter = false; vc.nee_light = -1; vc.nee_w = 0.0f;
+    vc.wl = f3{0.f, 0.f, 0.f}; vc.wi = vc.wl;
+    sh.wi = {r.wi_pdf.x, r.wi_pdf.y, r.wi_pdf.z}; sh.pdf = r.wi_pdf.w;
+    sh.ok = f & kFOk; sh.terminal = f & kFTerminal; sh.delta = f & kFDelta; sh.ev = (f >> kEvShift) & 3u;
+    ne.state = (int)((f >> kNeeShift) & 3u);
+    ne.l = r.ids.y >> 16;
+    ne.wl = {r.wl_ps.x, r.wl_ps.y, r.wl_ps.z}; vc.pspec = r.wl_ps.w;
+    ne.pl = r.misc.x; ne.cx = r.misc.y;
+    vc.alpha = r.mat.x; vc.alb[0] = r.mat.y; vc.alb[1] = r.mat.z; vc.alb[2] = r.mat.w;
+    return true;
+}
+
+constexpr int kMissCode = (int)0x80000000;
+
+struct WfState {
+    WfPath* path;
+    WfVtx* vtx;
+    float4* hit;        // (t, b1, b2, BVH slot | -(sphere + 1) | kMissCode)
+    WfRay* ray;         // shadow rays
+    int* visible;
+    float4* raw;        // raw Stokes per path, 3 per path
+    float* cache;
+    long long Q;
+    int cap;
+    // where the traversal stores each vertex's hit for the replay: the cache record of
+    // (vertex slot, path) is rec_floats floats, its hit at hit_comp and its bin word at
+    // vis_comp (36, 32, 31: the cache of the cached replay; 4, 0, -1: the hits of the hybrid
+    // replay, which keeps no bin word)
+    int rec_floats, hit_comp, vis_comp;
+    __device__ __forceinline__ float* rec(int v, int q) const { return cache + ((long long)v * Q + q) * kWfCacheComps; }
+    __device__ __forceinline__ float* hit_rec(int v, int q) const { return cache + ((long long)v * Q + q) * rec_floats; }
+};
+// the code of a traversal's result: the BVH slot of a triangle, -(sphere + 1), or kMissCode
+__device__ __forceinline__ int code_of(const DScene& S, bool hit, const HitRec& h) {
+    return !hit ? kMissCode : h.prim < S.num_tris ? h.slot : -(h.prim - S.num_tris + 1);
+}
+// the hit of a code (not a miss)
+__device__ __forceinline__ void decode_hit(const DScene& S, const float4& hv, HitRec& h) {
+    const int code = __float_as_int(hv.w);
+    h.t = hv.x; h.b1 = hv.y; h.b2 = hv.z;
+    if (code >= 0) { h.slot = code; h.prim = __float_as_int(__ldg(&S.tris[3 * code].w)); }
+    else { h.slot = -1; h.prim = S.num_tris + (-code - 1); }
+}
+
+struct WfLists {
+    int* l0;      // live paths of the cache pass
+    int* next0;
+    int* shadow;
+    // counts of this iteration: [0] cache-pass paths, [4] shadow rays, [8 + b] replay bin b;
+    // nxt: the same for the next iteration ([0] and [8 + b] are appended to).  The two
+    // 16-int halves of the count array alternate between iterations, and each iteration's
+    // k_wf_extend zeroes the counts the iteration appends to.
+    int* cur;
+    int* nxt;
+    // replayed paths binned by the material type of their vertex: bin b at bins + b * binQ
+    // (this iteration) and nbins + b * binQ (the next one)
+    int* bins;
+    int* nbins;
+    int binQ;
+};
+
+// A wave: pieces of one or more jobs (whole pixels each) laid out back to back in the wave's
+// path slots.  Piece k holds pixels pix0 .. pix0 + npix - 1 of job `job`, its paths in slots
+// q0 .. q0 + npix * spp - 1 and its pixels at wave-pixel index qpix0 onward.
+struct WaveSeg { int job, pad; long long pix0, npix, q0, qpix0; };
+struct WaveTable {
+    WaveSeg seg[kMaxJobsPerLaunch];
+    int nseg, depth;          // pieces; the largest max_depth among them
+    long long nq, npix;       // paths and pixels of the wave
+};
+// the piece holding wave slot q (pieces are sorted by q0)
+__device__ __forceinline__ int wave_piece_of_slot(const WaveTable& wt, long long q) {
+    int lo = 0, hi = wt.nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (wt.seg[mid].q0 <= q) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int wave_piece_of_pixel(const WaveTable& wt, long long i) {
+    int lo = 0, hi = wt.nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (wt.seg[mid].qpix0 <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+// starts the path of wave slot q: camera ray, path record, job-local path id
+__device__ __forceinline__ void wave_start_path(const DScene& S, const JobTable& T, const WaveTable& wt, int q,
+                                                WfState& W, Walk& w) {
+    const WaveSeg& sg = wt.seg[wave_piece_of_slot(wt, q)];
+    const DJob& J = T.job[sg.job];
+    const unsigned long long pid = (unsigned long long)(sg.pix0 * J.spp + (q - sg.q0));
+    walk_begin(S, J, pid, (long long)(pid / J.spp), w);
+    put_walk(W.path + q, w);
+    W.path[q].meta = WfMeta{(unsigned)pid, (unsigned)(pid >> 32), sg.job, 0};
+}
+
+// Replay bins: the material types with a replay kernel of their own (diffuse, rough
+// conductor, rough dielectric, polarizer and retarder sheets), and one bin for everything
+// else (smooth dielectrics, emitter hits, paths that left the scene).
+constexpr int kBinOther = 7;
+// the bin word of a cache slot whose ray left the scene: the replay of a path ends at the
+// vertex before it, with no launch for the miss
+constexpr int kBinMiss = 15;
+constexpr unsigned kBinnedTypes = (1u << DPPT_MAT_DIFFUSE) | (1u << DPPT_MAT_CONDUCTOR_GGX) |
+                                  (1u << DPPT_MAT_PLASTIC_GGX) | (1u << DPPT_MAT_POLARIZER_SHEET) |
+                                  (1u << DPPT_MAT_RETARDER_SHEET);
+
+// Appends path q to the next iteration's replay bin b.  Appends are warp-aggregated: the
+// lanes of a warp going to the same bin take consecutive slots with one atomic.
+__device__ __forceinline__ void bin_append(const WfLists& L, int b, int q) {
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, b);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(L.nxt + 8 + b, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    L.nbins[(long long)b * L.binQ + base + __popc(peers & ((1u << lane) - 1u))] = q;
+}
+
+// The cache record's visibility word (kWfVisComp) holds, as an int, the light sample's
+// visibility in bit 0 and the vertex's replay bin above it: the material type when that
+// type has a replay kernel of its own, kBinMiss when the ray left the scene, else kBinOther.
+__device__ __forceinline__ int replay_bin(const DScene& S, int mat) {
+    const int t = __ldg(&S.mats[mat].type);
+    return (kBinnedTypes >> t) & 1u ? t : kBinOther;
+}
+__device__ __forceinline__ int replay_bin_of(const WfState& W, int q, int v) {
+    return __float_as_int(W.rec(v, q)[kWfVisComp]) >> 1;
+}
+
+}  // namespace dppt
+
+namespace dppt {
+
+// The hybrid cached replay (Sec. 4.4) in the wavefront schedule: the traversal stores each
+// vertex's hit (16 B, in WfState's cache with a 4-float stride) and the cache pass its light
+// sample's visibility (a byte), instead of the 144-byte cached vertex; per path the hybrid
+// visitor keeps its block data [nb][60], route bytes [rstride], look-ahead [K][31], the
+// replay's running block throughput and emission [60] and the flags of recomputed blocks
+// [fw], all in the workspace (layout: wavefront_bytes with K > 1).
+struct HybWs {
+    float* ck;
+    unsigned char* route;
+    float* blk;
+    float* btr;
+    unsigned* flags;
+    unsigned char* vis;     // [vertex slot][Q]
+    int nb, rstride, fw;
+    float gamma, eps;
+};
+// the hybrid's cache pass (phase 0) or replay (phase 1) over this iteration's cache-pass list
+// or replay list (replay bin kBinOther), for checkpoint interval K in {4, 8, 16}
+cudaError_t launch_wf_hybrid(int phase, int K, const DScene& S, const DParams& P, const DGrads& G,
+                             const JobTable& T, const WfState& W, const WfLists& L, const HybWs& H, int grid,
+                             size_t smem, cudaStream_t st);
+
+}  // namespace dppt

@@ -11,7 +11,8 @@ every k vertices; with --pprb, for the basic polarized PRB baseline, which keeps
   * megakernel schedules: the per-thread local cache (bytes per thread, from the compiled
     kernel) times the threads resident on the GPU -- independent of the image size;
   * wavefront schedule: the library workspace (path state + per-vertex cache of one wave,
-    waves capped at 32 GiB).
+    waves capped at 32 GiB; with the hybrid, each vertex's hit and the checkpoint data
+    instead of the cache).  --hybrid runs on every schedule given with --hybrid-schedules.
 The loss is a seeded linear functional of the image.  Prints one JSON line per
 (schedule, depth) and a final summary line.
 
@@ -39,6 +40,7 @@ def main(argv=None):
     ap.add_argument("--height", type=int, default=720)
     ap.add_argument("--sheets", type=int, default=85)
     ap.add_argument("--hybrid", type=int, nargs="*", default=[], help="checkpoint intervals k of hybrid replay runs")
+    ap.add_argument("--hybrid-schedules", nargs="+", default=["grid"], choices=list(SCHEDULE_IDS))
     ap.add_argument("--gamma", type=float, default=0.0)
     ap.add_argument("--eps", type=float, default=float("inf"))
     ap.add_argument("--pprb", type=float, default=None,
@@ -54,12 +56,13 @@ def main(argv=None):
     gs = api.GpuScene(dctx, scene)
     stream = torch.cuda.Stream()
     rows = []
-    runs = [(s_, 1, "cached") for s_ in args.schedules] + [("grid", k, "cached") for k in args.hybrid]
+    runs = [(s_, 1, "cached") for s_ in args.schedules] + [(s_, k, "cached") for s_ in args.hybrid_schedules
+                                                                 for k in args.hybrid]
     if args.pprb is not None:
         runs.append(("grid", 1, "pprb"))
     for sched, kint, method in runs:
         dctx.set_replay(kint, args.gamma, args.eps, method=method, sigma=args.pprb or 0.0)
-        label = "grid/pprb" if method == "pprb" else sched if kint == 1 else f"grid/hybrid-k{kint}"
+        label = "grid/pprb" if method == "pprb" else sched if kint == 1 else f"{sched}/hybrid-k{kint}"
         for d in args.depths:
             job = copy.copy(job0)
             job.max_depth = d

@@ -5,7 +5,9 @@ Thresholds are chosen where the route decisions cannot flip between FP32 and FP6
 gamma = 0 never takes the scalar route; eps = +inf never inverts (every non-checkpoint
 suffix recomputed: the exact gradient); eps = 1e-3 inverts only blocks whose |det| is far
 from it (polarizers and diffuse bounces have det 0, retarders det 1).  The scalar route is
-tested on the diffuse furnace, where every block throughput has DI = 0 exactly."""
+tested on the diffuse furnace, where every block throughput has DI = 0 exactly.  Every
+schedule runs the hybrid: the megakernels trace a recomputed block again, the wavefront
+re-shades it from the hits it keeps per vertex."""
 import math
 
 import numpy as np
@@ -87,7 +89,7 @@ def _compare(scene, got, ref, name):
     assert checked >= 2
 
 
-@pytest.mark.parametrize("sched", [0, 1], ids=["grid", "persistent"])
+@pytest.mark.parametrize("sched", [0, 1, 2], ids=["grid", "persistent", "wavefront"])
 @pytest.mark.parametrize("cfg", CONFIGS, ids=[f"k{c[0]}_eps{c[2]}" for c in CONFIGS])
 @pytest.mark.parametrize("name", list(SCENES))
 def test_hybrid_matches_oracle(env, name, cfg, sched):
@@ -104,21 +106,23 @@ def test_hybrid_matches_oracle(env, name, cfg, sched):
     _compare(scene, got, ref, name)
 
 
-def test_hybrid_exact_routes_equal_cached_replay(env):
+@pytest.mark.parametrize("sched", [0, 2], ids=["grid", "wavefront"])
+def test_hybrid_exact_routes_equal_cached_replay(env, sched):
     """With eps = +inf the hybrid is exact: it matches the oracle's fully cached replay."""
     api, dctx, O = env
     scene, job = SCENES["deep"]
     job.pass_id = 1
     try:
         dI = _adjoint_input(api, dctx, scene, job, O, 3)
-        got = _gpu_grad(api, dctx, scene, job, dI, 0, 8, 0.0, INF)
+        got = _gpu_grad(api, dctx, scene, job, dI, sched, 8, 0.0, INF)
         ref = O.OracleScene(scene).gradient(job, scene.params(), dI, mode="replay")
     finally:
         job.pass_id = 0
     _compare(scene, got, ref, "deep")
 
 
-def test_hybrid_scalar_route_on_furnace(env):
+@pytest.mark.parametrize("sched", [0, 2], ids=["grid", "wavefront"])
+def test_hybrid_scalar_route_on_furnace(env, sched):
     """Every block of the diffuse furnace is an ideal depolarizer: the scalar PRB route is
     taken for every non-checkpoint vertex and is exact."""
     api, dctx, O = env
@@ -126,7 +130,7 @@ def test_hybrid_scalar_route_on_furnace(env):
     job.max_depth = 30
     job.pass_id = 1
     dI = np.random.default_rng(4).normal(size=(job.num_angles, job.num_pixels, 3, 4))
-    got = _gpu_grad(api, dctx, scene, job, dI, 0, 4, 0.5, INF)
+    got = _gpu_grad(api, dctx, scene, job, dI, sched, 4, 0.5, INF)
     _, routes = O.OracleScene(scene).gradient_hybrid(job, scene.params(), dI, 4, 0.5, INF)
     ref = O.OracleScene(scene).gradient(job, scene.params(), dI, mode="tape")
     assert routes["scalar"] > 0 and routes["recompute"] == 0
@@ -148,8 +152,9 @@ def test_hybrid_settings_and_errors(env):
     import torch
     prev = dctx.get_launch()
     dctx.set_launch(2, 128, 0)
-    dctx.set_replay(8, 0.0, INF)
+    dctx.set_replay(1, method="pprb", sigma=0.01)
     try:
+        # P-PRB has no wavefront form
         with pytest.raises(_lib.DpptError, match="UNSUPPORTED"):
             api.render_adjoint(dctx, gs, batch, P, torch.zeros(batch.image_floats, device="cuda"))
     finally:
@@ -170,3 +175,31 @@ def test_hybrid_footprint_is_smaller(env):
         dctx.set_launch(*prev)
     assert full["local_bytes_per_thread"] >= 128 * 124
     assert hyb["local_bytes_per_thread"] < 0.5 * full["local_bytes_per_thread"]
+
+
+def test_wavefront_hybrid_workspace_and_primal(env):
+    """The wavefront with k = 16 keeps each vertex's hit and the checkpoint data instead of
+    the 144-byte cached vertex: at depth 128 its workspace is at most half the cached
+    replay's.  Its primal waves fold over blocks; the image equals the cached primal's to
+    FP32 rounding."""
+    import torch
+    from parity import image_rel_err, flat
+    api, dctx, _ = env
+    scene, job = SCENES["deep"]
+    gs = api.GpuScene(dctx, scene)
+    batch = api.pack_jobs([job])
+    P = api.device_params(scene, batch)
+    prev = dctx.get_launch()
+    dctx.set_launch(2, 128, 0)
+    try:
+        full = dctx.query_workspace(batch)
+        img_full = api.image_views(batch, api.render_primal(dctx, gs, batch, P))[0].double().cpu().numpy()
+        dctx.set_replay(16, 0.0, INF)
+        hyb = dctx.query_workspace(batch)
+        img_hyb = api.image_views(batch, api.render_primal(dctx, gs, batch, P))[0].double().cpu().numpy()
+        dctx.sync_status()
+    finally:
+        dctx.set_replay(1)
+        dctx.set_launch(*prev)
+    assert hyb <= 0.5 * full, (hyb, full)
+    assert float(image_rel_err(flat(img_hyb), flat(img_full)).max()) <= 1e-4
