@@ -13,12 +13,13 @@ with nonzero determinants) behind a quarter-wave plate and a polarizer, max dept
 the thresholds do choose approximate routes.  A seeded linear loss on the image.
 Reference: the fully cached replay (k = 1), which equals the FP64 oracle's gradient within
 the parity tolerance.  For each (k, gamma, eps): the relative L2 error of every gradient
-group, the adjoint time (CUDA events, median of `reps`) and the per-thread local cache of
-the hybrid megakernel times the resident threads.  Prints one JSON line per configuration
-and a summary line.
+group, the adjoint time (CUDA events, median of `reps`) and the memory of the replay: on
+the grid schedule the per-thread local cache of the megakernel times the resident threads,
+on the wavefront the library workspace.  Prints one JSON line per configuration and a
+summary line.
 
-  python -m paper_2607_13265_gb300.hybrid_sweep [--scene deep|rocks] [--depth 64] [--ks 4 8 16]
-      [--gammas ...] [--epss ...]
+  python -m paper_2607_13265_gb300.hybrid_sweep [--scene deep|rocks] [--schedule grid|wavefront]
+      [--depth 64] [--ks 4 8 16] [--gammas ...] [--epss ...]
 """
 from __future__ import annotations
 
@@ -39,6 +40,7 @@ def main(argv=None):
     ap.add_argument("--width", type=int, default=None, help="default: 1280 deep, 256 rocks")
     ap.add_argument("--height", type=int, default=None, help="default: 720 deep, 256 rocks")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--schedule", choices=["grid", "wavefront"], default="grid")
     args = ap.parse_args(argv)
 
     import torch
@@ -57,7 +59,8 @@ def main(argv=None):
     adj = api.pack_jobs(api.adjoint_jobs([job]))
     P = api.device_params(scene, adj)
     dI = torch.as_tensor(np.random.default_rng(3).normal(size=adj.image_floats), dtype=torch.float32, device="cuda")
-    dctx.set_launch(0, 128, 0)
+    wave = args.schedule == "wavefront"
+    dctx.set_launch(2 if wave else 0, 128, 0)
 
     def run(k, gamma, eps):
         dctx.set_replay(k, gamma, eps)
@@ -73,7 +76,7 @@ def main(argv=None):
             times.append(a.elapsed_time(b))
         dctx.sync_status()
         fp = dctx.adjoint_footprint(job.max_depth)
-        cache = fp["local_bytes_per_thread"] * fp["threads_per_sm"] * fp["sms"]
+        cache = dctx.query_workspace(adj) if wave else fp["local_bytes_per_thread"] * fp["threads_per_sm"] * fp["sms"]
         return {n: v.double().cpu().numpy() for n, v in g.items()}, float(np.median(times)), int(cache)
 
     ref, t_ref, cache_ref = run(1, 0.0, float("inf"))
@@ -103,7 +106,7 @@ def main(argv=None):
                 print(json.dumps(row), flush=True)
     dctx.set_replay(1)
     print(json.dumps({"workload": (f"deep_stack85_{W_}x{H_}_{spp}spp_depth{depth}" if deep
-                                   else f"rocks100k_{W_}x{H_}_{spp}spp_depth{depth}"),
+                                   else f"rocks100k_{W_}x{H_}_{spp}spp_depth{depth}"), "schedule": args.schedule,
                       "reference": "fully cached replay (k = 1)",
                       "summary": [(r["k"], r["gamma"], r["eps"], round(r["adjoint_ms"], 1), r["cache_bytes"],
                                    {n: (round(v, 5) if v is not None else None) for n, v in r["errors"].items()})
