@@ -14,6 +14,10 @@ the same seeded inputs and paths, at the workloads' full sizes.
   gradient of a nonnegative intensity loss on an 8x8 crop (the 1024^2 maps on 32x32-texel
   block sums, as in test_gpu_workloads).
 
+Each workload runs in the launch configuration its benchmark or run uses: the icosphere,
+rocks and large workloads on the wavefront (4,194,304-path waves), the views with the grid
+primal and the wavefront adjoint, Cornell on the grid megakernel.
+
 Images: the per-pixel relative error of tests/parity.py (p99.9 and max) over pixels whose
 paths are all identical in FP32 and FP64, once over all of them and once over the
 well-conditioned ones, whose FP64 image moves by at most 1e-5 when the inputs are rounded to
@@ -40,6 +44,17 @@ pytestmark = pytest.mark.gpu
 
 TABLE = {}
 COND_MOVE = 1e-5
+WAVEFRONT = (2, 128, 0, 2, 64, 0, 1)          # primal / adjoint schedule, block, blocks per SM; lane scatter
+VIEWS_LAUNCH = (0, 256, 0, 2, 64, 0, 0)
+
+
+@pytest.fixture
+def launch(env):
+    """Sets the context's launch shapes for one test and restores them."""
+    dctx = env[2]
+    prev = dctx.get_launch()
+    yield lambda shape: dctx.set_launch(*shape)
+    dctx.set_launch(*prev)
 
 
 @pytest.fixture(scope="module")
@@ -175,22 +190,26 @@ def _sampled_and_crop(env, name, scene, job, npix, crop, nonneg=False, block_map
     _record(name, image, _grad_errors(got, ref, scene, block_maps))
 
 
-def test_icosphere(env):
+def test_icosphere(env, launch):
+    launch(WAVEFRONT)
     scene, job = sg.icosphere_scene()
     _sampled_and_crop(env, "icosphere", scene, job, 256, _crop(job, 120, 120, 16), seed=3)
 
 
-def test_rocks(env):
+def test_rocks(env, launch):
+    launch(WAVEFRONT)
     scene, job = sg.rocks_scene()
     _sampled_and_crop(env, "rocks", scene, job, 256, _crop(job, 300, 220, 8), seed=5)
 
 
-def test_large(env):
+def test_large(env, launch):
+    launch(WAVEFRONT)
     scene, job = sg.large_scene()
     _sampled_and_crop(env, "large", scene, job, 24, _crop(job, 480, 560, 8), nonneg=True, block_maps=True, seed=23)
 
 
-def test_views(env):
+def test_views(env, launch):
+    launch(VIEWS_LAUNCH)
     torch, api, dctx, O = env
     scene, jobs = sg.cornell_views(8, 64, 16, 8)
     gs = api.GpuScene(dctx, scene)
