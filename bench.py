@@ -760,7 +760,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50, help="timed steps (graph replays: p50 and p99 over them)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--schedule", type=int, default=None, help="0 grid, 1 persistent, 2 wavefront (default: autotuner)")
