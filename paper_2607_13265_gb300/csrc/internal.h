@@ -108,7 +108,8 @@ struct LaunchCfg {
 };
 
 // Kernel launches per stage, and (when timing is on) CUDA events recorded on
-// the launching stream around every launch.
+// the launching stream around every record: one launch, or several (begin's `kernels`)
+// issued back to back for one stage.
 enum Stage {
     kStagePrimal = 0, kStageAdjoint, kStageWfInit, kStageWfExtend, kStageWfShade, kStageWfShadow,
     kStageWfCache, kStageWfReplay, kStageReserved, kStageWfPixels, kStageFilter, kStageCount
@@ -124,8 +125,8 @@ struct StageLog {
         if (spare.empty()) { cudaEvent_t e = nullptr; cudaEventCreate(&e); return e; }
         cudaEvent_t e = spare.back(); spare.pop_back(); return e;
     }
-    int begin(int stage, cudaStream_t st) {
-        launches[stage]++;
+    int begin(int stage, cudaStream_t st, int kernels = 1) {
+        launches[stage] += kernels;
         if (!timing) return -1;
         Rec r{stage, take(), take()};
         cudaEventRecord(r.a, st);

@@ -552,8 +552,8 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                 if ((e = launch_wf_hybrid(1, hy.k, S, P, G, T, W, L, H, fgrid, smem, st)) != cudaSuccess) return e;
                 log->end(tok, st);
             } else if (mode == 1 && it > 0) {
-                tok = log->begin(kStageWfReplay, st);
                 // one replay kernel per binned material type present, then the other bin
+                tok = log->begin(kStageWfReplay, st, 1 + __builtin_popcount(types & kBinnedTypes));
                 const ReplayArgs ra{S, P, G, T, W, L, fgrid, smem, st, nmaps};
                 if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) launch_replay_bin<DPPT_MAT_CONDUCTOR_GGX>(ra);
                 if (types & (1u << DPPT_MAT_PLASTIC_GGX)) launch_replay_bin<DPPT_MAT_PLASTIC_GGX>(ra);
