@@ -1530,9 +1530,12 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
         long long g = pers ? L.grid : T.total_chunks;                                                            \
         if (g <= 0) return cudaSuccess;                                                                          \
         if (g > 0x7fffffffLL) g = 0x7fffffffLL;                                                                  \
-        if (mode == 0)                                                                                           \
-            k_trace<B, 0, false><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, nullptr);         \
-        else if (mode == 1) {                                                                                    \
+        if (mode == 0) {                                                                                         \
+            if (S.tri_tan)                                                                                       \
+                k_trace<B, 0, false, true><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, nullptr); \
+            else                                                                                                 \
+                k_trace<B, 0, false, false><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, nullptr);\
+        } else if (mode == 1) {                                                                                  \
             size_t sm = sgrad_bytes(S);                                                                         \
             if (S.tri_tan)                                                                                       \
                 k_trace<B, 1, false, true><<<(int)g, L.block, sm, st>>>(S, P, G, T, counter, status, pers, nullptr); \
@@ -1542,15 +1545,15 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
             k_trace<B, 0, true><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, work);             \
         return cudaGetLastError();                                                                               \
     }                                                                                                            \
-    /* the adjoint's attributes are those of the kernel without normal-map code (the same  */                  \
-    /* launch bounds as the one with it)                                                    */                  \
+    /* the attributes are those of the kernels without normal-map code (the same launch     */                  \
+    /* bounds as the ones with it)                                                          */                  \
     cudaError_t trace_attributes_##B(int mode, cudaFuncAttributes* a) {                                         \
-        return cudaFuncGetAttributes(a, mode == 0 ? reinterpret_cast<const void*>(&k_trace<B, 0, false>)          \
+        return cudaFuncGetAttributes(a, mode == 0 ? reinterpret_cast<const void*>(&k_trace<B, 0, false, false>)   \
                                                   : reinterpret_cast<const void*>(&k_trace<B, 1, false, false>)); \
     }                                                                                                            \
     int trace_occupancy_##B(int mode, int block, size_t smem) {                                                  \
         int nb = 0;                                                                                              \
-        const void* f = mode == 0 ? reinterpret_cast<const void*>(&k_trace<B, 0, false>)                          \
+        const void* f = mode == 0 ? reinterpret_cast<const void*>(&k_trace<B, 0, false, false>)                   \
                                   : reinterpret_cast<const void*>(&k_trace<B, 1, false, false>);                 \
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, smem) != cudaSuccess) return 0;          \
         return nb;                                                                                               \

@@ -39,8 +39,6 @@
 #ifndef DPPT_WF_REPLAY_DIFFUSE_MIN_BLOCKS
 #define DPPT_WF_REPLAY_DIFFUSE_MIN_BLOCKS 4
 #endif
-// resident 512-thread blocks per SM the shade kernel's register allocation must allow
-// (2 -> at most 64 registers per thread)
 // resident 512-thread blocks per SM the fused extend + shade kernel's registers must allow
 #ifndef DPPT_WF_EXTEND_SHADE_MIN_BLOCKS
 #define DPPT_WF_EXTEND_SHADE_MIN_BLOCKS 2
@@ -49,6 +47,8 @@
 #ifndef DPPT_WF_FUSE_SHADE
 #define DPPT_WF_FUSE_SHADE 1
 #endif
+// resident 512-thread blocks per SM the shade kernel's register allocation must allow
+// (2 -> at most 64 registers per thread)
 #ifndef DPPT_WF_SHADE_MIN_BLOCKS
 #define DPPT_WF_SHADE_MIN_BLOCKS 2
 #endif
