@@ -114,6 +114,9 @@ def stage_flops(w: dict, passes: int) -> dict:
     V = w["vertices"]
     out = {"wf_extend": closest, "wf_shadow": shadow, "wf_shade": V * F_SHADE, "wf_cache": V * F_CACHE}
     if passes == 2:
+        # the sweep schedule's forward sweep: one megakernel for the adjoint's tracing,
+        # shading, evaluation and fold
+        out["wf_sweep"] = closest + shadow + V * F_VERTEX_PRIMAL
         out["wf_replay"] = V * (F_REPLAY + F_SHADE)     # the replay kernels shade their own vertices
         out["adjoint"] = 2 * (closest + shadow) + V * F_VERTEX_ADJOINT
     else:

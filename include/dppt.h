@@ -65,9 +65,15 @@ enum { DPPT_FILTER_NONE = 0, DPPT_FILTER_POLARIZER = 1, DPPT_FILTER_QWP_POLARIZE
 
 /* Kernel schedule chosen by the autotuner (or set by the caller): the
  * megakernel with one block per chunk of paths, the megakernel as a
- * persistent kernel pulling chunks from an atomic counter, or the wavefront
- * schedule (stage kernels over compacted lists of live paths). */
-enum { DPPT_SCHED_GRID = 0, DPPT_SCHED_PERSISTENT = 1, DPPT_SCHED_WAVEFRONT = 2 };
+ * persistent kernel pulling chunks from an atomic counter, the wavefront
+ * schedule (stage kernels over compacted lists of live paths), or, for
+ * render_adjoint, the sweep schedule: in waves like the wavefront, each wave's
+ * forward sweep (tracing, thread-local cache, fold) in one megakernel that
+ * keeps per vertex only the hit, the light sample's visibility and the suffix,
+ * then the wavefront's replay iterations.  render_primal runs the sweep
+ * schedule as the grid schedule; with the hybrid replay (k > 1) the adjoint
+ * runs it as the wavefront schedule. */
+enum { DPPT_SCHED_GRID = 0, DPPT_SCHED_PERSISTENT = 1, DPPT_SCHED_WAVEFRONT = 2, DPPT_SCHED_SWEEP = 3 };
 
 typedef struct dppt_ctx dppt_ctx;
 typedef struct dppt_scene dppt_scene;
@@ -233,7 +239,7 @@ dppt_status dppt_render_adjoint_l2(dppt_ctx* ctx, const dppt_scene* scene, const
  * context's current launch shapes and replay: filter buffers, plus the
  * wavefront path state and per-vertex cache (with the hybrid replay, k > 1:
  * each vertex's hit and the checkpoint data instead) when a wavefront
- * schedule is selected.  The wavefront runs in waves of at most 4,194,304
+ * schedule, or the sweep schedule for the adjoint, is selected.  The wavefront runs in waves of at most 4,194,304
  * paths (whole pixels), fewer when the wave's state and cache would pass
  * 32 GiB (deep paths). */
 dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int32_t njobs, size_t* bytes);
@@ -243,13 +249,14 @@ dppt_status dppt_set_launch(dppt_ctx* ctx, const dppt_launch* launch);
 dppt_status dppt_get_launch(const dppt_ctx* ctx, dppt_launch* launch);
 
 /* Autotuner: times render_primal and render_adjoint of the given jobs for
- * every schedule (grid, persistent, wavefront) and block size (64, 128, 256),
+ * every schedule (grid, persistent, wavefront, sweep: its adjoint only) and
+ * block size (64, 128, 256),
  * then the adjoint's fastest shape with the other texel-gradient scatter
  * with CUDA events on `stream` (one warm-up call and `reps` timed calls per
  * candidate), keeps the fastest shape for each of the two calls in the
  * context and returns it in *best.  times_ms (nullable) receives the
- * measured mean milliseconds [9 candidates][2: primal, adjoint] in the order
- * schedule-major, block-minor.  Allocates its scratch image, adjoint input and
+ * measured mean milliseconds [12 candidates][2: primal, adjoint] in the order
+ * schedule-major, block-minor (+inf where a call was not timed).  Allocates its scratch image, adjoint input and
  * gradient buffers on the device and frees them before returning; gradients
  * produced while tuning are discarded.  Synchronous. */
 dppt_status dppt_autotune(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* jobs, int32_t njobs,
@@ -276,7 +283,8 @@ dppt_status dppt_autotune(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job
  * 0x5bd1e995) ^ 3 * 0x9E3779B97F4A7C15 and the job's stream, counter (path,
  * vertex), Box-Muller).  It is exact only where every factor is invertible;
  * it exists to measure that baseline (grid and persistent schedules;
- * render_adjoint returns DPPT_ERR_UNSUPPORTED with the wavefront).  Errors:
+ * render_adjoint returns DPPT_ERR_UNSUPPORTED with the wavefront and sweep
+ * schedules).  Errors:
  * INVALID_ARG for another method or k, a negative or NaN threshold or sigma. */
 enum { DPPT_REPLAY_CACHED = 0, DPPT_REPLAY_PPRB = 1 };
 typedef struct {
@@ -332,8 +340,9 @@ dppt_status dppt_render_primal_noalloc(dppt_ctx* ctx, const dppt_scene* scene, c
  * around each launch.  Stages: 0 primal megakernel, 1 adjoint megakernel,
  * 2-7 wavefront init, extend (closest hit; with the default build it also
  * shades the vertex and starts a wave's paths, so stages 2 and 4 have no
- * launches), shade, shadow (any hit), cache pass, replay pass; 8 reserved (no
- * launches); 9 wavefront pixel sums; 10 camera-filter folds.  The call
+ * launches), shade, shadow (any hit), cache pass, replay pass; 8 the sweep
+ * schedule's forward-sweep megakernel; 9 wavefront pixel sums; 10
+ * camera-filter folds.  The call
  * waits for the recorded events, copies the counters to launches[16] and
  * ms[16] (either may be NULL), clears them when reset != 0 and then sets
  * timing on or off for the following launches. */

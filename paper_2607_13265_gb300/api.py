@@ -103,7 +103,7 @@ class Context:
         return {"local_bytes_per_thread": out[0], "registers": out[1], "threads_per_sm": out[2], "sms": out[3]}
 
     STAGES = ("primal", "adjoint", "wf_init", "wf_extend", "wf_shade", "wf_shadow", "wf_cache", "wf_replay",
-              "reserved", "wf_pixels", "filter")
+              "wf_sweep", "wf_pixels", "filter")
 
     def stage_stats(self, timing: bool = False, reset: bool = True) -> dict:
         """{stage: (launches, ms)} since the last reset; then switches event timing on/off."""
@@ -251,18 +251,18 @@ def count_work(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict) -> dic
     return dict(zip(WORK_KEYS, [int(x) for x in out]))
 
 
-SCHEDULE_NAMES = {0: "grid", 1: "persistent", 2: "wavefront"}
+SCHEDULE_NAMES = {0: "grid", 1: "persistent", 2: "wavefront", 3: "sweep"}
 
 
 def autotune(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict, reps: int = 2) -> dict:
     """Run the library's autotuner on these jobs; the context keeps the fastest shapes."""
     best = L.Launch()
-    times = (ctypes.c_float * 18)()
+    times = (ctypes.c_float * 24)()
     cp = _c_params(params)
     _check(ctx.h, ctx.lib.dppt_autotune(ctx.h, gs.h, batch.c_jobs, batch.n, ctypes.byref(cp), reps,
                                         ctypes.byref(best), times), "dppt_autotune")
     table = {}
-    for si in range(3):
+    for si in range(4):
         for bi, b in enumerate((64, 128, 256)):
             k = 3 * si + bi
             table[f"{SCHEDULE_NAMES[si]}/{b}"] = {"primal_ms": times[2 * k], "adjoint_ms": times[2 * k + 1]}

@@ -826,7 +826,7 @@ dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_jo
         }
         if (wave) {
             cudaError_t e = run_wavefront(0, s->d, P, G, T, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
-                                          shape.block, hy, ctx->d_status, cs, &ctx->log);
+                                          shape.block, hy, 0, ctx->d_status, cs, &ctx->log);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront primal");
             continue;
         }
@@ -864,7 +864,7 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
     if (!ctx || !s) return fail(ctx, DPPT_ERR_INVALID_ARG, "null context or scene");
     DScene Sd = s->d;   // the adjoint launches' copy, with the texel-gradient scatter of the launch shape
     Sd.scatter_lane = ctx->launch.adj_scatter == DPPT_SCATTER_LANE ? 1 : 0;
-    Sd.sgrad_lanes = ctx->launch.adj_schedule == DPPT_SCHED_WAVEFRONT ? 1 : 0;
+    Sd.sgrad_lanes = ctx->launch.adj_schedule == DPPT_SCHED_WAVEFRONT || ctx->launch.adj_schedule == DPPT_SCHED_SWEEP;
     if (!grads) return fail(ctx, DPPT_ERR_INVALID_ARG, "grads is null");
     if (!l2 && !d_image && njobs > 0) return fail(ctx, DPPT_ERR_INVALID_ARG, "d_image is null");
     cudaSetDevice(ctx->device);
@@ -873,9 +873,9 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
     dppt_status st = check_jobs(ctx, s, jobs, njobs, params, true, plan, ws, l2 != nullptr);
     if (st != DPPT_OK) return st;
     const Shape shape = shape_of(ctx, 1);
-    const bool wave = shape.schedule == DPPT_SCHED_WAVEFRONT;
+    const bool wave = shape.schedule == DPPT_SCHED_WAVEFRONT || shape.schedule == DPPT_SCHED_SWEEP;
     if (wave && ctx->replay.method == DPPT_REPLAY_PPRB)
-        return fail(ctx, DPPT_ERR_UNSUPPORTED, "P-PRB runs on the grid and persistent schedules");
+        return fail(ctx, DPPT_ERR_UNSUPPORTED, "P-PRB runs on the grid and persistent schedules only");
     const WfHybrid hy = wf_hybrid(ctx);
     const long long Q = wave ? wave_paths(jobs, njobs, hy.k) : 0;
     const int cap = max_depth_of(jobs, njobs);
@@ -929,8 +929,9 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
             }
         }
         if (wave) {
+            const int sweep = shape.schedule == DPPT_SCHED_SWEEP ? depth_bucket(cap) : 0;
             cudaError_t e = run_wavefront(1, Sd, P, G, T, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
-                                          shape.block, hy, ctx->d_status, cs, &ctx->log);
+                                          shape.block, hy, sweep, ctx->d_status, cs, &ctx->log);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront adjoint");
             continue;
         }
@@ -1104,7 +1105,8 @@ dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int3
     for (int i = 0; i < njobs; ++i)
         if (jobs[i].filter != DPPT_FILTER_NONE)
             b = align256(b + 2 * (size_t)jobs[i].width * jobs[i].height * 12 * sizeof(float));
-    if (njobs > 0 && (ctx->launch.schedule == DPPT_SCHED_WAVEFRONT || ctx->launch.adj_schedule == DPPT_SCHED_WAVEFRONT))
+    if (njobs > 0 && (ctx->launch.schedule == DPPT_SCHED_WAVEFRONT || ctx->launch.adj_schedule == DPPT_SCHED_WAVEFRONT ||
+                      ctx->launch.adj_schedule == DPPT_SCHED_SWEEP))
         b += wavefront_bytes(wave_paths(jobs, njobs, wf_hybrid(ctx).k), max_depth_of(jobs, njobs), wf_hybrid(ctx).k);
     *bytes = b;
     return DPPT_OK;
@@ -1112,7 +1114,9 @@ dppt_status dppt_query_workspace(const dppt_ctx* ctx, const dppt_job* jobs, int3
 
 dppt_status dppt_set_launch(dppt_ctx* ctx, const dppt_launch* l) {
     if (!ctx || !l) return DPPT_ERR_INVALID_ARG;
-    auto sched_ok = [](int s) { return s == DPPT_SCHED_GRID || s == DPPT_SCHED_PERSISTENT || s == DPPT_SCHED_WAVEFRONT; };
+    auto sched_ok = [](int s) {
+        return s == DPPT_SCHED_GRID || s == DPPT_SCHED_PERSISTENT || s == DPPT_SCHED_WAVEFRONT || s == DPPT_SCHED_SWEEP;
+    };
     auto block_ok = [](int b) { return b == 64 || b == 128 || b == 256 || b == 512; };
     if (!sched_ok(l->schedule) || !sched_ok(l->adj_schedule)) return fail(ctx, DPPT_ERR_INVALID_ARG, "unknown schedule");
     if (!block_ok(l->block_size) || !block_ok(l->adj_block_size))
@@ -1197,16 +1201,18 @@ dppt_status dppt_autotune(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jo
                  g + s->tex_size + s->d.num_ior + 12 * s->d.num_lights,
                  g + s->tex_size + s->d.num_ior + 12 * s->d.num_lights + s->d.num_sheets};
     const dppt_launch saved = ctx->launch;
-    const int scheds[3] = {DPPT_SCHED_GRID, DPPT_SCHED_PERSISTENT, DPPT_SCHED_WAVEFRONT};
+    const int scheds[4] = {DPPT_SCHED_GRID, DPPT_SCHED_PERSISTENT, DPPT_SCHED_WAVEFRONT, DPPT_SCHED_SWEEP};
     const int blocks[3] = {64, 128, 256};
     float best_t[2] = {INFINITY, INFINITY};
     dppt_launch pick = saved;
     dppt_status result = DPPT_OK;
-    for (int si = 0; si < 3 && result == DPPT_OK; ++si)
+    for (int si = 0; si < 4 && result == DPPT_OK; ++si)
         for (int bi = 0; bi < 3 && result == DPPT_OK; ++bi) {
             ctx->launch = dppt_launch{scheds[si], blocks[bi], 0, scheds[si], blocks[bi], 0, DPPT_SCATTER_WARP};
             float t[2] = {INFINITY, INFINITY};
             for (int mode = 0; mode < 2; ++mode) {
+                // the sweep schedule's primal is the grid schedule's: timed once, as grid
+                if (mode == 0 && scheds[si] == DPPT_SCHED_SWEEP) continue;
                 auto call = [&]() {
                     return mode == 0 ? dppt_render_primal(ctx, s, jobs, njobs, params, image, st)
                                      : dppt_render_adjoint(ctx, s, jobs, njobs, params, dimage, &G, st);

@@ -112,7 +112,7 @@ struct LaunchCfg {
 // issued back to back for one stage.
 enum Stage {
     kStagePrimal = 0, kStageAdjoint, kStageWfInit, kStageWfExtend, kStageWfShade, kStageWfShadow,
-    kStageWfCache, kStageWfReplay, kStageReserved, kStageWfPixels, kStageFilter, kStageCount
+    kStageWfCache, kStageWfReplay, kStageWfSweep, kStageWfPixels, kStageFilter, kStageCount
 };
 struct StageLog {
     int64_t launches[kStageCount] = {0};
@@ -190,11 +190,14 @@ DPPT_DECLARE_HYBRID(16)
 
 // wavefront schedule (wavefront.cu): workspace bytes for waves of Q paths with a cache of
 // `cap` vertices (k > 1: the hybrid replay's checkpoints every k vertices instead of the
-// per-vertex cache), and the run of every job of a table (several jobs share a wave)
+// per-vertex cache), and the run of every job of a table (several jobs share a wave).
+// sweep > 0 (the adjoint of schedule DPPT_SCHED_SWEEP, fully cached replay): each wave's
+// forward sweep runs in the megakernel of cache-depth bucket `sweep` instead of the stage
+// kernels.
 struct WfHybrid { int k; float gamma, eps; };   // k = 1: the fully cached replay
 size_t wavefront_bytes(long long Q, int cap, int k);
 cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T,
-                          void* ws, long long Q, int cap, int block, const WfHybrid& hy, unsigned* status,
+                          void* ws, long long Q, int cap, int block, const WfHybrid& hy, int sweep, unsigned* status,
                           cudaStream_t st, StageLog* log);
 
 // read-only views of the opaque context and scene (host.cpp), for entry points

@@ -1184,6 +1184,27 @@ struct GlobalCache {
     }
 };
 
+// The backward fold of cached vertices top .. 0 (Sec. 4.3: L_v = E_v + W_v L_{v+1}): L enters
+// as the suffix of vertex top + 1 and leaves as that of vertex 0; the adjoint keeps each
+// suffix of a vertex v >= 1 in the cache for the replay, which reads L_{v+1}.
+template <class Cache>
+__device__ __forceinline__ void fold_cached(const Cache& C, int top, bool adjoint, float L[12]) {
+    for (int v = top; v >= 0; --v) {
+        Compact<float> W;
+        C.get_w(v, W);
+        float e[12];
+        C.get_e(v, e);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float y[4];
+            compact_apply(W, c, &L[4 * c], y);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) L[4 * c + k] = e[4 * c + k] + y[k];
+        }
+        if (adjoint && v >= 1) C.put_e(v, L);
+    }
+}
+
 // Local vector-Jacobian products of one dual-number evaluation of a replayed vertex:
 // per channel J_c = a_c^T (W_c L_c + f_c Le_c nee_w) (W and the NEE operator f from
 // eval_vertex<D3>, Ln the suffix L[v+1]); returns the three slots' derivatives, the third
@@ -1345,30 +1366,14 @@ struct PathVis {
 
     // backward fold of the cached vertices into suffixes; returns L[1] in L0
     __device__ __forceinline__ void fold(float L0[12]) {
-        float L[12];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) L[k] = has_last ? lastE[k] : 0.0f;
+        for (int k = 0; k < 12; ++k) L0[k] = has_last ? lastE[k] : 0.0f;
         int v = n - 1;
         if (has_last) {
-            if (adjoint && v >= 1) C.put_e(v, L);
+            if (adjoint && v >= 1) C.put_e(v, L0);
             --v;
         }
-        for (; v >= 0; --v) {
-            Compact<float> W;
-            C.get_w(v, W);
-            float e[12];
-            C.get_e(v, e);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float y[4];
-                compact_apply(W, c, &L[4 * c], y);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) L[4 * c + k] = e[4 * c + k] + y[k];
-            }
-            if (adjoint && v >= 1) C.put_e(v, L);
-        }
-#pragma unroll
-        for (int k = 0; k < 12; ++k) L0[k] = L[k];
+        fold_cached(C, v, adjoint, L0);
     }
 
     __device__ void replay_vertex(const VCtx& vc) {

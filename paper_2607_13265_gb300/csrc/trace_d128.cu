@@ -1,6 +1,7 @@
 // Kernels of the depth-128 cache bucket (paths of at most 128 vertices).
-#include "trace.cuh"
+#include "wavefront.cuh"
 
 namespace dppt {
 DPPT_TRACE_BUCKET(128)
+DPPT_SWEEP_BUCKET(128)
 }  // namespace dppt

@@ -1,6 +1,7 @@
 // Kernels of the depth-4 cache bucket (paths of at most 4 vertices).
-#include "trace.cuh"
+#include "wavefront.cuh"
 
 namespace dppt {
 DPPT_TRACE_BUCKET(4)
+DPPT_SWEEP_BUCKET(4)
 }  // namespace dppt

@@ -409,6 +409,33 @@ static void launch_replay_bin(const ReplayArgs& a) {
     if (a.nmaps) k_wf_finish<1, 1, true, MT, MT><<<a.grid, 128, a.smem, a.st>>>(a.S, a.P, a.G, a.T, a.W, a.L);
     else k_wf_finish<1, 1, false, MT, MT><<<a.grid, 128, a.smem, a.st>>>(a.S, a.P, a.G, a.T, a.W, a.L);
 }
+// One replay iteration: a kernel per binned material type present, then the other bin.
+static void replay_iteration(const ReplayArgs& ra, unsigned types, StageLog* log) {
+    const int tok = log->begin(kStageWfReplay, ra.st, 1 + __builtin_popcount(types & kBinnedTypes));
+    if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) launch_replay_bin<DPPT_MAT_CONDUCTOR_GGX>(ra);
+    if (types & (1u << DPPT_MAT_PLASTIC_GGX)) launch_replay_bin<DPPT_MAT_PLASTIC_GGX>(ra);
+    if (types & (1u << DPPT_MAT_DIFFUSE)) launch_replay_bin<DPPT_MAT_DIFFUSE>(ra);
+    if (types & (1u << DPPT_MAT_POLARIZER_SHEET)) launch_replay_bin<DPPT_MAT_POLARIZER_SHEET>(ra);
+    if (types & (1u << DPPT_MAT_RETARDER_SHEET)) launch_replay_bin<DPPT_MAT_RETARDER_SHEET>(ra);
+    if (ra.nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<ra.grid, 128, ra.smem, ra.st>>>(ra.S, ra.P, ra.G, ra.T, ra.W, ra.L);
+    else k_wf_finish<1, 1, false, -1, kBinOther><<<ra.grid, 128, ra.smem, ra.st>>>(ra.S, ra.P, ra.G, ra.T, ra.W, ra.L);
+    log->end(tok, ra.st);
+}
+
+// the forward-sweep megakernel of a cache-depth bucket
+static cudaError_t launch_wf_sweep(int bucket, bool nmaps, const DScene& S, const DParams& P, const JobTable& T,
+                                   const WaveTable& wt, const WfState& W, const WfLists& L, int block, unsigned* status,
+                                   cudaStream_t st) {
+    switch (bucket) {
+        case 4: return launch_wf_sweep_4(nmaps, S, P, T, wt, W, L, block, status, st);
+        case 8: return launch_wf_sweep_8(nmaps, S, P, T, wt, W, L, block, status, st);
+        case 16: return launch_wf_sweep_16(nmaps, S, P, T, wt, W, L, block, status, st);
+        case 32: return launch_wf_sweep_32(nmaps, S, P, T, wt, W, L, block, status, st);
+        case 64: return launch_wf_sweep_64(nmaps, S, P, T, wt, W, L, block, status, st);
+        case 128: return launch_wf_sweep_128(nmaps, S, P, T, wt, W, L, block, status, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 // The waves of a table's jobs: the jobs in order, each cut at pixel boundaries into pieces
 // that fill waves of at most Q paths (a wave closes when the next pixel does not fit or it
@@ -442,7 +469,7 @@ static std::vector<WaveTable> plan_waves(const JobTable& T, long long Q) {
 // Renders (mode 0) or differentiates (mode 1) every job of the table in waves of at most Q
 // paths, several jobs sharing a wave, and writes each job's per-pixel raw image to J.raw.
 cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T,
-                          void* ws, long long Q, int cap, int block, const WfHybrid& hy, unsigned* status,
+                          void* ws, long long Q, int cap, int block, const WfHybrid& hy, int sweep, unsigned* status,
                           cudaStream_t st, StageLog* log) {
     char* p = static_cast<char*>(ws);
     WfState W;
@@ -497,6 +524,25 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
         cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 32, st);
         if (e != cudaSuccess) return e;
         int tok = 0;
+        if (mode == 1 && !hyb && sweep > 0) {
+            // the forward sweep in one megakernel; every path then starts its replay at the first
+            // replay iteration, so depth iterations finish the wave
+            tok = log->begin(kStageWfSweep, st);
+            e = launch_wf_sweep(sweep, nmaps, S, P, T, wt, W, A, std::min(block, 256), status, st);
+            log->end(tok, st);
+            if (e != cudaSuccess) return e;
+            for (int it = 1; it <= wt.depth; ++it) {
+                const WfLists& L = (it & 1) ? B : A;
+                if ((e = cudaMemsetAsync(L.nxt, 0, sizeof(int) * 16, st)) != cudaSuccess) return e;
+                replay_iteration(ReplayArgs{S, P, G, T, W, L, fgrid, smem, st, nmaps}, types, log);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            }
+            tok = log->begin(kStageWfPixels, st);
+            k_wf_pixels<<<(int)((wt.npix + 127) / 128), 128, 0, st>>>(W.raw, T, wt);
+            log->end(tok, st);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            continue;
+        }
 #if !DPPT_WF_FUSE_SHADE
         tok = log->begin(kStageWfInit, st);
         k_wf_init<<<grid, block, 0, st>>>(S, T, wt, W, A);
@@ -552,17 +598,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                 if ((e = launch_wf_hybrid(1, hy.k, S, P, G, T, W, L, H, fgrid, smem, st)) != cudaSuccess) return e;
                 log->end(tok, st);
             } else if (mode == 1 && it > 0) {
-                // one replay kernel per binned material type present, then the other bin
-                tok = log->begin(kStageWfReplay, st, 1 + __builtin_popcount(types & kBinnedTypes));
-                const ReplayArgs ra{S, P, G, T, W, L, fgrid, smem, st, nmaps};
-                if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) launch_replay_bin<DPPT_MAT_CONDUCTOR_GGX>(ra);
-                if (types & (1u << DPPT_MAT_PLASTIC_GGX)) launch_replay_bin<DPPT_MAT_PLASTIC_GGX>(ra);
-                if (types & (1u << DPPT_MAT_DIFFUSE)) launch_replay_bin<DPPT_MAT_DIFFUSE>(ra);
-                if (types & (1u << DPPT_MAT_POLARIZER_SHEET)) launch_replay_bin<DPPT_MAT_POLARIZER_SHEET>(ra);
-                if (types & (1u << DPPT_MAT_RETARDER_SHEET)) launch_replay_bin<DPPT_MAT_RETARDER_SHEET>(ra);
-                if (nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L);
-                else k_wf_finish<1, 1, false, -1, kBinOther><<<fgrid, 128, smem, st>>>(S, P, G, T, W, L);
-                log->end(tok, st);
+                replay_iteration(ReplayArgs{S, P, G, T, W, L, fgrid, smem, st, nmaps}, types, log);
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }

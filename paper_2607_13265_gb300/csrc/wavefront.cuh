@@ -197,6 +197,126 @@ __device__ __forceinline__ int replay_bin_of(const WfState& W, int q, int v) {
     return __float_as_int(W.rec(v, q)[kWfVisComp]) >> 1;
 }
 
+// The cache the forward sweep folds: E_v and W_v from the thread-local arrays, the suffixes
+// into the wave's per-vertex records (components 0-11), where the replay reads them.
+template <int MAXD>
+struct SweepCache {
+    LocalCache<MAXD> loc;
+    GlobalCache glob;
+    __device__ __forceinline__ void get_w(int v, Compact<float>& W) const { loc.get_w(v, W); }
+    __device__ __forceinline__ void get_e(int v, float e[12]) const { loc.get_e(v, e); }
+    __device__ __forceinline__ void put_e(int v, const float e[12]) const { glob.put_e(v, e); }
+};
+
+// The adjoint's forward sweep in one kernel (schedule DPPT_SCHED_SWEEP), one thread per wave
+// slot: the thread runs its path to the end as the megakernel does (closest hit, shading,
+// light sample and shadow ray, E_v and the compact W_v in thread-local arrays) and keeps in the
+// slot's per-vertex records only what the replay reads back: the closest hit (kWfHitComp),
+// the light sample's visibility with the vertex's replay bin (kWfVisComp), and after the
+// backward fold the suffixes L_v of v >= 1.  It then stores the path's raw Stokes value and
+// starts the replay (the adjoint row of its pixel, the walk begun again, the path in the bin
+// of its first vertex); the replay's iterations run as in the wavefront schedule.
+template <int MAXD, bool NM>
+__global__ void __launch_bounds__(256, DPPT_MIN_BLOCKS_PRIMAL)
+k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, const __grid_constant__ WaveTable wt,
+           WfState W, WfLists L, unsigned* status) {
+    float cE[MAXD][12];
+    float cW[MAXD][19];
+    const long long qq = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (qq >= wt.nq) return;
+    const int q = (int)qq;
+    const WaveSeg& sg = wt.seg[wave_piece_of_slot(wt, q)];
+    const DJob& J = T.job[sg.job];
+    const unsigned long long pid = (unsigned long long)(sg.pix0 * J.spp + (q - sg.q0));
+    const long long pix = (long long)(pid / J.spp);
+    Walk w;
+    walk_begin(S, J, pid, pix, w);
+    PathVis<LocalCache<MAXD>, -1, NM> vis;
+    vis.S = &S; vis.P = &P; vis.G = nullptr; vis.sgrad = nullptr;
+    vis.C.cE = cE; vis.C.cW = cW;
+    vis.n = 0; vis.i = 0; vis.phase = 0; vis.has_last = false; vis.adjoint = true;
+    for (;;) {
+        HitRec h;
+        const bool hit = trace_closest<false>(S, w.o, w.d, h, status, nullptr);
+        float* rec = W.rec(w.v - 1, q);
+        if (!hit) {
+            *reinterpret_cast<float4*>(rec + kWfHitComp) = make_float4(0.f, 0.f, 0.f, __int_as_float(kMissCode));
+            rec[kWfVisComp] = __int_as_float(kBinMiss << 1);
+            break;
+        }
+        *reinterpret_cast<float4*>(rec + kWfHitComp) = make_float4(h.t, h.b1, h.b2, __int_as_float(code_of(S, true, h)));
+        VCtx vc;
+        NeePending ne;
+        Shade sh;
+        walk_shade<NM>(S, P, J, pid, w, h, vc, ne, sh);
+        bool visible = false;
+        if (ne.state == 1) visible = !trace_any<false>(S, ne.o2, ne.dir, ne.tmax, status, nullptr);
+        const bool cont = walk_finish(S, P, w, vc, ne, visible, sh, vis);
+        rec[kWfVisComp] = __int_as_float(replay_bin(S, vc.mat) << 1 | (visible ? 1 : 0));
+        if (!cont) break;
+    }
+    SweepCache<MAXD> C;
+    C.loc = vis.C;
+    C.glob.base = W.cache; C.glob.Q = W.Q; C.glob.q = q; C.glob.cap = W.cap;
+    float L0[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) L0[k] = vis.has_last ? vis.lastE[k] : 0.0f;
+    int top = vis.n - 1;
+    if (vis.has_last) {
+        if (top >= 1) C.put_e(top, L0);
+        --top;
+    }
+    fold_cached(C, top, true, L0);
+    const Rot<float> Rc = camera_rot(S.cams[J.cam], w.d1);
+    const float inv = 1.0f / (float)J.spp;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float v[4] = {L0[4 * c], L0[4 * c + 1], L0[4 * c + 2], L0[4 * c + 3]};
+        rot_apply(Rc, v);
+        W.raw[3 * (long long)q + c] = make_float4(v[0] * inv, v[1] * inv, v[2] * inv, v[3] * inv);
+    }
+    if (vis.n == 0) {
+        if (J.sig) J.sig[pid] = fnv(w.sig, (unsigned)w.nv);
+        return;
+    }
+    const float* ds = J.dS + pix * 12;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float av[4] = {__ldg(ds + 4 * c) * inv, __ldg(ds + 4 * c + 1) * inv, __ldg(ds + 4 * c + 2) * inv,
+                       __ldg(ds + 4 * c + 3) * inv};
+        rot_apply_row(Rc, av);
+        W.path[q].arow[c] = make_float4(av[0], av[1], av[2], av[3]);
+    }
+    walk_begin(S, J, pid, pix, w);
+    put_walk(W.path + q, w);
+    W.path[q].meta = WfMeta{(unsigned)pid, (unsigned)(pid >> 32), sg.job, 1 | (vis.n << 8)};
+    bin_append(L, replay_bin_of(W, q, 0), q);
+}
+
+// one translation unit per cache depth instantiates the forward-sweep kernels and their launcher
+#define DPPT_SWEEP_BUCKET(B)                                                                                        \
+    cudaError_t launch_wf_sweep_##B(bool nmaps, const DScene& S, const DParams& P, const JobTable& T,              \
+                                    const WaveTable& wt, const WfState& W, const WfLists& L, int block,           \
+                                    unsigned* status, cudaStream_t st) {                                          \
+        const long long g = (wt.nq + block - 1) / block;                                                         \
+        if (g <= 0) return cudaSuccess;                                                                          \
+        if (nmaps) k_wf_sweep<B, true><<<(int)g, block, 0, st>>>(S, P, T, wt, W, L, status);                       \
+        else k_wf_sweep<B, false><<<(int)g, block, 0, st>>>(S, P, T, wt, W, L, status);                           \
+        return cudaGetLastError();                                                                               \
+    }
+
+#define DPPT_DECLARE_SWEEP(B)                                                                                       \
+    cudaError_t launch_wf_sweep_##B(bool nmaps, const DScene& S, const DParams& P, const JobTable& T,              \
+                                    const WaveTable& wt, const WfState& W, const WfLists& L, int block,           \
+                                    unsigned* status, cudaStream_t st);
+DPPT_DECLARE_SWEEP(4)
+DPPT_DECLARE_SWEEP(8)
+DPPT_DECLARE_SWEEP(16)
+DPPT_DECLARE_SWEEP(32)
+DPPT_DECLARE_SWEEP(64)
+DPPT_DECLARE_SWEEP(128)
+#undef DPPT_DECLARE_SWEEP
+
 }  // namespace dppt
 
 namespace dppt {

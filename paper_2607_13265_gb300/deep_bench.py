@@ -10,9 +10,10 @@ replay and, with --hybrid k.., for the hybrid cached replay of Sec. 4.4 with che
 every k vertices; with --pprb, for the basic polarized PRB baseline, which keeps no cache):
   * megakernel schedules: the per-thread local cache (bytes per thread, from the compiled
     kernel) times the threads resident on the GPU -- independent of the image size;
-  * wavefront schedule: the library workspace (path state + per-vertex cache of one wave,
-    waves capped at 32 GiB; with the hybrid, each vertex's hit and the checkpoint data
-    instead of the cache).  --hybrid runs on every schedule given with --hybrid-schedules.
+  * wavefront and sweep schedules: the library workspace (path state + per-vertex cache of
+    one wave, waves capped at 32 GiB; with the hybrid, each vertex's hit and the checkpoint
+    data instead of the cache; the sweep's megakernel also holds the thread-local cache of
+    its resident threads).  --hybrid runs on every schedule given with --hybrid-schedules.
 The loss is a seeded linear functional of the image.  Prints one JSON line per
 (schedule, depth) and a final summary line.
 
@@ -27,7 +28,7 @@ import json
 
 import numpy as np
 
-SCHEDULE_IDS = {"grid": 0, "persistent": 1, "wavefront": 2}
+SCHEDULE_IDS = {"grid": 0, "persistent": 1, "wavefront": 2, "sweep": 3}
 
 
 def main(argv=None):
@@ -102,7 +103,7 @@ def main(argv=None):
                    "vertices_per_path": work["vertices"] / job.num_paths,
                    "primal_ms": float(np.median(tp)), "adjoint_ms": float(np.median(ta)),
                    "adjoint_vertices_per_s": work["vertices"] / (float(np.median(ta)) / 1e3),
-                   "cache_bytes": int(ws if sched == "wavefront" else mega_cache),
+                   "cache_bytes": int(ws if sched in ("wavefront", "sweep") else mega_cache),
                    "replay": {"method": method, "checkpoint_interval": kint, "gamma": args.gamma, "eps": args.eps,
                               "sigma": args.pprb if method == "pprb" else None},
                    "workspace_bytes": int(ws), "local_bytes_per_thread": int(fp["local_bytes_per_thread"]),

@@ -64,9 +64,11 @@ def test_workspace_grows_with_depth_in_the_wavefront(env):
             sizes.append(dctx.query_workspace(api.pack_jobs([job])))
         dctx.set_launch(0, 128, 0)
         grid = dctx.query_workspace(api.pack_jobs([job]))
+        dctx.set_launch(3, 128, 0)      # the sweep's adjoint keeps the wavefront's waves
+        sweep = dctx.query_workspace(api.pack_jobs([job]))
     finally:
         dctx.set_launch(*prev)
-    assert sizes[0] < sizes[1] < sizes[2]
+    assert sizes[0] < sizes[1] < sizes[2] == sweep
     # the cache grows by 144 bytes per vertex and path (64x64 pixels x 16 spp)
     assert sizes[2] - sizes[1] >= 24 * 144 * job.num_paths
     assert grid < sizes[0]
@@ -95,6 +97,34 @@ def test_stage_statistics_count_launches(env):
     assert st_grid["wf_extend"][0] == 0
 
 
+def test_stage_statistics_of_the_sweep_schedule(env):
+    """The sweep schedule's adjoint: one forward-sweep megakernel per wave, then max_depth
+    replay iterations (every path starts its replay at the first), one pixel sum; none of
+    the forward sweep's stage kernels.  Its primal is the grid schedule's megakernel."""
+    import torch
+    api, dctx, _ = env
+    scene, job = sg.cornell_box()
+    gs = api.GpuScene(dctx, scene)
+    prev = dctx.get_launch()
+    try:
+        dctx.set_launch(3, 128, 0)
+        dctx.stage_stats(timing=False, reset=True)
+        (img,), batch, P = gpu_image(api, dctx, gs, [job])
+        st_p = dctx.stage_stats(timing=False, reset=True)
+        dI = torch.ones(img.size, dtype=torch.float32, device="cuda")
+        api.render_adjoint(dctx, gs, batch, P, dI)
+        dctx.sync_status()
+        st = dctx.stage_stats(timing=False, reset=True)
+    finally:
+        dctx.set_launch(*prev)
+    assert st_p["primal"][0] == 1 and st_p["wf_sweep"][0] == 0
+    assert st["wf_sweep"][0] == 1 and st["wf_pixels"][0] == 1
+    assert st["wf_extend"][0] == st["wf_shadow"][0] == st["wf_cache"][0] == 0
+    assert st["primal"][0] == st["adjoint"][0] == 0
+    n = st["wf_replay"][0]
+    assert n >= job.max_depth and n % job.max_depth == 0
+
+
 def test_autotune_picks_valid_shapes_with_equal_results(env):
     import torch
     api, dctx, _ = env
@@ -110,7 +140,9 @@ def test_autotune_picks_valid_shapes_with_equal_results(env):
         g_ref = {k: v.double().cpu().numpy() for k, v in api.render_adjoint(dctx, gs, batch, P, dI).items()}
         t = api.autotune(dctx, gs, batch, P, reps=1)
         assert t["primal"][0] in ("grid", "persistent", "wavefront") and t["primal"][1] in (64, 128, 256)
-        assert t["adjoint"][0] in ("grid", "persistent", "wavefront") and t["adjoint"][1] in (64, 128, 256)
+        assert t["adjoint"][0] in ("grid", "persistent", "wavefront", "sweep") and t["adjoint"][1] in (64, 128, 256)
+        assert all(np.isinf(t["times_ms"][f"sweep/{b}"]["primal_ms"]) for b in (64, 128, 256))
+        assert all(np.isfinite(t["times_ms"][f"sweep/{b}"]["adjoint_ms"]) for b in (64, 128, 256))
         assert t["adjoint_scatter"] in ("warp", "lane")
         timed = [v for v in t["times_ms"].values() if v["primal_ms"] > 0]
         assert len(timed) >= 3

@@ -89,7 +89,8 @@ def _compare(scene, got, ref, name):
     assert checked >= 2
 
 
-@pytest.mark.parametrize("sched", [0, 1, 2], ids=["grid", "persistent", "wavefront"])
+# the sweep schedule runs the hybrid replay as the wavefront schedule
+@pytest.mark.parametrize("sched", [0, 1, 2, 3], ids=["grid", "persistent", "wavefront", "sweep"])
 @pytest.mark.parametrize("cfg", CONFIGS, ids=[f"k{c[0]}_eps{c[2]}" for c in CONFIGS])
 @pytest.mark.parametrize("name", list(SCENES))
 def test_hybrid_matches_oracle(env, name, cfg, sched):
@@ -151,12 +152,13 @@ def test_hybrid_settings_and_errors(env):
     P = api.device_params(scene, batch)
     import torch
     prev = dctx.get_launch()
-    dctx.set_launch(2, 128, 0)
     dctx.set_replay(1, method="pprb", sigma=0.01)
     try:
-        # P-PRB has no wavefront form
-        with pytest.raises(_lib.DpptError, match="UNSUPPORTED"):
-            api.render_adjoint(dctx, gs, batch, P, torch.zeros(batch.image_floats, device="cuda"))
+        # P-PRB has no wavefront form, and the sweep schedule replays in waves
+        for sched in (2, 3):
+            dctx.set_launch(sched, 128, 0)
+            with pytest.raises(_lib.DpptError, match="UNSUPPORTED"):
+                api.render_adjoint(dctx, gs, batch, P, torch.zeros(batch.image_floats, device="cuda"))
     finally:
         dctx.set_replay(1)
         dctx.set_launch(*prev)

@@ -72,7 +72,9 @@ MIN_IDENTICAL = {"deep": 0.85}
 SCENES = small_scenes()
 
 
-SCHEDULES = {"grid": (0, 128), "persistent": (1, 256), "wavefront": (2, 128)}
+# the sweep schedule renders the primal as the grid schedule; its adjoint traces each wave in one
+# forward-sweep megakernel and replays it with the wavefront's kernels
+SCHEDULES = {"grid": (0, 128), "persistent": (1, 256), "wavefront": (2, 128), "sweep": (3, 128)}
 
 
 @pytest.fixture(params=list(SCHEDULES))
@@ -217,7 +219,7 @@ def test_batched_angles_equal_separate_jobs(env):
     assert np.linalg.norm(tex_b - tex_s) <= 1e-4 * np.linalg.norm(tex_s)
 
 
-@pytest.mark.parametrize("schedule,block", [(0, 64), (0, 256), (1, 128), (1, 256), (2, 64), (2, 256)])
+@pytest.mark.parametrize("schedule,block", [(0, 64), (0, 256), (1, 128), (1, 256), (2, 64), (2, 256), (3, 256)])
 def test_schedules_agree(env, schedule, block):
     api, dctx, _ = env
     scene, job = SCENES["mixed"]
@@ -274,7 +276,8 @@ def test_shallow_paths(env, sched, depth):
 
 def test_wavefront_waves_match_megakernel(env):
     """A job of 7.84 M paths runs as two wavefront waves (at most 4,194,304 paths each, whole
-    pixels): image and gradients equal the grid megakernel's, which has no waves, up to
+    pixels), by the stage kernels and by the sweep schedule's forward-sweep megakernel: image
+    and gradients equal the grid megakernel's, which has no waves, up to
     summation order.  A gradient element sums millions of FP32 atomic additions in an order
     that differs between the schedules (about sqrt(N) * 6e-8 ~ 2e-4 relative at N = 8e6);
     a lost or repeated wave would be an O(1) error."""
@@ -288,7 +291,7 @@ def test_wavefront_waves_match_megakernel(env):
     prev = dctx.get_launch()
     out = []
     try:
-        for sched in (0, 2):
+        for sched in (0, 2, 3):
             dctx.set_launch(sched, 128, 0, sched, 128, 0)
             (img,), batch, P = gpu_image(api, dctx, gs, [job])
             dI = torch.as_tensor(np.random.default_rng(5).normal(size=img.size), dtype=torch.float32, device="cuda")
@@ -297,12 +300,13 @@ def test_wavefront_waves_match_megakernel(env):
             out.append((img, {k: v.double().cpu().numpy() for k, v in g.items()}))
     finally:
         dctx.set_launch(*prev)
-    (ri, rg), (wi, wg) = out
+    (ri, rg), *waved = out
     assert np.abs(ri).max() > 0
-    assert np.allclose(ri, wi, rtol=1e-5, atol=1e-6 * np.abs(ri).max())
-    for k in ("tex", "ior", "le", "theta"):
-        assert np.linalg.norm(rg[k]) > 0, k
-        assert grad_rel(wg[k], rg[k]) <= GRAD_TOL, (k, grad_rel(wg[k], rg[k]))
+    for wi, wg in waved:
+        assert np.allclose(ri, wi, rtol=1e-5, atol=1e-6 * np.abs(ri).max())
+        for k in ("tex", "ior", "le", "theta"):
+            assert np.linalg.norm(rg[k]) > 0, k
+            assert grad_rel(wg[k], rg[k]) <= GRAD_TOL, (k, grad_rel(wg[k], rg[k]))
 
 
 @pytest.mark.parametrize("w,h,spp", [(37, 23, 3), (19, 5, 64), (1, 1, 1), (7, 9, 33)])

@@ -42,7 +42,8 @@ def _signatures(torch, api, dctx, gs, jobs, P):
     return api.pack_jobs(jobs), img, sig.cpu().numpy().view(np.uint32)
 
 
-@pytest.mark.parametrize("schedule", [(0, 128), (1, 256), (2, 128)], ids=["grid", "persistent", "wavefront"])
+@pytest.mark.parametrize("schedule", [(0, 128), (1, 256), (2, 128), (3, 128)],
+                         ids=["grid", "persistent", "wavefront", "sweep"])
 def test_views_angles_batch_matches_oracle_per_job(env, schedule):
     torch, api, dctx, O = env
     scene, jobs = sg.cornell_views(3, 4, 4, 6, (24, 17, 31))
