@@ -228,9 +228,8 @@ k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
     const WaveSeg& sg = wt.seg[wave_piece_of_slot(wt, q)];
     const DJob& J = T.job[sg.job];
     const unsigned long long pid = (unsigned long long)(sg.pix0 * J.spp + (q - sg.q0));
-    const long long pix = (long long)(pid / J.spp);
     Walk w;
-    walk_begin(S, J, pid, pix, w);
+    walk_begin(S, J, pid, (long long)(pid / J.spp), w);
     PathVis<LocalCache<MAXD>, -1, NM> vis;
     vis.S = &S; vis.P = &P; vis.G = nullptr; vis.sgrad = nullptr;
     vis.C.cE = cE; vis.C.cW = cW;
@@ -238,22 +237,24 @@ k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
     for (;;) {
         HitRec h;
         const bool hit = trace_closest<false>(S, w.o, w.d, h, status, nullptr);
-        float* rec = W.rec(w.v - 1, q);
         if (!hit) {
+            float* rec = W.rec(w.v - 1, q);
             *reinterpret_cast<float4*>(rec + kWfHitComp) = make_float4(0.f, 0.f, 0.f, __int_as_float(kMissCode));
             rec[kWfVisComp] = __int_as_float(kBinMiss << 1);
             break;
         }
-        *reinterpret_cast<float4*>(rec + kWfHitComp) = make_float4(h.t, h.b1, h.b2, __int_as_float(code_of(S, true, h)));
+        *reinterpret_cast<float4*>(W.rec(w.v - 1, q) + kWfHitComp) =
+            make_float4(h.t, h.b1, h.b2, __int_as_float(code_of(S, true, h)));
         VCtx vc;
         NeePending ne;
         Shade sh;
         walk_shade<NM>(S, P, J, pid, w, h, vc, ne, sh);
         bool visible = false;
         if (ne.state == 1) visible = !trace_any<false>(S, ne.o2, ne.dir, ne.tmax, status, nullptr);
-        const bool cont = walk_finish(S, P, w, vc, ne, visible, sh, vis);
-        rec[kWfVisComp] = __int_as_float(replay_bin(S, vc.mat) << 1 | (visible ? 1 : 0));
-        if (!cont) break;
+        // stored before walk_finish, so that nothing of it stays live through the vertex's
+        // evaluation (the thread-local cache writes no record)
+        W.rec(w.v - 1, q)[kWfVisComp] = __int_as_float(replay_bin(S, vc.mat) << 1 | (visible ? 1 : 0));
+        if (!walk_finish(S, P, w, vc, ne, visible, sh, vis)) break;
     }
     SweepCache<MAXD> C;
     C.loc = vis.C;
@@ -279,6 +280,7 @@ k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
         if (J.sig) J.sig[pid] = fnv(w.sig, (unsigned)w.nv);
         return;
     }
+    const long long pix = (long long)(pid / J.spp);
     const float* ds = J.dS + pix * 12;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
