@@ -767,7 +767,9 @@ def main():
     ap.add_argument("--steps", type=int, default=50, help="timed steps (graph replays: p50 and p99 over them)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--schedule", type=int, default=None, help="0 grid, 1 persistent, 2 wavefront (default: autotuner)")
+    ap.add_argument("--schedule", type=int, default=None,
+                    help="0 grid, 1 persistent, 2 wavefront, 3 sweep (adjoint; its primal is the grid's) "
+                         "(default: autotuner)")
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--adj-schedule", type=int, default=None, help="adjoint schedule (default: same as --schedule)")
     ap.add_argument("--adj-block", type=int, default=None)

@@ -1141,13 +1141,19 @@ struct LocalCache {
 constexpr int kWfCacheComps = 36;
 constexpr int kWfVisComp = 31;
 constexpr int kWfHitComp = 32;
+// The sweep schedule's records keep only what the replay reads: 64 bytes per (vertex, path),
+// the suffix L_v (0-11) and the hit (12-15), so that its writes fill whole 32-byte sectors;
+// the visibility words are in a plane of their own.
+constexpr int kSweepRecFloats = 16;
+constexpr int kSweepHitComp = 12;
 struct GlobalCache {
     float* base;
     long long Q, q;
     int cap;
+    int stride;     // floats per record: kWfCacheComps, or kSweepRecFloats (suffix first in both)
     static constexpr bool kUnrollScatter = false;
     __device__ __forceinline__ float4* rec(int v) const {
-        return reinterpret_cast<float4*>(base + ((long long)v * Q + q) * kWfCacheComps);
+        return reinterpret_cast<float4*>(base + ((long long)v * Q + q) * stride);
     }
     // writes E_v and W_v (and a zero visibility, which the caller sets afterwards)
     __device__ __forceinline__ void put(int v, const float E[12], const Compact<float>& W) const {

@@ -245,7 +245,7 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
         get_walk(W.path + q, w);
         PathVis<GlobalCache, MT, NM> vis;
         vis.S = &S; vis.P = &P; vis.G = &G; vis.sgrad = sgrad;
-        vis.C.base = W.cache; vis.C.Q = W.Q; vis.C.q = q; vis.C.cap = W.cap;
+        vis.C.base = W.cache; vis.C.Q = W.Q; vis.C.q = q; vis.C.cap = W.cap; vis.C.stride = W.rec_floats;
         vis.n = (m.pni >> 8) & 0xff; vis.i = (m.pni >> 16) & 0xff; vis.phase = PHASE;
         vis.has_last = false;          // set, and consumed by the fold, within this launch
         vis.adjoint = MODE == 1;
@@ -264,8 +264,7 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
                     W.rec(slot, q)[kWfVisComp] = __int_as_float(replay_bin(S, vc.mat) << 1 | (visible != 0 ? 1 : 0));
             }
         } else {
-            const float* rec = W.rec(w.v - 1, q);
-            const float4 hv = *reinterpret_cast<const float4*>(rec + kWfHitComp);
+            const float4 hv = *reinterpret_cast<const float4*>(W.rec(w.v - 1, q) + W.hit_comp);
             if (__float_as_int(hv.w) != kMissCode) {
                 HitRec h;
                 decode_hit(S, hv, h);
@@ -276,7 +275,7 @@ k_wf_finish(const DScene S, const DParams P, const DGrads G, const __grid_consta
                     float4 r = W.path[q].arow[c];
                     vis.a[c][0] = r.x; vis.a[c][1] = r.y; vis.a[c][2] = r.z; vis.a[c][3] = r.w;
                 }
-                cont = walk_finish(S, P, w, vc, ne, (__float_as_int(rec[kWfVisComp]) & 1) != 0, sh, vis);
+                cont = walk_finish(S, P, w, vc, ne, (W.vis_word(w.v - 1, q) & 1) != 0, sh, vis);
             }
         }
         bool done = false;
@@ -409,16 +408,22 @@ static void launch_replay_bin(const ReplayArgs& a) {
     if (a.nmaps) k_wf_finish<1, 1, true, MT, MT><<<a.grid, 128, a.smem, a.st>>>(a.S, a.P, a.G, a.T, a.W, a.L);
     else k_wf_finish<1, 1, false, MT, MT><<<a.grid, 128, a.smem, a.st>>>(a.S, a.P, a.G, a.T, a.W, a.L);
 }
-// One replay iteration: a kernel per binned material type present, then the other bin.
+// One replay iteration: a kernel per binned material type present, then the other bin when
+// the scene has a type without a kernel of its own.
 static void replay_iteration(const ReplayArgs& ra, unsigned types, StageLog* log) {
-    const int tok = log->begin(kStageWfReplay, ra.st, 1 + __builtin_popcount(types & kBinnedTypes));
+    const bool other = (types & ~kBinnedTypes) != 0;
+    const int tok = log->begin(kStageWfReplay, ra.st, (other ? 1 : 0) + __builtin_popcount(types & kBinnedTypes));
     if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) launch_replay_bin<DPPT_MAT_CONDUCTOR_GGX>(ra);
     if (types & (1u << DPPT_MAT_PLASTIC_GGX)) launch_replay_bin<DPPT_MAT_PLASTIC_GGX>(ra);
     if (types & (1u << DPPT_MAT_DIFFUSE)) launch_replay_bin<DPPT_MAT_DIFFUSE>(ra);
+    if (types & (1u << DPPT_MAT_SMOOTH_DIELECTRIC)) launch_replay_bin<DPPT_MAT_SMOOTH_DIELECTRIC>(ra);
     if (types & (1u << DPPT_MAT_POLARIZER_SHEET)) launch_replay_bin<DPPT_MAT_POLARIZER_SHEET>(ra);
     if (types & (1u << DPPT_MAT_RETARDER_SHEET)) launch_replay_bin<DPPT_MAT_RETARDER_SHEET>(ra);
-    if (ra.nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<ra.grid, 128, ra.smem, ra.st>>>(ra.S, ra.P, ra.G, ra.T, ra.W, ra.L);
-    else k_wf_finish<1, 1, false, -1, kBinOther><<<ra.grid, 128, ra.smem, ra.st>>>(ra.S, ra.P, ra.G, ra.T, ra.W, ra.L);
+    if (types & (1u << DPPT_MAT_EMITTER)) launch_replay_bin<DPPT_MAT_EMITTER>(ra);
+    if (other) {
+        if (ra.nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<ra.grid, 128, ra.smem, ra.st>>>(ra.S, ra.P, ra.G, ra.T, ra.W, ra.L);
+        else k_wf_finish<1, 1, false, -1, kBinOther><<<ra.grid, 128, ra.smem, ra.st>>>(ra.S, ra.P, ra.G, ra.T, ra.W, ra.L);
+    }
     log->end(tok, ra.st);
 }
 
@@ -487,7 +492,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
     W.cache = reinterpret_cast<float*>(p);
     W.Q = Q;
     W.cap = cap;
-    W.rec_floats = kWfCacheComps; W.hit_comp = kWfHitComp; W.vis_comp = kWfVisComp;
+    W.rec_floats = kWfCacheComps; W.hit_comp = kWfHitComp; W.vis_comp = kWfVisComp; W.vis_plane = nullptr;
     const bool hyb = hy.k > 1;
     HybWs H{};
     if (hyb) {
@@ -505,6 +510,12 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
         H.flags = reinterpret_cast<unsigned*>(p);
         H.gamma = hy.gamma;
         H.eps = hy.eps;
+    }
+    const bool swp = mode == 1 && !hyb && sweep > 0;
+    if (swp) {
+        // the sweep's 64-byte records, then its plane of visibility words, in the cache's space
+        W.rec_floats = kSweepRecFloats; W.hit_comp = kSweepHitComp; W.vis_comp = -1;
+        W.vis_plane = reinterpret_cast<int*>(W.cache + (size_t)kSweepRecFloats * cap * Q);
     }
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
@@ -524,7 +535,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
         cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * 32, st);
         if (e != cudaSuccess) return e;
         int tok = 0;
-        if (mode == 1 && !hyb && sweep > 0) {
+        if (swp) {
             // the forward sweep in one megakernel; every path then starts its replay at the first
             // replay iteration, so depth iterations finish the wave
             tok = log->begin(kStageWfSweep, st);

@@ -13,6 +13,8 @@ struct __align__(128) WfPath { float4 a, b, c, d; float4 arow[3]; WfMeta meta; }
 struct __align__(128) WfVtx { float4 x_tu, ng_tv, wi_pdf, wl_ps, misc, mat; int4 ids; float4 pad; };
 struct __align__(16) WfRay { float4 o_tmax, dir; };
 static_assert(sizeof(WfPath) == 128 && sizeof(WfVtx) == 128, "one 128-byte record per path");
+static_assert(kSweepRecFloats == 16 && kSweepHitComp == 12 && kSweepRecFloats + 1 <= kWfCacheComps,
+              "the sweep's records (suffix, hit) and visibility plane fit in the cache's space");
 
 enum : unsigned {
     kFEmit = 1u, kFOutside = 2u, kFOk = 4u, kFTerminal = 8u, kFDelta = 16u, kFHit = 32u,
@@ -91,11 +93,16 @@ struct WfState {
     int cap;
     // where the traversal stores each vertex's hit for the replay: the cache record of
     // (vertex slot, path) is rec_floats floats, its hit at hit_comp and its bin word at
-    // vis_comp (36, 32, 31: the cache of the cached replay; 4, 0, -1: the hits of the hybrid
+    // vis_comp, or in vis_plane[vertex slot][path] (36, 32, 31: the cache of the cached
+    // replay; 16, 12, plane: the sweep schedule's records; 4, 0, -1: the hits of the hybrid
     // replay, which keeps no bin word)
     int rec_floats, hit_comp, vis_comp;
-    __device__ __forceinline__ float* rec(int v, int q) const { return cache + ((long long)v * Q + q) * kWfCacheComps; }
-    __device__ __forceinline__ float* hit_rec(int v, int q) const { return cache + ((long long)v * Q + q) * rec_floats; }
+    int* vis_plane;
+    __device__ __forceinline__ float* rec(int v, int q) const { return cache + ((long long)v * Q + q) * rec_floats; }
+    __device__ __forceinline__ float* hit_rec(int v, int q) const { return rec(v, q); }
+    __device__ __forceinline__ int vis_word(int v, int q) const {
+        return vis_plane ? vis_plane[(long long)v * Q + q] : __float_as_int(rec(v, q)[vis_comp]);
+    }
 };
 // the code of a traversal's result: the BVH slot of a triangle, -(sphere + 1), or kMissCode
 __device__ __forceinline__ int code_of(const DScene& S, bool hit, const HitRec& h) {
@@ -163,16 +170,18 @@ __device__ __forceinline__ void wave_start_path(const DScene& S, const JobTable&
     W.path[q].meta = WfMeta{(unsigned)pid, (unsigned)(pid >> 32), sg.job, 0};
 }
 
-// Replay bins: the material types with a replay kernel of their own (diffuse, rough
-// conductor, rough dielectric, polarizer and retarder sheets), and one bin for everything
-// else (smooth dielectrics, emitter hits, paths that left the scene).
+// Replay bins: every material type has a replay kernel of its own (compiled for that type
+// only, so that it holds no other type's code and registers); bin kBinOther, replayed by the
+// kernel for any type, is kept for types without one.
 constexpr int kBinOther = 7;
 // the bin word of a cache slot whose ray left the scene: the replay of a path ends at the
 // vertex before it, with no launch for the miss
 constexpr int kBinMiss = 15;
-constexpr unsigned kBinnedTypes = (1u << DPPT_MAT_DIFFUSE) | (1u << DPPT_MAT_CONDUCTOR_GGX) |
-                                  (1u << DPPT_MAT_PLASTIC_GGX) | (1u << DPPT_MAT_POLARIZER_SHEET) |
-                                  (1u << DPPT_MAT_RETARDER_SHEET);
+constexpr unsigned kBinnedTypes = (1u << DPPT_MAT_DIFFUSE) | (1u << DPPT_MAT_SMOOTH_DIELECTRIC) |
+                                  (1u << DPPT_MAT_CONDUCTOR_GGX) | (1u << DPPT_MAT_PLASTIC_GGX) |
+                                  (1u << DPPT_MAT_POLARIZER_SHEET) | (1u << DPPT_MAT_RETARDER_SHEET) |
+                                  (1u << DPPT_MAT_EMITTER);
+static_assert(DPPT_MAT_EMITTER < kBinOther, "a binned type's bin is its type");
 
 // Appends path q to the next iteration's replay bin b.  Appends are warp-aggregated: the
 // lanes of a warp going to the same bin take consecutive slots with one atomic.
@@ -193,12 +202,11 @@ __device__ __forceinline__ int replay_bin(const DScene& S, int mat) {
     const int t = __ldg(&S.mats[mat].type);
     return (kBinnedTypes >> t) & 1u ? t : kBinOther;
 }
-__device__ __forceinline__ int replay_bin_of(const WfState& W, int q, int v) {
-    return __float_as_int(W.rec(v, q)[kWfVisComp]) >> 1;
-}
+__device__ __forceinline__ int replay_bin_of(const WfState& W, int q, int v) { return W.vis_word(v, q) >> 1; }
 
 // The cache the forward sweep folds: E_v and W_v from the thread-local arrays, the suffixes
-// into the wave's per-vertex records (components 0-11), where the replay reads them.
+// into the wave's per-vertex records (components 0-11 of kSweepRecFloats), where the replay
+// reads them.
 template <int MAXD>
 struct SweepCache {
     LocalCache<MAXD> loc;
@@ -210,10 +218,12 @@ struct SweepCache {
 
 // The adjoint's forward sweep in one kernel (schedule DPPT_SCHED_SWEEP), one thread per wave
 // slot: the thread runs its path to the end as the megakernel does (closest hit, shading,
-// light sample and shadow ray, E_v and the compact W_v in thread-local arrays) and keeps in the
-// slot's per-vertex records only what the replay reads back: the closest hit (kWfHitComp),
-// the light sample's visibility with the vertex's replay bin (kWfVisComp), and after the
-// backward fold the suffixes L_v of v >= 1.  It then stores the path's raw Stokes value and
+// light sample and shadow ray, E_v and the compact W_v in thread-local arrays) and keeps per
+// vertex only what the replay reads back: the closest hit (kSweepHitComp of the 64-byte
+// record), the light sample's visibility with the vertex's replay bin (W.vis_plane), and after
+// the backward fold the suffix L_v (components 0-11; L_0 too, although the replay never reads
+// it, and zeros beside a miss's hit, so that every written 32-byte sector is written whole:
+// a partly written sector costs the memory a read of it).  It then stores the path's raw Stokes value and
 // starts the replay (the adjoint row of its pixel, the walk begun again, the path in the bin
 // of its first vertex); the replay's iterations run as in the wavefront schedule.
 template <int MAXD, bool NM>
@@ -238,12 +248,13 @@ k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
         HitRec h;
         const bool hit = trace_closest<false>(S, w.o, w.d, h, status, nullptr);
         if (!hit) {
-            float* rec = W.rec(w.v - 1, q);
-            *reinterpret_cast<float4*>(rec + kWfHitComp) = make_float4(0.f, 0.f, 0.f, __int_as_float(kMissCode));
-            rec[kWfVisComp] = __int_as_float(kBinMiss << 1);
+            float4* rec = reinterpret_cast<float4*>(W.rec(w.v - 1, q));
+            rec[kSweepHitComp / 4 - 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            rec[kSweepHitComp / 4] = make_float4(0.f, 0.f, 0.f, __int_as_float(kMissCode));
+            W.vis_plane[(long long)(w.v - 1) * W.Q + q] = kBinMiss << 1;
             break;
         }
-        *reinterpret_cast<float4*>(W.rec(w.v - 1, q) + kWfHitComp) =
+        reinterpret_cast<float4*>(W.rec(w.v - 1, q))[kSweepHitComp / 4] =
             make_float4(h.t, h.b1, h.b2, __int_as_float(code_of(S, true, h)));
         VCtx vc;
         NeePending ne;
@@ -253,12 +264,12 @@ k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
         if (ne.state == 1) visible = !trace_any<false>(S, ne.o2, ne.dir, ne.tmax, status, nullptr);
         // stored before walk_finish, so that nothing of it stays live through the vertex's
         // evaluation (the thread-local cache writes no record)
-        W.rec(w.v - 1, q)[kWfVisComp] = __int_as_float(replay_bin(S, vc.mat) << 1 | (visible ? 1 : 0));
+        W.vis_plane[(long long)(w.v - 1) * W.Q + q] = replay_bin(S, vc.mat) << 1 | (visible ? 1 : 0);
         if (!walk_finish(S, P, w, vc, ne, visible, sh, vis)) break;
     }
     SweepCache<MAXD> C;
     C.loc = vis.C;
-    C.glob.base = W.cache; C.glob.Q = W.Q; C.glob.q = q; C.glob.cap = W.cap;
+    C.glob.base = W.cache; C.glob.Q = W.Q; C.glob.q = q; C.glob.cap = W.cap; C.glob.stride = kSweepRecFloats;
     float L0[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) L0[k] = vis.has_last ? vis.lastE[k] : 0.0f;
@@ -268,6 +279,7 @@ k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
         --top;
     }
     fold_cached(C, top, true, L0);
+    if (vis.n > 0) C.put_e(0, L0);
     const Rot<float> Rc = camera_rot(S.cams[J.cam], w.d1);
     const float inv = 1.0f / (float)J.spp;
 #pragma unroll

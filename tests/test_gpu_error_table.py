@@ -45,7 +45,7 @@ pytestmark = pytest.mark.gpu
 TABLE = {}
 COND_MOVE = 1e-5
 WAVEFRONT = (2, 128, 0, 2, 64, 0, 1)          # primal / adjoint schedule, block, blocks per SM; lane scatter
-VIEWS_LAUNCH = (0, 256, 0, 2, 64, 0, 0)
+VIEWS_LAUNCH = (0, 256, 0, 3, 256, 0, 0)      # grid primal, sweep adjoint
 
 
 @pytest.fixture
