@@ -74,17 +74,14 @@ B_CACHE_VERTEX_PRIMAL, B_CACHE_VERTEX_ADJOINT = 420, 424
 B_CACHE_PATH_PRIMAL, B_CACHE_PATH_ADJOINT = 48, 216
 
 # DRAM traffic per launch (bytes; dram__bytes_read.sum + dram__bytes_write.sum, cold caches)
-# keyed by (workload, stage): a stage's bytes per iteration over its kernel launches (the
-# replay of the views workload launches two per iteration, the diffuse and the other bin).
-# Captured on the views workload with every image
-# side halved, whose per-launch work equals the full size's (one wave of 3.78M against 4.19M
-# paths: 2.09M vertices per cache launch, 1.12M per replay iteration at both sizes), and
-# scaled by the vertices processed: 93 B per primal vertex, 865 B per cache-pass vertex, 548 B
-# per replayed vertex.  Absent for a kernel changed since its capture.
+# keyed by (workload, stage), for the stages the benchmark's launch shapes run: captured on the
+# views workload with every image side halved (3,779,744 paths per pass, one wave) and scaled
+# by the paths a full-size launch processes: the primal megakernel 410 B per path (one launch
+# of 15,125,952 paths per step), the forward sweep 2,010 B per path (four waves, 3,781,488
+# paths per launch on average).  Absent for a kernel changed since its capture.
 DRAM_BYTES_PER_LAUNCH = {
-    ("cornell_views8x64angles_16spp_depth8", "primal"): 6.256e9,
-    ("cornell_views8x64angles_16spp_depth8", "wf_cache"): 1.813e9,
-    ("cornell_views8x64angles_16spp_depth8", "wf_replay"): 0.613e9 / 2,
+    ("cornell_views8x64angles_16spp_depth8", "primal"): 6.203e9,
+    ("cornell_views8x64angles_16spp_depth8", "wf_sweep"): 7.600e9,
 }
 
 # floats per vertex of the wavefront cache: E_v 12, compact W_v 19, visibility 1, the hit 4
