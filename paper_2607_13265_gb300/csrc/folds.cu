@@ -1,6 +1,8 @@
 // Camera-filter folds for batches of polarizer angles: the filter does not
 // change the paths, so the raw sensor-frame image is rendered once and each
 // angle's image, the adjoint input and the angle gradients are per-pixel maps.
+#include <algorithm>
+
 #include "device_math.cuh"
 #include "internal.h"
 
@@ -151,115 +153,132 @@ __device__ __forceinline__ void residual4(const float* C, const float* v, const 
     for (int i = 0; i < 4; ++i) d[i] = C[4 * i] * v[0] + C[4 * i + 1] * v[1] + C[4 * i + 2] * v[2] + C[4 * i + 3] * v[3] - t[i];
 }
 
-__global__ void k_l2_loss(const float* __restrict__ raw, const float* __restrict__ target, int npix, int filter,
-                          const float* __restrict__ theta, int nang, double scale, double* loss) {
+// Every job of a call in one launch: each block belongs to one job (the jobs' blocks back to
+// back, block0[j] the first of job j), so that the small images of a batch, which cannot fill
+// the GPU alone, run side by side instead of one launch after another.
+struct L2FoldBatch {
+    L2FoldJob job[kMaxFoldJobs];
+    int block0[kMaxFoldJobs + 1];
+    int njobs;
+};
+__device__ __forceinline__ int fold_job_of_block(const L2FoldBatch& b) {
+    int lo = 0, hi = b.njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.block0[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// scale * sum_a sum_pix |C_a raw - T_a|^2 of every job, added into *loss
+__global__ void k_l2_loss(const __grid_constant__ L2FoldBatch b, double scale, double* loss) {
     extern __shared__ float sC[];
     __shared__ double swarp[32];
-    for (int a = threadIdx.x; a < nang; a += blockDim.x) {
+    const int jb = fold_job_of_block(b);
+    const L2FoldJob& J = b.job[jb];
+    for (int a = threadIdx.x; a < J.nang; a += blockDim.x) {
         float C[16], dC[16];
-        filter_or_identity(filter, theta, a, C, dC);
+        filter_or_identity(J.filter, J.theta, a, C, dC);
         for (int k = 0; k < 16; ++k) sC[16 * a + k] = C[k];
     }
     __syncthreads();
+    const long long pix = (long long)(blockIdx.x - b.block0[jb]) * blockDim.x + threadIdx.x;
     double acc = 0.0;
-    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix; pix += (long long)gridDim.x * blockDim.x) {
+    if (pix < J.npix) {
         float r[12], t[12];
-        load12(raw + pix * 12, r);
+        load12(J.raw + pix * 12, r);
         float part = 0.0f;
-        for (int a = 0; a < nang; ++a) {
-            load12(target + ((long long)a * npix + pix) * 12, t);
+        for (int a = 0; a < J.nang; ++a) {
+            load12(J.target + ((long long)a * J.npix + pix) * 12, t);
             for (int c = 0; c < 3; ++c) {
                 float d[4];
                 residual4(sC + 16 * a, r + 4 * c, t + 4 * c, d);
                 part += d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + d[3] * d[3];
             }
         }
-        acc += (double)part;
+        acc = (double)part;
     }
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if ((threadIdx.x & 31) == 0) swarp[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double b = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += swarp[w];
-        if (b != 0.0) atomicAdd(loss, b * scale);
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += swarp[w];
+        if (s != 0.0) atomicAdd(loss, s * scale);
     }
 }
 
-// dS = 2 scale sum_a C_a^T (C_a raw - T_a)
-__global__ void k_l2_adjoint_input(const float* __restrict__ raw, const float* __restrict__ target, float* __restrict__ dS,
-                                   int npix, int filter, const float* __restrict__ theta, int nang, float scale2) {
+// dS = 2 scale sum_a C_a^T (C_a raw - T_a) of every job
+__global__ void k_l2_adjoint_input(const __grid_constant__ L2FoldBatch b, float scale2) {
     extern __shared__ float sC[];
-    for (int a = threadIdx.x; a < nang; a += blockDim.x) {
+    const int jb = fold_job_of_block(b);
+    const L2FoldJob& J = b.job[jb];
+    for (int a = threadIdx.x; a < J.nang; a += blockDim.x) {
         float C[16], dC[16];
-        filter_or_identity(filter, theta, a, C, dC);
+        filter_or_identity(J.filter, J.theta, a, C, dC);
         for (int k = 0; k < 16; ++k) sC[16 * a + k] = C[k];
     }
     __syncthreads();
-    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix; pix += (long long)gridDim.x * blockDim.x) {
-        float r[12], t[12], acc[12];
-        load12(raw + pix * 12, r);
-        for (int k = 0; k < 12; ++k) acc[k] = 0.0f;
-        for (int a = 0; a < nang; ++a) {
-            const float* C = sC + 16 * a;
-            load12(target + ((long long)a * npix + pix) * 12, t);
-            for (int c = 0; c < 3; ++c) {
-                float d[4];
-                residual4(C, r + 4 * c, t + 4 * c, d);
-                for (int j = 0; j < 4; ++j)
-                    acc[4 * c + j] += C[j] * d[0] + C[4 + j] * d[1] + C[8 + j] * d[2] + C[12 + j] * d[3];
-            }
+    const long long pix = (long long)(blockIdx.x - b.block0[jb]) * blockDim.x + threadIdx.x;
+    if (pix >= J.npix) return;
+    float r[12], t[12], acc[12];
+    load12(J.raw + pix * 12, r);
+    for (int k = 0; k < 12; ++k) acc[k] = 0.0f;
+    for (int a = 0; a < J.nang; ++a) {
+        const float* C = sC + 16 * a;
+        load12(J.target + ((long long)a * J.npix + pix) * 12, t);
+        for (int c = 0; c < 3; ++c) {
+            float d[4];
+            residual4(C, r + 4 * c, t + 4 * c, d);
+            for (int j = 0; j < 4; ++j)
+                acc[4 * c + j] += C[j] * d[0] + C[4 + j] * d[1] + C[8 + j] * d[2] + C[12 + j] * d[3];
         }
-        float4* o = reinterpret_cast<float4*>(dS + pix * 12);
-        for (int q = 0; q < 3; ++q)
-            o[q] = make_float4(scale2 * acc[4 * q], scale2 * acc[4 * q + 1], scale2 * acc[4 * q + 2], scale2 * acc[4 * q + 3]);
     }
+    float4* o = reinterpret_cast<float4*>(J.dS + pix * 12);
+    for (int q = 0; q < 3; ++q)
+        o[q] = make_float4(scale2 * acc[4 * q], scale2 * acc[4 * q + 1], scale2 * acc[4 * q + 2], scale2 * acc[4 * q + 3]);
 }
 
-// dtheta_a += 2 scale sum_pix (C_a raw - T_a)^T dC_a S_adj
-__global__ void k_l2_theta_grad(const float* __restrict__ raw, const float* __restrict__ target,
-                                const float* __restrict__ S_adj, int npix, int filter, const float* __restrict__ theta,
-                                int nang, float scale2, float* __restrict__ dtheta) {
+// dtheta_a += 2 scale sum_pix (C_a raw - T_a)^T dC_a S_adj of every (filtered) job
+__global__ void k_l2_theta_grad(const __grid_constant__ L2FoldBatch b, float scale2) {
     extern __shared__ float sm[];
+    const int jb = fold_job_of_block(b);
+    const L2FoldJob& J = b.job[jb];
+    const int nang = J.nang;
     float* sC = sm;                 // [nang][16]
     float* sdC = sm + 16 * nang;    // [nang][16]
     float* sacc = sm + 32 * nang;   // [nang]
     for (int a = threadIdx.x; a < nang; a += blockDim.x) {
         float C[16], dC[16];
-        filter_matrix(filter, __ldg(theta + a), C, dC);
+        filter_matrix(J.filter, __ldg(J.theta + a), C, dC);
         for (int k = 0; k < 16; ++k) { sC[16 * a + k] = C[k]; sdC[16 * a + k] = dC[k]; }
         sacc[a] = 0.0f;
     }
     __syncthreads();
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long rounds = (npix + stride - 1) / stride;
-    for (long long it = 0; it < rounds; ++it) {
-        const long long pix = first + it * stride;
-        const bool act = pix < npix;
-        float r[12], s[12], t[12];
-        for (int k = 0; k < 12; ++k) { r[k] = 0.0f; s[k] = 0.0f; }
-        if (act) { load12(raw + pix * 12, r); load12(S_adj + pix * 12, s); }
-        for (int a = 0; a < nang; ++a) {
-            float v = 0.0f;
-            if (act) {
-                load12(target + ((long long)a * npix + pix) * 12, t);
-                const float* dC = sdC + 16 * a;
-                for (int c = 0; c < 3; ++c) {
-                    float d[4];
-                    residual4(sC + 16 * a, r + 4 * c, t + 4 * c, d);
-                    for (int i = 0; i < 4; ++i)
-                        v += d[i] * (dC[4 * i] * s[4 * c] + dC[4 * i + 1] * s[4 * c + 1] + dC[4 * i + 2] * s[4 * c + 2] +
-                                     dC[4 * i + 3] * s[4 * c + 3]);
-                }
+    const long long pix = (long long)(blockIdx.x - b.block0[jb]) * blockDim.x + threadIdx.x;
+    const bool act = pix < J.npix;     // every lane takes part in the warp sums below
+    float r[12], s[12], t[12];
+    for (int k = 0; k < 12; ++k) { r[k] = 0.0f; s[k] = 0.0f; }
+    if (act) { load12(J.raw + pix * 12, r); load12(J.S_adj + pix * 12, s); }
+    for (int a = 0; a < nang; ++a) {
+        float v = 0.0f;
+        if (act) {
+            load12(J.target + ((long long)a * J.npix + pix) * 12, t);
+            const float* dC = sdC + 16 * a;
+            for (int c = 0; c < 3; ++c) {
+                float d[4];
+                residual4(sC + 16 * a, r + 4 * c, t + 4 * c, d);
+                for (int i = 0; i < 4; ++i)
+                    v += d[i] * (dC[4 * i] * s[4 * c] + dC[4 * i + 1] * s[4 * c + 1] + dC[4 * i + 2] * s[4 * c + 2] +
+                                 dC[4 * i + 3] * s[4 * c + 3]);
             }
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(sacc + a, v * scale2);
         }
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(sacc + a, v * scale2);
     }
     __syncthreads();
     for (int a = threadIdx.x; a < nang; a += blockDim.x)
-        if (sacc[a] != 0.0f) atomicAdd(dtheta + a, sacc[a]);
+        if (sacc[a] != 0.0f) atomicAdd(J.dtheta + a, sacc[a]);
 }
 
 static int fold_grid(int npix, int block) {
@@ -282,28 +301,55 @@ cudaError_t launch_theta_grad(const float* dimage, const float* S_adj, int npix,
     return cudaGetLastError();
 }
 
-cudaError_t launch_l2_loss(const float* raw, const float* target, int npix, int filter, const float* theta, int nang,
-                           double scale, double* loss, cudaStream_t st) {
-    k_l2_loss<<<fold_grid(npix, 256), 256, sizeof(float) * 16 * nang, st>>>(raw, target, npix, filter, theta, nang,
-                                                                              scale, loss);
-    return cudaGetLastError();
-}
-cudaError_t launch_l2_adjoint_input(const float* raw, const float* target, float* dS, int npix, int filter,
-                                    const float* theta, int nang, float scale2, cudaStream_t st) {
-    k_l2_adjoint_input<<<fold_grid(npix, 256), 256, sizeof(float) * 16 * nang, st>>>(raw, target, dS, npix, filter,
-                                                                                       theta, nang, scale2);
-    return cudaGetLastError();
-}
-cudaError_t launch_l2_theta_grad(const float* raw, const float* target, const float* S_adj, int npix, int filter,
-                                 const float* theta, int nang, float scale2, float* dtheta, cudaStream_t st) {
-    const size_t smem = sizeof(float) * 33 * nang;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_l2_theta_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// The batched L2 folds: the jobs in chunks of kMaxFoldJobs, one launch per chunk, 256 threads
+// per block, one pixel per thread.  smem_per_angle: floats of shared memory per angle.
+template <class Launch>
+static cudaError_t launch_fold_batches(const L2FoldJob* jobs, int njobs, int smem_per_angle, const void* kernel,
+                                       Launch launch) {
+    constexpr int kBlock = 256;
+    for (int j0 = 0; j0 < njobs; j0 += kMaxFoldJobs) {
+        L2FoldBatch b{};
+        b.njobs = std::min(kMaxFoldJobs, njobs - j0);
+        long long blocks = 0;
+        int nang = 1;
+        for (int k = 0; k < b.njobs; ++k) {
+            b.job[k] = jobs[j0 + k];
+            b.block0[k] = (int)blocks;
+            blocks += (b.job[k].npix + kBlock - 1) / kBlock;
+            nang = std::max(nang, b.job[k].nang);
+        }
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+        b.block0[b.njobs] = (int)blocks;
+        if (blocks == 0) continue;
+        const size_t smem = sizeof(float) * (size_t)smem_per_angle * nang;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        launch(b, (int)blocks, kBlock, smem);
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    k_l2_theta_grad<<<fold_grid(npix, 256), 256, smem, st>>>(raw, target, S_adj, npix, filter, theta, nang, scale2,
-                                                              dtheta);
-    return cudaGetLastError();
+    return cudaSuccess;
+}
+int l2_fold_launches(int njobs) { return (njobs + kMaxFoldJobs - 1) / kMaxFoldJobs; }
+cudaError_t launch_l2_loss(const L2FoldJob* jobs, int njobs, double scale, double* loss, cudaStream_t st) {
+    return launch_fold_batches(jobs, njobs, 16, reinterpret_cast<const void*>(&k_l2_loss),
+                               [&](const L2FoldBatch& b, int g, int blk, size_t sm) {
+                                   k_l2_loss<<<g, blk, sm, st>>>(b, scale, loss);
+                               });
+}
+cudaError_t launch_l2_adjoint_input(const L2FoldJob* jobs, int njobs, float scale2, cudaStream_t st) {
+    return launch_fold_batches(jobs, njobs, 16, reinterpret_cast<const void*>(&k_l2_adjoint_input),
+                               [&](const L2FoldBatch& b, int g, int blk, size_t sm) {
+                                   k_l2_adjoint_input<<<g, blk, sm, st>>>(b, scale2);
+                               });
+}
+cudaError_t launch_l2_theta_grad(const L2FoldJob* jobs, int njobs, float scale2, cudaStream_t st) {
+    return launch_fold_batches(jobs, njobs, 33, reinterpret_cast<const void*>(&k_l2_theta_grad),
+                               [&](const L2FoldBatch& b, int g, int blk, size_t sm) {
+                                   k_l2_theta_grad<<<g, blk, sm, st>>>(b, scale2);
+                               });
 }
 
 }  // namespace dppt

@@ -888,40 +888,45 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
     build_tables(jobs, njobs, plan, shape.block, first, tables, maxd);
     DParams P = dparams(params);
     DGrads G{grads->tex, grads->ior, grads->le, grads->sheet};
+    // the adjoint inputs: the fused L2 loss's of every job in one batched launch, or the
+    // camera filter's fold of each filtered job's image adjoint
+    auto ws_floats = [&](size_t off) { return reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + off); };
+    if (l2) {
+        std::vector<L2FoldJob> fj;
+        for (int i = 0; i < njobs; ++i)
+            fj.push_back(L2FoldJob{l2->raw + l2->raw_offsets[i], l2->target + jobs[i].out_offset, ws_floats(plan[i].ws_a),
+                                   nullptr, plan[i].filtered ? params->theta + jobs[i].theta_offset : nullptr, nullptr,
+                                   plan[i].npix, plan[i].filtered ? jobs[i].filter : DPPT_FILTER_NONE,
+                                   plan[i].filtered ? plan[i].nang : 1});
+        int tok = ctx->log.begin(kStageFilter, cs, l2_fold_launches(njobs));
+        cudaError_t e = launch_l2_adjoint_input(fj.data(), njobs, 2.0f * l2->scale, cs);
+        ctx->log.end(tok, cs);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "L2 adjoint input launch");
+    } else {
+        for (int i = 0; i < njobs; ++i) {
+            if (!plan[i].filtered) continue;
+            int tok = ctx->log.begin(kStageFilter, cs);
+            cudaError_t e = launch_filter_adjoint_input(d_image + jobs[i].out_offset, ws_floats(plan[i].ws_a),
+                                                        (int)plan[i].npix, jobs[i].filter,
+                                                        params->theta + jobs[i].theta_offset, plan[i].nang, cs);
+            ctx->log.end(tok, cs);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "filter adjoint launch");
+        }
+    }
     for (size_t g = 0; g < tables.size(); ++g) {
         JobTable& T = tables[g];
         for (int k = 0; k < T.njobs; ++k) {
             const int i = first[g] + k;
             DJob& J = T.job[k];
             if (plan[i].filtered) {
-                float* dS = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_a);
-                float* Sa = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_b);
-                int tok = ctx->log.begin(kStageFilter, cs);
-                cudaError_t e =
-                    l2 ? launch_l2_adjoint_input(l2->raw + l2->raw_offsets[i], l2->target + jobs[i].out_offset, dS,
-                                                 (int)plan[i].npix, jobs[i].filter,
-                                                 params->theta + jobs[i].theta_offset, plan[i].nang,
-                                                 2.0f * l2->scale, cs)
-                       : launch_filter_adjoint_input(d_image + jobs[i].out_offset, dS, (int)plan[i].npix,
-                                                     jobs[i].filter, params->theta + jobs[i].theta_offset,
-                                                     plan[i].nang, cs);
-                ctx->log.end(tok, cs);
-                if (e != cudaSuccess) return cuda_fail(ctx, e, "filter adjoint launch");
-                J.dS = dS;
-                J.raw = grads->theta ? Sa : nullptr;
+                J.dS = ws_floats(plan[i].ws_a);
+                J.raw = grads->theta ? ws_floats(plan[i].ws_b) : nullptr;
                 if (J.raw && J.red_mode != 0 && !wave) {
-                    e = cudaMemsetAsync(J.raw, 0, (size_t)plan[i].npix * 12 * sizeof(float), cs);
+                    cudaError_t e = cudaMemsetAsync(J.raw, 0, (size_t)plan[i].npix * 12 * sizeof(float), cs);
                     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
                 }
             } else if (l2) {
-                float* dS = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + plan[i].ws_a);
-                int tok = ctx->log.begin(kStageFilter, cs);
-                cudaError_t e = launch_l2_adjoint_input(l2->raw + l2->raw_offsets[i], l2->target + jobs[i].out_offset,
-                                                        dS, (int)plan[i].npix, DPPT_FILTER_NONE, nullptr, 1,
-                                                        2.0f * l2->scale, cs);
-                ctx->log.end(tok, cs);
-                if (e != cudaSuccess) return cuda_fail(ctx, e, "L2 adjoint input launch");
-                J.dS = dS;
+                J.dS = ws_floats(plan[i].ws_a);
                 J.raw = nullptr;
             } else {
                 J.dS = d_image + jobs[i].out_offset;
@@ -995,18 +1000,27 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
         ctx->log.end(tok, cs);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
     }
-    if (grads->theta) {
+    if (grads->theta && l2) {
+        // the angle gradients of every filtered job in one batched launch
+        std::vector<L2FoldJob> fj;
+        for (int i = 0; i < njobs; ++i)
+            if (plan[i].filtered)
+                fj.push_back(L2FoldJob{l2->raw + l2->raw_offsets[i], l2->target + jobs[i].out_offset, nullptr,
+                                       ws_floats(plan[i].ws_b), params->theta + jobs[i].theta_offset,
+                                       grads->theta + jobs[i].theta_offset, plan[i].npix, jobs[i].filter, plan[i].nang});
+        if (!fj.empty()) {
+            int tok = ctx->log.begin(kStageFilter, cs, l2_fold_launches((int)fj.size()));
+            cudaError_t e = launch_l2_theta_grad(fj.data(), (int)fj.size(), 2.0f * l2->scale, cs);
+            ctx->log.end(tok, cs);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "theta-gradient launch");
+        }
+    } else if (grads->theta) {
         for (int i = 0; i < njobs; ++i) {
             if (!plan[i].filtered) continue;
-            const float* Sa = reinterpret_cast<const float*>(static_cast<char*>(ctx->ws) + plan[i].ws_b);
             int tok = ctx->log.begin(kStageFilter, cs);
-            cudaError_t e =
-                l2 ? launch_l2_theta_grad(l2->raw + l2->raw_offsets[i], l2->target + jobs[i].out_offset, Sa,
-                                          (int)plan[i].npix, jobs[i].filter, params->theta + jobs[i].theta_offset,
-                                          plan[i].nang, 2.0f * l2->scale, grads->theta + jobs[i].theta_offset, cs)
-                   : launch_theta_grad(d_image + jobs[i].out_offset, Sa, (int)plan[i].npix, jobs[i].filter,
-                                       params->theta + jobs[i].theta_offset, plan[i].nang,
-                                       grads->theta + jobs[i].theta_offset, cs);
+            cudaError_t e = launch_theta_grad(d_image + jobs[i].out_offset, ws_floats(plan[i].ws_b), (int)plan[i].npix,
+                                              jobs[i].filter, params->theta + jobs[i].theta_offset, plan[i].nang,
+                                              grads->theta + jobs[i].theta_offset, cs);
             ctx->log.end(tok, cs);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "theta-gradient launch");
         }
@@ -1055,14 +1069,15 @@ dppt_status dppt_loss_l2(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* job
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), cs);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
-    for (int i = 0; i < njobs; ++i) {
-        int tok = ctx->log.begin(kStageFilter, cs);
-        e = launch_l2_loss(raw + raw_offsets[i], target + jobs[i].out_offset, (int)plan[i].npix, jobs[i].filter,
-                           plan[i].filtered ? params->theta + jobs[i].theta_offset : nullptr, plan[i].nang, scale,
-                           loss, cs);
-        ctx->log.end(tok, cs);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "L2 loss launch");
-    }
+    std::vector<L2FoldJob> fj;
+    for (int i = 0; i < njobs; ++i)
+        fj.push_back(L2FoldJob{raw + raw_offsets[i], target + jobs[i].out_offset, nullptr, nullptr,
+                               plan[i].filtered ? params->theta + jobs[i].theta_offset : nullptr, nullptr, plan[i].npix,
+                               plan[i].filtered ? jobs[i].filter : DPPT_FILTER_NONE, plan[i].filtered ? plan[i].nang : 1});
+    int tok = ctx->log.begin(kStageFilter, cs, l2_fold_launches(njobs));
+    e = launch_l2_loss(fj.data(), njobs, scale, loss, cs);
+    ctx->log.end(tok, cs);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "L2 loss launch");
     return DPPT_OK;
 }
 

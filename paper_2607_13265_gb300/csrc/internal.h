@@ -217,11 +217,22 @@ cudaError_t launch_filter_adjoint_input(const float* dimage, float* dS, int npix
                                         const float* theta, int nang, cudaStream_t st);
 cudaError_t launch_theta_grad(const float* dimage, const float* S_adj, int npix, int filter, const float* theta,
                               int nang, float* dtheta, cudaStream_t st);
-// fused mean-squared-error folds (residual C_a raw - T_a formed per pixel)
-cudaError_t launch_l2_loss(const float* raw, const float* target, int npix, int filter, const float* theta, int nang,
-                           double scale, double* loss, cudaStream_t st);
-cudaError_t launch_l2_adjoint_input(const float* raw, const float* target, float* dS, int npix, int filter,
-                                    const float* theta, int nang, float scale2, cudaStream_t st);
-cudaError_t launch_l2_theta_grad(const float* raw, const float* target, const float* S_adj, int npix, int filter,
-                                 const float* theta, int nang, float scale2, float* dtheta, cudaStream_t st);
+// fused mean-squared-error folds (residual C_a raw - T_a formed per pixel), every job of a
+// call in one launch (one per kMaxFoldJobs jobs; l2_fold_launches counts them).  A job
+// without a camera filter has filter DPPT_FILTER_NONE, theta null and nang 1 (C = I).
+struct L2FoldJob {
+    const float* raw;       // [pix][12], the primal paths' raw image
+    const float* target;    // [a][pix][12]
+    float* dS;              // adjoint input out [pix][12] (adjoint-input fold)
+    const float* S_adj;     // the adjoint paths' raw image [pix][12] (angle-gradient fold)
+    const float* theta;     // [nang] filter angles, or null
+    float* dtheta;          // [nang] angle gradients, added into (angle-gradient fold)
+    long long npix;
+    int filter, nang;
+};
+constexpr int kMaxFoldJobs = 64;
+int l2_fold_launches(int njobs);
+cudaError_t launch_l2_loss(const L2FoldJob* jobs, int njobs, double scale, double* loss, cudaStream_t st);
+cudaError_t launch_l2_adjoint_input(const L2FoldJob* jobs, int njobs, float scale2, cudaStream_t st);
+cudaError_t launch_l2_theta_grad(const L2FoldJob* jobs, int njobs, float scale2, cudaStream_t st);
 }  // namespace dppt
