@@ -20,9 +20,16 @@ def test_batched_graph_and_plain_form():
     assert all(v["dtheta_l2"] > 0 for v in out["per_view_gradients"])
 
 
-def test_fused_l2_equals_image_form():
+# (views, angles, spp, sizes, adjoint schedule): a few views and an unfiltered job on the
+# default launch; 70 small views, more than one launch's 64 jobs, so that the L2 folds and the
+# job tables run in two chunks, under the sweep schedule
+FUSED_CASES = {"few_views": (3, 8, 4, (24, 40, 32), None), "70_views_sweep": (70, 3, 2, (8, 12, 9), 3)}
+
+
+@pytest.mark.parametrize("case", list(FUSED_CASES))
+def test_fused_l2_equals_image_form(case):
     """PolarizedL2 (loss folded into the camera filter) gives the loss and every gradient of
-    PolarizedRender + ImageL2 on the same paths -- views with 8 polarizer angles each, plus
+    PolarizedRender + ImageL2 on the same paths -- views with polarizer angles, plus
     an unfiltered job -- while keeping 12 floats per pixel instead of one image per angle."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
@@ -32,9 +39,12 @@ def test_fused_l2_equals_image_form():
     from paper_2607_13265_gb300 import api, build, scenegen as sg
     build.build()
     dctx = api.Context(0)
-    scene, jobs = sg.cornell_views(3, 8, 4, 4, (24, 40, 32))
+    nviews, nang, spp, sizes, adj_sched = FUSED_CASES[case]
+    if adj_sched is not None:
+        dctx.set_launch(0, 128, 0, adj_sched, 128, 0)
+    scene, jobs = sg.cornell_views(nviews, nang, spp, 4, sizes)
     plain = copy.copy(jobs[0])
-    plain.filter, plain.thetas, plain.stream = sg.FILTER_NONE, [], 7
+    plain.filter, plain.thetas, plain.stream = sg.FILTER_NONE, [], 7 + nviews
     jobs = jobs + [plain]
     gs = api.GpuScene(dctx, scene)
     batch = api.pack_jobs(jobs)
