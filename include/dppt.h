@@ -300,7 +300,9 @@ dppt_status dppt_get_replay(const dppt_ctx* ctx, dppt_replay* replay);
 /* Per-thread local cache bytes and registers of the adjoint kernel used for
  * max_depth, and the resident threads per SM for the current launch shape:
  * out[0] = local bytes/thread, out[1] = registers/thread, out[2] = threads/SM,
- * out[3] = SMs. */
+ * out[3] = SMs.  The kernel is the adjoint megakernel (the hybrid's with k > 1,
+ * P-PRB's with that method), or, under the sweep schedule's cached replay, the
+ * forward-sweep megakernel. */
 dppt_status dppt_adjoint_footprint(const dppt_ctx* ctx, int32_t max_depth, int64_t out[4]);
 
 /* Work units of the jobs' paths, counted by an instrumented (untimed) instance

@@ -35,102 +35,121 @@ __device__ __forceinline__ void filter_matrix(int filter, float theta, float C[1
     }
 }
 
-__global__ void k_apply_filter(const float* __restrict__ raw, float* __restrict__ image, int npix, int filter,
-                               const float* __restrict__ theta, int nang) {
+// Every job of a call in one launch: each block belongs to one job (the jobs' blocks back to
+// back, block0[j] the first of job j), so that the small images of a batch, which cannot fill
+// the GPU alone, run side by side instead of one launch after another.
+struct FoldBatch {
+    FoldJob job[kMaxFoldJobs];
+    int block0[kMaxFoldJobs + 1];
+    int njobs;
+};
+__device__ __forceinline__ int fold_job_of_block(const FoldBatch& b) {
+    int lo = 0, hi = b.njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.block0[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// image[a][pix] = C(theta_a) raw[pix] of every filtered job
+__global__ void k_apply_filter(const __grid_constant__ FoldBatch b) {
     extern __shared__ float sC[];
-    for (int a = threadIdx.x; a < nang; a += blockDim.x) {
+    const int jb = fold_job_of_block(b);
+    const FoldJob& J = b.job[jb];
+    for (int a = threadIdx.x; a < J.nang; a += blockDim.x) {
         float C[16], dC[16];
-        filter_matrix(filter, __ldg(theta + a), C, dC);
+        filter_matrix(J.filter, __ldg(J.theta + a), C, dC);
         for (int k = 0; k < 16; ++k) sC[16 * a + k] = C[k];
     }
     __syncthreads();
-    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix; pix += (long long)gridDim.x * blockDim.x) {
-        float r[12];
-        const float4* rp = reinterpret_cast<const float4*>(raw + pix * 12);
-        for (int q = 0; q < 3; ++q) { float4 t = __ldg(rp + q); r[4 * q] = t.x; r[4 * q + 1] = t.y; r[4 * q + 2] = t.z; r[4 * q + 3] = t.w; }
-        for (int a = 0; a < nang; ++a) {
-            const float* C = sC + 16 * a;
-            float4* op = reinterpret_cast<float4*>(image + ((long long)a * npix + pix) * 12);
-            for (int c = 0; c < 3; ++c) {
-                const float* v = r + 4 * c;
-                float o[4];
-                for (int i = 0; i < 4; ++i) o[i] = C[4 * i] * v[0] + C[4 * i + 1] * v[1] + C[4 * i + 2] * v[2] + C[4 * i + 3] * v[3];
-                op[c] = make_float4(o[0], o[1], o[2], o[3]);
-            }
+    const long long pix = (long long)(blockIdx.x - b.block0[jb]) * blockDim.x + threadIdx.x;
+    if (pix >= J.npix) return;
+    float r[12];
+    const float4* rp = reinterpret_cast<const float4*>(J.raw + pix * 12);
+    for (int q = 0; q < 3; ++q) { float4 t = __ldg(rp + q); r[4 * q] = t.x; r[4 * q + 1] = t.y; r[4 * q + 2] = t.z; r[4 * q + 3] = t.w; }
+    for (int a = 0; a < J.nang; ++a) {
+        const float* C = sC + 16 * a;
+        float4* op = reinterpret_cast<float4*>(J.image + ((long long)a * J.npix + pix) * 12);
+        for (int c = 0; c < 3; ++c) {
+            const float* v = r + 4 * c;
+            float o[4];
+            for (int i = 0; i < 4; ++i) o[i] = C[4 * i] * v[0] + C[4 * i + 1] * v[1] + C[4 * i + 2] * v[2] + C[4 * i + 3] * v[3];
+            op[c] = make_float4(o[0], o[1], o[2], o[3]);
         }
     }
 }
 
-__global__ void k_filter_adjoint_input(const float* __restrict__ dimage, float* __restrict__ dS, int npix, int filter,
-                                       const float* __restrict__ theta, int nang) {
+// dS[pix] = sum_a C_a^T dI_a[pix] of every filtered job
+__global__ void k_filter_adjoint_input(const __grid_constant__ FoldBatch b) {
     extern __shared__ float sC[];
-    for (int a = threadIdx.x; a < nang; a += blockDim.x) {
+    const int jb = fold_job_of_block(b);
+    const FoldJob& J = b.job[jb];
+    for (int a = threadIdx.x; a < J.nang; a += blockDim.x) {
         float C[16], dC[16];
-        filter_matrix(filter, __ldg(theta + a), C, dC);
+        filter_matrix(J.filter, __ldg(J.theta + a), C, dC);
         for (int k = 0; k < 16; ++k) sC[16 * a + k] = C[k];
     }
     __syncthreads();
-    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix; pix += (long long)gridDim.x * blockDim.x) {
-        float acc[12];
-        for (int k = 0; k < 12; ++k) acc[k] = 0.0f;
-        for (int a = 0; a < nang; ++a) {
-            const float* C = sC + 16 * a;
-            const float4* dp = reinterpret_cast<const float4*>(dimage + ((long long)a * npix + pix) * 12);
-            for (int c = 0; c < 3; ++c) {
-                float4 t = __ldg(dp + c);
-                float g[4] = {t.x, t.y, t.z, t.w};
-                for (int j = 0; j < 4; ++j)
-                    acc[4 * c + j] += C[j] * g[0] + C[4 + j] * g[1] + C[8 + j] * g[2] + C[12 + j] * g[3];
-            }
+    const long long pix = (long long)(blockIdx.x - b.block0[jb]) * blockDim.x + threadIdx.x;
+    if (pix >= J.npix) return;
+    float acc[12];
+    for (int k = 0; k < 12; ++k) acc[k] = 0.0f;
+    for (int a = 0; a < J.nang; ++a) {
+        const float* C = sC + 16 * a;
+        const float4* dp = reinterpret_cast<const float4*>(J.dimage + ((long long)a * J.npix + pix) * 12);
+        for (int c = 0; c < 3; ++c) {
+            float4 t = __ldg(dp + c);
+            float g[4] = {t.x, t.y, t.z, t.w};
+            for (int j = 0; j < 4; ++j)
+                acc[4 * c + j] += C[j] * g[0] + C[4 + j] * g[1] + C[8 + j] * g[2] + C[12 + j] * g[3];
         }
-        float4* o = reinterpret_cast<float4*>(dS + pix * 12);
-        for (int q = 0; q < 3; ++q) o[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
     }
+    float4* o = reinterpret_cast<float4*>(J.dS + pix * 12);
+    for (int q = 0; q < 3; ++q) o[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
 }
 
-__global__ void k_theta_grad(const float* __restrict__ dimage, const float* __restrict__ S_adj, int npix, int filter,
-                             const float* __restrict__ theta, int nang, float* __restrict__ dtheta) {
+// dtheta_a += sum_pix dI_a[pix]^T dC_a/dtheta S_adj[pix] of every filtered job
+__global__ void k_theta_grad(const __grid_constant__ FoldBatch b) {
     extern __shared__ float sm[];
+    const int jb = fold_job_of_block(b);
+    const FoldJob& J = b.job[jb];
+    const int nang = J.nang;
     float* sdC = sm;               // [nang][16]
     float* sacc = sm + 16 * nang;  // [nang]
     for (int a = threadIdx.x; a < nang; a += blockDim.x) {
         float C[16], dC[16];
-        filter_matrix(filter, __ldg(theta + a), C, dC);
+        filter_matrix(J.filter, __ldg(J.theta + a), C, dC);
         for (int k = 0; k < 16; ++k) sdC[16 * a + k] = dC[k];
         sacc[a] = 0.0f;
     }
     __syncthreads();
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long rounds = (npix + stride - 1) / stride;
-    for (long long it = 0; it < rounds; ++it) {
-        long long pix = first + it * stride;
-        bool act = pix < npix;
-        float s[12];
-        for (int k = 0; k < 12; ++k) s[k] = 0.0f;
+    const long long pix = (long long)(blockIdx.x - b.block0[jb]) * blockDim.x + threadIdx.x;
+    const bool act = pix < J.npix;     // every lane takes part in the warp sums below
+    float s[12];
+    for (int k = 0; k < 12; ++k) s[k] = 0.0f;
+    if (act) {
+        const float4* sp = reinterpret_cast<const float4*>(J.S_adj + pix * 12);
+        for (int q = 0; q < 3; ++q) { float4 t = __ldg(sp + q); s[4 * q] = t.x; s[4 * q + 1] = t.y; s[4 * q + 2] = t.z; s[4 * q + 3] = t.w; }
+    }
+    for (int a = 0; a < nang; ++a) {
+        float v = 0.0f;
         if (act) {
-            const float4* sp = reinterpret_cast<const float4*>(S_adj + pix * 12);
-            for (int q = 0; q < 3; ++q) { float4 t = __ldg(sp + q); s[4 * q] = t.x; s[4 * q + 1] = t.y; s[4 * q + 2] = t.z; s[4 * q + 3] = t.w; }
-        }
-        for (int a = 0; a < nang; ++a) {
-            float v = 0.0f;
-            if (act) {
-                const float* dC = sdC + 16 * a;
-                const float4* dp = reinterpret_cast<const float4*>(dimage + ((long long)a * npix + pix) * 12);
-                for (int c = 0; c < 3; ++c) {
-                    float4 t = __ldg(dp + c);
-                    float g[4] = {t.x, t.y, t.z, t.w};
-                    for (int i = 0; i < 4; ++i)
-                        v += g[i] * (dC[4 * i] * s[4 * c] + dC[4 * i + 1] * s[4 * c + 1] + dC[4 * i + 2] * s[4 * c + 2] + dC[4 * i + 3] * s[4 * c + 3]);
-                }
+            const float* dC = sdC + 16 * a;
+            const float4* dp = reinterpret_cast<const float4*>(J.dimage + ((long long)a * J.npix + pix) * 12);
+            for (int c = 0; c < 3; ++c) {
+                float4 t = __ldg(dp + c);
+                float g[4] = {t.x, t.y, t.z, t.w};
+                for (int i = 0; i < 4; ++i)
+                    v += g[i] * (dC[4 * i] * s[4 * c] + dC[4 * i + 1] * s[4 * c + 1] + dC[4 * i + 2] * s[4 * c + 2] + dC[4 * i + 3] * s[4 * c + 3]);
             }
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(sacc + a, v);
         }
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(sacc + a, v);
     }
     __syncthreads();
     for (int a = threadIdx.x; a < nang; a += blockDim.x)
-        if (sacc[a] != 0.0f) atomicAdd(dtheta + a, sacc[a]);
+        if (sacc[a] != 0.0f) atomicAdd(J.dtheta + a, sacc[a]);
 }
 
 // ================================================================== fused L2 loss folds
@@ -153,29 +172,12 @@ __device__ __forceinline__ void residual4(const float* C, const float* v, const 
     for (int i = 0; i < 4; ++i) d[i] = C[4 * i] * v[0] + C[4 * i + 1] * v[1] + C[4 * i + 2] * v[2] + C[4 * i + 3] * v[3] - t[i];
 }
 
-// Every job of a call in one launch: each block belongs to one job (the jobs' blocks back to
-// back, block0[j] the first of job j), so that the small images of a batch, which cannot fill
-// the GPU alone, run side by side instead of one launch after another.
-struct L2FoldBatch {
-    L2FoldJob job[kMaxFoldJobs];
-    int block0[kMaxFoldJobs + 1];
-    int njobs;
-};
-__device__ __forceinline__ int fold_job_of_block(const L2FoldBatch& b) {
-    int lo = 0, hi = b.njobs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (b.block0[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 // scale * sum_a sum_pix |C_a raw - T_a|^2 of every job, added into *loss
-__global__ void k_l2_loss(const __grid_constant__ L2FoldBatch b, double scale, double* loss) {
+__global__ void k_l2_loss(const __grid_constant__ FoldBatch b, double scale, double* loss) {
     extern __shared__ float sC[];
     __shared__ double swarp[32];
     const int jb = fold_job_of_block(b);
-    const L2FoldJob& J = b.job[jb];
+    const FoldJob& J = b.job[jb];
     for (int a = threadIdx.x; a < J.nang; a += blockDim.x) {
         float C[16], dC[16];
         filter_or_identity(J.filter, J.theta, a, C, dC);
@@ -209,10 +211,10 @@ __global__ void k_l2_loss(const __grid_constant__ L2FoldBatch b, double scale, d
 }
 
 // dS = 2 scale sum_a C_a^T (C_a raw - T_a) of every job
-__global__ void k_l2_adjoint_input(const __grid_constant__ L2FoldBatch b, float scale2) {
+__global__ void k_l2_adjoint_input(const __grid_constant__ FoldBatch b, float scale2) {
     extern __shared__ float sC[];
     const int jb = fold_job_of_block(b);
-    const L2FoldJob& J = b.job[jb];
+    const FoldJob& J = b.job[jb];
     for (int a = threadIdx.x; a < J.nang; a += blockDim.x) {
         float C[16], dC[16];
         filter_or_identity(J.filter, J.theta, a, C, dC);
@@ -240,10 +242,10 @@ __global__ void k_l2_adjoint_input(const __grid_constant__ L2FoldBatch b, float 
 }
 
 // dtheta_a += 2 scale sum_pix (C_a raw - T_a)^T dC_a S_adj of every (filtered) job
-__global__ void k_l2_theta_grad(const __grid_constant__ L2FoldBatch b, float scale2) {
+__global__ void k_l2_theta_grad(const __grid_constant__ FoldBatch b, float scale2) {
     extern __shared__ float sm[];
     const int jb = fold_job_of_block(b);
-    const L2FoldJob& J = b.job[jb];
+    const FoldJob& J = b.job[jb];
     const int nang = J.nang;
     float* sC = sm;                 // [nang][16]
     float* sdC = sm + 16 * nang;    // [nang][16]
@@ -281,34 +283,14 @@ __global__ void k_l2_theta_grad(const __grid_constant__ L2FoldBatch b, float sca
         if (sacc[a] != 0.0f) atomicAdd(J.dtheta + a, sacc[a]);
 }
 
-static int fold_grid(int npix, int block) {
-    long long g = ((long long)npix + block - 1) / block;
-    return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
-}
-cudaError_t launch_apply_filter(const float* raw, float* image, int npix, int filter, const float* theta,
-                                int nang, cudaStream_t st) {
-    k_apply_filter<<<fold_grid(npix, 256), 256, sizeof(float) * 16 * nang, st>>>(raw, image, npix, filter, theta, nang);
-    return cudaGetLastError();
-}
-cudaError_t launch_filter_adjoint_input(const float* dimage, float* dS, int npix, int filter,
-                                        const float* theta, int nang, cudaStream_t st) {
-    k_filter_adjoint_input<<<fold_grid(npix, 256), 256, sizeof(float) * 16 * nang, st>>>(dimage, dS, npix, filter, theta, nang);
-    return cudaGetLastError();
-}
-cudaError_t launch_theta_grad(const float* dimage, const float* S_adj, int npix, int filter, const float* theta,
-                              int nang, float* dtheta, cudaStream_t st) {
-    k_theta_grad<<<fold_grid(npix, 256), 256, sizeof(float) * 17 * nang, st>>>(dimage, S_adj, npix, filter, theta, nang, dtheta);
-    return cudaGetLastError();
-}
-
-// The batched L2 folds: the jobs in chunks of kMaxFoldJobs, one launch per chunk, 256 threads
+// The batched folds: the jobs in chunks of kMaxFoldJobs, one launch per chunk, 256 threads
 // per block, one pixel per thread.  smem_per_angle: floats of shared memory per angle.
 template <class Launch>
-static cudaError_t launch_fold_batches(const L2FoldJob* jobs, int njobs, int smem_per_angle, const void* kernel,
+static cudaError_t launch_fold_batches(const FoldJob* jobs, int njobs, int smem_per_angle, const void* kernel,
                                        Launch launch) {
     constexpr int kBlock = 256;
     for (int j0 = 0; j0 < njobs; j0 += kMaxFoldJobs) {
-        L2FoldBatch b{};
+        FoldBatch b{};
         b.njobs = std::min(kMaxFoldJobs, njobs - j0);
         long long blocks = 0;
         int nang = 1;
@@ -332,22 +314,36 @@ static cudaError_t launch_fold_batches(const L2FoldJob* jobs, int njobs, int sme
     }
     return cudaSuccess;
 }
-int l2_fold_launches(int njobs) { return (njobs + kMaxFoldJobs - 1) / kMaxFoldJobs; }
-cudaError_t launch_l2_loss(const L2FoldJob* jobs, int njobs, double scale, double* loss, cudaStream_t st) {
+int fold_launches(int njobs) { return (njobs + kMaxFoldJobs - 1) / kMaxFoldJobs; }
+cudaError_t launch_apply_filter(const FoldJob* jobs, int njobs, cudaStream_t st) {
+    return launch_fold_batches(jobs, njobs, 16, reinterpret_cast<const void*>(&k_apply_filter),
+                               [&](const FoldBatch& b, int g, int blk, size_t sm) { k_apply_filter<<<g, blk, sm, st>>>(b); });
+}
+cudaError_t launch_filter_adjoint_input(const FoldJob* jobs, int njobs, cudaStream_t st) {
+    return launch_fold_batches(jobs, njobs, 16, reinterpret_cast<const void*>(&k_filter_adjoint_input),
+                               [&](const FoldBatch& b, int g, int blk, size_t sm) {
+                                   k_filter_adjoint_input<<<g, blk, sm, st>>>(b);
+                               });
+}
+cudaError_t launch_theta_grad(const FoldJob* jobs, int njobs, cudaStream_t st) {
+    return launch_fold_batches(jobs, njobs, 17, reinterpret_cast<const void*>(&k_theta_grad),
+                               [&](const FoldBatch& b, int g, int blk, size_t sm) { k_theta_grad<<<g, blk, sm, st>>>(b); });
+}
+cudaError_t launch_l2_loss(const FoldJob* jobs, int njobs, double scale, double* loss, cudaStream_t st) {
     return launch_fold_batches(jobs, njobs, 16, reinterpret_cast<const void*>(&k_l2_loss),
-                               [&](const L2FoldBatch& b, int g, int blk, size_t sm) {
+                               [&](const FoldBatch& b, int g, int blk, size_t sm) {
                                    k_l2_loss<<<g, blk, sm, st>>>(b, scale, loss);
                                });
 }
-cudaError_t launch_l2_adjoint_input(const L2FoldJob* jobs, int njobs, float scale2, cudaStream_t st) {
+cudaError_t launch_l2_adjoint_input(const FoldJob* jobs, int njobs, float scale2, cudaStream_t st) {
     return launch_fold_batches(jobs, njobs, 16, reinterpret_cast<const void*>(&k_l2_adjoint_input),
-                               [&](const L2FoldBatch& b, int g, int blk, size_t sm) {
+                               [&](const FoldBatch& b, int g, int blk, size_t sm) {
                                    k_l2_adjoint_input<<<g, blk, sm, st>>>(b, scale2);
                                });
 }
-cudaError_t launch_l2_theta_grad(const L2FoldJob* jobs, int njobs, float scale2, cudaStream_t st) {
+cudaError_t launch_l2_theta_grad(const FoldJob* jobs, int njobs, float scale2, cudaStream_t st) {
     return launch_fold_batches(jobs, njobs, 33, reinterpret_cast<const void*>(&k_l2_theta_grad),
-                               [&](const L2FoldBatch& b, int g, int blk, size_t sm) {
+                               [&](const FoldBatch& b, int g, int blk, size_t sm) {
                                    k_l2_theta_grad<<<g, blk, sm, st>>>(b, scale2);
                                });
 }

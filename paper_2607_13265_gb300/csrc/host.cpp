@@ -312,6 +312,28 @@ int trace_occupancy(int bucket, int mode, int block, size_t smem) {
     }
     return 0;
 }
+static cudaError_t sweep_attributes(int bucket, cudaFuncAttributes* a) {
+    switch (bucket) {
+        case 4: return sweep_attributes_4(a);
+        case 8: return sweep_attributes_8(a);
+        case 16: return sweep_attributes_16(a);
+        case 32: return sweep_attributes_32(a);
+        case 64: return sweep_attributes_64(a);
+        case 128: return sweep_attributes_128(a);
+    }
+    return cudaErrorInvalidValue;
+}
+static int sweep_occupancy(int bucket, int block) {
+    switch (bucket) {
+        case 4: return sweep_occupancy_4(block);
+        case 8: return sweep_occupancy_8(block);
+        case 16: return sweep_occupancy_16(block);
+        case 32: return sweep_occupancy_32(block);
+        case 64: return sweep_occupancy_64(block);
+        case 128: return sweep_occupancy_128(block);
+    }
+    return 0;
+}
 
 // hybrid cached replay kernels: interval k in {4, 8, 16}, depth buckets 8..128
 int hybrid_bucket(int max_depth) { return std::max(8, depth_bucket(max_depth)); }
@@ -350,6 +372,17 @@ struct JobPlan {
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// A job's entry in a batched camera-filter fold, its buffers left for the caller: the filter
+// and its angles, or none (C = I, one angle) for a job without a camera filter.
+static FoldJob fold_job(const JobPlan& pl, const dppt_job& j, const dppt_params* params) {
+    FoldJob f{};
+    f.npix = pl.npix;
+    f.filter = pl.filtered ? j.filter : DPPT_FILTER_NONE;
+    f.theta = pl.filtered ? params->theta + j.theta_offset : nullptr;
+    f.nang = pl.filtered ? pl.nang : 1;
+    return f;
+}
 
 dppt_status check_jobs(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* jobs, int32_t njobs,
                        const dppt_params* p, bool adjoint, std::vector<JobPlan>& plan, size_t& ws_bytes,
@@ -842,12 +875,18 @@ dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_jo
         ctx->log.end(tok, cs);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "primal launch");
     }
+    // every filtered job's per-angle images in one batched launch
+    std::vector<FoldJob> fj;
     for (int i = 0; i < njobs; ++i) {
         if (!plan[i].filtered) continue;
-        const float* raw = reinterpret_cast<const float*>(static_cast<char*>(ctx->ws) + plan[i].ws_a);
-        int tok = ctx->log.begin(kStageFilter, cs);
-        cudaError_t e = launch_apply_filter(raw, image + jobs[i].out_offset, (int)plan[i].npix, jobs[i].filter,
-                                            params->theta + jobs[i].theta_offset, plan[i].nang, cs);
+        FoldJob f = fold_job(plan[i], jobs[i], params);
+        f.raw = reinterpret_cast<const float*>(static_cast<char*>(ctx->ws) + plan[i].ws_a);
+        f.image = image + jobs[i].out_offset;
+        fj.push_back(f);
+    }
+    if (!fj.empty()) {
+        int tok = ctx->log.begin(kStageFilter, cs, fold_launches((int)fj.size()));
+        cudaError_t e = launch_apply_filter(fj.data(), (int)fj.size(), cs);
         ctx->log.end(tok, cs);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "filter launch");
     }
@@ -888,29 +927,25 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
     build_tables(jobs, njobs, plan, shape.block, first, tables, maxd);
     DParams P = dparams(params);
     DGrads G{grads->tex, grads->ior, grads->le, grads->sheet};
-    // the adjoint inputs: the fused L2 loss's of every job in one batched launch, or the
+    // the adjoint inputs of every job in one batched launch: the fused L2 loss's, or the
     // camera filter's fold of each filtered job's image adjoint
     auto ws_floats = [&](size_t off) { return reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + off); };
-    if (l2) {
-        std::vector<L2FoldJob> fj;
-        for (int i = 0; i < njobs; ++i)
-            fj.push_back(L2FoldJob{l2->raw + l2->raw_offsets[i], l2->target + jobs[i].out_offset, ws_floats(plan[i].ws_a),
-                                   nullptr, plan[i].filtered ? params->theta + jobs[i].theta_offset : nullptr, nullptr,
-                                   plan[i].npix, plan[i].filtered ? jobs[i].filter : DPPT_FILTER_NONE,
-                                   plan[i].filtered ? plan[i].nang : 1});
-        int tok = ctx->log.begin(kStageFilter, cs, l2_fold_launches(njobs));
-        cudaError_t e = launch_l2_adjoint_input(fj.data(), njobs, 2.0f * l2->scale, cs);
-        ctx->log.end(tok, cs);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "L2 adjoint input launch");
-    } else {
+    {
+        std::vector<FoldJob> fj;
         for (int i = 0; i < njobs; ++i) {
-            if (!plan[i].filtered) continue;
-            int tok = ctx->log.begin(kStageFilter, cs);
-            cudaError_t e = launch_filter_adjoint_input(d_image + jobs[i].out_offset, ws_floats(plan[i].ws_a),
-                                                        (int)plan[i].npix, jobs[i].filter,
-                                                        params->theta + jobs[i].theta_offset, plan[i].nang, cs);
+            if (!l2 && !plan[i].filtered) continue;
+            FoldJob f = fold_job(plan[i], jobs[i], params);
+            if (l2) { f.raw = l2->raw + l2->raw_offsets[i]; f.target = l2->target + jobs[i].out_offset; }
+            else f.dimage = d_image + jobs[i].out_offset;
+            f.dS = ws_floats(plan[i].ws_a);
+            fj.push_back(f);
+        }
+        if (!fj.empty()) {
+            int tok = ctx->log.begin(kStageFilter, cs, fold_launches((int)fj.size()));
+            cudaError_t e = l2 ? launch_l2_adjoint_input(fj.data(), (int)fj.size(), 2.0f * l2->scale, cs)
+                               : launch_filter_adjoint_input(fj.data(), (int)fj.size(), cs);
             ctx->log.end(tok, cs);
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "filter adjoint launch");
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint input launch");
         }
     }
     for (size_t g = 0; g < tables.size(); ++g) {
@@ -1000,27 +1035,22 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
         ctx->log.end(tok, cs);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
     }
-    if (grads->theta && l2) {
+    if (grads->theta) {
         // the angle gradients of every filtered job in one batched launch
-        std::vector<L2FoldJob> fj;
-        for (int i = 0; i < njobs; ++i)
-            if (plan[i].filtered)
-                fj.push_back(L2FoldJob{l2->raw + l2->raw_offsets[i], l2->target + jobs[i].out_offset, nullptr,
-                                       ws_floats(plan[i].ws_b), params->theta + jobs[i].theta_offset,
-                                       grads->theta + jobs[i].theta_offset, plan[i].npix, jobs[i].filter, plan[i].nang});
-        if (!fj.empty()) {
-            int tok = ctx->log.begin(kStageFilter, cs, l2_fold_launches((int)fj.size()));
-            cudaError_t e = launch_l2_theta_grad(fj.data(), (int)fj.size(), 2.0f * l2->scale, cs);
-            ctx->log.end(tok, cs);
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "theta-gradient launch");
-        }
-    } else if (grads->theta) {
+        std::vector<FoldJob> fj;
         for (int i = 0; i < njobs; ++i) {
             if (!plan[i].filtered) continue;
-            int tok = ctx->log.begin(kStageFilter, cs);
-            cudaError_t e = launch_theta_grad(d_image + jobs[i].out_offset, ws_floats(plan[i].ws_b), (int)plan[i].npix,
-                                              jobs[i].filter, params->theta + jobs[i].theta_offset, plan[i].nang,
-                                              grads->theta + jobs[i].theta_offset, cs);
+            FoldJob f = fold_job(plan[i], jobs[i], params);
+            if (l2) { f.raw = l2->raw + l2->raw_offsets[i]; f.target = l2->target + jobs[i].out_offset; }
+            else f.dimage = d_image + jobs[i].out_offset;
+            f.S_adj = ws_floats(plan[i].ws_b);
+            f.dtheta = grads->theta + jobs[i].theta_offset;
+            fj.push_back(f);
+        }
+        if (!fj.empty()) {
+            int tok = ctx->log.begin(kStageFilter, cs, fold_launches((int)fj.size()));
+            cudaError_t e = l2 ? launch_l2_theta_grad(fj.data(), (int)fj.size(), 2.0f * l2->scale, cs)
+                               : launch_theta_grad(fj.data(), (int)fj.size(), cs);
             ctx->log.end(tok, cs);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "theta-gradient launch");
         }
@@ -1069,12 +1099,14 @@ dppt_status dppt_loss_l2(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* job
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), cs);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
-    std::vector<L2FoldJob> fj;
-    for (int i = 0; i < njobs; ++i)
-        fj.push_back(L2FoldJob{raw + raw_offsets[i], target + jobs[i].out_offset, nullptr, nullptr,
-                               plan[i].filtered ? params->theta + jobs[i].theta_offset : nullptr, nullptr, plan[i].npix,
-                               plan[i].filtered ? jobs[i].filter : DPPT_FILTER_NONE, plan[i].filtered ? plan[i].nang : 1});
-    int tok = ctx->log.begin(kStageFilter, cs, l2_fold_launches(njobs));
+    std::vector<FoldJob> fj;
+    for (int i = 0; i < njobs; ++i) {
+        FoldJob f = fold_job(plan[i], jobs[i], params);
+        f.raw = raw + raw_offsets[i];
+        f.target = target + jobs[i].out_offset;
+        fj.push_back(f);
+    }
+    int tok = ctx->log.begin(kStageFilter, cs, fold_launches(njobs));
     e = launch_l2_loss(fj.data(), njobs, scale, loss, cs);
     ctx->log.end(tok, cs);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "L2 loss launch");
@@ -1153,15 +1185,22 @@ dppt_status dppt_adjoint_footprint(const dppt_ctx* ctx, int32_t max_depth, int64
     if (!ctx || !out || max_depth < 1 || max_depth > kMaxDepth) return DPPT_ERR_INVALID_ARG;
     const int k = ctx->replay.checkpoint_interval, blk = ctx->launch.adj_block_size;
     const bool pprb = ctx->replay.method == DPPT_REPLAY_PPRB;
+    // the sweep schedule's cached replay: its forward-sweep megakernel (at most 256 threads a block)
+    const bool sweep = !pprb && k == 1 && ctx->launch.adj_schedule == DPPT_SCHED_SWEEP;
     const int bucket = k > 1 ? hybrid_bucket(max_depth) : depth_bucket(max_depth);
     cudaFuncAttributes a;
-    cudaError_t e = pprb ? pprb_attributes(&a) : k > 1 ? hybrid_attributes(k, bucket, &a) : trace_attributes(bucket, 1, &a);
+    cudaError_t e = pprb    ? pprb_attributes(&a)
+                    : k > 1 ? hybrid_attributes(k, bucket, &a)
+                    : sweep ? sweep_attributes(bucket, &a)
+                            : trace_attributes(bucket, 1, &a);
     if (e != cudaSuccess) return DPPT_ERR_CUDA;
     out[0] = (int64_t)a.localSizeBytes;
     out[1] = a.numRegs;
-    out[2] = (int64_t)(pprb     ? pprb_occupancy(blk, 1024)
-                       : k > 1 ? hybrid_occupancy(k, bucket, blk, 1024)
-                               : trace_occupancy(bucket, 1, blk, 1024)) * blk;
+    const int sblk = std::min(blk, 256);
+    out[2] = pprb    ? (int64_t)pprb_occupancy(blk, 1024) * blk
+             : k > 1 ? (int64_t)hybrid_occupancy(k, bucket, blk, 1024) * blk
+             : sweep ? (int64_t)sweep_occupancy(bucket, sblk) * sblk
+                     : (int64_t)trace_occupancy(bucket, 1, blk, 1024) * blk;
     out[3] = ctx->sm_count;
     return DPPT_OK;
 }

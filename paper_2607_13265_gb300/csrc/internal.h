@@ -160,7 +160,10 @@ struct StageLog {
                                  const LaunchCfg& L, unsigned long long* counter, unsigned* status,             \
                                  unsigned long long* work, cudaStream_t st);                                    \
     cudaError_t trace_attributes_##B(int mode, cudaFuncAttributes* a);                                         \
-    int trace_occupancy_##B(int mode, int block, size_t smem);
+    int trace_occupancy_##B(int mode, int block, size_t smem);                                                  \
+    /* the sweep schedule's forward-sweep kernel of the bucket (wavefront.cuh) */                               \
+    cudaError_t sweep_attributes_##B(cudaFuncAttributes* a);                                                    \
+    int sweep_occupancy_##B(int block);
 DPPT_DECLARE_BUCKET(4)
 DPPT_DECLARE_BUCKET(8)
 DPPT_DECLARE_BUCKET(16)
@@ -209,30 +212,34 @@ const DScene* scene_view(const dppt_scene* s);
 int scene_num_cameras(const dppt_scene* s);
 int64_t scene_tex_size(const dppt_scene* s);
 
-// camera-filter folds: image[a][pix] = C(theta_a) raw[pix]; dS[pix] = sum_a C_a^T dI_a[pix];
-// dtheta_a += sum_pix dI_a[pix]^T dC_a/dtheta S_adj[pix]
-cudaError_t launch_apply_filter(const float* raw, float* image, int npix, int filter, const float* theta,
-                                int nang, cudaStream_t st);
-cudaError_t launch_filter_adjoint_input(const float* dimage, float* dS, int npix, int filter,
-                                        const float* theta, int nang, cudaStream_t st);
-cudaError_t launch_theta_grad(const float* dimage, const float* S_adj, int npix, int filter, const float* theta,
-                              int nang, float* dtheta, cudaStream_t st);
-// fused mean-squared-error folds (residual C_a raw - T_a formed per pixel), every job of a
-// call in one launch (one per kMaxFoldJobs jobs; l2_fold_launches counts them).  A job
-// without a camera filter has filter DPPT_FILTER_NONE, theta null and nang 1 (C = I).
-struct L2FoldJob {
-    const float* raw;       // [pix][12], the primal paths' raw image
-    const float* target;    // [a][pix][12]
-    float* dS;              // adjoint input out [pix][12] (adjoint-input fold)
-    const float* S_adj;     // the adjoint paths' raw image [pix][12] (angle-gradient fold)
+// Camera-filter folds, every job of a call in one launch (one per kMaxFoldJobs jobs;
+// fold_launches counts them).  A job's fields by fold:
+//   apply_filter:          image[a][pix] = C(theta_a) raw[pix]
+//   filter_adjoint_input:  dS[pix] = sum_a C_a^T dimage_a[pix]
+//   theta_grad:            dtheta_a += sum_pix dimage_a[pix]^T dC_a/dtheta S_adj[pix]
+//   l2_loss:               *loss += scale sum_a sum_pix |C_a raw - target_a|^2
+//   l2_adjoint_input:      dS[pix] = 2 scale sum_a C_a^T (C_a raw - target_a)
+//   l2_theta_grad:         dtheta_a += 2 scale sum_pix (C_a raw - target_a)^T dC_a S_adj[pix]
+// The L2 folds take a job without a camera filter as filter DPPT_FILTER_NONE, theta null and
+// nang 1 (C = I).  Images are [pix][12] and per-angle images [a][pix][12] float32.
+struct FoldJob {
+    const float* raw;       // the primal paths' raw image
+    const float* target;    // the L2 target
+    const float* dimage;    // the image adjoint dg/dI
+    float* image;           // the filtered images out
+    float* dS;              // the adjoint input out
+    const float* S_adj;     // the adjoint paths' raw image
     const float* theta;     // [nang] filter angles, or null
-    float* dtheta;          // [nang] angle gradients, added into (angle-gradient fold)
+    float* dtheta;          // [nang] angle gradients, added into
     long long npix;
     int filter, nang;
 };
 constexpr int kMaxFoldJobs = 64;
-int l2_fold_launches(int njobs);
-cudaError_t launch_l2_loss(const L2FoldJob* jobs, int njobs, double scale, double* loss, cudaStream_t st);
-cudaError_t launch_l2_adjoint_input(const L2FoldJob* jobs, int njobs, float scale2, cudaStream_t st);
-cudaError_t launch_l2_theta_grad(const L2FoldJob* jobs, int njobs, float scale2, cudaStream_t st);
+int fold_launches(int njobs);
+cudaError_t launch_apply_filter(const FoldJob* jobs, int njobs, cudaStream_t st);
+cudaError_t launch_filter_adjoint_input(const FoldJob* jobs, int njobs, cudaStream_t st);
+cudaError_t launch_theta_grad(const FoldJob* jobs, int njobs, cudaStream_t st);
+cudaError_t launch_l2_loss(const FoldJob* jobs, int njobs, double scale, double* loss, cudaStream_t st);
+cudaError_t launch_l2_adjoint_input(const FoldJob* jobs, int njobs, float scale2, cudaStream_t st);
+cudaError_t launch_l2_theta_grad(const FoldJob* jobs, int njobs, float scale2, cudaStream_t st);
 }  // namespace dppt

@@ -137,8 +137,14 @@ extern "C" dppt_status dppt_render_primal_noalloc(dppt_ctx* ctx, const dppt_scen
     e = launch_bucket(bucket, S, P, G, T, L, ctx_status_word(ctx), st);
     if (e != cudaSuccess) return bad(ctx, DPPT_ERR_CUDA, std::string("primal launch: ") + cudaGetErrorString(e));
     if (filtered) {
-        e = launch_apply_filter(static_cast<const float*>(base), image + j.out_offset, (int)npix, j.filter,
-                                params->theta + j.theta_offset, j.num_angles, st);
+        FoldJob f{};
+        f.raw = static_cast<const float*>(base);
+        f.image = image + j.out_offset;
+        f.theta = params->theta + j.theta_offset;
+        f.npix = npix;
+        f.filter = j.filter;
+        f.nang = j.num_angles;
+        e = launch_apply_filter(&f, 1, st);
         if (e != cudaSuccess) return bad(ctx, DPPT_ERR_CUDA, std::string("filter launch: ") + cudaGetErrorString(e));
     }
     return DPPT_OK;

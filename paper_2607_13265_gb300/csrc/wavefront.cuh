@@ -317,6 +317,18 @@ k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
         if (nmaps) k_wf_sweep<B, true><<<(int)g, block, 0, st>>>(S, P, T, wt, W, L, status);                       \
         else k_wf_sweep<B, false><<<(int)g, block, 0, st>>>(S, P, T, wt, W, L, status);                           \
         return cudaGetLastError();                                                                               \
+    }                                                                                                            \
+    /* the attributes and occupancy of the kernel without normal-map code (the same launch  */                  \
+    /* bounds as the one with it)                                                           */                  \
+    cudaError_t sweep_attributes_##B(cudaFuncAttributes* a) {                                                   \
+        return cudaFuncGetAttributes(a, reinterpret_cast<const void*>(&k_wf_sweep<B, false>));                   \
+    }                                                                                                            \
+    int sweep_occupancy_##B(int block) {                                                                         \
+        int nb = 0;                                                                                              \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, reinterpret_cast<const void*>(&k_wf_sweep<B, false>), \
+                                                          block, 0) != cudaSuccess)                              \
+            return 0;                                                                                            \
+        return nb;                                                                                               \
     }
 
 #define DPPT_DECLARE_SWEEP(B)                                                                                       \

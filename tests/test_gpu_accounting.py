@@ -125,6 +125,25 @@ def test_stage_statistics_of_the_sweep_schedule(env):
     assert n >= job.max_depth and n % job.max_depth == 0
 
 
+def test_adjoint_footprint_follows_the_schedule(env):
+    """Under the sweep schedule the footprint is the forward-sweep megakernel's: its
+    thread-local arrays hold E_v and W_v (31 floats) per vertex of the cache depth, and at
+    most 256 threads a block (a 512-thread shape runs its sweep at 256)."""
+    api, dctx, _ = env
+    prev = dctx.get_launch()
+    try:
+        dctx.set_launch(0, 256, 0, 3, 512, 0)
+        sw = dctx.adjoint_footprint(8)
+        dctx.set_launch(0, 256, 0, 0, 256, 0)
+        mk = dctx.adjoint_footprint(8)
+    finally:
+        dctx.set_launch(*prev)
+    assert sw["local_bytes_per_thread"] >= 8 * 31 * 4 and mk["local_bytes_per_thread"] >= 8 * 31 * 4
+    assert sw["registers"] <= 128 and sw["threads_per_sm"] % 256 == 0 and 256 <= sw["threads_per_sm"] <= 2048
+    assert sw["threads_per_sm"] >= mk["threads_per_sm"]      # the primal's launch bounds, not the adjoint's
+    assert sw["sms"] == mk["sms"] > 0
+
+
 def test_autotune_picks_valid_shapes_with_equal_results(env):
     import torch
     api, dctx, _ = env
