@@ -86,6 +86,9 @@ DRAM_BYTES_PER_LAUNCH = {
 
 # floats per vertex of the wavefront cache: E_v 12, compact W_v 19, visibility 1, the hit 4
 WF_CACHE_FLOATS = 36
+# bytes per vertex the sweep schedule keeps for the replay: the suffix 48, the hit 16 and the
+# visibility word 4 (besides its megakernel's thread-local arrays)
+SWEEP_RECORD_BYTES = 68
 
 
 def wave_paths(jobs) -> int:
@@ -674,6 +677,9 @@ def run_icosphere(args, api, dctx, rank, dev, peaks):
             "roofline": roofline_of(stages, flops, cbytes, props, peaks, {}, ICO_WORKLOAD, work),
             "memory": {"workspace_bytes": dctx.query_workspace(adj),
                        "prb_cache_bytes": (wave_paths([job]) * job.max_depth * WF_CACHE_FLOATS * 4 if lc[3] == 2
+                                           else wave_paths([job]) * job.max_depth * SWEEP_RECORD_BYTES
+                                           + fp["local_bytes_per_thread"] * fp["threads_per_sm"] * fp["sms"]
+                                           if lc[3] == 3
                                            else fp["local_bytes_per_thread"] * fp["threads_per_sm"] * fp["sms"]),
                        "megakernel_local_bytes_per_thread": fp["local_bytes_per_thread"],
                        "megakernel_adjoint_registers": fp["registers"]},
