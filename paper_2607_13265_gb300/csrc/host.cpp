@@ -904,6 +904,10 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
     DScene Sd = s->d;   // the adjoint launches' copy, with the texel-gradient scatter of the launch shape
     Sd.scatter_lane = ctx->launch.adj_scatter == DPPT_SCATTER_LANE ? 1 : 0;
     Sd.sgrad_lanes = ctx->launch.adj_schedule == DPPT_SCHED_WAVEFRONT || ctx->launch.adj_schedule == DPPT_SCHED_SWEEP;
+    // the replay kernels of those schedules sum the texel gradients of a scene whose textures
+    // are small in all in their per-block accumulators too, with 32 copies each
+    Sd.tex_shared = Sd.sgrad_lanes && grads && grads->tex && sgrad_texel_base(Sd) + s->tex_size <= kSharedGradFloats
+                        ? (int)s->tex_size : 0;
     if (!grads) return fail(ctx, DPPT_ERR_INVALID_ARG, "grads is null");
     if (!l2 && !d_image && njobs > 0) return fail(ctx, DPPT_ERR_INVALID_ARG, "d_image is null");
     cudaSetDevice(ctx->device);

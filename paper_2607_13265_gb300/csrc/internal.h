@@ -51,6 +51,8 @@ struct DScene {
     int num_ior, num_sheets;
     int scatter_lane;       // adjoint: texel gradients one atomic per lane (1) or per warp group (0)
     int sgrad_lanes;        // adjoint: scalar-gradient accumulators with a copy per lane (1) or one (0)
+    int tex_shared;         // adjoint: texel gradients summed in the block's accumulators too (the
+                            // texel floats, when every texture together is that small), or 0
     int mat_types;          // bit t set when a triangle or sphere uses a material of type t
 };
 
@@ -59,8 +61,14 @@ struct DScene {
 // sgrad_lanes (the wavefront replay) each scalar has 32 copies when they fit in 16 KB: lane
 // l of a warp adds to copy l, so the lanes of a warp adding to one scalar use 32 banks
 // instead of serialising on one address.  The megakernels keep one copy: their thread-local
-// caches live in L1, which a larger shared-memory carveout would shrink.
-inline __host__ __device__ int sgrad_scalars(const DScene& S) { return S.num_ior + S.num_sheets + 12 * S.num_lights; }
+// caches live in L1, which a larger shared-memory carveout would shrink.  When a scene's
+// textures hold few texels in all (tex_shared), their gradients join the accumulators after
+// the scalars: every replayed vertex adds to the same few texels, and global atomics on them
+// serialise across the whole GPU.
+inline __host__ __device__ int sgrad_texel_base(const DScene& S) { return S.num_ior + S.num_sheets + 12 * S.num_lights; }
+inline __host__ __device__ int sgrad_scalars(const DScene& S) { return sgrad_texel_base(S) + S.tex_shared; }
+// the largest accumulator count that keeps 32 copies within 16 KB
+constexpr int kSharedGradFloats = 16384 / (32 * 4);
 inline __host__ __device__ int sgrad_copies(const DScene& S) {
     return S.sgrad_lanes && sgrad_scalars(S) * 32 * (int)sizeof(float) <= 16384 ? 32 : 1;
 }

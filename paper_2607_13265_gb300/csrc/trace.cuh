@@ -1034,7 +1034,7 @@ __device__ __forceinline__ void sgrad_add(const DScene& S, float* sg, int k, flo
 __device__ __forceinline__ void sgrad_flush(const DScene& S, const DGrads& G, const float* sg) {
     __syncthreads();
     const int nscal = sgrad_scalars(S), copies = sgrad_copies(S);
-    const int nI = S.num_ior, nS = S.num_sheets;
+    const int nI = S.num_ior, nS = S.num_sheets, nT = sgrad_texel_base(S);
     for (int k = threadIdx.x; k < nscal; k += blockDim.x) {
         float v = 0.0f;
         for (int c = 0; c < copies; ++c) v += sg[k * copies + ((c + k) & (copies - 1))];
@@ -1043,7 +1043,8 @@ __device__ __forceinline__ void sgrad_flush(const DScene& S, const DGrads& G, co
         int off;
         if (k < nI) { base = G.ior; off = k; }
         else if (k < nI + nS) { base = G.sheet; off = k - nI; }
-        else { base = G.le; off = k - nI - nS; }
+        else if (k < nT) { base = G.le; off = k - nI - nS; }
+        else { base = G.tex; off = k - nT; }
         if (base) atomicAdd(base + off, v);
     }
 }
@@ -1052,6 +1053,26 @@ __device__ __forceinline__ void sgrad_flush(const DScene& S, const DGrads& G, co
 // UNROLL = false keeps the sixteen sites as a loop: the wavefront replay kernels are bound by
 // instruction fetch, and sixteen inlined copies of the grouping code would enlarge them.
 // The megakernels are bound by their thread-local cache and run faster unrolled.
+// The same sums into the block's accumulators (DScene::tex_shared): no grouping, each lane adds
+// to its own copy.
+template <int NC>
+__device__ __forceinline__ void scatter_taps_shared(const DScene& S, float* sg, const Taps& tp0, const float* vals,
+                                                    int ch) {
+    Taps tp = tp0;
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < k; ++j)
+            if (tp.w[k] != 0.0f && tp.idx[k] == tp.idx[j]) { tp.w[j] += tp.w[k]; tp.w[k] = 0.0f; }
+    const int base = sgrad_texel_base(S);
+#pragma unroll 1
+    for (int c = 0; c < NC; ++c)
+#pragma unroll 1
+        for (int k = 0; k < 4; ++k) {
+            const float v = vals[c] * tp.w[k];
+            if (v != 0.0f) sgrad_add(S, sg, base + (int)tp.idx[k] + min(c, ch - 1), v);
+        }
+}
 template <int NC, bool UNROLL>
 __device__ __forceinline__ void scatter_taps(float* g, const Taps& tp0, const float* vals, int ch, bool per_lane) {
     // taps on the same texel (a texture one or two texels wide, wrapped) are merged first,
@@ -1311,13 +1332,15 @@ __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, 
     if (G->tex) {
         if ((m.type == DPPT_MAT_CONDUCTOR_GGX || m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.rough_tex].pad) {
             Taps tp = tex_taps(S->tex[m.rough_tex], vc.tu, vc.tv);
-            scatter_taps<1, UNROLL>(G->tex, tp, &g_slot0, 1, S->scatter_lane != 0);
+            if (S->tex_shared) scatter_taps_shared<1>(*S, sgrad, tp, &g_slot0, 1);
+            else scatter_taps<1, UNROLL>(G->tex, tp, &g_slot0, 1, S->scatter_lane != 0);
         }
         if (m.albedo_tex >= 0 && (m.type == DPPT_MAT_DIFFUSE || m.type == DPPT_MAT_CONDUCTOR_GGX ||
                                   m.type == DPPT_MAT_PLASTIC_GGX) && S->tex[m.albedo_tex].pad) {
             DTex t = S->tex[m.albedo_tex];
             Taps tp = tex_taps(t, vc.tu, vc.tv);
-            scatter_taps<3, UNROLL>(G->tex, tp, g_alb, t.ch, S->scatter_lane != 0);
+            if (S->tex_shared) scatter_taps_shared<3>(*S, sgrad, tp, g_alb, t.ch);
+            else scatter_taps<3, UNROLL>(G->tex, tp, g_alb, t.ch, S->scatter_lane != 0);
         }
     }
     if constexpr (NM) {
