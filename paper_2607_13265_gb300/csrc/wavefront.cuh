@@ -224,8 +224,9 @@ struct SweepCache {
 // the backward fold the suffix L_v (components 0-11; L_0 too, although the replay never reads
 // it, and zeros beside a miss's hit, so that every written 32-byte sector is written whole:
 // a partly written sector costs the memory a read of it).  It then stores the path's raw Stokes value and
-// starts the replay (the adjoint row of its pixel, the walk begun again, the path in the bin
-// of its first vertex); the replay's iterations run as in the wavefront schedule.
+// starts the replay: the adjoint row of its pixel, the path in the bin of its first vertex,
+// and the walk as begun, which went to the path record before the walk.  The replay's
+// iterations run as in the wavefront schedule.
 template <int MAXD, bool NM>
 __global__ void __launch_bounds__(256, DPPT_MIN_BLOCKS_PRIMAL)
 k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, const __grid_constant__ WaveTable wt,
@@ -240,6 +241,7 @@ k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
     const unsigned long long pid = (unsigned long long)(sg.pix0 * J.spp + (q - sg.q0));
     Walk w;
     walk_begin(S, J, pid, (long long)(pid / J.spp), w);
+    put_walk(W.path + q, w);      // the replay's start: the same walk, begun again
     PathVis<LocalCache<MAXD>, -1, NM> vis;
     vis.S = &S; vis.P = &P; vis.G = nullptr; vis.sgrad = nullptr;
     vis.C.cE = cE; vis.C.cW = cW;
@@ -301,8 +303,6 @@ k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
         rot_apply_row(Rc, av);
         W.path[q].arow[c] = make_float4(av[0], av[1], av[2], av[3]);
     }
-    walk_begin(S, J, pid, pix, w);
-    put_walk(W.path + q, w);
     W.path[q].meta = WfMeta{(unsigned)pid, (unsigned)(pid >> 32), sg.job, 1 | (vis.n << 8)};
     bin_append(L, replay_bin_of(W, q, 0), q);
 }
