@@ -1128,28 +1128,41 @@ __device__ __forceinline__ void unpack_w(const float o[19], Compact<float>& W) {
     }
 }
 
+// The megakernels' thread-local cache: per vertex E_v in three float4s and W_v in five (19
+// floats and a pad), so that a vertex moves with eight vector accesses.
 template <int MAXD>
 struct LocalCache {
-    float (*cE)[12];
-    float (*cW)[19];
+    float4 (*cE)[3];
+    float4 (*cW)[5];
     static constexpr int cap = MAXD;
     static constexpr bool kUnrollScatter = true;
     __device__ __forceinline__ void put(int v, const float E[12], const Compact<float>& W) const {
         float o[20];
         pack_w(W, o);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) cE[v][k] = E[k];
+        for (int k = 0; k < 3; ++k) cE[v][k] = make_float4(E[4 * k], E[4 * k + 1], E[4 * k + 2], E[4 * k + 3]);
 #pragma unroll
-        for (int k = 0; k < 19; ++k) cW[v][k] = o[k];
+        for (int k = 0; k < 5; ++k) cW[v][k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
     }
-    __device__ __forceinline__ void get_w(int v, Compact<float>& W) const { unpack_w(cW[v], W); }
+    __device__ __forceinline__ void get_w(int v, Compact<float>& W) const {
+        float o[20];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const float4 t = cW[v][k];
+            o[4 * k] = t.x; o[4 * k + 1] = t.y; o[4 * k + 2] = t.z; o[4 * k + 3] = t.w;
+        }
+        unpack_w(o, W);
+    }
     __device__ __forceinline__ void get_e(int v, float e[12]) const {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) e[k] = cE[v][k];
+        for (int k = 0; k < 3; ++k) {
+            const float4 t = cE[v][k];
+            e[4 * k] = t.x; e[4 * k + 1] = t.y; e[4 * k + 2] = t.z; e[4 * k + 3] = t.w;
+        }
     }
     __device__ __forceinline__ void put_e(int v, const float e[12]) const {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) cE[v][k] = e[k];
+        for (int k = 0; k < 3; ++k) cE[v][k] = make_float4(e[4 * k], e[4 * k + 1], e[4 * k + 2], e[4 * k + 3]);
     }
 };
 
@@ -1470,8 +1483,8 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
     extern __shared__ float sgrad[];
     __shared__ long long s_chunk;
     if (MODE == 1) sgrad_zero(S, sgrad);
-    float cE[MAXD][12];
-    float cW[MAXD][19];
+    float4 cE[MAXD][3];
+    float4 cW[MAXD][5];
     WorkCount wc = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     unsigned long long paths_done = 0;
     long long chunk = blockIdx.x;

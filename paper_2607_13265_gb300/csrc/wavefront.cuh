@@ -231,8 +231,8 @@ template <int MAXD, bool NM>
 __global__ void __launch_bounds__(256, DPPT_MIN_BLOCKS_PRIMAL)
 k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, const __grid_constant__ WaveTable wt,
            WfState W, WfLists L, unsigned* status) {
-    float cE[MAXD][12];
-    float cW[MAXD][19];
+    float4 cE[MAXD][3];
+    float4 cW[MAXD][5];
     const long long qq = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (qq >= wt.nq) return;
     const int q = (int)qq;
