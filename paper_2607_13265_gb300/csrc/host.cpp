@@ -24,6 +24,7 @@ struct dppt_ctx {
     dppt_launch launch{DPPT_SCHED_GRID, 128, 0, DPPT_SCHED_GRID, 128, 0, DPPT_SCATTER_WARP};
     dppt_replay replay{DPPT_REPLAY_CACHED, 1, 0.0f, 0.0f, 0.0f};
     StageLog log;
+    SideStream side{nullptr, nullptr, nullptr};   // the replay's second stream (wavefront.cu)
 };
 
 struct dppt_scene {
@@ -504,6 +505,16 @@ dppt_status dppt_create(dppt_ctx** out, int device) {
     }
     cudaMemset(c->d_status, 0, sizeof(unsigned));
     cudaMemset(c->d_counter, 0, sizeof(unsigned long long));
+    if (cudaStreamCreateWithFlags(&c->side.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->side.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->side.join, cudaEventDisableTiming) != cudaSuccess) {
+        if (c->side.fork) cudaEventDestroy(c->side.fork);
+        if (c->side.st) cudaStreamDestroy(c->side.st);
+        cudaFree(c->d_status);
+        cudaFree(c->d_counter);
+        delete c;
+        return DPPT_ERR_CUDA;
+    }
     *out = c;
     return DPPT_OK;
 }
@@ -515,6 +526,9 @@ void dppt_destroy(dppt_ctx* ctx) {
     cudaFree(ctx->ws);
     cudaFree(ctx->d_status);
     cudaFree(ctx->d_counter);
+    cudaEventDestroy(ctx->side.fork);
+    cudaEventDestroy(ctx->side.join);
+    cudaStreamDestroy(ctx->side.st);
     delete ctx;
 }
 
@@ -859,7 +873,7 @@ dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* s, const dppt_jo
         }
         if (wave) {
             cudaError_t e = run_wavefront(0, s->d, P, G, T, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
-                                          shape.block, hy, 0, ctx->d_status, cs, &ctx->log);
+                                          shape.block, hy, 0, ctx->d_status, cs, &ctx->side, &ctx->log);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront primal");
             continue;
         }
@@ -975,7 +989,7 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
         if (wave) {
             const int sweep = shape.schedule == DPPT_SCHED_SWEEP ? depth_bucket(cap) : 0;
             cudaError_t e = run_wavefront(1, Sd, P, G, T, static_cast<char*>(ctx->ws) + ws_jobs, Q, cap,
-                                          shape.block, hy, sweep, ctx->d_status, cs, &ctx->log);
+                                          shape.block, hy, sweep, ctx->d_status, cs, &ctx->side, &ctx->log);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "wavefront adjoint");
             continue;
         }

@@ -206,10 +206,14 @@ DPPT_DECLARE_HYBRID(16)
 // forward sweep runs in the megakernel of cache-depth bucket `sweep` instead of the stage
 // kernels.
 struct WfHybrid { int k; float gamma, eps; };   // k = 1: the fully cached replay
+// A second stream of the context with two events: a replay iteration runs its small bins on
+// it beside the diffuse bin (forked from and joined back into the launching stream, so the
+// launches stay one capturable sequence on that stream)
+struct SideStream { cudaStream_t st; cudaEvent_t fork, join; };
 size_t wavefront_bytes(long long Q, int cap, int k);
 cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T,
                           void* ws, long long Q, int cap, int block, const WfHybrid& hy, int sweep, unsigned* status,
-                          cudaStream_t st, StageLog* log);
+                          cudaStream_t st, const SideStream* side, StageLog* log);
 
 // read-only views of the opaque context and scene (host.cpp), for entry points
 // implemented in other translation units

@@ -409,20 +409,33 @@ static void launch_replay_bin(const ReplayArgs& a) {
     else k_wf_finish<1, 1, false, MT, MT><<<a.grid, 128, a.smem, a.st>>>(a.S, a.P, a.G, a.T, a.W, a.L);
 }
 // One replay iteration: a kernel per binned material type present, then the other bin when
-// the scene has a type without a kernel of its own.
-static void replay_iteration(const ReplayArgs& ra, unsigned types, StageLog* log) {
+// the scene has a type without a kernel of its own.  The bins hold disjoint paths, so with a
+// side stream every bin but the diffuse one runs on it, beside the diffuse kernel: the small
+// bins are latency-bound on few paths and would otherwise run after it.
+static void replay_iteration(const ReplayArgs& ra, unsigned types, const SideStream* side, StageLog* log) {
     const bool other = (types & ~kBinnedTypes) != 0;
     const int tok = log->begin(kStageWfReplay, ra.st, (other ? 1 : 0) + __builtin_popcount(types & kBinnedTypes));
-    if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) launch_replay_bin<DPPT_MAT_CONDUCTOR_GGX>(ra);
-    if (types & (1u << DPPT_MAT_PLASTIC_GGX)) launch_replay_bin<DPPT_MAT_PLASTIC_GGX>(ra);
+    const bool fork = side && (types & (1u << DPPT_MAT_DIFFUSE)) && ((types & ~(1u << DPPT_MAT_DIFFUSE)) != 0);
+    ReplayArgs rs = ra;
+    if (fork) {
+        cudaEventRecord(side->fork, ra.st);
+        cudaStreamWaitEvent(side->st, side->fork, 0);
+        rs.st = side->st;
+    }
     if (types & (1u << DPPT_MAT_DIFFUSE)) launch_replay_bin<DPPT_MAT_DIFFUSE>(ra);
-    if (types & (1u << DPPT_MAT_SMOOTH_DIELECTRIC)) launch_replay_bin<DPPT_MAT_SMOOTH_DIELECTRIC>(ra);
-    if (types & (1u << DPPT_MAT_POLARIZER_SHEET)) launch_replay_bin<DPPT_MAT_POLARIZER_SHEET>(ra);
-    if (types & (1u << DPPT_MAT_RETARDER_SHEET)) launch_replay_bin<DPPT_MAT_RETARDER_SHEET>(ra);
-    if (types & (1u << DPPT_MAT_EMITTER)) launch_replay_bin<DPPT_MAT_EMITTER>(ra);
+    if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) launch_replay_bin<DPPT_MAT_CONDUCTOR_GGX>(rs);
+    if (types & (1u << DPPT_MAT_PLASTIC_GGX)) launch_replay_bin<DPPT_MAT_PLASTIC_GGX>(rs);
+    if (types & (1u << DPPT_MAT_SMOOTH_DIELECTRIC)) launch_replay_bin<DPPT_MAT_SMOOTH_DIELECTRIC>(rs);
+    if (types & (1u << DPPT_MAT_POLARIZER_SHEET)) launch_replay_bin<DPPT_MAT_POLARIZER_SHEET>(rs);
+    if (types & (1u << DPPT_MAT_RETARDER_SHEET)) launch_replay_bin<DPPT_MAT_RETARDER_SHEET>(rs);
+    if (types & (1u << DPPT_MAT_EMITTER)) launch_replay_bin<DPPT_MAT_EMITTER>(rs);
     if (other) {
-        if (ra.nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<ra.grid, 128, ra.smem, ra.st>>>(ra.S, ra.P, ra.G, ra.T, ra.W, ra.L);
-        else k_wf_finish<1, 1, false, -1, kBinOther><<<ra.grid, 128, ra.smem, ra.st>>>(ra.S, ra.P, ra.G, ra.T, ra.W, ra.L);
+        if (rs.nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<rs.grid, 128, rs.smem, rs.st>>>(rs.S, rs.P, rs.G, rs.T, rs.W, rs.L);
+        else k_wf_finish<1, 1, false, -1, kBinOther><<<rs.grid, 128, rs.smem, rs.st>>>(rs.S, rs.P, rs.G, rs.T, rs.W, rs.L);
+    }
+    if (fork) {
+        cudaEventRecord(side->join, side->st);
+        cudaStreamWaitEvent(ra.st, side->join, 0);
     }
     log->end(tok, ra.st);
 }
@@ -475,7 +488,7 @@ static std::vector<WaveTable> plan_waves(const JobTable& T, long long Q) {
 // paths, several jobs sharing a wave, and writes each job's per-pixel raw image to J.raw.
 cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGrads& G, const JobTable& T,
                           void* ws, long long Q, int cap, int block, const WfHybrid& hy, int sweep, unsigned* status,
-                          cudaStream_t st, StageLog* log) {
+                          cudaStream_t st, const SideStream* side, StageLog* log) {
     char* p = static_cast<char*>(ws);
     WfState W;
     W.path = reinterpret_cast<WfPath*>(p); p += align_up(sizeof(WfPath) * Q);
@@ -545,7 +558,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
             for (int it = 1; it <= wt.depth; ++it) {
                 const WfLists& L = (it & 1) ? B : A;
                 if ((e = cudaMemsetAsync(L.nxt, 0, sizeof(int) * 16, st)) != cudaSuccess) return e;
-                replay_iteration(ReplayArgs{S, P, G, T, W, L, fgrid, smem, st, nmaps}, types, log);
+                replay_iteration(ReplayArgs{S, P, G, T, W, L, fgrid, smem, st, nmaps}, types, side, log);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
             }
             tok = log->begin(kStageWfPixels, st);
@@ -609,7 +622,7 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                 if ((e = launch_wf_hybrid(1, hy.k, S, P, G, T, W, L, H, fgrid, smem, st)) != cudaSuccess) return e;
                 log->end(tok, st);
             } else if (mode == 1 && it > 0) {
-                replay_iteration(ReplayArgs{S, P, G, T, W, L, fgrid, smem, st, nmaps}, types, log);
+                replay_iteration(ReplayArgs{S, P, G, T, W, L, fgrid, smem, st, nmaps}, types, side, log);
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
