@@ -410,28 +410,35 @@ static void launch_replay_bin(const ReplayArgs& a) {
 }
 // One replay iteration: a kernel per binned material type present, then the other bin when
 // the scene has a type without a kernel of its own.  The bins hold disjoint paths, so with a
-// side stream every bin but the diffuse one runs on it, beside the diffuse kernel: the small
-// bins are latency-bound on few paths and would otherwise run after it.
+// side stream the first bin runs on the launching stream and every other bin on the side
+// stream beside it: the small bins are latency-bound on few paths and would otherwise run
+// one after another.
 static void replay_iteration(const ReplayArgs& ra, unsigned types, const SideStream* side, StageLog* log) {
     const bool other = (types & ~kBinnedTypes) != 0;
-    const int tok = log->begin(kStageWfReplay, ra.st, (other ? 1 : 0) + __builtin_popcount(types & kBinnedTypes));
-    const bool fork = side && (types & (1u << DPPT_MAT_DIFFUSE)) && ((types & ~(1u << DPPT_MAT_DIFFUSE)) != 0);
+    const int nbins = (other ? 1 : 0) + __builtin_popcount(types & kBinnedTypes);
+    const int tok = log->begin(kStageWfReplay, ra.st, nbins);
+    const bool fork = side && nbins > 1;
     ReplayArgs rs = ra;
     if (fork) {
         cudaEventRecord(side->fork, ra.st);
         cudaStreamWaitEvent(side->st, side->fork, 0);
         rs.st = side->st;
     }
-    if (types & (1u << DPPT_MAT_DIFFUSE)) launch_replay_bin<DPPT_MAT_DIFFUSE>(ra);
-    if (types & (1u << DPPT_MAT_CONDUCTOR_GGX)) launch_replay_bin<DPPT_MAT_CONDUCTOR_GGX>(rs);
-    if (types & (1u << DPPT_MAT_PLASTIC_GGX)) launch_replay_bin<DPPT_MAT_PLASTIC_GGX>(rs);
-    if (types & (1u << DPPT_MAT_SMOOTH_DIELECTRIC)) launch_replay_bin<DPPT_MAT_SMOOTH_DIELECTRIC>(rs);
-    if (types & (1u << DPPT_MAT_POLARIZER_SHEET)) launch_replay_bin<DPPT_MAT_POLARIZER_SHEET>(rs);
-    if (types & (1u << DPPT_MAT_RETARDER_SHEET)) launch_replay_bin<DPPT_MAT_RETARDER_SHEET>(rs);
-    if (types & (1u << DPPT_MAT_EMITTER)) launch_replay_bin<DPPT_MAT_EMITTER>(rs);
+    int k = 0;   // bins launched so far: the first on the launching stream
+    auto bin = [&](int t, void (*launch)(const ReplayArgs&)) {
+        if (types & (1u << t)) launch(k++ == 0 ? ra : rs);
+    };
+    bin(DPPT_MAT_DIFFUSE, launch_replay_bin<DPPT_MAT_DIFFUSE>);
+    bin(DPPT_MAT_CONDUCTOR_GGX, launch_replay_bin<DPPT_MAT_CONDUCTOR_GGX>);
+    bin(DPPT_MAT_PLASTIC_GGX, launch_replay_bin<DPPT_MAT_PLASTIC_GGX>);
+    bin(DPPT_MAT_SMOOTH_DIELECTRIC, launch_replay_bin<DPPT_MAT_SMOOTH_DIELECTRIC>);
+    bin(DPPT_MAT_POLARIZER_SHEET, launch_replay_bin<DPPT_MAT_POLARIZER_SHEET>);
+    bin(DPPT_MAT_RETARDER_SHEET, launch_replay_bin<DPPT_MAT_RETARDER_SHEET>);
+    bin(DPPT_MAT_EMITTER, launch_replay_bin<DPPT_MAT_EMITTER>);
     if (other) {
-        if (rs.nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<rs.grid, 128, rs.smem, rs.st>>>(rs.S, rs.P, rs.G, rs.T, rs.W, rs.L);
-        else k_wf_finish<1, 1, false, -1, kBinOther><<<rs.grid, 128, rs.smem, rs.st>>>(rs.S, rs.P, rs.G, rs.T, rs.W, rs.L);
+        const ReplayArgs& ro = k++ == 0 ? ra : rs;
+        if (ro.nmaps) k_wf_finish<1, 1, true, -1, kBinOther><<<ro.grid, 128, ro.smem, ro.st>>>(ro.S, ro.P, ro.G, ro.T, ro.W, ro.L);
+        else k_wf_finish<1, 1, false, -1, kBinOther><<<ro.grid, 128, ro.smem, ro.st>>>(ro.S, ro.P, ro.G, ro.T, ro.W, ro.L);
     }
     if (fork) {
         cudaEventRecord(side->join, side->st);
