@@ -583,6 +583,12 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
             // lists, counts and bins alternate between two buffers: the next ones of an
             // iteration are the live ones of the following iteration
             const WfLists& L = (it & 1) ? B : A;
+            // While paths still run their cache pass, an iteration's replay (the paths that
+            // finished theirs) runs on the side stream beside its shadow rays and cache pass:
+            // the two touch disjoint paths and both append to the next iteration's bins with
+            // atomics.  It starts after the iteration's extend launch, which zeroes the counts it
+            // appends to, and joins before the next extend, which zeroes the counts it reads.
+            const bool overlap = side && mode == 1 && !hyb && it > 0 && it < wt.depth;
             // a path's cache pass ends by iteration depth - 1 (one vertex per iteration), and no
             // path replays before iteration 1: the launches with nothing to do are skipped
             if (it >= wt.depth) {
@@ -609,6 +615,11 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                 else k_wf_shade<false><<<grid, block, 0, st>>>(S, P, T, W, L, mode == 1);
                 log->end(tok, st);
 #endif
+                if (overlap) {
+                    cudaEventRecord(side->fork, st);
+                    cudaStreamWaitEvent(side->st, side->fork, 0);
+                    replay_iteration(ReplayArgs{S, P, G, T, W, L, fgrid, smem, side->st, nmaps}, types, nullptr, log);
+                }
                 tok = log->begin(kStageWfShadow, st);
                 k_wf_shadow<<<grid, block, tsm, st>>>(S, W, L, status);
                 log->end(tok, st);
@@ -623,12 +634,16 @@ cudaError_t run_wavefront(int mode, const DScene& S, const DParams& P, const DGr
                     else k_wf_finish<1, 0, false><<<fgrid, 128, 0, st>>>(S, P, G, T, W, L);
                 }
                 log->end(tok, st);
+                if (overlap) {
+                    cudaEventRecord(side->join, side->st);
+                    cudaStreamWaitEvent(st, side->join, 0);
+                }
             }
             if (mode == 1 && it > 0 && hyb) {
                 tok = log->begin(kStageWfReplay, st);
                 if ((e = launch_wf_hybrid(1, hy.k, S, P, G, T, W, L, H, fgrid, smem, st)) != cudaSuccess) return e;
                 log->end(tok, st);
-            } else if (mode == 1 && it > 0) {
+            } else if (mode == 1 && it > 0 && !overlap) {
                 replay_iteration(ReplayArgs{S, P, G, T, W, L, fgrid, smem, st, nmaps}, types, side, log);
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
