@@ -179,7 +179,13 @@ typedef struct {
 } dppt_launch;
 enum { DPPT_SCATTER_WARP = 0, DPPT_SCATTER_LANE = 1 };
 
-/* Create a context on CUDA device `device` (made current for the call). */
+/* Create a context on CUDA device `device` (made current for the call).  The
+ * context owns a second stream and two events: the adjoint of the wavefront
+ * and sweep schedules runs some of its replay kernels on that stream, beside the
+ * kernels on the caller's stream.  That work is forked from and joined back into
+ * the caller's stream with events before the call's last launch, so every call
+ * stays ordered on the caller's stream and can be captured into a CUDA graph.
+ * Errors: INVALID_ARG for a bad device, OUT_OF_MEMORY, CUDA. */
 dppt_status dppt_create(dppt_ctx** out, int device);
 void dppt_destroy(dppt_ctx* ctx);
 /* Message of the last failed call on this context; owned by the context. */
