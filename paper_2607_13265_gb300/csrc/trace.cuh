@@ -636,12 +636,32 @@ __device__ __forceinline__ Rot<float> emitter_rot(const DLight& L, f3 p) {
     return rot_between(p, xe, onb_t1(p));
 }
 
+// Material-type specializations of a kernel: MT >= 0 is one type, -1 any type, and
+// type_mask_mt(mask) a set of types (kernels for scenes whose materials all have a type of
+// the set; the host chooses them from DScene::mat_types).
+constexpr int type_mask_mt(unsigned mask) { return -2 - (int)mask; }
+// diffuse surfaces, smooth dielectrics and emitters: a Cornell box
+constexpr unsigned kDiffuseDielectricTypes =
+    (1u << DPPT_MAT_DIFFUSE) | (1u << DPPT_MAT_SMOOTH_DIELECTRIC) | (1u << DPPT_MAT_EMITTER);
+// The type t written as a choice among the types of TM: every comparison of it with a type
+// outside TM then folds to false at compile time.
+template <unsigned TM>
+__device__ __forceinline__ int typed_as(int t) {
+    constexpr int hi = 31 - __builtin_clz(TM);
+    int r = hi;
+#pragma unroll
+    for (int k = 0; k < hi; ++k)
+        if ((TM >> k) & 1u) r = t == k ? k : r;
+    return r;
+}
 // The material of a vertex; MT >= 0 states its type at compile time (kernels specialized
-// to one material type), so that the other types' code folds away.
+// to one material type) and MT < -1 the set its type belongs to, so that the other types'
+// code folds away.
 template <int MT>
 __device__ __forceinline__ DMat load_mat(const DScene& S, int mat) {
     DMat m = S.mats[mat];
-    if (MT >= 0) m.type = MT;
+    if constexpr (MT >= 0) m.type = MT;
+    else if constexpr (MT < -1) m.type = typed_as<(unsigned)(-MT - 2)>(m.type);
     return m;
 }
 
@@ -944,7 +964,7 @@ __device__ __forceinline__ void walk_shade(const DScene& S, const DParams& P, co
 
 // Completes the vertex once the visibility of its light sample is known;
 // returns true when the path continues.
-template <class Vis>
+template <int MT = -1, class Vis>
 __device__ __forceinline__ bool walk_finish(const DScene& S, const DParams& P, Walk& w, VCtx& vc,
                                             const NeePending& ne, bool visible, const Shade& sh, Vis& vis) {
     unsigned neeflag = 2u;
@@ -954,7 +974,7 @@ __device__ __forceinline__ bool walk_finish(const DScene& S, const DParams& P, W
         if (ne.state != 2) {
             neeflag = 0u;
             if (ne.state == 1 && visible) {
-                const DMat m = S.mats[vc.mat];
+                const DMat m = load_mat<MT>(S, vc.mat);
                 float pl = ne.pl;
                 float pb = bsdf_pdf(S, P, m, vc, ne.wl);
                 float wm = pl * pl / (pl * pl + pb * pb);
@@ -982,7 +1002,7 @@ __device__ __forceinline__ bool walk_finish(const DScene& S, const DParams& P, W
 
 // Traces vertex w.v of the path and calls vis(vc) for it.  Returns true when
 // the path continues with vertex w.v + 1.
-template <class Vis, bool COUNT, bool NM = true>
+template <class Vis, bool COUNT, bool NM = true, int MT = -1>
 __device__ __forceinline__ bool walk_step(const DScene& S, const DParams& P, const DJob& J, unsigned long long pid,
                                           Walk& w, Vis& vis, unsigned* status, WorkCount* wc) {
     HitRec h;
@@ -991,10 +1011,10 @@ __device__ __forceinline__ bool walk_step(const DScene& S, const DParams& P, con
     VCtx vc;
     NeePending ne;
     Shade sh;
-    walk_shade<NM>(S, P, J, pid, w, h, vc, ne, sh);
+    walk_shade<NM, MT>(S, P, J, pid, w, h, vc, ne, sh);
     bool visible = false;
     if (ne.state == 1) visible = !trace_any<COUNT>(S, ne.o2, ne.dir, ne.tmax, status, wc);
-    return walk_finish(S, P, w, vc, ne, visible, sh, vis);
+    return walk_finish<MT>(S, P, w, vc, ne, visible, sh, vis);
 }
 
 // Gradient scatter of texel derivatives, chosen per launch (DScene::scatter_lane): either
@@ -1476,7 +1496,7 @@ __device__ __forceinline__ void pixel_reduce(const DJob& J, float* dst, long lon
 // NM = false compiles the normal-map code out: the adjoint is launched with it only for
 // scenes that have normal maps (their second dual evaluation would otherwise raise the
 // register pressure of every adjoint).
-template <int MAXD, int MODE, bool COUNT, bool NM = true>
+template <int MAXD, int MODE, bool COUNT, bool NM = true, int MT = -1>
 __global__ void __launch_bounds__(256, MODE == 1 ? DPPT_MIN_BLOCKS_ADJOINT : DPPT_MIN_BLOCKS_PRIMAL)
 k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__ JobTable T,
         unsigned long long* counter, unsigned* status, int persistent, unsigned long long* work) {
@@ -1504,7 +1524,7 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
         for (int k = 0; k < 12; ++k) raw[k] = 0.0f;
         if (active) {
             const long long pix = p / J.spp;
-            PathVis<LocalCache<MAXD>, -1, NM> vis;
+            PathVis<LocalCache<MAXD>, MT, NM> vis;
             vis.S = &S; vis.P = &P; vis.G = &G; vis.sgrad = sgrad;
             vis.C.cE = cE; vis.C.cW = cW;
             vis.n = 0; vis.i = 0; vis.has_last = false; vis.adjoint = MODE == 1;
@@ -1515,7 +1535,7 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
             for (int phase = 0; phase < passes; ++phase) {
                 vis.phase = phase;
                 walk_begin(S, J, (unsigned long long)p, pix, w);
-                while (walk_step<PathVis<LocalCache<MAXD>, -1, NM>, COUNT, NM>(S, P, J, (unsigned long long)p, w, vis,
+                while (walk_step<PathVis<LocalCache<MAXD>, MT, NM>, COUNT, NM, MT>(S, P, J, (unsigned long long)p, w, vis,
                                                                                status, &wc)) {
                 }
                 if (phase == 0) {
@@ -1580,6 +1600,9 @@ k_trace(const DScene S, const DParams P, const DGrads G, const __grid_constant__
         if (mode == 0) {                                                                                         \
             if (S.tri_tan)                                                                                       \
                 k_trace<B, 0, false, true><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, nullptr); \
+            else if ((S.mat_types & ~kDiffuseDielectricTypes) == 0)                                              \
+                k_trace<B, 0, false, false, type_mask_mt(kDiffuseDielectricTypes)>                              \
+                    <<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, nullptr);                    \
             else                                                                                                 \
                 k_trace<B, 0, false, false><<<(int)g, L.block, 0, st>>>(S, P, G, T, counter, status, pers, nullptr);\
         } else if (mode == 1) {                                                                                  \

@@ -227,7 +227,7 @@ struct SweepCache {
 // starts the replay: the adjoint row of its pixel, the path in the bin of its first vertex,
 // and the walk as begun, which went to the path record before the walk.  The replay's
 // iterations run as in the wavefront schedule.
-template <int MAXD, bool NM>
+template <int MAXD, bool NM, int MT = -1>
 __global__ void __launch_bounds__(256, DPPT_MIN_BLOCKS_PRIMAL)
 k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, const __grid_constant__ WaveTable wt,
            WfState W, WfLists L, unsigned* status) {
@@ -242,7 +242,7 @@ k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
     Walk w;
     walk_begin(S, J, pid, (long long)(pid / J.spp), w);
     put_walk(W.path + q, w);      // the replay's start: the same walk, begun again
-    PathVis<LocalCache<MAXD>, -1, NM> vis;
+    PathVis<LocalCache<MAXD>, MT, NM> vis;
     vis.S = &S; vis.P = &P; vis.G = nullptr; vis.sgrad = nullptr;
     vis.C.cE = cE; vis.C.cW = cW;
     vis.n = 0; vis.i = 0; vis.phase = 0; vis.has_last = false; vis.adjoint = true;
@@ -261,13 +261,13 @@ k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
         VCtx vc;
         NeePending ne;
         Shade sh;
-        walk_shade<NM>(S, P, J, pid, w, h, vc, ne, sh);
+        walk_shade<NM, MT>(S, P, J, pid, w, h, vc, ne, sh);
         bool visible = false;
         if (ne.state == 1) visible = !trace_any<false>(S, ne.o2, ne.dir, ne.tmax, status, nullptr);
         // stored before walk_finish, so that nothing of it stays live through the vertex's
         // evaluation (the thread-local cache writes no record)
         W.vis_plane[(long long)(w.v - 1) * W.Q + q] = replay_bin(S, vc.mat) << 1 | (visible ? 1 : 0);
-        if (!walk_finish(S, P, w, vc, ne, visible, sh, vis)) break;
+        if (!walk_finish<MT>(S, P, w, vc, ne, visible, sh, vis)) break;
     }
     SweepCache<MAXD> C;
     C.loc = vis.C;
@@ -315,6 +315,9 @@ k_wf_sweep(const DScene S, const DParams P, const __grid_constant__ JobTable T, 
         const long long g = (wt.nq + block - 1) / block;                                                         \
         if (g <= 0) return cudaSuccess;                                                                          \
         if (nmaps) k_wf_sweep<B, true><<<(int)g, block, 0, st>>>(S, P, T, wt, W, L, status);                       \
+        else if ((S.mat_types & ~kDiffuseDielectricTypes) == 0)                                                  \
+            k_wf_sweep<B, false, type_mask_mt(kDiffuseDielectricTypes)><<<(int)g, block, 0, st>>>(S, P, T, wt, W, L, \
+                                                                                                  status);       \
         else k_wf_sweep<B, false><<<(int)g, block, 0, st>>>(S, P, T, wt, W, L, status);                           \
         return cudaGetLastError();                                                                               \
     }                                                                                                            \
