@@ -76,12 +76,12 @@ B_CACHE_PATH_PRIMAL, B_CACHE_PATH_ADJOINT = 48, 216
 # DRAM traffic per launch (bytes; dram__bytes_read.sum + dram__bytes_write.sum, cold caches)
 # keyed by (workload, stage), for the stages the benchmark's launch shapes run: captured on the
 # views workload with every image side halved (3,779,744 paths per pass, one wave) and scaled
-# by the paths a full-size launch processes: the primal megakernel 441 B per path (one launch
+# by the paths a full-size launch processes: the primal megakernel 466 B per path (one launch
 # of 15,125,952 paths per step), the forward sweep 2,203 B per path (four waves, 3,781,488
 # paths per launch on average).  Absent for a kernel changed since its capture.
 DRAM_BYTES_PER_LAUNCH = {
-    ("cornell_views8x64angles_16spp_depth8", "primal"): 6.668e9,
-    ("cornell_views8x64angles_16spp_depth8", "wf_sweep"): 8.331e9,
+    ("cornell_views8x64angles_16spp_depth8", "primal"): 7.052e9,
+    ("cornell_views8x64angles_16spp_depth8", "wf_sweep"): 8.329e9,
 }
 
 # floats per vertex of the wavefront cache: E_v 12, compact W_v 19, visibility 1, the hit 4
