@@ -1076,7 +1076,7 @@ static dppt_status adjoint_impl(dppt_ctx* ctx, const dppt_scene* s, const dppt_j
     return DPPT_OK;
 }
 
-static dppt_status check_l2(dppt_ctx* ctx, const dppt_job* jobs, int32_t njobs, const float* raw,
+static dppt_status check_l2(dppt_ctx* ctx, int32_t njobs, const float* raw,
                             const int64_t* raw_offsets, const float* target) {
     if (njobs > 0 && (!raw || !raw_offsets || !target))
         return fail(ctx, DPPT_ERR_INVALID_ARG, "raw, raw_offsets and target must not be null");
@@ -1098,7 +1098,7 @@ dppt_status dppt_render_adjoint_l2(dppt_ctx* ctx, const dppt_scene* s, const dpp
                                    const dppt_params* params, const float* raw, const int64_t* raw_offsets,
                                    const float* target, float scale, const dppt_grads* grads, void* stream) {
     if (!ctx) return DPPT_ERR_INVALID_ARG;
-    dppt_status st = check_l2(ctx, jobs, njobs, raw, raw_offsets, target);
+    dppt_status st = check_l2(ctx, njobs, raw, raw_offsets, target);
     if (st != DPPT_OK) return st;
     const L2Spec l2{raw, raw_offsets, target, scale};
     return adjoint_impl(ctx, s, jobs, njobs, params, nullptr, &l2, grads, stream);
@@ -1113,7 +1113,7 @@ dppt_status dppt_loss_l2(dppt_ctx* ctx, const dppt_scene* s, const dppt_job* job
     size_t ws = 0;
     dppt_status st = check_jobs(ctx, s, jobs, njobs, params, false, plan, ws);
     if (st != DPPT_OK) return st;
-    if ((st = check_l2(ctx, jobs, njobs, raw, raw_offsets, target)) != DPPT_OK) return st;
+    if ((st = check_l2(ctx, njobs, raw, raw_offsets, target)) != DPPT_OK) return st;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), cs);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");

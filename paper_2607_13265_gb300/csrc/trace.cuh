@@ -1324,7 +1324,6 @@ __device__ __forceinline__ void replay_vjp(const DScene& S_, const DParams& P_, 
                                            const VCtx& vc, const Compact<DT>& W, const Compact<DT>& f,
                                            const float Ln[3][4], float a[3][4]) {
     const DScene* S = &S_;
-    const DParams* P = &P_;
     const DGrads* G = &G_;
     const DMat m = load_mat<MT>(S_, vc.mat);
     Rot<float> Rle = {1.0f, 0.0f};
