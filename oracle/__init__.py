@@ -230,42 +230,48 @@ def stats(reset: bool = True) -> dict:
     return dict(zip(keys, out.tolist()))
 
 
-def philox4x64(counter, key) -> np.ndarray:
+def _lib_or(library):
+    """The given oracle library (a copy built from other sources, as the tests that plant
+    mistakes use), else the oracle's own."""
+    return library if library is not None else lib()
+
+
+def philox4x64(counter, key, library=None) -> np.ndarray:
     c = np.ascontiguousarray(counter, np.uint64)
     k = np.ascontiguousarray(key, np.uint64)
     o = np.zeros(4, np.uint64)
-    lib().orc_philox(_p(c), _p(k), _p(o))
+    _lib_or(library).orc_philox(_p(c), _p(k), _p(o))
     return o
 
 
-def uniforms(seed, pass_id, stream, path, vertex) -> np.ndarray:
+def uniforms(seed, pass_id, stream, path, vertex, library=None) -> np.ndarray:
     u = np.zeros(8)
-    lib().orc_uniforms(seed, pass_id, stream, path, vertex, _p(u))
+    _lib_or(library).orc_uniforms(seed, pass_id, stream, path, vertex, _p(u))
     return u
 
 
-def fresnel_reflect(cos_i, eta_i, eta_t: complex) -> np.ndarray:
+def fresnel_reflect(cos_i, eta_i, eta_t: complex, library=None) -> np.ndarray:
     o = np.zeros(4)
-    lib().orc_fresnel_reflect(cos_i, eta_i, complex(eta_t).real, complex(eta_t).imag, _p(o))
+    _lib_or(library).orc_fresnel_reflect(cos_i, eta_i, complex(eta_t).real, complex(eta_t).imag, _p(o))
     return o
 
 
-def fresnel_transmit(cos_i, eta_i, eta_t) -> np.ndarray:
+def fresnel_transmit(cos_i, eta_i, eta_t, library=None) -> np.ndarray:
     o = np.zeros(4)
-    lib().orc_fresnel_transmit(cos_i, eta_i, eta_t, _p(o))
+    _lib_or(library).orc_fresnel_transmit(cos_i, eta_i, eta_t, _p(o))
     return o
 
 
-def camera_filter(filter_type: int, theta: float) -> np.ndarray:
+def camera_filter(filter_type: int, theta: float, library=None) -> np.ndarray:
     o = np.zeros(16)
-    lib().orc_camera_filter(filter_type, theta, _p(o))
+    _lib_or(library).orc_camera_filter(filter_type, theta, _p(o))
     return o.reshape(4, 4)
 
 
-def ggx(cos_h: float, cos_v: float, cos_vh: float, alpha: float) -> tuple[float, float]:
+def ggx(cos_h: float, cos_v: float, cos_vh: float, alpha: float, library=None) -> tuple[float, float]:
     """The oracle's GGX D(cos_h) and Smith G1(cos_v, cos_vh) for roughness alpha."""
     o = np.zeros(2)
-    lib().orc_ggx(float(cos_h), float(cos_v), float(cos_vh), float(alpha), _p(o))
+    _lib_or(library).orc_ggx(float(cos_h), float(cos_v), float(cos_vh), float(alpha), _p(o))
     return float(o[0]), float(o[1])
 
 

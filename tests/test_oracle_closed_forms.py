@@ -19,9 +19,13 @@ with the oracle's own formulas:
     goes to 0.01 -- with the light's Stokes vector given in a frame that shares its x
     axis with the s axis, so that every frame rotation on the way must cancel.
 
+The building blocks are held the same way: Philox against numpy's, the Fresnel
+coefficients at Brewster's angle, the GGX normalization and Smith masking identities,
+the polarizer as a projector, Malus's law, the white furnace, and cached suffix replay
+against taped AD.
 test_planted_mistake_is_caught builds copies of oracle.cpp with one line changed (a
-dropped term, a swapped operand, an inverted rotation or factor, a wrong sign) and
-requires the check named for each to fail on it.
+dropped term, a swapped operand, an inverted rotation or factor, a wrong sign or index)
+and requires the check named for each to fail on it.
 """
 import concurrent.futures
 import math
@@ -176,8 +180,136 @@ def check_rough_limit(make, kind, theta, light_size=8.0, s0_tol=0.05):
         assert px[0] == pytest.approx(ref[0], rel=s0_tol), (px[0], ref[0])
 
 
+class Oracle:
+    """The oracle a check runs on: the oracle's own library, or a copy built from oracle.cpp
+    with one line changed.  Called with a scene it returns that library's OracleScene."""
+
+    def __init__(self, mod, library=None):
+        self.mod, self.library = mod, library
+
+    def __call__(self, s):
+        return self.mod.OracleScene(s, library=self.library)
+
+
 def _real(oracle_mod):
-    return lambda s: oracle_mod.OracleScene(s)
+    return Oracle(oracle_mod)
+
+
+# ---------------------------------------------------------------- building blocks
+# The checks below hold the oracle's building blocks and its replay algebra; each expected
+# value comes from a published definition, a textbook closed form or the other derivative
+# route, so that the planted mistakes further down have something to fail against.
+def check_philox(make):
+    """Philox4x64-10 (Salmon et al. 2011) against numpy.random.Philox, which advances its
+    counter before producing a block."""
+    rng = np.random.default_rng(5)
+    for _ in range(8):
+        key = rng.integers(0, 2**63, 2, dtype=np.uint64)
+        ctr = rng.integers(0, 2**63, 4, dtype=np.uint64)
+        ref = np.random.Philox(key=key, counter=ctr).random_raw(4)
+        nxt = ctr.copy()
+        nxt[0] += np.uint64(1)
+        assert np.array_equal(make.mod.philox4x64(nxt, key, library=make.library), ref)
+
+
+def check_uniforms(make):
+    """The uniforms of (path, vertex): u = (w >> 8) 2^-24 for the low then the high 32-bit
+    half of each Philox output word, key (seed ^ pass * 0x9E3779B97F4A7C15, stream)."""
+    seed, pas, stream, path, vertex = 91, 1, 2, 987654321, 3
+    k0 = np.uint64(seed) ^ np.uint64((pas * 0x9E3779B97F4A7C15) % 2**64)
+    ref = np.random.Philox(key=[k0, np.uint64(stream)], counter=[path - 1, vertex, 0, 0]).random_raw(4)
+    words = []
+    for x in ref:
+        words += [int(x) & 0xFFFFFFFF, int(x) >> 32]
+    expect = np.array([(w >> 8) / 2**24 for w in words])
+    assert np.array_equal(make.mod.uniforms(seed, pas, stream, path, vertex, library=make.library), expect)
+
+
+def check_brewster(make, n=1.5):
+    """At Brewster's angle (tan theta = n) r_p = 0 and r_s = (1 - n^2) / (1 + n^2): the
+    reflection is A = B = r_s^2 / 2, C = S = 0."""
+    A, B, C, S = make.mod.fresnel_reflect(math.cos(math.atan(n)), 1.0, n, library=make.library)
+    rs = (1 - n * n) / (1 + n * n)
+    assert A == pytest.approx(rs * rs / 2, rel=1e-12) and B == pytest.approx(rs * rs / 2, rel=1e-12)
+    assert abs(C) < 1e-15 and abs(S) < 1e-15
+
+
+def _ggx_knots(alpha):
+    return [0.0, max(0.0, 1.0 - 4.0 * alpha * alpha), 1.0]
+
+
+def check_ggx_area(make, alpha=0.3):
+    """The GGX microfacet normals cover the macro-surface once: 2 pi int_0^1 D(mu) mu dmu = 1."""
+    integrate = pytest.importorskip("scipy.integrate")
+    D = lambda mu: make.mod.ggx(mu, 1.0, 1.0, alpha, library=make.library)[0]
+    k = _ggx_knots(alpha)
+    area = sum(integrate.quad(lambda m: D(m) * m, a, b, epsabs=1e-13, epsrel=1e-11, limit=400)[0]
+               for a, b in zip(k[:-1], k[1:]) if b > a)
+    assert 2.0 * math.pi * area == pytest.approx(1.0, rel=1e-8)
+
+
+def check_ggx_masking(make, alpha=0.5, theta_o=1.0):
+    """Smith masking normalizes the visible projected area (Heitz 2014):
+    G1(o) int max(0, o.h) D(h) dw_h = cos(theta_o).  It ties G1's alpha to D's."""
+    integrate = pytest.importorskip("scipy.integrate")
+    D = lambda mu: make.mod.ggx(mu, 1.0, 1.0, alpha, library=make.library)[0]
+    so, co = math.sin(theta_o), math.cos(theta_o)
+
+    def inner(mu):
+        s = math.sqrt(max(0.0, 1.0 - mu * mu))
+        return integrate.quad(lambda ph: max(0.0, so * s * math.cos(ph) + co * mu), 0.0, math.pi,
+                              epsabs=1e-12, limit=200)[0] * D(mu)
+
+    k = _ggx_knots(alpha)
+    proj = 2.0 * sum(integrate.quad(inner, a, b, epsabs=1e-10, epsrel=1e-8, limit=200)[0]
+                     for a, b in zip(k[:-1], k[1:]) if b > a)
+    g1 = make.mod.ggx(1.0, co, 1.0, alpha, library=make.library)[1]
+    assert g1 * proj == pytest.approx(co, rel=1e-6)
+
+
+def check_polarizer(make):
+    """The camera's ideal linear polarizer at theta, with its transmission axis along the
+    sensor's x axis at theta = 0: a rank-1 projector that sends unpolarized light to
+    (1, cos 2 theta, sin 2 theta, 0) / 2."""
+    for th in (0.4, 1.3):
+        P = make.mod.camera_filter(sg.FILTER_POLARIZER, th, library=make.library)
+        assert np.allclose(P @ P, P, atol=1e-15)
+        assert np.allclose(P @ [1, 0, 0, 0], [0.5, 0.5 * math.cos(2 * th), 0.5 * math.sin(2 * th), 0], atol=1e-15)
+
+
+def check_malus(make, alpha=0.3, theta=1.1, L=2.0):
+    """Unpolarized light through a sheet polarizer at alpha, then the camera polarizer at
+    theta: Malus's law, I = (L / 2) cos^2(theta - alpha)."""
+    s, job = sg.malus_scene(alpha, le=L)
+    job.thetas = [theta]
+    img = make(s).render(job, s.params())
+    assert np.allclose(img[0, :, :, 0], 0.5 * L * math.cos(theta - alpha) ** 2, rtol=1e-6, atol=1e-9)
+
+
+def check_furnace(make, a=0.6, e=1.5, depth=3):
+    """A closed diffuse box that emits e everywhere: every path carries e sum_{k<depth} a^k,
+    whatever its directions (cosine sampling weight a per bounce)."""
+    s, job = sg.furnace_scene(a, e)
+    job.max_depth = depth
+    img = make(s).render(job, s.params())
+    assert np.allclose(img[0, :, :, 0], e * sum(a**k for k in range(depth)), rtol=1e-12)
+
+
+def check_tape_equals_replay(make):
+    """Cached suffix replay (Sec. 4.3) against conventional taped AD over the whole path, on a
+    small scene with every material: a wrong suffix index, a transposed adjoint-row update
+    or a dropped term of the fold L_v = E_v + W_v L_{v+1} changes only the replay."""
+    s, job = sg.mixed_scene(width=10, spp=2, depth=5)
+    o = make(s)
+    img = o.render(job, s.params())
+    dI = np.random.default_rng(2).normal(size=img.shape)
+    g1 = o.gradient(job, s.params(), dI, mode="tape")
+    g2 = o.gradient(job, s.params(), dI, mode="replay")
+    for k in g1:
+        if len(g1[k]) == 0:
+            continue
+        assert np.linalg.norm(g1[k]) > 0, k
+        assert np.allclose(g1[k], g2[k], rtol=1e-9, atol=1e-10 * np.abs(g1[k]).max()), k
 
 
 def test_nee_mis_matches_polygon_irradiance(oracle_mod):
@@ -253,6 +385,32 @@ MUTANTS = [
      0, lambda m: check_smooth_reflection(m)),
     ("emitter_frame_reversed_for_nee", "M4<double> R = emitter_rot(L, -vt.wl);", "M4<double> R = emitter_rot(L, vt.wl);",
      0, lambda m: check_rough_limit(m, "conductor", 50.0, light_size=0.4, s0_tol=None)),
+    # building blocks: the counter-based generator, Fresnel, GGX, the elements, the depolarizer
+    ("philox_round_reads_wrong_word", "unsigned __int128 p1 = (unsigned __int128)M1 * c2;",
+     "unsigned __int128 p1 = (unsigned __int128)M1 * c1;", 0, check_philox),
+    ("philox_key_bumped_before_first_round", "if (r > 0) { k0 += W0; k1 += W1; }", "{ k0 += W0; k1 += W1; }", 0,
+     check_philox),
+    ("uniform_from_wrong_half", "r.u[2 * k] = (double)(lo >> 8) * (1.0 / 16777216.0);",
+     "r.u[2 * k] = (double)(hi >> 8) * (1.0 / 16777216.0);", 0, check_uniforms),
+    ("fresnel_rs_cosines_swapped", "Cx<T> a = cmul(ei, ci), b = cmul(eta_t, cos_t);",
+     "Cx<T> a = cmul(ei, cos_t), b = cmul(eta_t, ci);", 0, check_brewster),
+    ("fresnel_rp_negated", "Cx<T> rp = cdiv(csub(c, d), cadd(c, d));", "Cx<T> rp = cdiv(csub(d, c), cadd(c, d));", 0,
+     check_smooth_reflection),
+    ("ggx_D_drops_pi", "return a2 / (k * k * M_PI);", "return a2 / (k * k);", 0, check_ggx_area),
+    ("ggx_D_alpha_unsquared", "T a2 = alpha * alpha;", "T a2 = alpha;", 0, check_ggx_masking),
+    ("ggx_G1_alpha_unsquared", "sqrt(alpha * alpha * t2 + 1.0)", "sqrt(alpha * t2 + 1.0)", 0, check_ggx_masking),
+    ("polarizer_axis_along_y", "r.m[0][1] = T(0.5); r.m[1][0] = T(0.5);", "r.m[0][1] = T(-0.5); r.m[1][0] = T(-0.5);",
+     0, check_polarizer),
+    ("element_rotated_backwards", "return mmul(mmul(rot_cs<T>(c, -s), m), rot_cs<T>(c, s));",
+     "return mmul(mmul(rot_cs<T>(c, s), m), rot_cs<T>(c, -s));", 0, check_malus),
+    ("diffuse_drops_one_over_pi", "f[c].m[0][0] = alb[c] * (1.0 / M_PI);", "f[c].m[0][0] = alb[c];", 0, check_furnace),
+    # the cached suffix replay's algebra
+    ("replay_reads_own_suffix", "S4<Var> wl = mvec(e.W[c], Lc[v + 1][c]);", "S4<Var> wl = mvec(e.W[c], Lc[v][c]);", 0,
+     check_tape_equals_replay),
+    ("replay_adjoint_row_transposed", "sacc += arow[c][k] * ev[v].W[c].m[k][j];",
+     "sacc += arow[c][k] * ev[v].W[c].m[j][k];", 0, check_tape_equals_replay),
+    ("replay_fold_drops_emission", "for (int k = 0; k < 4; ++k) Lc[v][c].s[k] = ev[v].E[c].s[k] + wl.s[k];",
+     "for (int k = 0; k < 4; ++k) Lc[v][c].s[k] = wl.s[k];", 0, check_tape_equals_replay),
 ]
 
 
@@ -290,4 +448,4 @@ def test_planted_mistake_is_caught(oracle_mod, mutant_libs, name):
     check(_real(oracle_mod))                      # the unmodified oracle passes the check
     library = mutant_libs[name]
     with pytest.raises(AssertionError):
-        check(lambda s: oracle_mod.OracleScene(s, library=library))
+        check(Oracle(oracle_mod, library))
