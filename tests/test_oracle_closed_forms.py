@@ -21,8 +21,10 @@ with the oracle's own formulas:
 
 The building blocks are held the same way: Philox against numpy's, the Fresnel
 coefficients at Brewster's angle, the GGX normalization and Smith masking identities,
-the polarizer as a projector, Malus's law, the white furnace, and cached suffix replay
-against taped AD.
+the polarizer as a projector, Malus's law, the white furnace, cached suffix replay and
+the hybrid's exact configurations against taped AD, basic polarized PRB's O(sigma)
+convergence behind depolarizers (Sec. 4.1), and a flat normal map against the geometric
+normal.
 test_planted_mistake_is_caught builds copies of oracle.cpp with one line changed (a
 dropped term, a swapped operand, an inverted rotation or factor, a wrong sign or index)
 and requires the check named for each to fail on it.
@@ -349,6 +351,62 @@ def test_rough_dielectric_at_brewster_is_s_polarized(oracle_mod):
     assert abs(px[2]) < 2e-3 * px[0] and abs(px[3]) < 2e-3 * px[0]
 
 
+def check_hybrid_exact(make, k, gamma, eps):
+    """Hybrid cached replay (Sec. 4.4) in a configuration that recovers every missing suffix
+    exactly (gamma = 0 with eps = 0: inversion wherever det != 0, else recomputation; eps =
+    inf: recomputation only) equals taped AD on a small scene with every material."""
+    s, job = sg.mixed_scene(width=12, spp=2, depth=6)
+    o = make(s)
+    P = s.params()
+    dI = np.random.default_rng(1).normal(size=o.render(job, P).shape)
+    tape = o.gradient(job, P, dI, mode="tape")
+    g, routes = o.gradient_hybrid(job, P, dI, k, gamma, eps)
+    assert routes["inverse" if eps == 0.0 else "recompute"] > 0
+    for key in ("tex", "ior", "le", "sheet", "theta"):
+        if tape[key].size and np.linalg.norm(tape[key]) > 0:
+            assert np.linalg.norm(g[key] - tape[key]) < 1e-9 * np.linalg.norm(tape[key]), key
+
+
+def check_hybrid_scalar_furnace(make):
+    """The hybrid's scalar route is exact behind ideal depolarizers (the diffuse furnace)."""
+    s, job = sg.furnace_scene(0.5, 1.0)
+    job.max_depth = 12
+    o = make(s)
+    P = s.params()
+    dI = np.random.default_rng(2).normal(size=o.render(job, P).shape)
+    tape = o.gradient(job, P, dI, mode="tape")["tex"]
+    g, routes = o.gradient_hybrid(job, P, dI, 4, 0.5, 1e-6)
+    assert routes["scalar"] > 0
+    assert np.linalg.norm(g["tex"] - tape) < 1e-12 * np.linalg.norm(tape)
+
+
+def check_flat_normal_map(make):
+    """A flat tangent-space normal map (texel (0.5, 0.5, 1), n = 2c - 1 = (0, 0, 1)) shades
+    with the geometric normal: every path the map leaves unchanged carries the same value."""
+    sf, job = sg.normal_map_scene(flat=True)
+    s0, _ = sg.normal_map_scene(flat=True)
+    for m in s0.materials:
+        m.normal_tex = -1
+    _, pf, sig_f = make(sf).render(job, sf.params(), paths=True)
+    _, p0, sig_0 = make(s0).render(job, s0.params(), paths=True)
+    same = sig_f == sig_0
+    assert same.mean() >= 0.99
+    assert np.abs(pf[same] - p0[same]).max() <= 1e-12 * max(1.0, np.abs(p0).max())
+
+
+def check_pprb_furnace(make, sigma=1e-3):
+    """Basic polarized PRB behind ideal depolarizers (Sec. 4.1, case 2): the diffuse furnace's
+    albedo derivative is recovered with an error of the noise's order, below sigma / 2."""
+    s, job = sg.furnace_scene(0.5, 1.0)
+    job.max_depth = 4
+    o = make(s)
+    P = s.params()
+    dI = np.random.default_rng(1).normal(size=o.render(job, P).shape)
+    tape = o.gradient(job, P, dI, mode="tape")["tex"]
+    g = o.gradient(job, P, dI, mode="pprb", sigma=sigma)["tex"]
+    assert np.linalg.norm(g - tape) < 0.5 * sigma * np.linalg.norm(tape)
+
+
 # ---------------------------------------------------------------- planted mistakes
 # (name, text in oracle.cpp, replacement, which occurrence, the check that must catch it)
 _NEE = lambda m: check_nee_mis(m)
@@ -411,6 +469,20 @@ MUTANTS = [
      "sacc += arow[c][k] * ev[v].W[c].m[j][k];", 0, check_tape_equals_replay),
     ("replay_fold_drops_emission", "for (int k = 0; k < 4; ++k) Lc[v][c].s[k] = ev[v].E[c].s[k] + wl.s[k];",
      "for (int k = 0; k < 4; ++k) Lc[v][c].s[k] = wl.s[k];", 0, check_tape_equals_replay),
+    # the hybrid cached replay's recovery of the suffixes between checkpoints
+    ("hybrid_block_emission_after_throughput", "S4<double> be = mvec(bt[c], ev.E[c]);",
+     "S4<double> be = mvec(mmul(bt[c], ev.W[c]), ev.E[c]);", 0, lambda m: check_hybrid_exact(m, 4, 0.0, 0.0)),
+    ("hybrid_block_throughput_reversed", "bt[c] = mmul(bt[c], ev.W[c]);", "bt[c] = mmul(ev.W[c], bt[c]);", 0,
+     lambda m: check_hybrid_exact(m, 4, 0.0, 0.0)),
+    ("hybrid_recompute_skips_a_vertex", "for (int j = v + 1; j < std::min(next, n); ++j) {",
+     "for (int j = v + 2; j < std::min(next, n); ++j) {", 0, lambda m: check_hybrid_exact(m, 4, 0.0, float("inf"))),
+    ("hybrid_scalar_route_undivided", "Ln[c].s[0] = r.s[0] / bt[c].m[0][0];", "Ln[c].s[0] = r.s[0];", 0,
+     check_hybrid_scalar_furnace),
+    # the normal map's decoding and basic polarized PRB's inversion
+    ("normal_map_x_not_decoded", "T a = tex_lookup<T>(s, P, m.normal_tex, 0, vt.tu, vt.tv) * 2.0 - 1.0;",
+     "T a = tex_lookup<T>(s, P, m.normal_tex, 0, vt.tu, vt.tv);", 0, check_flat_normal_map),
+    ("pprb_emission_not_removed", "m[k][4] = L[c][k] - (T)ev[v].E[c].s[k];", "m[k][4] = L[c][k];", 0,
+     check_pprb_furnace),
 ]
 
 
