@@ -483,6 +483,9 @@ MUTANTS = [
      "T a = tex_lookup<T>(s, P, m.normal_tex, 0, vt.tu, vt.tv);", 0, check_flat_normal_map),
     ("pprb_emission_not_removed", "m[k][4] = L[c][k] - (T)ev[v].E[c].s[k];", "m[k][4] = L[c][k];", 0,
      check_pprb_furnace),
+    # sampling: the GGX half-vector pdf without the Jacobian 1 / (4 cos theta_oh) biases the lobe
+    ("ggx_pdf_drops_half_vector_jacobian", "return ggx_D<double>(ch, alpha) * ch / (4.0 * oh);",
+     "return ggx_D<double>(ch, alpha) * ch;", 0, lambda m: check_rough_limit(m, "conductor", 50.0)),
 ]
 
 
