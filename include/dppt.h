@@ -196,7 +196,9 @@ const char* dppt_version(void);
 /* Validate the scene, build its BVH (binned SAH) on the host and copy
  * geometry, materials, lights and cameras to the device.  The scene is owned
  * by the library until dppt_scene_destroy.  Errors: INVALID_ARG for bad
- * counts, indices or degenerate lights; OUT_OF_MEMORY; CUDA. */
+ * counts, indices or degenerate lights; UNSUPPORTED for a BVH whose
+ * traversal would need more than the kernels' 64-entry stack (a binary depth
+ * of 64 or more, or a 4-wide depth d with 3d + 1 >= 64); OUT_OF_MEMORY; CUDA. */
 dppt_status dppt_scene_upload(dppt_ctx* ctx, const dppt_scene_desc* desc, dppt_scene** out);
 void dppt_scene_destroy(dppt_scene* scene);
 /* info[0] = BVH nodes, [1] = triangles, [2] = spheres, [3] = device bytes, [4] = BVH depth */
