@@ -206,18 +206,30 @@ dppt_status dppt_scene_info(const dppt_scene* scene, int64_t info[5]);
 
 /* Phase 1 of PRB (Sec. 3.2): the primal image.  For each job, writes its
  * [num_angles][H][W][3][4] block of `image` (device, caller-owned) at
- * job.out_offset; the whole block is overwritten.  All jobs of the call run
- * in one launch (persistent or grid schedule). */
+ * job.out_offset; the whole block is overwritten.  With the grid or
+ * persistent schedule all jobs of the call run in one megakernel launch per
+ * depth bucket; the wavefront schedule runs them in waves of stage kernels
+ * (the sweep schedule's primal is the grid one).  Errors: INVALID_ARG for a
+ * null scene, image or params pointer that the scene needs, or a job whose
+ * camera, size, spp (1..2^20), max_depth (1..128), filter, angle count
+ * (1..512), theta_offset (>= 0; a filtered job needs params.theta) or
+ * out_offset (>= 0, a multiple of 4) is out of range, or a block size above
+ * the kernel's limit; OUT_OF_MEMORY when
+ * the workspace must grow and cannot; CUDA for a launch error. */
 dppt_status dppt_render_primal(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* jobs, int32_t njobs,
                                const dppt_params* params, float* image, void* stream);
 
 /* Phases 2+3 of PRB with cached suffix replay (Sec. 4.3, Fig. 2): for every
  * path of every job, a decorrelated primal pass stores the per-vertex
- * emission E_i and transport factor W_i in thread-local arrays, a backward
- * fold turns them into suffixes L[i] = E_i + W_i L[i+1], and the replay
- * regenerates the same path, differentiates the local vertex only and
- * multiplies by the cached L[i+1].  d_image holds dg/dI in the image layout;
- * gradients are ADDED into `grads`. */
+ * emission E_i and transport factor W_i (in thread-local arrays on the grid
+ * and persistent schedules, in the workspace's per-vertex records on the
+ * wavefront and sweep schedules), a backward fold turns them into suffixes
+ * L[i] = E_i + W_i L[i+1], and the replay regenerates the same path (or
+ * re-shades each vertex from its cached hit), differentiates the local
+ * vertex only and multiplies by the cached L[i+1].  d_image holds dg/dI in
+ * the image layout; gradients are ADDED into `grads`.  Errors: as
+ * render_primal, plus INVALID_ARG for a null grads or d_image and
+ * UNSUPPORTED for the P-PRB replay on the wavefront or sweep schedule. */
 dppt_status dppt_render_adjoint(dppt_ctx* ctx, const dppt_scene* scene, const dppt_job* jobs, int32_t njobs,
                                 const dppt_params* params, const float* d_image, const dppt_grads* grads,
                                 void* stream);
