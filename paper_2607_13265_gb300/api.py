@@ -229,7 +229,8 @@ def _c_params(p: dict) -> L.Params:
 
 def render_primal(ctx: Context, gs: GpuScene, batch: JobBatch, params: dict, image: torch.Tensor | None = None,
                   stream=None) -> torch.Tensor:
-    """Phase 1: the primal Stokes images of all jobs, in one launch."""
+    """Phase 1: the primal Stokes images of all jobs (one megakernel launch per depth bucket, or the
+    wavefront's stage kernels, by the context's schedule)."""
     if image is None:
         image = torch.empty(batch.image_floats, dtype=torch.float32, device=params["tex"].device)
     cp = _c_params(params)
