@@ -193,11 +193,15 @@ class JobBatch:
 
 
 def pack_jobs(jobs, path_sig: torch.Tensor | None = None) -> JobBatch:
-    """Lay the jobs' images out back to back and collect their filter angles."""
+    """Lay the jobs' images out back to back and collect their filter angles.  A job seen
+    through a camera filter needs at least one angle: with none, the angle offsets of the
+    later jobs would no longer match the angle vector."""
     arr = (L.Job * len(jobs))()
     off, toff, offsets, thetas = 0, 0, [], []
     sig_off = 0
     for i, j in enumerate(jobs):
+        if j.filter != FILTER_NONE and len(j.thetas) == 0:
+            raise ValueError(f"job {i}: a camera filter needs at least one angle")
         nang = j.num_angles
         arr[i] = L.Job(j.camera, j.width, j.height, j.spp, j.max_depth, j.filter,
                        nang if j.filter != FILTER_NONE else 1, toff if j.filter != FILTER_NONE else 0,
