@@ -82,3 +82,19 @@ def test_adjoint_jobs_change_only_the_pass():
         assert (a.camera, a.width, a.height, a.spp, a.max_depth, a.seed, a.stream, a.filter, a.thetas) == \
             (j.camera, j.width, j.height, j.spp, j.max_depth, j.seed, j.stream, j.filter, j.thetas)
     assert [j.pass_id for j in jobs] == [0, 0, 0, 1, 0]
+
+
+def test_raw_batch_drops_the_filters_and_keeps_the_paths():
+    """The fused L2 loss reads each job's raw image [H][W][3][4] at its raw offset: the raw
+    batch has the same jobs without their filters, one image each, back to back."""
+    jobs = _jobs()
+    rb = api.raw_batch(api.pack_jobs(jobs))
+    sizes = [j.num_pixels * 12 for j in jobs]
+    assert rb.offsets == np.concatenate([[0], np.cumsum(sizes)[:-1]]).tolist()
+    assert rb.image_floats == sum(sizes)
+    for i, j in enumerate(jobs):
+        c = rb.c_jobs[i]
+        assert c.filter == F_NONE and c.num_angles == 1
+        assert (c.camera, c.width, c.height, c.spp, c.max_depth, c.seed, c.stream, c.pass_) == \
+            (j.camera, j.width, j.height, j.spp, j.max_depth, j.seed, j.stream, j.pass_id)
+    assert jobs[1].filter == F_POL and len(jobs[1].thetas) == 3      # the caller's jobs are untouched
