@@ -24,9 +24,6 @@ from __future__ import annotations
 import argparse
 import copy
 import json
-import math
-import os
-import sys
 
 import numpy as np
 

@@ -1,7 +1,6 @@
 """Deep paths on the GPU: the deep-path benchmark module at a reduced image size runs every
 schedule at depths 8 and 128 and the schedules agree on the gradient (they trace the same
 paths; only the order of the floating-point gradient sums differs)."""
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu

@@ -8,7 +8,6 @@ from it (polarizers and diffuse bounces have det 0, retarders det 1).  The scala
 tested on the diffuse furnace, where every block throughput has DI = 0 exactly.  Every
 schedule runs the hybrid: the megakernels trace a recomputed block again, the wavefront
 re-shades it from the hits it keeps per vertex."""
-import math
 
 import numpy as np
 import pytest
