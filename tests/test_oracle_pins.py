@@ -334,3 +334,20 @@ def test_central_differences(mixed):
         an = g[name][idx]
         assert an != 0.0, (name, idx)
         assert abs(an - fd) <= 1e-6 * max(1.0, abs(fd)), (name, idx, an, fd)
+
+
+def test_conventional_ad_tape_model(oracle_mod):
+    """The memory model of conventional reverse AD (oracle/tape_memory.py) on a small sample of
+    the deep-stack workload: the tape holds a fixed number of nodes per vertex, so it grows in
+    proportion to the path's vertices, while the replay's cache holds 124 B per vertex."""
+    from oracle import tape_memory
+    rows = tape_memory.main(["--depths", "4", "16", "--width", "8", "--height", "5"])
+    assert [r["depth"] for r in rows] == [4, 16]
+    for r in rows:
+        assert r["tape_nodes_per_path"] > 0 and r["vertices_per_path"] > 1
+        assert r["conv_ad_bytes_16B"] == pytest.approx(4 * r["conv_ad_bytes_4B_lower_bound"])
+        assert r["cache_bytes_full"] == pytest.approx(r["vertices_per_path"] * 1280 * 720 * 124)
+    shallow, deep = rows
+    assert deep["vertices_per_path"] > 2 * shallow["vertices_per_path"]
+    assert deep["tape_nodes_per_vertex"] == pytest.approx(shallow["tape_nodes_per_vertex"], rel=0.05)
+    assert deep["conv_ad_bytes_16B"] > 10 * deep["cache_bytes_full"]
