@@ -407,6 +407,27 @@ def check_pprb_furnace(make, sigma=1e-3):
     assert np.linalg.norm(g - tape) < 0.5 * sigma * np.linalg.norm(tape)
 
 
+def check_camera(make, W=24, H=16, vfov=40.0, dist=5.0):
+    """The pinhole camera: pixel (0, 0) is the top-left; the vertical field of view is vfov; a
+    world point at (x, y) in the plane dist in front of a camera looking down -z with up +y
+    lands at pixel column W/2 (1 + x / (dist t a)) and row H/2 (1 - y / (dist t)),
+    t = tan(vfov / 2), a = W / H.  Emitting squares half a pixel wide, centred on chosen pixel
+    centres, must light exactly those pixels."""
+    s = sg.Scene()
+    t, a = math.tan(math.radians(vfov) / 2), W / H
+    side = 0.5 * 2 * t / H * dist                   # half a pixel, in world units
+    targets = [(3, 2), (20, 13), (12, 4), (1, 12)]
+    for px, py in targets:
+        x = ((px + 0.5) / W * 2 - 1) * dist * t * a
+        y = (1 - (py + 0.5) / H * 2) * dist * t
+        s.add_light((x - side / 2, y - side / 2, 0.0), (side, 0, 0), (0, side, 0), 1.0)
+    s.add_camera((0, 0, dist), (0, 0, 0), (0, 1, 0), vfov)
+    job = sg.Job(camera=0, width=W, height=H, spp=64, max_depth=1)
+    img = make(s).render(job, s.params())[0, :, 0, 0].reshape(H, W)
+    lit = {(int(c), int(r)) for r, c in zip(*np.nonzero(img > 0))}
+    assert lit == set(targets), sorted(lit)
+
+
 # ---------------------------------------------------------------- planted mistakes
 # (name, text in oracle.cpp, replacement, which occurrence, the check that must catch it)
 _NEE = lambda m: check_nee_mis(m)
@@ -486,6 +507,15 @@ MUTANTS = [
     # sampling: the GGX half-vector pdf without the Jacobian 1 / (4 cos theta_oh) biases the lobe
     ("ggx_pdf_drops_half_vector_jacobian", "return ggx_D<double>(ch, alpha) * ch / (4.0 * oh);",
      "return ggx_D<double>(ch, alpha) * ch;", 0, lambda m: check_rough_limit(m, "conductor", 50.0)),
+    # the pinhole camera
+    ("camera_rows_flipped", "double sy = (1.0 - 2.0 * (py + jv) / H) * c.tanh;",
+     "double sy = (2.0 * (py + jv) / H - 1.0) * c.tanh;", 0, check_camera),
+    ("camera_right_reversed", "cm.right = normalize(cross(cm.fwd, ld3(c + 6)));",
+     "cm.right = normalize(cross(ld3(c + 6), cm.fwd));", 0, check_camera),
+    ("camera_aspect_dropped", "double sx = (2.0 * (px + ju) / W - 1.0) * c.tanh * aspect;",
+     "double sx = (2.0 * (px + ju) / W - 1.0) * c.tanh;", 0, check_camera),
+    ("camera_full_field_angle", "cm.tanh = std::tan(0.5 * c[9] * M_PI / 180.0);",
+     "cm.tanh = std::tan(c[9] * M_PI / 180.0);", 0, check_camera),
 ]
 
 
@@ -524,3 +554,7 @@ def test_planted_mistake_is_caught(oracle_mod, mutant_libs, name):
     library = mutant_libs[name]
     with pytest.raises(AssertionError):
         check(Oracle(oracle_mod, library))
+
+
+def test_pinhole_camera(oracle_mod):
+    check_camera(_real(oracle_mod))
