@@ -428,6 +428,40 @@ def check_camera(make, W=24, H=16, vfov=40.0, dist=5.0):
     assert lit == set(targets), sorted(lit)
 
 
+def check_intersections(make):
+    """Closest hits against analytic distances: the triangle (0,0,0), (1,0,0), (0,1,0) in
+    z = 0 and a sphere of radius 0.5 at (3, 0, 0); rays just inside and outside the triangle
+    (both faces), the sphere's near root from outside, its exit from inside, a chord at
+    height 0.4 (t = 2 - sqrt(0.25 - 0.16)), a miss, and an oblique ray whose hit is the smaller
+    root of |o + t d - c|^2 = r^2.  The tree and the brute-force loop must both give them."""
+    s = sg.Scene()
+    m = s.add_material(sg.Material(sg.MAT_DIFFUSE))
+    s.add_mesh(np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], float), np.array([[0, 1, 2]]), m, np.zeros((3, 2)))
+    s.add_sphere((3, 0, 0), 0.5, m)
+    s.add_light((10, 10, 10), (1, 0, 0), (0, 1, 0), 1.0)
+    s.add_camera((0, 0, 5), (0, 0, 0), (0, 1, 0), 40.0)
+    sph = len(s.tris)                              # spheres are numbered after the triangles
+    d_ob = np.array([0.3, 0.1, -1.0]) / math.sqrt(1.1)
+    o_ob = np.array([2.8, -0.1, 2.0])
+    lc = o_ob - np.array([3.0, 0.0, 0.0])
+    b = float(lc @ d_ob)
+    t_ob = -b - math.sqrt(b * b - (float(lc @ lc) - 0.25))
+    d_tri = np.array([0.1, 0.0, -1.0]) / math.sqrt(1.01)
+    rays = [((0.2, 0.2, 1), (0, 0, -1), 0, 1.0), ((0.2, 0.2, -1), (0, 0, 1), 0, 1.0),
+            ((0.25, 0.25, 1), d_tri, 0, math.sqrt(1.01)),
+            ((0.6, 0.6, 1), (0, 0, -1), -1, None), ((-0.2, 0.3, 1), (0, 0, -1), -1, None),
+            ((3, 0, 2), (0, 0, -1), sph, 1.5), ((3, 0, 0), (1, 0, 0), sph, 0.5),
+            ((3, 0.4, 2), (0, 0, -1), sph, 2.0 - math.sqrt(0.25 - 0.16)), ((3, 0.6, 2), (0, 0, -1), -1, None),
+            (o_ob, d_ob, sph, t_ob)]
+    o = make(s)
+    for org, d, prim, t_hit in rays:
+        for brute in (False, True):
+            p, th = o.closest(org, d, brute=brute)
+            assert p == prim, (org, d, brute, p)
+            if prim >= 0:
+                assert th == pytest.approx(t_hit, rel=1e-12), (org, d, brute, th, t_hit)
+
+
 # ---------------------------------------------------------------- planted mistakes
 # (name, text in oracle.cpp, replacement, which occurrence, the check that must catch it)
 _NEE = lambda m: check_nee_mis(m)
@@ -516,6 +550,15 @@ MUTANTS = [
      "double sx = (2.0 * (px + ju) / W - 1.0) * c.tanh;", 0, check_camera),
     ("camera_full_field_angle", "cm.tanh = std::tan(0.5 * c[9] * M_PI / 180.0);",
      "cm.tanh = std::tan(c[9] * M_PI / 180.0);", 0, check_camera),
+    # ray intersection
+    ("triangle_u_lower_bound_dropped", "if (u < 0.0 || u > 1.0) return -1.0;", "if (u > 1.0) return -1.0;", 0,
+     check_intersections),
+    ("triangle_tests_w_not_u_plus_w", "if (w < 0.0 || u + w > 1.0) return -1.0;", "if (w < 0.0 || w > 1.0) return -1.0;",
+     0, check_intersections),
+    ("sphere_radius_unsquared", "double disc = rad * rad - dot(f, f);", "double disc = rad - dot(f, f);", 0,
+     check_intersections),
+    ("sphere_far_root_first", "if (t0 > 0.0 && t0 < tmax) return t0;", "if (t1 > 0.0 && t1 < tmax) return t1;", 0,
+     check_intersections),
 ]
 
 
@@ -558,3 +601,7 @@ def test_planted_mistake_is_caught(oracle_mod, mutant_libs, name):
 
 def test_pinhole_camera(oracle_mod):
     check_camera(_real(oracle_mod))
+
+
+def test_ray_intersections(oracle_mod):
+    check_intersections(_real(oracle_mod))
