@@ -65,6 +65,8 @@ def _configure(L):
     L.orc_camera_filter.argtypes = [i32, dbl, P]
     L.orc_csqrt.argtypes = [dbl, dbl, P]
     L.orc_ggx.argtypes = [dbl, dbl, dbl, dbl, P]
+    L.orc_tex_lookup.restype = dbl
+    L.orc_tex_lookup.argtypes = [i32, i32, i32, P, i32, dbl, dbl]
     L.orc_closest.restype = i32
     L.orc_closest.argtypes = [P, P, P, i32, P]
     L.orc_stats.argtypes = [P, i32]
@@ -273,6 +275,13 @@ def ggx(cos_h: float, cos_v: float, cos_vh: float, alpha: float, library=None) -
     o = np.zeros(2)
     _lib_or(library).orc_ggx(float(cos_h), float(cos_v), float(cos_vh), float(alpha), _p(o))
     return float(o[0]), float(o[1])
+
+
+def tex_lookup(texels: np.ndarray, c: int, u: float, v: float, library=None) -> float:
+    """The oracle's bilinear lookup of channel c at (u, v) in texels [h][w][ch]."""
+    t = np.ascontiguousarray(texels, np.float64)
+    h, w, ch = t.shape
+    return float(_lib_or(library).orc_tex_lookup(w, h, ch, _p(t), c, float(u), float(v)))
 
 
 def csqrt(z: complex) -> complex:

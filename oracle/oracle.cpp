@@ -1550,6 +1550,15 @@ void orc_ggx(double cos_h, double cos_v, double cos_vh, double alpha, double* ou
     out[0] = ggx_D<double>(cos_h, alpha);
     out[1] = ggx_G1<double>(cos_v, cos_vh, alpha);
 }
+// bilinear texture lookup of channel c at (u, v) in a w x h texture of ch channels, texels
+// [h][w][ch] in `texels`
+double orc_tex_lookup(int w, int h, int ch, const double* texels, int c, double u, double v) {
+    Scene s;
+    s.tex.push_back({0, w, h, ch});
+    Layout lay{};
+    Params<double> P{texels, lay};
+    return tex_lookup<double>(s, P, 0, c, u, v);
+}
 void orc_csqrt(double re, double im, double* out) {
     Cx<double> r = csqrt(Cx<double>{re, im});
     out[0] = r.re; out[1] = r.im;

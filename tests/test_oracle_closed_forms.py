@@ -462,6 +462,31 @@ def check_intersections(make):
                 assert th == pytest.approx(t_hit, rel=1e-12), (org, d, brute, th, t_hit)
 
 
+def check_texture(make):
+    """Bilinear filtering of texels [h][w][ch] with texel centres at ((i + 1/2) / w,
+    (j + 1/2) / h) and wrap-around addressing: a texel centre returns that texel, a midpoint
+    between two centres their mean, the centre of four texels their mean, and the seam at
+    u = 0 (or v = 0) mixes the last and first columns (rows); u + 1 reads what u reads."""
+    w, h, ch = 5, 4, 2
+    tex = np.random.default_rng(9).uniform(0.1, 0.9, (h, w, ch))
+    look = lambda c, u, v: make.mod.tex_lookup(tex, c, u, v, library=make.library)
+    for c in range(ch):
+        for j in range(h):
+            for i in range(w):
+                assert look(c, (i + 0.5) / w, (j + 0.5) / h) == pytest.approx(tex[j, i, c], abs=1e-15)
+                i1, j1 = (i + 1) % w, (j + 1) % h
+                assert look(c, (i + 1.0) / w, (j + 0.5) / h) == pytest.approx((tex[j, i, c] + tex[j, i1, c]) / 2,
+                                                                              abs=1e-15)
+                assert look(c, (i + 0.5) / w, (j + 1.0) / h) == pytest.approx((tex[j, i, c] + tex[j1, i, c]) / 2,
+                                                                              abs=1e-15)
+                quad = (tex[j, i, c] + tex[j, i1, c] + tex[j1, i, c] + tex[j1, i1, c]) / 4
+                assert look(c, (i + 1.0) / w, (j + 1.0) / h) == pytest.approx(quad, abs=1e-15)
+        assert look(c, 0.0, 0.5 / h) == pytest.approx((tex[0, 0, c] + tex[0, w - 1, c]) / 2, abs=1e-15)
+        assert look(c, 0.5 / w, 0.0) == pytest.approx((tex[0, 0, c] + tex[h - 1, 0, c]) / 2, abs=1e-15)
+        assert look(c, 1.37, 0.61) == pytest.approx(look(c, 0.37, 0.61), abs=1e-14)
+        assert look(c, -0.21, 0.3) == pytest.approx(look(c, 0.79, 0.3), abs=1e-14)
+
+
 # ---------------------------------------------------------------- planted mistakes
 # (name, text in oracle.cpp, replacement, which occurrence, the check that must catch it)
 _NEE = lambda m: check_nee_mis(m)
@@ -559,6 +584,15 @@ MUTANTS = [
      check_intersections),
     ("sphere_far_root_first", "if (t0 > 0.0 && t0 < tmax) return t0;", "if (t1 > 0.0 && t1 < tmax) return t1;", 0,
      check_intersections),
+    # texture filtering
+    ("texture_half_texel_offset_dropped", "double x = u * (double)t.w - 0.5, y = v * (double)t.h - 0.5;",
+     "double x = u * (double)t.w, y = v * (double)t.h - 0.5;", 0, check_texture),
+    ("texture_tap_column_swapped", "tp.idx[1] = t.off + (ya * t.w + xb) * t.ch;",
+     "tp.idx[1] = t.off + (ya * t.w + xa) * t.ch;", 0, check_texture),
+    ("texture_clamped_not_wrapped", "auto wrap = [](int64_t a, int64_t n) { int64_t m = a % n; return m < 0 ? m + n : m; };",
+     "auto wrap = [](int64_t a, int64_t n) { int64_t m = a % n; return m < 0 ? 0 : m; };", 0, check_texture),
+    ("texture_tap_index_transposed", "tp.idx[0] = t.off + (ya * t.w + xa) * t.ch;",
+     "tp.idx[0] = t.off + (xa * t.h + ya) * t.ch;", 0, check_texture),
 ]
 
 
@@ -605,3 +639,7 @@ def test_pinhole_camera(oracle_mod):
 
 def test_ray_intersections(oracle_mod):
     check_intersections(_real(oracle_mod))
+
+
+def test_texture_filtering(oracle_mod):
+    check_texture(_real(oracle_mod))
