@@ -1,6 +1,7 @@
 """CPU checks of the boundary: the C-ABI library builds, loads and exports every
-symbol include/dppt.h declares; the ctypes structures match the header's layout.
-No compute call is made (there may be no GPU here)."""
+symbol include/dppt.h declares; the ctypes structures match the header's layout; every
+entry point turns null arguments and bad devices into status codes.  No compute call is
+made (there may be no GPU here)."""
 import ctypes
 import os
 import re
@@ -95,3 +96,30 @@ def test_missing_library_fails_loudly(tmp_path):
             _lib.load(str(tmp_path / "missing.so"))
     finally:
         _lib._lib = saved
+
+
+def test_null_arguments_return_status_codes(lib):
+    """Host-side fault handling: every entry point called with a null context and null or zero
+    arguments returns DPPT_ERR_INVALID_ARG (the void ones return), touching no device."""
+    from paper_2607_13265_gb300 import _lib
+    ints = (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t)
+    for name, (res, args) in sorted(_lib.SIGNATURES.items()):
+        vals = [0 if a in ints else 0.0 if a in (ctypes.c_float, ctypes.c_double) else None for a in args]
+        r = getattr(lib, name)(*vals)
+        if name == "dppt_version":
+            continue
+        if name == "dppt_last_error":
+            assert r.decode() == "null context"
+        elif res is None:
+            assert r is None, name
+        else:
+            assert r == -1, (name, r)               # DPPT_ERR_INVALID_ARG
+
+
+def test_create_rejects_bad_devices(lib):
+    import torch
+    ctx = ctypes.c_void_p()
+    for dev in (-1, 1 << 20):
+        assert lib.dppt_create(ctypes.byref(ctx), dev) == -1 and not ctx.value
+    if not torch.cuda.is_available():            # no device at all: a status code, not a crash
+        assert lib.dppt_create(ctypes.byref(ctx), 0) == -1 and not ctx.value
