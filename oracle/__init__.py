@@ -65,6 +65,8 @@ def _configure(L):
     L.orc_camera_filter.argtypes = [i32, dbl, P]
     L.orc_csqrt.argtypes = [dbl, dbl, P]
     L.orc_ggx.argtypes = [dbl, dbl, dbl, dbl, P]
+    L.orc_depol_index.restype = dbl
+    L.orc_depol_index.argtypes = [P]
     L.orc_tex_lookup.restype = dbl
     L.orc_tex_lookup.argtypes = [i32, i32, i32, P, i32, dbl, dbl]
     L.orc_closest.restype = i32
@@ -275,6 +277,12 @@ def ggx(cos_h: float, cos_v: float, cos_vh: float, alpha: float, library=None) -
     o = np.zeros(2)
     _lib_or(library).orc_ggx(float(cos_h), float(cos_v), float(cos_vh), float(alpha), _p(o))
     return float(o[0]), float(o[1])
+
+
+def depol_index(m: np.ndarray, library=None) -> float:
+    """The oracle's depolarization index of a 4x4 Mueller matrix (the hybrid's scalar-route test)."""
+    a = np.ascontiguousarray(m, np.float64).reshape(16)
+    return float(_lib_or(library).orc_depol_index(_p(a)))
 
 
 def tex_lookup(texels: np.ndarray, c: int, u: float, v: float, library=None) -> float:

@@ -1550,6 +1550,12 @@ void orc_ggx(double cos_h, double cos_v, double cos_vh, double alpha, double* ou
     out[0] = ggx_D<double>(cos_h, alpha);
     out[1] = ggx_G1<double>(cos_v, cos_vh, alpha);
 }
+// depolarization index (Gil and Bernabeu) of a Mueller matrix m16, row-major
+double orc_depol_index(const double* m16) {
+    M4<double> m;
+    for (int i = 0; i < 4; ++i) for (int j = 0; j < 4; ++j) m.m[i][j] = m16[4 * i + j];
+    return depol_index(m);
+}
 // bilinear texture lookup of channel c at (u, v) in a w x h texture of ch channels, texels
 // [h][w][ch] in `texels`
 double orc_tex_lookup(int w, int h, int ch, const double* texels, int c, double u, double v) {

@@ -487,6 +487,25 @@ def check_texture(make):
         assert look(c, -0.21, 0.3) == pytest.approx(look(c, 0.79, 0.3), abs=1e-14)
 
 
+def check_depolarization_index(make):
+    """The depolarization index of Gil and Bernabeu, sqrt(sum m_ij^2 - m00^2) / (sqrt(3) m00),
+    which the hybrid replay (Sec. 4.4) compares with gamma: 1 for every non-depolarizing
+    operator (identity, a frame rotation, an ideal polarizer, a Fresnel reflection), 0 for the
+    ideal depolarizer that keeps only M00 (Sec. 4.1), a for the partial depolarizer
+    diag(1, a, a, a), and independent of the operator's scale."""
+    di = lambda m: make.mod.depol_index(np.asarray(m, float), library=make.library)
+    c, s = math.cos(0.8), math.sin(0.8)
+    rot = [[1, 0, 0, 0], [0, c, s, 0], [0, -s, c, 0], [0, 0, 0, 1]]
+    A, B, C, S = make.mod.fresnel_reflect(0.6, 1.0, complex(0.2, 3.0))
+    fres = [[A, B, 0, 0], [B, A, 0, 0], [0, 0, C, S], [0, 0, -S, C]]
+    pol = make.mod.camera_filter(sg.FILTER_POLARIZER, 0.4)
+    for m in (np.eye(4), rot, fres, pol, 3.5 * np.asarray(pol)):
+        assert di(m) == pytest.approx(1.0, abs=1e-12)
+    assert di(np.diag([0.7, 0, 0, 0])) == 0.0
+    for a in (0.1, 0.5, 0.9):
+        assert di(np.diag([2.0, 2 * a, 2 * a, 2 * a])) == pytest.approx(a, abs=1e-14)
+
+
 # ---------------------------------------------------------------- planted mistakes
 # (name, text in oracle.cpp, replacement, which occurrence, the check that must catch it)
 _NEE = lambda m: check_nee_mis(m)
@@ -593,6 +612,14 @@ MUTANTS = [
      "auto wrap = [](int64_t a, int64_t n) { int64_t m = a % n; return m < 0 ? 0 : m; };", 0, check_texture),
     ("texture_tap_index_transposed", "tp.idx[0] = t.off + (ya * t.w + xa) * t.ch;",
      "tp.idx[0] = t.off + (xa * t.h + ya) * t.ch;", 0, check_texture),
+    # the hybrid's depolarization index
+    ("depol_index_three_for_root_three",
+     "return std::sqrt(std::max(0.0, s2 - m.m[0][0] * m.m[0][0])) / (std::sqrt(3.0) * m.m[0][0]);",
+     "return std::sqrt(std::max(0.0, s2 - m.m[0][0] * m.m[0][0])) / (3.0 * m.m[0][0]);", 0,
+     check_depolarization_index),
+    ("depol_index_keeps_m00",
+     "return std::sqrt(std::max(0.0, s2 - m.m[0][0] * m.m[0][0])) / (std::sqrt(3.0) * m.m[0][0]);",
+     "return std::sqrt(std::max(0.0, s2)) / (std::sqrt(3.0) * m.m[0][0]);", 0, check_depolarization_index),
 ]
 
 
@@ -643,3 +670,7 @@ def test_ray_intersections(oracle_mod):
 
 def test_texture_filtering(oracle_mod):
     check_texture(_real(oracle_mod))
+
+
+def test_depolarization_index(oracle_mod):
+    check_depolarization_index(_real(oracle_mod))
